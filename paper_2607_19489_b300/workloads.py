@@ -1,0 +1,275 @@
+"""Seeded synthetic AMR hierarchies (inputs only; none of the solver's arithmetic).
+
+A hierarchy is a graded octree over the unit box (Sec. 3.2 of the paper): per
+AMR level l in [lmin, lmax] a list of leaf cells (integer ijk in [0, 2^l)) with
+masses.  Refined cells are implied (they are the parents of finer cells).
+Every generator is deterministic: random numbers come from a counter-based
+SplitMix64 stream keyed by (seed, stream, counter), so the same inputs are
+produced on any machine.
+
+The density recipes follow the workloads the method is measured on:
+Plummer spheres sampled at cell centres with uniform or lognormal noise,
+nested refined boxes, Gaussian blobs (Sec. 4 uses NFW halos and uniform
+spheres built from particle deposits; those need the paper's initial
+conditions, which stand in here as analytic profiles).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+_GOLD = np.uint64(0x9E3779B97F4A7C15)
+_C1 = np.uint64(0xBF58476D1CE4E5B9)
+_C2 = np.uint64(0x94D049BB133111EB)
+_STREAM = np.uint64(0xD1B54A32D192ED03)
+
+
+def _splitmix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) on uint64 arrays (wrapping)."""
+    with np.errstate(over="ignore"):
+        z = z + _GOLD
+        z = (z ^ (z >> np.uint64(30))) * _C1
+        z = (z ^ (z >> np.uint64(27))) * _C2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, stream: int, counter: np.ndarray | int) -> np.ndarray:
+    """U[0,1) doubles from (seed, stream, counter) with 53 random bits."""
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) * _GOLD + np.uint64(stream) * _STREAM + c
+    z = _splitmix64(_splitmix64(z))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, stream: int, counter: np.ndarray | int) -> np.ndarray:
+    """Standard normal by Box-Muller from two independent uniform streams."""
+    u1 = uniform(seed, 2 * stream + 1, counter)
+    u2 = uniform(seed, 2 * stream + 2, counter)
+    return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+
+@dataclass
+class Hierarchy:
+    """Leaf cells per AMR level; ijk[k], mass[k] belong to level lmin + k."""
+
+    lmin: int
+    lmax: int
+    ijk: list = field(default_factory=list)    # int32 [n, 3] per level
+    mass: list = field(default_factory=list)   # float64 [n] per level
+    name: str = ""
+
+    @property
+    def levels(self):
+        return list(range(self.lmin, self.lmax + 1))
+
+    def n(self, level: int) -> int:
+        return int(self.ijk[level - self.lmin].shape[0])
+
+    @property
+    def n_cells(self) -> int:
+        return int(sum(a.shape[0] for a in self.ijk))
+
+    def total_mass(self) -> float:
+        return float(sum(m.sum() for m in self.mass))
+
+    def centres(self, level: int) -> np.ndarray:
+        return (self.ijk[level - self.lmin].astype(np.float64) + 0.5) * 2.0 ** (-level)
+
+    def copy(self) -> "Hierarchy":
+        return Hierarchy(self.lmin, self.lmax, [a.copy() for a in self.ijk],
+                         [m.copy() for m in self.mass], self.name)
+
+
+# ---------------------------------------------------------------------------
+# Geometry: which cells are refined at each level.
+
+def _grid(n: int) -> np.ndarray:
+    ax = np.arange(n, dtype=np.int32)
+    g = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), axis=-1).reshape(-1, 3)
+    return g
+
+
+def leaves_from_refined(lmin: int, lmax: int, refined: dict) -> list:
+    """Leaf cells per level, given boolean refined masks per level.
+
+    refined[l] is a dense bool array of shape (2^l,)*3 for l in [lmin, lmax-1];
+    a level l+1 cell exists iff its parent is refined.  Returns a list of int32
+    [n,3] leaf arrays for levels lmin..lmax (lexicographic order).
+    """
+    out = []
+    exists = np.ones((2 ** lmin,) * 3, dtype=bool)
+    for l in range(lmin, lmax + 1):
+        ref = refined.get(l)
+        if ref is None or l == lmax:
+            ref = np.zeros_like(exists)
+        leaf = exists & ~ref
+        out.append(np.argwhere(leaf).astype(np.int32))
+        if l < lmax:
+            exists = np.repeat(np.repeat(np.repeat(exists & ref, 2, 0), 2, 1), 2, 2)
+    return out
+
+
+def graded_filter(refined_coarse: np.ndarray, cand_fine: np.ndarray) -> np.ndarray:
+    """Keep candidate refinements at level l+1 allowed by the graded rule.
+
+    A level-(l+1) cell may be refined only if the 3^3 neighbours of its father
+    (level l) are all refined (Sec. 3.2).  refined_coarse: bool (2^l)^3;
+    cand_fine: bool (2^(l+1))^3.
+    """
+    n = refined_coarse.shape[0]
+    pad = np.pad(refined_coarse, 1, constant_values=True)  # outside the box: no constraint
+    ok = np.ones_like(refined_coarse)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                ok &= pad[1 + dx:1 + dx + n, 1 + dy:1 + dy + n, 1 + dz:1 + dz + n]
+    ok &= refined_coarse
+    ok_f = np.repeat(np.repeat(np.repeat(ok, 2, 0), 2, 1), 2, 2)
+    return cand_fine & ok_f
+
+
+def nested_boxes(lmin: int, boxes: list) -> dict:
+    """Refined masks for nested boxes: boxes[k] = (lo, hi) in level (lmin+k) cells,
+    half-open, the cells of level lmin+k that are refined."""
+    refined = {}
+    for k, (lo, hi) in enumerate(boxes):
+        l = lmin + k
+        m = np.zeros((2 ** l,) * 3, dtype=bool)
+        lo3 = np.broadcast_to(np.asarray(lo), (3,))
+        hi3 = np.broadcast_to(np.asarray(hi), (3,))
+        m[lo3[0]:hi3[0], lo3[1]:hi3[1], lo3[2]:hi3[2]] = True
+        refined[l] = m
+    return refined
+
+
+# ---------------------------------------------------------------------------
+# Densities (mass = rho(centre) * h^3, renormalised to total mass 1).
+
+def plummer_rho(x: np.ndarray, centre, a: float, M: float = 1.0) -> np.ndarray:
+    r2 = ((x - np.asarray(centre)) ** 2).sum(-1)
+    return 3.0 * M / (4.0 * np.pi * a ** 3) * (1.0 + r2 / a ** 2) ** (-2.5)
+
+
+def _assemble(lmin, lmax, leaves, rho_fn, name):
+    h = Hierarchy(lmin, lmax, name=name)
+    for k, c in enumerate(leaves):
+        l = lmin + k
+        x = (c.astype(np.float64) + 0.5) * 2.0 ** (-l)
+        h.ijk.append(np.ascontiguousarray(c, dtype=np.int32))
+        h.mass.append(rho_fn(x) * 8.0 ** (-l))
+    return h
+
+
+def _normalise(h: Hierarchy, total: float = 1.0) -> Hierarchy:
+    s = h.total_mass()
+    h.mass = [m * (total / s) for m in h.mass]
+    return h
+
+
+def _uniform_noise(h: Hierarchy, seed: int, amp: float) -> Hierarchy:
+    for k, m in enumerate(h.mass):
+        u = uniform(seed, 100 + h.lmin + k, np.arange(m.size))
+        h.mass[k] = m * (1.0 + amp * (2.0 * u - 1.0))
+    return h
+
+
+def _lognormal_noise(h: Hierarchy, seed: int, sigma: float) -> Hierarchy:
+    for k, m in enumerate(h.mass):
+        xi = normal(seed, 200 + h.lmin + k, np.arange(m.size))
+        h.mass[k] = m * np.exp(sigma * xi - 0.5 * sigma ** 2)
+    return h
+
+
+# ---------------------------------------------------------------------------
+# The measured workloads.
+
+def unigrid_plummer(level: int = 5, a: float = 0.1, noise: float = 0.01, seed: int = 1) -> Hierarchy:
+    """Unigrid 2^level cubed, Plummer sphere (scale a, centred, M=1) at cell
+    centres plus seeded uniform noise of relative amplitude `noise`."""
+    leaves = leaves_from_refined(level, level, {})
+    h = _assemble(level, level, leaves, lambda x: plummer_rho(x, (0.5, 0.5, 0.5), a),
+                  f"unigrid {2**level}^3 plummer")
+    return _normalise(_uniform_noise(_normalise(h), seed, noise))
+
+
+def two_level_plummer(base: int = 6, lo: int = 24, hi: int = 40, a: float = 0.05,
+                      sigma: float = 0.3, seed: int = 2) -> Hierarchy:
+    """Base 2^base cubed plus one refined level over coarse cells [lo,hi)^3;
+    Plummer density (scale a) with seeded lognormal noise (sigma)."""
+    refined = nested_boxes(base, [(lo, hi)])
+    leaves = leaves_from_refined(base, base + 1, refined)
+    h = _assemble(base, base + 1, leaves, lambda x: plummer_rho(x, (0.5, 0.5, 0.5), a),
+                  f"two-level {2**base}^3 + {2*(hi-lo)}^3 plummer")
+    return _normalise(_lognormal_noise(_normalise(h), seed, sigma))
+
+
+def nested_two_plummer(base: int = 7, boxes=((24, 104), (76, 180)), seed: int = 4) -> Hierarchy:
+    """Base 2^base cubed with nested refined boxes (one per extra level), two
+    Plummer spheres (a = 0.03 and 0.05, masses 1/2 each, centres 0.5 -+ 0.08 in x)."""
+    refined = nested_boxes(base, list(boxes))
+    lmax = base + len(boxes)
+    leaves = leaves_from_refined(base, lmax, refined)
+
+    def rho(x):
+        return (plummer_rho(x, (0.42, 0.5, 0.5), 0.03, 0.5) +
+                plummer_rho(x, (0.58, 0.5, 0.5), 0.05, 0.5))
+
+    h = _assemble(base, lmax, leaves, rho, f"nested two-plummer {2**base}^3 + {len(boxes)} levels")
+    return _normalise(h)
+
+
+def random_amr(lmin: int, lmax: int, seed: int, frac: float = 0.3, blobs: int = 3) -> Hierarchy:
+    """Small random graded hierarchy for tests: at each level a union of seeded
+    spherical regions is proposed for refinement and filtered by the graded
+    rule; masses are seeded lognormal."""
+    refined = {}
+    prev = None
+    counter = 0
+    for l in range(lmin, lmax):
+        n = 2 ** l
+        x = (_grid(n).astype(np.float64) + 0.5) / n
+        cand = np.zeros(n ** 3, dtype=bool)
+        for b in range(blobs):
+            c = uniform(seed, 10 + l, np.arange(counter, counter + 3)) * 0.6 + 0.2
+            counter += 3
+            rad = frac * (0.5 + 0.5 * uniform(seed, 20 + l, counter))
+            counter += 1
+            cand |= ((x - c) ** 2).sum(-1) < rad ** 2
+        cand = cand.reshape(n, n, n)
+        if prev is not None:
+            exists = np.repeat(np.repeat(np.repeat(prev, 2, 0), 2, 1), 2, 2)
+            cand &= exists
+            cand = graded_filter(prev, cand)
+        refined[l] = cand
+        prev = cand
+        if not cand.any():
+            break
+    leaves = leaves_from_refined(lmin, lmax, refined)
+    h = Hierarchy(lmin, lmax, name=f"random amr {lmin}-{lmax} seed {seed}")
+    for k, c in enumerate(leaves):
+        l = lmin + k
+        h.ijk.append(np.ascontiguousarray(c, dtype=np.int32))
+        xi = normal(seed, 300 + l, np.arange(c.shape[0]))
+        h.mass.append(np.exp(0.5 * xi) * 8.0 ** (-l))
+    return _normalise(h)
+
+
+def permute(h: Hierarchy, seed: int) -> Hierarchy:
+    """Same hierarchy with each level's leaf list in a seeded random order."""
+    out = h.copy()
+    for k in range(len(out.ijk)):
+        n = out.ijk[k].shape[0]
+        order = np.argsort(uniform(seed, 400 + k, np.arange(n)), kind="stable")
+        out.ijk[k] = np.ascontiguousarray(out.ijk[k][order])
+        out.mass[k] = np.ascontiguousarray(out.mass[k][order])
+    return out
+
+
+CONFIGS = {
+    "unigrid32_p4": dict(make=lambda: unigrid_plummer(5), p=4),
+    "twolevel64_p6": dict(make=lambda: two_level_plummer(), p=6),
+    "nested128_p6": dict(make=lambda: nested_two_plummer(), p=6),
+}

@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against mathematics it does not itself contain.
+
+Each test ties one part of the oracle to something fixed outside it: closed
+forms of the derivatives of 1/r and the Legendre identity, the M2M and L2L
+exactness identities, analytic truncation behaviour, the O(N^2) direct sum,
+linearity, mirror symmetry, the exact antisymmetry of nearest-field pairs
+(Sec. 3.2) and the graded-octree validation rules.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.special import eval_legendre
+from math import factorial
+
+import oracle
+from paper_2607_19489_b300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def idx_of(p):
+    mi = oracle.multi_index(p)
+    return {tuple(m): k for k, m in enumerate(mi)}
+
+
+# ---------------------------------------------------------------- derivatives
+
+def test_inv_r_closed_forms():
+    rng = np.random.default_rng(0)
+    I = idx_of(4)
+    for _ in range(20):
+        R = rng.uniform(-3, 3, 3)
+        x, y, z = R
+        r = np.linalg.norm(R)
+        d = oracle.inv_r_derivs(4, R)
+        assert d[I[(0, 0, 0)]] == pytest.approx(1 / r, rel=1e-14)
+        assert d[I[(1, 0, 0)]] == pytest.approx(-x / r ** 3, rel=1e-13)
+        assert d[I[(0, 2, 0)]] == pytest.approx((3 * y * y - r * r) / r ** 5, rel=1e-12, abs=1e-12 / r ** 3)
+        assert d[I[(1, 0, 1)]] == pytest.approx(3 * x * z / r ** 5, rel=1e-12)
+        assert d[I[(1, 1, 1)]] == pytest.approx(-15 * x * y * z / r ** 7, rel=1e-12)
+
+
+@pytest.mark.parametrize("n", range(0, 9))
+def test_inv_r_axis_legendre(n):
+    # d^n/dx^n (1/r) = (-1)^n n! P_n(x/r) / r^(n+1)   (Legendre generating function)
+    rng = np.random.default_rng(n)
+    I = idx_of(8)
+    for _ in range(10):
+        R = rng.uniform(-2, 2, 3)
+        r = np.linalg.norm(R)
+        want = (-1) ** n * factorial(n) * eval_legendre(n, R[0] / r) / r ** (n + 1)
+        got = oracle.inv_r_derivs(8, R)[I[(n, 0, 0)]]
+        scale = factorial(n) / r ** (n + 1)
+        assert abs(got - want) <= 1e-12 * scale
+
+
+def test_inv_r_laplace_and_fd():
+    q = 7
+    I = idx_of(q)
+    R = np.array([1.3, -0.7, 2.1])
+    d = oracle.inv_r_derivs(q, R)
+    mi = oracle.multi_index(q)
+    for g in mi:
+        g = tuple(int(v) for v in g)
+        if sum(g) <= q - 2:   # 1/r is harmonic: the trace of every derivative vanishes
+            s = sum(d[I[(g[0] + 2 * (i == 0), g[1] + 2 * (i == 1), g[2] + 2 * (i == 2))]] for i in range(3))
+            mag = max(abs(d[I[(g[0] + 2 * (i == 0), g[1] + 2 * (i == 1), g[2] + 2 * (i == 2))]]) for i in range(3))
+            assert abs(s) <= 1e-12 * mag
+        if sum(g) <= q - 1:   # central finite difference of the lower derivative
+            for i in range(3):
+                e = np.zeros(3)
+                e[i] = 1e-5
+                fd = (oracle.inv_r_derivs(q, R + e)[I[g]] - oracle.inv_r_derivs(q, R - e)[I[g]]) / 2e-5
+                gi = (g[0] + (i == 0), g[1] + (i == 1), g[2] + (i == 2))
+                assert fd == pytest.approx(d[I[gi]], rel=1e-6, abs=1e-9)
+
+
+def test_inv_r_numerators_golden_and_trace():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "inv_r_numerators.txt"))
+            if l.strip() and not l.startswith("#")]
+    I = idx_of(4)
+    for r in rows:
+        g = tuple(int(v) for v in r[0:3])
+        u = [int(v) for v in r[3:6]]
+        assert oracle.numerators(4, u)[I[g]] == int(r[6]), r
+    # exact integer Laplace identity: P_{g+2ex} + P_{g+2ey} + P_{g+2ez} == 0
+    q = 9
+    I = idx_of(q)
+    for u in ([3, -5, 7], [13, 1, -9], [4, 4, 1]):
+        P = oracle.numerators(q, u)
+        for g in oracle.multi_index(q - 2):
+            g = tuple(int(v) for v in g)
+            s = sum(int(P[I[(g[0] + 2 * (i == 0), g[1] + 2 * (i == 1), g[2] + 2 * (i == 2))]]) for i in range(3))
+            assert s == 0
+
+
+# ---------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_m2m_equals_direct_p2m(p):
+    # moments of 8 child clusters shifted to the parent == moments taken at the parent
+    rng = np.random.default_rng(p)
+    cp = np.array([0.5, 0.5, 0.5])
+    Mp_direct = np.zeros(oracle.ncoef(p))
+    Mp_shift = np.zeros(oracle.ncoef(p))
+    for k in range(8):
+        s = np.array([k & 1, (k >> 1) & 1, (k >> 2) & 1]) - 0.5
+        cc = cp + 0.25 * s
+        Mc = np.zeros(oracle.ncoef(p))
+        for _ in range(5):
+            x = cc + rng.uniform(-0.25, 0.25, 3)
+            m = rng.uniform(0.1, 1.0)
+            Mc = oracle.p2m(p, m, x, cc, Mc)
+            Mp_direct = oracle.p2m(p, m, x, cp, Mp_direct)
+        Mp_shift = oracle.m2m(p, Mc, cc, cp, Mp_shift)
+    np.testing.assert_allclose(Mp_shift, Mp_direct, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [3, 6])
+def test_l2l_and_l2p_exact_for_polynomials(p):
+    # A local expansion is a degree-p polynomial; shifting it is exact.
+    rng = np.random.default_rng(10 + p)
+    L = rng.normal(size=oracle.ncoef(p))
+    c = np.array([0.2, 0.4, 0.6])
+    c2 = c + np.array([0.05, -0.05, 0.05])
+    L2 = oracle.l2l(p, L, c, c2)
+    for _ in range(5):
+        x = c2 + rng.uniform(-0.1, 0.1, 3)
+        np.testing.assert_allclose(oracle.l2p(p, L2, c2, x), oracle.l2p(p, L, c, x), rtol=1e-11, atol=1e-12)
+    # gradient of L2P is the derivative of its potential
+    x = c + np.array([0.03, 0.02, -0.01])
+    g = oracle.l2p(p, L, c, x)
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = 1e-6
+        fd = (oracle.l2p(p, L, c, x + e)[0] - oracle.l2p(p, L, c, x - e)[0]) / 2e-6
+        assert fd == pytest.approx(g[1 + i], rel=1e-6, abs=1e-8)
+
+
+def _cluster(rng, c, half, n=6):
+    xs = c + rng.uniform(-half, half, (n, 3))
+    ms = rng.uniform(0.1, 1.0, n)
+    return xs, ms
+
+
+def _exact(xs, ms, x):
+    d = x - xs
+    r = np.linalg.norm(d, axis=1)
+    return np.array([-(ms / r).sum(), *((ms[:, None] * d / r[:, None] ** 3).sum(0))])
+
+
+def test_m2p_and_m2l_truncation():
+    # Single-box multipole seen from a well-separated point: error falls with p
+    # and stays within the classical bound M (rho/R)^(p+1) / (R - rho).
+    rng = np.random.default_rng(3)
+    cs = np.array([0.0, 0.0, 0.0])
+    xs, ms = _cluster(rng, cs, 0.5)
+    ct = np.array([2.0, 1.0, 0.0])
+    x = ct + np.array([0.3, -0.2, 0.1])
+    exact = _exact(xs, ms, x)
+    rho = np.sqrt(3) * 0.5
+    prev_m2p = prev_m2l = np.inf
+    for p in (2, 4, 6, 8):
+        M = np.zeros(oracle.ncoef(p))
+        for xi, mi in zip(xs, ms):
+            M = oracle.p2m(p, mi, xi, cs, M)
+        e_m2p = abs(oracle.m2p(p, M, cs, x)[0] - exact[0])
+        R = np.linalg.norm(x - cs)
+        assert e_m2p <= ms.sum() * (rho / R) ** (p + 1) / (R - rho)
+        L = oracle.m2l(p, M, cs, ct)
+        e_m2l = np.abs(oracle.l2p(p, L, ct, x) - exact).max()
+        assert e_m2p < prev_m2p and e_m2l < prev_m2l
+        prev_m2p, prev_m2l = e_m2p, e_m2l
+    assert prev_m2l < 1e-3 * abs(exact[0])
+
+
+# ---------------------------------------------------------------- whole solver
+
+def _solve_vs_direct(h, p):
+    phi, a = oracle.solve(h, p)
+    phid, ad = oracle.direct(h)
+    A = np.concatenate([a[l] for l in h.levels])
+    AD = np.concatenate([ad[l] for l in h.levels])
+    P = np.concatenate([phi[l] for l in h.levels])
+    PD = np.concatenate([phid[l] for l in h.levels])
+    return rel_rms(A, AD), rel_rms(P, PD)
+
+
+def test_no_far_field_is_direct_sum():
+    # 4^3 unigrid: every FMM box is a neighbour, all interactions are P2P.
+    h = W.unigrid_plummer(2, seed=5)
+    ea, ep = _solve_vs_direct(h, 4)
+    assert ea < 1e-14 and ep < 1e-14
+
+
+@pytest.mark.parametrize("level", [3, 4])
+def test_unigrid_converges_to_direct_sum(level):
+    errs = [_solve_vs_direct(W.unigrid_plummer(level), p)[0] for p in (2, 4, 6)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < (1e-5 if level == 3 else 3e-3)
+
+
+def test_amr_converges_to_direct_sum():
+    # Every region of an AMR hierarchy is covered exactly once only if the error
+    # keeps falling with p (a missing or doubled region would leave a floor).
+    h = W.random_amr(3, 5, seed=7)
+    errs = [_solve_vs_direct(h, p)[0] for p in (2, 4, 6, 8)]
+    assert all(errs[i] > errs[i + 1] for i in range(3))
+    assert errs[-1] < 1e-4
+
+
+def test_point_mass():
+    # one unit mass: within the 3^3 oct neighbourhood the answer is exactly -1/r
+    lev = 4
+    h = W.unigrid_plummer(lev)
+    h.mass[0][:] = 0.0
+    src = np.where((h.ijk[0] == [7, 8, 6]).all(1))[0][0]
+    h.mass[0][src] = 1.0
+    phi, a = oracle.solve(h, 6)
+    x = h.centres(lev)
+    d = x - x[src]
+    r = np.linalg.norm(d, axis=1)
+    ok = r > 0
+    exact = -1.0 / r[ok]
+    near = (np.abs((h.ijk[0] >> 1) - (h.ijk[0][src] >> 1)).max(1) <= 1)[ok]
+    np.testing.assert_allclose(phi[lev][ok][near], exact[near], rtol=1e-14)
+    # beyond it the truncation error falls with the order
+    e6 = np.abs(phi[lev][ok] - exact).max() / np.abs(exact).max()
+    phi4, _ = oracle.solve(h, 4)
+    e4 = np.abs(phi4[lev][ok] - exact).max() / np.abs(exact).max()
+    assert e6 < e4 and e6 < 5e-3
+
+
+def test_linearity():
+    h1 = W.random_amr(3, 5, seed=14)
+    h2 = h1.copy()
+    h2.mass = [np.sqrt(np.abs(np.sin(np.arange(m.size) + 1.0))) * 1e-3 for m in h1.mass]
+    h3 = h1.copy()
+    h3.mass = [0.7 * m1 - 1.9 * m2 for m1, m2 in zip(h1.mass, h2.mass)]
+    _, a1 = oracle.solve(h1, 4)
+    _, a2 = oracle.solve(h2, 4)
+    _, a3 = oracle.solve(h3, 4)
+    for l in h1.levels:
+        if a3[l].size == 0:
+            continue
+        np.testing.assert_allclose(a3[l], 0.7 * a1[l] - 1.9 * a2[l], rtol=1e-10, atol=1e-12 * np.abs(a3[l]).max())
+
+
+def test_mirror_symmetry():
+    h = W.random_amr(3, 5, seed=13)
+    m = h.copy()
+    for k, l in enumerate(h.levels):
+        m.ijk[k] = h.ijk[k].copy()
+        m.ijk[k][:, 0] = (1 << l) - 1 - h.ijk[k][:, 0]
+    phi, a = oracle.solve(h, 4)
+    phim, am = oracle.solve(m, 4)
+    for l in h.levels:
+        if a[l].size == 0:
+            continue
+        np.testing.assert_allclose(phim[l], phi[l], rtol=1e-12)
+        np.testing.assert_allclose(am[l][:, 0], -a[l][:, 0], rtol=1e-10, atol=1e-10 * np.abs(a[l]).max())
+        np.testing.assert_allclose(am[l][:, 1:], a[l][:, 1:], rtol=1e-10, atol=1e-10 * np.abs(a[l]).max())
+
+
+def test_nearest_field_pairs_are_antisymmetric():
+    # Sec. 3.2: a coarse leaf t and a fine leaf s touching it interact by P2P in
+    # both directions, so a_t(m_s = 1) == -a_s(m_t = 1) bit for bit.
+    h = W.two_level_plummer(base=3, lo=2, hi=6, seed=2)   # 8^3 base, refined [2,6)^3
+    lc, lf = h.lmin, h.lmax
+    coarse, fine = h.ijk[0], h.ijk[1]
+    t = np.where((coarse == [1, 3, 3]).all(1))[0][0]    # leaf left of the refined block
+    s_cells = [[4, 6, 6], [4, 7, 7], [4, 6, 7]]          # fine leaves on the block's face
+    for sc in s_cells:
+        s = np.where((fine == sc).all(1))[0][0]
+        ht = h.copy()
+        ht.mass = [np.zeros_like(m) for m in h.mass]
+        ht.mass[1][s] = 1.0
+        hs = h.copy()
+        hs.mass = [np.zeros_like(m) for m in h.mass]
+        hs.mass[0][t] = 1.0
+        _, at = oracle.solve(ht, 4, sel={lc: np.array([t])})
+        _, as_ = oracle.solve(hs, 4, sel={lf: np.array([s])})
+        assert np.array_equal(at[lc][0], -as_[lf][0])
+        assert np.abs(at[lc][0]).max() > 0
+
+
+def test_momentum_small():
+    h = W.random_amr(3, 5, seed=19)
+    _, a = oracle.solve(h, 6)
+    f = sum((h.mass[k][:, None] * a[l]).sum(0) for k, l in enumerate(h.levels))
+    fabs = sum((h.mass[k] * np.linalg.norm(a[l], axis=1)).sum() for k, l in enumerate(h.levels))
+    assert np.linalg.norm(f) / fabs < 1e-3
+
+
+# ---------------------------------------------------------------- validation
+
+def test_validation_codes():
+    h = W.two_level_plummer(base=3, lo=2, hi=6)
+    assert oracle.validate(h) == 0
+    bad = h.copy()
+    bad.ijk[0] = np.concatenate([bad.ijk[0], bad.ijk[0][:1]])
+    bad.mass[0] = np.concatenate([bad.mass[0], bad.mass[0][:1]])
+    assert oracle.validate(bad) == -3            # duplicate cell
+    bad = h.copy()
+    bad.ijk[0] = bad.ijk[0].copy()
+    bad.ijk[0][0] = [8, 0, 0]
+    assert oracle.validate(bad) == -4            # outside the box
+    bad = h.copy()
+    bad.ijk[1] = bad.ijk[1][1:].copy()
+    bad.mass[1] = bad.mass[1][1:].copy()
+    assert oracle.validate(bad) == -10           # incomplete oct
+    # refine a fine cell next to the coarse-fine interface: its father's neighbours
+    # are not all refined
+    bad = h.copy()
+    ch = np.array([[8 + (k & 1), 8 + ((k >> 1) & 1), 8 + ((k >> 2) & 1)] for k in range(8)], np.int32)
+    keep = ~(bad.ijk[1] == [4, 4, 4]).all(1)
+    bad.ijk[1] = bad.ijk[1][keep]
+    bad.mass[1] = bad.mass[1][keep]
+    bad.lmax = 5
+    bad.ijk.append(ch)
+    bad.mass.append(np.ones(8) * 1e-3)
+    assert oracle.validate(bad) == -2
+
+
+def test_tree_brute_force():
+    # Canonical index rebuilt from geometry alone on a tiny graded hierarchy.
+    h = W.random_amr(3, 5, seed=13)
+    T = oracle.tree(h)
+
+    def key(c, l):
+        k = 0
+        for b in range(l):
+            k |= ((c[0] >> b) & 1) << (3 * b) | ((c[1] >> b) & 1) << (3 * b + 1) | ((c[2] >> b) & 1) << (3 * b + 2)
+        return k
+
+    cells = {}
+    for k, l in enumerate(h.levels):
+        for i, c in enumerate(h.ijk[k]):
+            cells[(l, tuple(int(v) for v in c))] = ("leaf", i)
+    for l in range(h.lmax, 0, -1):
+        for (ll, c), _ in list(cells.items()):
+            if ll == l:
+                cells.setdefault((l - 1, (c[0] >> 1, c[1] >> 1, c[2] >> 1)), ("ref", None))
+    for l in range(0, h.lmin):
+        n = 1 << l
+        for i in range(n):
+            for j in range(n):
+                for kk in range(n):
+                    cells.setdefault((l, (i, j, kk)), ("ref", None))
+    for l in range(1, h.lmax + 1):
+        keys, status, nbr = T[l]
+        parents = sorted((key(c, l - 1), c) for (ll, c), v in cells.items() if ll == l - 1 and v[0] == "ref")
+        assert [k for k, _ in parents] == [int(k) for k in keys]
+        rank = {c: o for o, (_, c) in enumerate(parents)}
+        nxt = {}
+        if l < h.lmax:
+            nxt = {c: o for o, (_, c) in enumerate(sorted((key(c, l), c) for (ll, c), v in cells.items() if ll == l and v[0] == "ref"))}
+        for o, (_, P) in enumerate(parents):
+            for k in range(8):
+                c = (2 * P[0] + (k & 1), 2 * P[1] + ((k >> 1) & 1), 2 * P[2] + ((k >> 2) & 1))
+                kind, i = cells[(l, c)]
+                assert status[8 * o + k] == (-1 - i if kind == "leaf" else nxt[c])
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        Q = (P[0] + dx, P[1] + dy, P[2] + dz)
+                        v = nbr[o, (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]
+                        if min(Q) < 0 or max(Q) >= (1 << (l - 1)):
+                            assert v == -1
+                        elif cells[(l - 1, Q)][0] == "ref":
+                            assert v == rank[Q]
+                        else:
+                            # cell id of the level l-1 leaf: 8 * oct(parent of Q) + position
+                            prev = sorted(key(c, l - 2) for (ll, c), vv in cells.items() if ll == l - 2 and vv[0] == "ref")
+                            po = prev.index(key((Q[0] >> 1, Q[1] >> 1, Q[2] >> 1), l - 2))
+                            cid = 8 * po + ((Q[0] & 1) | ((Q[1] & 1) << 1) | ((Q[2] & 1) << 2))
+                            assert v == -2 - cid
