@@ -1,0 +1,160 @@
+/*
+ * fmm.h -- C ABI of the B300 adaptive FMM Poisson solver.
+ *
+ * The library computes the gravitational potential and acceleration of every
+ * leaf cell of a graded AMR octree with isolated boundaries, following the
+ * adaptive FMM of Lee & Teyssier (arXiv 2607.19489): one FMM tree per AMR level
+ * (Sec. 3.1), P2M/M2M upward pass (Eqs. 1-2), M2L over the 6^3-3^3 interaction
+ * list and L2L downward pass (Eqs. 3-4, Alg. 3), and the far / intermediate /
+ * near / nearest field evaluation (Sec. 3.2, Fig. 2, Alg. 4).
+ *
+ * Geometry.  The domain is the unit box [0,1)^3.  Level l has 2^l cells per
+ * axis of size h_l = 2^-l; cell (i,j,k) has centre ((i,j,k)+1/2) h_l and is a
+ * point mass there.  Levels lmin..lmax hold leaf cells; a cell is refined when
+ * cells exist one level finer inside it.  RAMSES rules apply: refined cells
+ * have all 8 children (octs), level lmin covers the whole box, and a cell may
+ * be refined only if the 3^3 neighbours of its father are refined (Sec. 3.2).
+ *
+ * Conventions.  g(R) = -1/|R|; phi_i = G sum_{j != i} m_j g(x_i - x_j) as
+ * approximated by the FMM; accel = -grad phi.  Expansion order p applies to
+ * multipoles and locals alike; M2L keeps |alpha|+|beta| <= p (Eq. 3).
+ *
+ * Errors.  Every call returns an fmm_status.  No call aborts or throws.
+ * Device-side errors found by kernels are latched in the context and returned
+ * by the next call that synchronises (fmm_set_levels, fmm_sync).
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ * default stream.  fmm_solve is asynchronous on that stream; it allocates
+ * nothing and never synchronises (all workspace is sized by fmm_set_levels).
+ *
+ * Threading.  A context may be used by one host thread at a time.
+ */
+#ifndef FMM_H
+#define FMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_ctx fmm_ctx;
+
+typedef enum {
+  FMM_OK = 0,
+  FMM_ERR_ARG = -1,         /* bad argument (NULL pointer, level range, p, ...) */
+  FMM_ERR_NOT_GRADED = -2,  /* hierarchy violates the graded-octree rule (Sec. 3.2) */
+  FMM_ERR_DUPLICATE = -3,   /* a cell given twice, or given as a leaf while refined */
+  FMM_ERR_OUT_OF_BOX = -4,  /* a cell index outside [0, 2^l) */
+  FMM_ERR_OOM = -5,         /* device allocation failed or exceeded the budget */
+  FMM_ERR_CUDA = -6,        /* a CUDA runtime call failed (fmm_last_error has the text) */
+  FMM_ERR_NONFINITE = -7,   /* a mass is NaN or infinite */
+  FMM_ERR_STATE = -8,       /* call out of order (e.g. solve before set_levels) */
+  FMM_ERR_TIMEOUT = -9,     /* a bounded device-side wait gave up */
+  FMM_ERR_INCOMPLETE = -10  /* a refined cell lacks some of its 8 children, or the
+                               base level does not cover the box */
+} fmm_status;
+
+typedef enum {
+  FMM_FP64 = 0,          /* every step in FP64 (DFMA) */
+  FMM_MIXED_BF16X3 = 1   /* M2L/M2P on tcgen05 tensor cores in split-BF16 (3 products,
+                            FP32 accumulation), P2P in FP32, FP64 for box levels <= 4
+                            of M2M, for L2L and for local-expansion accumulation */
+} fmm_precision;
+
+typedef struct {
+  int p;              /* expansion order, 1..8 (Eq. 3 truncation) */
+  int precision;      /* fmm_precision */
+  double G;           /* gravitational constant (outputs scale linearly) */
+  int out_fp32;       /* 0: phi/accel outputs are double, 1: float */
+  size_t mem_budget;  /* 0: unlimited; else fmm_set_levels fails with FMM_ERR_OOM when
+                         the device workspace would exceed this many bytes */
+} fmm_config;
+
+/* Create a context on the current CUDA device.  The config is copied.
+ * Returns FMM_ERR_ARG for p outside 1..8 or an unknown precision. */
+fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out);
+
+/* Set the AMR hierarchy, or replace its levels lo..lmax (adaptive time
+ * stepping: Alg. 1 rebuilds the trees of the active levels only).
+ *
+ *   n[k]    host int64, number of leaf cells of level lo+k, k = 0..lmax-lo
+ *   ijk[k]  int32 [n[k]][3] cell indices of level lo+k, each in [0, 2^(lo+k))
+ *   mass[k] double [n[k]] masses
+ * ijk/mass may be device or host pointers (host data is copied in on
+ * `stream`).  The caller keeps ownership; the library copies what it needs
+ * before returning, so the buffers may be reused afterwards.  The first call
+ * must have lo == lmin; later calls must keep lmin and lmax (FMM_ERR_STATE).
+ * Levels below lo keep their previous cells and masses.  The tree index of
+ * the whole hierarchy (Morton-sorted octs, parents, children, 27-neighbour
+ * tables) is rebuilt and validated; this call synchronises `stream`.
+ * Requires 2 <= lmin <= lmax <= 20. */
+fmm_status fmm_set_levels(fmm_ctx* ctx, int lmin, int lmax, int lo, const int64_t* n,
+                          const int32_t* const* ijk, const double* const* mass, void* stream);
+
+/* Solve for the leaf cells of levels lo..lmax (Alg. 1 for l = lo..lmax, which
+ * share one upward and one downward pass: the far field of a box does not
+ * depend on the target level).  phi[k] / accel[k] receive level lo+k in the
+ * caller's input order: phi [n][1], accel [n][3], double or float per
+ * config.out_fp32.  Device or host pointers (host outputs are copied back on
+ * `stream`; the caller synchronises before reading them).  Asynchronous. */
+fmm_status fmm_solve(fmm_ctx* ctx, int lo, void* const* phi, void* const* accel, void* stream);
+
+/* Wait for all work of the context on its last stream and return any
+ * latched device error (FMM_ERR_TIMEOUT from a bounded wait, FMM_ERR_CUDA). */
+fmm_status fmm_sync(fmm_ctx* ctx);
+
+/* Text of the last error of this context (static storage inside ctx). */
+const char* fmm_last_error(const fmm_ctx* ctx);
+
+void fmm_destroy(fmm_ctx* ctx);
+
+/* ---- introspection (tests and tools) ---------------------------------- */
+
+/* Number of octs per level l = 0..lmax (n_oct[0] = 0) of the current tree. */
+fmm_status fmm_tree_counts(const fmm_ctx* ctx, int64_t* n_oct);
+
+/* Copy the tree index of level l (1..lmax) to host buffers, in canonical
+ * order: octs sorted by the Morton key of their parent cell (x in the lowest
+ * bit of each triple), cell id = 8*oct + (x&1 | (y&1)<<1 | (z&1)<<2).
+ *   oct_key  uint64 [n_oct]     Morton key of the parent cell (level l-1)
+ *   status   int64  [8 n_oct]   refined: child oct id at l+1; leaf: -1 - input index
+ *   nbr      int64  [27 n_oct]  oct whose parent is the parent's neighbour
+ *            (dx,dy,dz) at index (dx+1)+3(dy+1)+9(dz+1); -2 - (cell id at l-1)
+ *            if that neighbour is a leaf; -1 outside the unit box. */
+fmm_status fmm_tree_export(const fmm_ctx* ctx, int level, uint64_t* oct_key, int64_t* status,
+                           int64_t* nbr);
+
+/* Host-only: integer numerators P_gamma(u) of d^gamma (1/r) = P_gamma(u) /
+ * |u|^(2|gamma|+1) at an integer point u, for all |gamma| <= q (q <= 12), in
+ * graded order (degree, then a descending, then b descending).  These build
+ * the library's translation tables.  Needs no GPU. */
+fmm_status fmm_host_numerators(int q, const int64_t* u, int64_t* out);
+
+/* Host-only: the FP64 translation operators the library builds, for checks.
+ * which = 0: bottom M2P   [256][26*8*nc]   (n = (f*8+t)*4+comp; k = (q*8+s)*nc+alpha)
+ *         1: M2L          [8*nc][26*8*nc]  (n = b*nc+beta)
+ *         2: near M2P     [343][nc][4]     (R = target - source in [-3,3]^3)
+ *         3: L2P          [64][nc][4]      (position f*8+t inside the level l-2 box)
+ *         4: M2M          [8][nc][nc]      (child c, output alpha, input gamma)
+ *         5: L2L          [8][nc][nc]      (child c, output beta, input gamma)
+ * Expansions are in box units (multipoles / h^|alpha|, locals * h^(|beta|+1));
+ * comp 0 is phi, comps 1..3 are accel = -grad phi.  Returns FMM_ERR_ARG if
+ * `n` (doubles) is too small.  Needs no GPU. */
+fmm_status fmm_host_table(int p, int which, double* out, int64_t n);
+
+/* Counters since fmm_create: out[0] = launches of this library's own kernels,
+ * out[1] = calls into CUB primitives (radix sort, scan, select) during tree
+ * builds, out[2] = fmm_solve calls, out[3] = fmm_set_levels calls. */
+fmm_status fmm_stats(const fmm_ctx* ctx, int64_t* out4);
+
+/* Per-stage device times (ms) of the last solve when timing is enabled with
+ * fmm_set_timing(ctx, 1): upward, downward, m2p, near (4 doubles). */
+fmm_status fmm_set_timing(fmm_ctx* ctx, int on);
+fmm_status fmm_stage_times(const fmm_ctx* ctx, double* ms4);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_H */

@@ -1,0 +1,496 @@
+// api.cu -- the C ABI (include/fmm.h): context, hierarchy, and the solve
+// schedule of Alg. 1 for the target levels lo..lmax.
+//
+// Schedule of fmm_solve (all on one stream, no host synchronisation):
+//   1. Upward (Alg. 2): P2M/M2M from the finest level to level 1, giving
+//      every cell the multipole of all mass inside it (the sum of the paper's
+//      per-level trees; stale levels keep the masses they were last given).
+//   2. MultipoleToLocal (Alg. 3): for box levels 2..lmax-2, L2L from the
+//      parent then M2L over the interaction list (gathered contraction).
+//      The far field of a box does not depend on the target level, so one
+//      downward pass serves all target levels.
+//   3. PotentialEvaluation (Alg. 4) per target level: the bottom intermediate
+//      field as an M2P contraction, then near/nearest fields, L2P and the
+//      scatter to the caller's order.
+#include <cmath>
+#include <cstring>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+cudaError_t buf_ensure(Ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return cudaSuccess;
+  if (b.ptr) {
+    cudaFree(b.ptr);
+    c->bytes_in_use -= b.bytes;
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  if (c->cfg.mem_budget && c->bytes_in_use + bytes > c->cfg.mem_budget) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(&b.ptr, bytes);
+  if (e != cudaSuccess) {
+    b.ptr = nullptr;
+    cudaGetLastError();
+    return e;
+  }
+  b.bytes = bytes;
+  c->bytes_in_use += bytes;
+  return cudaSuccess;
+}
+
+static void buf_free(Ctx* c, DevBuf& b) {
+  if (b.ptr) {
+    cudaFree(b.ptr);
+    c->bytes_in_use -= b.bytes;
+  }
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+namespace {
+
+#define CKS(x)                                                             \
+  do {                                                                     \
+    cudaError_t e_ = (x);                                                  \
+    if (e_ != cudaSuccess) {                                               \
+      c->last_error = std::string(#x) + ": " + cudaGetErrorString(e_);     \
+      return e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA; \
+    }                                                                      \
+  } while (0)
+
+template <typename T>
+fmm_status upload(Ctx* c, DevBuf& b, const std::vector<T>& v) {
+  CKS(buf_ensure(c, b, v.size() * sizeof(T)));
+  CKS(cudaMemcpy(b.ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FMM_OK;
+}
+
+#define TRY(x)                     \
+  do {                             \
+    fmm_status s_ = (x);           \
+    if (s_ != FMM_OK) return s_;   \
+  } while (0)
+
+inline uint16_t bf16_bits(float f) {  // round to nearest even
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  uint32_t r = u + 0x7FFF + ((u >> 16) & 1);
+  return (uint16_t)(r >> 16);
+}
+inline float bf16_val(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Build the device copies of one contraction operator.  `src` is [N][K] with
+// K ordered (q, s, alpha).
+fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& src, int N, bool m2l) {
+  const int nc = c->tab.nc, KQ = 8 * nc, K = 26 * KQ;
+  op.N = N;
+  op.K = K;
+  op.kseg = KQ;
+  if (c->cfg.precision == FMM_FP64) {
+    // [K'][N] with K' ordered (q, alpha, s) and per-column segment limits
+    std::vector<double> f((size_t)K * N);
+    std::vector<int32_t> lim(N);
+    for (int n = 0; n < N; ++n) {
+      int d = m2l ? c->tab.degree[n % nc] : 0;
+      lim[n] = m2l ? 8 * ncoef(c->tab.p - d) : KQ;
+    }
+    for (int q = 0; q < 26; ++q)
+      for (int s = 0; s < 8; ++s)
+        for (int a = 0; a < nc; ++a) {
+          size_t kin = (size_t)(q * 8 + s) * nc + a;
+          size_t kout = (size_t)q * KQ + a * 8 + s;
+          for (int n = 0; n < N; ++n) f[kout * N + n] = src[(size_t)n * K + kin];
+        }
+    TRY(upload(c, op.f64, f));
+    TRY(upload(c, op.klimit, lim));
+    op.BN = 256;
+    op.ntile = (N + 255) / 256;
+    return FMM_OK;
+  }
+  op.ntile = (N + 255) / 256;
+  op.BN = ((N + op.ntile - 1) / op.ntile + 31) / 32 * 32;  // the epilogue reads 32 columns at a time
+  op.Npad = op.ntile * op.BN;
+  op.Kpad = (K + 63) / 64 * 64;
+  std::vector<uint16_t> hi((size_t)op.Npad * op.Kpad, 0), lo((size_t)op.Npad * op.Kpad, 0);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      double v = src[(size_t)n * K + k];
+      uint16_t h = bf16_bits((float)v);
+      uint16_t l = bf16_bits((float)(v - (double)bf16_val(h)));
+      hi[(size_t)n * op.Kpad + k] = h;
+      lo[(size_t)n * op.Kpad + k] = l;
+    }
+  TRY(upload(c, op.hi, hi));
+  TRY(upload(c, op.lo, lo));
+  return make_tensor_maps(c, op);
+}
+
+fmm_status init_tables(Ctx* c) {
+  Tables& t = c->tab;
+  t.build(c->cfg.p);
+  TRY(upload(c, c->d_m2m_off, t.m2m_off));
+  TRY(upload(c, c->d_m2m_g, t.m2m_g));
+  TRY(upload(c, c->d_m2m_e, t.m2m_e));
+  TRY(upload(c, c->d_m2m_c, t.m2m_c));
+  TRY(upload(c, c->d_l2l_off, t.l2l_off));
+  TRY(upload(c, c->d_l2l_g, t.l2l_g));
+  TRY(upload(c, c->d_l2l_e, t.l2l_e));
+  TRY(upload(c, c->d_l2l_c, t.l2l_c));
+  if (c->cfg.precision == FMM_FP64) {
+    TRY(upload(c, c->d_near64, t.nearop));
+    TRY(upload(c, c->d_l2p64, t.l2p));
+  } else {
+    std::vector<float> nf(t.nearop.begin(), t.nearop.end()), lf(t.l2p.begin(), t.l2p.end());
+    TRY(upload(c, c->d_near32, nf));
+    TRY(upload(c, c->d_l2p32, lf));
+  }
+  TRY(build_operator(c, c->op_m2p, t.m2p, 256, false));
+  TRY(build_operator(c, c->op_m2l, t.m2l, 8 * t.nc, true));
+  // the tables are only needed on the device from here on
+  std::vector<double>().swap(t.m2p);
+  std::vector<double>().swap(t.m2l);
+  c->tables_on_device = true;
+  return FMM_OK;
+}
+
+// Sizes every per-level array so that fmm_solve allocates nothing.
+fmm_status size_expansions(Ctx* c) {
+  const int nc = c->tab.nc;
+  const bool f64 = c->cfg.precision == FMM_FP64;
+  for (int l = 1; l <= c->lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    const int64_t ncell = 8 * T.n_oct;
+    T.m_is_f64 = f64 || l <= kTopLevelFP64;
+    CKS(buf_ensure(c, T.mono, ncell * 8));
+    if (l < c->lmax) {
+      CKS(buf_ensure(c, T.M, ncell * nc * (T.m_is_f64 ? 8 : 4)));
+      if (!f64) {
+        CKS(buf_ensure(c, T.Mhi, ncell * nc * 2));
+        CKS(buf_ensure(c, T.Mlo, ncell * nc * 2));
+      }
+    }
+    if (l >= 2 && l <= c->lmax - 2) CKS(buf_ensure(c, T.L, ncell * nc * 8));
+    if (l >= c->lmin) CKS(buf_ensure(c, T.acc, ncell * 4 * (f64 ? 8 : 4)));
+  }
+  return FMM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void stage_event(Ctx* c, int i, cudaStream_t st) {
+  if (c->timing) cudaEventRecord(c->ev[i], st);
+}
+
+}  // namespace
+}  // namespace fmm
+
+using namespace fmm;
+
+struct fmm_ctx : public fmm::Ctx {};
+
+extern "C" {
+
+fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
+  if (!cfg || !out) return FMM_ERR_ARG;
+  *out = nullptr;
+  if (cfg->p < 1 || cfg->p > 8) return FMM_ERR_ARG;
+  if (cfg->precision != FMM_FP64 && cfg->precision != FMM_MIXED_BF16X3) return FMM_ERR_ARG;
+  if (!std::isfinite(cfg->G)) return FMM_ERR_ARG;
+  fmm_ctx* c = new fmm_ctx();
+  c->cfg = *cfg;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return FMM_ERR_CUDA;
+  }
+  c->device = dev;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaMalloc(&c->d_err, 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;
+  }
+  cudaMemset(c->d_err, 0, 16);
+  for (auto& ev : c->ev) cudaEventCreate(&ev);
+  fmm_status s = init_tables(c);
+  if (s != FMM_OK) {
+    fmm_destroy(c);
+    return s;
+  }
+  *out = c;
+  return FMM_OK;
+}
+
+fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t* n, const int32_t* const* ijk,
+                          const double* const* mass, void* stream) {
+  if (!c || !n || !ijk || !mass) return FMM_ERR_ARG;
+  if (lmin < 2 || lmax < lmin || lmax > kMaxLevel || lo < lmin || lo > lmax) return FMM_ERR_ARG;
+  if (!c->have_levels) {
+    if (lo != lmin) {
+      c->last_error = "first fmm_set_levels must give the whole hierarchy (lo == lmin)";
+      return FMM_ERR_STATE;
+    }
+  } else if (lmin != c->lmin || lmax != c->lmax) {
+    c->last_error = "fmm_set_levels: lmin/lmax differ from the hierarchy being updated";
+    return FMM_ERR_STATE;
+  }
+  for (int k = 0; k <= lmax - lo; ++k)
+    if (n[k] < 0 || (n[k] > 0 && (!ijk[k] || !mass[k]))) return FMM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  ++c->n_set;
+  c->lmin = lmin;
+  c->lmax = lmax;
+  c->have_levels = false;
+  for (int l = lo; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    int64_t nl = n[l - lo];
+    T.n_leaf = nl;
+    CKS(buf_ensure(c, T.ijk, nl * 12));
+    CKS(buf_ensure(c, T.mass, nl * 8));
+    if (nl) {
+      CKS(cudaMemcpyAsync(T.ijk.ptr, ijk[l - lo], nl * 12, cudaMemcpyDefault, st));
+      CKS(cudaMemcpyAsync(T.mass.ptr, mass[l - lo], nl * 8, cudaMemcpyDefault, st));
+    }
+  }
+  fmm_status s = tree_build(c, st);
+  if (s != FMM_OK) return s;
+  s = size_expansions(c);
+  if (s != FMM_OK) return s;
+  CKS(cudaStreamSynchronize(st));
+  c->have_levels = true;
+  return FMM_OK;
+}
+
+fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, void* stream) {
+  if (!c || !phi || !accel) return FMM_ERR_ARG;
+  if (!c->have_levels) {
+    c->last_error = "fmm_solve before fmm_set_levels";
+    return FMM_ERR_STATE;
+  }
+  if (lo < c->lmin || lo > c->lmax) return FMM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  ++c->n_solve;
+  const bool f64 = c->cfg.precision == FMM_FP64;
+  const int ob = c->cfg.out_fp32 ? 4 : 8;
+  // outputs: device pointers are written directly, host pointers go through staging
+  std::vector<void*> dphi(c->lmax + 1, nullptr), dacc(c->lmax + 1, nullptr);
+  std::vector<char> host_out(c->lmax + 1, 0);
+  size_t stage_bytes = 0;
+  for (int l = lo; l <= c->lmax; ++l) {
+    int64_t nl = c->lev[l].n_leaf;
+    if (!nl) continue;
+    if (!phi[l - lo] || !accel[l - lo]) return FMM_ERR_ARG;
+    host_out[l] = !(is_device_ptr(phi[l - lo]) && is_device_ptr(accel[l - lo]));
+    if (host_out[l]) stage_bytes += nl * 4 * ob + 256;
+  }
+  if (stage_bytes) {
+    if (c->out_stage.bytes < stage_bytes) {
+      // only host outputs ever allocate here; device outputs never do
+      CKS(buf_ensure(c, c->out_stage, stage_bytes));
+    }
+    size_t off = 0;
+    for (int l = lo; l <= c->lmax; ++l)
+      if (host_out[l]) {
+        int64_t nl = c->lev[l].n_leaf;
+        dphi[l] = (char*)c->out_stage.ptr + off;
+        off += (nl * ob + 255) / 256 * 256;
+        dacc[l] = (char*)c->out_stage.ptr + off;
+        off += (nl * 3 * ob + 255) / 256 * 256;
+      }
+  }
+  for (int l = lo; l <= c->lmax; ++l)
+    if (!host_out[l]) {
+      dphi[l] = phi[l - lo];
+      dacc[l] = accel[l - lo];
+    }
+
+  stage_event(c, 0, st);
+  // 1. upward
+  launch_mono_leaves(c, c->lmax, st);
+  for (int b = c->lmax - 1; b >= 1; --b) launch_upward(c, b, st);
+  stage_event(c, 1, st);
+  // 2. downward: L2L + M2L, box levels 2..lmax-2
+  if (c->lmax - 2 >= 2) CKS(cudaMemsetAsync(c->lev[2].L.ptr, 0, c->lev[2].L.bytes, st));
+  for (int b = 2; b <= c->lmax - 2; ++b) {
+    if (b >= 3) launch_l2l(c, b, st);
+    if (f64)
+      launch_gemm_f64(c, c->op_m2l, kModeM2L, b, st);
+    else
+      launch_gemm_tc(c, c->op_m2l, kModeM2L, b, st);
+  }
+  stage_event(c, 2, st);
+  // 3a. bottom intermediate field, M2P from level l-1 cells
+  for (int l = lo; l <= c->lmax; ++l) {
+    if (!c->lev[l].n_leaf) continue;
+    CKS(cudaMemsetAsync(c->lev[l].acc.ptr, 0, c->lev[l].acc.bytes, st));
+    if (f64)
+      launch_gemm_f64(c, c->op_m2p, kModeM2P, l - 1, st);
+    else
+      launch_gemm_tc(c, c->op_m2p, kModeM2P, l - 1, st);
+  }
+  stage_event(c, 3, st);
+  // 3b. near / nearest / far fields and the scatter
+  for (int l = lo; l <= c->lmax; ++l) {
+    if (!c->lev[l].n_leaf) continue;
+    launch_near(c, l, dphi[l], dacc[l], c->cfg.out_fp32, st);
+  }
+  stage_event(c, 4, st);
+  CKS(cudaGetLastError());
+  for (int l = lo; l <= c->lmax; ++l)
+    if (host_out[l]) {
+      int64_t nl = c->lev[l].n_leaf;
+      CKS(cudaMemcpyAsync(phi[l - lo], dphi[l], nl * ob, cudaMemcpyDeviceToHost, st));
+      CKS(cudaMemcpyAsync(accel[l - lo], dacc[l], nl * 3 * ob, cudaMemcpyDeviceToHost, st));
+    }
+  return FMM_OK;
+}
+
+fmm_status fmm_sync(fmm_ctx* c) {
+  if (!c) return FMM_ERR_ARG;
+  CKS(cudaStreamSynchronize(c->last_stream));
+  unsigned e = 0;
+  CKS(cudaMemcpy(&e, c->d_err, 4, cudaMemcpyDeviceToHost));
+  if (c->timing) {
+    for (int i = 0; i < 4; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+      c->stage_ms[i] = ms;
+    }
+  }
+  if (e & kErrTimeout) {
+    c->last_error = "a bounded device-side wait timed out";
+    cudaMemset(c->d_err, 0, 4);
+    return FMM_ERR_TIMEOUT;
+  }
+  return FMM_OK;
+}
+
+const char* fmm_last_error(const fmm_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+void fmm_destroy(fmm_ctx* c) {
+  if (!c) return;
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  for (auto& T : c->lev) {
+    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.tgt, &T.ijk,
+                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.acc})
+      buf_free(c, *b);
+  }
+  for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_g,
+                    &c->d_l2l_e, &c->d_l2l_c, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
+                    &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
+                    &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
+                    &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->out_stage, &c->in_stage})
+    buf_free(c, *b);
+  if (c->d_err) cudaFree(c->d_err);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete c;
+}
+
+fmm_status fmm_tree_counts(const fmm_ctx* c, int64_t* n_oct) {
+  if (!c || !n_oct) return FMM_ERR_ARG;
+  if (!c->have_levels) return FMM_ERR_STATE;
+  for (int l = 0; l <= c->lmax; ++l) n_oct[l] = (l == 0) ? 0 : c->lev[l].n_oct;
+  return FMM_OK;
+}
+
+fmm_status fmm_tree_export(const fmm_ctx* cc, int level, uint64_t* oct_key, int64_t* status, int64_t* nbr) {
+  fmm_ctx* c = const_cast<fmm_ctx*>(cc);
+  if (!c || !oct_key || !status || !nbr) return FMM_ERR_ARG;
+  if (!c->have_levels) return FMM_ERR_STATE;
+  if (level < 1 || level > c->lmax) return FMM_ERR_ARG;
+  const LevelTree& T = c->lev[level];
+  int64_t no = T.n_oct;
+  std::vector<int32_t> cc32(8 * no), nb32(27 * no);
+  CKS(cudaMemcpy(oct_key, T.oct_key.ptr, no * 8, cudaMemcpyDeviceToHost));
+  CKS(cudaMemcpy(cc32.data(), T.cell_child.ptr, no * 32, cudaMemcpyDeviceToHost));
+  CKS(cudaMemcpy(nb32.data(), T.nbr.ptr, no * 27 * 4, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < 8 * no; ++i) {
+    int32_t v = cc32[i];
+    // the finest level has no refined cells: a non-negative entry cannot occur there
+    status[i] = v;
+  }
+  for (int64_t i = 0; i < 27 * no; ++i) nbr[i] = nb32[i];
+  return FMM_OK;
+}
+
+fmm_status fmm_host_numerators(int q, const int64_t* u, int64_t* out) {
+  if (!u || !out || q < 0 || q > 12) return FMM_ERR_ARG;
+  MultiIdx mi;
+  mi.build(q);
+  std::vector<__int128> P;
+  inv_r_numerators(q, u, P, mi);
+  for (int k = 0; k < mi.size(); ++k) {
+    if (P[k] > (__int128)INT64_MAX || P[k] < (__int128)INT64_MIN) return FMM_ERR_ARG;
+    out[k] = (int64_t)P[k];
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_host_table(int p, int which, double* out, int64_t n) {
+  if (p < 1 || p > 8 || !out || which < 0 || which > 5) return FMM_ERR_ARG;
+  Tables t;
+  t.build(p);
+  const int nc = t.nc;
+  std::vector<double> v;
+  if (which == 0) v = t.m2p;
+  if (which == 1) v = t.m2l;
+  if (which == 2) v = t.nearop;
+  if (which == 3) v = t.l2p;
+  if (which == 4 || which == 5) {
+    const auto& off = which == 4 ? t.m2m_off : t.l2l_off;
+    const auto& g = which == 4 ? t.m2m_g : t.l2l_g;
+    const auto& e = which == 4 ? t.m2m_e : t.l2l_e;
+    const auto& cf = which == 4 ? t.m2m_c : t.l2l_c;
+    v.assign((size_t)8 * nc * nc, 0.0);
+    for (int c = 0; c < 8; ++c)
+      for (int a = 0; a < nc; ++a)
+        for (int j = off[a]; j < off[a + 1]; ++j)
+          v[((size_t)c * nc + a) * nc + g[j]] += cf[j] * child_sign(c, e[j]);
+  }
+  if ((int64_t)v.size() > n) return FMM_ERR_ARG;
+  std::memcpy(out, v.data(), v.size() * sizeof(double));
+  return FMM_OK;
+}
+
+fmm_status fmm_stats(const fmm_ctx* c, int64_t* out4) {
+  if (!c || !out4) return FMM_ERR_ARG;
+  out4[0] = c->n_launch;
+  out4[1] = c->n_cub;
+  out4[2] = c->n_solve;
+  out4[3] = c->n_set;
+  return FMM_OK;
+}
+
+fmm_status fmm_set_timing(fmm_ctx* c, int on) {
+  if (!c) return FMM_ERR_ARG;
+  c->timing = on != 0;
+  return FMM_OK;
+}
+
+fmm_status fmm_stage_times(const fmm_ctx* c, double* ms4) {
+  if (!c || !ms4) return FMM_ERR_ARG;
+  for (int i = 0; i < 4; ++i) ms4[i] = c->stage_ms[i];
+  return FMM_OK;
+}
+
+}  // extern "C"

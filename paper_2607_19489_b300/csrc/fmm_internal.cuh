@@ -1,0 +1,124 @@
+// fmm_internal.cuh -- shared declarations of the CUDA library.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fmm.h"
+#include "tables.h"
+
+namespace fmm {
+
+constexpr int kMaxLevel = 20;
+constexpr int kTopLevelFP64 = 4;  // mixed precision: box levels <= 4 use FP64 M2M
+
+// Error bits latched by kernels (atomicOr into DeviceState::err).
+enum : unsigned {
+  kErrOutOfBox = 1u,
+  kErrDuplicate = 2u,
+  kErrNotGraded = 4u,
+  kErrIncomplete = 8u,
+  kErrNonFinite = 16u,
+  kErrTimeout = 32u,
+};
+
+// Sign of prod_{i: e_i = 1} s_i for child c, s_i = +1 if bit i of c is set
+// (child in the upper half along axis i) else -1.
+__host__ __device__ inline int child_sign(int c, int e) {
+  return (__builtin_popcount(e & ~c & 7) & 1) ? -1 : 1;
+}
+
+// A grow-only device allocation.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx;
+cudaError_t buf_ensure(Ctx* c, DevBuf& b, size_t bytes);
+
+// Device-resident tree of one level.
+struct LevelTree {
+  int64_t n_oct = 0;     // octs of this level (level 0: 0; its single cell is the root)
+  int64_t n_leaf = 0;    // input leaves of this level
+  int64_t n_rows = 0;    // octs holding at least one refined cell
+  int64_t n_tgt = 0;     // octs holding at least one leaf cell
+  DevBuf oct_key;        // uint64 [n_oct]
+  DevBuf oct_parent;     // int32 [n_oct] cell id at level-1
+  DevBuf cell_child;     // int32 [8 n_oct]: >=0 child oct at level+1, else -1-leaf index
+  DevBuf nbr;            // int32 [n_oct][27]
+  DevBuf leaf_cell;      // int32 [n_leaf]
+  DevBuf rows;           // int32 [n_rows]
+  DevBuf tgt;            // int32 [n_tgt]
+  // inputs kept for adaptive time stepping (replaced by set_levels)
+  DevBuf ijk;            // int32 [n_leaf][3]
+  DevBuf mass;           // double [n_leaf]
+  // expansions (box units)
+  DevBuf M;              // [8 n_oct][nc] double (FP64 path / top levels) or float
+  DevBuf Mhi, Mlo;       // bf16 [8 n_oct][nc] (mixed path GEMM operands)
+  DevBuf mono;           // [8 n_oct] total mass per cell (double or float)
+  DevBuf L;              // double [8 n_oct][nc] local expansions (levels 2..lmax-2)
+  DevBuf acc;            // [8 n_oct][4] M2P result (double or float), targets of this level
+  bool m_is_f64 = true;
+};
+
+struct GemmOperand {  // one operator for the GEMM kernels
+  int N = 0, K = 0;     // logical sizes
+  int Npad = 0, Kpad = 0, BN = 0, ntile = 0;
+  DevBuf f64;           // FP64 [K][N] (N fastest) for the DFMA kernel
+  DevBuf hi, lo;        // bf16 [Npad][Kpad] (K fastest) for tcgen05
+  alignas(64) unsigned char tmap_hi[128];
+  alignas(64) unsigned char tmap_lo[128];
+  DevBuf klimit;        // int32 [N]: K entries per 26-offset segment to visit (FP64 kernel)
+  int kseg = 0;         // entries per offset segment (8*nc)
+};
+
+struct Ctx {
+  fmm_config cfg{};
+  Tables tab;
+  int lmin = -1, lmax = -1;
+  bool have_levels = false;
+  LevelTree lev[kMaxLevel + 1];
+  // device tables
+  DevBuf d_m2m_off, d_m2m_g, d_m2m_e, d_m2m_c;
+  DevBuf d_l2l_off, d_l2l_g, d_l2l_e, d_l2l_c;
+  DevBuf d_near64, d_near32, d_l2p64, d_l2p32;
+  GemmOperand op_m2p, op_m2l;
+  // scratch
+  DevBuf sort_tmp, keys_a, keys_b, vals_a, vals_b, flags, scan, err_word, counter;
+  DevBuf out_stage;     // device staging for host outputs
+  DevBuf in_stage;      // device staging for host inputs
+  unsigned* d_err = nullptr;
+  size_t bytes_in_use = 0;
+  std::string last_error;
+  cudaStream_t last_stream = nullptr;
+  int device = 0;
+  int num_sms = 148;
+  bool timing = false;
+  cudaEvent_t ev[5] = {};
+  double stage_ms[4] = {0, 0, 0, 0};
+  bool tables_on_device = false;
+  int64_t n_launch = 0, n_cub = 0, n_solve = 0, n_set = 0;
+};
+
+// ---- launchers (stream-ordered, no synchronisation) -----------------------
+// tree.cu
+fmm_status tree_build(Ctx* c, cudaStream_t st);
+// upward.cu
+void launch_mono_leaves(Ctx* c, int level, cudaStream_t st);
+void launch_upward(Ctx* c, int level, cudaStream_t st);
+void launch_l2l(Ctx* c, int level, cudaStream_t st);
+// gemm_f64.cu
+void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st);
+// gemm_tc.cu
+fmm_status make_tensor_maps(Ctx* c, GemmOperand& op);
+void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st);
+// near.cu
+void launch_near(Ctx* c, int level, void* phi, void* acc, int out_fp32, cudaStream_t st);
+
+enum { kModeM2P = 0, kModeM2L = 1 };
+
+}  // namespace fmm

@@ -1,0 +1,122 @@
+// gemm_f64.cu -- M2L (Eq. 3) and bottom M2P (Fig. 2, Alg. 4) in FP64 as
+// gathered contractions on the CUDA cores.
+//
+// A row is an oct of the source/target grid.  For each of the 26 neighbour
+// offsets q of the oct's parent, the 8 cells of the neighbour oct supply their
+// multipoles (the sources of the interaction list, Sec. 2); the operator maps
+// them to the 8 target cells (M2L: 8 local expansions) or to the 64 grandchild
+// cells (M2P: phi and accel).  The operator table is stored [K][N] with K
+// ordered (q, alpha, s) so that an output column with |beta| = d only visits
+// the prefix |alpha| <= p - d of each offset segment (the Eq. 3 truncation),
+// which skips the zeros of M2L entirely.
+#include "fmm_internal.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr int TM = 16;   // rows per block
+constexpr int KC = 64;   // K chunk staged in shared memory
+__constant__ int c_nbr26[26] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12,
+                                14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26};
+
+struct F64Params {
+  const double* M;          // sources [cells][nc] of the row level
+  const int32_t* rows;
+  int64_t nrows;
+  const int32_t* nbr;       // [oct][27] of the row level
+  const double* B;          // [26*KQ][N]
+  const int32_t* klimit;    // [N]
+  int KQ, N, nc;
+  int mode;
+  double* acc;              // M2P: [cells of level l][4]
+  const int32_t* cell_child_rows;
+  double* L;                // M2L: [cells][nc]
+};
+
+__global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
+  __shared__ double As[TM][KC];
+  __shared__ int32_t src[TM][26];
+  const int n = blockIdx.y * 256 + threadIdx.x;
+  const bool col_ok = n < P.N;
+  const int64_t r0 = (int64_t)blockIdx.x * TM;
+  for (int i = threadIdx.x; i < TM * 26; i += 256) {
+    int r = i / 26, q = i - r * 26;
+    int64_t ri = r0 + r;
+    src[r][q] = (ri < P.nrows) ? P.nbr[(int64_t)P.rows[ri] * 27 + c_nbr26[q]] : -1;
+  }
+  // block-wide K extent of a segment: max klimit over this block's columns
+  __shared__ int kmax_s;
+  if (threadIdx.x == 0) kmax_s = 0;
+  __syncthreads();
+  const int mylim = col_ok ? P.klimit[n] : 0;
+  atomicMax(&kmax_s, mylim);
+  __syncthreads();
+  const int kmax = kmax_s;
+  double acc[TM];
+#pragma unroll
+  for (int r = 0; r < TM; ++r) acc[r] = 0.0;
+  for (int q = 0; q < 26; ++q) {
+    for (int k0 = 0; k0 < kmax; k0 += KC) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < TM * KC; i += 256) {
+        int r = i / KC, kk = i - r * KC;
+        int k = k0 + kk;  // k = alpha*8 + s inside the segment
+        double v = 0.0;
+        int32_t so = src[r][q];
+        if (so >= 0 && k < P.KQ) {
+          int alpha = k >> 3, s = k & 7;
+          v = P.M[((int64_t)so * 8 + s) * P.nc + alpha];
+        }
+        As[r][kk] = v;
+      }
+      __syncthreads();
+      int kend = min(KC, mylim - k0);
+      const double* Bp = P.B + ((int64_t)q * P.KQ + k0) * P.N + n;
+      for (int kk = 0; kk < kend; ++kk) {
+        double b = Bp[(int64_t)kk * P.N];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) acc[r] = fma(As[r][kk], b, acc[r]);
+      }
+    }
+  }
+  if (!col_ok) return;
+  for (int r = 0; r < TM; ++r) {
+    int64_t ri = r0 + r;
+    if (ri >= P.nrows) break;
+    int32_t o = P.rows[ri];
+    if (P.mode == kModeM2P) {
+      int f = n >> 5, t = (n >> 2) & 7, comp = n & 3;
+      int32_t ch = P.cell_child_rows[(int64_t)o * 8 + f];
+      if (ch >= 0) P.acc[((int64_t)ch * 8 + t) * 4 + comp] = acc[r];
+    } else {
+      int b = n / P.nc, beta = n - b * P.nc;
+      P.L[((int64_t)o * 8 + b) * P.nc + beta] += acc[r];
+    }
+  }
+}
+
+}  // namespace
+
+void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream_t st) {
+  LevelTree& R = c->lev[lr];
+  if (!R.n_rows) return;
+  F64Params P;
+  P.M = (const double*)R.M.ptr;
+  P.rows = (const int32_t*)R.rows.ptr;
+  P.nrows = R.n_rows;
+  P.nbr = (const int32_t*)R.nbr.ptr;
+  P.B = (const double*)op.f64.ptr;
+  P.klimit = (const int32_t*)op.klimit.ptr;
+  P.KQ = op.kseg;
+  P.N = op.N;
+  P.nc = c->tab.nc;
+  P.mode = mode;
+  P.acc = (mode == kModeM2P) ? (double*)c->lev[lr + 1].acc.ptr : nullptr;
+  P.cell_child_rows = (const int32_t*)R.cell_child.ptr;
+  P.L = (mode == kModeM2L) ? (double*)R.L.ptr : nullptr;
+  dim3 grid((unsigned)((R.n_rows + TM - 1) / TM), (unsigned)((op.N + 255) / 256));
+  ++c->n_launch;
+  k_gemm_f64<<<grid, 256, 0, st>>>(P);
+}
+
+}  // namespace fmm

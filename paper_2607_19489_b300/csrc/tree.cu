@@ -1,0 +1,331 @@
+// tree.cu -- BuildTree for all levels (Sec. 3.1, Alg. 2) and the neighbour
+// index that the merged-tree searches of Sec. 3.2 reduce to.
+//
+// Per level l, from lmax down to lmin, the cells of level l are the input
+// leaves plus the parents of the level l+1 octs.  They are radix sorted by
+// Morton key (x in the lowest bit of each triple); consecutive runs of the
+// same key>>3 are the octs of level l, so after sorting cell id = 8*oct +
+// (key & 7), the order the paper's oct tree (RAMSES) and the oracle use.
+// Duplicates, incomplete octs, out-of-box indices and non-finite masses are
+// latched as error bits.  Levels below lmin are complete grids.
+//
+// The 27-neighbour index is then built top-down without hashing: the
+// neighbour (dx,dy,dz) of oct o's parent cell lies in the parent oct's own
+// neighbour table, and its child oct (or its leaf status) is read from that
+// level's cell_child array -- the fully threaded tree idea of RAMSES.
+#include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+namespace {
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1FFFFF;
+  x = (x | (x << 32)) & 0x1F00000000FFFFull;
+  x = (x | (x << 16)) & 0x1F0000FF0000FFull;
+  x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+  x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__global__ void k_leaf_keys(int64_t n, const int32_t* __restrict__ ijk, const double* __restrict__ mass,
+                            int level, uint64_t* keys, int32_t* vals, unsigned* err) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x = ijk[3 * i], y = ijk[3 * i + 1], z = ijk[3 * i + 2];
+  int lim = 1 << level;
+  if (x < 0 || y < 0 || z < 0 || x >= lim || y >= lim || z >= lim) {
+    atomicOr(err, kErrOutOfBox);
+    x = y = z = 0;
+  }
+  if (!isfinite(mass[i])) atomicOr(err, kErrNonFinite);
+  keys[i] = spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+  vals[i] = (int32_t)(-1 - i);
+}
+
+__global__ void k_refined_keys(int64_t n, const uint64_t* __restrict__ octkey_next, uint64_t* keys,
+                               int32_t* vals) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = octkey_next[i];
+  vals[i] = (int32_t)i;
+}
+
+__global__ void k_oct_flags(int64_t n, const uint64_t* __restrict__ k, int32_t* flags, unsigned* err) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = 1;
+  if (i > 0) {
+    if (k[i] == k[i - 1]) atomicOr(err, kErrDuplicate);
+    f = (k[i] >> 3) != (k[i - 1] >> 3);
+  }
+  flags[i] = f;
+}
+
+__global__ void k_scatter_level(int64_t n, const uint64_t* __restrict__ k, const int32_t* __restrict__ v,
+                                const int32_t* __restrict__ scan, uint64_t* oct_key, int32_t* cell_child,
+                                int32_t* leaf_cell, int32_t* oct_parent_next, int64_t n_oct_next,
+                                int64_t n_leaf, unsigned* err) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t oct = scan[i] - 1;
+  uint64_t key = k[i];
+  if (i == 0 || (k[i - 1] >> 3) != (key >> 3)) oct_key[oct] = key >> 3;
+  if (i != 8 * oct + (int64_t)(key & 7)) {
+    atomicOr(err, kErrIncomplete);
+    return;
+  }
+  int32_t val = v[i];
+  cell_child[i] = val;
+  if (val >= 0) {
+    if (val < n_oct_next) oct_parent_next[val] = (int32_t)i;
+  } else {
+    int64_t li = -1 - (int64_t)val;
+    if (li < n_leaf) leaf_cell[li] = (int32_t)i;
+  }
+}
+
+__global__ void k_full_level(int64_t n_oct, uint64_t* oct_key, int32_t* oct_parent, int32_t* cell_child) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n_oct) {
+    oct_key[i] = (uint64_t)i;
+    oct_parent[i] = (int32_t)i;
+  }
+  if (i < 8 * n_oct) cell_child[i] = (int32_t)i;
+}
+
+__global__ void k_iota(int64_t n, int32_t* a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (int32_t)i;
+}
+
+// nbr[l][o][q] from the level l-1 tables.  One thread per (oct, q).
+__global__ void k_nbr(int level, int64_t n_oct, const int32_t* __restrict__ oct_parent,
+                      const int32_t* __restrict__ nbr_up, const int32_t* __restrict__ cell_child_up,
+                      const int32_t* __restrict__ cell_child_here, int32_t* nbr, unsigned* err) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_oct * 27) return;
+  int64_t o = t / 27;
+  int q = (int)(t - o * 27);
+  int d[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+  int32_t res;
+  if (level == 1) {
+    res = (q == 13) ? 0 : -1;
+  } else {
+    int32_t pc = oct_parent[o];
+    int32_t op = pc >> 3;
+    int cp = pc & 7;
+    int e = 0, newc = 0, mul = 1;
+    for (int i = 0; i < 3; ++i) {
+      int ex = ((cp >> i) & 1) + d[i];  // -1..2
+      int ei = (ex < 0) ? -1 : (ex >> 1);
+      e += (ei + 1) * mul;
+      mul *= 3;
+      newc |= (ex & 1) << i;
+    }
+    int32_t nb = nbr_up[(int64_t)op * 27 + e];
+    if (nb == -1) {
+      res = -1;  // outside the unit box
+    } else if (nb < -1) {
+      // the parent's neighbour at level l-1 does not exist although the parent is
+      // refined: its father has an unrefined neighbour (Sec. 3.2)
+      atomicOr(err, kErrNotGraded);
+      res = -1;
+    } else {
+      int32_t ncell = nb * 8 + newc;
+      int32_t ch = cell_child_up[ncell];
+      res = (ch >= 0) ? ch : (-2 - ncell);
+    }
+  }
+  nbr[t] = res;
+  // graded rule: a refined cell of this oct needs all in-box neighbours of its father refined
+  if (res < -1) {
+    bool any_ref = false;
+    for (int c = 0; c < 8; ++c) any_ref |= cell_child_here[o * 8 + c] >= 0;
+    if (any_ref) atomicOr(err, kErrNotGraded);
+  }
+}
+
+__global__ void k_oct_kind_flags(int64_t n_oct, const int32_t* __restrict__ cell_child, int32_t* f_rows,
+                                 int32_t* f_tgt) {
+  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  int r = 0, t = 0;
+  for (int c = 0; c < 8; ++c) {
+    int32_t ch = cell_child[o * 8 + c];
+    r |= ch >= 0;
+    t |= ch < 0;
+  }
+  f_rows[o] = r;
+  f_tgt[o] = t;
+}
+
+inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+#define CK(x)                                                        \
+  do {                                                               \
+    cudaError_t e_ = (x);                                            \
+    if (e_ != cudaSuccess) {                                         \
+      c->last_error = std::string("tree: ") + cudaGetErrorString(e_); \
+      return e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA; \
+    }                                                                \
+  } while (0)
+
+fmm_status err_to_status(unsigned e) {
+  if (e & kErrOutOfBox) return FMM_ERR_OUT_OF_BOX;
+  if (e & kErrNonFinite) return FMM_ERR_NONFINITE;
+  if (e & kErrDuplicate) return FMM_ERR_DUPLICATE;
+  if (e & kErrIncomplete) return FMM_ERR_INCOMPLETE;
+  if (e & kErrNotGraded) return FMM_ERR_NOT_GRADED;
+  if (e & kErrTimeout) return FMM_ERR_TIMEOUT;
+  return FMM_OK;
+}
+
+}  // namespace
+
+fmm_status tree_build(Ctx* c, cudaStream_t st) {
+  const int lmin = c->lmin, lmax = c->lmax;
+  unsigned* err = c->d_err;
+  CK(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  // ---- bottom-up sorted passes, levels lmax..lmin -------------------------
+  for (int l = lmax; l >= lmin; --l) {
+    LevelTree& T = c->lev[l];
+    int64_t n_ref = (l < lmax) ? c->lev[l + 1].n_oct : 0;
+    int64_t n = T.n_leaf + n_ref;
+    if (n == 0 || n > (int64_t)INT32_MAX / 2) {
+      c->last_error = "tree: level " + std::to_string(l) + " has no cells or too many";
+      return n == 0 ? FMM_ERR_INCOMPLETE : FMM_ERR_ARG;
+    }
+    CK(buf_ensure(c, c->keys_a, n * 8));
+    CK(buf_ensure(c, c->keys_b, n * 8));
+    CK(buf_ensure(c, c->vals_a, n * 4));
+    CK(buf_ensure(c, c->vals_b, n * 4));
+    CK(buf_ensure(c, c->flags, n * 4));
+    CK(buf_ensure(c, c->scan, n * 4));
+    uint64_t* ka = (uint64_t*)c->keys_a.ptr;
+    uint64_t* kb = (uint64_t*)c->keys_b.ptr;
+    int32_t* va = (int32_t*)c->vals_a.ptr;
+    int32_t* vb = (int32_t*)c->vals_b.ptr;
+    if (T.n_leaf)
+      ++c->n_launch;
+      k_leaf_keys<<<nblk(T.n_leaf), 256, 0, st>>>(T.n_leaf, (const int32_t*)T.ijk.ptr,
+                                                  (const double*)T.mass.ptr, l, ka, va, err);
+    if (n_ref) ++c->n_launch;
+    if (n_ref)
+      k_refined_keys<<<nblk(n_ref), 256, 0, st>>>(n_ref, (const uint64_t*)c->lev[l + 1].oct_key.ptr,
+                                                  ka + T.n_leaf, va + T.n_leaf);
+    size_t tmp = 0;
+    ++c->n_cub; CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
+    CK(buf_ensure(c, c->sort_tmp, tmp));
+    ++c->n_cub; CK(cub::DeviceRadixSort::SortPairs(c->sort_tmp.ptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
+    int32_t* flags = (int32_t*)c->flags.ptr;
+    int32_t* scan = (int32_t*)c->scan.ptr;
+    ++c->n_launch;
+    k_oct_flags<<<nblk(n), 256, 0, st>>>(n, kb, flags, err);
+    tmp = 0;
+    ++c->n_cub; CK(cub::DeviceScan::InclusiveSum(nullptr, tmp, flags, scan, (int)n, st));
+    CK(buf_ensure(c, c->sort_tmp, tmp));
+    ++c->n_cub; CK(cub::DeviceScan::InclusiveSum(c->sort_tmp.ptr, tmp, flags, scan, (int)n, st));
+    int32_t n_oct32 = 0;
+    CK(cudaMemcpyAsync(&n_oct32, scan + n - 1, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    T.n_oct = n_oct32;
+    if (8 * T.n_oct != n || (l == lmin && T.n_oct != (int64_t)1 << (3 * (l - 1)))) {
+      c->last_error = "tree: level " + std::to_string(l) + " has incomplete octs or does not cover the box";
+      unsigned e = 0;
+      CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      fmm_status s = err_to_status(e);
+      return s != FMM_OK ? s : FMM_ERR_INCOMPLETE;
+    }
+    CK(buf_ensure(c, T.oct_key, T.n_oct * 8));
+    CK(buf_ensure(c, T.oct_parent, T.n_oct * 4));
+    CK(buf_ensure(c, T.cell_child, T.n_oct * 32));
+    CK(buf_ensure(c, T.leaf_cell, std::max<int64_t>(T.n_leaf, 1) * 4));
+    int32_t* par_next = (l < lmax) ? (int32_t*)c->lev[l + 1].oct_parent.ptr : nullptr;
+    ++c->n_launch;
+    k_scatter_level<<<nblk(n), 256, 0, st>>>(n, kb, vb, scan, (uint64_t*)T.oct_key.ptr,
+                                             (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr,
+                                             par_next, n_ref, T.n_leaf, err);
+  }
+  {  // stop before the neighbour stage if the sorted passes found an invalid hierarchy:
+     // its parent/child links may be incomplete
+    unsigned e = 0;
+    CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (e) {
+      c->last_error = "tree: invalid hierarchy (error bits " + std::to_string(e) + ")";
+      return err_to_status(e);
+    }
+  }
+  // ---- complete grids below lmin and the root ------------------------------
+  for (int l = 1; l < lmin; ++l) {
+    LevelTree& T = c->lev[l];
+    T.n_oct = (int64_t)1 << (3 * (l - 1));
+    T.n_leaf = 0;
+    CK(buf_ensure(c, T.oct_key, T.n_oct * 8));
+    CK(buf_ensure(c, T.oct_parent, T.n_oct * 4));
+    CK(buf_ensure(c, T.cell_child, T.n_oct * 32));
+    ++c->n_launch;
+    k_full_level<<<nblk(8 * T.n_oct), 256, 0, st>>>(T.n_oct, (uint64_t*)T.oct_key.ptr,
+                                                     (int32_t*)T.oct_parent.ptr, (int32_t*)T.cell_child.ptr);
+  }
+  // octs of level lmin: their parents are the complete grid of level lmin-1
+  ++c->n_launch;
+  k_iota<<<nblk(c->lev[lmin].n_oct), 256, 0, st>>>(c->lev[lmin].n_oct, (int32_t*)c->lev[lmin].oct_parent.ptr);
+  {
+    LevelTree& R = c->lev[0];
+    R.n_oct = 0;
+    CK(buf_ensure(c, R.cell_child, 32));
+    CK(cudaMemsetAsync(R.cell_child.ptr, 0, 4, st));
+  }
+  // ---- neighbour tables top-down -------------------------------------------
+  for (int l = 1; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    CK(buf_ensure(c, T.nbr, T.n_oct * 27 * 4));
+    const int32_t* nbr_up = (l >= 2) ? (const int32_t*)c->lev[l - 1].nbr.ptr : nullptr;
+    const int32_t* cc_up = (const int32_t*)c->lev[l - 1].cell_child.ptr;
+    ++c->n_launch;
+    k_nbr<<<nblk(T.n_oct * 27), 256, 0, st>>>(l, T.n_oct, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
+                                              (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr, err);
+  }
+  // ---- row lists: octs with a refined cell / with a leaf cell ----------------
+  std::vector<int32_t> counts(2 * (lmax + 1), 0);
+  CK(buf_ensure(c, c->counter, 8 * (lmax + 1) + 8));
+  int32_t* d_counts = (int32_t*)c->counter.ptr;
+  for (int l = 1; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    int64_t n = T.n_oct;
+    CK(buf_ensure(c, c->flags, n * 8));
+    CK(buf_ensure(c, T.rows, n * 4));
+    CK(buf_ensure(c, T.tgt, n * 4));
+    int32_t* fr = (int32_t*)c->flags.ptr;
+    int32_t* ft = fr + n;
+    ++c->n_launch;
+    k_oct_kind_flags<<<nblk(n), 256, 0, st>>>(n, (const int32_t*)T.cell_child.ptr, fr, ft);
+    thrust::counting_iterator<int32_t> it(0);
+    size_t tmp = 0;
+    ++c->n_cub; CK(cub::DeviceSelect::Flagged(nullptr, tmp, it, fr, (int32_t*)T.rows.ptr, d_counts + 2 * l, (int)n, st));
+    CK(buf_ensure(c, c->sort_tmp, tmp));
+    ++c->n_cub; CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, fr, (int32_t*)T.rows.ptr, d_counts + 2 * l,
+                                  (int)n, st));
+    ++c->n_cub; CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, ft, (int32_t*)T.tgt.ptr, d_counts + 2 * l + 1,
+                                  (int)n, st));
+  }
+  CK(cudaMemcpyAsync(counts.data() + 2, d_counts + 2, 8 * lmax, cudaMemcpyDeviceToHost, st));
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int l = 1; l <= lmax; ++l) {
+    c->lev[l].n_rows = counts[2 * l];
+    c->lev[l].n_tgt = counts[2 * l + 1];
+  }
+  fmm_status s = err_to_status(e);
+  if (s != FMM_OK) c->last_error = "tree: invalid hierarchy (error bits " + std::to_string(e) + ")";
+  return s;
+}
+
+}  // namespace fmm

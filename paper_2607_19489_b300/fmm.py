@@ -1,0 +1,231 @@
+"""Python binding of libfmm (include/fmm.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library; this module only passes
+pointers, sizes and streams.  PyTorch provides device memory and streams.
+If the compiled library is missing the import of `lib()` raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmm.so")
+
+STATUS = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_NOT_GRADED", -3: "FMM_ERR_DUPLICATE",
+          -4: "FMM_ERR_OUT_OF_BOX", -5: "FMM_ERR_OOM", -6: "FMM_ERR_CUDA", -7: "FMM_ERR_NONFINITE",
+          -8: "FMM_ERR_STATE", -9: "FMM_ERR_TIMEOUT", -10: "FMM_ERR_INCOMPLETE"}
+PRECISION = {"fp64": 0, "mixed": 1, "bf16x3": 1}
+
+EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_error", "fmm_destroy",
+            "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
+            "fmm_set_timing", "fmm_stage_times", "fmm_stats"]
+
+
+class FMMError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("G", ctypes.c_double),
+                ("out_fp32", ctypes.c_int), ("mem_budget", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfmm.so (built by paper_2607_19489_b300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2607_19489_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    L.fmm_create.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(P)]
+    L.fmm_set_levels.argtypes = [P, I, I, I, P, P, P, P]
+    L.fmm_solve.argtypes = [P, I, P, P, P]
+    L.fmm_sync.argtypes = [P]
+    L.fmm_last_error.argtypes = [P]
+    L.fmm_last_error.restype = ctypes.c_char_p
+    L.fmm_destroy.argtypes = [P]
+    L.fmm_destroy.restype = None
+    L.fmm_tree_counts.argtypes = [P, P]
+    L.fmm_tree_export.argtypes = [P, I, P, P, P]
+    L.fmm_host_numerators.argtypes = [I, P, P]
+    L.fmm_host_table.argtypes = [I, I, P, I64]
+    L.fmm_stats.argtypes = [P, P]
+    L.fmm_set_timing.argtypes = [P, I]
+    L.fmm_stage_times.argtypes = [P, P]
+    for name in EXPORTED:
+        fn = getattr(L, name)
+        if name not in ("fmm_last_error", "fmm_destroy"):
+            fn.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptrs(values):
+    arr = (ctypes.c_void_p * max(1, len(values)))()
+    for i, v in enumerate(values):
+        arr[i] = v
+    return arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def host_numerators(q: int, u) -> np.ndarray:
+    """Integer numerators of d^gamma(1/r) at integer u, |gamma| <= q (host only)."""
+    u = np.ascontiguousarray(u, dtype=np.int64)
+    n = (q + 1) * (q + 2) * (q + 3) // 6
+    out = np.zeros(n, np.int64)
+    rc = lib().fmm_host_numerators(q, u.ctypes.data, out.ctypes.data)
+    if rc:
+        raise FMMError(rc, "fmm_host_numerators")
+    return out
+
+
+_TABLE_SHAPES = {
+    0: lambda nc: (256, 26 * 8 * nc), 1: lambda nc: (8 * nc, 26 * 8 * nc), 2: lambda nc: (343, nc, 4),
+    3: lambda nc: (64, nc, 4), 4: lambda nc: (8, nc, nc), 5: lambda nc: (8, nc, nc)}
+TABLES = {"m2p": 0, "m2l": 1, "near": 2, "l2p": 3, "m2m": 4, "l2l": 5}
+
+
+def host_table(p: int, which: str) -> np.ndarray:
+    """FP64 translation operator built by the library's host code (no GPU)."""
+    nc = (p + 1) * (p + 2) * (p + 3) // 6
+    shape = _TABLE_SHAPES[TABLES[which]](nc)
+    out = np.zeros(int(np.prod(shape)), np.float64)
+    rc = lib().fmm_host_table(p, TABLES[which], out.ctypes.data, out.size)
+    if rc:
+        raise FMMError(rc, "fmm_host_table")
+    return out.reshape(shape)
+
+
+class Solver:
+    """One FMM context (fmm_ctx) on the current CUDA device."""
+
+    def __init__(self, p: int = 6, precision: str = "mixed", G: float = 1.0, out_fp32: bool = False,
+                 mem_budget: int = 0):
+        self.p = p
+        self.precision = precision
+        self.out_fp32 = out_fp32
+        cfg = _Config(p, PRECISION[precision], float(G), int(out_fp32), int(mem_budget))
+        h = ctypes.c_void_p()
+        rc = lib().fmm_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc:
+            raise FMMError(rc, "fmm_create")
+        self._h = h
+        self.lmin = self.lmax = None
+        self.n = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.fmm_destroy(h)
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    def _check(self, rc, what):
+        if rc:
+            msg = lib().fmm_last_error(self._h)
+            raise FMMError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_levels(self, lmin: int, lmax: int, ijk, mass, lo: int | None = None, stream=None):
+        """ijk[k] int32 [n,3] and mass[k] float64 [n] for levels lo..lmax (torch tensors on
+        the device, or numpy arrays on the host)."""
+        lo = lmin if lo is None else lo
+        n = np.array([int(a.shape[0]) for a in ijk], dtype=np.int64)
+        keep = list(ijk) + list(mass)
+        pi = _ptrs([_data_ptr(a) for a in ijk])
+        pm = _ptrs([_data_ptr(m) for m in mass])
+        rc = lib().fmm_set_levels(self._h, lmin, lmax, lo, n.ctypes.data, pi, pm, _stream_ptr(stream))
+        del keep
+        if rc:
+            self.lmin = self.lmax = None
+        self._check(rc, "fmm_set_levels")
+        self.lmin, self.lmax = lmin, lmax
+        for k, l in enumerate(range(lo, lmax + 1)):
+            self.n[l] = int(n[k])
+
+    def set_hierarchy(self, h, device="cuda", lo: int | None = None, stream=None):
+        import torch
+        lo = h.lmin if lo is None else lo
+        ks = range(lo - h.lmin, h.lmax - h.lmin + 1)
+        ijk = [torch.as_tensor(h.ijk[k], dtype=torch.int32, device=device).contiguous() for k in ks]
+        mass = [torch.as_tensor(h.mass[k], dtype=torch.float64, device=device).contiguous() for k in ks]
+        self.set_levels(h.lmin, h.lmax, ijk, mass, lo=lo, stream=stream)
+
+    def alloc_outputs(self, lo: int | None = None, device="cuda"):
+        import torch
+        lo = self.lmin if lo is None else lo
+        dt = torch.float32 if self.out_fp32 else torch.float64
+        phi = {l: torch.empty(self.n[l], dtype=dt, device=device) for l in range(lo, self.lmax + 1)}
+        acc = {l: torch.empty(self.n[l], 3, dtype=dt, device=device) for l in range(lo, self.lmax + 1)}
+        return phi, acc
+
+    def solve(self, lo: int | None = None, out=None, stream=None):
+        """Returns (phi, acc): dicts level -> tensor in the caller's input order."""
+        if self.lmin is None:  # no hierarchy yet: let the library report the state error
+            empty = _ptrs([])
+            self._check(lib().fmm_solve(self._h, 0 if lo is None else lo, empty, empty, _stream_ptr(stream)),
+                        "fmm_solve")
+        lo = self.lmin if lo is None else lo
+        phi, acc = out if out is not None else self.alloc_outputs(lo)
+        levels = range(lo, self.lmax + 1)
+        pp = _ptrs([_data_ptr(phi[l]) for l in levels])
+        pa = _ptrs([_data_ptr(acc[l]) for l in levels])
+        rc = lib().fmm_solve(self._h, lo, pp, pa, _stream_ptr(stream))
+        self._check(rc, "fmm_solve")
+        return phi, acc
+
+    def sync(self):
+        self._check(lib().fmm_sync(self._h), "fmm_sync")
+
+    def set_timing(self, on: bool):
+        self._check(lib().fmm_set_timing(self._h, int(on)), "fmm_set_timing")
+
+    def stage_times(self):
+        out = np.zeros(4)
+        self._check(lib().fmm_stage_times(self._h, out.ctypes.data), "fmm_stage_times")
+        return dict(zip(["upward", "downward", "m2p", "near"], out.tolist()))
+
+    def stats(self):
+        out = np.zeros(4, np.int64)
+        self._check(lib().fmm_stats(self._h, out.ctypes.data), "fmm_stats")
+        return dict(zip(["launches", "cub_calls", "solves", "set_levels"], out.tolist()))
+
+    def tree_counts(self):
+        out = np.zeros(self.lmax + 1, np.int64)
+        self._check(lib().fmm_tree_counts(self._h, out.ctypes.data), "fmm_tree_counts")
+        return out
+
+    def tree_export(self, level: int):
+        n_oct = int(self.tree_counts()[level])
+        keys = np.zeros(n_oct, np.uint64)
+        status = np.zeros(8 * n_oct, np.int64)
+        nbr = np.zeros(27 * n_oct, np.int64)
+        self._check(lib().fmm_tree_export(self._h, level, keys.ctypes.data, status.ctypes.data,
+                                          nbr.ctypes.data), "fmm_tree_export")
+        return keys, status, nbr.reshape(-1, 27)
+
+
+def _data_ptr(a):
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr() if a.numel() else None
+    a = np.asarray(a)
+    return a.ctypes.data if a.size else None

@@ -1,0 +1,231 @@
+"""CUDA path against the CPU oracle, through the C ABI.
+
+Bars (from the method's accuracy targets): FP64 path relative RMS error
+<= 1e-10 in phi and accel; mixed path (split-BF16 tensor-core M2L/M2P, FP32
+P2P) <= 1e-4 in accel; tree index bit-exact.  Cases span several GEMM tiles
+with ragged tails, coarse-fine interfaces, an empty base level, the smallest
+hierarchy (4^3, no far field) and the two-level 64^3 + 32^3 workload on
+sampled targets."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_19489_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-4
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def run(h, p, precision, lo=None, out_fp32=False, sel=None):
+    from paper_2607_19489_b300 import fmm
+    torch = _torch()
+    s = fmm.Solver(p, precision, out_fp32=out_fp32)
+    s.set_hierarchy(h)
+    phi, acc = s.solve(lo)
+    torch.cuda.synchronize()
+    s.sync()
+    out_p = {l: phi[l].double().cpu().numpy() for l in phi}
+    out_a = {l: acc[l].double().cpu().numpy() for l in acc}
+    if sel is not None:
+        out_p = {l: out_p[l][sel[l]] for l in sel}
+        out_a = {l: out_a[l][sel[l]] for l in sel}
+    return out_p, out_a
+
+
+def rel_rms(got: dict, ref: dict):
+    num = sum(((got[l] - ref[l]) ** 2).sum() for l in ref)
+    den = sum((ref[l] ** 2).sum() for l in ref)
+    return float(np.sqrt(num / den))
+
+
+def small_cases():
+    return {
+        "unigrid16": W.unigrid_plummer(4),
+        "amr_3_5": W.random_amr(3, 5, seed=13),
+        "amr_3_5b": W.random_amr(3, 5, seed=19),
+        "twolevel16": W.two_level_plummer(base=4, lo=4, hi=12, seed=3),
+        "empty_base": _empty_base(),
+        "tiny4": W.unigrid_plummer(2),
+    }
+
+
+def _empty_base():
+    refined = W.nested_boxes(3, [(0, 8), (4, 12)])
+    leaves = W.leaves_from_refined(3, 5, refined)
+    h = W.Hierarchy(3, 5, name="empty base level")
+    for k, c in enumerate(leaves):
+        h.ijk.append(np.ascontiguousarray(c, dtype=np.int32))
+        h.mass.append(W.uniform(9, 50 + k, np.arange(c.shape[0])) + 0.1)
+    return h
+
+
+CASES = small_cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tree_bit_exact(name):
+    from paper_2607_19489_b300 import fmm
+    h = CASES[name]
+    ref = oracle.tree(h)
+    s = fmm.Solver(4, "fp64")
+    s.set_hierarchy(h)
+    for l in range(1, h.lmax + 1):
+        k, st, nb = s.tree_export(l)
+        rk, rst, rnb = ref[l]
+        assert np.array_equal(k, rk), (name, l)
+        assert np.array_equal(st, rst), (name, l)
+        assert np.array_equal(nb, rnb), (name, l)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("p", [4, 6])
+def test_fp64_matches_oracle(name, p):
+    h = CASES[name]
+    rp, ra = oracle.solve(h, p)
+    gp, ga = run(h, p, "fp64")
+    assert rel_rms(gp, rp) <= FP64_TOL
+    assert rel_rms(ga, ra) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("p", [4, 6])
+def test_mixed_matches_oracle(name, p):
+    h = CASES[name]
+    rp, ra = oracle.solve(h, p)
+    gp, ga = run(h, p, "mixed")
+    assert rel_rms(ga, ra) <= MIXED_TOL
+    assert rel_rms(gp, rp) <= MIXED_TOL
+
+
+def test_unigrid32_p4_fp64_full():
+    # 32^3 Plummer, p = 4, FP64 path on every cell
+    h = W.unigrid_plummer(5)
+    rp, ra = oracle.solve(h, 4)
+    gp, ga = run(h, 4, "fp64")
+    assert rel_rms(ga, ra) <= FP64_TOL and rel_rms(gp, rp) <= FP64_TOL
+
+
+def _sample(h, n_per_level, seed):
+    sel = {}
+    for k, l in enumerate(h.levels):
+        n = h.n(l)
+        u = W.uniform(seed, 900 + l, np.arange(min(n, n_per_level)))
+        idx = np.unique((u * n).astype(np.int64))
+        # also every cell next to a coarse-fine interface of this level
+        sel[l] = idx
+    return sel
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_TOL), ("fp64", FP64_TOL)])
+def test_twolevel64_p6_sampled(precision, tol):
+    # 64^3 base + 32^3 refined block, p = 6 (the measured workload), sampled targets
+    h = W.two_level_plummer()
+    sel = _sample(h, 1500, 77)
+    # add the cells on both sides of the coarse-fine interface
+    c = h.ijk[0]
+    ring = np.where((np.abs(c - 31.5).max(1) >= 8) & (np.abs(c - 31.5).max(1) <= 10))[0]
+    sel[6] = np.unique(np.concatenate([sel[6], ring[::7]]))
+    f = h.ijk[1]
+    edge = np.where(np.abs(f - 63.5).max(1) >= 15)[0]
+    sel[7] = np.unique(np.concatenate([sel[7], edge[::13]]))
+    rp, ra = oracle.solve(h, 6, sel=sel)
+    gp, ga = run(h, 6, precision, sel=sel)
+    assert rel_rms(ga, ra) <= tol
+    assert rel_rms(gp, rp) <= tol
+
+
+def test_caller_order_is_kept():
+    h = CASES["amr_3_5"]
+    hp = W.permute(h, seed=5)
+    gp, ga = run(h, 6, "fp64")
+    pp, pa = run(hp, 6, "fp64")
+    for k, l in enumerate(h.levels):
+        # map each permuted cell back to the original index
+        key = lambda a: a[:, 0] * 1_000_000 + a[:, 1] * 1000 + a[:, 2]
+        order = np.argsort(key(h.ijk[k]))
+        porder = np.argsort(key(hp.ijk[k]))
+        assert np.array_equal(pa[l][porder], ga[l][order])
+        assert np.array_equal(pp[l][porder], gp[l][order])
+
+
+def test_host_pointers_and_fp32_outputs():
+    from paper_2607_19489_b300 import fmm
+    h = CASES["twolevel16"]
+    gp, ga = run(h, 4, "mixed")
+    s = fmm.Solver(4, "mixed", out_fp32=True)
+    s.set_levels(h.lmin, h.lmax, [np.ascontiguousarray(a) for a in h.ijk], [np.ascontiguousarray(m) for m in h.mass])
+    phi = {l: np.zeros(h.n(l), np.float32) for l in h.levels}
+    acc = {l: np.zeros((h.n(l), 3), np.float32) for l in h.levels}
+    s.solve(out=(phi, acc))
+    s.sync()
+    for l in h.levels:
+        np.testing.assert_allclose(acc[l], ga[l], rtol=2e-5, atol=2e-6 * np.abs(ga[l]).max())
+        np.testing.assert_allclose(phi[l], gp[l], rtol=2e-6)
+
+
+def test_subcycle_levels_match_oracle():
+    # fmm_set_levels(lo) replaces the finer levels; fmm_solve(lo) returns levels lo..lmax
+    from paper_2607_19489_b300 import fmm
+    torch = _torch()
+    h = CASES["amr_3_5"]
+    s = fmm.Solver(6, "fp64")
+    s.set_hierarchy(h)
+    h2 = h.copy()
+    for k in (1, 2):
+        h2.mass[k] = h.mass[k] * (1.0 + 1e-3 * (2 * W.uniform(4, 60 + k, np.arange(h.mass[k].size)) - 1))
+    s.set_hierarchy(h2, lo=4)
+    phi, acc = s.solve(4)
+    torch.cuda.synchronize()
+    s.sync()
+    rp, ra = oracle.solve(h2, 6, lo=4)
+    assert set(phi) == {4, 5}
+    assert rel_rms({l: acc[l].cpu().numpy() for l in (4, 5)}, ra) <= FP64_TOL
+
+
+def test_invalid_hierarchies_rejected():
+    from paper_2607_19489_b300 import fmm
+    h = W.two_level_plummer(base=3, lo=2, hi=6)
+    cases = {}
+    bad = h.copy()
+    bad.ijk[0] = np.concatenate([bad.ijk[0], bad.ijk[0][:1]])
+    bad.mass[0] = np.concatenate([bad.mass[0], bad.mass[0][:1]])
+    cases["FMM_ERR_DUPLICATE"] = bad
+    bad = h.copy()
+    bad.ijk[0] = bad.ijk[0].copy()
+    bad.ijk[0][3] = [8, 0, 0]
+    cases["FMM_ERR_OUT_OF_BOX"] = bad
+    bad = h.copy()
+    bad.ijk[1] = bad.ijk[1][1:].copy()
+    bad.mass[1] = bad.mass[1][1:].copy()
+    cases["FMM_ERR_INCOMPLETE"] = bad
+    bad = h.copy()
+    bad.mass[1] = bad.mass[1].copy()
+    bad.mass[1][5] = np.nan
+    cases["FMM_ERR_NONFINITE"] = bad
+    bad = h.copy()
+    keep = ~(bad.ijk[1] == [4, 4, 4]).all(1)
+    bad.ijk[1] = bad.ijk[1][keep]
+    bad.mass[1] = bad.mass[1][keep]
+    bad.lmax = 5
+    bad.ijk.append(np.array([[8 + (k & 1), 8 + ((k >> 1) & 1), 8 + ((k >> 2) & 1)] for k in range(8)], np.int32))
+    bad.mass.append(np.ones(8) * 1e-3)
+    cases["FMM_ERR_NOT_GRADED"] = bad
+    for want, hh in cases.items():
+        s = fmm.Solver(4, "mixed")
+        with pytest.raises(fmm.FMMError) as ei:
+            s.set_hierarchy(hh)
+        assert ei.value.name == want
+        with pytest.raises(fmm.FMMError) as ei:
+            s.solve()
+        assert ei.value.name == "FMM_ERR_STATE"
+    s = fmm.Solver(4, "mixed")
+    with pytest.raises(fmm.FMMError) as ei:
+        s.set_hierarchy(h, lo=4)
+    assert ei.value.name == "FMM_ERR_STATE"
