@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs = []
     for src in sources():
         obj = os.path.join(out_dir, os.path.basename(src) + ".o")
-        cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+        cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "--ftz=true", "-Xcompiler", "-fPIC",
                "-I", cccl, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-c", src, "-o", obj]

@@ -139,7 +139,9 @@ fmm_status init_tables(Ctx* c) {
   TRY(upload(c, c->d_m2m_g, t.m2m_g));
   TRY(upload(c, c->d_m2m_e, t.m2m_e));
   TRY(upload(c, c->d_m2m_c, t.m2m_c));
+  TRY(upload(c, c->d_m2m_c32, std::vector<float>(t.m2m_c.begin(), t.m2m_c.end())));
   TRY(upload(c, c->d_l2l_off, t.l2l_off));
+  TRY(upload(c, c->d_l2l_off8, t.l2l_off8));
   TRY(upload(c, c->d_l2l_g, t.l2l_g));
   TRY(upload(c, c->d_l2l_e, t.l2l_e));
   TRY(upload(c, c->d_l2l_c, t.l2l_c));
@@ -176,8 +178,23 @@ fmm_status size_expansions(Ctx* c) {
         CKS(buf_ensure(c, T.Mlo, ncell * nc * 2));
       }
     }
-    if (l >= 2 && l <= c->lmax - 2) CKS(buf_ensure(c, T.L, ncell * nc * 8));
+    if (l >= 2 && l <= c->lmax - 2) {
+      CKS(buf_ensure(c, T.L, ncell * nc * 8));
+      if (!f64) CKS(buf_ensure(c, T.Lm, ncell * nc * 4));
+    }
     if (l >= c->lmin) CKS(buf_ensure(c, T.acc, ncell * 4 * (f64 ? 8 : 4)));
+  }
+  return FMM_OK;
+}
+
+// Leaf cells only ever carry a monopole: clear every multipole array once per
+// hierarchy so that each solve writes one value per leaf.
+fmm_status zero_expansions(Ctx* c, cudaStream_t st) {
+  for (int l = 1; l < c->lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    CKS(cudaMemsetAsync(T.M.ptr, 0, T.M.bytes, st));
+    if (T.Mhi.ptr) CKS(cudaMemsetAsync(T.Mhi.ptr, 0, T.Mhi.bytes, st));
+    if (T.Mlo.ptr) CKS(cudaMemsetAsync(T.Mlo.ptr, 0, T.Mlo.bytes, st));
   }
   return FMM_OK;
 }
@@ -229,7 +246,8 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
   }
   cudaMemset(c->d_err, 0, 16);
   for (auto& ev : c->ev) cudaEventCreate(&ev);
-  fmm_status s = init_tables(c);
+  fmm_status s = near_init(c);
+  if (s == FMM_OK) s = init_tables(c);
   if (s != FMM_OK) {
     fmm_destroy(c);
     return s;
@@ -273,6 +291,8 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
   fmm_status s = tree_build(c, st);
   if (s != FMM_OK) return s;
   s = size_expansions(c);
+  if (s != FMM_OK) return s;
+  s = zero_expansions(c, st);
   if (s != FMM_OK) return s;
   CKS(cudaStreamSynchronize(st));
   c->have_levels = true;
@@ -324,35 +344,42 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
     }
 
   stage_event(c, 0, st);
-  // 1. upward
-  launch_mono_leaves(c, c->lmax, st);
+  // 1. upward: leaf monopoles, then M2M from the finest level up
+  for (int l = 1; l <= c->lmax; ++l) launch_mono_leaves(c, l, st);
   for (int b = c->lmax - 1; b >= 1; --b) launch_upward(c, b, st);
   stage_event(c, 1, st);
-  // 2. downward: L2L + M2L, box levels 2..lmax-2
-  if (c->lmax - 2 >= 2) CKS(cudaMemsetAsync(c->lev[2].L.ptr, 0, c->lev[2].L.bytes, st));
-  for (int b = 2; b <= c->lmax - 2; ++b) {
-    if (b >= 3) launch_l2l(c, b, st);
-    if (f64)
+  // 2. downward over box levels 2..lmax-2: L = L2L(parent) + M2L
+  if (f64) {
+    for (int b = 2; b <= c->lmax - 2; ++b) {
+      launch_l2l_add(c, b, st);
       launch_gemm_f64(c, c->op_m2l, kModeM2L, b, st);
-    else
-      launch_gemm_tc(c, c->op_m2l, kModeM2L, b, st);
+    }
+  } else if (c->lmax - 2 >= 2) {
+    std::vector<int> lv;
+    for (int b = 2; b <= c->lmax - 2; ++b) {
+      CKS(cudaMemsetAsync(c->lev[b].Lm.ptr, 0, c->lev[b].Lm.bytes, st));
+      lv.push_back(b);
+    }
+    launch_gemm_tc(c, c->op_m2l, kModeM2L, lv.data(), (int)lv.size(), st);  // all levels in one launch
+    for (int b = 2; b <= c->lmax - 2; ++b) launch_l2l_add(c, b, st);
   }
   stage_event(c, 2, st);
   // 3a. bottom intermediate field, M2P from level l-1 cells
-  for (int l = lo; l <= c->lmax; ++l) {
-    if (!c->lev[l].n_leaf) continue;
-    CKS(cudaMemsetAsync(c->lev[l].acc.ptr, 0, c->lev[l].acc.bytes, st));
-    if (f64)
-      launch_gemm_f64(c, c->op_m2p, kModeM2P, l - 1, st);
-    else
-      launch_gemm_tc(c, c->op_m2p, kModeM2P, l - 1, st);
+  {
+    std::vector<int> lv;
+    for (int l = lo; l <= c->lmax; ++l) {
+      if (!c->lev[l].n_leaf) continue;
+      CKS(cudaMemsetAsync(c->lev[l].acc.ptr, 0, c->lev[l].acc.bytes, st));
+      if (f64)
+        launch_gemm_f64(c, c->op_m2p, kModeM2P, l - 1, st);
+      else
+        lv.push_back(l - 1);
+    }
+    if (!f64 && !lv.empty()) launch_gemm_tc(c, c->op_m2p, kModeM2P, lv.data(), (int)lv.size(), st);
   }
   stage_event(c, 3, st);
-  // 3b. near / nearest / far fields and the scatter
-  for (int l = lo; l <= c->lmax; ++l) {
-    if (!c->lev[l].n_leaf) continue;
-    launch_near(c, l, dphi[l], dacc[l], c->cfg.out_fp32, st);
-  }
+  // 3b. near / nearest / far fields and the scatter, all target levels in one launch
+  launch_near(c, lo, dphi.data() + lo, dacc.data() + lo, c->cfg.out_fp32, st);
   stage_event(c, 4, st);
   CKS(cudaGetLastError());
   for (int l = lo; l <= c->lmax; ++l)
@@ -391,11 +418,11 @@ void fmm_destroy(fmm_ctx* c) {
   if (c->last_stream) cudaStreamSynchronize(c->last_stream);
   for (auto& T : c->lev) {
     for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.tgt, &T.ijk,
-                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.acc})
+                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lm, &T.acc})
       buf_free(c, *b);
   }
-  for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_g,
-                    &c->d_l2l_e, &c->d_l2l_c, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
+  for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_off8, &c->d_l2l_g,
+                    &c->d_l2l_e, &c->d_l2l_c, &c->d_m2m_c32, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
                     &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->out_stage, &c->in_stage})

@@ -46,6 +46,7 @@ struct LevelTree {
   int64_t n_leaf = 0;    // input leaves of this level
   int64_t n_rows = 0;    // octs holding at least one refined cell
   int64_t n_tgt = 0;     // octs holding at least one leaf cell
+  int64_t n_rowsL = 0;   // octs holding a cell with grandchildren (need a local expansion)
   DevBuf oct_key;        // uint64 [n_oct]
   DevBuf oct_parent;     // int32 [n_oct] cell id at level-1
   DevBuf cell_child;     // int32 [8 n_oct]: >=0 child oct at level+1, else -1-leaf index
@@ -53,6 +54,7 @@ struct LevelTree {
   DevBuf leaf_cell;      // int32 [n_leaf]
   DevBuf rows;           // int32 [n_rows]
   DevBuf tgt;            // int32 [n_tgt]
+  DevBuf rowsL;          // int32 [n_rowsL]
   // inputs kept for adaptive time stepping (replaced by set_levels)
   DevBuf ijk;            // int32 [n_leaf][3]
   DevBuf mass;           // double [n_leaf]
@@ -61,6 +63,7 @@ struct LevelTree {
   DevBuf Mhi, Mlo;       // bf16 [8 n_oct][nc] (mixed path GEMM operands)
   DevBuf mono;           // [8 n_oct] total mass per cell (double or float)
   DevBuf L;              // double [8 n_oct][nc] local expansions (levels 2..lmax-2)
+  DevBuf Lm;             // float [8 n_oct][nc] this level's M2L sum (mixed path)
   DevBuf acc;            // [8 n_oct][4] M2P result (double or float), targets of this level
   bool m_is_f64 = true;
 };
@@ -83,8 +86,8 @@ struct Ctx {
   bool have_levels = false;
   LevelTree lev[kMaxLevel + 1];
   // device tables
-  DevBuf d_m2m_off, d_m2m_g, d_m2m_e, d_m2m_c;
-  DevBuf d_l2l_off, d_l2l_g, d_l2l_e, d_l2l_c;
+  DevBuf d_m2m_off, d_m2m_g, d_m2m_e, d_m2m_c, d_m2m_c32;
+  DevBuf d_l2l_off, d_l2l_off8, d_l2l_g, d_l2l_e, d_l2l_c;
   DevBuf d_near64, d_near32, d_l2p64, d_l2p32;
   GemmOperand op_m2p, op_m2l;
   // scratch
@@ -110,14 +113,15 @@ fmm_status tree_build(Ctx* c, cudaStream_t st);
 // upward.cu
 void launch_mono_leaves(Ctx* c, int level, cudaStream_t st);
 void launch_upward(Ctx* c, int level, cudaStream_t st);
-void launch_l2l(Ctx* c, int level, cudaStream_t st);
+void launch_l2l_add(Ctx* c, int level, cudaStream_t st);
 // gemm_f64.cu
 void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st);
 // gemm_tc.cu
 fmm_status make_tensor_maps(Ctx* c, GemmOperand& op);
-void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st);
+void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* row_levels, int nlev, cudaStream_t st);
 // near.cu
-void launch_near(Ctx* c, int level, void* phi, void* acc, int out_fp32, cudaStream_t st);
+fmm_status near_init(Ctx* c);
+void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st);
 
 enum { kModeM2P = 0, kModeM2L = 1 };
 

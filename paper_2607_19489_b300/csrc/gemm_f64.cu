@@ -99,11 +99,13 @@ __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
 
 void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream_t st) {
   LevelTree& R = c->lev[lr];
-  if (!R.n_rows) return;
+  // M2P: octs with a refined cell; M2L: octs with a cell that has grandchildren
+  const int64_t nr = (mode == kModeM2P) ? R.n_rows : R.n_rowsL;
+  if (!nr) return;
   F64Params P;
   P.M = (const double*)R.M.ptr;
-  P.rows = (const int32_t*)R.rows.ptr;
-  P.nrows = R.n_rows;
+  P.rows = (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
+  P.nrows = nr;
   P.nbr = (const int32_t*)R.nbr.ptr;
   P.B = (const double*)op.f64.ptr;
   P.klimit = (const int32_t*)op.klimit.ptr;
@@ -114,7 +116,7 @@ void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream
   P.acc = (mode == kModeM2P) ? (double*)c->lev[lr + 1].acc.ptr : nullptr;
   P.cell_child_rows = (const int32_t*)R.cell_child.ptr;
   P.L = (mode == kModeM2L) ? (double*)R.L.ptr : nullptr;
-  dim3 grid((unsigned)((R.n_rows + TM - 1) / TM), (unsigned)((op.N + 255) / 256));
+  dim3 grid((unsigned)((nr + TM - 1) / TM), (unsigned)((op.N + 255) / 256));
   ++c->n_launch;
   k_gemm_f64<<<grid, 256, 0, st>>>(P);
 }

@@ -26,28 +26,36 @@ namespace fmm {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;  // bf16 elements per row per stage = 128 bytes
-constexpr int STAGES = 2;
+constexpr int BK = 32;  // bf16 elements per row per stage = 64 bytes (64-byte swizzle)
+constexpr int STAGES = 4;
+constexpr int kNbrStride = 27;  // shared-memory row stride of the per-row neighbour table
 constexpr int THREADS = 192;
+constexpr int kMaxSeg = 24;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 __constant__ int c_nbr26[26] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12,
                                 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26};
 
-struct TcParams {
+// One segment = the rows of one level: its sources, neighbour table and output.
+struct TcSeg {
   const __nv_bfloat16* Ahi;
   const __nv_bfloat16* Alo;
   const int32_t* rows;
-  int nrows;
   const int32_t* nbr;
+  const int32_t* cell_child_rows;  // M2P: cell_child of the row level
+  float* out;                      // M2P: [cells of target level][4]; M2L: [cells][nc]
+  int nrows;
+  int tile0;                       // first M tile of this segment
+};
+
+struct TcParams {
+  TcSeg seg[kMaxSeg];
+  int nseg;
   int KQ;          // K per neighbour offset (8 * nc)
   int Kvalid;      // 26 * KQ
   int nchunks;     // Kpad / BK
   int chunks_per_split;
   int BN, N, nc, mode;
-  float* acc;                      // M2P: float [cells of target level][4]
-  const int32_t* cell_child_rows;  // M2P
-  double* L;                       // M2L: [cells][nc]
   unsigned* err;
 };
 
@@ -95,13 +103,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   }
 }
 
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+// K-major operand tile, rows of BK bf16 (64 B), 64-byte swizzle: the 16-byte
+// chunk j of row r sits at chunk j ^ ((r >> 1) & 3); 8 rows form a 512 B atom.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
   d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)(512 >> 4) << 32;         // stride byte offset: 8 rows x 64 B
   d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  d |= (uint64_t)4 << 61;                  // 64-byte swizzle
   return d;
 }
 
@@ -149,6 +159,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* bars = (uint64_t*)(Blo + STAGES * b_bytes);  // full[S], empty[S], done
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
+  int32_t* s_nbr = (int32_t*)(tmem_slot + 4);  // [BM][kNbrStride] source octs of each row
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kc_begin = blockIdx.z * P.chunks_per_split;
@@ -180,30 +191,36 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp < 4) {
     // ---------------- A gather (one row per thread) ----------------
     const int t = threadIdx.x;
-    const int64_t row_idx = (int64_t)blockIdx.x * BM + t;
-    const bool valid = row_idx < P.nrows;
-    const int32_t roct = valid ? P.rows[row_idx] : 0;
-    const int32_t* myn = P.nbr + (int64_t)roct * 27;
-    const uint32_t ahi0 = smem_u32(Ahi) + t * 128, alo0 = smem_u32(Alo) + t * 128;
+    int si = 0;
+    while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].tile0) ++si;
+    const TcSeg& S = P.seg[si];
+    const int64_t row_idx = (int64_t)(blockIdx.x - S.tile0) * BM + t;
+    const bool valid = row_idx < S.nrows;
+    const int32_t roct = valid ? S.rows[row_idx] : 0;
+    int32_t* myn = s_nbr + t * kNbrStride;  // read by this thread only
+    for (int q = 0; q < 26; ++q) myn[q] = valid ? S.nbr[(int64_t)roct * 27 + c_nbr26[q]] : -1;
+    const uint32_t ahi0 = smem_u32(Ahi) + t * (BK * 2), alo0 = smem_u32(Alo) + t * (BK * 2);
     bool ok = true;
     for (int it = 0; it < nit && ok; ++it) {
       const int s = it % STAGES;
       if (it >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, abort);
       if (!ok) break;
       const int k0 = (kc_begin + it) * BK;
+      const int qi0 = k0 / P.KQ;  // a BK-wide slice spans at most two offset segments
+      const int kb = (qi0 + 1) * P.KQ;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < BK / 8; ++j) {
         const int k = k0 + 8 * j;
         int32_t src = -1;
         int off = 0;
-        if (valid && k < P.Kvalid) {
-          int qi = k / P.KQ;
+        if (k < P.Kvalid) {
+          const int qi = (k >= kb) ? qi0 + 1 : qi0;
           off = k - qi * P.KQ;
-          src = myn[c_nbr26[qi]];
+          src = myn[qi];
         }
-        const uint32_t sw = (uint32_t)((j ^ (t & 7)) << 4);
-        const __nv_bfloat16* gh = src >= 0 ? P.Ahi + (int64_t)src * P.KQ + off : P.Ahi;
-        const __nv_bfloat16* gl = src >= 0 ? P.Alo + (int64_t)src * P.KQ + off : P.Alo;
+        const uint32_t sw = (uint32_t)((j ^ ((t >> 1) & 3)) << 4);
+        const __nv_bfloat16* gh = src >= 0 ? S.Ahi + (int64_t)src * P.KQ + off : S.Ahi;
+        const __nv_bfloat16* gl = src >= 0 ? S.Alo + (int64_t)src * P.KQ + off : S.Alo;
         const uint32_t sz = src >= 0 ? 16u : 0u;
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(ahi0 + s * a_bytes + sw), "l"(gh),
                      "r"(sz)
@@ -236,9 +253,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int n0 = blockIdx.y * P.BN + j * 32;
       if (P.mode == kModeM2P) {
         const int f = n0 >> 5;
-        const int32_t ch = P.cell_child_rows[(int64_t)roct * 8 + f];
+        const int32_t ch = S.cell_child_rows[(int64_t)roct * 8 + f];
         if (ch >= 0) {
-          float* dst = P.acc + (int64_t)ch * 32;
+          float* dst = S.out + (int64_t)ch * 32;
 #pragma unroll
           for (int u = 0; u < 8; ++u)
             asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * u), "f"(__uint_as_float(v[4 * u])),
@@ -247,12 +264,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                          : "memory");
         }
       } else {
-        double* dst = P.L + (int64_t)roct * 8 * P.nc;
+        float* dst = S.out + (int64_t)roct * 8 * P.nc + n0;
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          int n = n0 + u;
-          if (n < P.N) atomicAdd(dst + n, (double)__uint_as_float(v[u]));
-        }
+        for (int u = 0; u < 8; ++u)
+          if (n0 + 4 * u < P.N)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * u),
+                         "f"(__uint_as_float(v[4 * u])), "f"(__uint_as_float(v[4 * u + 1])),
+                         "f"(__uint_as_float(v[4 * u + 2])), "f"(__uint_as_float(v[4 * u + 3]))
+                         : "memory");
       }
     }
   } else if (warp == 4) {
@@ -292,7 +311,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t accum = (it | part | kk) != 0;
-            mma_bf16(tmem, sdesc_sw128(a + kk * 32), sdesc_sw128(b + kk * 32), idesc, accum);
+            mma_bf16(tmem, sdesc_sw64(a + kk * 32), sdesc_sw64(b + kk * 32), idesc, accum);
           }
         }
         mma_commit(empty0 + 8 * s);
@@ -324,7 +343,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 size_t smem_bytes(int BN) {
-  return 1024 + STAGES * (2 * BM * BK * 2 + 2 * BN * BK * 2) + (2 * STAGES + 1) * 8 + 16;
+  return 1024 + STAGES * (2 * BM * BK * 2 + 2 * BN * BK * 2) + (2 * STAGES + 1) * 8 + 16 + BM * kNbrStride * 4;
 }
 
 // split-K factor minimising waves x chunks per CTA
@@ -360,7 +379,7 @@ fmm_status make_tensor_maps(Ctx* c, GemmOperand& op) {
     void* g = w == 0 ? op.hi.ptr : op.lo.ptr;
     CUtensorMap* tm = (CUtensorMap*)(w == 0 ? op.tmap_hi : op.tmap_lo);
     CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       c->last_error = "cuTensorMapEncodeTiled failed: " + std::to_string((int)r);
@@ -375,31 +394,41 @@ fmm_status make_tensor_maps(Ctx* c, GemmOperand& op) {
   return FMM_OK;
 }
 
-void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream_t st) {
-  LevelTree& R = c->lev[lr];
-  if (!R.n_rows) return;
+void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, int nlev, cudaStream_t st) {
   TcParams P;
-  P.Ahi = (const __nv_bfloat16*)R.Mhi.ptr;
-  P.Alo = (const __nv_bfloat16*)R.Mlo.ptr;
-  P.rows = (const int32_t*)R.rows.ptr;
-  P.nrows = (int)R.n_rows;
-  P.nbr = (const int32_t*)R.nbr.ptr;
+  int tiles = 0;
+  P.nseg = 0;
+  for (int i = 0; i < nlev && P.nseg < kMaxSeg; ++i) {
+    const int lr = levels[i];  // row level
+    LevelTree& R = c->lev[lr];
+    // M2P: octs with a refined cell (their children hold the targets);
+    // M2L: octs with a cell that has grandchildren (those need a local expansion)
+    const int64_t nr = (mode == kModeM2P) ? R.n_rows : R.n_rowsL;
+    if (!nr) continue;
+    TcSeg& S = P.seg[P.nseg++];
+    S.Ahi = (const __nv_bfloat16*)R.Mhi.ptr;
+    S.Alo = (const __nv_bfloat16*)R.Mlo.ptr;
+    S.rows = (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
+    S.nbr = (const int32_t*)R.nbr.ptr;
+    S.cell_child_rows = (const int32_t*)R.cell_child.ptr;
+    S.out = (mode == kModeM2P) ? (float*)c->lev[lr + 1].acc.ptr : (float*)R.Lm.ptr;
+    S.nrows = (int)nr;
+    S.tile0 = tiles;
+    tiles += (int)((nr + BM - 1) / BM);
+  }
+  if (!tiles) return;
   P.KQ = op.kseg;
   P.Kvalid = op.K;
   P.nchunks = op.Kpad / BK;
-  const int mt = (int)((R.n_rows + BM - 1) / BM);
-  const int split = choose_split(mt * op.ntile, P.nchunks, c->num_sms);
+  const int split = choose_split(tiles * op.ntile, P.nchunks, c->num_sms);
   P.chunks_per_split = (P.nchunks + split - 1) / split;
   const int nz = (P.nchunks + P.chunks_per_split - 1) / P.chunks_per_split;
   P.BN = op.BN;
   P.N = op.N;
   P.nc = c->tab.nc;
   P.mode = mode;
-  P.acc = (mode == kModeM2P) ? (float*)c->lev[lr + 1].acc.ptr : nullptr;
-  P.cell_child_rows = (const int32_t*)R.cell_child.ptr;
-  P.L = (mode == kModeM2L) ? (double*)R.L.ptr : nullptr;
   P.err = c->d_err;
-  dim3 grid((unsigned)mt, (unsigned)op.ntile, (unsigned)nz);
+  dim3 grid((unsigned)tiles, (unsigned)op.ntile, (unsigned)nz);
   ++c->n_launch;
   k_gemm_tc<<<grid, THREADS, smem_bytes(op.BN), st>>>(*(const CUtensorMap*)op.tmap_hi,
                                                        *(const CUtensorMap*)op.tmap_lo, P);

@@ -1,6 +1,6 @@
-// near.cu -- PotentialEvaluation (Alg. 4) for the leaf cells of one level:
-// near and nearest fields (Sec. 3.2, Fig. 2), the far field by L2P from the
-// level l-2 local expansion, plus the bottom intermediate field computed
+// near.cu -- PotentialEvaluation (Alg. 4) for the leaf cells of the target
+// levels: near and nearest fields (Sec. 3.2, Fig. 2), the far field by L2P from
+// the level l-2 local expansion, plus the bottom intermediate field computed
 // beforehand by the M2P contraction; scattered to the caller's order.
 //
 // For a target t at level l with parent F (level l-1), the sources are the
@@ -13,10 +13,39 @@
 //       - refined, not touching-> M2P from P's multipole (the merged tree
 //                                 at FMM level l).
 // Offsets are exact in level-l units (integers, halves and quarters).
+//
+// Layout: 8 threads per target oct (one per cell), OPB octs per block, all
+// target levels in one launch (a segment per level).  The 216 source cells of
+// an oct are staged once in shared memory: their masses (zero for anything
+// that is not a level-l leaf) and a short list of the coarse-leaf and refined
+// entries, which only occur next to coarse-fine interfaces; the 27 rounds of
+// source loads are independent, so they are issued back to back.  The P2P
+// loop is then branch-free except for the self term.  The local expansion of
+// the oct's level l-2 box is staged too and evaluated directly,
+// phi = sum_beta L_beta rho^beta / beta!.
 #include "fmm_internal.cuh"
 
 namespace fmm {
 namespace {
+
+constexpr int kNcMax = 168;  // ncoef(8) = 165
+constexpr int kMaxNearSeg = 24;
+
+// Source positions relative to the target oct's origin, level-l units:
+// cell c of neighbour slot q sits at 2 dq + bits(c) (its lower corner; the
+// target uses the same convention, so differences are centre differences).
+__constant__ float c_src_pos[216][3];
+// index of the multi-index (a,b,c) in the graded order, a,b,c <= 8
+__constant__ int16_t c_lut[9][9][9];
+// 1/(k+1) in each precision (an FP32 table would limit the FP64 path to 1e-8)
+__constant__ float c_inv_f[9] = {1.f, 1.f / 2, 1.f / 3, 1.f / 4, 1.f / 5, 1.f / 6, 1.f / 7, 1.f / 8, 1.f / 9};
+__constant__ double c_inv_d[9] = {1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9};
+template <typename T>
+__device__ __forceinline__ T inv_k(int k);
+template <>
+__device__ __forceinline__ float inv_k<float>(int k) { return c_inv_f[k]; }
+template <>
+__device__ __forceinline__ double inv_k<double>(int k) { return c_inv_d[k]; }
 
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
@@ -38,171 +67,298 @@ __device__ __forceinline__ void p2p(T m, T dx, T dy, T dz, T& phi, T& ax, T& ay,
   az += mir3 * dz;
 }
 
-struct NearParams {
-  int level, nc;
-  int64_t n_tgt;
+struct NearSeg {
   const int32_t* tgt;         // target octs (level l)
   const int32_t* nbr;         // [oct][27] level l
   const int32_t* cc_l;        // cell_child level l
-  const int32_t* cc_up;       // cell_child level l-1 (unused)
   const int32_t* par_l;       // oct_parent level l
   const int32_t* par_up;      // oct_parent level l-1
-  const double* mono_up;      // masses of level l-1 cells
-  const double* mono_l;       // level l
-  const double* mono_dn;      // level l+1
+  const void* mono_up;        // masses of level l-1 cells (in the kernel's precision)
+  const void* mono_l;         // level l
+  const void* mono_dn;        // level l+1
   const void* M_l;            // multipoles of level l cells
-  int M_l_f64;
   const double* L2;           // local expansions of level l-2 (or null)
   const void* acc;            // M2P results for level l cells [cells][4]
-  const void* nearop;         // [343][nc][4]
-  const void* l2pop;          // [64][nc][4]
-  double G, h;                // gravitational constant, cell size of level l
   void* phi;
   void* accel;
-  int out_fp32;
+  double s1, s2;              // G / h and G / h^2, h the cell size of level l
+  int64_t n_tgt;
+  int blk0;                   // first block of this segment
+  int M_l_f64;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_near(NearParams P) {
-  const int64_t gi = (int64_t)blockIdx.x * 16 + (threadIdx.x >> 3);
-  if (gi >= P.n_tgt) return;
-  const int tp = threadIdx.x & 7;
-  const int32_t o = P.tgt[gi];
+struct NearParams {
+  NearSeg seg[kMaxNearSeg];
+  int nseg, nc, p, out_fp32;
+  const void* nearop;         // [343][nc][4]
+  double G;
+};
+
+template <typename T, int OPB>
+__global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearParams P) {
+  __shared__ T s_m[OPB][216];
+  __shared__ T s_L[OPB][kNcMax];          // local expansion of the oct's level l-2 box
+  __shared__ int32_t s_nb[OPB][28];        // the 27 neighbour slots of the oct
+  __shared__ uint8_t s_spec[OPB][216];     // source slots that are coarse leaves or refined cells
+  __shared__ int s_nspec[OPB];
+  int si = 0;
+  while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].blk0) ++si;
+  const NearSeg& S = P.seg[si];
+  const int g = threadIdx.x >> 3, tp = threadIdx.x & 7;
+  const int64_t gi = (int64_t)(blockIdx.x - S.blk0) * OPB + g;
+  const bool oct_ok = gi < S.n_tgt;
+  const int32_t o = oct_ok ? S.tgt[gi] : 0;
+  if (tp == 0) s_nspec[g] = 0;
+  if (oct_ok)
+    for (int q = tp; q < 27; q += 8) s_nb[g][q] = S.nbr[(int64_t)o * 27 + q];
+  __syncthreads();
+  // ---- stage the 216 sources of this oct: thread tp takes cell tp of every slot ----
+  if (oct_ok) {
+#pragma unroll 9
+    for (int q = 0; q < 27; ++q) {
+      const int32_t nb = s_nb[g][q];
+      const int64_t pc = (int64_t)(nb >= 0 ? nb : 0) * 8 + tp;
+      const int32_t ch = S.cc_l[pc];
+      const T mm = ((const T*)S.mono_l)[pc];
+      const int s = q * 8 + tp;
+      T m = 0;
+      if (nb >= 0) {
+        if (ch < 0)
+          m = (T)mm;
+        else
+          s_spec[g][atomicAdd(&s_nspec[g], 1)] = (uint8_t)s;  // refined cell
+      } else if (nb <= -2 && tp == 0) {
+        s_spec[g][atomicAdd(&s_nspec[g], 1)] = (uint8_t)s;  // a level l-1 leaf, counted once
+      }
+      s_m[g][s] = m;
+    }
+    if (S.L2) {
+      const int32_t G2 = S.par_up[S.par_l[o] >> 3];
+      for (int b = tp; b < P.nc; b += 8) s_L[g][b] = (T)S.L2[(int64_t)G2 * P.nc + b];
+    }
+  }
+  __syncthreads();
+  if (!oct_ok) return;
   const int64_t cell = (int64_t)o * 8 + tp;
-  const int32_t self = P.cc_l[cell];
+  const int32_t self = S.cc_l[cell];
   if (self >= 0) return;  // refined: not a target of this level
-  const int tb[3] = {tp & 1, (tp >> 1) & 1, (tp >> 2) & 1};
-  const T* nearop = (const T*)P.nearop;
+  const int tbx = tp & 1, tby = (tp >> 1) & 1, tbz = (tp >> 2) & 1;
+  const T tx = (T)tbx, ty = (T)tby, tz = (T)tbz;
   T phi = 0, ax = 0, ay = 0, az = 0;
-  const int32_t* nb27 = P.nbr + (int64_t)o * 27;
+  // ---- P2P with the level-l leaves of the 3^3 neighbour octs ----
+  // Source cell c of slot q has its lower corner at 2 dq + bits(c); relative to
+  // the target that is i - 2 - t along each axis, i = 2 (dq+1) + bit in 0..5.
+  // With both loops unrolled the six offsets per axis live in registers.
+  T X[6], Y[6], Z[6], X2[6], Y2[6], Z2[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    X[i] = (T)(i - 2) - tx;
+    Y[i] = (T)(i - 2) - ty;
+    Z[i] = (T)(i - 2) - tz;
+    X2[i] = X[i] * X[i];
+    Y2[i] = Y[i] * Y[i];
+    Z2[i] = Z[i] * Z[i];
+  }
+  const T* sm = s_m[g];
+#pragma unroll
   for (int q = 0; q < 27; ++q) {
-    const int32_t nb = nb27[q];
-    if (nb == -1) continue;
-    const int dq[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
-    if (nb <= -2) {  // coarse leaf of level l-1: centre at 2 dq + 1 in level-l units
-      const T m = (T)P.mono_up[-2 - (int64_t)nb];
-      p2p<T>(m, (T)(2 * dq[0] - tb[0]) + (T)0.5, (T)(2 * dq[1] - tb[1]) + (T)0.5,
-             (T)(2 * dq[2] - tb[2]) + (T)0.5, phi, ax, ay, az);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int ix = 2 * (q % 3) + (c & 1), iy = 2 * ((q / 3) % 3) + ((c >> 1) & 1),
+                iz = 2 * (q / 9) + ((c >> 2) & 1);
+      T m = sm[q * 8 + c];
+      T r2 = X2[ix] + Y2[iy] + Z2[iz];
+      if (q == 13) {  // the target's own oct: skip the self term
+        const bool me = (c == tp);
+        m = me ? (T)0 : m;
+        r2 = me ? (T)1 : r2;
+      }
+      const T ir = rsqrt_t<T>(r2);
+      const T mir = m * ir;
+      const T mir3 = mir * (ir * ir);
+      phi -= mir;
+      ax += mir3 * X[ix];
+      ay += mir3 * Y[iy];
+      az += mir3 * Z[iz];
+    }
+  }
+  // ---- coarse leaves and refined cells (coarse-fine interfaces only) ----
+  const T* nearop = (const T*)P.nearop;
+  const int nspec = s_nspec[g];
+  for (int k = 0; k < nspec; ++k) {
+    const int s = s_spec[g][k];
+    const int32_t nb = s_nb[g][s >> 3];
+    if (nb <= -2) {  // coarse leaf of level l-1: centre at 2 dq + 1
+      const T m = ((const T*)S.mono_up)[-2 - (int64_t)nb];
+      p2p<T>(m, (T)c_src_pos[s][0] + (T)0.5 - tx, (T)c_src_pos[s][1] + (T)0.5 - ty,
+             (T)c_src_pos[s][2] + (T)0.5 - tz, phi, ax, ay, az);
       continue;
     }
-    for (int c = 0; c < 8; ++c) {
-      const int rx = 2 * dq[0] + (c & 1) - tb[0];
-      const int ry = 2 * dq[1] + ((c >> 1) & 1) - tb[1];
-      const int rz = 2 * dq[2] + ((c >> 2) & 1) - tb[2];
-      if ((rx | ry | rz) == 0) continue;
-      const int64_t pc = (int64_t)nb * 8 + c;
-      const int32_t ch = P.cc_l[pc];
-      if (ch < 0) {
-        p2p<T>((T)P.mono_l[pc], (T)rx, (T)ry, (T)rz, phi, ax, ay, az);
-      } else if (abs(rx) <= 1 && abs(ry) <= 1 && abs(rz) <= 1) {
-        // nearest field: the 8 children of the touching refined cell
-        for (int k = 0; k < 8; ++k) {
-          const T m = (T)P.mono_dn[(int64_t)ch * 8 + k];
-          p2p<T>(m, (T)rx + (T)(((k & 1) * 2 - 1)) * (T)0.25, (T)ry + (T)((((k >> 1) & 1) * 2 - 1)) * (T)0.25,
-                 (T)rz + (T)((((k >> 2) & 1) * 2 - 1)) * (T)0.25, phi, ax, ay, az);
+    const int64_t pc = (int64_t)nb * 8 + (s & 7);
+    const int rx = (int)c_src_pos[s][0] - tbx;
+    const int ry = (int)c_src_pos[s][1] - tby;
+    const int rz = (int)c_src_pos[s][2] - tbz;
+    if (abs(rx) <= 1 && abs(ry) <= 1 && abs(rz) <= 1) {
+      // nearest field: the 8 children of the touching refined cell
+      const int32_t ch = S.cc_l[pc];
+      for (int kk = 0; kk < 8; ++kk) {
+        const T m = ((const T*)S.mono_dn)[(int64_t)ch * 8 + kk];
+        p2p<T>(m, (T)rx + (T)((kk & 1) * 2 - 1) * (T)0.25, (T)ry + (T)(((kk >> 1) & 1) * 2 - 1) * (T)0.25,
+               (T)rz + (T)(((kk >> 2) & 1) * 2 - 1) * (T)0.25, phi, ax, ay, az);
+      }
+    } else {
+      // near-field refined cell: M2P at integer offset R = t - P
+      const int ridx = ((-rz + 3) * 7 + (-ry + 3)) * 7 + (-rx + 3);
+      const T* op = nearop + (int64_t)ridx * P.nc * 4;
+      if (S.M_l_f64) {
+        const double* M = (const double*)S.M_l + pc * P.nc;
+        for (int a = 0; a < P.nc; ++a) {
+          T mv = (T)M[a];
+          phi += op[4 * a] * mv;
+          ax += op[4 * a + 1] * mv;
+          ay += op[4 * a + 2] * mv;
+          az += op[4 * a + 3] * mv;
         }
       } else {
-        // near-field refined cell: M2P at integer offset R = t - P
-        const int ridx = ((-rz + 3) * 7 + (-ry + 3)) * 7 + (-rx + 3);
-        const T* op = nearop + (int64_t)ridx * P.nc * 4;
-        if (P.M_l_f64) {
-          const double* M = (const double*)P.M_l + pc * P.nc;
-          for (int a = 0; a < P.nc; ++a) {
-            T mv = (T)M[a];
-            phi += op[4 * a] * mv;
-            ax += op[4 * a + 1] * mv;
-            ay += op[4 * a + 2] * mv;
-            az += op[4 * a + 3] * mv;
-          }
-        } else {
-          const float* M = (const float*)P.M_l + pc * P.nc;
-          for (int a = 0; a < P.nc; ++a) {
-            T mv = (T)M[a];
-            phi += op[4 * a] * mv;
-            ax += op[4 * a + 1] * mv;
-            ay += op[4 * a + 2] * mv;
-            az += op[4 * a + 3] * mv;
-          }
+        const float* M = (const float*)S.M_l + pc * P.nc;
+        for (int a = 0; a < P.nc; ++a) {
+          T mv = (T)M[a];
+          phi += op[4 * a] * mv;
+          ax += op[4 * a + 1] * mv;
+          ay += op[4 * a + 2] * mv;
+          az += op[4 * a + 3] * mv;
         }
       }
     }
   }
-  // bottom intermediate field (M2P, level l-1 units) and far field (L2P, level l-2 units)
-  const T* acc = (const T*)P.acc;
+  // ---- bottom intermediate field (M2P, level l-1 units) and far field (L2P, level l-2 units)
+  const T* acc = (const T*)S.acc;
   T pm = acc[cell * 4], xm = acc[cell * 4 + 1], ym = acc[cell * 4 + 2], zm = acc[cell * 4 + 3];
   T pl = 0, xl = 0, yl = 0, zl = 0;
-  if (P.L2) {
-    const int32_t F = P.par_l[o];
-    const int32_t G2 = P.par_up[F >> 3];
-    const int pos = (F & 7) * 8 + tp;
-    const double* L = P.L2 + (int64_t)G2 * P.nc;
-    const T* op = (const T*)P.l2pop + (int64_t)pos * P.nc * 4;
-    for (int b = 0; b < P.nc; ++b) {
-      T lb = (T)L[b];
-      pl += op[4 * b] * lb;
-      xl += op[4 * b + 1] * lb;
-      yl += op[4 * b + 2] * lb;
-      zl += op[4 * b + 3] * lb;
+  if (S.L2) {
+    // phi = sum_beta L_beta rho^beta / beta!, grad_i = sum_gamma L_{gamma+e_i} rho^gamma / gamma!,
+    // rho = target - box centre in units of the level l-2 box
+    const int fpos = S.par_l[o] & 7;
+    const T rx = (T)(2 * (fpos & 1) + tbx) * (T)0.25 - (T)0.375;
+    const T ry = (T)(2 * ((fpos >> 1) & 1) + tby) * (T)0.25 - (T)0.375;
+    const T rz = (T)(2 * ((fpos >> 2) & 1) + tbz) * (T)0.25 - (T)0.375;
+    const T* L = s_L[g];
+    const int p = P.p;
+    T xa = 1;
+    for (int a = 0; a <= p; ++a) {
+      T xy = xa;
+      for (int b = 0; a + b <= p; ++b) {
+        T m = xy;
+        for (int cz = 0; a + b + cz <= p; ++cz) {
+          pl += L[c_lut[a][b][cz]] * m;
+          if (a + b + cz < p) {
+            xl -= L[c_lut[a + 1][b][cz]] * m;
+            yl -= L[c_lut[a][b + 1][cz]] * m;
+            zl -= L[c_lut[a][b][cz + 1]] * m;
+          }
+          m *= rz * inv_k<T>(cz);
+        }
+        xy *= ry * inv_k<T>(b);
+      }
+      xa *= rx * inv_k<T>(a);
     }
   }
-  const double s1 = P.G / P.h, s2 = P.G / (P.h * P.h);
-  const double ph = s1 * ((double)phi + 0.5 * (double)pm + 0.25 * (double)pl);
-  const double gx = s2 * ((double)ax + 0.25 * (double)xm + 0.0625 * (double)xl);
-  const double gy = s2 * ((double)ay + 0.25 * (double)ym + 0.0625 * (double)yl);
-  const double gz = s2 * ((double)az + 0.25 * (double)zm + 0.0625 * (double)zl);
+  // level-l units: the M2P sum is in level l-1 units, the local expansion in level l-2 units
+  const T s1 = (T)S.s1, s2 = (T)S.s2;
+  const T ph = s1 * (phi + (T)0.5 * pm + (T)0.25 * pl);
+  const T gx = s2 * (ax + (T)0.25 * xm + (T)0.0625 * xl);
+  const T gy = s2 * (ay + (T)0.25 * ym + (T)0.0625 * yl);
+  const T gz = s2 * (az + (T)0.25 * zm + (T)0.0625 * zl);
   const int64_t li = -1 - (int64_t)self;
   if (P.out_fp32) {
-    ((float*)P.phi)[li] = (float)ph;
-    float* a = (float*)P.accel + 3 * li;
+    ((float*)S.phi)[li] = (float)ph;
+    float* a = (float*)S.accel + 3 * li;
     a[0] = (float)gx;
     a[1] = (float)gy;
     a[2] = (float)gz;
   } else {
-    ((double*)P.phi)[li] = ph;
-    double* a = (double*)P.accel + 3 * li;
-    a[0] = gx;
-    a[1] = gy;
-    a[2] = gz;
+    ((double*)S.phi)[li] = (double)ph;
+    double* a = (double*)S.accel + 3 * li;
+    a[0] = (double)gx;
+    a[1] = (double)gy;
+    a[2] = (double)gz;
   }
 }
 
 }  // namespace
 
-void launch_near(Ctx* c, int l, void* phi, void* accel, int out_fp32, cudaStream_t st) {
-  LevelTree& T = c->lev[l];
-  if (!T.n_tgt) return;
+fmm_status near_init(Ctx* c) {
+  int16_t lut[9][9][9];
+  {
+    int k = 0;
+    for (int n = 0; n <= 24; ++n)
+      for (int a = n; a >= 0; --a)
+        for (int b = n - a; b >= 0; --b) {
+          int cc = n - a - b;
+          if (a <= 8 && b <= 8 && cc <= 8) lut[a][b][cc] = (int16_t)(n <= 8 ? k : -1);
+          ++k;
+        }
+  }
+  cudaError_t el = cudaMemcpyToSymbol(c_lut, lut, sizeof(lut));
+  if (el != cudaSuccess) {
+    c->last_error = std::string("near_init: ") + cudaGetErrorString(el);
+    return FMM_ERR_CUDA;
+  }
+  float pos[216][3];
+  for (int s = 0; s < 216; ++s) {
+    int q = s >> 3, cc = s & 7;
+    int dq[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+    for (int i = 0; i < 3; ++i) pos[s][i] = (float)(2 * dq[i] + ((cc >> i) & 1));
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_src_pos, pos, sizeof(pos));
+  if (e != cudaSuccess) {
+    c->last_error = std::string("near_init: ") + cudaGetErrorString(e);
+    return FMM_ERR_CUDA;
+  }
+  return FMM_OK;
+}
+
+void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st) {
   const bool f64 = c->cfg.precision == FMM_FP64;
+  const int opb = f64 ? 8 : 16;
   NearParams P;
-  P.level = l;
+  P.nseg = 0;
   P.nc = c->tab.nc;
-  P.n_tgt = T.n_tgt;
-  P.tgt = (const int32_t*)T.tgt.ptr;
-  P.nbr = (const int32_t*)T.nbr.ptr;
-  P.cc_l = (const int32_t*)T.cell_child.ptr;
-  P.cc_up = (const int32_t*)c->lev[l - 1].cell_child.ptr;
-  P.par_l = (const int32_t*)T.oct_parent.ptr;
-  P.par_up = (const int32_t*)c->lev[l - 1].oct_parent.ptr;
-  P.mono_up = (const double*)c->lev[l - 1].mono.ptr;
-  P.mono_l = (const double*)T.mono.ptr;
-  P.mono_dn = (l < c->lmax) ? (const double*)c->lev[l + 1].mono.ptr : nullptr;
-  P.M_l = T.M.ptr;
-  P.M_l_f64 = T.m_is_f64 ? 1 : 0;
-  P.L2 = (l - 2 >= 2) ? (const double*)c->lev[l - 2].L.ptr : nullptr;
-  P.acc = T.acc.ptr;
-  P.nearop = f64 ? c->d_near64.ptr : c->d_near32.ptr;
-  P.l2pop = f64 ? c->d_l2p64.ptr : c->d_l2p32.ptr;
-  P.G = c->cfg.G;
-  P.h = std::ldexp(1.0, -l);
-  P.phi = phi;
-  P.accel = accel;
+  P.p = c->cfg.p;
   P.out_fp32 = out_fp32;
-  unsigned grid = (unsigned)((T.n_tgt + 15) / 16);
+  P.nearop = f64 ? c->d_near64.ptr : c->d_near32.ptr;
+  P.G = c->cfg.G;
+  int blocks = 0;
+  for (int l = lo; l <= c->lmax && P.nseg < kMaxNearSeg; ++l) {
+    LevelTree& T = c->lev[l];
+    if (!T.n_tgt || !T.n_leaf) continue;
+    NearSeg& S = P.seg[P.nseg++];
+    S.tgt = (const int32_t*)T.tgt.ptr;
+    S.nbr = (const int32_t*)T.nbr.ptr;
+    S.cc_l = (const int32_t*)T.cell_child.ptr;
+    S.par_l = (const int32_t*)T.oct_parent.ptr;
+    S.par_up = (const int32_t*)c->lev[l - 1].oct_parent.ptr;
+    S.mono_up = (const double*)c->lev[l - 1].mono.ptr;
+    S.mono_l = (const double*)T.mono.ptr;
+    S.mono_dn = (l < c->lmax) ? (const double*)c->lev[l + 1].mono.ptr : nullptr;
+    S.M_l = T.M.ptr;
+    S.M_l_f64 = T.m_is_f64 ? 1 : 0;
+    S.L2 = (l - 2 >= 2) ? (const double*)c->lev[l - 2].L.ptr : nullptr;
+    S.acc = T.acc.ptr;
+    S.phi = phi[l - lo];
+    S.accel = accel[l - lo];
+    S.s1 = c->cfg.G * std::ldexp(1.0, l);
+    S.s2 = c->cfg.G * std::ldexp(1.0, 2 * l);
+    S.n_tgt = T.n_tgt;
+    S.blk0 = blocks;
+    blocks += (int)((T.n_tgt + opb - 1) / opb);
+  }
+  if (!blocks) return;
+  ++c->n_launch;
   if (f64)
-    ++c->n_launch;
-    k_near<double><<<grid, 128, 0, st>>>(P);
+    k_near<double, 8><<<(unsigned)blocks, 64, 0, st>>>(P);
   else
-    ++c->n_launch;
-    k_near<float><<<grid, 128, 0, st>>>(P);
+    k_near<float, 16><<<(unsigned)blocks, 128, 0, st>>>(P);
 }
 
 }  // namespace fmm

@@ -238,23 +238,30 @@ void Tables::build(int p_) {
     }
     m2m_off.push_back((int)m2m_g.size());
   }
-  // ---- L2L pair lists -----------------------------------------------------
+  // ---- L2L pair lists, grouped by sign pattern e within each beta ------------
+  // l2l_off8[beta*8 + e] .. l2l_off8[beta*8 + e + 1] are the pairs of beta with
+  // pattern e, so the device can sum each pattern into its own register.
   l2l_off.assign(1, 0);
+  l2l_off8.assign(1, 0);
   l2l_g.clear();
   l2l_e.clear();
   l2l_c.clear();
   for (int be = 0; be < nc; ++be) {
     const auto& B = mi.list[be];
-    for (int g = 0; g < nc; ++g) {
-      const auto& Gm = mi.list[g];
-      if (Gm[0] < B[0] || Gm[1] < B[1] || Gm[2] < B[2]) continue;
-      std::array<int, 3> al = {Gm[0] - B[0], Gm[1] - B[1], Gm[2] - B[2]};
-      int e = (al[0] & 1) | ((al[1] & 1) << 1) | ((al[2] & 1) << 2);
-      int da = al[0] + al[1] + al[2];
-      double c = std::ldexp(1.0, -2 * da - degree[be] - 1) / mfact(al);
-      l2l_g.push_back(g);
-      l2l_e.push_back(e);
-      l2l_c.push_back(c);
+    for (int ee = 0; ee < 8; ++ee) {
+      for (int g = 0; g < nc; ++g) {
+        const auto& Gm = mi.list[g];
+        if (Gm[0] < B[0] || Gm[1] < B[1] || Gm[2] < B[2]) continue;
+        std::array<int, 3> al = {Gm[0] - B[0], Gm[1] - B[1], Gm[2] - B[2]};
+        int e = (al[0] & 1) | ((al[1] & 1) << 1) | ((al[2] & 1) << 2);
+        if (e != ee) continue;
+        int da = al[0] + al[1] + al[2];
+        double c = std::ldexp(1.0, -2 * da - degree[be] - 1) / mfact(al);
+        l2l_g.push_back(g);
+        l2l_e.push_back(e);
+        l2l_c.push_back(c);
+      }
+      l2l_off8.push_back((int)l2l_g.size());
     }
     l2l_off.push_back((int)l2l_g.size());
   }

@@ -62,7 +62,7 @@ struct Tables {
   std::vector<double> m2m_c;
   // L2L (Eq. 4) as pair lists per output beta: input gamma, sign pattern e,
   // coefficient.
-  std::vector<int> l2l_off, l2l_g, l2l_e;
+  std::vector<int> l2l_off, l2l_off8, l2l_g, l2l_e;
   std::vector<double> l2l_c;
   // degree of each coefficient (|alpha|) for alpha < nc
   std::vector<int> degree;

@@ -163,13 +163,22 @@ __global__ void k_oct_kind_flags(int64_t n_oct, const int32_t* __restrict__ cell
   f_tgt[o] = t;
 }
 
+// Marks the octs of level b that hold a cell with grandchildren: the parents of
+// the level b+1 octs that hold a refined cell.
+__global__ void k_mark_rowsL(int64_t n_rows_next, const int32_t* __restrict__ rows_next,
+                             const int32_t* __restrict__ oct_parent_next, int32_t* flags) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_rows_next) return;
+  flags[oct_parent_next[rows_next[i]] >> 3] = 1;
+}
+
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
 #define CK(x)                                                        \
   do {                                                               \
     cudaError_t e_ = (x);                                            \
     if (e_ != cudaSuccess) {                                         \
-      c->last_error = std::string("tree: ") + cudaGetErrorString(e_); \
+      c->last_error = std::string("tree: " #x ": ") + cudaGetErrorString(e_); \
       return e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA; \
     }                                                                \
   } while (0)
@@ -209,14 +218,16 @@ fmm_status tree_build(Ctx* c, cudaStream_t st) {
     uint64_t* kb = (uint64_t*)c->keys_b.ptr;
     int32_t* va = (int32_t*)c->vals_a.ptr;
     int32_t* vb = (int32_t*)c->vals_b.ptr;
-    if (T.n_leaf)
+    if (T.n_leaf) {
       ++c->n_launch;
       k_leaf_keys<<<nblk(T.n_leaf), 256, 0, st>>>(T.n_leaf, (const int32_t*)T.ijk.ptr,
                                                   (const double*)T.mass.ptr, l, ka, va, err);
-    if (n_ref) ++c->n_launch;
-    if (n_ref)
+    }
+    if (n_ref) {
+      ++c->n_launch;
       k_refined_keys<<<nblk(n_ref), 256, 0, st>>>(n_ref, (const uint64_t*)c->lev[l + 1].oct_key.ptr,
                                                   ka + T.n_leaf, va + T.n_leaf);
+    }
     size_t tmp = 0;
     ++c->n_cub; CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
     CK(buf_ensure(c, c->sort_tmp, tmp));
@@ -316,13 +327,38 @@ fmm_status tree_build(Ctx* c, cudaStream_t st) {
                                   (int)n, st));
   }
   CK(cudaMemcpyAsync(counts.data() + 2, d_counts + 2, 8 * lmax, cudaMemcpyDeviceToHost, st));
-  unsigned e = 0;
-  CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   for (int l = 1; l <= lmax; ++l) {
     c->lev[l].n_rows = counts[2 * l];
     c->lev[l].n_tgt = counts[2 * l + 1];
   }
+  // ---- octs that need a local expansion (cells with grandchildren), levels 1..lmax-2
+  std::vector<int32_t> countsL(lmax + 1, 0);
+  for (int l = 1; l + 2 <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    LevelTree& N = c->lev[l + 1];
+    int64_t n = T.n_oct;
+    CK(buf_ensure(c, c->flags, n * 4));
+    CK(buf_ensure(c, T.rowsL, n * 4));
+    int32_t* fl = (int32_t*)c->flags.ptr;
+    CK(cudaMemsetAsync(fl, 0, n * 4, st));
+    if (N.n_rows) {
+      ++c->n_launch;
+      k_mark_rowsL<<<nblk(N.n_rows), 256, 0, st>>>(N.n_rows, (const int32_t*)N.rows.ptr,
+                                                    (const int32_t*)N.oct_parent.ptr, fl);
+    }
+    thrust::counting_iterator<int32_t> it(0);
+    size_t tmp = 0;
+    ++c->n_cub; CK(cub::DeviceSelect::Flagged(nullptr, tmp, it, fl, (int32_t*)T.rowsL.ptr, d_counts + l, (int)n, st));
+    CK(buf_ensure(c, c->sort_tmp, tmp));
+    ++c->n_cub; CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, fl, (int32_t*)T.rowsL.ptr, d_counts + l,
+                                  (int)n, st));
+  }
+  if (lmax >= 3) CK(cudaMemcpyAsync(countsL.data() + 1, d_counts + 1, 4 * (lmax - 2), cudaMemcpyDeviceToHost, st));
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int l = 1; l <= lmax; ++l) c->lev[l].n_rowsL = (l + 2 <= lmax) ? countsL[l] : 0;
   fmm_status s = err_to_status(e);
   if (s != FMM_OK) c->last_error = "tree: invalid hierarchy (error bits " + std::to_string(e) + ")";
   return s;

@@ -1,18 +1,25 @@
-// upward.cu -- Upward pass (P2M, Eq. 1; M2M, Eq. 2; Alg. 2) and L2L (Eq. 4).
+// upward.cu -- Upward pass (P2M, Eq. 1; M2M, Eq. 2; Alg. 2) and the L2L step
+// of the downward pass (Eq. 4, Alg. 3).
 //
 // Expansions are kept in box units (tables.h).  A leaf cell's multipole is its
-// mass as a monopole; a refined cell's multipole is the M2M sum of its eight
-// children.  Because the eight child offsets are (+-1/4)^3 of the parent box,
+// mass as a monopole (P2M of one point mass at the cell centre); its other
+// coefficients are zero and are cleared once per hierarchy, so each solve
+// writes one value per leaf.  A refined cell's multipole is the M2M sum of its
+// eight children.  Because the child offsets are (+-1/4)^3 of the parent box,
 // M2M factors into a sign transform over the children,
 //     S_e[gamma] = sum_c sign(c, e) Mt_c[gamma],  e in {0,1}^3,
-// followed by one short sum per output coefficient alpha over gamma <= alpha
-// with the sign pattern e = (alpha - gamma) mod 2.  L2L uses the same sign
-// rule on the parent's local expansion.
+// (a 3-stage butterfly, one stage per axis) followed by one short sum per
+// output coefficient alpha over gamma <= alpha with the sign pattern
+// e = (alpha - gamma) mod 2.  L2L runs the same factorisation backwards: per
+// output beta one sum per pattern e, then the butterfly over the children.
 //
-// The multipole of a box equals the sum over all trees T_j of the paper's
-// per-level multipoles (each tree holds the mass of one AMR level, and M2M is
-// linear), which is the form the M2L and M2P sources need (the merged tree of
-// Sec. 3.1 plus the tree of the target level).
+// The multipole of a box is the sum over the paper's per-level trees T_j of
+// their multipoles (each tree holds the mass of one AMR level and M2M is
+// linear): the sources M2L and M2P need (the merged tree of Sec. 3.1 plus the
+// tree of the target level).
+//
+// Cell masses ("mono") are stored in the precision of the near-field kernel
+// that reads them: FP32 in the mixed path, FP64 in the FP64 path.
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -21,37 +28,73 @@ namespace {
 constexpr int kNcMax = 168;  // ncoef(8) = 165
 
 template <typename T>
-__device__ __forceinline__ float to_f(T v) { return (float)v; }
+__device__ __forceinline__ void split_bf16(T v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  float f = (float)v;
+  h = __float2bfloat16_rn(f);
+  l = __float2bfloat16_rn(f - __bfloat162float(h));
+}
 
-template <typename Tin, typename Tacc, typename Tout>
-__global__ void __launch_bounds__(192) k_upward(
-    int nc, const int32_t* __restrict__ cell_child, const int32_t* __restrict__ cell_child_next,
-    const Tin* __restrict__ Mnext, const double* __restrict__ mass_here,
-    const double* __restrict__ mass_next, Tout* __restrict__ Mout, __nv_bfloat16* __restrict__ hi,
-    __nv_bfloat16* __restrict__ lo, double* __restrict__ mono, const int* __restrict__ poff,
-    const int* __restrict__ pg, const int* __restrict__ pe, const double* __restrict__ pc) {
+// x[c] -> S[e] = sum_c sign(c, e) x[c]: per axis, (a, b) -> (a + b, b - a).
+template <typename T>
+__device__ __forceinline__ void sign_transform(T x[8]) {
+#pragma unroll
+  for (int axis = 0; axis < 3; ++axis) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c & (1 << axis)) continue;
+      const T a = x[c], b = x[c | (1 << axis)];
+      x[c] = a + b;
+      x[c | (1 << axis)] = b - a;
+    }
+  }
+}
+
+// S[e] -> y[c] = sum_e sign(c, e) S[e]: per axis, (s0, s1) -> (s0 - s1, s0 + s1).
+template <typename T>
+__device__ __forceinline__ void sign_transform_back(T x[8]) {
+#pragma unroll
+  for (int axis = 0; axis < 3; ++axis) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c & (1 << axis)) continue;
+      const T s0 = x[c], s1 = x[c | (1 << axis)];
+      x[c] = s0 - s1;
+      x[c | (1 << axis)] = s0 + s1;
+    }
+  }
+}
+
+// Leaf cells of one level: monopole = mass.
+template <typename Tout, typename TMono>
+__global__ void k_leaf_mono(int64_t ncell, int nc, const int32_t* __restrict__ cell_child,
+                            const double* __restrict__ mass, Tout* __restrict__ M, __nv_bfloat16* __restrict__ hi,
+                            __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ncell) return;
+  int32_t ch = cell_child[i];
+  if (ch >= 0) return;
+  double m = mass[-1 - (int64_t)ch];
+  mono[i] = (TMono)m;
+  if (M) {
+    M[i * nc] = (Tout)m;
+    if (hi) split_bf16((Tout)m, hi[i * nc], lo[i * nc]);
+  }
+}
+
+// M2M: one block per oct of level b+1, i.e. per refined cell of level b.
+template <typename Tin, typename Tacc, typename Tout, typename TMono>
+__global__ void __launch_bounds__(128) k_m2m(
+    int nc, const int32_t* __restrict__ oct_parent_next, const int32_t* __restrict__ cell_child_next,
+    const Tin* __restrict__ Mnext, const double* __restrict__ mass_next, Tout* __restrict__ Mout,
+    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono,
+    const int* __restrict__ poff, const int* __restrict__ pg, const int* __restrict__ pe,
+    const Tacc* __restrict__ pc) {
   __shared__ Tacc Mc[8 * kNcMax];
   __shared__ Tacc S[8 * kNcMax];
-  const int64_t cell = blockIdx.x;
-  const int a = threadIdx.x;
-  const int32_t ch = cell_child[cell];
-  if (ch < 0) {  // leaf: monopole = mass (P2M of a single point mass at the cell centre)
-    Tout m = (Tout)mass_here[-1 - (int64_t)ch];
-    for (int k = a; k < nc; k += blockDim.x) {
-      Tout v = (k == 0) ? m : (Tout)0;
-      Mout[cell * nc + k] = v;
-      if (hi) {
-        float f = to_f(v);
-        __nv_bfloat16 h = __float2bfloat16_rn(f);
-        hi[cell * nc + k] = h;
-        lo[cell * nc + k] = __float2bfloat16_rn(f - __bfloat162float(h));
-      }
-    }
-    if (a == 0) mono[cell] = (double)m;
-    return;
-  }
-  const int64_t c0 = (int64_t)ch * 8;
-  for (int idx = a; idx < 8 * nc; idx += blockDim.x) {
+  const int64_t o = blockIdx.x;
+  const int64_t cell = oct_parent_next[o];
+  const int64_t c0 = o * 8;
+  for (int idx = threadIdx.x; idx < 8 * nc; idx += blockDim.x) {
     int c = idx / nc, g = idx - c * nc;
     int32_t cc = cell_child_next[c0 + c];
     Tacc v;
@@ -62,60 +105,55 @@ __global__ void __launch_bounds__(192) k_upward(
     Mc[c * nc + g] = v;
   }
   __syncthreads();
-  for (int g = a; g < nc; g += blockDim.x) {
+  for (int g = threadIdx.x; g < nc; g += blockDim.x) {
     Tacc x[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) x[c] = Mc[c * nc + g];
+    sign_transform(x);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      Tacc s = 0;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) s += (child_sign(c, e) > 0) ? x[c] : -x[c];
-      S[e * nc + g] = s;
-    }
+    for (int e = 0; e < 8; ++e) S[e * nc + g] = x[e];
   }
   __syncthreads();
-  for (int k = a; k < nc; k += blockDim.x) {
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     Tacc out = 0;
-    for (int j = poff[k]; j < poff[k + 1]; ++j) out += (Tacc)pc[j] * S[pe[j] * nc + pg[j]];
+    for (int j = poff[k]; j < poff[k + 1]; ++j) out += pc[j] * S[pe[j] * nc + pg[j]];
     Tout v = (Tout)out;
     Mout[cell * nc + k] = v;
-    if (hi) {
-      float f = to_f(v);
-      __nv_bfloat16 h = __float2bfloat16_rn(f);
-      hi[cell * nc + k] = h;
-      lo[cell * nc + k] = __float2bfloat16_rn(f - __bfloat162float(h));
-    }
-    if (k == 0) mono[cell] = (double)v;
+    if (hi) split_bf16(v, hi[cell * nc + k], lo[cell * nc + k]);
+    if (k == 0) mono[cell] = (TMono)v;
   }
 }
 
-__global__ void k_mono_leaves(int64_t ncell, const int32_t* __restrict__ cell_child,
-                              const double* __restrict__ mass, double* __restrict__ mono) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= ncell) return;
-  int32_t ch = cell_child[i];
-  mono[i] = (ch < 0) ? mass[-1 - (int64_t)ch] : 0.0;
-}
-
-// L2L into the 8 cells of each row oct of level b from its parent cell (b-1).
-__global__ void __launch_bounds__(256) k_l2l(int nc, int64_t n_rows, const int32_t* __restrict__ rows,
-                                             const int32_t* __restrict__ oct_parent,
-                                             const double* __restrict__ Lup, double* __restrict__ L,
-                                             const int* __restrict__ poff, const int* __restrict__ pg,
-                                             const int* __restrict__ pe, const double* __restrict__ pc) {
+// Downward step for the row octs of level b: L = L2L(parent's L) + this level's
+// M2L sum (accumulated by the contraction in FP32, added here in FP64).
+// One thread per output coefficient beta, all 8 children at once.
+__global__ void __launch_bounds__(128) k_l2l_add(int nc, const int32_t* __restrict__ rows,
+                                                 const int32_t* __restrict__ oct_parent,
+                                                 const double* __restrict__ Lup, const float* __restrict__ Lm,
+                                                 double* __restrict__ L, const int* __restrict__ poff8,
+                                                 const int* __restrict__ pg, const double* __restrict__ pc) {
   __shared__ double Lp[kNcMax];
-  int64_t r = blockIdx.x;
-  if (r >= n_rows) return;
-  int32_t o = rows[r];
-  int32_t par = oct_parent[o];
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) Lp[k] = Lup[(int64_t)par * nc + k];
+  const int32_t o = rows[blockIdx.x];
+  if (Lup) {
+    const int32_t par = oct_parent[o];
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) Lp[k] = Lup[(int64_t)par * nc + k];
+  }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 8 * nc; idx += blockDim.x) {
-    int c = idx / nc, b = idx - c * nc;
-    double s = 0.0;
-    for (int j = poff[b]; j < poff[b + 1]; ++j) s += pc[j] * (double)child_sign(c, pe[j]) * Lp[pg[j]];
-    L[((int64_t)o * 8 + c) * nc + b] = s;
+  for (int b = threadIdx.x; b < nc; b += blockDim.x) {
+    double acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      double s = 0.0;
+      if (Lup)
+        for (int j = poff8[b * 8 + e]; j < poff8[b * 8 + e + 1]; ++j) s += pc[j] * Lp[pg[j]];
+      acc[e] = s;
+    }
+    sign_transform_back(acc);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int64_t idx = ((int64_t)o * 8 + c) * nc + b;
+      L[idx] = Lm ? acc[c] + (double)Lm[idx] : acc[c];
+    }
   }
 }
 
@@ -124,60 +162,71 @@ __global__ void __launch_bounds__(256) k_l2l(int nc, int64_t n_rows, const int32
 void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {
   LevelTree& T = c->lev[l];
   int64_t n = 8 * T.n_oct;
-  if (!n) return;
+  if (!n || !T.n_leaf) return;
   unsigned g = (unsigned)((n + 255) / 256);
+  const int nc = c->tab.nc;
+  const bool f64 = c->cfg.precision == FMM_FP64;
+  __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
+  __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
+  const int32_t* cc = (const int32_t*)T.cell_child.ptr;
+  const double* mass = (const double*)T.mass.ptr;
   ++c->n_launch;
-  k_mono_leaves<<<g, 256, 0, st>>>(n, (const int32_t*)T.cell_child.ptr, (const double*)T.mass.ptr,
-                                   (double*)T.mono.ptr);
+  if (f64)
+    k_leaf_mono<double, double><<<g, 256, 0, st>>>(n, nc, cc, mass, l == c->lmax ? nullptr : (double*)T.M.ptr,
+                                                   hi, lo, (double*)T.mono.ptr);
+  else if (l == c->lmax || T.m_is_f64)
+    k_leaf_mono<double, float><<<g, 256, 0, st>>>(n, nc, cc, mass, l == c->lmax ? nullptr : (double*)T.M.ptr,
+                                                  hi, lo, (float*)T.mono.ptr);
+  else
+    k_leaf_mono<float, float><<<g, 256, 0, st>>>(n, nc, cc, mass, (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr);
 }
 
 void launch_upward(Ctx* c, int b, cudaStream_t st) {
   LevelTree& T = c->lev[b];
   LevelTree& N = c->lev[b + 1];
-  int64_t ncell = (b == 0) ? 1 : 8 * T.n_oct;
-  if (!ncell) return;
+  if (!N.n_oct) return;
   const int nc = c->tab.nc;
+  const bool f64 = c->cfg.precision == FMM_FP64;
   const int* poff = (const int*)c->d_m2m_off.ptr;
   const int* pg = (const int*)c->d_m2m_g.ptr;
   const int* pe = (const int*)c->d_m2m_e.ptr;
   const double* pc = (const double*)c->d_m2m_c.ptr;
-  int threads = ((nc + 31) / 32) * 32;
-  if (threads > 192) threads = 192;
-  dim3 grid((unsigned)ncell);
-  const int32_t* cc = (const int32_t*)T.cell_child.ptr;
+  dim3 grid((unsigned)N.n_oct);
+  const int32_t* par = (const int32_t*)N.oct_parent.ptr;
   const int32_t* ccn = (const int32_t*)N.cell_child.ptr;
-  const double* mh = (const double*)T.mass.ptr;
   const double* mn = (const double*)N.mass.ptr;
   __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
   __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
-  if (T.m_is_f64) {
-    if (N.m_is_f64)
-      ++c->n_launch;
-      k_upward<double, double, double><<<grid, threads, 0, st>>>(nc, cc, ccn, (const double*)N.M.ptr, mh, mn,
-                                                                 (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
-                                                                 poff, pg, pe, pc);
-    else
-      ++c->n_launch;
-      k_upward<float, double, double><<<grid, threads, 0, st>>>(nc, cc, ccn, (const float*)N.M.ptr, mh, mn,
+  ++c->n_launch;
+  if (f64) {
+    k_m2m<double, double, double, double><<<grid, 128, 0, st>>>(nc, par, ccn, (const double*)N.M.ptr, mn,
                                                                 (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
                                                                 poff, pg, pe, pc);
+  } else if (T.m_is_f64) {  // mixed path, top of the tree: FP64 shifts
+    if (N.m_is_f64)
+      k_m2m<double, double, double, float><<<grid, 128, 0, st>>>(nc, par, ccn, (const double*)N.M.ptr, mn,
+                                                                 (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
+                                                                 poff, pg, pe, pc);
+    else
+      k_m2m<float, double, double, float><<<grid, 128, 0, st>>>(nc, par, ccn, (const float*)N.M.ptr, mn,
+                                                                (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
+                                                                poff, pg, pe, pc);
   } else {
-    ++c->n_launch;
-    k_upward<float, float, float><<<grid, threads, 0, st>>>(nc, cc, ccn, (const float*)N.M.ptr, mh, mn,
-                                                            (float*)T.M.ptr, hi, lo, (double*)T.mono.ptr, poff,
-                                                            pg, pe, pc);
+    k_m2m<float, float, float, float><<<grid, 128, 0, st>>>(nc, par, ccn, (const float*)N.M.ptr, mn,
+                                                            (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg,
+                                                            pe, (const float*)c->d_m2m_c32.ptr);
   }
 }
 
-void launch_l2l(Ctx* c, int b, cudaStream_t st) {
+void launch_l2l_add(Ctx* c, int b, cudaStream_t st) {
   LevelTree& T = c->lev[b];
-  if (!T.n_rows) return;
+  if (!T.n_rowsL) return;
   ++c->n_launch;
-  k_l2l<<<(unsigned)T.n_rows, 256, 0, st>>>(c->tab.nc, T.n_rows, (const int32_t*)T.rows.ptr,
-                                            (const int32_t*)T.oct_parent.ptr, (const double*)c->lev[b - 1].L.ptr,
-                                            (double*)T.L.ptr, (const int*)c->d_l2l_off.ptr,
-                                            (const int*)c->d_l2l_g.ptr, (const int*)c->d_l2l_e.ptr,
-                                            (const double*)c->d_l2l_c.ptr);
+  k_l2l_add<<<(unsigned)T.n_rowsL, 128, 0, st>>>(
+      c->tab.nc, (const int32_t*)T.rowsL.ptr, (const int32_t*)T.oct_parent.ptr,
+      b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
+      c->cfg.precision == FMM_FP64 ? nullptr : (const float*)T.Lm.ptr, (double*)T.L.ptr,
+      (const int*)c->d_l2l_off8.ptr, (const int*)c->d_l2l_g.ptr, (const double*)c->d_l2l_c.ptr);
 }
 
 }  // namespace fmm
