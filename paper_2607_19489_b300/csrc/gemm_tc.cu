@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int32_t roct = valid ? S.rows[row_idx] : 0;
     int32_t* myn = s_nbr + t * kNbrStride;  // read by this thread only
     for (int q = 0; q < 26; ++q) myn[q] = valid ? S.nbr[(int64_t)roct * 27 + c_nbr26[q]] : -1;
+    const uint32_t myn_s = smem_u32(myn);  // read back with ld.shared (a plain pointer would be generic)
     const uint32_t ahi0 = smem_u32(Ahi) + t * (BK * 2), alo0 = smem_u32(Alo) + t * (BK * 2);
     bool ok = true;
     for (int it = 0; it < nit && ok; ++it) {
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (k < P.Kvalid) {
           const int qi = (k >= kb) ? qi0 + 1 : qi0;
           off = k - qi * P.KQ;
-          src = myn[qi];
+          asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
         }
         const uint32_t sw = (uint32_t)((j ^ ((t >> 1) & 3)) << 4);
         const __nv_bfloat16* gh = src >= 0 ? S.Ahi + (int64_t)src * P.KQ + off : S.Ahi;

@@ -29,7 +29,7 @@ namespace fmm {
 namespace {
 
 constexpr int kNcMax = 168;  // ncoef(8) = 165
-constexpr int kMaxNearSeg = 24;
+constexpr int kMaxNearSeg = 8;  // levels per launch (keeps the parameter block ~1 KB)
 
 // Source positions relative to the target oct's origin, level-l units:
 // cell c of neighbour slot q sits at 2 dq + bits(c) (its lower corner; the
@@ -159,14 +159,13 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     Y2[i] = Y[i] * Y[i];
     Z2[i] = Z[i] * Z[i];
   }
-  const T* sm = s_m[g];
 #pragma unroll
   for (int q = 0; q < 27; ++q) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int ix = 2 * (q % 3) + (c & 1), iy = 2 * ((q / 3) % 3) + ((c >> 1) & 1),
                 iz = 2 * (q / 9) + ((c >> 2) & 1);
-      T m = sm[q * 8 + c];
+      T m = s_m[g][q * 8 + c];  // indexed directly so the compiler emits shared-memory loads
       T r2 = X2[ix] + Y2[iy] + Z2[iz];
       if (q == 13) {  // the target's own oct: skip the self term
         const bool me = (c == tp);
@@ -242,7 +241,7 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     const T rx = (T)(2 * (fpos & 1) + tbx) * (T)0.25 - (T)0.375;
     const T ry = (T)(2 * ((fpos >> 1) & 1) + tby) * (T)0.25 - (T)0.375;
     const T rz = (T)(2 * ((fpos >> 2) & 1) + tbz) * (T)0.25 - (T)0.375;
-    const T* L = s_L[g];
+    // s_L indexed directly (a plain pointer into it compiles to generic loads)
     const int p = P.p;
     T xa = 1;
     for (int a = 0; a <= p; ++a) {
@@ -250,11 +249,11 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
       for (int b = 0; a + b <= p; ++b) {
         T m = xy;
         for (int cz = 0; a + b + cz <= p; ++cz) {
-          pl += L[c_lut[a][b][cz]] * m;
+          pl += s_L[g][c_lut[a][b][cz]] * m;
           if (a + b + cz < p) {
-            xl -= L[c_lut[a + 1][b][cz]] * m;
-            yl -= L[c_lut[a][b + 1][cz]] * m;
-            zl -= L[c_lut[a][b][cz + 1]] * m;
+            xl -= s_L[g][c_lut[a + 1][b][cz]] * m;
+            yl -= s_L[g][c_lut[a][b + 1][cz]] * m;
+            zl -= s_L[g][c_lut[a][b][cz + 1]] * m;
           }
           m *= rz * inv_k<T>(cz);
         }
@@ -321,44 +320,47 @@ fmm_status near_init(Ctx* c) {
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st) {
   const bool f64 = c->cfg.precision == FMM_FP64;
   const int opb = f64 ? 8 : 16;
-  NearParams P;
-  P.nseg = 0;
-  P.nc = c->tab.nc;
-  P.p = c->cfg.p;
-  P.out_fp32 = out_fp32;
-  P.nearop = f64 ? c->d_near64.ptr : c->d_near32.ptr;
-  P.G = c->cfg.G;
-  int blocks = 0;
-  for (int l = lo; l <= c->lmax && P.nseg < kMaxNearSeg; ++l) {
-    LevelTree& T = c->lev[l];
-    if (!T.n_tgt || !T.n_leaf) continue;
-    NearSeg& S = P.seg[P.nseg++];
-    S.tgt = (const int32_t*)T.tgt.ptr;
-    S.nbr = (const int32_t*)T.nbr.ptr;
-    S.cc_l = (const int32_t*)T.cell_child.ptr;
-    S.par_l = (const int32_t*)T.oct_parent.ptr;
-    S.par_up = (const int32_t*)c->lev[l - 1].oct_parent.ptr;
-    S.mono_up = (const double*)c->lev[l - 1].mono.ptr;
-    S.mono_l = (const double*)T.mono.ptr;
-    S.mono_dn = (l < c->lmax) ? (const double*)c->lev[l + 1].mono.ptr : nullptr;
-    S.M_l = T.M.ptr;
-    S.M_l_f64 = T.m_is_f64 ? 1 : 0;
-    S.L2 = (l - 2 >= 2) ? (const double*)c->lev[l - 2].L.ptr : nullptr;
-    S.acc = T.acc.ptr;
-    S.phi = phi[l - lo];
-    S.accel = accel[l - lo];
-    S.s1 = c->cfg.G * std::ldexp(1.0, l);
-    S.s2 = c->cfg.G * std::ldexp(1.0, 2 * l);
-    S.n_tgt = T.n_tgt;
-    S.blk0 = blocks;
-    blocks += (int)((T.n_tgt + opb - 1) / opb);
+  int l = lo;
+  while (l <= c->lmax) {  // up to kMaxNearSeg target levels per launch
+    NearParams P;
+    P.nseg = 0;
+    P.nc = c->tab.nc;
+    P.p = c->cfg.p;
+    P.out_fp32 = out_fp32;
+    P.nearop = f64 ? c->d_near64.ptr : c->d_near32.ptr;
+    P.G = c->cfg.G;
+    int blocks = 0;
+    for (; l <= c->lmax && P.nseg < kMaxNearSeg; ++l) {
+      LevelTree& T = c->lev[l];
+      if (!T.n_tgt || !T.n_leaf) continue;
+      NearSeg& S = P.seg[P.nseg++];
+      S.tgt = (const int32_t*)T.tgt.ptr;
+      S.nbr = (const int32_t*)T.nbr.ptr;
+      S.cc_l = (const int32_t*)T.cell_child.ptr;
+      S.par_l = (const int32_t*)T.oct_parent.ptr;
+      S.par_up = (const int32_t*)c->lev[l - 1].oct_parent.ptr;
+      S.mono_up = c->lev[l - 1].mono.ptr;
+      S.mono_l = T.mono.ptr;
+      S.mono_dn = (l < c->lmax) ? c->lev[l + 1].mono.ptr : nullptr;
+      S.M_l = T.M.ptr;
+      S.M_l_f64 = T.m_is_f64 ? 1 : 0;
+      S.L2 = (l - 2 >= 2) ? (const double*)c->lev[l - 2].L.ptr : nullptr;
+      S.acc = T.acc.ptr;
+      S.phi = phi[l - lo];
+      S.accel = accel[l - lo];
+      S.s1 = c->cfg.G * std::ldexp(1.0, l);
+      S.s2 = c->cfg.G * std::ldexp(1.0, 2 * l);
+      S.n_tgt = T.n_tgt;
+      S.blk0 = blocks;
+      blocks += (int)((T.n_tgt + opb - 1) / opb);
+    }
+    if (!blocks) continue;
+    ++c->n_launch;
+    if (f64)
+      k_near<double, 8><<<(unsigned)blocks, 64, 0, st>>>(P);
+    else
+      k_near<float, 16><<<(unsigned)blocks, 128, 0, st>>>(P);
   }
-  if (!blocks) return;
-  ++c->n_launch;
-  if (f64)
-    k_near<double, 8><<<(unsigned)blocks, 64, 0, st>>>(P);
-  else
-    k_near<float, 16><<<(unsigned)blocks, 128, 0, st>>>(P);
 }
 
 }  // namespace fmm
