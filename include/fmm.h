@@ -110,6 +110,29 @@ const char* fmm_last_error(const fmm_ctx* ctx);
 
 void fmm_destroy(fmm_ctx* ctx);
 
+/* Solve a complete unigrid of level 2..4 (n = 8^level cells, at most 16^3)
+ * without allocating any device memory.  The paper has no counterpart to this
+ * call; it exists for callers that cannot call cudaMalloc while they run, such
+ * as host codes whose device memory is owned by another allocator (one that
+ * reserves the whole GPU at start-up, say) or loops that must not allocate
+ * after initialisation.
+ *   ctx       an existing context (any precision, p <= 6); only its translation
+ *             tables are used, its own hierarchy is left as it was
+ *   ijk/mass  device pointers, int32 [n][3] and double [n], every cell of the
+ *             grid exactly once, any order
+ *   phi/accel device pointers, [n] and [n][3], double or float per
+ *             ctx's out_fp32, written in the input order
+ * All per-hierarchy scratch lives in one static device array of 2 MiB inside
+ * the library (every GPU that loads the library holds it until the process
+ * exits).  The first call on a device looks up that array's address; make it
+ * before any stream capture on the device.  All calls share the array, so
+ * calls that overlap on the GPU race.  The call synchronises `stream` once, to
+ * report invalid cells.  Returns FMM_ERR_ARG (with fmm_last_error set) for a
+ * level outside 2..4, n != 8^level or p > 6, and FMM_ERR_OUT_OF_BOX,
+ * FMM_ERR_DUPLICATE or FMM_ERR_NONFINITE for invalid cells. */
+fmm_status fmm_solve_unigrid_static(fmm_ctx* ctx, int level, int64_t n, const int32_t* ijk,
+                                    const double* mass, void* phi, void* accel, void* stream);
+
 /* ---- introspection (tests and tools) ---------------------------------- */
 
 /* Number of octs per level l = 0..lmax (n_oct[0] = 0) of the current tree. */

@@ -22,7 +22,7 @@ PRECISION = {"fp64": 0, "mixed": 1, "bf16x3": 1}
 
 EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_error", "fmm_destroy",
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
-            "fmm_set_timing", "fmm_stage_times", "fmm_stats"]
+            "fmm_set_timing", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static"]
 
 
 class FMMError(RuntimeError):
@@ -62,6 +62,7 @@ def lib() -> ctypes.CDLL:
     L.fmm_host_numerators.argtypes = [I, P, P]
     L.fmm_host_table.argtypes = [I, I, P, I64]
     L.fmm_stats.argtypes = [P, P]
+    L.fmm_solve_unigrid_static.argtypes = [P, I, I64, P, P, P, P, P]
     L.fmm_set_timing.argtypes = [P, I]
     L.fmm_stage_times.argtypes = [P, P]
     for name in EXPORTED:
@@ -203,6 +204,13 @@ class Solver:
         out = np.zeros(4)
         self._check(lib().fmm_stage_times(self._h, out.ctypes.data), "fmm_stage_times")
         return dict(zip(["upward", "downward", "m2p", "near"], out.tolist()))
+
+    def solve_unigrid_static(self, level: int, ijk, mass, phi, accel, stream=None):
+        """Unigrid solve (level 2..4) that allocates no device memory; all arguments are
+        device tensors (see fmm_solve_unigrid_static in include/fmm.h)."""
+        rc = lib().fmm_solve_unigrid_static(self._h, level, int(ijk.shape[0]), _data_ptr(ijk), _data_ptr(mass),
+                                            _data_ptr(phi), _data_ptr(accel), _stream_ptr(stream))
+        self._check(rc, "fmm_solve_unigrid_static")
 
     def stats(self):
         out = np.zeros(4, np.int64)
