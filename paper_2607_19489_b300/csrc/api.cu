@@ -379,6 +379,7 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
   }
   stage_event(c, 3, st);
   // 3b. near / nearest / far fields and the scatter, all target levels in one launch
+  launch_near_m2p(c, lo, st);  // refined cells of the near field (interface octs only)
   launch_near(c, lo, dphi.data() + lo, dacc.data() + lo, c->cfg.out_fp32, st);
   stage_event(c, 4, st);
   CKS(cudaGetLastError());
@@ -417,7 +418,7 @@ void fmm_destroy(fmm_ctx* c) {
   if (!c) return;
   if (c->last_stream) cudaStreamSynchronize(c->last_stream);
   for (auto& T : c->lev) {
-    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.tgt, &T.ijk,
+    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.tgt, &T.ijk,
                       &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lm, &T.acc})
       buf_free(c, *b);
   }

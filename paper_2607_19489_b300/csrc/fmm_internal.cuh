@@ -47,6 +47,7 @@ struct LevelTree {
   int64_t n_rows = 0;    // octs holding at least one refined cell
   int64_t n_tgt = 0;     // octs holding at least one leaf cell
   int64_t n_rowsL = 0;   // octs holding a cell with grandchildren (need a local expansion)
+  int64_t n_irows = 0;   // target octs with a refined cell among their 3^3 neighbour octs
   DevBuf oct_key;        // uint64 [n_oct]
   DevBuf oct_parent;     // int32 [n_oct] cell id at level-1
   DevBuf cell_child;     // int32 [8 n_oct]: >=0 child oct at level+1, else -1-leaf index
@@ -55,6 +56,8 @@ struct LevelTree {
   DevBuf rows;           // int32 [n_rows]
   DevBuf tgt;            // int32 [n_tgt]
   DevBuf rowsL;          // int32 [n_rowsL]
+  DevBuf irows;          // int32 [n_irows]
+  DevBuf leafmask;       // uint8 [n_oct]: bit c set when cell c of the oct is a leaf
   // inputs kept for adaptive time stepping (replaced by set_levels)
   DevBuf ijk;            // int32 [n_leaf][3]
   DevBuf mass;           // double [n_leaf]
@@ -121,6 +124,7 @@ fmm_status make_tensor_maps(Ctx* c, GemmOperand& op);
 void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* row_levels, int nlev, cudaStream_t st);
 // near.cu
 fmm_status near_init(Ctx* c);
+void launch_near_m2p(Ctx* c, int lo, cudaStream_t st);
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st);
 
 enum { kModeM2P = 0, kModeM2L = 1 };

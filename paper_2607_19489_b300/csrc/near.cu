@@ -94,7 +94,14 @@ struct NearParams {
   double G;
 };
 
-template <typename T, int OPB>
+// Index of the multi-index (a,b,c) in the graded order (degree, a descending,
+// b descending), for compile-time evaluation.
+__host__ __device__ constexpr int gidx(int a, int b, int c) {
+  return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+
+// PC > 0: expansion order known at compile time (the L2P loops unroll); 0: runtime P.p.
+template <typename T, int OPB, int PC>
 __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearParams P) {
   __shared__ T s_m[OPB][216];
   __shared__ T s_L[OPB][kNcMax];          // local expansion of the oct's level l-2 box
@@ -205,30 +212,8 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
         p2p<T>(m, (T)rx + (T)((kk & 1) * 2 - 1) * (T)0.25, (T)ry + (T)(((kk >> 1) & 1) * 2 - 1) * (T)0.25,
                (T)rz + (T)(((kk >> 2) & 1) * 2 - 1) * (T)0.25, phi, ax, ay, az);
       }
-    } else {
-      // near-field refined cell: M2P at integer offset R = t - P
-      const int ridx = ((-rz + 3) * 7 + (-ry + 3)) * 7 + (-rx + 3);
-      const T* op = nearop + (int64_t)ridx * P.nc * 4;
-      if (S.M_l_f64) {
-        const double* M = (const double*)S.M_l + pc * P.nc;
-        for (int a = 0; a < P.nc; ++a) {
-          T mv = (T)M[a];
-          phi += op[4 * a] * mv;
-          ax += op[4 * a + 1] * mv;
-          ay += op[4 * a + 2] * mv;
-          az += op[4 * a + 3] * mv;
-        }
-      } else {
-        const float* M = (const float*)S.M_l + pc * P.nc;
-        for (int a = 0; a < P.nc; ++a) {
-          T mv = (T)M[a];
-          phi += op[4 * a] * mv;
-          ax += op[4 * a + 1] * mv;
-          ay += op[4 * a + 2] * mv;
-          az += op[4 * a + 3] * mv;
-        }
-      }
     }
+    // refined cells not touching t: M2P, done beforehand by k_near_m2p into acc
   }
   // ---- bottom intermediate field (M2P, level l-1 units) and far field (L2P, level l-2 units)
   const T* acc = (const T*)S.acc;
@@ -242,6 +227,29 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     const T ry = (T)(2 * ((fpos >> 1) & 1) + tby) * (T)0.25 - (T)0.375;
     const T rz = (T)(2 * ((fpos >> 2) & 1) + tbz) * (T)0.25 - (T)0.375;
     // s_L indexed directly (a plain pointer into it compiles to generic loads)
+    if constexpr (PC > 0) {
+      T xa = 1;
+#pragma unroll
+      for (int a = 0; a <= PC; ++a) {
+        T xy = xa;
+#pragma unroll
+        for (int b = 0; a + b <= PC; ++b) {
+          T m = xy;
+#pragma unroll
+          for (int cz = 0; a + b + cz <= PC; ++cz) {
+            pl += s_L[g][gidx(a, b, cz)] * m;
+            if (a + b + cz < PC) {
+              xl -= s_L[g][gidx(a + 1, b, cz)] * m;
+              yl -= s_L[g][gidx(a, b + 1, cz)] * m;
+              zl -= s_L[g][gidx(a, b, cz + 1)] * m;
+            }
+            m *= rz * (T)(1.0 / (cz + 1));
+          }
+          xy *= ry * (T)(1.0 / (b + 1));
+        }
+        xa *= rx * (T)(1.0 / (a + 1));
+      }
+    } else {
     const int p = P.p;
     T xa = 1;
     for (int a = 0; a <= p; ++a) {
@@ -260,6 +268,7 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
         xy *= ry * inv_k<T>(b);
       }
       xa *= rx * inv_k<T>(a);
+    }
     }
   }
   // level-l units: the M2P sum is in level l-1 units, the local expansion in level l-2 units
@@ -281,6 +290,128 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     a[0] = (double)gx;
     a[1] = (double)gy;
     a[2] = (double)gz;
+  }
+}
+
+
+// Near-field M2P (Fig. 2: "M2P from the merged tree at FMM level l") for the
+// target octs that have refined cells among their 3^3 neighbour octs: one warp
+// per oct.  The refined cells are listed with a ballot, each one's multipole is
+// staged in shared memory, and lane 4t + j sums phi and accel of target t over
+// the coefficients alpha = j, j+4, ... with float4 loads of the [R][alpha][4]
+// operator.  Cells touching t are left to the nearest field.  The result is
+// added to the M2P accumulator of the target (level l-1 units: x2, x4).
+struct NearM2PSeg {
+  const int32_t* irows;
+  const int32_t* nbr;
+  const int32_t* cc_l;
+  const void* M_l;
+  void* acc;
+  int64_t n;
+  int blk0, M_l_f64;
+};
+struct NearM2PParams {
+  NearM2PSeg seg[kMaxNearSeg];
+  int nseg, nc;
+  const void* nearop;
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<double> {
+  using type = double4;
+};
+
+// One block of 8 warps per interface oct: warp 0 lists the refined cells, the
+// warps take every 8th cell, and the partial sums of the 8 targets are reduced
+// through shared memory at the end.
+template <typename T>
+__global__ void __launch_bounds__(256) k_near_m2p(const __grid_constant__ NearM2PParams P) {
+  __shared__ int16_t s_list[216];
+  __shared__ int s_cnt;
+  __shared__ int32_t s_nb[27];
+  __shared__ T s_M[8][kNcMax];
+  __shared__ T s_part[8][32][4];
+  int si = 0;
+  while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].blk0) ++si;
+  const NearM2PSeg& S = P.seg[si];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gi = (int64_t)(blockIdx.x - S.blk0);
+  if (gi >= S.n) return;  // whole block
+  const int32_t o = S.irows[gi];
+  if (threadIdx.x < 27) s_nb[threadIdx.x] = S.nbr[(int64_t)o * 27 + threadIdx.x];
+  __syncthreads();
+  if (w == 0) {  // list the refined cells of the 27 neighbour octs
+    int cnt = 0;
+    for (int s0 = 0; s0 < 216; s0 += 32) {
+      const int s = s0 + lane;
+      const int32_t nb = (s < 216) ? s_nb[s >> 3] : -1;
+      const bool ref = nb >= 0 && S.cc_l[(int64_t)nb * 8 + (s & 7)] >= 0;
+      const unsigned m = __ballot_sync(0xffffffffu, ref);
+      if (ref) s_list[cnt + __popc(m & ((1u << lane) - 1))] = (int16_t)s;
+      cnt += __popc(m);
+    }
+    if (lane == 0) s_cnt = cnt;
+  }
+  __syncthreads();
+  const int cnt = s_cnt;
+  const int t = lane >> 2, j = lane & 3;
+  const int tbx = t & 1, tby = (t >> 1) & 1, tbz = (t >> 2) & 1;
+  const int nc = P.nc;
+  using V4 = typename Vec4<T>::type;
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  for (int k = w; k < cnt; k += 8) {
+    const int s = s_list[k];
+    const int q = s >> 3, cc = s & 7;
+    const int64_t pc = (int64_t)s_nb[q] * 8 + cc;
+    if (S.M_l_f64)
+      for (int a = lane; a < nc; a += 32) s_M[w][a] = (T)((const double*)S.M_l)[pc * nc + a];
+    else
+      for (int a = lane; a < nc; a += 32) s_M[w][a] = (T)((const float*)S.M_l)[pc * nc + a];
+    __syncwarp();
+    // R = t - P in level-l units (lower corners: P at 2 dq + bits(cc))
+    const int rx = tbx - (2 * (q % 3 - 1) + (cc & 1));
+    const int ry = tby - (2 * ((q / 3) % 3 - 1) + ((cc >> 1) & 1));
+    const int rz = tbz - (2 * (q / 9 - 1) + ((cc >> 2) & 1));
+    if (abs(rx) > 1 || abs(ry) > 1 || abs(rz) > 1) {
+      const int ridx = ((rz + 3) * 7 + (ry + 3)) * 7 + (rx + 3);
+      const V4* op = (const V4*)((const T*)P.nearop + (int64_t)ridx * nc * 4);
+#pragma unroll 4
+      for (int a = j; a < nc; a += 4) {
+        const T mv = s_M[w][a];
+        const V4 o4 = op[a];
+        a0 += o4.x * mv;
+        a1 += o4.y * mv;
+        a2 += o4.z * mv;
+        a3 += o4.w * mv;
+      }
+    }
+    __syncwarp();
+  }
+  // sum the four coefficient phases of each target, then the eight warps
+#pragma unroll
+  for (int d = 1; d < 4; d <<= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, d);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, d);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, d);
+    a3 += __shfl_xor_sync(0xffffffffu, a3, d);
+  }
+  s_part[w][lane][0] = a0;
+  s_part[w][lane][1] = a1;
+  s_part[w][lane][2] = a2;
+  s_part[w][lane][3] = a3;
+  __syncthreads();
+  if (threadIdx.x < 32) {  // thread 4t + comp
+    const int tt = threadIdx.x >> 2, comp = threadIdx.x & 3;
+    T v = 0;
+    for (int ww = 0; ww < 8; ++ww) v += s_part[ww][tt * 4][comp];
+    const int64_t cell = (int64_t)o * 8 + tt;
+    if (S.cc_l[cell] < 0) ((T*)S.acc)[cell * 4 + comp] += (comp == 0 ? (T)2 : (T)4) * v;
   }
 }
 
@@ -356,10 +487,54 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
     }
     if (!blocks) continue;
     ++c->n_launch;
+    const int p = c->cfg.p;
+    if (f64) {
+      if (p == 4)
+        k_near<double, 8, 4><<<(unsigned)blocks, 64, 0, st>>>(P);
+      else if (p == 6)
+        k_near<double, 8, 6><<<(unsigned)blocks, 64, 0, st>>>(P);
+      else
+        k_near<double, 8, 0><<<(unsigned)blocks, 64, 0, st>>>(P);
+    } else {
+      if (p == 4)
+        k_near<float, 16, 4><<<(unsigned)blocks, 128, 0, st>>>(P);
+      else if (p == 6)
+        k_near<float, 16, 6><<<(unsigned)blocks, 128, 0, st>>>(P);
+      else
+        k_near<float, 16, 0><<<(unsigned)blocks, 128, 0, st>>>(P);
+    }
+  }
+}
+
+void launch_near_m2p(Ctx* c, int lo, cudaStream_t st) {
+  const bool f64 = c->cfg.precision == FMM_FP64;
+  int l = lo;
+  while (l <= c->lmax) {
+    NearM2PParams P;
+    P.nseg = 0;
+    P.nc = c->tab.nc;
+    P.nearop = f64 ? c->d_near64.ptr : c->d_near32.ptr;
+    int blocks = 0;
+    for (; l <= c->lmax && P.nseg < kMaxNearSeg; ++l) {
+      LevelTree& T = c->lev[l];
+      if (!T.n_irows || !T.n_leaf) continue;
+      NearM2PSeg& S = P.seg[P.nseg++];
+      S.irows = (const int32_t*)T.irows.ptr;
+      S.nbr = (const int32_t*)T.nbr.ptr;
+      S.cc_l = (const int32_t*)T.cell_child.ptr;
+      S.M_l = T.M.ptr;
+      S.M_l_f64 = T.m_is_f64 ? 1 : 0;
+      S.acc = T.acc.ptr;
+      S.n = T.n_irows;
+      S.blk0 = blocks;
+      blocks += (int)T.n_irows;
+    }
+    if (!blocks) continue;
+    ++c->n_launch;
     if (f64)
-      k_near<double, 8><<<(unsigned)blocks, 64, 0, st>>>(P);
+      k_near_m2p<double><<<(unsigned)blocks, 256, 0, st>>>(P);
     else
-      k_near<float, 16><<<(unsigned)blocks, 128, 0, st>>>(P);
+      k_near_m2p<float><<<(unsigned)blocks, 256, 0, st>>>(P);
   }
 }
 

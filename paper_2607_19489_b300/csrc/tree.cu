@@ -6,13 +6,19 @@
 // Morton key (x in the lowest bit of each triple); consecutive runs of the
 // same key>>3 are the octs of level l, so after sorting cell id = 8*oct +
 // (key & 7), the order the paper's oct tree (RAMSES) and the oracle use.
-// Duplicates, incomplete octs, out-of-box indices and non-finite masses are
-// latched as error bits.  Levels below lmin are complete grids.
+// Levels below lmin are complete grids.
 //
 // The 27-neighbour index is then built top-down without hashing: the
 // neighbour (dx,dy,dz) of oct o's parent cell lies in the parent oct's own
 // neighbour table, and its child oct (or its leaf status) is read from that
 // level's cell_child array -- the fully threaded tree idea of RAMSES.
+//
+// Oct counts follow from the leaf counts alone (n_oct[l] = (leaves[l] +
+// n_oct[l+1]) / 8), so the host sizes everything up front and the whole build
+// runs without synchronising; duplicates, incomplete octs, out-of-box
+// indices, non-finite masses and graded-rule violations are latched as error
+// bits, every kernel bounds-checks the indices it follows, and one
+// synchronisation at the end reads the error word and the list lengths.
 #include <cub/cub.cuh>
 #include <thrust/iterator/counting_iterator.h>
 
@@ -65,19 +71,23 @@ __global__ void k_oct_flags(int64_t n, const uint64_t* __restrict__ k, int32_t* 
   flags[i] = f;
 }
 
-__global__ void k_scatter_level(int64_t n, const uint64_t* __restrict__ k, const int32_t* __restrict__ v,
-                                const int32_t* __restrict__ scan, uint64_t* oct_key, int32_t* cell_child,
-                                int32_t* leaf_cell, int32_t* oct_parent_next, int64_t n_oct_next,
-                                int64_t n_leaf, unsigned* err) {
+// Cell id = sorted position.  A level is consistent only if every run of
+// siblings is a complete oct, i.e. position == 8 * oct + (key & 7) everywhere
+// and the number of octs equals the count derived from the leaf counts.
+__global__ void k_scatter_level(int64_t n, int64_t n_oct, const uint64_t* __restrict__ k,
+                                const int32_t* __restrict__ v, const int32_t* __restrict__ scan, uint64_t* oct_key,
+                                int32_t* cell_child, int32_t* leaf_cell, int32_t* oct_parent_next,
+                                int64_t n_oct_next, int64_t n_leaf, unsigned* err) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t oct = scan[i] - 1;
   uint64_t key = k[i];
-  if (i == 0 || (k[i - 1] >> 3) != (key >> 3)) oct_key[oct] = key >> 3;
-  if (i != 8 * oct + (int64_t)(key & 7)) {
+  if (i == n - 1 && oct + 1 != n_oct) atomicOr(err, kErrIncomplete);
+  if (oct >= n_oct || i != 8 * oct + (int64_t)(key & 7)) {
     atomicOr(err, kErrIncomplete);
     return;
   }
+  if (i == 0 || (k[i - 1] >> 3) != (key >> 3)) oct_key[oct] = key >> 3;
   int32_t val = v[i];
   cell_child[i] = val;
   if (val >= 0) {
@@ -103,7 +113,7 @@ __global__ void k_iota(int64_t n, int32_t* a) {
 }
 
 // nbr[l][o][q] from the level l-1 tables.  One thread per (oct, q).
-__global__ void k_nbr(int level, int64_t n_oct, const int32_t* __restrict__ oct_parent,
+__global__ void k_nbr(int level, int64_t n_oct, int64_t n_oct_up, const int32_t* __restrict__ oct_parent,
                       const int32_t* __restrict__ nbr_up, const int32_t* __restrict__ cell_child_up,
                       const int32_t* __restrict__ cell_child_here, int32_t* nbr, unsigned* err) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -111,11 +121,16 @@ __global__ void k_nbr(int level, int64_t n_oct, const int32_t* __restrict__ oct_
   int64_t o = t / 27;
   int q = (int)(t - o * 27);
   int d[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
-  int32_t res;
+  int32_t res = -1;
   if (level == 1) {
     res = (q == 13) ? 0 : -1;
   } else {
     int32_t pc = oct_parent[o];
+    if (pc < 0 || pc >= 8 * n_oct_up) {  // only after an inconsistent level (already flagged)
+      atomicOr(err, kErrIncomplete);
+      nbr[t] = -1;
+      return;
+    }
     int32_t op = pc >> 3;
     int cp = pc & 7;
     int e = 0, newc = 0, mul = 1;
@@ -129,7 +144,7 @@ __global__ void k_nbr(int level, int64_t n_oct, const int32_t* __restrict__ oct_
     int32_t nb = nbr_up[(int64_t)op * 27 + e];
     if (nb == -1) {
       res = -1;  // outside the unit box
-    } else if (nb < -1) {
+    } else if (nb < -1 || nb >= n_oct_up) {
       // the parent's neighbour at level l-1 does not exist although the parent is
       // refined: its father has an unrefined neighbour (Sec. 3.2)
       atomicOr(err, kErrNotGraded);
@@ -149,38 +164,63 @@ __global__ void k_nbr(int level, int64_t n_oct, const int32_t* __restrict__ oct_
   }
 }
 
+// Per oct: does it hold a refined cell (f_rows) / a leaf (f_tgt), and which
+// of its cells are leaves (bit c of leafmask).
 __global__ void k_oct_kind_flags(int64_t n_oct, const int32_t* __restrict__ cell_child, int32_t* f_rows,
-                                 int32_t* f_tgt) {
+                                 int32_t* f_tgt, uint8_t* leafmask) {
   int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (o >= n_oct) return;
-  int r = 0, t = 0;
+  int r = 0, t = 0, m = 0;
   for (int c = 0; c < 8; ++c) {
     int32_t ch = cell_child[o * 8 + c];
     r |= ch >= 0;
     t |= ch < 0;
+    m |= (ch < 0) << c;
   }
   f_rows[o] = r;
   f_tgt[o] = t;
+  leafmask[o] = (uint8_t)m;
 }
 
 // Marks the octs of level b that hold a cell with grandchildren: the parents of
-// the level b+1 octs that hold a refined cell.
-__global__ void k_mark_rowsL(int64_t n_rows_next, const int32_t* __restrict__ rows_next,
-                             const int32_t* __restrict__ oct_parent_next, int32_t* flags) {
+// the level b+1 octs that hold a refined cell.  One thread per level b+1 oct.
+__global__ void k_mark_rowsL(int64_t n_oct_next, const int32_t* __restrict__ cell_child_next,
+                             const int32_t* __restrict__ oct_parent_next, int64_t n_oct, int32_t* flags) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_rows_next) return;
-  flags[oct_parent_next[rows_next[i]] >> 3] = 1;
+  if (i >= n_oct_next) return;
+  bool ref = false;
+  for (int c = 0; c < 8; ++c) ref |= cell_child_next[i * 8 + c] >= 0;
+  if (!ref) return;
+  const int64_t o = oct_parent_next[i] >> 3;
+  if (o >= 0 && o < n_oct) flags[o] = 1;
+}
+
+// Marks the octs of a level that hold a leaf and have a refined cell in one of
+// their 3^3 neighbour octs (the near field then needs M2P or nearest-field
+// P2P).  One thread per oct.
+__global__ void k_mark_irows(int64_t n_oct, const int32_t* __restrict__ nbr, const int32_t* __restrict__ cell_child,
+                             int32_t* flags) {
+  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  bool leaf = false, ref = false;
+  for (int c = 0; c < 8; ++c) leaf |= cell_child[o * 8 + c] < 0;
+  for (int q = 0; q < 27 && leaf && !ref; ++q) {
+    const int32_t nb = nbr[o * 27 + q];
+    if (nb < 0 || nb >= n_oct) continue;
+    for (int c = 0; c < 8; ++c) ref |= cell_child[(int64_t)nb * 8 + c] >= 0;
+  }
+  flags[o] = leaf && ref;
 }
 
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
-#define CK(x)                                                        \
-  do {                                                               \
-    cudaError_t e_ = (x);                                            \
-    if (e_ != cudaSuccess) {                                         \
-      c->last_error = std::string("tree: " #x ": ") + cudaGetErrorString(e_); \
-      return e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA; \
-    }                                                                \
+#define CK(x)                                                                  \
+  do {                                                                         \
+    cudaError_t e_ = (x);                                                      \
+    if (e_ != cudaSuccess) {                                                   \
+      c->last_error = std::string("tree: " #x ": ") + cudaGetErrorString(e_);  \
+      return e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;     \
+    }                                                                          \
   } while (0)
 
 fmm_status err_to_status(unsigned e) {
@@ -193,27 +233,80 @@ fmm_status err_to_status(unsigned e) {
   return FMM_OK;
 }
 
+// Stream compaction of the oct indices whose flag is set (CUB select).
+fmm_status select_flagged(Ctx* c, const int32_t* flags, int64_t n, int32_t* out, int32_t* d_count,
+                          cudaStream_t st) {
+  thrust::counting_iterator<int32_t> it(0);
+  size_t tmp = 0;
+  CK(cub::DeviceSelect::Flagged(nullptr, tmp, it, flags, out, d_count, (int)n, st));
+  CK(buf_ensure(c, c->sort_tmp, tmp));
+  ++c->n_cub;
+  CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, flags, out, d_count, (int)n, st));
+  return FMM_OK;
+}
+
+#define TRYT(x)                  \
+  do {                           \
+    fmm_status s_ = (x);         \
+    if (s_ != FMM_OK) return s_; \
+  } while (0)
+
 }  // namespace
 
 fmm_status tree_build(Ctx* c, cudaStream_t st) {
   const int lmin = c->lmin, lmax = c->lmax;
   unsigned* err = c->d_err;
-  CK(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
-  // ---- bottom-up sorted passes, levels lmax..lmin -------------------------
+  // ---- oct counts from the leaf counts ----------------------------------------
+  // An inconsistent count is latched, not returned at once: the device checks
+  // below may name the cause (a duplicate, an out-of-box index) more precisely.
+  unsigned host_err = 0;
   for (int l = lmax; l >= lmin; --l) {
-    LevelTree& T = c->lev[l];
-    int64_t n_ref = (l < lmax) ? c->lev[l + 1].n_oct : 0;
-    int64_t n = T.n_leaf + n_ref;
+    const int64_t n = c->lev[l].n_leaf + ((l < lmax) ? c->lev[l + 1].n_oct : 0);
     if (n == 0 || n > (int64_t)INT32_MAX / 2) {
       c->last_error = "tree: level " + std::to_string(l) + " has no cells or too many";
       return n == 0 ? FMM_ERR_INCOMPLETE : FMM_ERR_ARG;
     }
-    CK(buf_ensure(c, c->keys_a, n * 8));
-    CK(buf_ensure(c, c->keys_b, n * 8));
-    CK(buf_ensure(c, c->vals_a, n * 4));
-    CK(buf_ensure(c, c->vals_b, n * 4));
-    CK(buf_ensure(c, c->flags, n * 4));
-    CK(buf_ensure(c, c->scan, n * 4));
+    if (n % 8) host_err |= kErrIncomplete;
+    c->lev[l].n_oct = (n + 7) / 8;
+  }
+  if (c->lev[lmin].n_oct != (int64_t)1 << (3 * (lmin - 1))) host_err |= kErrIncomplete;
+  for (int l = 1; l < lmin; ++l) {
+    c->lev[l].n_oct = (int64_t)1 << (3 * (l - 1));
+    c->lev[l].n_leaf = 0;
+  }
+  c->lev[0].n_oct = 0;
+  // ---- size everything ----------------------------------------------------------
+  int64_t nmax = 0;
+  for (int l = 1; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    nmax = std::max<int64_t>(nmax, 8 * T.n_oct);
+    CK(buf_ensure(c, T.oct_key, T.n_oct * 8));
+    CK(buf_ensure(c, T.oct_parent, T.n_oct * 4));
+    CK(buf_ensure(c, T.cell_child, T.n_oct * 32));
+    CK(buf_ensure(c, T.leaf_cell, std::max<int64_t>(T.n_leaf, 1) * 4));
+    CK(buf_ensure(c, T.nbr, T.n_oct * 27 * 4));
+    CK(buf_ensure(c, T.rows, T.n_oct * 4));
+    CK(buf_ensure(c, T.tgt, T.n_oct * 4));
+    CK(buf_ensure(c, T.rowsL, T.n_oct * 4));
+    CK(buf_ensure(c, T.irows, T.n_oct * 4));
+    CK(buf_ensure(c, T.leafmask, T.n_oct));
+  }
+  CK(buf_ensure(c, c->lev[0].cell_child, 32));
+  CK(buf_ensure(c, c->keys_a, nmax * 8));
+  CK(buf_ensure(c, c->keys_b, nmax * 8));
+  CK(buf_ensure(c, c->vals_a, nmax * 4));
+  CK(buf_ensure(c, c->vals_b, nmax * 4));
+  CK(buf_ensure(c, c->flags, nmax * 8));
+  CK(buf_ensure(c, c->scan, nmax * 4));
+  CK(buf_ensure(c, c->counter, 4 * 4 * (lmax + 2)));
+  int32_t* d_counts = (int32_t*)c->counter.ptr;  // [4][lmax+2]: rows, tgt, rowsL, irows
+  CK(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  CK(cudaMemsetAsync(d_counts, 0, 4 * 4 * (lmax + 2), st));
+  // ---- bottom-up sorted passes, levels lmax..lmin -------------------------
+  for (int l = lmax; l >= lmin; --l) {
+    LevelTree& T = c->lev[l];
+    const int64_t n_ref = (l < lmax) ? c->lev[l + 1].n_oct : 0;
+    const int64_t n = T.n_leaf + n_ref;
     uint64_t* ka = (uint64_t*)c->keys_a.ptr;
     uint64_t* kb = (uint64_t*)c->keys_b.ptr;
     int32_t* va = (int32_t*)c->vals_a.ptr;
@@ -229,57 +322,28 @@ fmm_status tree_build(Ctx* c, cudaStream_t st) {
                                                   ka + T.n_leaf, va + T.n_leaf);
     }
     size_t tmp = 0;
-    ++c->n_cub; CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
+    CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
     CK(buf_ensure(c, c->sort_tmp, tmp));
-    ++c->n_cub; CK(cub::DeviceRadixSort::SortPairs(c->sort_tmp.ptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
+    ++c->n_cub;
+    CK(cub::DeviceRadixSort::SortPairs(c->sort_tmp.ptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
     int32_t* flags = (int32_t*)c->flags.ptr;
     int32_t* scan = (int32_t*)c->scan.ptr;
     ++c->n_launch;
     k_oct_flags<<<nblk(n), 256, 0, st>>>(n, kb, flags, err);
     tmp = 0;
-    ++c->n_cub; CK(cub::DeviceScan::InclusiveSum(nullptr, tmp, flags, scan, (int)n, st));
+    CK(cub::DeviceScan::InclusiveSum(nullptr, tmp, flags, scan, (int)n, st));
     CK(buf_ensure(c, c->sort_tmp, tmp));
-    ++c->n_cub; CK(cub::DeviceScan::InclusiveSum(c->sort_tmp.ptr, tmp, flags, scan, (int)n, st));
-    int32_t n_oct32 = 0;
-    CK(cudaMemcpyAsync(&n_oct32, scan + n - 1, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    T.n_oct = n_oct32;
-    if (8 * T.n_oct != n || (l == lmin && T.n_oct != (int64_t)1 << (3 * (l - 1)))) {
-      c->last_error = "tree: level " + std::to_string(l) + " has incomplete octs or does not cover the box";
-      unsigned e = 0;
-      CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      fmm_status s = err_to_status(e);
-      return s != FMM_OK ? s : FMM_ERR_INCOMPLETE;
-    }
-    CK(buf_ensure(c, T.oct_key, T.n_oct * 8));
-    CK(buf_ensure(c, T.oct_parent, T.n_oct * 4));
-    CK(buf_ensure(c, T.cell_child, T.n_oct * 32));
-    CK(buf_ensure(c, T.leaf_cell, std::max<int64_t>(T.n_leaf, 1) * 4));
+    ++c->n_cub;
+    CK(cub::DeviceScan::InclusiveSum(c->sort_tmp.ptr, tmp, flags, scan, (int)n, st));
     int32_t* par_next = (l < lmax) ? (int32_t*)c->lev[l + 1].oct_parent.ptr : nullptr;
     ++c->n_launch;
-    k_scatter_level<<<nblk(n), 256, 0, st>>>(n, kb, vb, scan, (uint64_t*)T.oct_key.ptr,
-                                             (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr,
-                                             par_next, n_ref, T.n_leaf, err);
-  }
-  {  // stop before the neighbour stage if the sorted passes found an invalid hierarchy:
-     // its parent/child links may be incomplete
-    unsigned e = 0;
-    CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (e) {
-      c->last_error = "tree: invalid hierarchy (error bits " + std::to_string(e) + ")";
-      return err_to_status(e);
-    }
+    k_scatter_level<<<nblk(n), 256, 0, st>>>(n, T.n_oct, kb, vb, scan, (uint64_t*)T.oct_key.ptr,
+                                             (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next,
+                                             n_ref, T.n_leaf, err);
   }
   // ---- complete grids below lmin and the root ------------------------------
   for (int l = 1; l < lmin; ++l) {
     LevelTree& T = c->lev[l];
-    T.n_oct = (int64_t)1 << (3 * (l - 1));
-    T.n_leaf = 0;
-    CK(buf_ensure(c, T.oct_key, T.n_oct * 8));
-    CK(buf_ensure(c, T.oct_parent, T.n_oct * 4));
-    CK(buf_ensure(c, T.cell_child, T.n_oct * 32));
     ++c->n_launch;
     k_full_level<<<nblk(8 * T.n_oct), 256, 0, st>>>(T.n_oct, (uint64_t*)T.oct_key.ptr,
                                                      (int32_t*)T.oct_parent.ptr, (int32_t*)T.cell_child.ptr);
@@ -287,81 +351,69 @@ fmm_status tree_build(Ctx* c, cudaStream_t st) {
   // octs of level lmin: their parents are the complete grid of level lmin-1
   ++c->n_launch;
   k_iota<<<nblk(c->lev[lmin].n_oct), 256, 0, st>>>(c->lev[lmin].n_oct, (int32_t*)c->lev[lmin].oct_parent.ptr);
-  {
-    LevelTree& R = c->lev[0];
-    R.n_oct = 0;
-    CK(buf_ensure(c, R.cell_child, 32));
-    CK(cudaMemsetAsync(R.cell_child.ptr, 0, 4, st));
-  }
+  CK(cudaMemsetAsync(c->lev[0].cell_child.ptr, 0, 4, st));
   // ---- neighbour tables top-down -------------------------------------------
   for (int l = 1; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
-    CK(buf_ensure(c, T.nbr, T.n_oct * 27 * 4));
     const int32_t* nbr_up = (l >= 2) ? (const int32_t*)c->lev[l - 1].nbr.ptr : nullptr;
     const int32_t* cc_up = (const int32_t*)c->lev[l - 1].cell_child.ptr;
+    const int64_t n_up = (l >= 2) ? c->lev[l - 1].n_oct : 1;
     ++c->n_launch;
-    k_nbr<<<nblk(T.n_oct * 27), 256, 0, st>>>(l, T.n_oct, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
+    k_nbr<<<nblk(T.n_oct * 27), 256, 0, st>>>(l, T.n_oct, n_up, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
                                               (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr, err);
   }
-  // ---- row lists: octs with a refined cell / with a leaf cell ----------------
-  std::vector<int32_t> counts(2 * (lmax + 1), 0);
-  CK(buf_ensure(c, c->counter, 8 * (lmax + 1) + 8));
-  int32_t* d_counts = (int32_t*)c->counter.ptr;
-  for (int l = 1; l <= lmax; ++l) {
+  // ---- row lists ------------------------------------------------------------
+  const int stride = lmax + 2;
+  for (int l = 1; l <= lmax; ++l) {  // octs with a refined cell / with a leaf, leaf masks
     LevelTree& T = c->lev[l];
-    int64_t n = T.n_oct;
-    CK(buf_ensure(c, c->flags, n * 8));
-    CK(buf_ensure(c, T.rows, n * 4));
-    CK(buf_ensure(c, T.tgt, n * 4));
     int32_t* fr = (int32_t*)c->flags.ptr;
-    int32_t* ft = fr + n;
+    int32_t* ft = fr + T.n_oct;
     ++c->n_launch;
-    k_oct_kind_flags<<<nblk(n), 256, 0, st>>>(n, (const int32_t*)T.cell_child.ptr, fr, ft);
-    thrust::counting_iterator<int32_t> it(0);
-    size_t tmp = 0;
-    ++c->n_cub; CK(cub::DeviceSelect::Flagged(nullptr, tmp, it, fr, (int32_t*)T.rows.ptr, d_counts + 2 * l, (int)n, st));
-    CK(buf_ensure(c, c->sort_tmp, tmp));
-    ++c->n_cub; CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, fr, (int32_t*)T.rows.ptr, d_counts + 2 * l,
-                                  (int)n, st));
-    ++c->n_cub; CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, ft, (int32_t*)T.tgt.ptr, d_counts + 2 * l + 1,
-                                  (int)n, st));
+    k_oct_kind_flags<<<nblk(T.n_oct), 256, 0, st>>>(T.n_oct, (const int32_t*)T.cell_child.ptr, fr, ft,
+                                                     (uint8_t*)T.leafmask.ptr);
+    TRYT(select_flagged(c, fr, T.n_oct, (int32_t*)T.rows.ptr, d_counts + 0 * stride + l, st));
+    TRYT(select_flagged(c, ft, T.n_oct, (int32_t*)T.tgt.ptr, d_counts + 1 * stride + l, st));
   }
-  CK(cudaMemcpyAsync(counts.data() + 2, d_counts + 2, 8 * lmax, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  for (int l = 1; l <= lmax; ++l) {
-    c->lev[l].n_rows = counts[2 * l];
-    c->lev[l].n_tgt = counts[2 * l + 1];
-  }
-  // ---- octs that need a local expansion (cells with grandchildren), levels 1..lmax-2
-  std::vector<int32_t> countsL(lmax + 1, 0);
+  // octs that need a local expansion (cells with grandchildren), levels 1..lmax-2
   for (int l = 1; l + 2 <= lmax; ++l) {
     LevelTree& T = c->lev[l];
     LevelTree& N = c->lev[l + 1];
-    int64_t n = T.n_oct;
-    CK(buf_ensure(c, c->flags, n * 4));
-    CK(buf_ensure(c, T.rowsL, n * 4));
     int32_t* fl = (int32_t*)c->flags.ptr;
-    CK(cudaMemsetAsync(fl, 0, n * 4, st));
-    if (N.n_rows) {
-      ++c->n_launch;
-      k_mark_rowsL<<<nblk(N.n_rows), 256, 0, st>>>(N.n_rows, (const int32_t*)N.rows.ptr,
-                                                    (const int32_t*)N.oct_parent.ptr, fl);
-    }
-    thrust::counting_iterator<int32_t> it(0);
-    size_t tmp = 0;
-    ++c->n_cub; CK(cub::DeviceSelect::Flagged(nullptr, tmp, it, fl, (int32_t*)T.rowsL.ptr, d_counts + l, (int)n, st));
-    CK(buf_ensure(c, c->sort_tmp, tmp));
-    ++c->n_cub; CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, fl, (int32_t*)T.rowsL.ptr, d_counts + l,
-                                  (int)n, st));
+    CK(cudaMemsetAsync(fl, 0, T.n_oct * 4, st));
+    ++c->n_launch;
+    k_mark_rowsL<<<nblk(N.n_oct), 256, 0, st>>>(N.n_oct, (const int32_t*)N.cell_child.ptr,
+                                                 (const int32_t*)N.oct_parent.ptr, T.n_oct, fl);
+    TRYT(select_flagged(c, fl, T.n_oct, (int32_t*)T.rowsL.ptr, d_counts + 2 * stride + l, st));
   }
-  if (lmax >= 3) CK(cudaMemcpyAsync(countsL.data() + 1, d_counts + 1, 4 * (lmax - 2), cudaMemcpyDeviceToHost, st));
+  // target octs next to refined cells (near-field M2P / nearest field), levels lmin..lmax
+  for (int l = lmin; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    int32_t* fl = (int32_t*)c->flags.ptr;
+    ++c->n_launch;
+    k_mark_irows<<<nblk(T.n_oct), 256, 0, st>>>(T.n_oct, (const int32_t*)T.nbr.ptr, (const int32_t*)T.cell_child.ptr,
+                                                fl);
+    TRYT(select_flagged(c, fl, T.n_oct, (int32_t*)T.irows.ptr, d_counts + 3 * stride + l, st));
+  }
+  // ---- the one synchronisation: error word and list lengths ------------------
+  std::vector<int32_t> counts(4 * stride, 0);
+  CK(cudaMemcpyAsync(counts.data(), d_counts, 4 * 4 * stride, cudaMemcpyDeviceToHost, st));
   unsigned e = 0;
   CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  for (int l = 1; l <= lmax; ++l) c->lev[l].n_rowsL = (l + 2 <= lmax) ? countsL[l] : 0;
+  e |= host_err;
   fmm_status s = err_to_status(e);
-  if (s != FMM_OK) c->last_error = "tree: invalid hierarchy (error bits " + std::to_string(e) + ")";
-  return s;
+  if (s != FMM_OK) {
+    c->last_error = "tree: invalid hierarchy (error bits " + std::to_string(e) + ")";
+    return s;
+  }
+  for (int l = 1; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    T.n_rows = counts[0 * stride + l];
+    T.n_tgt = counts[1 * stride + l];
+    T.n_rowsL = (l + 2 <= lmax) ? counts[2 * stride + l] : 0;
+    T.n_irows = (l >= lmin) ? counts[3 * stride + l] : 0;
+  }
+  return FMM_OK;
 }
 
 }  // namespace fmm
