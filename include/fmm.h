@@ -59,7 +59,7 @@ typedef enum {
 typedef enum {
   FMM_FP64 = 0,          /* every step in FP64 (DFMA) */
   FMM_MIXED_BF16X3 = 1   /* M2L/M2P on tcgen05 tensor cores in split-BF16 (3 products,
-                            FP32 accumulation), P2P in FP32, FP64 for box levels <= 4
+                            FP32 accumulation), P2P in FP32, FP64 for box levels <= 3
                             of M2M, for L2L and for local-expansion accumulation */
 } fmm_precision;
 
@@ -84,11 +84,13 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out);
  *   mass[k] double [n[k]] masses
  * ijk/mass may be device or host pointers (host data is copied in on
  * `stream`).  The caller keeps ownership; the library copies what it needs
- * before returning, so the buffers may be reused afterwards.  The first call
- * must have lo == lmin; later calls must keep lmin and lmax (FMM_ERR_STATE).
- * Levels below lo keep their previous cells and masses.  The tree index of
- * the whole hierarchy (Morton-sorted octs, parents, children, 27-neighbour
- * tables) is rebuilt and validated; this call synchronises `stream`.
+ * before returning, so the buffers may be reused afterwards.  A call with
+ * lo == lmin replaces the whole hierarchy (lmin and lmax may change); a call
+ * with lo > lmin must keep lmin and lmax (FMM_ERR_STATE), and levels below lo
+ * keep their previous cells and masses.  The first call must have lo == lmin.
+ * The tree index of the whole hierarchy (Morton-sorted octs, parents,
+ * children, 27-neighbour tables) is rebuilt and validated, as a CUDA graph
+ * when graphs are on (fmm_set_graphs); this call synchronises `stream` once.
  * Requires 2 <= lmin <= lmax <= 20. */
 fmm_status fmm_set_levels(fmm_ctx* ctx, int lmin, int lmax, int lo, const int64_t* n,
                           const int32_t* const* ijk, const double* const* mass, void* stream);
@@ -171,6 +173,14 @@ fmm_status fmm_host_table(int p, int which, double* out, int64_t n);
  * out[1] = calls into CUB primitives (radix sort, scan, select) during tree
  * builds, out[2] = fmm_solve calls, out[3] = fmm_set_levels calls. */
 fmm_status fmm_stats(const fmm_ctx* ctx, int64_t* out4);
+
+/* fmm_solve replays its device work as a CUDA graph (on by default): the
+ * first solve for a given lo, output pointers and tree layout captures it on
+ * a stream of the library's own, later ones launch it on `stream`.  A new
+ * hierarchy with other list lengths, or a reallocated workspace, captures
+ * again.  on = 0 launches every kernel directly.  With timing on (below) the
+ * solve never uses a graph. */
+fmm_status fmm_set_graphs(fmm_ctx* ctx, int on);
 
 /* Per-stage device times (ms) of the last solve when timing is enabled with
  * fmm_set_timing(ctx, 1): upward, downward, m2p, near (4 doubles). */

@@ -28,6 +28,7 @@ cudaError_t buf_ensure(Ctx* c, DevBuf& b, size_t bytes) {
     b.ptr = nullptr;
     b.bytes = 0;
   }
+  ++c->layout_gen;  // cached solve graphs hold the old pointers
   if (c->cfg.mem_budget && c->bytes_in_use + bytes > c->cfg.mem_budget) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc(&b.ptr, bytes);
   if (e != cudaSuccess) {
@@ -140,6 +141,19 @@ fmm_status init_tables(Ctx* c) {
   TRY(upload(c, c->d_m2m_e, t.m2m_e));
   TRY(upload(c, c->d_m2m_c, t.m2m_c));
   TRY(upload(c, c->d_m2m_c32, std::vector<float>(t.m2m_c.begin(), t.m2m_c.end())));
+  {  // the gamma = 0 term of each alpha: all an oct of point masses needs
+    std::vector<double> w0(t.nc, 0.0);
+    std::vector<int> e0(t.nc, 0);
+    for (int k = 0; k < t.nc; ++k)
+      for (int j = t.m2m_off[k]; j < t.m2m_off[k + 1]; ++j)
+        if (t.m2m_g[j] == 0) {
+          w0[k] = t.m2m_c[j];
+          e0[k] = t.m2m_e[j];
+        }
+    TRY(upload(c, c->d_m2m_w0, w0));
+    TRY(upload(c, c->d_m2m_w0_32, std::vector<float>(w0.begin(), w0.end())));
+    TRY(upload(c, c->d_m2m_e0, e0));
+  }
   TRY(upload(c, c->d_l2l_off, t.l2l_off));
   TRY(upload(c, c->d_l2l_off8, t.l2l_off8));
   TRY(upload(c, c->d_l2l_g, t.l2l_g));
@@ -183,18 +197,6 @@ fmm_status size_expansions(Ctx* c) {
       if (!f64) CKS(buf_ensure(c, T.Lm, ncell * nc * 4));
     }
     if (l >= c->lmin) CKS(buf_ensure(c, T.acc, ncell * 4 * (f64 ? 8 : 4)));
-  }
-  return FMM_OK;
-}
-
-// Leaf cells only ever carry a monopole: clear every multipole array once per
-// hierarchy so that each solve writes one value per leaf.
-fmm_status zero_expansions(Ctx* c, cudaStream_t st) {
-  for (int l = 1; l < c->lmax; ++l) {
-    LevelTree& T = c->lev[l];
-    CKS(cudaMemsetAsync(T.M.ptr, 0, T.M.bytes, st));
-    if (T.Mhi.ptr) CKS(cudaMemsetAsync(T.Mhi.ptr, 0, T.Mhi.bytes, st));
-    if (T.Mlo.ptr) CKS(cudaMemsetAsync(T.Mlo.ptr, 0, T.Mlo.bytes, st));
   }
   return FMM_OK;
 }
@@ -256,6 +258,50 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
   return FMM_OK;
 }
 
+// The tree build's device work as a
+// CUDA graph, captured once per (layout generation, levels, leaf counts).
+static fmm_status launch_tree_graph(Ctx* c, cudaStream_t st) {
+  std::vector<uintptr_t> key = {(uintptr_t)c->layout_gen, (uintptr_t)c->lmin, (uintptr_t)c->lmax};
+  for (int l = c->lmin; l <= c->lmax; ++l) key.push_back((uintptr_t)c->lev[l].n_leaf);
+  Ctx::SolveGraph* g = nullptr;
+  for (auto& e : c->tree_graphs)
+    if (e.key == key) g = &e;
+  if (!g) {
+    for (size_t i = 0; i < c->tree_graphs.size();)
+      if (c->tree_graphs[i].key[0] != (uintptr_t)c->layout_gen || c->tree_graphs.size() >= 4) {
+        cudaGraphExecDestroy(c->tree_graphs[i].exec);
+        c->tree_graphs.erase(c->tree_graphs.begin() + i);
+      } else {
+        ++i;
+      }
+    if (!c->cap_stream) CKS(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const int64_t n0 = c->n_launch, k0 = c->n_cub;
+    CKS(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    fmm_status s = tree_enqueue(c, c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (s != FMM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    CKS(ee);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CKS(ei);
+    c->tree_graphs.push_back({key, exec, c->n_launch - n0, c->n_cub - k0});
+    c->n_launch = n0;
+    c->n_cub = k0;
+    ++c->n_graph_build;
+    g = &c->tree_graphs.back();
+  }
+  CKS(cudaGraphLaunch(g->exec, st));
+  c->n_launch += g->launches;
+  c->n_cub += g->cub_calls;
+  ++c->n_graph_launch;
+  return FMM_OK;
+}
+
 fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t* n, const int32_t* const* ijk,
                           const double* const* mass, void* stream) {
   if (!c || !n || !ijk || !mass) return FMM_ERR_ARG;
@@ -265,7 +311,7 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
       c->last_error = "first fmm_set_levels must give the whole hierarchy (lo == lmin)";
       return FMM_ERR_STATE;
     }
-  } else if (lmin != c->lmin || lmax != c->lmax) {
+  } else if (lo > lmin && (lmin != c->lmin || lmax != c->lmax)) {
     c->last_error = "fmm_set_levels: lmin/lmax differ from the hierarchy being updated";
     return FMM_ERR_STATE;
   }
@@ -288,61 +334,32 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
       CKS(cudaMemcpyAsync(T.mass.ptr, mass[l - lo], nl * 8, cudaMemcpyDefault, st));
     }
   }
-  fmm_status s = tree_build(c, st);
-  if (s != FMM_OK) return s;
-  s = size_expansions(c);
-  if (s != FMM_OK) return s;
-  s = zero_expansions(c, st);
-  if (s != FMM_OK) return s;
-  CKS(cudaStreamSynchronize(st));
+  TRY(tree_prepare(c));
+  TRY(size_expansions(c));
+  if (c->use_graphs) {
+    TRY(launch_tree_graph(c, st));
+  } else {
+    TRY(tree_enqueue(c, st));
+  }
+  TRY(tree_finish(c, st));
+  {  // list lengths decide grid sizes: a change retires the cached solve graphs
+    std::vector<int64_t> sig = {c->lmin, c->lmax};
+    for (int l = 0; l <= c->lmax; ++l) {
+      const LevelTree& T = c->lev[l];
+      sig.insert(sig.end(), {T.n_oct, T.n_leaf, T.n_rows, T.n_tgt, T.n_rowsL, T.n_irows});
+    }
+    if (sig != c->count_sig) {
+      c->count_sig = std::move(sig);
+      ++c->layout_gen;
+    }
+  }
   c->have_levels = true;
   return FMM_OK;
 }
 
-fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, void* stream) {
-  if (!c || !phi || !accel) return FMM_ERR_ARG;
-  if (!c->have_levels) {
-    c->last_error = "fmm_solve before fmm_set_levels";
-    return FMM_ERR_STATE;
-  }
-  if (lo < c->lmin || lo > c->lmax) return FMM_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  c->last_stream = st;
-  ++c->n_solve;
+// The device work of one solve (no host synchronisation, no allocation).
+static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* dacc, cudaStream_t st) {
   const bool f64 = c->cfg.precision == FMM_FP64;
-  const int ob = c->cfg.out_fp32 ? 4 : 8;
-  // outputs: device pointers are written directly, host pointers go through staging
-  std::vector<void*> dphi(c->lmax + 1, nullptr), dacc(c->lmax + 1, nullptr);
-  std::vector<char> host_out(c->lmax + 1, 0);
-  size_t stage_bytes = 0;
-  for (int l = lo; l <= c->lmax; ++l) {
-    int64_t nl = c->lev[l].n_leaf;
-    if (!nl) continue;
-    if (!phi[l - lo] || !accel[l - lo]) return FMM_ERR_ARG;
-    host_out[l] = !(is_device_ptr(phi[l - lo]) && is_device_ptr(accel[l - lo]));
-    if (host_out[l]) stage_bytes += nl * 4 * ob + 256;
-  }
-  if (stage_bytes) {
-    if (c->out_stage.bytes < stage_bytes) {
-      // only host outputs ever allocate here; device outputs never do
-      CKS(buf_ensure(c, c->out_stage, stage_bytes));
-    }
-    size_t off = 0;
-    for (int l = lo; l <= c->lmax; ++l)
-      if (host_out[l]) {
-        int64_t nl = c->lev[l].n_leaf;
-        dphi[l] = (char*)c->out_stage.ptr + off;
-        off += (nl * ob + 255) / 256 * 256;
-        dacc[l] = (char*)c->out_stage.ptr + off;
-        off += (nl * 3 * ob + 255) / 256 * 256;
-      }
-  }
-  for (int l = lo; l <= c->lmax; ++l)
-    if (!host_out[l]) {
-      dphi[l] = phi[l - lo];
-      dacc[l] = accel[l - lo];
-    }
-
   stage_event(c, 0, st);
   // 1. upward: leaf monopoles, then M2M from the finest level up
   for (int l = 1; l <= c->lmax; ++l) launch_mono_leaves(c, l, st);
@@ -380,8 +397,105 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
   stage_event(c, 3, st);
   // 3b. near / nearest / far fields and the scatter, all target levels in one launch
   launch_near_m2p(c, lo, st);  // refined cells of the near field (interface octs only)
-  launch_near(c, lo, dphi.data() + lo, dacc.data() + lo, c->cfg.out_fp32, st);
+  launch_near(c, lo, dphi + lo, dacc + lo, c->cfg.out_fp32, st);
   stage_event(c, 4, st);
+  return FMM_OK;
+}
+
+// Replays the solve as a CUDA graph: captured once per (layout generation, lo,
+// output pointers) on the library's own stream, then launched on the caller's.
+static fmm_status launch_solve_graph(Ctx* c, int lo, void* const* dphi, void* const* dacc, cudaStream_t st) {
+  std::vector<uintptr_t> key = {(uintptr_t)c->layout_gen, (uintptr_t)lo};
+  for (int l = lo; l <= c->lmax; ++l) {
+    key.push_back((uintptr_t)dphi[l]);
+    key.push_back((uintptr_t)dacc[l]);
+  }
+  Ctx::SolveGraph* g = nullptr;
+  for (auto& e : c->graphs)
+    if (e.key == key) g = &e;
+  if (!g) {
+    // drop graphs of older layouts, and the oldest if the cache is full
+    for (size_t i = 0; i < c->graphs.size();)
+      if (c->graphs[i].key[0] != (uintptr_t)c->layout_gen || c->graphs.size() >= 8) {
+        cudaGraphExecDestroy(c->graphs[i].exec);
+        c->graphs.erase(c->graphs.begin() + i);
+      } else {
+        ++i;
+      }
+    if (!c->cap_stream) CKS(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const int64_t n0 = c->n_launch;
+    CKS(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    fmm_status s = enqueue_solve(c, lo, dphi, dacc, c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (s != FMM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    CKS(ee);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CKS(ei);
+    c->graphs.push_back({key, exec, c->n_launch - n0});
+    c->n_launch = n0;  // counted when launched
+    ++c->n_graph_build;
+    g = &c->graphs.back();
+  }
+  CKS(cudaGraphLaunch(g->exec, st));
+  c->n_launch += g->launches;
+  ++c->n_graph_launch;
+  return FMM_OK;
+}
+
+fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, void* stream) {
+  if (!c || !phi || !accel) return FMM_ERR_ARG;
+  if (!c->have_levels) {
+    c->last_error = "fmm_solve before fmm_set_levels";
+    return FMM_ERR_STATE;
+  }
+  if (lo < c->lmin || lo > c->lmax) return FMM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  ++c->n_solve;
+  const int ob = c->cfg.out_fp32 ? 4 : 8;
+  // outputs: device pointers are written directly, host pointers go through staging
+  std::vector<void*> dphi(c->lmax + 1, nullptr), dacc(c->lmax + 1, nullptr);
+  std::vector<char> host_out(c->lmax + 1, 0);
+  size_t stage_bytes = 0;
+  for (int l = lo; l <= c->lmax; ++l) {
+    int64_t nl = c->lev[l].n_leaf;
+    if (!nl) continue;
+    if (!phi[l - lo] || !accel[l - lo]) return FMM_ERR_ARG;
+    host_out[l] = !(is_device_ptr(phi[l - lo]) && is_device_ptr(accel[l - lo]));
+    if (host_out[l]) stage_bytes += nl * 4 * ob + 256;
+  }
+  if (stage_bytes) {
+    if (c->out_stage.bytes < stage_bytes) {
+      // only host outputs ever allocate here; device outputs never do
+      CKS(buf_ensure(c, c->out_stage, stage_bytes));
+    }
+    size_t off = 0;
+    for (int l = lo; l <= c->lmax; ++l)
+      if (host_out[l]) {
+        int64_t nl = c->lev[l].n_leaf;
+        dphi[l] = (char*)c->out_stage.ptr + off;
+        off += (nl * ob + 255) / 256 * 256;
+        dacc[l] = (char*)c->out_stage.ptr + off;
+        off += (nl * 3 * ob + 255) / 256 * 256;
+      }
+  }
+  for (int l = lo; l <= c->lmax; ++l)
+    if (!host_out[l]) {
+      dphi[l] = phi[l - lo];
+      dacc[l] = accel[l - lo];
+    }
+
+  if (c->timing || !c->use_graphs) {
+    TRY(enqueue_solve(c, lo, dphi.data(), dacc.data(), st));
+  } else {
+    TRY(launch_solve_graph(c, lo, dphi.data(), dacc.data(), st));
+  }
   CKS(cudaGetLastError());
   for (int l = lo; l <= c->lmax; ++l)
     if (host_out[l]) {
@@ -423,12 +537,15 @@ void fmm_destroy(fmm_ctx* c) {
       buf_free(c, *b);
   }
   for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_off8, &c->d_l2l_g,
-                    &c->d_l2l_e, &c->d_l2l_c, &c->d_m2m_c32, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
+                    &c->d_l2l_e, &c->d_l2l_c, &c->d_m2m_c32, &c->d_m2m_w0, &c->d_m2m_w0_32, &c->d_m2m_e0, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
                     &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->out_stage, &c->in_stage})
     buf_free(c, *b);
   if (c->d_err) cudaFree(c->d_err);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : c->tree_graphs) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   delete c;
@@ -506,6 +623,12 @@ fmm_status fmm_stats(const fmm_ctx* c, int64_t* out4) {
   out4[1] = c->n_cub;
   out4[2] = c->n_solve;
   out4[3] = c->n_set;
+  return FMM_OK;
+}
+
+fmm_status fmm_set_graphs(fmm_ctx* c, int on) {
+  if (!c) return FMM_ERR_ARG;
+  c->use_graphs = on != 0;
   return FMM_OK;
 }
 

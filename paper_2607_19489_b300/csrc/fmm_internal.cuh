@@ -13,7 +13,7 @@
 namespace fmm {
 
 constexpr int kMaxLevel = 20;
-constexpr int kTopLevelFP64 = 4;  // mixed precision: box levels <= 4 use FP64 M2M
+constexpr int kTopLevelFP64 = 3;  // mixed precision: box levels <= 3 use FP64 M2M
 
 // Error bits latched by kernels (atomicOr into DeviceState::err).
 enum : unsigned {
@@ -62,7 +62,8 @@ struct LevelTree {
   DevBuf ijk;            // int32 [n_leaf][3]
   DevBuf mass;           // double [n_leaf]
   // expansions (box units)
-  DevBuf M;              // [8 n_oct][nc] double (FP64 path / top levels) or float
+  DevBuf M;              // [8 n_oct][nc] double (FP64 path / top levels) or float; rows of
+                         // refined cells and of the leaves in interface octs (irows)
   DevBuf Mhi, Mlo;       // bf16 [8 n_oct][nc] (mixed path GEMM operands)
   DevBuf mono;           // [8 n_oct] total mass per cell (double or float)
   DevBuf L;              // double [8 n_oct][nc] local expansions (levels 2..lmax-2)
@@ -90,6 +91,7 @@ struct Ctx {
   LevelTree lev[kMaxLevel + 1];
   // device tables
   DevBuf d_m2m_off, d_m2m_g, d_m2m_e, d_m2m_c, d_m2m_c32;
+  DevBuf d_m2m_w0, d_m2m_w0_32, d_m2m_e0;  // per alpha: the gamma = 0 pair (leaf-only octs)
   DevBuf d_l2l_off, d_l2l_off8, d_l2l_g, d_l2l_e, d_l2l_c;
   DevBuf d_near64, d_near32, d_l2p64, d_l2p32;
   GemmOperand op_m2p, op_m2l;
@@ -108,11 +110,31 @@ struct Ctx {
   double stage_ms[4] = {0, 0, 0, 0};
   bool tables_on_device = false;
   int64_t n_launch = 0, n_cub = 0, n_solve = 0, n_set = 0;
+  // CUDA graphs of fmm_solve's device work, keyed by (layout generation, lo,
+  // output pointers).  The generation changes whenever a buffer is reallocated
+  // or the tree's list lengths change, so a cached graph never sees stale
+  // pointers or grid sizes.
+  struct SolveGraph {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;   // kernels of this library in the graph
+    int64_t cub_calls = 0;  // CUB primitives in the graph
+  };
+  std::vector<SolveGraph> graphs;
+  std::vector<SolveGraph> tree_graphs;  // tree build + clearing, keyed by layout and leaf counts
+  unsigned tree_host_err = 0;
+  uint64_t layout_gen = 1;
+  std::vector<int64_t> count_sig;
+  cudaStream_t cap_stream = nullptr;
+  bool use_graphs = true;
+  int64_t n_graph_launch = 0, n_graph_build = 0;
 };
 
 // ---- launchers (stream-ordered, no synchronisation) -----------------------
 // tree.cu
-fmm_status tree_build(Ctx* c, cudaStream_t st);
+fmm_status tree_prepare(Ctx* c);                 // oct counts, allocation (host)
+fmm_status tree_enqueue(Ctx* c, cudaStream_t st);  // device work, capturable
+fmm_status tree_finish(Ctx* c, cudaStream_t st);   // the one synchronisation
 // upward.cu
 void launch_mono_leaves(Ctx* c, int level, cudaStream_t st);
 void launch_upward(Ctx* c, int level, cudaStream_t st);

@@ -20,7 +20,6 @@
 // bits, every kernel bounds-checks the indices it follows, and one
 // synchronisation at the end reads the error word and the list lengths.
 #include <cub/cub.cuh>
-#include <thrust/iterator/counting_iterator.h>
 
 #include "fmm_internal.cuh"
 
@@ -164,52 +163,138 @@ __global__ void k_nbr(int level, int64_t n_oct, int64_t n_oct_up, const int32_t*
   }
 }
 
-// Per oct: does it hold a refined cell (f_rows) / a leaf (f_tgt), and which
-// of its cells are leaves (bit c of leafmask).
-__global__ void k_oct_kind_flags(int64_t n_oct, const int32_t* __restrict__ cell_child, int32_t* f_rows,
-                                 int32_t* f_tgt, uint8_t* leafmask) {
-  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
-  int r = 0, t = 0, m = 0;
+// ---- row lists of all levels in three launches -------------------------------
+// For every oct of every level four flags, all in gather form:
+//   rows  (bit 0): the oct holds a refined cell (its M2M output / M2P row);
+//   tgt   (bit 1): the oct holds a leaf (a target oct);
+//   rowsL (bit 2): a cell of the oct has grandchildren (it needs a local
+//                  expansion), levels 1..lmax-2;
+//   irows (bit 3): the oct holds a leaf and one of its 3^3 neighbour octs holds
+//                  a refined cell (near-field M2P / nearest field), levels
+//                  lmin..lmax.
+// Blocks of kListBlock octs never straddle levels; k_lists_count counts per
+// block, k_lists_scan turns the counts into per-level block offsets and list
+// lengths, k_lists_write compacts in ascending oct order.
+constexpr int kListBlock = 256;
+
+struct ListLevel {
+  int64_t n_oct, n_oct_next;
+  int64_t blk0;  // first block of this level
+  const int32_t* cell_child;
+  const int32_t* cell_child_next;  // level + 1, or null
+  const int32_t* nbr;
+  int32_t* out[4];  // rows, tgt, rowsL, irows
+  uint8_t* leafmask;
+  int want_rowsL, want_irows;
+};
+
+struct ListParams {
+  int nlev, level0, stride;
+  int64_t n_blocks;
+  ListLevel lev[kMaxLevel];
+};
+
+__device__ __forceinline__ int list_level(const ListParams& P, int64_t blk) {
+  int k = 0;
+  while (k + 1 < P.nlev && blk >= P.lev[k + 1].blk0) ++k;
+  return k;
+}
+
+__device__ __forceinline__ unsigned oct_list_flags(const ListLevel& L, int64_t o, uint8_t* leafmask_out) {
+  int refined = 0, leaf = 0, mask = 0, grand = 0;
   for (int c = 0; c < 8; ++c) {
-    int32_t ch = cell_child[o * 8 + c];
-    r |= ch >= 0;
-    t |= ch < 0;
-    m |= (ch < 0) << c;
+    const int32_t ch = L.cell_child[o * 8 + c];
+    refined |= ch >= 0;
+    leaf |= ch < 0;
+    mask |= (ch < 0) << c;
+    if (L.want_rowsL && ch >= 0 && ch < L.n_oct_next)
+      for (int cc = 0; cc < 8 && !grand; ++cc) grand |= L.cell_child_next[(int64_t)ch * 8 + cc] >= 0;
   }
-  f_rows[o] = r;
-  f_tgt[o] = t;
-  leafmask[o] = (uint8_t)m;
+  int near_ref = 0;
+  if (L.want_irows && leaf)
+    for (int q = 0; q < 27 && !near_ref; ++q) {
+      const int32_t nb = L.nbr[o * 27 + q];
+      if (nb < 0 || nb >= L.n_oct) continue;
+      for (int c = 0; c < 8; ++c) near_ref |= L.cell_child[(int64_t)nb * 8 + c] >= 0;
+    }
+  if (leafmask_out) *leafmask_out = (uint8_t)mask;
+  return (unsigned)refined | ((unsigned)leaf << 1) | ((unsigned)grand << 2) | ((unsigned)(leaf && near_ref) << 3);
 }
 
-// Marks the octs of level b that hold a cell with grandchildren: the parents of
-// the level b+1 octs that hold a refined cell.  One thread per level b+1 oct.
-__global__ void k_mark_rowsL(int64_t n_oct_next, const int32_t* __restrict__ cell_child_next,
-                             const int32_t* __restrict__ oct_parent_next, int64_t n_oct, int32_t* flags) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_oct_next) return;
-  bool ref = false;
-  for (int c = 0; c < 8; ++c) ref |= cell_child_next[i * 8 + c] >= 0;
-  if (!ref) return;
-  const int64_t o = oct_parent_next[i] >> 3;
-  if (o >= 0 && o < n_oct) flags[o] = 1;
+__global__ void __launch_bounds__(kListBlock) k_lists_count(const __grid_constant__ ListParams P, uint8_t* __restrict__ flags,
+                                                            int32_t* __restrict__ blk_counts) {
+  const int64_t blk = blockIdx.x;
+  const ListLevel& L = P.lev[list_level(P, blk)];
+  const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
+  unsigned f = 0;
+  if (o < L.n_oct) f = oct_list_flags(L, o, L.leafmask + o);
+  flags[blk * kListBlock + threadIdx.x] = (uint8_t)f;
+  for (int k = 0; k < 4; ++k) {
+    const int n = __syncthreads_count((f >> k) & 1);
+    if (threadIdx.x == 0) blk_counts[blk * 4 + k] = n;
+  }
 }
 
-// Marks the octs of a level that hold a leaf and have a refined cell in one of
-// their 3^3 neighbour octs (the near field then needs M2P or nearest-field
-// P2P).  One thread per oct.
-__global__ void k_mark_irows(int64_t n_oct, const int32_t* __restrict__ nbr, const int32_t* __restrict__ cell_child,
-                             int32_t* flags) {
-  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
-  bool leaf = false, ref = false;
-  for (int c = 0; c < 8; ++c) leaf |= cell_child[o * 8 + c] < 0;
-  for (int q = 0; q < 27 && leaf && !ref; ++q) {
-    const int32_t nb = nbr[o * 27 + q];
-    if (nb < 0 || nb >= n_oct) continue;
-    for (int c = 0; c < 8; ++c) ref |= cell_child[(int64_t)nb * 8 + c] >= 0;
+// One block: per level and list, an exclusive scan of the block counts.
+__global__ void __launch_bounds__(1024) k_lists_scan(const __grid_constant__ ListParams P, const int32_t* __restrict__ blk_counts,
+                                                     int32_t* __restrict__ blk_off, int32_t* __restrict__ counts) {
+  __shared__ int32_t warp_sum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int li = 0; li < P.nlev; ++li) {
+    const ListLevel& L = P.lev[li];
+    const int64_t nb = (L.n_oct + kListBlock - 1) / kListBlock;
+    for (int k = 0; k < 4; ++k) {
+      int32_t carry = 0;
+      for (int64_t base = 0; base < nb; base += 1024) {
+        const int64_t b = base + threadIdx.x;
+        const int32_t v = b < nb ? blk_counts[(L.blk0 + b) * 4 + k] : 0;
+        int32_t x = v;  // inclusive warp scan
+        for (int d = 1; d < 32; d <<= 1) {
+          const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+          if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+          int32_t w = warp_sum[lane];
+          for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+          }
+          warp_sum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const int32_t excl = x - v + (warp > 0 ? warp_sum[warp - 1] : 0);
+        if (b < nb) blk_off[(L.blk0 + b) * 4 + k] = carry + excl;
+        carry += warp_sum[31];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) counts[k * P.stride + P.level0 + li] = carry;
+    }
   }
-  flags[o] = leaf && ref;
+}
+
+__global__ void __launch_bounds__(kListBlock) k_lists_write(const __grid_constant__ ListParams P, const uint8_t* __restrict__ flags,
+                                                            const int32_t* __restrict__ blk_off) {
+  __shared__ int32_t warp_cnt[kListBlock / 32][4];
+  const int64_t blk = blockIdx.x;
+  const ListLevel& L = P.lev[list_level(P, blk)];
+  const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
+  const unsigned f = flags[blk * kListBlock + threadIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned ball[4];
+  for (int k = 0; k < 4; ++k) {
+    ball[k] = __ballot_sync(0xffffffffu, (f >> k) & 1);
+    if (lane == 0) warp_cnt[warp][k] = __popc(ball[k]);
+  }
+  __syncthreads();
+  if (o >= L.n_oct) return;
+  for (int k = 0; k < 4; ++k) {
+    if (!((f >> k) & 1)) continue;
+    int32_t pos = blk_off[blk * 4 + k] + __popc(ball[k] & ((1u << lane) - 1));
+    for (int w = 0; w < warp; ++w) pos += warp_cnt[w][k];
+    L.out[k][pos] = (int32_t)o;
+  }
 }
 
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
@@ -233,33 +318,15 @@ fmm_status err_to_status(unsigned e) {
   return FMM_OK;
 }
 
-// Stream compaction of the oct indices whose flag is set (CUB select).
-fmm_status select_flagged(Ctx* c, const int32_t* flags, int64_t n, int32_t* out, int32_t* d_count,
-                          cudaStream_t st) {
-  thrust::counting_iterator<int32_t> it(0);
-  size_t tmp = 0;
-  CK(cub::DeviceSelect::Flagged(nullptr, tmp, it, flags, out, d_count, (int)n, st));
-  CK(buf_ensure(c, c->sort_tmp, tmp));
-  ++c->n_cub;
-  CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, flags, out, d_count, (int)n, st));
-  return FMM_OK;
-}
-
-#define TRYT(x)                  \
-  do {                           \
-    fmm_status s_ = (x);         \
-    if (s_ != FMM_OK) return s_; \
-  } while (0)
-
 }  // namespace
 
-fmm_status tree_build(Ctx* c, cudaStream_t st) {
+fmm_status tree_prepare(Ctx* c) {
   const int lmin = c->lmin, lmax = c->lmax;
-  unsigned* err = c->d_err;
   // ---- oct counts from the leaf counts ----------------------------------------
   // An inconsistent count is latched, not returned at once: the device checks
   // below may name the cause (a duplicate, an out-of-box index) more precisely.
-  unsigned host_err = 0;
+  unsigned& host_err = c->tree_host_err;
+  host_err = 0;
   for (int l = lmax; l >= lmin; --l) {
     const int64_t n = c->lev[l].n_leaf + ((l < lmax) ? c->lev[l + 1].n_oct : 0);
     if (n == 0 || n > (int64_t)INT32_MAX / 2) {
@@ -296,9 +363,34 @@ fmm_status tree_build(Ctx* c, cudaStream_t st) {
   CK(buf_ensure(c, c->keys_b, nmax * 8));
   CK(buf_ensure(c, c->vals_a, nmax * 4));
   CK(buf_ensure(c, c->vals_b, nmax * 4));
-  CK(buf_ensure(c, c->flags, nmax * 8));
-  CK(buf_ensure(c, c->scan, nmax * 4));
+  int64_t list_blocks = 0;
+  for (int l = 1; l <= lmax; ++l) list_blocks += (c->lev[l].n_oct + kListBlock - 1) / kListBlock;
+  CK(buf_ensure(c, c->flags, std::max<int64_t>(nmax * 8, list_blocks * kListBlock)));
+  CK(buf_ensure(c, c->scan, std::max<int64_t>(nmax * 4, list_blocks * 32)));
   CK(buf_ensure(c, c->counter, 4 * 4 * (lmax + 2)));
+  // CUB temporary storage for the largest sort and scan of this hierarchy
+  size_t tmp_max = 0;
+  {
+    for (int l = lmin; l <= lmax; ++l) {
+      const int n = (int)(8 * c->lev[l].n_oct);
+      size_t t = 0;
+      CK(cub::DeviceRadixSort::SortPairs(nullptr, t, (uint64_t*)nullptr, (uint64_t*)nullptr, (int32_t*)nullptr,
+                                         (int32_t*)nullptr, n, 0, 3 * l));
+      tmp_max = std::max(tmp_max, t);
+      t = 0;
+      CK(cub::DeviceScan::InclusiveSum(nullptr, t, (int32_t*)nullptr, (int32_t*)nullptr, n));
+      tmp_max = std::max(tmp_max, t);
+    }
+  }
+  CK(buf_ensure(c, c->sort_tmp, tmp_max));
+  return FMM_OK;
+}
+
+// All device work of the tree build: stream-ordered, no allocation and no
+// synchronisation, so it can be captured in a CUDA graph.
+fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
+  const int lmin = c->lmin, lmax = c->lmax;
+  unsigned* err = c->d_err;
   int32_t* d_counts = (int32_t*)c->counter.ptr;  // [4][lmax+2]: rows, tgt, rowsL, irows
   CK(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   CK(cudaMemsetAsync(d_counts, 0, 4 * 4 * (lmax + 2), st));
@@ -321,18 +413,14 @@ fmm_status tree_build(Ctx* c, cudaStream_t st) {
       k_refined_keys<<<nblk(n_ref), 256, 0, st>>>(n_ref, (const uint64_t*)c->lev[l + 1].oct_key.ptr,
                                                   ka + T.n_leaf, va + T.n_leaf);
     }
-    size_t tmp = 0;
-    CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
-    CK(buf_ensure(c, c->sort_tmp, tmp));
+    size_t tmp = c->sort_tmp.bytes;
     ++c->n_cub;
     CK(cub::DeviceRadixSort::SortPairs(c->sort_tmp.ptr, tmp, ka, kb, va, vb, (int)n, 0, 3 * l, st));
     int32_t* flags = (int32_t*)c->flags.ptr;
     int32_t* scan = (int32_t*)c->scan.ptr;
     ++c->n_launch;
     k_oct_flags<<<nblk(n), 256, 0, st>>>(n, kb, flags, err);
-    tmp = 0;
-    CK(cub::DeviceScan::InclusiveSum(nullptr, tmp, flags, scan, (int)n, st));
-    CK(buf_ensure(c, c->sort_tmp, tmp));
+    tmp = c->sort_tmp.bytes;
     ++c->n_cub;
     CK(cub::DeviceScan::InclusiveSum(c->sort_tmp.ptr, tmp, flags, scan, (int)n, st));
     int32_t* par_next = (l < lmax) ? (int32_t*)c->lev[l + 1].oct_parent.ptr : nullptr;
@@ -363,38 +451,50 @@ fmm_status tree_build(Ctx* c, cudaStream_t st) {
                                               (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr, err);
   }
   // ---- row lists ------------------------------------------------------------
+  {
+    const int stride = lmax + 2;
+    ListParams P{};
+    P.nlev = lmax;
+    P.level0 = 1;
+    P.stride = stride;
+    int64_t nb = 0;
+    for (int l = 1; l <= lmax; ++l) {
+      LevelTree& T = c->lev[l];
+      ListLevel& L = P.lev[l - 1];
+      L.n_oct = T.n_oct;
+      L.n_oct_next = l < lmax ? c->lev[l + 1].n_oct : 0;
+      L.blk0 = nb;
+      L.cell_child = (const int32_t*)T.cell_child.ptr;
+      L.cell_child_next = l < lmax ? (const int32_t*)c->lev[l + 1].cell_child.ptr : nullptr;
+      L.nbr = (const int32_t*)T.nbr.ptr;
+      L.out[0] = (int32_t*)T.rows.ptr;
+      L.out[1] = (int32_t*)T.tgt.ptr;
+      L.out[2] = (int32_t*)T.rowsL.ptr;
+      L.out[3] = (int32_t*)T.irows.ptr;
+      L.leafmask = (uint8_t*)T.leafmask.ptr;
+      L.want_rowsL = l + 2 <= lmax;
+      L.want_irows = l >= lmin;
+      nb += (T.n_oct + kListBlock - 1) / kListBlock;
+    }
+    P.n_blocks = nb;
+    uint8_t* fl = (uint8_t*)c->flags.ptr;            // nb * kListBlock bytes
+    int32_t* blk_counts = (int32_t*)c->scan.ptr;     // nb * 4
+    int32_t* blk_off = blk_counts + nb * 4;          // nb * 4
+    c->n_launch += 3;
+    k_lists_count<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_counts);
+    k_lists_scan<<<1, 1024, 0, st>>>(P, blk_counts, blk_off, d_counts);
+    k_lists_write<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_off);
+  }
+  return FMM_OK;
+}
+
+// The one synchronisation of a tree build: error word and list lengths.
+fmm_status tree_finish(Ctx* c, cudaStream_t st) {
+  const int lmin = c->lmin, lmax = c->lmax;
   const int stride = lmax + 2;
-  for (int l = 1; l <= lmax; ++l) {  // octs with a refined cell / with a leaf, leaf masks
-    LevelTree& T = c->lev[l];
-    int32_t* fr = (int32_t*)c->flags.ptr;
-    int32_t* ft = fr + T.n_oct;
-    ++c->n_launch;
-    k_oct_kind_flags<<<nblk(T.n_oct), 256, 0, st>>>(T.n_oct, (const int32_t*)T.cell_child.ptr, fr, ft,
-                                                     (uint8_t*)T.leafmask.ptr);
-    TRYT(select_flagged(c, fr, T.n_oct, (int32_t*)T.rows.ptr, d_counts + 0 * stride + l, st));
-    TRYT(select_flagged(c, ft, T.n_oct, (int32_t*)T.tgt.ptr, d_counts + 1 * stride + l, st));
-  }
-  // octs that need a local expansion (cells with grandchildren), levels 1..lmax-2
-  for (int l = 1; l + 2 <= lmax; ++l) {
-    LevelTree& T = c->lev[l];
-    LevelTree& N = c->lev[l + 1];
-    int32_t* fl = (int32_t*)c->flags.ptr;
-    CK(cudaMemsetAsync(fl, 0, T.n_oct * 4, st));
-    ++c->n_launch;
-    k_mark_rowsL<<<nblk(N.n_oct), 256, 0, st>>>(N.n_oct, (const int32_t*)N.cell_child.ptr,
-                                                 (const int32_t*)N.oct_parent.ptr, T.n_oct, fl);
-    TRYT(select_flagged(c, fl, T.n_oct, (int32_t*)T.rowsL.ptr, d_counts + 2 * stride + l, st));
-  }
-  // target octs next to refined cells (near-field M2P / nearest field), levels lmin..lmax
-  for (int l = lmin; l <= lmax; ++l) {
-    LevelTree& T = c->lev[l];
-    int32_t* fl = (int32_t*)c->flags.ptr;
-    ++c->n_launch;
-    k_mark_irows<<<nblk(T.n_oct), 256, 0, st>>>(T.n_oct, (const int32_t*)T.nbr.ptr, (const int32_t*)T.cell_child.ptr,
-                                                fl);
-    TRYT(select_flagged(c, fl, T.n_oct, (int32_t*)T.irows.ptr, d_counts + 3 * stride + l, st));
-  }
-  // ---- the one synchronisation: error word and list lengths ------------------
+  int32_t* d_counts = (int32_t*)c->counter.ptr;
+  unsigned* err = c->d_err;
+  unsigned host_err = c->tree_host_err;
   std::vector<int32_t> counts(4 * stride, 0);
   CK(cudaMemcpyAsync(counts.data(), d_counts, 4 * 4 * stride, cudaMemcpyDeviceToHost, st));
   unsigned e = 0;

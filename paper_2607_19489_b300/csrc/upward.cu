@@ -2,10 +2,11 @@
 // of the downward pass (Eq. 4, Alg. 3).
 //
 // Expansions are kept in box units (tables.h).  A leaf cell's multipole is its
-// mass as a monopole (P2M of one point mass at the cell centre); its other
-// coefficients are zero and are cleared once per hierarchy, so each solve
-// writes one value per leaf.  A refined cell's multipole is the M2M sum of its
-// eight children.  Because the child offsets are (+-1/4)^3 of the parent box,
+// mass as a monopole (P2M of one point mass at the cell centre) with all other
+// coefficients zero.  It is kept as that one value ("mono"); a full coefficient
+// row is written only for the leaves that a contraction reads (those in the
+// interface octs, next to refined cells).  A refined cell's multipole is the M2M sum of its
+// eight children, read from their masses where they are leaves.  Because the child offsets are (+-1/4)^3 of the parent box,
 // M2M factors into a sign transform over the children,
 //     S_e[gamma] = sum_c sign(c, e) Mt_c[gamma],  e in {0,1}^3,
 // (a 3-stage butterfly, one stage per axis) followed by one short sum per
@@ -65,59 +66,121 @@ __device__ __forceinline__ void sign_transform_back(T x[8]) {
 }
 
 // Leaf cells of one level: monopole = mass.
-template <typename Tout, typename TMono>
-__global__ void k_leaf_mono(int64_t ncell, int nc, const int32_t* __restrict__ cell_child,
-                            const double* __restrict__ mass, Tout* __restrict__ M, __nv_bfloat16* __restrict__ hi,
-                            __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono) {
+template <typename TMono>
+__global__ void k_leaf_mono(int64_t ncell, const int32_t* __restrict__ cell_child, const double* __restrict__ mass,
+                            TMono* __restrict__ mono) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ncell) return;
   int32_t ch = cell_child[i];
   if (ch >= 0) return;
-  double m = mass[-1 - (int64_t)ch];
-  mono[i] = (TMono)m;
-  if (M) {
-    M[i * nc] = (Tout)m;
-    if (hi) split_bf16((Tout)m, hi[i * nc], lo[i * nc]);
+  mono[i] = (TMono)mass[-1 - (int64_t)ch];
+}
+
+// Coefficient rows of the leaf cells that a contraction can read: a leaf is a
+// source of M2L or M2P only when its oct lies in the 3^3 neighbourhood of an
+// oct with a refined cell, i.e. only in the interface octs (irows).  Those
+// rows get the monopole and explicit zeros; other leaf rows are never read and
+// never written.  One warp per interface oct.
+template <typename Tout>
+__global__ void __launch_bounds__(256) k_leaf_rows(int64_t n, int nc, const int32_t* __restrict__ irows,
+                                                   const int32_t* __restrict__ cell_child,
+                                                   const double* __restrict__ mass, Tout* __restrict__ M,
+                                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int64_t o = irows[w];
+  for (int c = 0; c < 8; ++c) {
+    const int32_t ch = cell_child[o * 8 + c];
+    if (ch >= 0) continue;
+    const Tout m = (Tout)mass[-1 - (int64_t)ch];
+    const int64_t row = (o * 8 + c) * nc;
+    for (int k = lane; k < nc; k += 32) {
+      const Tout v = k == 0 ? m : (Tout)0;
+      M[row + k] = v;
+      if (hi) split_bf16(v, hi[row + k], lo[row + k]);
+    }
   }
 }
 
-// M2M: one block per oct of level b+1, i.e. per refined cell of level b.
+// M2M: one warp per oct of level b+1, i.e. per refined cell of level b.
+// An oct whose eight cells are all leaves (the bulk of a refined region's
+// parent level) has point-mass children only: after the sign transform over
+// the children only gamma = 0 survives, so each output is one product
+// w0[alpha] * S[e0[alpha]] with S held in lanes 0..7.  Other octs stage the
+// children's coefficients in the warp's slice of shared memory, transform
+// them in place and run the short per-alpha sums.
+template <typename Tacc>
+struct M2MWarps {
+  static constexpr int kWarps = sizeof(Tacc) == 8 ? 4 : 8;  // 8 * kNcMax * kWarps * size <= 48 KB
+};
+
 template <typename Tin, typename Tacc, typename Tout, typename TMono>
-__global__ void __launch_bounds__(128) k_m2m(
-    int nc, const int32_t* __restrict__ oct_parent_next, const int32_t* __restrict__ cell_child_next,
-    const Tin* __restrict__ Mnext, const double* __restrict__ mass_next, Tout* __restrict__ Mout,
-    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono,
-    const int* __restrict__ poff, const int* __restrict__ pg, const int* __restrict__ pe,
-    const Tacc* __restrict__ pc) {
-  __shared__ Tacc Mc[8 * kNcMax];
-  __shared__ Tacc S[8 * kNcMax];
-  const int64_t o = blockIdx.x;
+__global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
+    int64_t n_oct_next, int nc, const int32_t* __restrict__ oct_parent_next,
+    const int32_t* __restrict__ cell_child_next, const Tin* __restrict__ Mnext,
+    const double* __restrict__ mass_next, Tout* __restrict__ Mout, __nv_bfloat16* __restrict__ hi,
+    __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono, const int* __restrict__ poff,
+    const int* __restrict__ pg, const int* __restrict__ pe, const Tacc* __restrict__ pc,
+    const Tacc* __restrict__ w0, const int* __restrict__ e0) {
+  constexpr int W = M2MWarps<Tacc>::kWarps;
+  __shared__ Tacc smem[W][8 * kNcMax];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t o = (int64_t)blockIdx.x * W + warp;
+  if (o >= n_oct_next) return;  // warp-uniform; no block-wide barrier below
   const int64_t cell = oct_parent_next[o];
   const int64_t c0 = o * 8;
-  for (int idx = threadIdx.x; idx < 8 * nc; idx += blockDim.x) {
-    int c = idx / nc, g = idx - c * nc;
-    int32_t cc = cell_child_next[c0 + c];
-    Tacc v;
-    if (cc < 0)
-      v = (g == 0) ? (Tacc)mass_next[-1 - (int64_t)cc] : (Tacc)0;
-    else
-      v = (Tacc)Mnext[(c0 + c) * nc + g];
-    Mc[c * nc + g] = v;
+  const int32_t cc = lane < 8 ? cell_child_next[c0 + lane] : -1;
+  const unsigned full = 0xffffffffu;
+  if (__all_sync(full, cc < 0)) {
+    Tacc m = lane < 8 ? (Tacc)mass_next[-1 - (int64_t)cc] : (Tacc)0;
+#pragma unroll
+    for (int axis = 0; axis < 3; ++axis) {  // S_e over lanes 0..7, as sign_transform
+      const Tacc other = __shfl_xor_sync(full, m, 1 << axis);
+      m = (lane & (1 << axis)) ? m - other : m + other;
+    }
+    for (int kb = 0; kb < nc; kb += 32) {
+      const int k = kb + lane;
+      const int e = k < nc ? e0[k] : 0;
+      const Tacc s = __shfl_sync(full, m, e);
+      if (k < nc) {
+        const Tout v = (Tout)(w0[k] * s);
+        Mout[cell * nc + k] = v;
+        if (hi) split_bf16(v, hi[cell * nc + k], lo[cell * nc + k]);
+        if (k == 0) mono[cell] = (TMono)v;
+      }
+    }
+    return;
   }
-  __syncthreads();
-  for (int g = threadIdx.x; g < nc; g += blockDim.x) {
+  Tacc* S = smem[warp];
+  for (int base = 0; base < 8 * nc; base += 32) {
+    const int idx = base + lane;
+    const int c = min(idx / nc, 7);
+    const int32_t ch = __shfl_sync(full, cc, c);
+    if (idx < 8 * nc) {
+      const int g = idx - c * nc;
+      Tacc v;
+      if (ch < 0)
+        v = (g == 0) ? (Tacc)mass_next[-1 - (int64_t)ch] : (Tacc)0;
+      else
+        v = (Tacc)Mnext[(c0 + c) * nc + g];
+      S[idx] = v;
+    }
+  }
+  __syncwarp();
+  for (int g = lane; g < nc; g += 32) {
     Tacc x[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) x[c] = Mc[c * nc + g];
+    for (int c = 0; c < 8; ++c) x[c] = S[c * nc + g];
     sign_transform(x);
 #pragma unroll
     for (int e = 0; e < 8; ++e) S[e * nc + g] = x[e];
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+  __syncwarp();
+  for (int k = lane; k < nc; k += 32) {
     Tacc out = 0;
     for (int j = poff[k]; j < poff[k + 1]; ++j) out += pc[j] * S[pe[j] * nc + pg[j]];
-    Tout v = (Tout)out;
+    const Tout v = (Tout)out;
     Mout[cell * nc + k] = v;
     if (hi) split_bf16(v, hi[cell * nc + k], lo[cell * nc + k]);
     if (k == 0) mono[cell] = (TMono)v;
@@ -164,21 +227,25 @@ void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {
   int64_t n = 8 * T.n_oct;
   if (!n || !T.n_leaf) return;
   unsigned g = (unsigned)((n + 255) / 256);
-  const int nc = c->tab.nc;
-  const bool f64 = c->cfg.precision == FMM_FP64;
-  __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
-  __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
   const int32_t* cc = (const int32_t*)T.cell_child.ptr;
   const double* mass = (const double*)T.mass.ptr;
+  const bool f64 = c->cfg.precision == FMM_FP64;
   ++c->n_launch;
   if (f64)
-    k_leaf_mono<double, double><<<g, 256, 0, st>>>(n, nc, cc, mass, l == c->lmax ? nullptr : (double*)T.M.ptr,
-                                                   hi, lo, (double*)T.mono.ptr);
-  else if (l == c->lmax || T.m_is_f64)
-    k_leaf_mono<double, float><<<g, 256, 0, st>>>(n, nc, cc, mass, l == c->lmax ? nullptr : (double*)T.M.ptr,
-                                                  hi, lo, (float*)T.mono.ptr);
+    k_leaf_mono<double><<<g, 256, 0, st>>>(n, cc, mass, (double*)T.mono.ptr);
   else
-    k_leaf_mono<float, float><<<g, 256, 0, st>>>(n, nc, cc, mass, (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr);
+    k_leaf_mono<float><<<g, 256, 0, st>>>(n, cc, mass, (float*)T.mono.ptr);
+  if (l == c->lmax || !T.n_irows) return;  // no coefficient rows at the finest level
+  const unsigned gr = (unsigned)((T.n_irows * 32 + 255) / 256);
+  const int32_t* ir = (const int32_t*)T.irows.ptr;
+  __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
+  __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
+  ++c->n_launch;
+  if (T.m_is_f64)
+    k_leaf_rows<double><<<gr, 256, 0, st>>>(T.n_irows, c->tab.nc, ir, cc, mass, (double*)T.M.ptr,
+                                            f64 ? nullptr : hi, f64 ? nullptr : lo);
+  else
+    k_leaf_rows<float><<<gr, 256, 0, st>>>(T.n_irows, c->tab.nc, ir, cc, mass, (float*)T.M.ptr, hi, lo);
 }
 
 void launch_upward(Ctx* c, int b, cudaStream_t st) {
@@ -191,30 +258,36 @@ void launch_upward(Ctx* c, int b, cudaStream_t st) {
   const int* pg = (const int*)c->d_m2m_g.ptr;
   const int* pe = (const int*)c->d_m2m_e.ptr;
   const double* pc = (const double*)c->d_m2m_c.ptr;
-  dim3 grid((unsigned)N.n_oct);
+  const double* w0 = (const double*)c->d_m2m_w0.ptr;
+  const int* e0 = (const int*)c->d_m2m_e0.ptr;
+  const int64_t n = N.n_oct;
   const int32_t* par = (const int32_t*)N.oct_parent.ptr;
   const int32_t* ccn = (const int32_t*)N.cell_child.ptr;
   const double* mn = (const double*)N.mass.ptr;
   __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
   __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
+  const unsigned g64 = (unsigned)((n + M2MWarps<double>::kWarps - 1) / M2MWarps<double>::kWarps);
+  const unsigned g32 = (unsigned)((n + M2MWarps<float>::kWarps - 1) / M2MWarps<float>::kWarps);
+  constexpr int t64 = 32 * M2MWarps<double>::kWarps, t32 = 32 * M2MWarps<float>::kWarps;
   ++c->n_launch;
   if (f64) {
-    k_m2m<double, double, double, double><<<grid, 128, 0, st>>>(nc, par, ccn, (const double*)N.M.ptr, mn,
-                                                                (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
-                                                                poff, pg, pe, pc);
+    k_m2m<double, double, double, double><<<g64, t64, 0, st>>>(n, nc, par, ccn, (const double*)N.M.ptr, mn,
+                                                               (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
+                                                               poff, pg, pe, pc, w0, e0);
   } else if (T.m_is_f64) {  // mixed path, top of the tree: FP64 shifts
     if (N.m_is_f64)
-      k_m2m<double, double, double, float><<<grid, 128, 0, st>>>(nc, par, ccn, (const double*)N.M.ptr, mn,
-                                                                 (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
-                                                                 poff, pg, pe, pc);
-    else
-      k_m2m<float, double, double, float><<<grid, 128, 0, st>>>(nc, par, ccn, (const float*)N.M.ptr, mn,
+      k_m2m<double, double, double, float><<<g64, t64, 0, st>>>(n, nc, par, ccn, (const double*)N.M.ptr, mn,
                                                                 (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
-                                                                poff, pg, pe, pc);
+                                                                poff, pg, pe, pc, w0, e0);
+    else
+      k_m2m<float, double, double, float><<<g64, t64, 0, st>>>(n, nc, par, ccn, (const float*)N.M.ptr, mn,
+                                                               (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
+                                                               poff, pg, pe, pc, w0, e0);
   } else {
-    k_m2m<float, float, float, float><<<grid, 128, 0, st>>>(nc, par, ccn, (const float*)N.M.ptr, mn,
-                                                            (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg,
-                                                            pe, (const float*)c->d_m2m_c32.ptr);
+    k_m2m<float, float, float, float><<<g32, t32, 0, st>>>(n, nc, par, ccn, (const float*)N.M.ptr, mn,
+                                                           (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg,
+                                                           pe, (const float*)c->d_m2m_c32.ptr,
+                                                           (const float*)c->d_m2m_w0_32.ptr, e0);
   }
 }
 

@@ -22,7 +22,7 @@ PRECISION = {"fp64": 0, "mixed": 1, "bf16x3": 1}
 
 EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_error", "fmm_destroy",
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
-            "fmm_set_timing", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static"]
+            "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static"]
 
 
 class FMMError(RuntimeError):
@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
     L.fmm_stats.argtypes = [P, P]
     L.fmm_solve_unigrid_static.argtypes = [P, I, I64, P, P, P, P, P]
     L.fmm_set_timing.argtypes = [P, I]
+    L.fmm_set_graphs.argtypes = [P, I]
     L.fmm_stage_times.argtypes = [P, P]
     for name in EXPORTED:
         fn = getattr(L, name)
@@ -199,6 +200,10 @@ class Solver:
 
     def set_timing(self, on: bool):
         self._check(lib().fmm_set_timing(self._h, int(on)), "fmm_set_timing")
+
+    def set_graphs(self, on: bool) -> None:
+        """Replay solves as CUDA graphs (default) or launch every kernel directly."""
+        self._check(lib().fmm_set_graphs(self._h, int(on)), "fmm_set_graphs")
 
     def stage_times(self):
         out = np.zeros(4)
