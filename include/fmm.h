@@ -103,6 +103,24 @@ fmm_status fmm_set_levels(fmm_ctx* ctx, int lmin, int lmax, int lo, const int64_
  * `stream`; the caller synchronises before reading them).  Asynchronous. */
 fmm_status fmm_solve(fmm_ctx* ctx, int lo, void* const* phi, void* const* accel, void* stream);
 
+/* Adjoint of fmm_solve (not in the paper: the exact transpose of its linear
+ * map from masses to outputs).  Given cotangents of the outputs of levels
+ * lo..lmax, writes the gradient of <g_phi, phi> + <g_accel, accel> with
+ * respect to the mass of every leaf of every level:
+ *   g_phi[k], g_accel[k]  level lo+k, [n][1] and [n][3] in the caller's input
+ *                         order, double or float per config.out_fp32
+ *   g_mass[k]             level lmin+k (all levels: far fields couple them),
+ *                         double [n]
+ * Device or host pointers.  The transposed chain runs in reverse (P2P^T,
+ * L2P^T, near-field M2P^T, M2P^T, M2L^T, L2L^T, M2M^T); the map is linear, so
+ * no forward state is kept or recomputed.  Needs an FMM_FP64 context
+ * (FMM_ERR_ARG otherwise).  The first call after fmm_set_levels builds the
+ * lists of source octs and synchronises `stream` once; the first call of a
+ * context builds the transposed operators (host work, about 130 MB of device
+ * memory at p = 6).  Asynchronous otherwise. */
+fmm_status fmm_solve_adjoint(fmm_ctx* ctx, int lo, const void* const* g_phi, const void* const* g_accel,
+                             double* const* g_mass, void* stream);
+
 /* Wait for all work of the context on its last stream and return any
  * latched device error (FMM_ERR_TIMEOUT from a bounded wait, FMM_ERR_CUDA). */
 fmm_status fmm_sync(fmm_ctx* ctx);

@@ -15,6 +15,9 @@
 #include <cmath>
 #include <cstring>
 
+#include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -213,6 +216,117 @@ bool is_device_ptr(const void* p) {
 
 void stage_event(Ctx* c, int i, cudaStream_t st) {
   if (c->timing) cudaEventRecord(c->ev[i], st);
+}
+
+// ---- adjoint preparation ------------------------------------------------------
+// Transposed pair lists of M2M (grouped by input gamma and sign pattern e) and
+// L2L (grouped by input gamma), and the contraction operators transposed per
+// neighbour offset: BT[qi][n][s*nc + alpha] = B[n][(qi*8 + s)*nc + alpha].
+fmm_status adjoint_tables(Ctx* c) {
+  if (c->adj_tables) return FMM_OK;
+  const Tables& t = c->tab;
+  const int nc = t.nc;
+  {
+    std::vector<std::vector<std::pair<int, double>>> by(nc * 8);
+    for (int a = 0; a < nc; ++a)
+      for (int j = t.m2m_off[a]; j < t.m2m_off[a + 1]; ++j) by[t.m2m_g[j] * 8 + t.m2m_e[j]].push_back({a, t.m2m_c[j]});
+    std::vector<int> off(1, 0), ia;
+    std::vector<double> cf;
+    for (auto& v : by) {
+      for (auto& pr : v) {
+        ia.push_back(pr.first);
+        cf.push_back(pr.second);
+      }
+      off.push_back((int)ia.size());
+    }
+    TRY(upload(c, c->d_m2mT_off, off));
+    TRY(upload(c, c->d_m2mT_a, ia));
+    TRY(upload(c, c->d_m2mT_c, cf));
+  }
+  {
+    struct E {
+      int b, e;
+      double c;
+    };
+    std::vector<std::vector<E>> by(nc);
+    for (int b = 0; b < nc; ++b)
+      for (int e = 0; e < 8; ++e)
+        for (int j = t.l2l_off8[b * 8 + e]; j < t.l2l_off8[b * 8 + e + 1]; ++j) by[t.l2l_g[j]].push_back({b, e, t.l2l_c[j]});
+    std::vector<int> off(1, 0), ib, ie;
+    std::vector<double> cf;
+    for (auto& v : by) {
+      for (auto& x : v) {
+        ib.push_back(x.b);
+        ie.push_back(x.e);
+        cf.push_back(x.c);
+      }
+      off.push_back((int)ib.size());
+    }
+    TRY(upload(c, c->d_l2lT_off, off));
+    TRY(upload(c, c->d_l2lT_b, ib));
+    TRY(upload(c, c->d_l2lT_e, ie));
+    TRY(upload(c, c->d_l2lT_c, cf));
+  }
+  const int KQ = 8 * nc, K = 26 * KQ;
+  Tables full;  // the context keeps no host copy of the contraction operators
+  full.build(c->cfg.p);
+  for (int w = 0; w < 2; ++w) {
+    const std::vector<double>& src = w == 0 ? full.m2p : full.m2l;
+    if (src.size() != (size_t)(w == 0 ? 256 : 8 * nc) * K) {
+      c->last_error = "adjoint: operator table has an unexpected size";
+      return FMM_ERR_ARG;
+    }
+    const int N = w == 0 ? 256 : 8 * nc;
+    std::vector<double> bt((size_t)26 * N * KQ);
+    for (int qi = 0; qi < 26; ++qi)
+      for (int n = 0; n < N; ++n)
+        std::memcpy(&bt[((size_t)qi * N + n) * KQ], &src[(size_t)n * K + (size_t)qi * KQ], KQ * sizeof(double));
+    TRY(upload(c, w == 0 ? c->d_m2pT : c->d_m2lT, bt));
+  }
+  c->adj_tables = true;
+  return FMM_OK;
+}
+
+// Per level the octs whose multipoles an M2P row (srcP) or an M2L row (srcL)
+// reads: the 26 neighbours of each row, compacted.  Built once per tree layout.
+fmm_status adjoint_lists(Ctx* c, cudaStream_t st) {
+  if (c->adj_gen == c->layout_gen) return FMM_OK;
+  const int lmax = c->lmax;
+  int64_t nmax = 1;
+  for (int l = 1; l <= lmax; ++l) nmax = std::max(nmax, c->lev[l].n_oct);
+  CKS(buf_ensure(c, c->flags, nmax * 4));
+  CKS(buf_ensure(c, c->counter, 8 * (lmax + 1)));
+  int32_t* flags = (int32_t*)c->flags.ptr;
+  int32_t* d_cnt = (int32_t*)c->counter.ptr;  // [lmax+1][2]
+  CKS(cudaMemsetAsync(d_cnt, 0, 8 * (lmax + 1), st));
+  thrust::counting_iterator<int32_t> it(0);
+  size_t tmp = 0;
+  CKS(cub::DeviceSelect::Flagged(nullptr, tmp, it, flags, (int32_t*)nullptr, d_cnt, (int)nmax, st));
+  CKS(buf_ensure(c, c->sort_tmp, tmp));
+  for (int b = 1; b <= lmax; ++b) {
+    LevelTree& B = c->lev[b];
+    CKS(buf_ensure(c, B.srcP, B.n_oct * 4));
+    CKS(buf_ensure(c, B.srcL, B.n_oct * 4));
+    for (int w = 0; w < 2; ++w) {
+      const bool m2p = w == 0;
+      const int64_t nr = m2p ? B.n_rows : B.n_rowsL;
+      if (!nr || (m2p ? b > lmax - 1 : (b < 2 || b > lmax - 2))) continue;
+      CKS(cudaMemsetAsync(flags, 0, B.n_oct * 4, st));
+      launch_adj_mark(c, (const int32_t*)(m2p ? B.rows.ptr : B.rowsL.ptr), nr, (const int32_t*)B.nbr.ptr, flags, st);
+      size_t tb = c->sort_tmp.bytes;
+      CKS(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tb, it, flags, (int32_t*)(m2p ? B.srcP.ptr : B.srcL.ptr),
+                                     d_cnt + 2 * b + w, (int)B.n_oct, st));
+    }
+  }
+  std::vector<int32_t> cnt(2 * (lmax + 1));
+  CKS(cudaMemcpyAsync(cnt.data(), d_cnt, 8 * (lmax + 1), cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+  for (int b = 1; b <= lmax; ++b) {
+    c->lev[b].n_srcP = cnt[2 * b];
+    c->lev[b].n_srcL = cnt[2 * b + 1];
+  }
+  c->adj_gen = c->layout_gen;
+  return FMM_OK;
 }
 
 }  // namespace
@@ -506,6 +620,72 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
   return FMM_OK;
 }
 
+fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const void* const* g_accel,
+                             double* const* g_mass, void* stream) {
+  if (!c || !g_phi || !g_accel || !g_mass) return FMM_ERR_ARG;
+  if (!c->have_levels) {
+    c->last_error = "fmm_solve_adjoint before fmm_set_levels";
+    return FMM_ERR_STATE;
+  }
+  if (c->cfg.precision != FMM_FP64) {
+    c->last_error = "fmm_solve_adjoint needs an FMM_FP64 context";
+    return FMM_ERR_ARG;
+  }
+  if (lo < c->lmin || lo > c->lmax) return FMM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  const int lmin = c->lmin, lmax = c->lmax;
+  const int ib = c->cfg.out_fp32 ? 4 : 8;
+  for (int l = lo; l <= lmax; ++l)
+    if (c->lev[l].n_leaf && (!g_phi[l - lo] || !g_accel[l - lo])) return FMM_ERR_ARG;
+  for (int l = lmin; l <= lmax; ++l)
+    if (c->lev[l].n_leaf && !g_mass[l - lmin]) return FMM_ERR_ARG;
+  for (int l = 1; l <= lmax; ++l)  // before the lists: an allocation here changes the layout generation
+    CKS(buf_ensure(c, c->lev[l].gmass, std::max<int64_t>(c->lev[l].n_leaf, 1) * 8));
+  TRY(adjoint_tables(c));
+  TRY(adjoint_lists(c, st));
+  // cotangent inputs: host arrays are staged on the device
+  std::vector<const void*> dphi(lmax + 1, nullptr), dacc(lmax + 1, nullptr);
+  size_t in_bytes = 0;
+  for (int l = lo; l <= lmax; ++l)
+    if (c->lev[l].n_leaf && !(is_device_ptr(g_phi[l - lo]) && is_device_ptr(g_accel[l - lo])))
+      in_bytes += (c->lev[l].n_leaf * 4 * ib + 255) / 256 * 256 + 256;
+  if (in_bytes) CKS(buf_ensure(c, c->in_stage, in_bytes));
+  size_t off = 0;
+  for (int l = lo; l <= lmax; ++l) {
+    const int64_t nl = c->lev[l].n_leaf;
+    if (!nl) continue;
+    if (is_device_ptr(g_phi[l - lo]) && is_device_ptr(g_accel[l - lo])) {
+      dphi[l] = g_phi[l - lo];
+      dacc[l] = g_accel[l - lo];
+      continue;
+    }
+    char* p = (char*)c->in_stage.ptr + off;
+    CKS(cudaMemcpyAsync(p, g_phi[l - lo], nl * ib, cudaMemcpyDefault, st));
+    dphi[l] = p;
+    off += (nl * ib + 255) / 256 * 256;
+    p = (char*)c->in_stage.ptr + off;
+    CKS(cudaMemcpyAsync(p, g_accel[l - lo], nl * 3 * ib, cudaMemcpyDefault, st));
+    dacc[l] = p;
+    off += (nl * 3 * ib + 255) / 256 * 256;
+  }
+  // cotangent buffers: the FP64 expansion arrays and one mass array per level
+  for (int l = 1; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    if (T.n_leaf) CKS(cudaMemsetAsync(T.gmass.ptr, 0, T.n_leaf * 8, st));
+    if (l < lmax) CKS(cudaMemsetAsync(T.M.ptr, 0, 8 * T.n_oct * c->tab.nc * 8, st));
+    if (l >= 2 && l <= lmax - 2) CKS(cudaMemsetAsync(T.L.ptr, 0, 8 * T.n_oct * c->tab.nc * 8, st));
+    if (l >= lmin) CKS(cudaMemsetAsync(T.acc.ptr, 0, 8 * T.n_oct * 4 * 8, st));
+  }
+  launch_adjoint(c, lo, dphi.data() + lo, dacc.data() + lo, c->cfg.out_fp32, st);
+  CKS(cudaGetLastError());
+  for (int l = lmin; l <= lmax; ++l) {
+    const int64_t nl = c->lev[l].n_leaf;
+    if (nl) CKS(cudaMemcpyAsync(g_mass[l - lmin], c->lev[l].gmass.ptr, nl * 8, cudaMemcpyDefault, st));
+  }
+  return FMM_OK;
+}
+
 fmm_status fmm_sync(fmm_ctx* c) {
   if (!c) return FMM_ERR_ARG;
   CKS(cudaStreamSynchronize(c->last_stream));
@@ -532,12 +712,14 @@ void fmm_destroy(fmm_ctx* c) {
   if (!c) return;
   if (c->last_stream) cudaStreamSynchronize(c->last_stream);
   for (auto& T : c->lev) {
-    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.tgt, &T.ijk,
+    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.tgt, &T.ijk,
                       &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lm, &T.acc})
       buf_free(c, *b);
   }
   for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_off8, &c->d_l2l_g,
-                    &c->d_l2l_e, &c->d_l2l_c, &c->d_m2m_c32, &c->d_m2m_w0, &c->d_m2m_w0_32, &c->d_m2m_e0, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
+                    &c->d_l2l_e, &c->d_l2l_c, &c->d_m2m_c32, &c->d_m2m_w0, &c->d_m2m_w0_32, &c->d_m2m_e0,
+                    &c->d_m2mT_off, &c->d_m2mT_a, &c->d_m2mT_c, &c->d_l2lT_off, &c->d_l2lT_b, &c->d_l2lT_e,
+                    &c->d_l2lT_c, &c->d_m2pT, &c->d_m2lT, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
                     &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->out_stage, &c->in_stage})

@@ -58,6 +58,10 @@ struct LevelTree {
   DevBuf rowsL;          // int32 [n_rowsL]
   DevBuf irows;          // int32 [n_irows]
   DevBuf leafmask;       // uint8 [n_oct]: bit c set when cell c of the oct is a leaf
+  // adjoint (FP64): mass cotangents and the octs read by the contractions
+  DevBuf gmass;          // double [n_leaf]
+  DevBuf srcP, srcL;     // int32: octs read by M2P rows / by M2L rows of this level
+  int64_t n_srcP = 0, n_srcL = 0;
   // inputs kept for adaptive time stepping (replaced by set_levels)
   DevBuf ijk;            // int32 [n_leaf][3]
   DevBuf mass;           // double [n_leaf]
@@ -121,7 +125,12 @@ struct Ctx {
     int64_t cub_calls = 0;  // CUB primitives in the graph
   };
   std::vector<SolveGraph> graphs;
-  std::vector<SolveGraph> tree_graphs;  // tree build + clearing, keyed by layout and leaf counts
+  std::vector<SolveGraph> tree_graphs;
+  // adjoint: transposed pair lists and operators (built on first use), and the
+  // layout generation the source lists were built for
+  DevBuf d_m2mT_off, d_m2mT_a, d_m2mT_c, d_l2lT_off, d_l2lT_b, d_l2lT_e, d_l2lT_c, d_m2pT, d_m2lT;
+  bool adj_tables = false;
+  uint64_t adj_gen = 0;  // tree build + clearing, keyed by layout and leaf counts
   unsigned tree_host_err = 0;
   uint64_t layout_gen = 1;
   std::vector<int64_t> count_sig;
@@ -148,6 +157,12 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* row_leve
 fmm_status near_init(Ctx* c);
 void launch_near_m2p(Ctx* c, int lo, cudaStream_t st);
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st);
+
+// adjoint.cu
+void launch_adj_mark(Ctx* c, const int32_t* rows, int64_t nrows, const int32_t* nbr, int32_t* flags,
+                     cudaStream_t st);
+void launch_adjoint(Ctx* c, int lo, const void* const* g_phi, const void* const* g_accel, int in_fp32,
+                    cudaStream_t st);
 
 enum { kModeM2P = 0, kModeM2L = 1 };
 

@@ -22,7 +22,8 @@ PRECISION = {"fp64": 0, "mixed": 1, "bf16x3": 1}
 
 EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_error", "fmm_destroy",
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
-            "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static"]
+            "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static",
+            "fmm_solve_adjoint"]
 
 
 class FMMError(RuntimeError):
@@ -65,6 +66,7 @@ def lib() -> ctypes.CDLL:
     L.fmm_solve_unigrid_static.argtypes = [P, I, I64, P, P, P, P, P]
     L.fmm_set_timing.argtypes = [P, I]
     L.fmm_set_graphs.argtypes = [P, I]
+    L.fmm_solve_adjoint.argtypes = [P, I, P, P, P, P]
     L.fmm_stage_times.argtypes = [P, P]
     for name in EXPORTED:
         fn = getattr(L, name)
@@ -194,6 +196,29 @@ class Solver:
         rc = lib().fmm_solve(self._h, lo, pp, pa, _stream_ptr(stream))
         self._check(rc, "fmm_solve")
         return phi, acc
+
+    def solve_adjoint(self, g_phi: dict, g_acc: dict, lo: int | None = None, out=None, stream=None):
+        """Gradient of <g_phi, phi> + <g_acc, acc> of solve(lo) with respect to the mass of
+        every leaf: dict level -> float64 tensor, levels lmin..lmax (FP64 solvers only).
+        g_phi / g_acc are dicts level -> tensor for levels lo..lmax, in the output dtype."""
+        if self.lmin is None:
+            empty = _ptrs([])
+            self._check(lib().fmm_solve_adjoint(self._h, 0 if lo is None else lo, empty, empty, empty,
+                                                _stream_ptr(stream)), "fmm_solve_adjoint")
+        import torch
+        lo = self.lmin if lo is None else lo
+        levels = range(lo, self.lmax + 1)
+        if out is None:
+            dev = next(iter(g_phi.values())).device if g_phi else "cuda"
+            out = {l: torch.empty(self.n[l], dtype=torch.float64, device=dev) for l in range(self.lmin, self.lmax + 1)}
+        keep = [g_phi[l] for l in levels] + [g_acc[l] for l in levels]
+        pp = _ptrs([_data_ptr(g_phi[l]) for l in levels])
+        pa = _ptrs([_data_ptr(g_acc[l]) for l in levels])
+        pm = _ptrs([_data_ptr(out[l]) for l in range(self.lmin, self.lmax + 1)])
+        rc = lib().fmm_solve_adjoint(self._h, lo, pp, pa, pm, _stream_ptr(stream))
+        del keep
+        self._check(rc, "fmm_solve_adjoint")
+        return out
 
     def sync(self):
         self._check(lib().fmm_sync(self._h), "fmm_sync")
