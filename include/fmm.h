@@ -103,6 +103,34 @@ fmm_status fmm_set_levels(fmm_ctx* ctx, int lmin, int lmax, int lo, const int64_
  * `stream`; the caller synchronises before reading them).  Asynchronous. */
 fmm_status fmm_solve(fmm_ctx* ctx, int lo, void* const* phi, void* const* accel, void* stream);
 
+/* Solves many independent hierarchies (one context each, same device) in one
+ * CUDA graph launch: the contexts' solves are branches of one graph, so small
+ * hierarchies run side by side.  The paper has no counterpart (it solves one
+ * hierarchy per MPI domain).
+ *   ctxs[i]     distinct contexts with a hierarchy set
+ *   lo[i]       first solved level of context i (as fmm_solve)
+ *   phi[i][k], accel[i][k]  DEVICE outputs of level lo[i]+k of context i
+ * The graph is captured on the first call for a given set of contexts,
+ * layouts, levels and output pointers (a few are cached) and launched on
+ * `stream`; later calls with the same arguments only launch it.
+ * Asynchronous; errors as fmm_solve (FMM_ERR_ARG for host outputs). */
+fmm_status fmm_batch_solve(fmm_ctx* const* ctxs, int nctx, const int* lo, void* const* const* phi,
+                           void* const* const* accel, void* stream);
+
+/* Autotuner: times the candidate launch shapes of the context's kernels on its
+ * current hierarchy (solves of levels lo..lmax into scratch outputs) and keeps
+ * the fastest: the split-K factor of the tcgen05 M2P and M2L contractions
+ * (mixed precision) and the target octs per block of the near-field kernel.
+ * Synchronises `stream`.  The choices stay with the context (also for later
+ * hierarchies) and are read back with fmm_get_tuning: out3 = {split M2P,
+ * split M2L (0 = built-in heuristic), near-field octs per block}. */
+fmm_status fmm_autotune(fmm_ctx* ctx, int lo, void* stream);
+fmm_status fmm_get_tuning(const fmm_ctx* ctx, int* out3);
+/* Sets the same three values (for instance one autotuned context's choices on
+ * the other contexts of a batch).  Unsupported octs-per-block values fall back
+ * to the built-in choice. */
+fmm_status fmm_set_tuning(fmm_ctx* ctx, const int* in3);
+
 /* Adjoint of fmm_solve (not in the paper: the exact transpose of its linear
  * map from masses to outputs).  Given cotangents of the outputs of levels
  * lo..lmax, writes the gradient of <g_phi, phi> + <g_accel, accel> with

@@ -14,6 +14,9 @@
 //      scatter to the caller's order.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cub/cub.cuh>
 #include <thrust/iterator/counting_iterator.h>
@@ -329,6 +332,104 @@ fmm_status adjoint_lists(Ctx* c, cudaStream_t st) {
   return FMM_OK;
 }
 
+// ---- translation tables shared between contexts ---------------------------------
+// The tables depend only on (device, p, precision) and are read-only once
+// built, so every context of the same kind uses one device copy (a batch of 64
+// hierarchies would otherwise hold 64 copies of the ~65 MB contraction
+// operators).  Reference-counted; the last context frees them.
+DevBuf Ctx::*const kTableBufs[] = {
+    &Ctx::d_m2m_off, &Ctx::d_m2m_g,   &Ctx::d_m2m_e,    &Ctx::d_m2m_c,  &Ctx::d_m2m_c32, &Ctx::d_m2m_w0,
+    &Ctx::d_m2m_w0_32, &Ctx::d_m2m_e0, &Ctx::d_l2l_off, &Ctx::d_l2l_off8, &Ctx::d_l2l_g, &Ctx::d_l2l_e,
+    &Ctx::d_l2l_c,   &Ctx::d_near64,  &Ctx::d_near32,   &Ctx::d_l2p64,  &Ctx::d_l2p32};
+constexpr int kNumTableBufs = sizeof(kTableBufs) / sizeof(kTableBufs[0]);
+
+struct TableSet {
+  int refs = 0;
+  Tables tab;
+  DevBuf bufs[kNumTableBufs];
+  GemmOperand op_m2p, op_m2l;
+};
+using TableKey = std::tuple<int, int, int>;
+std::mutex g_tables_mu;
+std::map<TableKey, TableSet*> g_tables;
+
+TableKey table_key(const Ctx* c) { return TableKey(c->device, c->cfg.p, c->cfg.precision); }
+
+fmm_status acquire_tables(Ctx* c) {
+  std::lock_guard<std::mutex> lock(g_tables_mu);
+  auto it = g_tables.find(table_key(c));
+  if (it != g_tables.end()) {
+    TableSet* ts = it->second;
+    ++ts->refs;
+    c->tab = ts->tab;
+    for (int i = 0; i < kNumTableBufs; ++i) c->*kTableBufs[i] = ts->bufs[i];
+    c->op_m2p = ts->op_m2p;
+    c->op_m2l = ts->op_m2l;
+    c->tables_on_device = true;
+    c->tables_shared = true;
+    return FMM_OK;
+  }
+  TRY(init_tables(c));
+  TableSet* ts = new TableSet();
+  ts->refs = 1;
+  ts->tab = c->tab;
+  for (int i = 0; i < kNumTableBufs; ++i) ts->bufs[i] = c->*kTableBufs[i];
+  ts->op_m2p = c->op_m2p;
+  ts->op_m2l = c->op_m2l;
+  g_tables[table_key(c)] = ts;
+  c->tables_shared = true;
+  return FMM_OK;
+}
+
+// Drops this context's reference; when others remain, clears its copies of
+// the shared buffers so that destroying it leaves them alone.
+void release_tables(Ctx* c) {
+  if (!c->tables_shared) return;
+  std::lock_guard<std::mutex> lock(g_tables_mu);
+  auto it = g_tables.find(table_key(c));
+  if (it == g_tables.end()) return;
+  TableSet* ts = it->second;
+  if (--ts->refs > 0) {
+    for (int i = 0; i < kNumTableBufs; ++i) c->*kTableBufs[i] = DevBuf();
+    for (GemmOperand* op : {&c->op_m2p, &c->op_m2l}) op->f64 = op->hi = op->lo = op->klimit = DevBuf();
+  } else {
+    g_tables.erase(it);
+    delete ts;  // this context frees the buffers
+  }
+  c->tables_shared = false;
+}
+
+// ---- batched solves -------------------------------------------------------------
+// One CUDA graph for the solves of many contexts: each context's work is a
+// branch of its own (forked from the capture stream, spread over a few
+// streams), so small hierarchies run side by side.  Cached by the contexts,
+// their layout generations, lo and the output pointers.
+struct BatchGraph {
+  std::vector<uintptr_t> key;
+  std::vector<Ctx*> ctxs;
+  std::vector<int64_t> launches;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch;
+constexpr int kBatchBranches = 8;
+cudaStream_t g_batch_streams[kBatchBranches + 1] = {};
+int g_batch_dev = -1;
+
+void drop_batch_graphs_of(Ctx* c) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (size_t i = 0; i < g_batch.size();) {
+    bool has = false;
+    for (Ctx* x : g_batch[i].ctxs) has |= x == c;
+    if (has) {
+      cudaGraphExecDestroy(g_batch[i].exec);
+      g_batch.erase(g_batch.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
 }  // namespace
 }  // namespace fmm
 
@@ -363,7 +464,7 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
   cudaMemset(c->d_err, 0, 16);
   for (auto& ev : c->ev) cudaEventCreate(&ev);
   fmm_status s = near_init(c);
-  if (s == FMM_OK) s = init_tables(c);
+  if (s == FMM_OK) s = acquire_tables(c);
   if (s != FMM_OK) {
     fmm_destroy(c);
     return s;
@@ -425,7 +526,7 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
       c->last_error = "first fmm_set_levels must give the whole hierarchy (lo == lmin)";
       return FMM_ERR_STATE;
     }
-  } else if (lo > lmin && (lmin != c->lmin || lmax != c->lmax)) {
+  } else if (lo > lmin && (lmin != c->lmin || lmax != c->lmax_user)) {
     c->last_error = "fmm_set_levels: lmin/lmax differ from the hierarchy being updated";
     return FMM_ERR_STATE;
   }
@@ -447,6 +548,15 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
       CKS(cudaMemcpyAsync(T.ijk.ptr, ijk[l - lo], nl * 12, cudaMemcpyDefault, st));
       CKS(cudaMemcpyAsync(T.mass.ptr, mass[l - lo], nl * 8, cudaMemcpyDefault, st));
     }
+  }
+  // trailing empty levels: the tree ends at the finest level that holds leaves
+  int eff = lmax;
+  while (eff > lmin && c->lev[eff].n_leaf == 0) --eff;
+  c->lmax = eff;
+  c->lmax_user = lmax;
+  for (int l = eff + 1; l <= lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    T.n_oct = T.n_rows = T.n_tgt = T.n_rowsL = T.n_irows = T.n_srcP = T.n_srcL = 0;
   }
   TRY(tree_prepare(c));
   TRY(size_expansions(c));
@@ -473,6 +583,7 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
 
 // The device work of one solve (no host synchronisation, no allocation).
 static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* dacc, cudaStream_t st) {
+  if (lo > c->lmax) return FMM_OK;  // only empty levels
   const bool f64 = c->cfg.precision == FMM_FP64;
   stage_event(c, 0, st);
   // 1. upward: leaf monopoles, then M2M from the finest level up
@@ -568,10 +679,11 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
     c->last_error = "fmm_solve before fmm_set_levels";
     return FMM_ERR_STATE;
   }
-  if (lo < c->lmin || lo > c->lmax) return FMM_ERR_ARG;
+  if (lo < c->lmin || lo > c->lmax_user) return FMM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
   ++c->n_solve;
+  if (lo > c->lmax) return FMM_OK;  // only empty levels
   const int ob = c->cfg.out_fp32 ? 4 : 8;
   // outputs: device pointers are written directly, host pointers go through staging
   std::vector<void*> dphi(c->lmax + 1, nullptr), dacc(c->lmax + 1, nullptr);
@@ -620,6 +732,221 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
   return FMM_OK;
 }
 
+fmm_status fmm_batch_solve(fmm_ctx* const* ctxs, int nctx, const int* lo, void* const* const* phi,
+                           void* const* const* accel, void* stream) {
+  if (!ctxs || nctx < 0 || (nctx && (!lo || !phi || !accel))) return FMM_ERR_ARG;
+  if (!nctx) return FMM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = -1;
+  std::vector<uintptr_t> key = {(uintptr_t)nctx};
+  std::vector<std::vector<void*>> dphi(nctx), dacc(nctx);
+  for (int i = 0; i < nctx; ++i) {
+    Ctx* c = ctxs[i];
+    if (!c || !phi[i] || !accel[i]) return FMM_ERR_ARG;
+    if (!c->have_levels) {
+      c->last_error = "fmm_batch_solve before fmm_set_levels";
+      return FMM_ERR_STATE;
+    }
+    if (lo[i] < c->lmin || lo[i] > c->lmax_user) return FMM_ERR_ARG;
+    if (dev < 0) dev = c->device;
+    if (c->device != dev) {
+      c->last_error = "fmm_batch_solve: contexts on different devices";
+      return FMM_ERR_ARG;
+    }
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) {
+        c->last_error = "fmm_batch_solve: a context appears twice";
+        return FMM_ERR_ARG;
+      }
+    dphi[i].assign(std::max(c->lmax, lo[i]) + 1, nullptr);
+    dacc[i].assign(std::max(c->lmax, lo[i]) + 1, nullptr);
+    key.insert(key.end(), {(uintptr_t)c, (uintptr_t)c->layout_gen, (uintptr_t)lo[i]});
+    for (int l = lo[i]; l <= c->lmax; ++l) {
+      if (!c->lev[l].n_leaf) continue;
+      void* pp = phi[i][l - lo[i]];
+      void* pa = accel[i][l - lo[i]];
+      if (!is_device_ptr(pp) || !is_device_ptr(pa)) {
+        c->last_error = "fmm_batch_solve takes device outputs only";
+        return FMM_ERR_ARG;
+      }
+      dphi[i][l] = pp;
+      dacc[i][l] = pa;
+      key.push_back((uintptr_t)pp);
+      key.push_back((uintptr_t)pa);
+    }
+  }
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BatchGraph* g = nullptr;
+  for (auto& b : g_batch)
+    if (b.key == key) g = &b;
+  if (!g) {
+    Ctx* c0 = ctxs[0];
+    Ctx* c = c0;  // error text goes to the first context
+    if (g_batch_dev != dev) {
+      for (auto& x : g_batch_streams)
+        if (!x) CKS(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+      g_batch_dev = dev;
+    }
+    while (g_batch.size() >= 4) {
+      cudaGraphExecDestroy(g_batch.front().exec);
+      g_batch.erase(g_batch.begin());
+    }
+    cudaStream_t cap = g_batch_streams[0];
+    std::vector<cudaEvent_t> evs(kBatchBranches + 1, nullptr);
+    for (auto& e : evs) CKS(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    BatchGraph b;
+    b.key = key;
+    fmm_status s = FMM_OK;
+    cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) ce = cudaEventRecord(evs[0], cap);
+    const int nbr = std::min(nctx, kBatchBranches);
+    for (int j = 0; j < nbr && ce == cudaSuccess; ++j) ce = cudaStreamWaitEvent(g_batch_streams[1 + j], evs[0], 0);
+    for (int i = 0; i < nctx && ce == cudaSuccess && s == FMM_OK; ++i) {
+      Ctx* c = ctxs[i];
+      const bool timing = c->timing;
+      c->timing = false;
+      const int64_t n0 = c->n_launch;
+      s = enqueue_solve(c, lo[i], dphi[i].data(), dacc[i].data(), g_batch_streams[1 + i % kBatchBranches]);
+      b.ctxs.push_back(c);
+      b.launches.push_back(c->n_launch - n0);
+      c->n_launch = n0;
+      c->timing = timing;
+    }
+    for (int j = 0; j < nbr && ce == cudaSuccess; ++j) {
+      ce = cudaEventRecord(evs[1 + j], g_batch_streams[1 + j]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, evs[1 + j], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+    for (auto& e : evs) cudaEventDestroy(e);
+    if (s != FMM_OK || ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (s == FMM_OK) {
+        c0->last_error = std::string("fmm_batch_solve capture: ") +
+                         cudaGetErrorString(ce != cudaSuccess ? ce : ee);
+        s = FMM_ERR_CUDA;
+      }
+      return s;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&b.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      c0->last_error = std::string("fmm_batch_solve instantiate: ") + cudaGetErrorString(ei);
+      return FMM_ERR_CUDA;
+    }
+    g_batch.push_back(std::move(b));
+    g = &g_batch.back();
+  }
+  cudaError_t e = cudaGraphLaunch(g->exec, st);
+  if (e != cudaSuccess) {
+    ctxs[0]->last_error = std::string("fmm_batch_solve launch: ") + cudaGetErrorString(e);
+    return FMM_ERR_CUDA;
+  }
+  for (size_t i = 0; i < g->ctxs.size(); ++i) {
+    g->ctxs[i]->n_launch += g->launches[i];
+    ++g->ctxs[i]->n_solve;
+    g->ctxs[i]->last_stream = st;
+  }
+  return FMM_OK;
+}
+
+// Times the candidate launch shapes on the context's own hierarchy (direct
+// launches, CUDA events, best of 3 after a warm-up) and keeps the fastest:
+// split-K of the two tcgen05 contractions (mixed precision), then the
+// near-field octs per block.
+fmm_status fmm_autotune(fmm_ctx* c, int lo, void* stream) {
+  if (!c) return FMM_ERR_ARG;
+  if (!c->have_levels) {
+    c->last_error = "fmm_autotune before fmm_set_levels";
+    return FMM_ERR_STATE;
+  }
+  if (lo < c->lmin || lo > c->lmax_user) return FMM_ERR_ARG;
+  if (lo > c->lmax) return FMM_OK;  // nothing to time
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  const int ob = c->cfg.out_fp32 ? 4 : 8;
+  size_t bytes = 0;
+  for (int l = lo; l <= c->lmax; ++l) bytes += (c->lev[l].n_leaf * 4 * ob + 255) / 256 * 256 + 256;
+  CKS(buf_ensure(c, c->out_stage, bytes));
+  std::vector<void*> dphi(c->lmax + 1, nullptr), dacc(c->lmax + 1, nullptr);
+  size_t off = 0;
+  for (int l = lo; l <= c->lmax; ++l) {
+    const int64_t nl = c->lev[l].n_leaf;
+    dphi[l] = (char*)c->out_stage.ptr + off;
+    off += (nl * ob + 255) / 256 * 256;
+    dacc[l] = (char*)c->out_stage.ptr + off;
+    off += (nl * 3 * ob + 255) / 256 * 256;
+  }
+  const bool timing = c->timing;
+  c->timing = false;
+  cudaEvent_t e0, e1;
+  CKS(cudaEventCreate(&e0));
+  CKS(cudaEventCreate(&e1));
+  auto measure = [&](float& best) -> fmm_status {
+    best = 1e30f;
+    for (int r = 0; r < 4; ++r) {
+      CKS(cudaEventRecord(e0, st));
+      TRY(enqueue_solve(c, lo, dphi.data(), dacc.data(), st));
+      CKS(cudaEventRecord(e1, st));
+      CKS(cudaEventSynchronize(e1));
+      float ms = 0;
+      CKS(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) best = std::min(best, ms);  // the first run warms up
+    }
+    return FMM_OK;
+  };
+  const int64_t n0 = c->n_launch;
+  fmm_status s = FMM_OK;
+  auto tune = [&](int* knob, const std::vector<int>& cands) {
+    int best_v = *knob;
+    float best_t = 1e30f;
+    for (int v : cands) {
+      if (s != FMM_OK) return;
+      *knob = v;
+      float t;
+      s = measure(t);
+      if (s == FMM_OK && t < best_t * 0.98f) {  // keep the earlier (simpler) choice within 2%
+        best_t = t;
+        best_v = v;
+      }
+    }
+    *knob = best_v;
+  };
+  if (c->cfg.precision != FMM_FP64) {
+    const std::vector<int> splits = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24};
+    tune(&c->tune_split[0], splits);
+    tune(&c->tune_split[1], splits);
+    tune(&c->tune_opb, {16, 8, 4});
+  } else {
+    tune(&c->tune_opb, {8, 4});
+  }
+  c->n_launch = n0;  // tuning runs are not the caller's solves
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing = timing;
+  ++c->layout_gen;  // cached graphs carry the old launch shapes
+  if (s == FMM_OK) s = fmm_sync(c);
+  return s;
+}
+
+fmm_status fmm_set_tuning(fmm_ctx* c, const int* in3) {
+  if (!c || !in3 || in3[0] < 0 || in3[1] < 0 || in3[2] < 0) return FMM_ERR_ARG;
+  c->tune_split[0] = in3[0];
+  c->tune_split[1] = in3[1];
+  c->tune_opb = in3[2];
+  ++c->layout_gen;
+  return FMM_OK;
+}
+
+fmm_status fmm_get_tuning(const fmm_ctx* c, int* out3) {
+  if (!c || !out3) return FMM_ERR_ARG;
+  out3[0] = c->tune_split[0];
+  out3[1] = c->tune_split[1];
+  out3[2] = near_opb(c);
+  return FMM_OK;
+}
+
+
 fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const void* const* g_accel,
                              double* const* g_mass, void* stream) {
   if (!c || !g_phi || !g_accel || !g_mass) return FMM_ERR_ARG;
@@ -631,7 +958,7 @@ fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const
     c->last_error = "fmm_solve_adjoint needs an FMM_FP64 context";
     return FMM_ERR_ARG;
   }
-  if (lo < c->lmin || lo > c->lmax) return FMM_ERR_ARG;
+  if (lo < c->lmin || lo > c->lmax_user) return FMM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
   const int lmin = c->lmin, lmax = c->lmax;
@@ -711,6 +1038,8 @@ const char* fmm_last_error(const fmm_ctx* c) { return c ? c->last_error.c_str() 
 void fmm_destroy(fmm_ctx* c) {
   if (!c) return;
   if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  drop_batch_graphs_of(c);
+  release_tables(c);
   for (auto& T : c->lev) {
     for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.tgt, &T.ijk,
                       &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lm, &T.acc})
@@ -736,7 +1065,7 @@ void fmm_destroy(fmm_ctx* c) {
 fmm_status fmm_tree_counts(const fmm_ctx* c, int64_t* n_oct) {
   if (!c || !n_oct) return FMM_ERR_ARG;
   if (!c->have_levels) return FMM_ERR_STATE;
-  for (int l = 0; l <= c->lmax; ++l) n_oct[l] = (l == 0) ? 0 : c->lev[l].n_oct;
+  for (int l = 0; l <= c->lmax_user; ++l) n_oct[l] = (l == 0 || l > c->lmax) ? 0 : c->lev[l].n_oct;
   return FMM_OK;
 }
 
@@ -744,7 +1073,8 @@ fmm_status fmm_tree_export(const fmm_ctx* cc, int level, uint64_t* oct_key, int6
   fmm_ctx* c = const_cast<fmm_ctx*>(cc);
   if (!c || !oct_key || !status || !nbr) return FMM_ERR_ARG;
   if (!c->have_levels) return FMM_ERR_STATE;
-  if (level < 1 || level > c->lmax) return FMM_ERR_ARG;
+  if (level < 1 || level > c->lmax_user) return FMM_ERR_ARG;
+  if (level > c->lmax) return FMM_OK;  // an empty level: no octs
   const LevelTree& T = c->lev[level];
   int64_t no = T.n_oct;
   std::vector<int32_t> cc32(8 * no), nb32(27 * no);

@@ -90,7 +90,8 @@ struct GemmOperand {  // one operator for the GEMM kernels
 struct Ctx {
   fmm_config cfg{};
   Tables tab;
-  int lmin = -1, lmax = -1;
+  int lmin = -1, lmax = -1;  // lmax: the finest level that holds cells
+  int lmax_user = -1;        // the caller's lmax (levels above lmax are empty)
   bool have_levels = false;
   LevelTree lev[kMaxLevel + 1];
   // device tables
@@ -136,6 +137,11 @@ struct Ctx {
   std::vector<int64_t> count_sig;
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
+  // launch shapes picked by fmm_autotune (0: built-in choice)
+  int tune_split[2] = {0, 0};  // split-K of the tcgen05 contraction, [kModeM2P], [kModeM2L]
+  int tune_opb = 0;            // target octs per block of the near-field kernel
+  // translation tables shared with other contexts of the same device, p and precision
+  bool tables_shared = false;
   int64_t n_graph_launch = 0, n_graph_build = 0;
 };
 
@@ -157,6 +163,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* row_leve
 fmm_status near_init(Ctx* c);
 void launch_near_m2p(Ctx* c, int lo, cudaStream_t st);
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st);
+int near_opb(const Ctx* c);
 
 // adjoint.cu
 void launch_adj_mark(Ctx* c, const int32_t* rows, int64_t nrows, const int32_t* nbr, int32_t* flags,

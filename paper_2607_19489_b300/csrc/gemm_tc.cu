@@ -421,7 +421,8 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.KQ = op.kseg;
   P.Kvalid = op.K;
   P.nchunks = op.Kpad / BK;
-  const int split = choose_split(tiles * op.ntile, P.nchunks, c->num_sms);
+  const int tuned = c->tune_split[mode == kModeM2P ? 0 : 1];
+  const int split = tuned > 0 ? std::min(tuned, P.nchunks) : choose_split(tiles * op.ntile, P.nchunks, c->num_sms);
   P.chunks_per_split = (P.nchunks + split - 1) / split;
   const int nz = (P.nchunks + P.chunks_per_split - 1) / P.chunks_per_split;
   P.BN = op.BN;

@@ -448,9 +448,30 @@ fmm_status near_init(Ctx* c) {
   return FMM_OK;
 }
 
+namespace {
+
+template <typename T, int OPB>
+void near_dispatch(int p, unsigned blocks, cudaStream_t st, const NearParams& P) {
+  if (p == 4)
+    k_near<T, OPB, 4><<<blocks, 8 * OPB, 0, st>>>(P);
+  else if (p == 6)
+    k_near<T, OPB, 6><<<blocks, 8 * OPB, 0, st>>>(P);
+  else
+    k_near<T, OPB, 0><<<blocks, 8 * OPB, 0, st>>>(P);
+}
+
+}  // namespace
+
+int near_opb(const Ctx* c) {
+  const bool f64 = c->cfg.precision == FMM_FP64;
+  const int o = c->tune_opb;
+  if (f64) return (o == 4 || o == 8) ? o : 8;
+  return (o == 4 || o == 8 || o == 16) ? o : 16;
+}
+
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st) {
   const bool f64 = c->cfg.precision == FMM_FP64;
-  const int opb = f64 ? 8 : 16;
+  const int opb = near_opb(c);
   int l = lo;
   while (l <= c->lmax) {  // up to kMaxNearSeg target levels per launch
     NearParams P;
@@ -489,19 +510,17 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
     ++c->n_launch;
     const int p = c->cfg.p;
     if (f64) {
-      if (p == 4)
-        k_near<double, 8, 4><<<(unsigned)blocks, 64, 0, st>>>(P);
-      else if (p == 6)
-        k_near<double, 8, 6><<<(unsigned)blocks, 64, 0, st>>>(P);
+      if (opb == 4)
+        near_dispatch<double, 4>(p, (unsigned)blocks, st, P);
       else
-        k_near<double, 8, 0><<<(unsigned)blocks, 64, 0, st>>>(P);
+        near_dispatch<double, 8>(p, (unsigned)blocks, st, P);
     } else {
-      if (p == 4)
-        k_near<float, 16, 4><<<(unsigned)blocks, 128, 0, st>>>(P);
-      else if (p == 6)
-        k_near<float, 16, 6><<<(unsigned)blocks, 128, 0, st>>>(P);
+      if (opb == 4)
+        near_dispatch<float, 4>(p, (unsigned)blocks, st, P);
+      else if (opb == 8)
+        near_dispatch<float, 8>(p, (unsigned)blocks, st, P);
       else
-        k_near<float, 16, 0><<<(unsigned)blocks, 128, 0, st>>>(P);
+        near_dispatch<float, 16>(p, (unsigned)blocks, st, P);
     }
   }
 }

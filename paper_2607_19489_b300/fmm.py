@@ -23,7 +23,8 @@ PRECISION = {"fp64": 0, "mixed": 1, "bf16x3": 1}
 EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_error", "fmm_destroy",
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
             "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static",
-            "fmm_solve_adjoint"]
+            "fmm_solve_adjoint", "fmm_batch_solve", "fmm_autotune", "fmm_get_tuning",
+            "fmm_set_tuning"]
 
 
 class FMMError(RuntimeError):
@@ -67,6 +68,10 @@ def lib() -> ctypes.CDLL:
     L.fmm_set_timing.argtypes = [P, I]
     L.fmm_set_graphs.argtypes = [P, I]
     L.fmm_solve_adjoint.argtypes = [P, I, P, P, P, P]
+    L.fmm_batch_solve.argtypes = [P, I, P, P, P, P]
+    L.fmm_autotune.argtypes = [P, I, P]
+    L.fmm_get_tuning.argtypes = [P, P]
+    L.fmm_set_tuning.argtypes = [P, P]
     L.fmm_stage_times.argtypes = [P, P]
     for name in EXPORTED:
         fn = getattr(L, name)
@@ -220,6 +225,21 @@ class Solver:
         self._check(rc, "fmm_solve_adjoint")
         return out
 
+    def autotune(self, lo: int | None = None, stream=None) -> dict:
+        """Time the candidate launch shapes on the current hierarchy and keep the fastest."""
+        lo = self.lmin if lo is None else lo
+        self._check(lib().fmm_autotune(self._h, lo, _stream_ptr(stream)), "fmm_autotune")
+        return self.tuning()
+
+    def set_tuning(self, t: dict) -> None:
+        v = np.array([t["split_m2p"], t["split_m2l"], t["near_octs_per_block"]], np.int32)
+        self._check(lib().fmm_set_tuning(self._h, v.ctypes.data), "fmm_set_tuning")
+
+    def tuning(self) -> dict:
+        out = np.zeros(3, np.int32)
+        self._check(lib().fmm_get_tuning(self._h, out.ctypes.data), "fmm_get_tuning")
+        return {"split_m2p": int(out[0]), "split_m2l": int(out[1]), "near_octs_per_block": int(out[2])}
+
     def sync(self):
         self._check(lib().fmm_sync(self._h), "fmm_sync")
 
@@ -267,3 +287,31 @@ def _data_ptr(a):
         return a.data_ptr() if a.numel() else None
     a = np.asarray(a)
     return a.ctypes.data if a.size else None
+
+
+def batch_solve(solvers, outs=None, los=None, stream=None):
+    """Solve every solver's hierarchy in one CUDA graph launch (fmm_batch_solve).
+
+    outs[i] = (phi, acc) dicts of device tensors as from Solver.alloc_outputs (allocated
+    here when omitted); los[i] the first solved level (default lmin).  Returns outs."""
+    n = len(solvers)
+    los = [s.lmin for s in solvers] if los is None else list(los)
+    if outs is None:
+        outs = [s.alloc_outputs(lo) for s, lo in zip(solvers, los)]
+    keep, pp_rows, pa_rows = [], [], []
+    for s, lo, (phi, acc) in zip(solvers, los, outs):
+        levels = range(lo, s.lmax + 1)
+        pp = _ptrs([_data_ptr(phi[l]) for l in levels])
+        pa = _ptrs([_data_ptr(acc[l]) for l in levels])
+        keep += [pp, pa]
+        pp_rows.append(ctypes.cast(pp, ctypes.c_void_p).value)
+        pa_rows.append(ctypes.cast(pa, ctypes.c_void_p).value)
+    hs = (ctypes.c_void_p * n)(*[s._h for s in solvers])
+    lo_arr = (ctypes.c_int * n)(*los)
+    pp_arr = (ctypes.c_void_p * n)(*pp_rows)
+    pa_arr = (ctypes.c_void_p * n)(*pa_rows)
+    rc = lib().fmm_batch_solve(hs, n, lo_arr, pp_arr, pa_arr, _stream_ptr(stream))
+    del keep
+    if rc:
+        raise FMMError(rc, "fmm_batch_solve: " + (lib().fmm_last_error(solvers[0]._h) or b"").decode())
+    return outs

@@ -273,3 +273,78 @@ CONFIGS = {
     "twolevel64_p6": dict(make=lambda: two_level_plummer(), p=6),
     "nested128_p6": dict(make=lambda: nested_two_plummer(), p=6),
 }
+
+
+def _box_cells(lo, hi) -> np.ndarray:
+    """All cells of the half-open box [lo, hi)^3 (per-axis bounds), int32 [n, 3]."""
+    ax = [np.arange(lo[i], hi[i], dtype=np.int32) for i in range(3)]
+    g = np.stack(np.meshgrid(*ax, indexing="ij"), -1)
+    return g.reshape(-1, 3)
+
+
+def _outside(cells: np.ndarray, lo, hi) -> np.ndarray:
+    inside = np.all((cells >= np.asarray(lo)) & (cells < np.asarray(hi)), axis=1)
+    return cells[~inside]
+
+
+def blob_hierarchy(base: int, widths: list, seed: int, stream: int) -> Hierarchy:
+    """Base grid 2^base cubed with len(widths) nested refined boxes, box k a
+    fraction widths[k] of the width of the region it refines (the whole box for
+    k = 0, else the previous refined box), placed by seed inside that region one
+    coarse cell in from its faces so that the graded rule holds.  Density: a sum
+    of 1-8 Gaussian blobs (widths 0.02-0.1 of the box, seeded centres and
+    weights) plus a floor of 1e-3 of the mean; total mass 1.  Built box by box,
+    without dense masks, so deep levels cost only their own cells."""
+    lmax = base + len(widths)
+    ctr = [0]
+
+    def u(n=1):
+        v = uniform(seed, stream, np.arange(ctr[0], ctr[0] + n))
+        ctr[0] += n
+        return v
+
+    # existing region of each level: a box [elo, ehi)^3 in that level's cells
+    elo, ehi = np.zeros(3, np.int64), np.full(3, 2 ** base, np.int64)
+    leaves = []
+    for k, f in enumerate(widths + [None]):
+        l = base + k
+        margin = 0 if k == 0 else 2  # one level l-1 cell = two level-l cells
+        span = ehi - elo - 2 * margin
+        if f is None or np.any(span < 2):  # finest level, or no room left for another box
+            leaves.append(_box_cells(elo, ehi))
+            break
+        w = np.maximum(2, np.round(f * (ehi - elo))).astype(np.int64)
+        w = np.minimum(w, span)
+        lo = elo + margin + np.floor(u(3) * (span - w + 1)).astype(np.int64)
+        hi = lo + w
+        leaves.append(_outside(_box_cells(elo, ehi), lo, hi))
+        elo, ehi = 2 * lo, 2 * hi
+    nb = 1 + int(u()[0] * 8)
+    cen = 0.2 + 0.6 * u(3 * nb).reshape(nb, 3)
+    sig = 0.02 + 0.08 * u(nb)
+    wt = 0.5 + u(nb)
+
+    def rho(x):
+        r = np.zeros(x.shape[0])
+        for j in range(nb):
+            r += wt[j] * np.exp(-((x - cen[j]) ** 2).sum(-1) / (2 * sig[j] ** 2)) / sig[j] ** 3
+        return r + 1e-3 * float((wt / sig ** 3).mean()) * 0.01
+
+    lmax = base + len(leaves) - 1
+    h = _assemble(base, lmax, leaves, rho, f"blobs {2**base}^3 + {lmax - base} levels")
+    return _normalise(h)
+
+
+def batched_blobs(count: int = 64, seed: int = 5, bases=(5, 6, 7)) -> list:
+    """`count` independent isolated hierarchies for one batched solve: base grid
+    2^b cubed with b drawn from `bases`, 1-3 nested refinement levels, each
+    refined region a seeded 1/4-1/2 of its parent's width, Gaussian-blob
+    densities (1-8 blobs, widths 0.02-0.1 box)."""
+    out = []
+    for i in range(count):
+        v = uniform(seed, 900, np.arange(5 * i, 5 * i + 5))
+        base = bases[min(int(v[0] * len(bases)), len(bases) - 1)]
+        nlev = 1 + min(int(v[1] * 3), 2)
+        widths = [0.25 + 0.25 * float(x) for x in v[2:2 + nlev]]
+        out.append(blob_hierarchy(base, widths, seed, 1000 + i))
+    return out
