@@ -47,6 +47,8 @@ WORKLOAD = "two-level AMR 64^3 + 32^3 refined block, Plummer a=0.05 + lognormal 
 # MEASURED_PEAKS.json, when present, takes precedence.
 RECORDED_PEAKS = {"hbm_gbs": 6513.0, "bf16_tflops": 1786.0, "bf16_tflops_sustained": 1405.0}
 NC = (P_ORDER + 1) * (P_ORDER + 2) * (P_ORDER + 3) // 6
+# DRAM bytes of one M2P launch (k_gemm_tc) of the headline workload, from ncu
+M2P_TRAFFIC_BYTES = 37_025_280
 
 
 def load_peaks():
@@ -118,7 +120,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
@@ -289,7 +291,9 @@ def gpu_arm(args, rank, world, local):
         "achieved": m2p_useful / (stage["m2p"] * 1e-3) / 1e12,
         "peak": peaks["bf16_tflops_sustained"] / 3.0,
         "unit": "TFLOP/s",
-        "traffic": None,
+        "traffic": M2P_TRAFFIC_BYTES,
+        "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one M2P launch of this workload "
+                        "(ncu, profiles/k_gemm_tc_two_level_64c_32c_p6.md); algorithmic ~38 MB",
         "peak_note": f"{peak_src} bf16 dense sustained / 3 (three bf16 products per split-BF16 product); "
                      "achieved counts useful flops 2*189*4*ncoef per target cell",
         "stage_ms": stage["m2p"],
@@ -314,12 +318,147 @@ def gpu_arm(args, rank, world, local):
         "roofline": roofline,
         "clocks": clocks,
     }
+    del mixed, fp64, e2e_solver
+    legs = [x for x in args.legs.split(",") if x and x != "none"]
+    for name in legs:
+        fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats}.get(name)
+        if fn is None:
+            continue
+        try:
+            line[name] = fn(args, torch, dev, stream, flush)
+        except Exception as e:  # an extra workload never hides the headline
+            line[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, per_level=args.cpu_sample)
     if rank == 0:
         print(json.dumps(line))
     barrier(dist)
     del rows
+
+
+# ---------------------------------------------------------------------------- extra workloads
+
+def _timed(torch, fn, K, W, stream):
+    for _ in range(W):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / K
+
+
+def leg_batched(args, torch, dev, stream, flush):
+    """64 independent hierarchies (32^3/64^3/128^3 bases, 1-3 nested levels,
+    Gaussian blobs), p = 6 mixed, one CUDA graph launch per batch; launch
+    shapes from the autotuner (one tuned context per base size)."""
+    from paper_2607_19489_b300 import fmm, workloads as W
+    t0 = time.perf_counter()
+    hs = W.batched_blobs(count=64, seed=5)
+    gen_s = time.perf_counter() - t0
+    solvers, tuned = [], {}
+    for h in hs:
+        s = fmm.Solver(P_ORDER, "mixed")
+        s.set_hierarchy(h, device=dev)
+        if h.lmin not in tuned:
+            tuned[h.lmin] = s.autotune()
+        else:
+            s.set_tuning(tuned[h.lmin])
+        solvers.append(s)
+    outs = [s.alloc_outputs(device=dev) for s in solvers]
+    free, total = torch.cuda.mem_get_info(dev)
+    cells = int(sum(h.n_cells for h in hs))
+    K = max(3, min(args.steps // 20, 20))
+    l0 = sum(s.stats()["launches"] for s in solvers)
+    ms_batch = _timed(torch, lambda: fmm.batch_solve(solvers, outs), K, 3, stream)
+    l1 = sum(s.stats()["launches"] for s in solvers)
+    ms_seq = _timed(torch, lambda: [s.solve(out=o) for s, o in zip(solvers, outs)], K, 2, stream)
+    for s in solvers:
+        s.sync()
+    out = {"workload": "64 isolated hierarchies, bases 32^3/64^3/128^3 by seed, 1-3 nested levels of 1/4-1/2 "
+                       "width, 1-8 Gaussian blobs, p=6 mixed", "hierarchies": len(hs), "cells": cells,
+           "value": cells / (ms_batch * 1e-3), "unit": UNIT, "ms_per_batch": ms_batch,
+           "one_graph_per_hierarchy_ms": ms_seq, "gpu_launches_per_batch": (l1 - l0) // (K + 3),
+           "tuning_by_base_level": {str(k): v for k, v in tuned.items()},
+           "device_memory_used_gb": (total - free) / 1e9, "generation_s": gen_s, "step": "fmm_batch_solve"}
+    del solvers, outs
+    return out
+
+
+def leg_adjoint(args, torch, dev, stream, flush):
+    """Nested two-Plummer hierarchy (128^3 base, refined central boxes at levels
+    8 and 9), FP64: forward solve and adjoint (loss = sum w . accel)."""
+    from paper_2607_19489_b300 import fmm, workloads as W
+    h = W.nested_two_plummer()
+    s = fmm.Solver(P_ORDER, "fp64")
+    ijk = [torch.as_tensor(a, device=dev).contiguous() for a in h.ijk]
+    mass = [torch.as_tensor(m, device=dev).contiguous() for m in h.mass]
+    s.set_levels(h.lmin, h.lmax, ijk, mass)
+    out = s.alloc_outputs(device=dev)
+    w = {l: torch.as_tensor(W.normal(31, 300 + l, np.arange(3 * h.n(l))).reshape(-1, 3), device=dev)
+         for l in h.levels}
+    zero = {l: torch.zeros(h.n(l), dtype=torch.float64, device=dev) for l in h.levels}
+    gm = {l: torch.empty(h.n(l), dtype=torch.float64, device=dev) for l in h.levels}
+    ms_fwd = _timed(torch, lambda: s.solve(out=out), 2, 1, stream)
+    ms_adj = _timed(torch, lambda: s.solve_adjoint(zero, w, out=gm), 2, 1, stream)
+    s.sync()
+    lhs = sum(float((w[l] * out[1][l]).sum()) for l in h.levels)
+    rhs = sum(float((gm[l] * mass[k]).sum()) for k, l in enumerate(h.levels))
+    res = {"workload": "nested two-Plummer 128^3 + 2 refined levels (central 1/4 and 1/16 volumes), p=6 FP64",
+           "cells": h.n_cells, "forward_ms": ms_fwd, "adjoint_ms": ms_adj, "adjoint_over_forward": ms_adj / ms_fwd,
+           "dot_identity_rel": abs(lhs - rhs) / max(abs(lhs), 1e-300),
+           "check": "<w, accel(m)> = <dL/dm, m> (linear map); finite differences run in the GPU tests"}
+    del s
+    return res
+
+
+def leg_ats(args, torch, dev, stream, flush):
+    """Lognormal 256^3 base (sigma 1, P(k) ~ k^-2), refined where the cell mass
+    exceeds 8x the mean base-cell mass (up to 4 levels); one coarse step = the
+    amr_step schedule of full and fine-level-only solves, each after rebuilding
+    the active levels with +-1e-3 perturbed masses; p = 6 mixed, FP32 outputs."""
+    from paper_2607_19489_b300 import fmm, workloads as W
+    t0 = time.perf_counter()
+    h = W.lognormal_amr(base=8)
+    gen_s = time.perf_counter() - t0
+    sched = W.ats_schedule(h.lmin, h.lmax)
+    s = fmm.Solver(P_ORDER, "mixed", out_fp32=True)
+    ijk = [torch.as_tensor(a, device=dev).contiguous() for a in h.ijk]
+    base = [torch.as_tensor(m, device=dev).contiguous() for m in h.mass]
+    s.set_levels(h.lmin, h.lmax, ijk, base)
+    tuning = s.autotune()
+    # perturbed masses of each rebuild, resident before the timed region
+    pert = []
+    for i, lo in enumerate(sched):
+        k0 = lo - h.lmin
+        pert.append([base[k] * torch.as_tensor(1.0 + 1e-3 * (2 * W.uniform(77, 1000 * i + k, np.arange(h.n(h.lmin + k))) - 1),
+                                               device=dev) for k in range(k0, len(base))])
+    outs = {lo: s.alloc_outputs(lo, device=dev) for lo in set(sched)}
+
+    def coarse_step():
+        for lo, ms in zip(sched, pert):
+            s.set_levels(h.lmin, h.lmax, ijk[lo - h.lmin:], ms, lo=lo)
+            s.solve(lo, out=outs[lo])
+
+    K = max(3, min(args.steps // 40, 10))
+    ms_step = _timed(torch, coarse_step, K, 3, stream)
+    s.set_levels(h.lmin, h.lmax, ijk, base)
+    ms_full = _timed(torch, lambda: (s.set_levels(h.lmin, h.lmax, ijk, base), s.solve(out=outs[h.lmin])), K, 2, stream)
+    s.sync()
+    updated = sum(sum(h.n(l) for l in range(lo, h.lmax + 1)) for lo in sched)
+    res = {"workload": h.name + ", p=6 mixed, FP32 outputs", "cells": h.n_cells,
+           "levels": [h.n(l) for l in h.levels], "schedule_lo": sched,
+           "value": updated / (ms_step * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms_step,
+           "cell_updates_per_coarse_step": updated, "full_rebuild_and_solve_ms": ms_full,
+           "tuning": tuning, "generation_s": gen_s,
+           "step": "per solve of the schedule: fmm_set_levels(lo) with perturbed masses + fmm_solve(lo)"}
+    del s
+    return res
 
 
 # ---------------------------------------------------------------------------- CPU oracle
@@ -364,12 +503,14 @@ def reference_arm(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4000, help="oracle targets per level for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=1000, help="oracle targets per level per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="batched,adjoint,ats",
+                    help="extra workloads reported beside the headline (comma list, or 'none')")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -348,3 +348,115 @@ def batched_blobs(count: int = 64, seed: int = 5, bases=(5, 6, 7)) -> list:
         widths = [0.25 + 0.25 * float(x) for x in v[2:2 + nlev]]
         out.append(blob_hierarchy(base, widths, seed, 1000 + i))
     return out
+
+
+def gaussian_field(n: int, slope: float, seed: int, stream: int = 0) -> np.ndarray:
+    """Periodic Gaussian random field on an n^3 grid with power spectrum
+    P(k) ~ k^slope (k in grid units, the k = 0 mode removed), normalised to
+    zero mean and unit variance; white noise from the counter-based generator."""
+    white = normal(seed, stream, np.arange(n ** 3)).reshape(n, n, n)
+    f = np.fft.rfftn(white)
+    kx = np.fft.fftfreq(n) * n
+    kz = np.fft.rfftfreq(n) * n
+    k2 = kx[:, None, None] ** 2 + kx[None, :, None] ** 2 + kz[None, None, :] ** 2
+    amp = np.zeros_like(k2)
+    amp[k2 > 0] = k2[k2 > 0] ** (slope / 4.0)  # sqrt(P(k)) = k^(slope/2)
+    g = np.fft.irfftn(f * amp, s=(n, n, n), axes=(0, 1, 2))
+    g -= g.mean()
+    return g / g.std()
+
+
+def _trilinear_periodic(g: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Trilinear interpolation of the cell-centred periodic grid g at points x in [0,1)^3."""
+    n = g.shape[0]
+    u = x * n - 0.5
+    i0 = np.floor(u).astype(np.int64)
+    t = u - i0
+    out = np.zeros(x.shape[0])
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                w = ((t[:, 0] if dx else 1 - t[:, 0]) * (t[:, 1] if dy else 1 - t[:, 1]) *
+                     (t[:, 2] if dz else 1 - t[:, 2]))
+                out += w * g[(i0[:, 0] + dx) % n, (i0[:, 1] + dy) % n, (i0[:, 2] + dz) % n]
+    return out
+
+
+def _dilate(mask: np.ndarray) -> np.ndarray:
+    out = mask.copy()
+    for axis in range(3):
+        out |= np.roll(out, 1, axis) | np.roll(out, -1, axis)
+    return out
+
+
+def lognormal_amr(base: int = 8, sigma: float = 1.0, slope: float = -2.0, threshold: float = 8.0,
+                  max_levels: int = 4, seed: int = 6) -> Hierarchy:
+    """Lognormal density on a 2^base cubed base grid, rho = exp(sigma g - sigma^2/2)
+    with g a P(k) ~ k^slope Gaussian field (mean density 1, total mass 1); a cell
+    is refined when its mass exceeds `threshold` times the mean base-cell mass
+    (a fixed mass threshold, as in quasi-Lagrangian AMR refinement), up to
+    `max_levels` levels above the base.  Finer cells take the field trilinearly
+    interpolated in g.  The flagged cells of each level are dilated by one cell
+    and then filtered by the graded rule; the isolated box has no periodic
+    images (the field is periodic only for its generation)."""
+    n = 2 ** base
+    g = gaussian_field(n, slope, seed)
+    m_thr = threshold / n ** 3  # threshold x mean base-cell mass (total mass 1, mean density 1)
+
+    def rho(x):
+        return np.exp(sigma * _trilinear_periodic(g, x) - 0.5 * sigma ** 2)
+
+    refined = {}
+    exists = np.ones((n,) * 3, dtype=bool)
+    prev = None
+    for k in range(max_levels):
+        l = base + k
+        nl = 2 ** l
+        idx = np.argwhere(exists)
+        x = (idx + 0.5) / nl
+        if k == 0:
+            mass = np.exp(sigma * g - 0.5 * sigma ** 2).reshape(-1)[np.ravel_multi_index(idx.T, (nl,) * 3)]
+        else:
+            mass = rho(x)
+        mass = mass / nl ** 3
+        flag = np.zeros((nl,) * 3, dtype=bool)
+        flag[tuple(idx[mass > m_thr].T)] = True
+        flag = _dilate(flag) & exists
+        if prev is not None:
+            flag = graded_filter(prev, flag)
+        if not flag.any():
+            break
+        refined[l] = flag
+        prev = flag
+        exists = np.repeat(np.repeat(np.repeat(flag, 2, 0), 2, 1), 2, 2)
+    lmax = base + len(refined)
+    leaves = leaves_from_refined(base, lmax, refined)
+    h = Hierarchy(base, lmax, name=f"lognormal {n}^3 sigma={sigma} P(k)~k^{slope:g}, {lmax - base} refined levels")
+    for k, c in enumerate(leaves):
+        l = base + k
+        x = (c.astype(np.float64) + 0.5) / 2 ** l
+        if k == 0:
+            m = np.exp(sigma * g[c[:, 0], c[:, 1], c[:, 2]] - 0.5 * sigma ** 2)
+        else:
+            m = rho(x)
+        h.ijk.append(np.ascontiguousarray(c, dtype=np.int32))
+        h.mass.append(m * 8.0 ** (-l))
+    return _normalise(h)
+
+
+def ats_schedule(lmin: int, lmax: int) -> list:
+    """The solves of one coarse step with adaptive time stepping (Alg. 1 inside
+    the amr_step recursion): level l is rebuilt and solved (levels l..lmax) when
+    l = lmin or on its second substep.  Returns the list of lo values in order;
+    lo = k occurs 2^(k-lmin-1) times for k > lmin."""
+    out = []
+
+    def step(l, icount):
+        if l == lmin or icount > 1:
+            out.append(l)
+        if l < lmax:
+            step(l + 1, 1)
+            step(l + 1, 2)
+
+    step(lmin, 1)
+    return out
