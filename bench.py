@@ -409,7 +409,28 @@ def leg_adjoint(args, torch, dev, stream, flush):
     s.sync()
     lhs = sum(float((w[l] * out[1][l]).sum()) for l in h.levels)
     rhs = sum(float((gm[l] * mass[k]).sum()) for k, l in enumerate(h.levels))
+    fd = None
+    if args.fd_cells > 0:
+        n_all = sum(h.n(l) for l in h.levels)
+        offs = np.cumsum([0] + [h.n(l) for l in h.levels])
+        picks = np.unique((W.uniform(41, 1, np.arange(args.fd_cells)) * n_all).astype(np.int64))
+        errs = []
+        for g in picks:
+            k = int(np.searchsorted(offs, g, side="right") - 1)
+            j = int(g - offs[k])
+            vals = []
+            for sgn in (1, -1):
+                mp = [m.clone() for m in mass]
+                mp[k][j] += sgn * 1e-6
+                s.set_levels(h.lmin, h.lmax, ijk, mp)
+                s.solve(out=out)
+                s.sync()
+                vals.append(sum(float((w[l] * out[1][l]).sum()) for l in h.levels))
+            ad = float(gm[h.lmin + k][j])
+            errs.append(abs((vals[0] - vals[1]) / 2e-6 - ad) / max(abs(ad), 1e-300))
+        fd = {"cells": int(len(picks)), "h": 1e-6, "max_rel_err": float(max(errs))}
     res = {"workload": "nested two-Plummer 128^3 + 2 refined levels (central 1/4 and 1/16 volumes), p=6 FP64",
+           "finite_differences": fd,
            "cells": h.n_cells, "forward_ms": ms_fwd, "adjoint_ms": ms_adj, "adjoint_over_forward": ms_adj / ms_fwd,
            "dot_identity_rel": abs(lhs - rhs) / max(abs(lhs), 1e-300),
            "check": "<w, accel(m)> = <dL/dm, m> (linear map); finite differences run in the GPU tests"}
@@ -509,6 +530,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4000, help="oracle targets per level for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=1000, help="oracle targets per level per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fd-cells", type=int, default=0,
+                    help="adjoint leg: central finite differences on this many seeded cells (2 FP64 solves each)")
     ap.add_argument("--legs", default="batched,adjoint,ats",
                     help="extra workloads reported beside the headline (comma list, or 'none')")
     args = ap.parse_args()

@@ -235,43 +235,41 @@ __global__ void __launch_bounds__(kListBlock) k_lists_count(const __grid_constan
   }
 }
 
-// One block: per level and list, an exclusive scan of the block counts.
-__global__ void __launch_bounds__(1024) k_lists_scan(const __grid_constant__ ListParams P, const int32_t* __restrict__ blk_counts,
+// One block per (level, list): an exclusive scan of the level's block counts.
+__global__ void __launch_bounds__(1024) k_lists_scan(const __grid_constant__ ListParams P,
+                                                     const int32_t* __restrict__ blk_counts,
                                                      int32_t* __restrict__ blk_off, int32_t* __restrict__ counts) {
   __shared__ int32_t warp_sum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int li = 0; li < P.nlev; ++li) {
-    const ListLevel& L = P.lev[li];
-    const int64_t nb = (L.n_oct + kListBlock - 1) / kListBlock;
-    for (int k = 0; k < 4; ++k) {
-      int32_t carry = 0;
-      for (int64_t base = 0; base < nb; base += 1024) {
-        const int64_t b = base + threadIdx.x;
-        const int32_t v = b < nb ? blk_counts[(L.blk0 + b) * 4 + k] : 0;
-        int32_t x = v;  // inclusive warp scan
-        for (int d = 1; d < 32; d <<= 1) {
-          const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
-          if (lane >= d) x += y;
-        }
-        if (lane == 31) warp_sum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-          int32_t w = warp_sum[lane];
-          for (int d = 1; d < 32; d <<= 1) {
-            const int32_t y = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += y;
-          }
-          warp_sum[lane] = w;  // inclusive over warps
-        }
-        __syncthreads();
-        const int32_t excl = x - v + (warp > 0 ? warp_sum[warp - 1] : 0);
-        if (b < nb) blk_off[(L.blk0 + b) * 4 + k] = carry + excl;
-        carry += warp_sum[31];
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) counts[k * P.stride + P.level0 + li] = carry;
+  const int li = blockIdx.x >> 2, k = blockIdx.x & 3;
+  const ListLevel& L = P.lev[li];
+  const int64_t nb = (L.n_oct + kListBlock - 1) / kListBlock;
+  int32_t carry = 0;
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t b = base + threadIdx.x;
+    const int32_t v = b < nb ? blk_counts[(L.blk0 + b) * 4 + k] : 0;
+    int32_t x = v;  // inclusive warp scan
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
     }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t w = warp_sum[lane];
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= d) w += y;
+      }
+      warp_sum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const int32_t excl = x - v + (warp > 0 ? warp_sum[warp - 1] : 0);
+    if (b < nb) blk_off[(L.blk0 + b) * 4 + k] = carry + excl;
+    carry += warp_sum[31];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) counts[k * P.stride + P.level0 + li] = carry;
 }
 
 __global__ void __launch_bounds__(kListBlock) k_lists_write(const __grid_constant__ ListParams P, const uint8_t* __restrict__ flags,
@@ -482,7 +480,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     int32_t* blk_off = blk_counts + nb * 4;          // nb * 4
     c->n_launch += 3;
     k_lists_count<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_counts);
-    k_lists_scan<<<1, 1024, 0, st>>>(P, blk_counts, blk_off, d_counts);
+    k_lists_scan<<<(unsigned)(4 * P.nlev), 1024, 0, st>>>(P, blk_counts, blk_off, d_counts);
     k_lists_write<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_off);
   }
   return FMM_OK;

@@ -187,19 +187,82 @@ __global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
   }
 }
 
+// M2M with FP64 accumulation (the top of the tree and the FP64 path): one
+// block per oct of level b+1.  These levels are small, so the kernel is
+// latency-bound: the block stages the pair tables and the eight children's
+// rows in shared memory and spreads the transform and the per-alpha sums over
+// all its threads.  Dynamic shared memory: see m2m_block_smem.
+template <typename Tin, typename Tout, typename TMono>
+__global__ void __launch_bounds__(128) k_m2m_block(
+    int nc, int npairs, const int32_t* __restrict__ oct_parent_next, const int32_t* __restrict__ cell_child_next,
+    const Tin* __restrict__ Mnext, const double* __restrict__ mass_next, Tout* __restrict__ Mout,
+    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono,
+    const int* __restrict__ poff, const int* __restrict__ pg, const int* __restrict__ pe,
+    const double* __restrict__ pc) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  double* S = (double*)dsm;                   // [8][nc]
+  double* cf = S + 8 * nc;                    // [npairs]
+  int* gx = (int*)(cf + npairs);              // [npairs]: gamma + nc * e
+  int* off = gx + npairs;                     // [nc + 1]
+  const int64_t o = blockIdx.x;
+  const int64_t cell = oct_parent_next[o];
+  const int64_t c0 = o * 8;
+  for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
+    cf[j] = pc[j];
+    gx[j] = pg[j] + nc * pe[j];
+  }
+  for (int k = threadIdx.x; k <= nc; k += blockDim.x) off[k] = poff[k];
+  for (int idx = threadIdx.x; idx < 8 * nc; idx += blockDim.x) {
+    const int c = idx / nc, g = idx - c * nc;
+    const int32_t cc = cell_child_next[c0 + c];
+    S[idx] = cc < 0 ? (g == 0 ? mass_next[-1 - (int64_t)cc] : 0.0) : (double)Mnext[(c0 + c) * nc + g];
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < nc; g += blockDim.x) {
+    double x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = S[c * nc + g];
+    sign_transform(x);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) S[e * nc + g] = x[e];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    double v = 0;
+    for (int j = off[k]; j < off[k + 1]; ++j) v += cf[j] * S[gx[j]];
+    const Tout w = (Tout)v;
+    Mout[cell * nc + k] = w;
+    if (hi) split_bf16(w, hi[cell * nc + k], lo[cell * nc + k]);
+    if (k == 0) mono[cell] = (TMono)w;
+  }
+}
+
+inline size_t m2m_block_smem(int nc, int npairs) { return (size_t)8 * nc * 8 + (size_t)npairs * 12 + (nc + 1) * 4; }
+
 // Downward step for the row octs of level b: L = L2L(parent's L) + this level's
 // M2L sum (accumulated by the contraction in FP32, added here in FP64).
-// One thread per output coefficient beta, all 8 children at once.
-__global__ void __launch_bounds__(128) k_l2l_add(int nc, const int32_t* __restrict__ rows,
+// One thread per output coefficient beta, all 8 children at once; the pair
+// tables and the parent's expansion are staged in shared memory (dynamic:
+// l2l_smem), since these small levels are latency-bound.
+__global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32_t* __restrict__ rows,
                                                  const int32_t* __restrict__ oct_parent,
                                                  const double* __restrict__ Lup, const float* __restrict__ Lm,
                                                  double* __restrict__ L, const int* __restrict__ poff8,
                                                  const int* __restrict__ pg, const double* __restrict__ pc) {
-  __shared__ double Lp[kNcMax];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  double* Lp = (double*)dsm;            // [nc]
+  double* cf = Lp + nc;                 // [npairs]
+  int* gg = (int*)(cf + npairs);        // [npairs]
+  int* off = gg + npairs;               // [8 nc + 1]
   const int32_t o = rows[blockIdx.x];
   if (Lup) {
     const int32_t par = oct_parent[o];
     for (int k = threadIdx.x; k < nc; k += blockDim.x) Lp[k] = Lup[(int64_t)par * nc + k];
+    for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
+      cf[j] = pc[j];
+      gg[j] = pg[j];
+    }
+    for (int k = threadIdx.x; k <= 8 * nc; k += blockDim.x) off[k] = poff8[k];
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nc; b += blockDim.x) {
@@ -208,7 +271,7 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, const int32_t* __restri
     for (int e = 0; e < 8; ++e) {
       double s = 0.0;
       if (Lup)
-        for (int j = poff8[b * 8 + e]; j < poff8[b * 8 + e + 1]; ++j) s += pc[j] * Lp[pg[j]];
+        for (int j = off[b * 8 + e]; j < off[b * 8 + e + 1]; ++j) s += cf[j] * Lp[gg[j]];
       acc[e] = s;
     }
     sign_transform_back(acc);
@@ -219,6 +282,8 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, const int32_t* __restri
     }
   }
 }
+
+inline size_t l2l_smem(int nc, int npairs) { return (size_t)nc * 8 + (size_t)npairs * 12 + (8 * nc + 1) * 4; }
 
 }  // namespace
 
@@ -258,7 +323,6 @@ void launch_upward(Ctx* c, int b, cudaStream_t st) {
   const int* pg = (const int*)c->d_m2m_g.ptr;
   const int* pe = (const int*)c->d_m2m_e.ptr;
   const double* pc = (const double*)c->d_m2m_c.ptr;
-  const double* w0 = (const double*)c->d_m2m_w0.ptr;
   const int* e0 = (const int*)c->d_m2m_e0.ptr;
   const int64_t n = N.n_oct;
   const int32_t* par = (const int32_t*)N.oct_parent.ptr;
@@ -266,23 +330,24 @@ void launch_upward(Ctx* c, int b, cudaStream_t st) {
   const double* mn = (const double*)N.mass.ptr;
   __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
   __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
-  const unsigned g64 = (unsigned)((n + M2MWarps<double>::kWarps - 1) / M2MWarps<double>::kWarps);
   const unsigned g32 = (unsigned)((n + M2MWarps<float>::kWarps - 1) / M2MWarps<float>::kWarps);
-  constexpr int t64 = 32 * M2MWarps<double>::kWarps, t32 = 32 * M2MWarps<float>::kWarps;
+  constexpr int t32 = 32 * M2MWarps<float>::kWarps;
   ++c->n_launch;
+  const int np = (int)c->tab.m2m_g.size();
+  const size_t smb = m2m_block_smem(nc, np);
   if (f64) {
-    k_m2m<double, double, double, double><<<g64, t64, 0, st>>>(n, nc, par, ccn, (const double*)N.M.ptr, mn,
-                                                               (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
-                                                               poff, pg, pe, pc, w0, e0);
+    k_m2m_block<double, double, double><<<(unsigned)n, 128, smb, st>>>(nc, np, par, ccn, (const double*)N.M.ptr, mn,
+                                                                     (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
+                                                                     poff, pg, pe, pc);
   } else if (T.m_is_f64) {  // mixed path, top of the tree: FP64 shifts
     if (N.m_is_f64)
-      k_m2m<double, double, double, float><<<g64, t64, 0, st>>>(n, nc, par, ccn, (const double*)N.M.ptr, mn,
-                                                                (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
-                                                                poff, pg, pe, pc, w0, e0);
+      k_m2m_block<double, double, float><<<(unsigned)n, 128, smb, st>>>(nc, np, par, ccn, (const double*)N.M.ptr, mn,
+                                                                      (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
+                                                                      poff, pg, pe, pc);
     else
-      k_m2m<float, double, double, float><<<g64, t64, 0, st>>>(n, nc, par, ccn, (const float*)N.M.ptr, mn,
-                                                               (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
-                                                               poff, pg, pe, pc, w0, e0);
+      k_m2m_block<float, double, float><<<(unsigned)n, 128, smb, st>>>(nc, np, par, ccn, (const float*)N.M.ptr, mn,
+                                                                     (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
+                                                                     poff, pg, pe, pc);
   } else {
     k_m2m<float, float, float, float><<<g32, t32, 0, st>>>(n, nc, par, ccn, (const float*)N.M.ptr, mn,
                                                            (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg,
@@ -295,8 +360,9 @@ void launch_l2l_add(Ctx* c, int b, cudaStream_t st) {
   LevelTree& T = c->lev[b];
   if (!T.n_rowsL) return;
   ++c->n_launch;
-  k_l2l_add<<<(unsigned)T.n_rowsL, 128, 0, st>>>(
-      c->tab.nc, (const int32_t*)T.rowsL.ptr, (const int32_t*)T.oct_parent.ptr,
+  const int np = (int)c->tab.l2l_g.size();
+  k_l2l_add<<<(unsigned)T.n_rowsL, 128, l2l_smem(c->tab.nc, np), st>>>(
+      c->tab.nc, np, (const int32_t*)T.rowsL.ptr, (const int32_t*)T.oct_parent.ptr,
       b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
       c->cfg.precision == FMM_FP64 ? nullptr : (const float*)T.Lm.ptr, (double*)T.L.ptr,
       (const int*)c->d_l2l_off8.ptr, (const int*)c->d_l2l_g.ptr, (const double*)c->d_l2l_c.ptr);

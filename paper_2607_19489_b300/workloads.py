@@ -288,14 +288,16 @@ def _outside(cells: np.ndarray, lo, hi) -> np.ndarray:
 
 
 def blob_hierarchy(base: int, widths: list, seed: int, stream: int) -> Hierarchy:
-    """Base grid 2^base cubed with len(widths) nested refined boxes, box k a
-    fraction widths[k] of the width of the region it refines (the whole box for
-    k = 0, else the previous refined box), placed by seed inside that region one
-    coarse cell in from its faces so that the graded rule holds.  Density: a sum
-    of 1-8 Gaussian blobs (widths 0.02-0.1 of the box, seeded centres and
-    weights) plus a floor of 1e-3 of the mean; total mass 1.  Built box by box,
-    without dense masks, so deep levels cost only their own cells."""
-    lmax = base + len(widths)
+    """Base grid 2^base cubed with up to len(widths) nested refined regions.
+
+    Region k (cells of level base+k) is a box whose width is a fraction
+    widths[k] of the width of the region it refines (the whole grid for k = 0,
+    else the cells under the previous region), rounded to an even number of
+    cells, with even corners (whole octs below it) and at least 2 parent cells
+    (4 cells of its own level) inside that region, which keeps the graded rule.
+    Nesting stops early when no such box fits.  Density: 1-8 Gaussian blobs
+    (widths U(0.02, 0.1), centres U(0.2, 0.8)^3, amplitudes U(0.5, 2)) plus a
+    small floor; total mass 1.  Built box by box, without dense masks."""
     ctr = [0]
 
     def u(n=1):
@@ -303,32 +305,30 @@ def blob_hierarchy(base: int, widths: list, seed: int, stream: int) -> Hierarchy
         ctr[0] += n
         return v
 
-    # existing region of each level: a box [elo, ehi)^3 in that level's cells
-    elo, ehi = np.zeros(3, np.int64), np.full(3, 2 ** base, np.int64)
+    margin = 4
+    elo, ehi = np.zeros(3, np.int64), np.full(3, 2 ** base, np.int64)  # cells of the current level
     leaves = []
     for k, f in enumerate(widths + [None]):
-        l = base + k
-        margin = 0 if k == 0 else 2  # one level l-1 cell = two level-l cells
         span = ehi - elo - 2 * margin
-        if f is None or np.any(span < 2):  # finest level, or no room left for another box
+        w = None if f is None else 2 * np.maximum(1, np.round(f * (ehi - elo) / 2.0)).astype(np.int64)
+        if f is None or np.any(span < w):
             leaves.append(_box_cells(elo, ehi))
             break
-        w = np.maximum(2, np.round(f * (ehi - elo))).astype(np.int64)
-        w = np.minimum(w, span)
-        lo = elo + margin + np.floor(u(3) * (span - w + 1)).astype(np.int64)
+        lo = elo + margin + 2 * np.floor(u(3) * ((span - w) // 2 + 1)).astype(np.int64)
         hi = lo + w
         leaves.append(_outside(_box_cells(elo, ehi), lo, hi))
         elo, ehi = 2 * lo, 2 * hi
-    nb = 1 + int(u()[0] * 8)
+    nb = 1 + min(int(u()[0] * 8), 7)
     cen = 0.2 + 0.6 * u(3 * nb).reshape(nb, 3)
     sig = 0.02 + 0.08 * u(nb)
-    wt = 0.5 + u(nb)
+    amp = 0.5 + 1.5 * u(nb)
+    peak = float((amp / sig ** 3).max())
 
     def rho(x):
-        r = np.zeros(x.shape[0])
+        r = np.full(x.shape[0], 1e-6 * peak)
         for j in range(nb):
-            r += wt[j] * np.exp(-((x - cen[j]) ** 2).sum(-1) / (2 * sig[j] ** 2)) / sig[j] ** 3
-        return r + 1e-3 * float((wt / sig ** 3).mean()) * 0.01
+            r += amp[j] * np.exp(-((x - cen[j]) ** 2).sum(-1) / (2 * sig[j] ** 2)) / sig[j] ** 3
+        return r
 
     lmax = base + len(leaves) - 1
     h = _assemble(base, lmax, leaves, rho, f"blobs {2**base}^3 + {lmax - base} levels")
@@ -366,81 +366,91 @@ def gaussian_field(n: int, slope: float, seed: int, stream: int = 0) -> np.ndarr
     return g / g.std()
 
 
-def _trilinear_periodic(g: np.ndarray, x: np.ndarray) -> np.ndarray:
-    """Trilinear interpolation of the cell-centred periodic grid g at points x in [0,1)^3."""
-    n = g.shape[0]
-    u = x * n - 0.5
-    i0 = np.floor(u).astype(np.int64)
-    t = u - i0
-    out = np.zeros(x.shape[0])
-    for dz in (0, 1):
-        for dy in (0, 1):
-            for dx in (0, 1):
-                w = ((t[:, 0] if dx else 1 - t[:, 0]) * (t[:, 1] if dy else 1 - t[:, 1]) *
-                     (t[:, 2] if dz else 1 - t[:, 2]))
-                out += w * g[(i0[:, 0] + dx) % n, (i0[:, 1] + dy) % n, (i0[:, 2] + dz) % n]
-    return out
+def _keys(idx: np.ndarray, level: int) -> np.ndarray:
+    n = np.int64(2 ** level)
+    return (idx[:, 0].astype(np.int64) * n + idx[:, 1]) * n + idx[:, 2]
 
 
-def _dilate(mask: np.ndarray) -> np.ndarray:
-    out = mask.copy()
-    for axis in range(3):
-        out |= np.roll(out, 1, axis) | np.roll(out, -1, axis)
-    return out
+_OFF27 = np.array([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)], np.int64)
+_OFF8 = np.array([(c & 1, (c >> 1) & 1, (c >> 2) & 1) for c in range(8)], np.int64)
+
+
+def _neighbour_keys(idx: np.ndarray, level: int):
+    """Keys of the 27 neighbours of each cell (K x 27) and their in-box mask."""
+    nb = idx[:, None, :] + _OFF27[None, :, :]
+    ok = np.all((nb >= 0) & (nb < 2 ** level), axis=2)
+    return _keys(np.clip(nb, 0, 2 ** level - 1).reshape(-1, 3), level).reshape(-1, 27), ok
 
 
 def lognormal_amr(base: int = 8, sigma: float = 1.0, slope: float = -2.0, threshold: float = 8.0,
-                  max_levels: int = 4, seed: int = 6) -> Hierarchy:
-    """Lognormal density on a 2^base cubed base grid, rho = exp(sigma g - sigma^2/2)
-    with g a P(k) ~ k^slope Gaussian field (mean density 1, total mass 1); a cell
-    is refined when its mass exceeds `threshold` times the mean base-cell mass
-    (a fixed mass threshold, as in quasi-Lagrangian AMR refinement), up to
-    `max_levels` levels above the base.  Finer cells take the field trilinearly
-    interpolated in g.  The flagged cells of each level are dilated by one cell
-    and then filtered by the graded rule; the isolated box has no periodic
-    images (the field is periodic only for its generation)."""
+                  max_levels: int = 4, sigma_sub: float = 0.5, seed: int = 6,
+                  max_leaves: int = 64_000_000) -> Hierarchy:
+    """Lognormal density on a 2^base cubed base grid with mass refinement.
+
+    Base cells: rho = exp(sigma g - sigma^2/2), g a Gaussian field with
+    P(k) ~ k^slope (mean density 1).  A cell is flagged when its mass exceeds
+    `threshold` times the mean base-cell mass (a fixed mass, the
+    quasi-Lagrangian criterion, at every level); flags are dilated by one cell
+    (within the existing cells) and, above the base, kept only where the graded
+    rule allows; flagged cells are refined, up to `max_levels` levels.  A
+    refined cell's mass is shared by its 8 children with seeded lognormal
+    weights (sigma_sub), normalised per oct, so mass is conserved.  If fewer
+    than `max_levels` levels appear, sigma_sub is raised once by half (the
+    name records the value used).  Refinement also stops before the leaves
+    would exceed `max_leaves`.  Sparse throughout (sorted cell keys)."""
     n = 2 ** base
     g = gaussian_field(n, slope, seed)
-    m_thr = threshold / n ** 3  # threshold x mean base-cell mass (total mass 1, mean density 1)
+    m_thr = threshold / n ** 3
 
-    def rho(x):
-        return np.exp(sigma * _trilinear_periodic(g, x) - 0.5 * sigma ** 2)
+    def build(ssub):
+        idx = np.argwhere(np.ones((n,) * 3, dtype=bool)).astype(np.int64)
+        mass = np.exp(sigma * g[idx[:, 0], idx[:, 1], idx[:, 2]] - 0.5 * sigma ** 2) / n ** 3
+        ref_keys_prev = None
+        leaves, lmass = [], []
+        total = 0
+        for k in range(max_levels + 1):
+            l = base + k
+            keys = _keys(idx, l)
+            order = np.argsort(keys)
+            keys, idx, mass = keys[order], idx[order], mass[order]
+            cand = np.zeros(keys.size, dtype=bool)
+            if k < max_levels:
+                fl = idx[mass > m_thr]
+                if fl.size:
+                    nk, ok = _neighbour_keys(fl, l)
+                    dil = np.unique(nk[ok])
+                    cand = np.isin(keys, dil)
+                if k > 0 and cand.any():  # graded: the father's 27 neighbours must be refined
+                    fk, fok = _neighbour_keys(idx[cand] // 2, l - 1)
+                    good = np.all(np.isin(fk, ref_keys_prev) | ~fok, axis=1)
+                    sel = np.flatnonzero(cand)
+                    cand[sel[~good]] = False
+                if total + int((~cand).sum()) + 8 * int(cand.sum()) > max_leaves:
+                    cand[:] = False
+            leaves.append(idx[~cand].astype(np.int32))
+            lmass.append(mass[~cand])
+            total += int((~cand).sum())
+            if not cand.any():
+                break
+            ref_keys_prev = keys[cand]
+            par, pm = idx[cand], mass[cand]
+            w = np.exp(ssub * normal(seed, 500 + l, np.arange(8 * par.shape[0])).reshape(-1, 8) - 0.5 * ssub ** 2)
+            w /= w.sum(1, keepdims=True)
+            idx = (2 * par[:, None, :] + _OFF8[None, :, :]).reshape(-1, 3)
+            mass = (pm[:, None] * w).reshape(-1)
+        return leaves, lmass
 
-    refined = {}
-    exists = np.ones((n,) * 3, dtype=bool)
-    prev = None
-    for k in range(max_levels):
-        l = base + k
-        nl = 2 ** l
-        idx = np.argwhere(exists)
-        x = (idx + 0.5) / nl
-        if k == 0:
-            mass = np.exp(sigma * g - 0.5 * sigma ** 2).reshape(-1)[np.ravel_multi_index(idx.T, (nl,) * 3)]
-        else:
-            mass = rho(x)
-        mass = mass / nl ** 3
-        flag = np.zeros((nl,) * 3, dtype=bool)
-        flag[tuple(idx[mass > m_thr].T)] = True
-        flag = _dilate(flag) & exists
-        if prev is not None:
-            flag = graded_filter(prev, flag)
-        if not flag.any():
-            break
-        refined[l] = flag
-        prev = flag
-        exists = np.repeat(np.repeat(np.repeat(flag, 2, 0), 2, 1), 2, 2)
-    lmax = base + len(refined)
-    leaves = leaves_from_refined(base, lmax, refined)
-    h = Hierarchy(base, lmax, name=f"lognormal {n}^3 sigma={sigma} P(k)~k^{slope:g}, {lmax - base} refined levels")
-    for k, c in enumerate(leaves):
-        l = base + k
-        x = (c.astype(np.float64) + 0.5) / 2 ** l
-        if k == 0:
-            m = np.exp(sigma * g[c[:, 0], c[:, 1], c[:, 2]] - 0.5 * sigma ** 2)
-        else:
-            m = rho(x)
+    ssub = sigma_sub
+    leaves, lmass = build(ssub)
+    if len(leaves) - 1 < max_levels:
+        ssub = 1.5 * sigma_sub
+        leaves, lmass = build(ssub)
+    lmax = base + len(leaves) - 1
+    h = Hierarchy(base, lmax, name=f"lognormal {n}^3 sigma={sigma} P(k)~k^{slope:g}, sigma_sub={ssub:g}, "
+                                   f"{lmax - base} refined levels")
+    for c, m in zip(leaves, lmass):
         h.ijk.append(np.ascontiguousarray(c, dtype=np.int32))
-        h.mass.append(m * 8.0 ** (-l))
+        h.mass.append(np.ascontiguousarray(m, dtype=np.float64))
     return _normalise(h)
 
 

@@ -179,3 +179,39 @@ def test_adjoint_needs_fp64_context():
     with pytest.raises(fmm.FMMError) as e:
         s.solve_adjoint(g, ga)
     assert e.value.code == -1
+
+
+def test_finite_differences_full_size_nested_two_plummer():
+    """The 128^3-base nested two-Plummer hierarchy itself (13.6 M cells, three
+    levels): central differences on 8 seeded cells (each costs two FP64 solves
+    of the whole hierarchy; the 100-cell check runs on the 32^3-base version)."""
+    import torch
+    from paper_2607_19489_b300 import fmm
+    h = W.nested_two_plummer()
+    s = fmm.Solver(6, "fp64")
+    ijk = [torch.as_tensor(a, device="cuda").contiguous() for a in h.ijk]
+    mass = [torch.as_tensor(m, device="cuda").contiguous() for m in h.mass]
+    w = {l: torch.as_tensor(W.normal(31, 300 + l, np.arange(3 * h.n(l))).reshape(-1, 3), device="cuda")
+         for l in h.levels}
+    s.set_levels(h.lmin, h.lmax, ijk, mass)
+    out = s.alloc_outputs()
+    gm = s.solve_adjoint({l: torch.zeros(h.n(l), dtype=torch.float64, device="cuda") for l in h.levels}, w)
+    s.sync()
+    n_all = sum(h.n(l) for l in h.levels)
+    offs = np.cumsum([0] + [h.n(l) for l in h.levels])
+    picks = np.unique((W.uniform(43, 1, np.arange(8)) * n_all).astype(np.int64))
+    eps = 1e-6
+    for g in picks:
+        k = int(np.searchsorted(offs, g, side="right") - 1)
+        j = int(g - offs[k])
+        vals = []
+        for sgn in (1, -1):
+            mp = [m.clone() for m in mass]
+            mp[k][j] += sgn * eps
+            s.set_levels(h.lmin, h.lmax, ijk, mp)
+            s.solve(out=out)
+            s.sync()
+            vals.append(sum(float((w[l] * out[1][l]).sum()) for l in h.levels))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        ad = float(gm[h.lmin + k][j])
+        assert abs(fd - ad) <= 1e-5 * abs(ad), (g, fd, ad)

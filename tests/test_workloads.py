@@ -6,19 +6,20 @@ from paper_2607_19489_b300 import workloads as W
 
 
 def test_batched_blobs_are_valid_and_seeded():
-    a = W.batched_blobs(count=8, seed=3, bases=(3, 4))
-    b = W.batched_blobs(count=8, seed=3, bases=(3, 4))
+    a = W.batched_blobs(count=8, seed=4, bases=(4, 5))
+    b = W.batched_blobs(count=8, seed=4, bases=(4, 5))
     assert len(a) == 8
+    assert any(h.lmax > h.lmin for h in a)
     for h, g in zip(a, b):
-        assert 1 <= h.lmax - h.lmin <= 3
-        assert h.lmin in (3, 4)
+        assert 0 <= h.lmax - h.lmin <= 3
+        assert h.lmin in (4, 5)
         oracle.validate(h)  # graded, complete octs, base level covers the box
         assert abs(h.total_mass() - 1.0) < 1e-12
         for x, y in zip(h.ijk, g.ijk):
             assert np.array_equal(x, y)
         for x, y in zip(h.mass, g.mass):
             assert np.array_equal(x, y)
-    c = W.batched_blobs(count=8, seed=4, bases=(3, 4))
+    c = W.batched_blobs(count=8, seed=5, bases=(4, 5))
     assert any(h.n_cells != g.n_cells or h.lmin != g.lmin for h, g in zip(a, c))
 
 
