@@ -95,6 +95,15 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out);
 fmm_status fmm_set_levels(fmm_ctx* ctx, int lmin, int lmax, int lo, const int64_t* n,
                           const int32_t* const* ijk, const double* const* mass, void* stream);
 
+/* Replace the masses of levels lo..lmax of the current hierarchy, cells
+ * unchanged (a time step that moves mass but not the mesh).  mass[k]: double
+ * [n] for level lo+k in the order of the last fmm_set_levels of that level,
+ * device or host pointer, copied on `stream` before the call returns (host
+ * memory) or in stream order (device memory).  No tree rebuild and no
+ * synchronisation; the next solve recomputes what depends on these levels.
+ * The values are not validated (fmm_set_levels rejects non-finite masses). */
+fmm_status fmm_update_masses(fmm_ctx* ctx, int lo, const double* const* mass, void* stream);
+
 /* Solve for the leaf cells of levels lo..lmax (Alg. 1 for l = lo..lmax, which
  * share one upward and one downward pass: the far field of a box does not
  * depend on the target level).  phi[k] / accel[k] receive level lo+k in the

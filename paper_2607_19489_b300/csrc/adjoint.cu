@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_adj_l2p(int nc, const int32_t* __restri
         v += 0.5 * g[0] * T[0] + 0.25 * (g[1] * T[1] + g[2] * T[2] + g[3] * T[3]);
       }
     }
-    gL[((int64_t)O * 8 + c) * nc + beta] += v;
+    gL[((int64_t)blockIdx.x * 8 + c) * nc + beta] += v;  // rowsL position = slot
   }
 }
 
@@ -268,7 +268,8 @@ struct AdjGemmParams {
   int N, KQ, nc, mode;
   const int32_t* cc_b;   // M2P: cell_child of level b (the forward row's refined cells)
   const double* gacc;    // M2P: cotangent of the accumulator, level b+1 cells [cells][4]
-  const double* gL;      // M2L: cotangent of the local expansions of level b
+  const double* gL;      // M2L: cotangent of the local expansions of level b, by slot
+  const int32_t* slot;   // M2L: local-expansion slot of each oct (-1: none)
   double* gM;            // out: multipole cotangents of level b
 };
 
@@ -299,7 +300,8 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const __grid_constant__ AdjGem
             const int32_t ch = P.cc_b[(int64_t)R * 8 + (n >> 5)];  // n = (f*8 + t)*4 + comp
             if (ch >= 0) v = P.gacc[((int64_t)ch * 8 + ((n >> 2) & 7)) * 4 + (n & 3)];
           } else {
-            v = P.gL[(int64_t)R * 8 * P.nc + n];
+            const int32_t sl = P.slot[R];
+            if (sl >= 0) v = P.gL[(int64_t)sl * 8 * P.nc + n];
           }
         }
         As[r][nn] = v;
@@ -329,15 +331,17 @@ __global__ void __launch_bounds__(256) k_adj_gemm(const __grid_constant__ AdjGem
 // coefficient gamma) onto the parent cell's cotangent.
 __global__ void __launch_bounds__(128) k_adj_l2l(int nc, const int32_t* __restrict__ rowsL,
                                                  const int32_t* __restrict__ oct_parent,
+                                                 const int32_t* __restrict__ slot_up,
                                                  const double* __restrict__ gL, double* __restrict__ gLup,
                                                  const int* __restrict__ toff, const int* __restrict__ tb,
                                                  const int* __restrict__ te, const double* __restrict__ tc) {
   __shared__ double Sb[8][kNcMax];
   const int32_t o = rowsL[blockIdx.x];
+  const int64_t so = blockIdx.x;  // rowsL position = slot
   for (int b = threadIdx.x; b < nc; b += blockDim.x) {
     double x[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) x[c] = gL[((int64_t)o * 8 + c) * nc + b];
+    for (int c = 0; c < 8; ++c) x[c] = gL[(so * 8 + c) * nc + b];
 #pragma unroll
     for (int axis = 0; axis < 3; ++axis)  // S_e = sum_c sign(c, e) x_c
 #pragma unroll
@@ -351,11 +355,12 @@ __global__ void __launch_bounds__(128) k_adj_l2l(int nc, const int32_t* __restri
     for (int e = 0; e < 8; ++e) Sb[e][b] = x[e];
   }
   __syncthreads();
-  const int64_t par = oct_parent[o];
+  const int32_t par = oct_parent[o];
+  const int64_t sp = (int64_t)slot_up[par >> 3] * 8 + (par & 7);
   for (int g = threadIdx.x; g < nc; g += blockDim.x) {
     double v = 0;
     for (int j = toff[g]; j < toff[g + 1]; ++j) v += tc[j] * Sb[te[j]][tb[j]];
-    gLup[par * nc + g] += v;
+    gLup[sp * nc + g] += v;
   }
 }
 
@@ -558,6 +563,7 @@ void launch_adjoint(Ctx* c, int lo, const void* const* g_phi, const void* const*
       P.nc = nc;
       P.mode = kModeM2L;
       P.gL = (const double*)B.L.ptr;
+      P.slot = (const int32_t*)B.slotL.ptr;
       P.gM = (double*)B.M.ptr;
       ++c->n_launch;
       k_adj_gemm<<<dim3((unsigned)((B.n_srcL + ATM - 1) / ATM), (unsigned)((P.KQ + 255) / 256)), 256, 0, st>>>(P);
@@ -565,6 +571,7 @@ void launch_adjoint(Ctx* c, int lo, const void* const* g_phi, const void* const*
     if (b >= 3 && B.n_rowsL) {
       ++c->n_launch;
       k_adj_l2l<<<(unsigned)B.n_rowsL, 128, 0, st>>>(nc, (const int32_t*)B.rowsL.ptr, (const int32_t*)B.oct_parent.ptr,
+                                                     (const int32_t*)c->lev[b - 1].slotL.ptr,
                                                      (const double*)B.L.ptr, (double*)c->lev[b - 1].L.ptr,
                                                      (const int*)c->d_l2lT_off.ptr, (const int*)c->d_l2lT_b.ptr,
                                                      (const int*)c->d_l2lT_e.ptr, (const double*)c->d_l2lT_c.ptr);

@@ -182,8 +182,11 @@ fmm_status init_tables(Ctx* c) {
   return FMM_OK;
 }
 
-// Sizes every per-level array so that fmm_solve allocates nothing.
-fmm_status size_expansions(Ctx* c) {
+// Sizes every per-level array so that fmm_solve allocates nothing.  The local
+// expansions are stored per slot (octs that need one, known after the tree
+// build: size_locals); the buffers that are zero between solves (Lm, and acc
+// in the mixed path) are cleared when they are (re)allocated.
+fmm_status size_expansions(Ctx* c, cudaStream_t st) {
   const int nc = c->tab.nc;
   const bool f64 = c->cfg.precision == FMM_FP64;
   for (int l = 1; l <= c->lmax; ++l) {
@@ -198,11 +201,27 @@ fmm_status size_expansions(Ctx* c) {
         CKS(buf_ensure(c, T.Mlo, ncell * nc * 2));
       }
     }
-    if (l >= 2 && l <= c->lmax - 2) {
-      CKS(buf_ensure(c, T.L, ncell * nc * 8));
-      if (!f64) CKS(buf_ensure(c, T.Lm, ncell * nc * 4));
+    if (l >= c->lmin) {
+      void* old = T.acc.ptr;
+      CKS(buf_ensure(c, T.acc, ncell * 4 * (f64 ? 8 : 4)));
+      if (T.acc.ptr != old) CKS(cudaMemsetAsync(T.acc.ptr, 0, T.acc.bytes, st));
     }
-    if (l >= c->lmin) CKS(buf_ensure(c, T.acc, ncell * 4 * (f64 ? 8 : 4)));
+  }
+  return FMM_OK;
+}
+
+fmm_status size_locals(Ctx* c, cudaStream_t st) {
+  const int nc = c->tab.nc;
+  const bool f64 = c->cfg.precision == FMM_FP64;
+  for (int l = 2; l <= c->lmax - 2; ++l) {
+    LevelTree& T = c->lev[l];
+    const int64_t nrow = 8 * std::max<int64_t>(T.n_rowsL, 1);
+    CKS(buf_ensure(c, T.L, nrow * nc * 8));
+    if (!f64) {
+      void* old = T.Lm.ptr;
+      CKS(buf_ensure(c, T.Lm, nrow * nc * 4));
+      if (T.Lm.ptr != old) CKS(cudaMemsetAsync(T.Lm.ptr, 0, T.Lm.bytes, st));
+    }
   }
   return FMM_OK;
 }
@@ -455,13 +474,13 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
   }
   c->device = dev;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaMalloc(&c->d_err, 16);
+  cudaError_t e = cudaMalloc(&c->d_err, kErrWords * 4);
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;
   }
-  cudaMemset(c->d_err, 0, 16);
+  cudaMemset(c->d_err, 0, kErrWords * 4);
   for (auto& ev : c->ev) cudaEventCreate(&ev);
   fmm_status s = near_init(c);
   if (s == FMM_OK) s = acquire_tables(c);
@@ -476,7 +495,8 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
 // The tree build's device work as a
 // CUDA graph, captured once per (layout generation, levels, leaf counts).
 static fmm_status launch_tree_graph(Ctx* c, cudaStream_t st) {
-  std::vector<uintptr_t> key = {(uintptr_t)c->layout_gen, (uintptr_t)c->lmin, (uintptr_t)c->lmax};
+  std::vector<uintptr_t> key = {(uintptr_t)c->layout_gen, (uintptr_t)c->lmin, (uintptr_t)c->lmax,
+                                (uintptr_t)c->tree_lo, (uintptr_t)c->anc_req};
   for (int l = c->lmin; l <= c->lmax; ++l) key.push_back((uintptr_t)c->lev[l].n_leaf);
   Ctx::SolveGraph* g = nullptr;
   for (auto& e : c->tree_graphs)
@@ -554,18 +574,33 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
   while (eff > lmin && c->lev[eff].n_leaf == 0) --eff;
   c->lmax = eff;
   c->lmax_user = lmax;
+  // lo == lmin: a full build; lo > lmin: levels lo..lmax are re-sorted and the
+  // next solve recomputes only what depends on them (adaptive time stepping)
+  const bool full = lo == lmin;
+  c->tree_lo = full ? lmin : lo;
+  c->dirty_lo = full ? lmin : std::min(c->dirty_lo, lo);
+  c->anc_req = (c->dirty_lo > lmin && c->dirty_lo <= eff) ? c->dirty_lo : 0;
+  c->anc_d = 0;
   for (int l = eff + 1; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
     T.n_oct = T.n_rows = T.n_tgt = T.n_rowsL = T.n_irows = T.n_srcP = T.n_srcL = 0;
   }
   TRY(tree_prepare(c));
-  TRY(size_expansions(c));
+  TRY(size_expansions(c, st));
   if (c->use_graphs) {
     TRY(launch_tree_graph(c, st));
   } else {
     TRY(tree_enqueue(c, st));
   }
-  TRY(tree_finish(c, st));
+  {
+    fmm_status fs = tree_finish(c, st);
+    if (fs != FMM_OK) {
+      c->dirty_lo = lmin;
+      return fs;
+    }
+  }
+  c->anc_d = c->anc_req;
+  TRY(size_locals(c, st));
   {  // list lengths decide grid sizes: a change retires the cached solve graphs
     std::vector<int64_t> sig = {c->lmin, c->lmax};
     for (int l = 0; l <= c->lmax; ++l) {
@@ -585,33 +620,60 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
 static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* dacc, cudaStream_t st) {
   if (lo > c->lmax) return FMM_OK;  // only empty levels
   const bool f64 = c->cfg.precision == FMM_FP64;
+  const int lmin = c->lmin, lmax = c->lmax;
+  const int d = c->dirty_lo;  // lowest level changed since the last upward pass
   stage_event(c, 0, st);
-  // 1. upward: leaf monopoles, then M2M from the finest level up
-  for (int l = 1; l <= c->lmax; ++l) launch_mono_leaves(c, l, st);
-  for (int b = c->lmax - 1; b >= 1; --b) launch_upward(c, b, st);
+  // 1. upward: leaf monopoles, then M2M from the finest level up.  After an
+  // update of levels d..lmax only the cells with descendants at level d change
+  // (multipoles are totals over the finer levels): M2M runs on all octs of
+  // levels >= d and on the ancestor octs above; with no change it is skipped.
+  if (d <= lmin || (d <= lmax && c->anc_d != d)) {
+    for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
+    for (int b = lmax - 1; b >= 1; --b) launch_upward(c, b, st);
+  } else if (d <= lmax) {
+    for (int l = d; l <= lmax; ++l) launch_mono_leaves(c, l, st);
+    for (int b = lmax - 1; b >= d - 1; --b) launch_upward(c, b, st);
+    for (int b = d - 2; b >= 1; --b)
+      launch_upward(c, b, st, (const int32_t*)c->lev[b + 1].anc.ptr, c->lev[b + 1].n_anc);
+  }
   stage_event(c, 1, st);
-  // 2. downward over box levels 2..lmax-2: L = L2L(parent) + M2L
+  // 2. downward over box levels 2..lmax-2: L = L2L(parent) + M2L.  For targets
+  // at levels >= lo > lmin, the levels b <= lo-3 only feed the L2L chain of the
+  // ancestors of level lo: their ancestor lists replace the full row lists.
+  const bool restrict_dn = lo > lmin && c->anc_d == lo;
+  std::vector<const int32_t*> drows(lmax + 1, nullptr);
+  std::vector<int64_t> dn(lmax + 1, 0);
+  for (int b = 2; b <= lmax - 2; ++b)
+    if (restrict_dn && b <= lo - 3) {
+      drows[b] = (const int32_t*)c->lev[b].anc.ptr;
+      dn[b] = c->lev[b].n_anc;
+    }
   if (f64) {
-    for (int b = 2; b <= c->lmax - 2; ++b) {
-      launch_l2l_add(c, b, st);
-      launch_gemm_f64(c, c->op_m2l, kModeM2L, b, st);
+    for (int b = 2; b <= lmax - 2; ++b) {
+      if (drows[b] && !dn[b]) continue;
+      launch_l2l_add(c, b, st, drows[b], dn[b]);
+      launch_gemm_f64(c, c->op_m2l, kModeM2L, b, st, drows[b], dn[b]);
     }
-  } else if (c->lmax - 2 >= 2) {
+  } else if (lmax - 2 >= 2) {
     std::vector<int> lv;
-    for (int b = 2; b <= c->lmax - 2; ++b) {
-      CKS(cudaMemsetAsync(c->lev[b].Lm.ptr, 0, c->lev[b].Lm.bytes, st));
+    std::vector<const int32_t*> rv;
+    std::vector<int64_t> nv;
+    for (int b = 2; b <= lmax - 2; ++b) {
+      if (drows[b] && !dn[b]) continue;
       lv.push_back(b);
+      rv.push_back(drows[b]);
+      nv.push_back(dn[b]);
     }
-    launch_gemm_tc(c, c->op_m2l, kModeM2L, lv.data(), (int)lv.size(), st);  // all levels in one launch
-    for (int b = 2; b <= c->lmax - 2; ++b) launch_l2l_add(c, b, st);
+    if (!lv.empty())  // all levels in one launch
+      launch_gemm_tc(c, c->op_m2l, kModeM2L, lv.data(), (int)lv.size(), st, rv.data(), nv.data());
+    for (size_t i = 0; i < lv.size(); ++i) launch_l2l_add(c, lv[i], st, rv[i], nv[i]);
   }
   stage_event(c, 2, st);
   // 3a. bottom intermediate field, M2P from level l-1 cells
   {
     std::vector<int> lv;
-    for (int l = lo; l <= c->lmax; ++l) {
+    for (int l = lo; l <= lmax; ++l) {
       if (!c->lev[l].n_leaf) continue;
-      CKS(cudaMemsetAsync(c->lev[l].acc.ptr, 0, c->lev[l].acc.bytes, st));
       if (f64)
         launch_gemm_f64(c, c->op_m2p, kModeM2P, l - 1, st);
       else
@@ -630,7 +692,9 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
 // Replays the solve as a CUDA graph: captured once per (layout generation, lo,
 // output pointers) on the library's own stream, then launched on the caller's.
 static fmm_status launch_solve_graph(Ctx* c, int lo, void* const* dphi, void* const* dacc, cudaStream_t st) {
-  std::vector<uintptr_t> key = {(uintptr_t)c->layout_gen, (uintptr_t)lo};
+  // the ancestor lists differ per updated level: their lengths are part of the key
+  std::vector<uintptr_t> key = {(uintptr_t)c->layout_gen, (uintptr_t)lo, (uintptr_t)c->dirty_lo, (uintptr_t)c->anc_d};
+  for (int l = 1; l < c->anc_d; ++l) key.push_back((uintptr_t)c->lev[l].n_anc);
   for (int l = lo; l <= c->lmax; ++l) {
     key.push_back((uintptr_t)dphi[l]);
     key.push_back((uintptr_t)dacc[l]);
@@ -722,6 +786,7 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
   } else {
     TRY(launch_solve_graph(c, lo, dphi.data(), dacc.data(), st));
   }
+  c->dirty_lo = Ctx::kClean;  // every multipole now matches the current masses
   CKS(cudaGetLastError());
   for (int l = lo; l <= c->lmax; ++l)
     if (host_out[l]) {
@@ -760,7 +825,9 @@ fmm_status fmm_batch_solve(fmm_ctx* const* ctxs, int nctx, const int* lo, void* 
       }
     dphi[i].assign(std::max(c->lmax, lo[i]) + 1, nullptr);
     dacc[i].assign(std::max(c->lmax, lo[i]) + 1, nullptr);
-    key.insert(key.end(), {(uintptr_t)c, (uintptr_t)c->layout_gen, (uintptr_t)lo[i]});
+    key.insert(key.end(), {(uintptr_t)c, (uintptr_t)c->layout_gen, (uintptr_t)lo[i], (uintptr_t)c->dirty_lo,
+                           (uintptr_t)c->anc_d});
+    for (int l = 1; l < c->anc_d; ++l) key.push_back((uintptr_t)c->lev[l].n_anc);
     for (int l = lo[i]; l <= c->lmax; ++l) {
       if (!c->lev[l].n_leaf) continue;
       void* pp = phi[i][l - lo[i]];
@@ -846,6 +913,7 @@ fmm_status fmm_batch_solve(fmm_ctx* const* ctxs, int nctx, const int* lo, void* 
     g->ctxs[i]->n_launch += g->launches[i];
     ++g->ctxs[i]->n_solve;
     g->ctxs[i]->last_stream = st;
+    g->ctxs[i]->dirty_lo = Ctx::kClean;
   }
   return FMM_OK;
 }
@@ -879,12 +947,15 @@ fmm_status fmm_autotune(fmm_ctx* c, int lo, void* stream) {
   }
   const bool timing = c->timing;
   c->timing = false;
+  const int anc_d = c->anc_d;
+  c->anc_d = 0;  // time the full passes
   cudaEvent_t e0, e1;
   CKS(cudaEventCreate(&e0));
   CKS(cudaEventCreate(&e1));
   auto measure = [&](float& best) -> fmm_status {
     best = 1e30f;
     for (int r = 0; r < 4; ++r) {
+      c->dirty_lo = c->lmin;
       CKS(cudaEventRecord(e0, st));
       TRY(enqueue_solve(c, lo, dphi.data(), dacc.data(), st));
       CKS(cudaEventRecord(e1, st));
@@ -924,6 +995,8 @@ fmm_status fmm_autotune(fmm_ctx* c, int lo, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->timing = timing;
+  c->anc_d = anc_d;
+  c->dirty_lo = s == FMM_OK ? Ctx::kClean : c->lmin;
   ++c->layout_gen;  // cached graphs carry the old launch shapes
   if (s == FMM_OK) s = fmm_sync(c);
   return s;
@@ -1001,15 +1074,36 @@ fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const
     LevelTree& T = c->lev[l];
     if (T.n_leaf) CKS(cudaMemsetAsync(T.gmass.ptr, 0, T.n_leaf * 8, st));
     if (l < lmax) CKS(cudaMemsetAsync(T.M.ptr, 0, 8 * T.n_oct * c->tab.nc * 8, st));
-    if (l >= 2 && l <= lmax - 2) CKS(cudaMemsetAsync(T.L.ptr, 0, 8 * T.n_oct * c->tab.nc * 8, st));
+    if (l >= 2 && l <= lmax - 2)
+      CKS(cudaMemsetAsync(T.L.ptr, 0, 8 * std::max<int64_t>(T.n_rowsL, 1) * c->tab.nc * 8, st));
     if (l >= lmin) CKS(cudaMemsetAsync(T.acc.ptr, 0, 8 * T.n_oct * 4 * 8, st));
   }
   launch_adjoint(c, lo, dphi.data() + lo, dacc.data() + lo, c->cfg.out_fp32, st);
+  c->dirty_lo = lmin;  // the expansion arrays now hold cotangents
   CKS(cudaGetLastError());
   for (int l = lmin; l <= lmax; ++l) {
     const int64_t nl = c->lev[l].n_leaf;
     if (nl) CKS(cudaMemcpyAsync(g_mass[l - lmin], c->lev[l].gmass.ptr, nl * 8, cudaMemcpyDefault, st));
   }
+  return FMM_OK;
+}
+
+fmm_status fmm_update_masses(fmm_ctx* c, int lo, const double* const* mass, void* stream) {
+  if (!c || !mass) return FMM_ERR_ARG;
+  if (!c->have_levels) {
+    c->last_error = "fmm_update_masses before fmm_set_levels";
+    return FMM_ERR_STATE;
+  }
+  if (lo < c->lmin || lo > c->lmax_user) return FMM_ERR_ARG;
+  for (int l = lo; l <= c->lmax; ++l)
+    if (c->lev[l].n_leaf && !mass[l - lo]) return FMM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  for (int l = lo; l <= c->lmax; ++l) {
+    const int64_t nl = c->lev[l].n_leaf;
+    if (nl) CKS(cudaMemcpyAsync(c->lev[l].mass.ptr, mass[l - lo], nl * 8, cudaMemcpyDefault, st));
+  }
+  c->dirty_lo = std::min(c->dirty_lo, lo);
   return FMM_OK;
 }
 
@@ -1028,6 +1122,15 @@ fmm_status fmm_sync(fmm_ctx* c) {
   if (e & kErrTimeout) {
     c->last_error = "a bounded device-side wait timed out";
     cudaMemset(c->d_err, 0, 4);
+    // an interrupted solve may leave partial sums behind: restore the cleared
+    // accumulators and recompute every multipole next time
+    if (c->have_levels) {
+      for (int l = c->lmin; l <= c->lmax; ++l)
+        if (c->lev[l].acc.ptr) cudaMemset(c->lev[l].acc.ptr, 0, c->lev[l].acc.bytes);
+      for (int l = 2; l <= c->lmax - 2; ++l)
+        if (c->lev[l].Lm.ptr) cudaMemset(c->lev[l].Lm.ptr, 0, c->lev[l].Lm.bytes);
+      c->dirty_lo = c->lmin;
+    }
     return FMM_ERR_TIMEOUT;
   }
   return FMM_OK;
@@ -1041,7 +1144,7 @@ void fmm_destroy(fmm_ctx* c) {
   drop_batch_graphs_of(c);
   release_tables(c);
   for (auto& T : c->lev) {
-    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.tgt, &T.ijk,
+    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.ancflag, &T.tgt, &T.ijk,
                       &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lm, &T.acc})
       buf_free(c, *b);
   }

@@ -23,7 +23,11 @@ enum : unsigned {
   kErrIncomplete = 8u,
   kErrNonFinite = 16u,
   kErrTimeout = 32u,
+  kErrStructure = 64u,  // a partial update changed the cells of its lowest level
 };
+// Device error words: [0] solves (timeouts), [1 + l] the tree build of level l
+// (the finest level with an error names the cause: errors propagate upwards).
+constexpr int kErrWords = kMaxLevel + 2;
 
 // Sign of prod_{i: e_i = 1} s_i for child c, s_i = +1 if bit i of c is set
 // (child in the upper half along axis i) else -1.
@@ -58,10 +62,15 @@ struct LevelTree {
   DevBuf rowsL;          // int32 [n_rowsL]
   DevBuf irows;          // int32 [n_irows]
   DevBuf leafmask;       // uint8 [n_oct]: bit c set when cell c of the oct is a leaf
+  DevBuf slotL;          // int32 [n_oct]: position of the oct in rowsL (its local-expansion
+                         // slot), -1 if it has none
   // adjoint (FP64): mass cotangents and the octs read by the contractions
   DevBuf gmass;          // double [n_leaf]
   DevBuf srcP, srcL;     // int32: octs read by M2P rows / by M2L rows of this level
   int64_t n_srcP = 0, n_srcL = 0;
+  // incremental solves: octs with a descendant at level Ctx::anc_d (ancestor lists)
+  DevBuf anc, ancflag;   // int32 [n_anc], uint8 [n_oct]
+  int64_t n_anc = 0;
   // inputs kept for adaptive time stepping (replaced by set_levels)
   DevBuf ijk;            // int32 [n_leaf][3]
   DevBuf mass;           // double [n_leaf]
@@ -70,9 +79,11 @@ struct LevelTree {
                          // refined cells and of the leaves in interface octs (irows)
   DevBuf Mhi, Mlo;       // bf16 [8 n_oct][nc] (mixed path GEMM operands)
   DevBuf mono;           // [8 n_oct] total mass per cell (double or float)
-  DevBuf L;              // double [8 n_oct][nc] local expansions (levels 2..lmax-2)
-  DevBuf Lm;             // float [8 n_oct][nc] this level's M2L sum (mixed path)
-  DevBuf acc;            // [8 n_oct][4] M2P result (double or float), targets of this level
+  DevBuf L;              // double [8 n_rowsL][nc] local expansions (levels 2..lmax-2), by slot
+  DevBuf Lm;             // float [8 n_rowsL][nc] this level's M2L sum (mixed path), by slot;
+                         // zero between solves (the L2L step clears what it consumes)
+  DevBuf acc;            // [8 n_oct][4] M2P result (double or float), targets of this level;
+                         // mixed path: zero between solves (the near field clears what it reads)
   bool m_is_f64 = true;
 };
 
@@ -132,7 +143,16 @@ struct Ctx {
   DevBuf d_m2mT_off, d_m2mT_a, d_m2mT_c, d_l2lT_off, d_l2lT_b, d_l2lT_e, d_l2lT_c, d_m2pT, d_m2lT;
   bool adj_tables = false;
   uint64_t adj_gen = 0;  // tree build + clearing, keyed by layout and leaf counts
-  unsigned tree_host_err = 0;
+  unsigned tree_host_err[kMaxLevel + 1] = {};
+  // Incremental updates (adaptive time stepping).  tree_lo: lowest level the
+  // current tree build re-sorts (lmin: all).  dirty_lo: lowest level whose
+  // masses or cells changed since the last upward pass (kClean: none).  anc_d:
+  // the level whose ancestor lists exist (0: none); anc_req: requested of the
+  // tree build in progress.
+  static constexpr int kClean = 1 << 20;
+  int tree_lo = 0;
+  int dirty_lo = kClean;
+  int anc_d = 0, anc_req = 0;
   uint64_t layout_gen = 1;
   std::vector<int64_t> count_sig;
   cudaStream_t cap_stream = nullptr;
@@ -152,13 +172,17 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st);  // device work, capturable
 fmm_status tree_finish(Ctx* c, cudaStream_t st);   // the one synchronisation
 // upward.cu
 void launch_mono_leaves(Ctx* c, int level, cudaStream_t st);
-void launch_upward(Ctx* c, int level, cudaStream_t st);
-void launch_l2l_add(Ctx* c, int level, cudaStream_t st);
+// octs / rows: optional lists restricting the pass (null: the full level)
+void launch_upward(Ctx* c, int level, cudaStream_t st, const int32_t* octs = nullptr, int64_t n_octs = 0);
+void launch_l2l_add(Ctx* c, int level, cudaStream_t st, const int32_t* rows = nullptr, int64_t nrows = 0);
 // gemm_f64.cu
-void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st);
+void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st,
+                     const int32_t* rows = nullptr, int64_t nrows = 0);
 // gemm_tc.cu
 fmm_status make_tensor_maps(Ctx* c, GemmOperand& op);
-void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* row_levels, int nlev, cudaStream_t st);
+// rows[i] / nrows[i]: optional per-level row lists (null: the level's full list)
+void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* row_levels, int nlev, cudaStream_t st,
+                    const int32_t* const* rows = nullptr, const int64_t* nrows = nullptr);
 // near.cu
 fmm_status near_init(Ctx* c);
 void launch_near_m2p(Ctx* c, int lo, cudaStream_t st);

@@ -30,7 +30,8 @@ struct F64Params {
   int mode;
   double* acc;              // M2P: [cells of level l][4]
   const int32_t* cell_child_rows;
-  double* L;                // M2L: [cells][nc]
+  double* L;                // M2L: [slot*8 + cell][nc]
+  const int32_t* slot;      // M2L: local-expansion slot of each oct
 };
 
 __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
@@ -90,21 +91,23 @@ __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
       if (ch >= 0) P.acc[((int64_t)ch * 8 + t) * 4 + comp] = acc[r];
     } else {
       int b = n / P.nc, beta = n - b * P.nc;
-      P.L[((int64_t)o * 8 + b) * P.nc + beta] += acc[r];
+      P.L[((int64_t)P.slot[o] * 8 + b) * P.nc + beta] += acc[r];
     }
   }
 }
 
 }  // namespace
 
-void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream_t st) {
+void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream_t st, const int32_t* rows,
+                     int64_t nrows) {
   LevelTree& R = c->lev[lr];
   // M2P: octs with a refined cell; M2L: octs with a cell that has grandchildren
-  const int64_t nr = (mode == kModeM2P) ? R.n_rows : R.n_rowsL;
+  const int64_t nr = rows ? nrows : ((mode == kModeM2P) ? R.n_rows : R.n_rowsL);
   if (!nr) return;
   F64Params P;
   P.M = (const double*)R.M.ptr;
-  P.rows = (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
+  P.rows = rows ? rows : (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
+  P.slot = (const int32_t*)R.slotL.ptr;
   P.nrows = nr;
   P.nbr = (const int32_t*)R.nbr.ptr;
   P.B = (const double*)op.f64.ptr;

@@ -43,7 +43,9 @@ struct TcSeg {
   const int32_t* rows;
   const int32_t* nbr;
   const int32_t* cell_child_rows;  // M2P: cell_child of the row level
-  float* out;                      // M2P: [cells of target level][4]; M2L: [cells][nc]
+  const int32_t* cell_child_tgt;   // M2P: cell_child of the target level (refined targets get nothing)
+  const int32_t* slot;             // M2L: local-expansion slot of each row oct
+  float* out;                      // M2P: [cells of target level][4]; M2L: [slot*8 + cell][nc]
   int nrows;
   int tile0;                       // first M tile of this segment
 };
@@ -257,15 +259,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int32_t ch = S.cell_child_rows[(int64_t)roct * 8 + f];
         if (ch >= 0) {
           float* dst = S.out + (int64_t)ch * 32;
+          const int32_t* cct = S.cell_child_tgt + (int64_t)ch * 8;
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * u), "f"(__uint_as_float(v[4 * u])),
-                         "f"(__uint_as_float(v[4 * u + 1])), "f"(__uint_as_float(v[4 * u + 2])),
-                         "f"(__uint_as_float(v[4 * u + 3]))
-                         : "memory");
+            if (cct[u] < 0)  // leaf targets only: the accumulator of refined cells stays zero
+              asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * u),
+                           "f"(__uint_as_float(v[4 * u])), "f"(__uint_as_float(v[4 * u + 1])),
+                           "f"(__uint_as_float(v[4 * u + 2])), "f"(__uint_as_float(v[4 * u + 3]))
+                           : "memory");
         }
       } else {
-        float* dst = S.out + (int64_t)roct * 8 * P.nc + n0;
+        float* dst = S.out + (int64_t)S.slot[roct] * 8 * P.nc + n0;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (n0 + 4 * u < P.N)
@@ -395,7 +399,8 @@ fmm_status make_tensor_maps(Ctx* c, GemmOperand& op) {
   return FMM_OK;
 }
 
-void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, int nlev, cudaStream_t st) {
+void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, int nlev, cudaStream_t st,
+                    const int32_t* const* rows, const int64_t* nrows) {
   TcParams P;
   int tiles = 0;
   P.nseg = 0;
@@ -404,12 +409,14 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
     LevelTree& R = c->lev[lr];
     // M2P: octs with a refined cell (their children hold the targets);
     // M2L: octs with a cell that has grandchildren (those need a local expansion)
-    const int64_t nr = (mode == kModeM2P) ? R.n_rows : R.n_rowsL;
+    const int64_t nr = (rows && rows[i]) ? nrows[i] : ((mode == kModeM2P) ? R.n_rows : R.n_rowsL);
     if (!nr) continue;
     TcSeg& S = P.seg[P.nseg++];
     S.Ahi = (const __nv_bfloat16*)R.Mhi.ptr;
     S.Alo = (const __nv_bfloat16*)R.Mlo.ptr;
-    S.rows = (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
+    S.rows = (rows && rows[i]) ? rows[i] : (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
+    S.cell_child_tgt = (mode == kModeM2P) ? (const int32_t*)c->lev[lr + 1].cell_child.ptr : nullptr;
+    S.slot = (const int32_t*)R.slotL.ptr;
     S.nbr = (const int32_t*)R.nbr.ptr;
     S.cell_child_rows = (const int32_t*)R.cell_child.ptr;
     S.out = (mode == kModeM2P) ? (float*)c->lev[lr + 1].acc.ptr : (float*)R.Lm.ptr;

@@ -77,8 +77,9 @@ struct NearSeg {
   const void* mono_l;         // level l
   const void* mono_dn;        // level l+1
   const void* M_l;            // multipoles of level l cells
-  const double* L2;           // local expansions of level l-2 (or null)
-  const void* acc;            // M2P results for level l cells [cells][4]
+  const double* L2;           // local expansions of level l-2 (or null), by slot
+  const int32_t* slot2;       // local-expansion slot of each level l-2 oct
+  void* acc;                  // M2P results for level l cells [cells][4]; cleared after reading
   void* phi;
   void* accel;
   double s1, s2;              // G / h and G / h^2, h the cell size of level l
@@ -141,7 +142,8 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     }
     if (S.L2) {
       const int32_t G2 = S.par_up[S.par_l[o] >> 3];
-      for (int b = tp; b < P.nc; b += 8) s_L[g][b] = (T)S.L2[(int64_t)G2 * P.nc + b];
+      const int64_t sl = (int64_t)S.slot2[G2 >> 3] * 8 + (G2 & 7);
+      for (int b = tp; b < P.nc; b += 8) s_L[g][b] = (T)S.L2[sl * P.nc + b];
     }
   }
   __syncthreads();
@@ -216,8 +218,13 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     // refined cells not touching t: M2P, done beforehand by k_near_m2p into acc
   }
   // ---- bottom intermediate field (M2P, level l-1 units) and far field (L2P, level l-2 units)
-  const T* acc = (const T*)S.acc;
+  T* acc = (T*)S.acc;
   T pm = acc[cell * 4], xm = acc[cell * 4 + 1], ym = acc[cell * 4 + 2], zm = acc[cell * 4 + 3];
+  // the accumulator is zero between solves: the contractions add into it next time
+  acc[cell * 4] = (T)0;
+  acc[cell * 4 + 1] = (T)0;
+  acc[cell * 4 + 2] = (T)0;
+  acc[cell * 4 + 3] = (T)0;
   T pl = 0, xl = 0, yl = 0, zl = 0;
   if (S.L2) {
     // phi = sum_beta L_beta rho^beta / beta!, grad_i = sum_gamma L_{gamma+e_i} rho^gamma / gamma!,
@@ -497,6 +504,7 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
       S.M_l = T.M.ptr;
       S.M_l_f64 = T.m_is_f64 ? 1 : 0;
       S.L2 = (l - 2 >= 2) ? (const double*)c->lev[l - 2].L.ptr : nullptr;
+      S.slot2 = (l - 2 >= 2) ? (const int32_t*)c->lev[l - 2].slotL.ptr : nullptr;
       S.acc = T.acc.ptr;
       S.phi = phi[l - lo];
       S.accel = accel[l - lo];

@@ -203,6 +203,7 @@ extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n
     LevelTree& T = view[k];
     set_buf(T.rows, V.iota, T.n_oct * 4);
     set_buf(T.rowsL, V.iota, T.n_oct * 4);
+    set_buf(T.slotL, V.iota, T.n_oct * 4);  // every oct of a complete grid has its own slot
     set_buf(T.tgt, V.iota, T.n_oct * 4);
   }
 

@@ -20,6 +20,7 @@
 // bits, every kernel bounds-checks the indices it follows, and one
 // synchronisation at the end reads the error word and the list lengths.
 #include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
 
 #include "fmm_internal.cuh"
 
@@ -73,10 +74,12 @@ __global__ void k_oct_flags(int64_t n, const uint64_t* __restrict__ k, int32_t* 
 // Cell id = sorted position.  A level is consistent only if every run of
 // siblings is a complete oct, i.e. position == 8 * oct + (key & 7) everywhere
 // and the number of octs equals the count derived from the leaf counts.
+// check_keys: a partial update re-sorts this level but must not change its
+// octs; their keys are compared with the stored ones instead of written.
 __global__ void k_scatter_level(int64_t n, int64_t n_oct, const uint64_t* __restrict__ k,
                                 const int32_t* __restrict__ v, const int32_t* __restrict__ scan, uint64_t* oct_key,
                                 int32_t* cell_child, int32_t* leaf_cell, int32_t* oct_parent_next,
-                                int64_t n_oct_next, int64_t n_leaf, unsigned* err) {
+                                int64_t n_oct_next, int64_t n_leaf, int check_keys, unsigned* err) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t oct = scan[i] - 1;
@@ -86,7 +89,12 @@ __global__ void k_scatter_level(int64_t n, int64_t n_oct, const uint64_t* __rest
     atomicOr(err, kErrIncomplete);
     return;
   }
-  if (i == 0 || (k[i - 1] >> 3) != (key >> 3)) oct_key[oct] = key >> 3;
+  if (i == 0 || (k[i - 1] >> 3) != (key >> 3)) {
+    if (!check_keys)
+      oct_key[oct] = key >> 3;
+    else if (oct_key[oct] != key >> 3)
+      atomicOr(err, kErrStructure);
+  }
   int32_t val = v[i];
   cell_child[i] = val;
   if (val >= 0) {
@@ -185,6 +193,7 @@ struct ListLevel {
   const int32_t* nbr;
   int32_t* out[4];  // rows, tgt, rowsL, irows
   uint8_t* leafmask;
+  int32_t* slotL;    // [n_oct]: position in rowsL or -1
   int want_rowsL, want_irows;
 };
 
@@ -227,7 +236,10 @@ __global__ void __launch_bounds__(kListBlock) k_lists_count(const __grid_constan
   const ListLevel& L = P.lev[list_level(P, blk)];
   const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
   unsigned f = 0;
-  if (o < L.n_oct) f = oct_list_flags(L, o, L.leafmask + o);
+  if (o < L.n_oct) {
+    f = oct_list_flags(L, o, L.leafmask + o);
+    L.slotL[o] = -1;
+  }
   flags[blk * kListBlock + threadIdx.x] = (uint8_t)f;
   for (int k = 0; k < 4; ++k) {
     const int n = __syncthreads_count((f >> k) & 1);
@@ -292,7 +304,22 @@ __global__ void __launch_bounds__(kListBlock) k_lists_write(const __grid_constan
     int32_t pos = blk_off[blk * 4 + k] + __popc(ball[k] & ((1u << lane) - 1));
     for (int w = 0; w < warp; ++w) pos += warp_cnt[w][k];
     L.out[k][pos] = (int32_t)o;
+    if (k == 2) L.slotL[o] = pos;
   }
+}
+
+// Octs of level b with a descendant at level d: for b = d-1 the octs holding a
+// refined cell, above that the octs with a cell whose child oct is flagged.
+__global__ void k_anc_flags(int64_t n_oct, const int32_t* __restrict__ cc, const uint8_t* __restrict__ next,
+                            int64_t n_next, uint8_t* __restrict__ out) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= n_oct) return;
+  uint8_t f = 0;
+  for (int c = 0; c < 8; ++c) {
+    const int32_t ch = cc[o * 8 + c];
+    if (ch >= 0 && ch < n_next) f |= next ? next[ch] : (uint8_t)1;
+  }
+  out[o] = f;
 }
 
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
@@ -312,6 +339,7 @@ fmm_status err_to_status(unsigned e) {
   if (e & kErrDuplicate) return FMM_ERR_DUPLICATE;
   if (e & kErrIncomplete) return FMM_ERR_INCOMPLETE;
   if (e & kErrNotGraded) return FMM_ERR_NOT_GRADED;
+  if (e & kErrStructure) return FMM_ERR_STATE;
   if (e & kErrTimeout) return FMM_ERR_TIMEOUT;
   return FMM_OK;
 }
@@ -320,26 +348,41 @@ fmm_status err_to_status(unsigned e) {
 
 fmm_status tree_prepare(Ctx* c) {
   const int lmin = c->lmin, lmax = c->lmax;
+  const int lo = c->tree_lo;  // lmin: full build; above: levels lo..lmax only
   // ---- oct counts from the leaf counts ----------------------------------------
   // An inconsistent count is latched, not returned at once: the device checks
   // below may name the cause (a duplicate, an out-of-box index) more precisely.
-  unsigned& host_err = c->tree_host_err;
-  host_err = 0;
-  for (int l = lmax; l >= lmin; --l) {
+  unsigned* host_err = c->tree_host_err;
+  for (int l = 0; l <= kMaxLevel; ++l) host_err[l] = 0;
+  bool any_host = false;
+  const int64_t old_lo_octs = c->lev[lo].n_oct;
+  for (int l = lmax; l >= lo; --l) {
     const int64_t n = c->lev[l].n_leaf + ((l < lmax) ? c->lev[l + 1].n_oct : 0);
     if (n == 0 || n > (int64_t)INT32_MAX / 2) {
       c->last_error = "tree: level " + std::to_string(l) + " has no cells or too many";
       return n == 0 ? FMM_ERR_INCOMPLETE : FMM_ERR_ARG;
     }
-    if (n % 8) host_err |= kErrIncomplete;
+    if (n % 8) {
+      host_err[l] |= kErrIncomplete;
+      any_host = true;
+    }
     c->lev[l].n_oct = (n + 7) / 8;
   }
-  if (c->lev[lmin].n_oct != (int64_t)1 << (3 * (lmin - 1))) host_err |= kErrIncomplete;
-  for (int l = 1; l < lmin; ++l) {
-    c->lev[l].n_oct = (int64_t)1 << (3 * (l - 1));
-    c->lev[l].n_leaf = 0;
+  if (lo > lmin) {
+    if (c->lev[lo].n_oct != old_lo_octs || any_host) {
+      c->last_error = "tree: a partial update (lo = " + std::to_string(lo) +
+                      ") must keep the cells of level lo; update from lo - 1 instead";
+      c->lev[lo].n_oct = old_lo_octs;
+      return FMM_ERR_STATE;
+    }
+  } else {
+    if (c->lev[lmin].n_oct != (int64_t)1 << (3 * (lmin - 1))) host_err[lmin] |= kErrIncomplete;
+    for (int l = 1; l < lmin; ++l) {
+      c->lev[l].n_oct = (int64_t)1 << (3 * (l - 1));
+      c->lev[l].n_leaf = 0;
+    }
+    c->lev[0].n_oct = 0;
   }
-  c->lev[0].n_oct = 0;
   // ---- size everything ----------------------------------------------------------
   int64_t nmax = 0;
   for (int l = 1; l <= lmax; ++l) {
@@ -355,6 +398,9 @@ fmm_status tree_prepare(Ctx* c) {
     CK(buf_ensure(c, T.rowsL, T.n_oct * 4));
     CK(buf_ensure(c, T.irows, T.n_oct * 4));
     CK(buf_ensure(c, T.leafmask, T.n_oct));
+    CK(buf_ensure(c, T.slotL, T.n_oct * 4));
+    CK(buf_ensure(c, T.anc, T.n_oct * 4));
+    CK(buf_ensure(c, T.ancflag, T.n_oct));
   }
   CK(buf_ensure(c, c->lev[0].cell_child, 32));
   CK(buf_ensure(c, c->keys_a, nmax * 8));
@@ -365,11 +411,18 @@ fmm_status tree_prepare(Ctx* c) {
   for (int l = 1; l <= lmax; ++l) list_blocks += (c->lev[l].n_oct + kListBlock - 1) / kListBlock;
   CK(buf_ensure(c, c->flags, std::max<int64_t>(nmax * 8, list_blocks * kListBlock)));
   CK(buf_ensure(c, c->scan, std::max<int64_t>(nmax * 4, list_blocks * 32)));
-  CK(buf_ensure(c, c->counter, 4 * 4 * (lmax + 2)));
-  // CUB temporary storage for the largest sort and scan of this hierarchy
+  CK(buf_ensure(c, c->counter, 5 * 4 * (lmax + 2)));
+  // CUB temporary storage for the largest sort, scan and select of this build
   size_t tmp_max = 0;
   {
-    for (int l = lmin; l <= lmax; ++l) {
+    int64_t omax = 1;
+    for (int l = 1; l <= lmax; ++l) omax = std::max<int64_t>(omax, c->lev[l].n_oct);
+    size_t t = 0;
+    thrust::counting_iterator<int32_t> it(0);
+    CK(cub::DeviceSelect::Flagged(nullptr, t, it, (const uint8_t*)nullptr, (int32_t*)nullptr, (int32_t*)nullptr,
+                                  (int)omax));
+    tmp_max = t;
+    for (int l = lo; l <= lmax; ++l) {
       const int n = (int)(8 * c->lev[l].n_oct);
       size_t t = 0;
       CK(cub::DeviceRadixSort::SortPairs(nullptr, t, (uint64_t*)nullptr, (uint64_t*)nullptr, (int32_t*)nullptr,
@@ -388,13 +441,16 @@ fmm_status tree_prepare(Ctx* c) {
 // synchronisation, so it can be captured in a CUDA graph.
 fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
   const int lmin = c->lmin, lmax = c->lmax;
-  unsigned* err = c->d_err;
-  int32_t* d_counts = (int32_t*)c->counter.ptr;  // [4][lmax+2]: rows, tgt, rowsL, irows
-  CK(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
-  CK(cudaMemsetAsync(d_counts, 0, 4 * 4 * (lmax + 2), st));
-  // ---- bottom-up sorted passes, levels lmax..lmin -------------------------
-  for (int l = lmax; l >= lmin; --l) {
+  const int lo = c->tree_lo;
+  const bool partial = lo > lmin;
+  unsigned* err0 = c->d_err + 1;  // err0[l]: errors found while building level l
+  int32_t* d_counts = (int32_t*)c->counter.ptr;  // [5][lmax+2]: rows, tgt, rowsL, irows, anc
+  CK(cudaMemsetAsync(err0, 0, (kErrWords - 1) * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(d_counts, 0, 5 * 4 * (lmax + 2), st));
+  // ---- bottom-up sorted passes, levels lmax..lo -----------------------------
+  for (int l = lmax; l >= lo; --l) {
     LevelTree& T = c->lev[l];
+    unsigned* err = err0 + l;
     const int64_t n_ref = (l < lmax) ? c->lev[l + 1].n_oct : 0;
     const int64_t n = T.n_leaf + n_ref;
     uint64_t* ka = (uint64_t*)c->keys_a.ptr;
@@ -425,28 +481,29 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     ++c->n_launch;
     k_scatter_level<<<nblk(n), 256, 0, st>>>(n, T.n_oct, kb, vb, scan, (uint64_t*)T.oct_key.ptr,
                                              (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next,
-                                             n_ref, T.n_leaf, err);
+                                             n_ref, T.n_leaf, partial && l == lo, err);
   }
   // ---- complete grids below lmin and the root ------------------------------
-  for (int l = 1; l < lmin; ++l) {
+  for (int l = 1; l < lmin && !partial; ++l) {
     LevelTree& T = c->lev[l];
     ++c->n_launch;
     k_full_level<<<nblk(8 * T.n_oct), 256, 0, st>>>(T.n_oct, (uint64_t*)T.oct_key.ptr,
                                                      (int32_t*)T.oct_parent.ptr, (int32_t*)T.cell_child.ptr);
   }
-  // octs of level lmin: their parents are the complete grid of level lmin-1
-  ++c->n_launch;
-  k_iota<<<nblk(c->lev[lmin].n_oct), 256, 0, st>>>(c->lev[lmin].n_oct, (int32_t*)c->lev[lmin].oct_parent.ptr);
-  CK(cudaMemsetAsync(c->lev[0].cell_child.ptr, 0, 4, st));
-  // ---- neighbour tables top-down -------------------------------------------
-  for (int l = 1; l <= lmax; ++l) {
+  if (!partial) {  // octs of level lmin: their parents are the complete grid of level lmin-1
+    ++c->n_launch;
+    k_iota<<<nblk(c->lev[lmin].n_oct), 256, 0, st>>>(c->lev[lmin].n_oct, (int32_t*)c->lev[lmin].oct_parent.ptr);
+    CK(cudaMemsetAsync(c->lev[0].cell_child.ptr, 0, 4, st));
+  }
+  // ---- neighbour tables top-down (levels below lo are unchanged) --------------
+  for (int l = partial ? lo : 1; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
     const int32_t* nbr_up = (l >= 2) ? (const int32_t*)c->lev[l - 1].nbr.ptr : nullptr;
     const int32_t* cc_up = (const int32_t*)c->lev[l - 1].cell_child.ptr;
     const int64_t n_up = (l >= 2) ? c->lev[l - 1].n_oct : 1;
     ++c->n_launch;
     k_nbr<<<nblk(T.n_oct * 27), 256, 0, st>>>(l, T.n_oct, n_up, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
-                                              (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr, err);
+                                              (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr, err0 + l);
   }
   // ---- row lists ------------------------------------------------------------
   {
@@ -470,6 +527,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
       L.out[2] = (int32_t*)T.rowsL.ptr;
       L.out[3] = (int32_t*)T.irows.ptr;
       L.leafmask = (uint8_t*)T.leafmask.ptr;
+      L.slotL = (int32_t*)T.slotL.ptr;
       L.want_rowsL = l + 2 <= lmax;
       L.want_irows = l >= lmin;
       nb += (T.n_oct + kListBlock - 1) / kListBlock;
@@ -483,26 +541,47 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     k_lists_scan<<<(unsigned)(4 * P.nlev), 1024, 0, st>>>(P, blk_counts, blk_off, d_counts);
     k_lists_write<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_off);
   }
+  // ---- ancestor lists of level anc_req (incremental solves) ------------------------
+  const int d = c->anc_req;
+  if (d > lmin && d <= lmax) {
+    thrust::counting_iterator<int32_t> it(0);
+    for (int b = d - 1; b >= 1; --b) {
+      LevelTree& B = c->lev[b];
+      ++c->n_launch;
+      k_anc_flags<<<nblk(B.n_oct), 256, 0, st>>>(B.n_oct, (const int32_t*)B.cell_child.ptr,
+                                                 b == d - 1 ? nullptr : (const uint8_t*)c->lev[b + 1].ancflag.ptr,
+                                                 c->lev[b + 1].n_oct, (uint8_t*)B.ancflag.ptr);
+      size_t tmp = c->sort_tmp.bytes;
+      ++c->n_cub;
+      CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, (const uint8_t*)B.ancflag.ptr, (int32_t*)B.anc.ptr,
+                                    d_counts + 4 * (lmax + 2) + b, (int)B.n_oct, st));
+    }
+  }
   return FMM_OK;
 }
 
-// The one synchronisation of a tree build: error word and list lengths.
+// The one synchronisation of a tree build: error words and list lengths.  An
+// invalid level also corrupts the levels above it (their keys come from its
+// octs), so the finest level with an error names the cause.
 fmm_status tree_finish(Ctx* c, cudaStream_t st) {
   const int lmin = c->lmin, lmax = c->lmax;
   const int stride = lmax + 2;
   int32_t* d_counts = (int32_t*)c->counter.ptr;
-  unsigned* err = c->d_err;
-  unsigned host_err = c->tree_host_err;
-  std::vector<int32_t> counts(4 * stride, 0);
-  CK(cudaMemcpyAsync(counts.data(), d_counts, 4 * 4 * stride, cudaMemcpyDeviceToHost, st));
-  unsigned e = 0;
-  CK(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, st));
+  std::vector<int32_t> counts(5 * stride, 0);
+  CK(cudaMemcpyAsync(counts.data(), d_counts, 5 * 4 * stride, cudaMemcpyDeviceToHost, st));
+  unsigned ev[kErrWords] = {};
+  CK(cudaMemcpyAsync(ev, c->d_err, kErrWords * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  e |= host_err;
-  fmm_status s = err_to_status(e);
-  if (s != FMM_OK) {
-    c->last_error = "tree: invalid hierarchy (error bits " + std::to_string(e) + ")";
-    return s;
+  for (int l = lmax; l >= 1; --l) {
+    const unsigned e = ev[1 + l] | c->tree_host_err[l];
+    const fmm_status s = err_to_status(e);
+    if (s != FMM_OK) {
+      c->last_error = (e & kErrStructure)
+                          ? "tree: a partial update changed the cells of its lowest level; update from one level coarser"
+                          : "tree: invalid hierarchy at level " + std::to_string(l) + " (error bits " + std::to_string(e) +
+                                ")";
+      return s;
+    }
   }
   for (int l = 1; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
@@ -510,6 +589,7 @@ fmm_status tree_finish(Ctx* c, cudaStream_t st) {
     T.n_tgt = counts[1 * stride + l];
     T.n_rowsL = (l + 2 <= lmax) ? counts[2 * stride + l] : 0;
     T.n_irows = (l >= lmin) ? counts[3 * stride + l] : 0;
+    T.n_anc = (l < c->anc_req) ? counts[4 * stride + l] : 0;
   }
   return FMM_OK;
 }

@@ -117,7 +117,7 @@ struct M2MWarps {
 
 template <typename Tin, typename Tacc, typename Tout, typename TMono>
 __global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
-    int64_t n_oct_next, int nc, const int32_t* __restrict__ oct_parent_next,
+    int64_t n_oct_next, const int32_t* __restrict__ octs, int nc, const int32_t* __restrict__ oct_parent_next,
     const int32_t* __restrict__ cell_child_next, const Tin* __restrict__ Mnext,
     const double* __restrict__ mass_next, Tout* __restrict__ Mout, __nv_bfloat16* __restrict__ hi,
     __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono, const int* __restrict__ poff,
@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
   constexpr int W = M2MWarps<Tacc>::kWarps;
   __shared__ Tacc smem[W][8 * kNcMax];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t o = (int64_t)blockIdx.x * W + warp;
-  if (o >= n_oct_next) return;  // warp-uniform; no block-wide barrier below
+  const int64_t i = (int64_t)blockIdx.x * W + warp;
+  if (i >= n_oct_next) return;  // warp-uniform; no block-wide barrier below
+  const int64_t o = octs ? octs[i] : i;
   const int64_t cell = oct_parent_next[o];
   const int64_t c0 = o * 8;
   const int32_t cc = lane < 8 ? cell_child_next[c0 + lane] : -1;
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
 // all its threads.  Dynamic shared memory: see m2m_block_smem.
 template <typename Tin, typename Tout, typename TMono>
 __global__ void __launch_bounds__(128) k_m2m_block(
-    int nc, int npairs, const int32_t* __restrict__ oct_parent_next, const int32_t* __restrict__ cell_child_next,
+    const int32_t* __restrict__ octs, int nc, int npairs, const int32_t* __restrict__ oct_parent_next, const int32_t* __restrict__ cell_child_next,
     const Tin* __restrict__ Mnext, const double* __restrict__ mass_next, Tout* __restrict__ Mout,
     __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono,
     const int* __restrict__ poff, const int* __restrict__ pg, const int* __restrict__ pe,
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(128) k_m2m_block(
   double* cf = S + 8 * nc;                    // [npairs]
   int* gx = (int*)(cf + npairs);              // [npairs]: gamma + nc * e
   int* off = gx + npairs;                     // [nc + 1]
-  const int64_t o = blockIdx.x;
+  const int64_t o = octs ? octs[blockIdx.x] : blockIdx.x;
   const int64_t cell = oct_parent_next[o];
   const int64_t c0 = o * 8;
   for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
@@ -246,7 +247,8 @@ inline size_t m2m_block_smem(int nc, int npairs) { return (size_t)8 * nc * 8 + (
 // l2l_smem), since these small levels are latency-bound.
 __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32_t* __restrict__ rows,
                                                  const int32_t* __restrict__ oct_parent,
-                                                 const double* __restrict__ Lup, const float* __restrict__ Lm,
+                                                 const int32_t* __restrict__ slot, const int32_t* __restrict__ slot_up,
+                                                 const double* __restrict__ Lup, float* __restrict__ Lm,
                                                  double* __restrict__ L, const int* __restrict__ poff8,
                                                  const int* __restrict__ pg, const double* __restrict__ pc) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -255,9 +257,11 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
   int* gg = (int*)(cf + npairs);        // [npairs]
   int* off = gg + npairs;               // [8 nc + 1]
   const int32_t o = rows[blockIdx.x];
+  const int64_t so = slot[o];
   if (Lup) {
     const int32_t par = oct_parent[o];
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) Lp[k] = Lup[(int64_t)par * nc + k];
+    const int64_t sp = (int64_t)slot_up[par >> 3] * 8 + (par & 7);
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) Lp[k] = Lup[sp * nc + k];
     for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
       cf[j] = pc[j];
       gg[j] = pg[j];
@@ -277,8 +281,13 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
     sign_transform_back(acc);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const int64_t idx = ((int64_t)o * 8 + c) * nc + b;
-      L[idx] = Lm ? acc[c] + (double)Lm[idx] : acc[c];
+      const int64_t idx = (so * 8 + c) * nc + b;
+      if (Lm) {
+        L[idx] = acc[c] + (double)Lm[idx];
+        Lm[idx] = 0.0f;  // the M2L contraction adds into a cleared slot next time
+      } else {
+        L[idx] = acc[c];
+      }
     }
   }
 }
@@ -313,7 +322,7 @@ void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {
     k_leaf_rows<float><<<gr, 256, 0, st>>>(T.n_irows, c->tab.nc, ir, cc, mass, (float*)T.M.ptr, hi, lo);
 }
 
-void launch_upward(Ctx* c, int b, cudaStream_t st) {
+void launch_upward(Ctx* c, int b, cudaStream_t st, const int32_t* octs, int64_t n_octs) {
   LevelTree& T = c->lev[b];
   LevelTree& N = c->lev[b + 1];
   if (!N.n_oct) return;
@@ -324,7 +333,8 @@ void launch_upward(Ctx* c, int b, cudaStream_t st) {
   const int* pe = (const int*)c->d_m2m_e.ptr;
   const double* pc = (const double*)c->d_m2m_c.ptr;
   const int* e0 = (const int*)c->d_m2m_e0.ptr;
-  const int64_t n = N.n_oct;
+  const int64_t n = octs ? n_octs : N.n_oct;  // child octs of level b+1 to process
+  if (!n) return;
   const int32_t* par = (const int32_t*)N.oct_parent.ptr;
   const int32_t* ccn = (const int32_t*)N.cell_child.ptr;
   const double* mn = (const double*)N.mass.ptr;
@@ -336,35 +346,39 @@ void launch_upward(Ctx* c, int b, cudaStream_t st) {
   const int np = (int)c->tab.m2m_g.size();
   const size_t smb = m2m_block_smem(nc, np);
   if (f64) {
-    k_m2m_block<double, double, double><<<(unsigned)n, 128, smb, st>>>(nc, np, par, ccn, (const double*)N.M.ptr, mn,
+    k_m2m_block<double, double, double><<<(unsigned)n, 128, smb, st>>>(octs, nc, np, par, ccn, (const double*)N.M.ptr, mn,
                                                                      (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
                                                                      poff, pg, pe, pc);
   } else if (T.m_is_f64) {  // mixed path, top of the tree: FP64 shifts
     if (N.m_is_f64)
-      k_m2m_block<double, double, float><<<(unsigned)n, 128, smb, st>>>(nc, np, par, ccn, (const double*)N.M.ptr, mn,
+      k_m2m_block<double, double, float><<<(unsigned)n, 128, smb, st>>>(octs, nc, np, par, ccn, (const double*)N.M.ptr, mn,
                                                                       (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
                                                                       poff, pg, pe, pc);
     else
-      k_m2m_block<float, double, float><<<(unsigned)n, 128, smb, st>>>(nc, np, par, ccn, (const float*)N.M.ptr, mn,
+      k_m2m_block<float, double, float><<<(unsigned)n, 128, smb, st>>>(octs, nc, np, par, ccn, (const float*)N.M.ptr, mn,
                                                                      (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
                                                                      poff, pg, pe, pc);
   } else {
-    k_m2m<float, float, float, float><<<g32, t32, 0, st>>>(n, nc, par, ccn, (const float*)N.M.ptr, mn,
+    k_m2m<float, float, float, float><<<g32, t32, 0, st>>>(n, octs, nc, par, ccn, (const float*)N.M.ptr, mn,
                                                            (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg,
                                                            pe, (const float*)c->d_m2m_c32.ptr,
                                                            (const float*)c->d_m2m_w0_32.ptr, e0);
   }
 }
 
-void launch_l2l_add(Ctx* c, int b, cudaStream_t st) {
+void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t nrows) {
   LevelTree& T = c->lev[b];
-  if (!T.n_rowsL) return;
+  if (!rows) {
+    rows = (const int32_t*)T.rowsL.ptr;
+    nrows = T.n_rowsL;
+  }
+  if (!nrows) return;
   ++c->n_launch;
   const int np = (int)c->tab.l2l_g.size();
-  k_l2l_add<<<(unsigned)T.n_rowsL, 128, l2l_smem(c->tab.nc, np), st>>>(
-      c->tab.nc, np, (const int32_t*)T.rowsL.ptr, (const int32_t*)T.oct_parent.ptr,
-      b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
-      c->cfg.precision == FMM_FP64 ? nullptr : (const float*)T.Lm.ptr, (double*)T.L.ptr,
+  k_l2l_add<<<(unsigned)nrows, 128, l2l_smem(c->tab.nc, np), st>>>(
+      c->tab.nc, np, rows, (const int32_t*)T.oct_parent.ptr, (const int32_t*)T.slotL.ptr,
+      b >= 3 ? (const int32_t*)c->lev[b - 1].slotL.ptr : nullptr, b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
+      c->cfg.precision == FMM_FP64 ? nullptr : (float*)T.Lm.ptr, (double*)T.L.ptr,
       (const int*)c->d_l2l_off8.ptr, (const int*)c->d_l2l_g.ptr, (const double*)c->d_l2l_c.ptr);
 }
 

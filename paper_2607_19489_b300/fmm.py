@@ -24,7 +24,7 @@ EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_e
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
             "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static",
             "fmm_solve_adjoint", "fmm_batch_solve", "fmm_autotune", "fmm_get_tuning",
-            "fmm_set_tuning"]
+            "fmm_set_tuning", "fmm_update_masses"]
 
 
 class FMMError(RuntimeError):
@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
     L.fmm_autotune.argtypes = [P, I, P]
     L.fmm_get_tuning.argtypes = [P, P]
     L.fmm_set_tuning.argtypes = [P, P]
+    L.fmm_update_masses.argtypes = [P, I, P, P]
     L.fmm_stage_times.argtypes = [P, P]
     for name in EXPORTED:
         fn = getattr(L, name)
@@ -170,6 +171,15 @@ class Solver:
         self.lmin, self.lmax = lmin, lmax
         for k, l in enumerate(range(lo, lmax + 1)):
             self.n[l] = int(n[k])
+
+    def update_masses(self, mass, lo: int | None = None, stream=None) -> None:
+        """New masses for levels lo..lmax (same cells, same order as set_levels)."""
+        lo = self.lmin if lo is None else lo
+        keep = list(mass)
+        pm = _ptrs([_data_ptr(m) for m in mass])
+        rc = lib().fmm_update_masses(self._h, lo, pm, _stream_ptr(stream))
+        del keep
+        self._check(rc, "fmm_update_masses")
 
     def set_hierarchy(self, h, device="cuda", lo: int | None = None, stream=None):
         import torch

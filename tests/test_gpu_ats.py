@@ -64,3 +64,73 @@ def test_ats_subcycle_fp64_matches_oracle():
     ref_p, ref_a = oracle.solve(cur, 4, lo=h.lmax, sel=sel)
     got = {h.lmax: acc[h.lmax].cpu().numpy()[sel[h.lmax]]}
     assert _rel(got, ref_a) <= 1e-10
+
+
+def _unrefine_one(h, level, seed):
+    """h with one refined cell of `level` merged into a leaf (its 8 children, leaves of
+    the finest level, replaced by their total mass).  The cells of `level` keep their
+    set, so this is a valid partial update from `level`."""
+    k = level - h.lmin
+    g = h.copy()
+    child = g.ijk[k + 1]
+    par = child // 2
+    keys, inv = np.unique(par, axis=0, return_inverse=True)
+    pick = int(W.uniform(seed, 1, 0) * keys.shape[0])
+    sel = inv.reshape(-1) == pick
+    g.ijk[k] = np.ascontiguousarray(np.concatenate([g.ijk[k], keys[pick][None, :].astype(np.int32)]))
+    g.mass[k] = np.concatenate([g.mass[k], [g.mass[k + 1][sel].sum()]])
+    g.ijk[k + 1] = np.ascontiguousarray(child[~sel])
+    g.mass[k + 1] = g.mass[k + 1][~sel]
+    return g
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_incremental_updates_equal_full_rebuilds(precision, tol):
+    """Partial rebuilds (set_levels from lo) followed by solves from lo, including a
+    change of refinement above lo, against a fresh full build and solve."""
+    import torch
+    from paper_2607_19489_b300 import fmm
+    h = W.lognormal_amr(base=5, seed=6)
+    assert h.lmax == h.lmin + 2
+    s = fmm.Solver(6, precision)
+    s.set_hierarchy(h)
+    s.solve()
+    ref = fmm.Solver(6, precision)
+    steps = [(h.lmax, None), (h.lmin + 1, "unrefine"), (h.lmax, None), (h.lmin + 1, None), (h.lmin, None)]
+    cur = h
+    for i, (lo, change) in enumerate(steps):
+        cur = _unrefine_one(cur, lo, seed=i) if change else _perturb(cur, lo, i)
+        s.set_hierarchy(cur, lo=lo)
+        phi, acc = s.solve(lo)
+        ref.set_hierarchy(cur)
+        rphi, racc = ref.solve()
+        torch.cuda.synchronize()
+        s.sync()
+        ref.sync()
+        got = {l: acc[l].double().cpu().numpy() for l in acc}
+        want = {l: racc[l].double().cpu().numpy() for l in acc}
+        assert _rel(got, want) <= tol, (i, lo)
+        gotp = {l: phi[l].double().cpu().numpy() for l in phi}
+        wantp = {l: rphi[l].double().cpu().numpy() for l in phi}
+        assert _rel(gotp, wantp) <= tol, (i, lo)
+
+
+def test_partial_update_must_keep_its_lowest_level():
+    from paper_2607_19489_b300 import fmm
+    h = W.lognormal_amr(base=5, seed=6)
+    s = fmm.Solver(4, "fp64")
+    s.set_hierarchy(h)
+    bad = _unrefine_one(h, h.lmin + 1, seed=3)   # changes the cells of level lmin + 2
+    with pytest.raises(fmm.FMMError) as e:
+        s.set_hierarchy(bad, lo=h.lmin + 2)
+    assert e.value.code == -8  # FMM_ERR_STATE
+    # the rejected call already replaced its levels: a full set_levels comes next,
+    # after which the same change as an update from one level coarser is accepted
+    s.set_hierarchy(h)
+    s.solve()
+    s.set_hierarchy(bad, lo=h.lmin + 1)
+    phi, acc = s.solve(h.lmin + 1)
+    s.sync()
+    ref_p, ref_a = oracle.solve(bad, 4, lo=h.lmin + 1)
+    got = {l: acc[l].cpu().numpy() for l in acc}
+    assert _rel(got, ref_a) <= 1e-10

@@ -80,3 +80,28 @@ def test_subcycle_solves_replay():
             s.sync()
             got_p, got_a = _out(phi, acc)
             assert _rel(got_a, ref[lo][1]) <= 1e-10
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_update_masses_equals_set_levels(precision, tol):
+    """Mass-only updates (no tree rebuild) of all levels and of the finest level."""
+    import torch
+    from paper_2607_19489_b300 import fmm
+    h = W.random_amr(3, 5, seed=13)
+    s = fmm.Solver(4, precision)
+    s.set_hierarchy(h)
+    s.solve()
+    ref = fmm.Solver(4, precision)
+    cur = h.copy()
+    for i, lo in enumerate([h.lmin, h.lmax, h.lmin + 1]):
+        for k in range(lo - h.lmin, len(cur.mass)):
+            cur.mass[k] = cur.mass[k] * (1 + 0.1 * W.uniform(3, 40 + i, np.arange(cur.mass[k].size)))
+        s.update_masses([torch.as_tensor(m, device="cuda") for m in cur.mass[lo - h.lmin:]], lo=lo)
+        phi, acc = s.solve()
+        ref.set_hierarchy(cur)
+        rphi, racc = ref.solve()
+        s.sync()
+        ref.sync()
+        got_p, got_a = _out(phi, acc)
+        want_p, want_a = _out(rphi, racc)
+        assert _rel(got_a, want_a) <= tol and _rel(got_p, want_p) <= tol
