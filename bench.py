@@ -154,9 +154,15 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- GPU arm
 
-def make_workload():
+WORKLOADS = {
+    "two_level": WORKLOAD,
+    "unigrid16": "unigrid 16^3 Plummer a=0.1, p=6 (a small case for checking the launch paths)",
+}
+
+
+def make_workload(name: str = "two_level"):
     from paper_2607_19489_b300 import workloads as W
-    return W.two_level_plummer()
+    return W.two_level_plummer() if name == "two_level" else W.unigrid_plummer(4)
 
 
 def rel_rms(a: dict, b: dict) -> float:
@@ -212,7 +218,7 @@ def gpu_arm(args, rank, world, local):
     dev = torch.device("cuda", local)
     dist = dist_init(world, "nccl")
     stream = torch.cuda.current_stream()
-    h = make_workload()
+    h = make_workload(args.workload)
     n_cells = h.n_cells
     ijk = [torch.as_tensor(a, device=dev).contiguous() for a in h.ijk]
     mass = [torch.as_tensor(m, device=dev).contiguous() for m in h.mass]
@@ -330,7 +336,7 @@ def gpu_arm(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic (seeded)",
-        "config": {"workload": WORKLOAD, "cells": n_cells, "levels": [h.n(l) for l in h.levels], "p": P_ORDER,
+        "config": {"workload": WORKLOADS[args.workload], "cells": n_cells, "levels": [h.n(l) for l in h.levels], "p": P_ORDER,
                    "step": "fmm_set_levels (tree build) + fmm_solve", "l2": "flushed (256 MB write) before each step",
                    "parallelism": f"replicas x{world} (independent hierarchies)"},
         "fp64_gpu": {"value": value_fp64, "ms_per_step": ms_fp64, "speedup_mixed_over_fp64": value / value_fp64},
@@ -545,7 +551,7 @@ def cpu_baseline(h, per_level: int):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    h = make_workload()
+    h = make_workload(args.workload)
     per = []
     cb = None
     for i in range(args.warmup + args.steps):
@@ -556,7 +562,7 @@ def reference_arm(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
-            "config": {"workload": WORKLOAD, "cells": h.n_cells, "p": P_ORDER},
+            "config": {"workload": WORKLOADS[args.workload], "cells": h.n_cells, "p": P_ORDER},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cb["cores"],
                              "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -572,6 +578,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=4000, help="oracle targets per level for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=1000, help="oracle targets per level per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="two_level", choices=sorted(WORKLOADS),
+                    help="two_level: the measured configuration; unigrid16: a small check of the launch paths")
     ap.add_argument("--fd-cells", type=int, default=0,
                     help="adjoint leg: central finite differences on this many seeded cells (2 FP64 solves each)")
     ap.add_argument("--legs", default="batched,adjoint,ats",
