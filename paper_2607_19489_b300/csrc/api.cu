@@ -221,6 +221,7 @@ fmm_status size_locals(Ctx* c, cudaStream_t st) {
       void* old = T.Lm.ptr;
       CKS(buf_ensure(c, T.Lm, nrow * nc * 4));
       if (T.Lm.ptr != old) CKS(cudaMemsetAsync(T.Lm.ptr, 0, T.Lm.bytes, st));
+      CKS(buf_ensure(c, T.Lf, nrow * nc * 4));
     }
   }
   return FMM_OK;
@@ -482,6 +483,12 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
   }
   cudaMemset(c->d_err, 0, kErrWords * 4);
   for (auto& ev : c->ev) cudaEventCreate(&ev);
+  if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    c->aux_stream = nullptr;  // one stream then: the solve stays correct, only serial
+  }
   fmm_status s = near_init(c);
   if (s == FMM_OK) s = acquire_tables(c);
   if (s != FMM_OK) {
@@ -640,50 +647,67 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // 2. downward over box levels 2..lmax-2: L = L2L(parent) + M2L.  For targets
   // at levels >= lo > lmin, the levels b <= lo-3 only feed the L2L chain of the
   // ancestors of level lo: their ancestor lists replace the full row lists.
-  const bool restrict_dn = lo > lmin && c->anc_d == lo;
-  std::vector<const int32_t*> drows(lmax + 1, nullptr);
-  std::vector<int64_t> dn(lmax + 1, 0);
-  for (int b = 2; b <= lmax - 2; ++b)
-    if (restrict_dn && b <= lo - 3) {
-      drows[b] = (const int32_t*)c->lev[b].anc.ptr;
-      dn[b] = c->lev[b].n_anc;
+  auto downward = [&](cudaStream_t s2) {
+    const bool restrict_dn = lo > lmin && c->anc_d == lo;
+    std::vector<const int32_t*> drows(lmax + 1, nullptr);
+    std::vector<int64_t> dn(lmax + 1, 0);
+    for (int b = 2; b <= lmax - 2; ++b)
+      if (restrict_dn && b <= lo - 3) {
+        drows[b] = (const int32_t*)c->lev[b].anc.ptr;
+        dn[b] = c->lev[b].n_anc;
+      }
+    if (f64) {
+      for (int b = 2; b <= lmax - 2; ++b) {
+        if (drows[b] && !dn[b]) continue;
+        launch_l2l_add(c, b, s2, drows[b], dn[b]);
+        launch_gemm_f64(c, c->op_m2l, kModeM2L, b, s2, drows[b], dn[b]);
+      }
+    } else if (lmax - 2 >= 2) {
+      std::vector<int> lv;
+      std::vector<const int32_t*> rv;
+      std::vector<int64_t> nv;
+      for (int b = 2; b <= lmax - 2; ++b) {
+        if (drows[b] && !dn[b]) continue;
+        lv.push_back(b);
+        rv.push_back(drows[b]);
+        nv.push_back(dn[b]);
+      }
+      if (!lv.empty())  // all levels in one launch
+        launch_gemm_tc(c, c->op_m2l, kModeM2L, lv.data(), (int)lv.size(), s2, rv.data(), nv.data());
+      for (size_t i = 0; i < lv.size(); ++i) launch_l2l_add(c, lv[i], s2, rv[i], nv[i]);
     }
-  if (f64) {
-    for (int b = 2; b <= lmax - 2; ++b) {
-      if (drows[b] && !dn[b]) continue;
-      launch_l2l_add(c, b, st, drows[b], dn[b]);
-      launch_gemm_f64(c, c->op_m2l, kModeM2L, b, st, drows[b], dn[b]);
-    }
-  } else if (lmax - 2 >= 2) {
-    std::vector<int> lv;
-    std::vector<const int32_t*> rv;
-    std::vector<int64_t> nv;
-    for (int b = 2; b <= lmax - 2; ++b) {
-      if (drows[b] && !dn[b]) continue;
-      lv.push_back(b);
-      rv.push_back(drows[b]);
-      nv.push_back(dn[b]);
-    }
-    if (!lv.empty())  // all levels in one launch
-      launch_gemm_tc(c, c->op_m2l, kModeM2L, lv.data(), (int)lv.size(), st, rv.data(), nv.data());
-    for (size_t i = 0; i < lv.size(); ++i) launch_l2l_add(c, lv[i], st, rv[i], nv[i]);
-  }
-  stage_event(c, 2, st);
-  // 3a. bottom intermediate field, M2P from level l-1 cells
-  {
+  };
+  // 3a. bottom intermediate field, M2P from level l-1 cells, then the near-field
+  // M2P of the interface octs (both add into the M2P accumulator)
+  auto bottom = [&](cudaStream_t s2, bool timed) {
     std::vector<int> lv;
     for (int l = lo; l <= lmax; ++l) {
       if (!c->lev[l].n_leaf) continue;
       if (f64)
-        launch_gemm_f64(c, c->op_m2p, kModeM2P, l - 1, st);
+        launch_gemm_f64(c, c->op_m2p, kModeM2P, l - 1, s2);
       else
         lv.push_back(l - 1);
     }
-    if (!f64 && !lv.empty()) launch_gemm_tc(c, c->op_m2p, kModeM2P, lv.data(), (int)lv.size(), st);
+    if (!f64 && !lv.empty()) launch_gemm_tc(c, c->op_m2p, kModeM2P, lv.data(), (int)lv.size(), s2);
+    if (timed) stage_event(c, 3, s2);  // the near-field stage starts here
+    launch_near_m2p(c, lo, s2);
+  };
+  // The bottom field needs only the multipoles: it runs on a second branch
+  // beside the downward pass.  With stage timing on, everything stays in order
+  // on one stream.
+  if (!c->timing && c->aux_stream) {
+    CKS(cudaEventRecord(c->ev_fork, st));
+    CKS(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
+    bottom(c->aux_stream, false);
+    CKS(cudaEventRecord(c->ev_join, c->aux_stream));
+    downward(st);
+    CKS(cudaStreamWaitEvent(st, c->ev_join, 0));
+  } else {
+    downward(st);
+    stage_event(c, 2, st);
+    bottom(st, true);
   }
-  stage_event(c, 3, st);
   // 3b. near / nearest / far fields and the scatter, all target levels in one launch
-  launch_near_m2p(c, lo, st);  // refined cells of the near field (interface octs only)
   launch_near(c, lo, dphi + lo, dacc + lo, c->cfg.out_fp32, st);
   stage_event(c, 4, st);
   return FMM_OK;
@@ -1145,7 +1169,7 @@ void fmm_destroy(fmm_ctx* c) {
   release_tables(c);
   for (auto& T : c->lev) {
     for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.ancflag, &T.tgt, &T.ijk,
-                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lm, &T.acc})
+                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc})
       buf_free(c, *b);
   }
   for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_off8, &c->d_l2l_g,
@@ -1160,6 +1184,9 @@ void fmm_destroy(fmm_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : c->tree_graphs) cudaGraphExecDestroy(g.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   delete c;

@@ -80,6 +80,7 @@ struct LevelTree {
   DevBuf Mhi, Mlo;       // bf16 [8 n_oct][nc] (mixed path GEMM operands)
   DevBuf mono;           // [8 n_oct] total mass per cell (double or float)
   DevBuf L;              // double [8 n_rowsL][nc] local expansions (levels 2..lmax-2), by slot
+  DevBuf Lf;             // float [8 n_rowsL][nc] FP32 copy of L read by the mixed near field
   DevBuf Lm;             // float [8 n_rowsL][nc] this level's M2L sum (mixed path), by slot;
                          // zero between solves (the L2L step clears what it consumes)
   DevBuf acc;            // [8 n_oct][4] M2P result (double or float), targets of this level;
@@ -156,6 +157,11 @@ struct Ctx {
   uint64_t layout_gen = 1;
   std::vector<int64_t> count_sig;
   cudaStream_t cap_stream = nullptr;
+  // second branch of a solve: the bottom M2P needs only the multipoles, so it
+  // runs beside the downward pass (fork after the upward pass, join before
+  // the near field)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool use_graphs = true;
   // launch shapes picked by fmm_autotune (0: built-in choice)
   int tune_split[2] = {0, 0};  // split-K of the tcgen05 contraction, [kModeM2P], [kModeM2L]

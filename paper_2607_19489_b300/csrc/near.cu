@@ -54,6 +54,20 @@ __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
 
+// float -> double by the IEEE-754 encodings (sign, exponent rebiased by
+// 1023 - 127, mantissa shifted by 52 - 23), exact for every normal value, zero,
+// inf and NaN; FP32 subnormals are flushed anyway (--ftz).  B300 runs the
+// hardware conversion on the FP64 pipe, which is what this avoids.
+__device__ __forceinline__ double widen(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint64_t ex = e == 0 ? 0ull : (e == 0xFFu ? 0x7FFull : (uint64_t)(e + 896u));
+  const uint64_t man = e == 0 ? 0ull : (uint64_t)(u & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | (ex << 52) | man));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 template <typename T>
 __device__ __forceinline__ void p2p(T m, T dx, T dy, T dz, T& phi, T& ax, T& ay, T& az) {
   // d = source - target; phi += -m/|d|, accel += m d / |d|^3
@@ -77,12 +91,13 @@ struct NearSeg {
   const void* mono_l;         // level l
   const void* mono_dn;        // level l+1
   const void* M_l;            // multipoles of level l cells
-  const double* L2;           // local expansions of level l-2 (or null), by slot
+  const void* L2;             // local expansions of level l-2 (or null), by slot, in T
   const int32_t* slot2;       // local-expansion slot of each level l-2 oct
   void* acc;                  // M2P results for level l cells [cells][4]; cleared after reading
   void* phi;
   void* accel;
   double s1, s2;              // G / h and G / h^2, h the cell size of level l
+  float s1f, s2f;             // the same in FP32
   int64_t n_tgt;
   int blk0;                   // first block of this segment
   int M_l_f64;
@@ -143,7 +158,7 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     if (S.L2) {
       const int32_t G2 = S.par_up[S.par_l[o] >> 3];
       const int64_t sl = (int64_t)S.slot2[G2 >> 3] * 8 + (G2 & 7);
-      for (int b = tp; b < P.nc; b += 8) s_L[g][b] = (T)S.L2[sl * P.nc + b];
+      for (int b = tp; b < P.nc; b += 8) s_L[g][b] = ((const T*)S.L2)[sl * P.nc + b];
     }
   }
   __syncthreads();
@@ -279,7 +294,14 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     }
   }
   // level-l units: the M2P sum is in level l-1 units, the local expansion in level l-2 units
-  const T s1 = (T)S.s1, s2 = (T)S.s2;
+  T s1, s2;
+  if constexpr (sizeof(T) == 4) {
+    s1 = S.s1f;
+    s2 = S.s2f;
+  } else {
+    s1 = S.s1;
+    s2 = S.s2;
+  }
   const T ph = s1 * (phi + (T)0.5 * pm + (T)0.25 * pl);
   const T gx = s2 * (ax + (T)0.25 * xm + (T)0.0625 * xl);
   const T gy = s2 * (ay + (T)0.25 * ym + (T)0.0625 * yl);
@@ -292,11 +314,11 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     a[1] = (float)gy;
     a[2] = (float)gz;
   } else {
-    ((double*)S.phi)[li] = (double)ph;
+    ((double*)S.phi)[li] = widen(ph);
     double* a = (double*)S.accel + 3 * li;
-    a[0] = (double)gx;
-    a[1] = (double)gy;
-    a[2] = (double)gz;
+    a[0] = widen(gx);
+    a[1] = widen(gy);
+    a[2] = widen(gz);
   }
 }
 
@@ -503,13 +525,15 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
       S.mono_dn = (l < c->lmax) ? c->lev[l + 1].mono.ptr : nullptr;
       S.M_l = T.M.ptr;
       S.M_l_f64 = T.m_is_f64 ? 1 : 0;
-      S.L2 = (l - 2 >= 2) ? (const double*)c->lev[l - 2].L.ptr : nullptr;
+      S.L2 = (l - 2 >= 2) ? (f64 ? c->lev[l - 2].L.ptr : c->lev[l - 2].Lf.ptr) : nullptr;
       S.slot2 = (l - 2 >= 2) ? (const int32_t*)c->lev[l - 2].slotL.ptr : nullptr;
       S.acc = T.acc.ptr;
       S.phi = phi[l - lo];
       S.accel = accel[l - lo];
       S.s1 = c->cfg.G * std::ldexp(1.0, l);
       S.s2 = c->cfg.G * std::ldexp(1.0, 2 * l);
+      S.s1f = (float)S.s1;
+      S.s2f = (float)S.s2;
       S.n_tgt = T.n_tgt;
       S.blk0 = blocks;
       blocks += (int)((T.n_tgt + opb - 1) / opb);

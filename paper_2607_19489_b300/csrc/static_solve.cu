@@ -186,7 +186,10 @@ extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n
     }
     if (k >= 2 && k + 2 <= L) {
       set_buf(T.L, cv.take(ncell * nc * 8), ncell * nc * 8);
-      if (!f64) set_buf(T.Lm, cv.take(ncell * nc * 4), ncell * nc * 4);
+      if (!f64) {
+        set_buf(T.Lm, cv.take(ncell * nc * 4), ncell * nc * 4);
+        set_buf(T.Lf, cv.take(ncell * nc * 4), ncell * nc * 4);  // FP32 copy for the near field
+      }
     }
     if (k == L) {
       set_buf(T.acc, cv.take(ncell * 4 * (f64 ? 8 : 4)), ncell * 4 * (f64 ? 8 : 4));

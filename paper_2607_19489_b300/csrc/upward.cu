@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
                                                  const int32_t* __restrict__ oct_parent,
                                                  const int32_t* __restrict__ slot, const int32_t* __restrict__ slot_up,
                                                  const double* __restrict__ Lup, float* __restrict__ Lm,
-                                                 double* __restrict__ L, const int* __restrict__ poff8,
+                                                 double* __restrict__ L, float* __restrict__ Lf,
+                                                 const int* __restrict__ poff8,
                                                  const int* __restrict__ pg, const double* __restrict__ pc) {
   extern __shared__ __align__(16) unsigned char dsm[];
   double* Lp = (double*)dsm;            // [nc]
@@ -283,8 +284,10 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
     for (int c = 0; c < 8; ++c) {
       const int64_t idx = (so * 8 + c) * nc + b;
       if (Lm) {
-        L[idx] = acc[c] + (double)Lm[idx];
-        Lm[idx] = 0.0f;  // the M2L contraction adds into a cleared slot next time
+        const double v = acc[c] + (double)Lm[idx];
+        L[idx] = v;
+        Lf[idx] = (float)v;  // converted once here rather than by every target of the near field
+        Lm[idx] = 0.0f;      // the M2L contraction adds into a cleared slot next time
       } else {
         L[idx] = acc[c];
       }
@@ -378,7 +381,7 @@ void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t
   k_l2l_add<<<(unsigned)nrows, 128, l2l_smem(c->tab.nc, np), st>>>(
       c->tab.nc, np, rows, (const int32_t*)T.oct_parent.ptr, (const int32_t*)T.slotL.ptr,
       b >= 3 ? (const int32_t*)c->lev[b - 1].slotL.ptr : nullptr, b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
-      c->cfg.precision == FMM_FP64 ? nullptr : (float*)T.Lm.ptr, (double*)T.L.ptr,
+      c->cfg.precision == FMM_FP64 ? nullptr : (float*)T.Lm.ptr, (double*)T.L.ptr, (float*)T.Lf.ptr,
       (const int*)c->d_l2l_off8.ptr, (const int*)c->d_l2l_g.ptr, (const double*)c->d_l2l_c.ptr);
 }
 

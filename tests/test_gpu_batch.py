@@ -61,10 +61,10 @@ def test_mixed_batch_matches_own_solves(p):
     outs = fmm.batch_solve(solvers, outs=outs)  # replay of the cached graph
     for s in solvers:
         s.sync()
-    for o, ref in zip(outs, own):
+    for o, ref in zip(outs, own):  # same kernels; atomics may add in another order
         got_p, got_a = _np(o)
-        assert _rel(got_a, ref[1]) <= 1e-6
-        assert _rel(got_p, ref[0]) <= 1e-6
+        assert _rel(got_a, ref[1]) <= 1e-5
+        assert _rel(got_p, ref[0]) <= 1e-5
 
 
 def test_batch_follows_hierarchy_changes_and_subcycles():
@@ -99,14 +99,15 @@ def test_autotune_keeps_results():
     assert t["split_m2p"] >= 0 and t["split_m2l"] >= 0 and t["near_octs_per_block"] in (4, 8, 16)
     after = _np(s.solve())
     s.sync()
-    assert _rel(after[1], before[1]) <= 1e-6
+    # another split-K factor sums the FP32 partial products in another order
+    assert _rel(after[1], before[1]) <= 1e-5
     s2 = fmm.Solver(6, "mixed")
     s2.set_hierarchy(h)
     s2.set_tuning(t)
     assert s2.tuning() == t
     again = _np(s2.solve())
     s2.sync()
-    assert _rel(again[1], before[1]) <= 1e-6
+    assert _rel(again[1], before[1]) <= 1e-5
 
 
 def test_shared_tables_survive_their_creator():
