@@ -647,39 +647,35 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // 2. downward over box levels 2..lmax-2: L = L2L(parent) + M2L.  For targets
   // at levels >= lo > lmin, the levels b <= lo-3 only feed the L2L chain of the
   // ancestors of level lo: their ancestor lists replace the full row lists.
-  auto downward = [&](cudaStream_t s2) {
-    const bool restrict_dn = lo > lmin && c->anc_d == lo;
-    std::vector<const int32_t*> drows(lmax + 1, nullptr);
-    std::vector<int64_t> dn(lmax + 1, 0);
-    for (int b = 2; b <= lmax - 2; ++b)
-      if (restrict_dn && b <= lo - 3) {
-        drows[b] = (const int32_t*)c->lev[b].anc.ptr;
-        dn[b] = c->lev[b].n_anc;
-      }
-    if (f64) {
-      for (int b = 2; b <= lmax - 2; ++b) {
-        if (drows[b] && !dn[b]) continue;
-        launch_l2l_add(c, b, s2, drows[b], dn[b]);
-        launch_gemm_f64(c, c->op_m2l, kModeM2L, b, s2, drows[b], dn[b]);
-      }
-    } else if (lmax - 2 >= 2) {
-      std::vector<int> lv;
-      std::vector<const int32_t*> rv;
-      std::vector<int64_t> nv;
-      for (int b = 2; b <= lmax - 2; ++b) {
-        if (drows[b] && !dn[b]) continue;
-        lv.push_back(b);
-        rv.push_back(drows[b]);
-        nv.push_back(dn[b]);
-      }
-      if (!lv.empty())  // all levels in one launch
-        launch_gemm_tc(c, c->op_m2l, kModeM2L, lv.data(), (int)lv.size(), s2, rv.data(), nv.data());
-      for (size_t i = 0; i < lv.size(); ++i) launch_l2l_add(c, lv[i], s2, rv[i], nv[i]);
+  const bool restrict_dn = lo > lmin && c->anc_d == lo;
+  std::vector<const int32_t*> drows(lmax + 1, nullptr);
+  std::vector<int64_t> dn(lmax + 1, 0);
+  for (int b = 2; b <= lmax - 2; ++b)
+    if (restrict_dn && b <= lo - 3) {
+      drows[b] = (const int32_t*)c->lev[b].anc.ptr;
+      dn[b] = c->lev[b].n_anc;
+    }
+  std::vector<int> dl;  // box levels with M2L rows
+  std::vector<const int32_t*> dr;
+  std::vector<int64_t> dnr;
+  for (int b = 2; b <= lmax - 2; ++b) {
+    if (drows[b] && !dn[b]) continue;
+    dl.push_back(b);
+    dr.push_back(drows[b]);
+    dnr.push_back(dn[b]);
+  }
+  // M2L of all box levels: one tcgen05 launch (mixed), or per level (FP64)
+  auto m2l_tc = [&](cudaStream_t s2) {
+    if (!dl.empty()) launch_gemm_tc(c, c->op_m2l, kModeM2L, dl.data(), (int)dl.size(), s2, dr.data(), dnr.data());
+  };
+  auto l2l_chain = [&](cudaStream_t s2) {
+    for (size_t i = 0; i < dl.size(); ++i) {
+      launch_l2l_add(c, dl[i], s2, dr[i], dnr[i]);
+      if (f64) launch_gemm_f64(c, c->op_m2l, kModeM2L, dl[i], s2, dr[i], dnr[i]);
     }
   };
-  // 3a. bottom intermediate field, M2P from level l-1 cells, then the near-field
-  // M2P of the interface octs (both add into the M2P accumulator)
-  auto bottom = [&](cudaStream_t s2, bool timed) {
+  // 3a. bottom intermediate field: M2P from level l-1 cells
+  auto m2p = [&](cudaStream_t s2) {
     std::vector<int> lv;
     for (int l = lo; l <= lmax; ++l) {
       if (!c->lev[l].n_leaf) continue;
@@ -689,23 +685,31 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
         lv.push_back(l - 1);
     }
     if (!f64 && !lv.empty()) launch_gemm_tc(c, c->op_m2p, kModeM2P, lv.data(), (int)lv.size(), s2);
-    if (timed) stage_event(c, 3, s2);  // the near-field stage starts here
-    launch_near_m2p(c, lo, s2);
   };
-  // The bottom field needs only the multipoles: it runs on a second branch
-  // beside the downward pass.  With stage timing on, everything stays in order
-  // on one stream.
+  // The bottom field needs only the multipoles, so it runs on a second branch
+  // beside the downward pass.  Mixed: the two tcgen05 contractions each fill the
+  // SMs' shared memory, so M2L goes first, then M2P overlaps the latency-bound
+  // L2L chain and the near-field M2P (both add atomically into the zeroed
+  // accumulator).  FP64: the DFMA contractions share SMs, so the fork comes
+  // right after the upward pass; the FP64 M2P assigns the accumulator, so the
+  // near-field M2P follows it.  With stage timing on, everything stays in order.
   if (!c->timing && c->aux_stream) {
+    if (!f64) m2l_tc(st);
     CKS(cudaEventRecord(c->ev_fork, st));
     CKS(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
-    bottom(c->aux_stream, false);
+    m2p(c->aux_stream);
+    if (f64) launch_near_m2p(c, lo, c->aux_stream);
     CKS(cudaEventRecord(c->ev_join, c->aux_stream));
-    downward(st);
+    l2l_chain(st);
+    if (!f64) launch_near_m2p(c, lo, st);
     CKS(cudaStreamWaitEvent(st, c->ev_join, 0));
   } else {
-    downward(st);
+    if (!f64) m2l_tc(st);
+    l2l_chain(st);
     stage_event(c, 2, st);
-    bottom(st, true);
+    m2p(st);
+    stage_event(c, 3, st);  // the near-field stage starts here
+    launch_near_m2p(c, lo, st);
   }
   // 3b. near / nearest / far fields and the scatter, all target levels in one launch
   launch_near(c, lo, dphi + lo, dacc + lo, c->cfg.out_fp32, st);

@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(256) k_near_m2p(const __grid_constant__ NearM2
     T v = 0;
     for (int ww = 0; ww < 8; ++ww) v += s_part[ww][tt * 4][comp];
     const int64_t cell = (int64_t)o * 8 + tt;
-    if (S.cc_l[cell] < 0) ((T*)S.acc)[cell * 4 + comp] += (comp == 0 ? (T)2 : (T)4) * v;
+    // atomic: in the mixed path the bottom M2P may be adding into the same cells concurrently
+    if (S.cc_l[cell] < 0) atomicAdd((T*)S.acc + cell * 4 + comp, (comp == 0 ? (T)2 : (T)4) * v);
   }
 }
 

@@ -105,18 +105,89 @@ __global__ void k_scatter_level(int64_t n, int64_t n_oct, const uint64_t* __rest
   }
 }
 
-__global__ void k_full_level(int64_t n_oct, uint64_t* oct_key, int32_t* oct_parent, int32_t* cell_child) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n_oct) {
-    oct_key[i] = (uint64_t)i;
-    oct_parent[i] = (int32_t)i;
+// The base level lmin covers the box, so in Morton order its cells are exactly
+// 0 .. 8^lmin - 1: a cell's sorted position is its key, and the leaves and the
+// parents of the level lmin+1 octs are placed there directly (no sort).  A
+// position taken twice is a duplicate; with the counts checked on the host,
+// no duplicate means no gap.  cell_child starts filled with kUnsetCell.
+constexpr int32_t kUnsetCell = (int32_t)0x80808080;  // byte 0x80 memset; never a valid entry
+
+__global__ void k_place_complete(int level, int64_t n_leaf, int64_t n_ref, int64_t n_cells,
+                                 const int32_t* __restrict__ ijk, const double* __restrict__ mass,
+                                 const uint64_t* __restrict__ octkey_next, int32_t* __restrict__ cell_child,
+                                 int32_t* __restrict__ leaf_cell, int32_t* __restrict__ oct_parent_next,
+                                 unsigned* err) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_leaf + n_ref) return;
+  uint64_t key;
+  int32_t val;
+  if (i < n_leaf) {
+    const int x = ijk[3 * i], y = ijk[3 * i + 1], z = ijk[3 * i + 2];
+    const int lim = 1 << level;
+    if (x < 0 || y < 0 || z < 0 || x >= lim || y >= lim || z >= lim) {
+      atomicOr(err, kErrOutOfBox);
+      return;
+    }
+    if (!isfinite(mass[i])) atomicOr(err, kErrNonFinite);
+    key = spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+    val = (int32_t)(-1 - i);
+    leaf_cell[i] = (int32_t)key;
+  } else {
+    const int64_t j = i - n_leaf;
+    key = octkey_next[j];
+    if (key >= (uint64_t)n_cells) {  // only after an invalid finer level (already flagged)
+      atomicOr(err, kErrIncomplete);
+      return;
+    }
+    val = (int32_t)j;
+    oct_parent_next[j] = (int32_t)key;
   }
-  if (i < 8 * n_oct) cell_child[i] = (int32_t)i;
+  if (atomicExch(cell_child + key, val) != kUnsetCell) atomicOr(err, kErrDuplicate);
 }
 
-__global__ void k_iota(int64_t n, int32_t* a) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) a[i] = (int32_t)i;
+// Levels 1..lmin (complete grids): oct o of level l sits under cell o of level
+// l-1, whose 27 neighbours are found by decoding o's Morton index; levels below
+// lmin are fully refined (the child oct of cell c is c).  One thread per oct of
+// all these levels; level lmin's cells come from k_place_complete.
+struct CompleteLevels {
+  int lmin;
+  int64_t oct0[kMaxLevel + 2];  // first oct of level l in the thread index space
+  uint64_t* oct_key[kMaxLevel + 1];
+  int32_t* oct_parent[kMaxLevel + 1];
+  int32_t* cell_child[kMaxLevel + 1];
+  int32_t* nbr[kMaxLevel + 1];
+};
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {  // inverse of spread3
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10C30C30C30C30C3ull;
+  x = (x ^ (x >> 4)) & 0x100F00F00F00F00Full;
+  x = (x ^ (x >> 8)) & 0x1F0000FF0000FFull;
+  x = (x ^ (x >> 16)) & 0x1F00000000FFFFull;
+  x = (x ^ (x >> 32)) & 0x1FFFFFull;
+  return (uint32_t)x;
+}
+
+__global__ void k_complete_levels(const __grid_constant__ CompleteLevels P) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= P.oct0[P.lmin + 1]) return;
+  int l = 1;
+  while (t >= P.oct0[l + 1]) ++l;
+  const int64_t o = t - P.oct0[l];
+  const int pl = l - 1;  // level of the parent cell o
+  const int px = (int)compact3((uint64_t)o), py = (int)compact3((uint64_t)o >> 1), pz = (int)compact3((uint64_t)o >> 2);
+  const int lim = 1 << pl;
+  int32_t* nb = P.nbr[l] + o * 27;
+  for (int q = 0; q < 27; ++q) {
+    const int x = px + q % 3 - 1, y = py + (q / 3) % 3 - 1, z = pz + q / 9 - 1;
+    nb[q] = (x < 0 || y < 0 || z < 0 || x >= lim || y >= lim || z >= lim)
+                ? -1
+                : (int32_t)(spread3(x) | (spread3(y) << 1) | (spread3(z) << 2));
+  }
+  P.oct_parent[l][o] = (int32_t)o;
+  P.oct_key[l][o] = (uint64_t)o;
+  if (l < P.lmin)
+    for (int c = 0; c < 8; ++c) P.cell_child[l][o * 8 + c] = (int32_t)(o * 8 + c);
 }
 
 // nbr[l][o][q] from the level l-1 tables.  One thread per (oct, q).
@@ -448,11 +519,24 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
   CK(cudaMemsetAsync(err0, 0, (kErrWords - 1) * sizeof(unsigned), st));
   CK(cudaMemsetAsync(d_counts, 0, 5 * 4 * (lmax + 2), st));
   // ---- bottom-up sorted passes, levels lmax..lo -----------------------------
+  // (a full build places the complete base level directly instead of sorting it)
+  const bool place_base = !partial && c->lev[lmin].n_oct == (int64_t)1 << (3 * (lmin - 1)) &&
+                          (c->lev[lmin].n_leaf + (lmin < lmax ? c->lev[lmin + 1].n_oct : 0)) % 8 == 0;
   for (int l = lmax; l >= lo; --l) {
     LevelTree& T = c->lev[l];
     unsigned* err = err0 + l;
     const int64_t n_ref = (l < lmax) ? c->lev[l + 1].n_oct : 0;
     const int64_t n = T.n_leaf + n_ref;
+    int32_t* par_next = (l < lmax) ? (int32_t*)c->lev[l + 1].oct_parent.ptr : nullptr;
+    if (l == lmin && place_base) {
+      CK(cudaMemsetAsync(T.cell_child.ptr, 0x80, T.n_oct * 32, st));
+      ++c->n_launch;
+      k_place_complete<<<nblk(n), 256, 0, st>>>(l, T.n_leaf, n_ref, 8 * T.n_oct, (const int32_t*)T.ijk.ptr,
+                                                (const double*)T.mass.ptr,
+                                                n_ref ? (const uint64_t*)c->lev[l + 1].oct_key.ptr : nullptr,
+                                                (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next, err);
+      continue;
+    }
     uint64_t* ka = (uint64_t*)c->keys_a.ptr;
     uint64_t* kb = (uint64_t*)c->keys_b.ptr;
     int32_t* va = (int32_t*)c->vals_a.ptr;
@@ -477,30 +561,38 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     tmp = c->sort_tmp.bytes;
     ++c->n_cub;
     CK(cub::DeviceScan::InclusiveSum(c->sort_tmp.ptr, tmp, flags, scan, (int)n, st));
-    int32_t* par_next = (l < lmax) ? (int32_t*)c->lev[l + 1].oct_parent.ptr : nullptr;
     ++c->n_launch;
     k_scatter_level<<<nblk(n), 256, 0, st>>>(n, T.n_oct, kb, vb, scan, (uint64_t*)T.oct_key.ptr,
                                              (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next,
                                              n_ref, T.n_leaf, partial && l == lo, err);
   }
-  // ---- complete grids below lmin and the root ------------------------------
-  for (int l = 1; l < lmin && !partial; ++l) {
-    LevelTree& T = c->lev[l];
+  // ---- complete grids: levels 1..lmin-1, and the parents and neighbours of the
+  // level-lmin octs (one launch); the root cell ------------------------------------
+  if (!partial) {
+    CompleteLevels P{};
+    P.lmin = lmin;
+    int64_t tot = 0;
+    for (int l = 1; l <= lmin; ++l) {
+      LevelTree& T = c->lev[l];
+      P.oct0[l] = tot;
+      tot += T.n_oct;
+      P.oct_key[l] = (uint64_t*)T.oct_key.ptr;
+      P.oct_parent[l] = (int32_t*)T.oct_parent.ptr;
+      P.cell_child[l] = (int32_t*)T.cell_child.ptr;
+      P.nbr[l] = (int32_t*)T.nbr.ptr;
+    }
+    P.oct0[lmin + 1] = tot;
     ++c->n_launch;
-    k_full_level<<<nblk(8 * T.n_oct), 256, 0, st>>>(T.n_oct, (uint64_t*)T.oct_key.ptr,
-                                                     (int32_t*)T.oct_parent.ptr, (int32_t*)T.cell_child.ptr);
-  }
-  if (!partial) {  // octs of level lmin: their parents are the complete grid of level lmin-1
-    ++c->n_launch;
-    k_iota<<<nblk(c->lev[lmin].n_oct), 256, 0, st>>>(c->lev[lmin].n_oct, (int32_t*)c->lev[lmin].oct_parent.ptr);
+    k_complete_levels<<<nblk(tot), 256, 0, st>>>(P);
     CK(cudaMemsetAsync(c->lev[0].cell_child.ptr, 0, 4, st));
   }
-  // ---- neighbour tables top-down (levels below lo are unchanged) --------------
-  for (int l = partial ? lo : 1; l <= lmax; ++l) {
+  // ---- neighbour tables above the complete levels, top-down (levels below lo
+  // are unchanged in a partial build) -----------------------------------------------
+  for (int l = partial ? lo : lmin + 1; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
-    const int32_t* nbr_up = (l >= 2) ? (const int32_t*)c->lev[l - 1].nbr.ptr : nullptr;
+    const int32_t* nbr_up = (const int32_t*)c->lev[l - 1].nbr.ptr;
     const int32_t* cc_up = (const int32_t*)c->lev[l - 1].cell_child.ptr;
-    const int64_t n_up = (l >= 2) ? c->lev[l - 1].n_oct : 1;
+    const int64_t n_up = c->lev[l - 1].n_oct;
     ++c->n_launch;
     k_nbr<<<nblk(T.n_oct * 27), 256, 0, st>>>(l, T.n_oct, n_up, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
                                               (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr, err0 + l);
