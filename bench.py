@@ -427,11 +427,25 @@ def leg_batched(args, torch, dev, stream, flush):
     ms_seq = _timed(torch, one_by_one, K, 2, stream)
     for s in solvers:
         s.sync()
+    # accuracy of the mixed batch against FP64 solves of the same hierarchies (the FP64
+    # path matches the oracle to 1e-10 in the tests): the largest hierarchy of each base size
+    acc_err = []
+    for i in sorted({min(range(len(hs)), key=lambda j: (hs[j].lmin != b, -hs[j].n_cells)) for b in (5, 6, 7)}):
+        ref = fmm.Solver(P_ORDER, "fp64")
+        ref.set_hierarchy(hs[i], device=dev)
+        rp, ra = ref.solve()
+        ref.sync()
+        got = outs[i][1]
+        num = sum(float(((got[l].double() - ra[l]) ** 2).sum()) for l in ra)
+        den = sum(float((ra[l] ** 2).sum()) for l in ra)
+        acc_err.append(float(np.sqrt(num / den)))
+        del ref
     out = {"workload": "64 isolated hierarchies, bases 32^3/64^3/128^3 by seed, 1-3 nested levels of 1/4-1/2 "
                        "width, 1-8 Gaussian blobs, p=6 mixed", "hierarchies": len(hs), "cells": cells,
            "value": cells / (ms_batch * 1e-3), "unit": UNIT, "ms_per_batch": ms_batch,
            "one_graph_per_hierarchy_ms": ms_seq, "gpu_launches_per_batch": (l1 - l0) // (K + 3),
            "tuning_by_base_level": {str(k): v for k, v in tuned.items()},
+           "rel_rms_accel_mixed_vs_fp64": acc_err,
            "device_memory_used_gb": (total - free) / 1e9, "generation_s": gen_s,
            "step": "fmm_update_masses (device copy, all 64) + fmm_batch_solve"}
     del solvers, outs
@@ -520,11 +534,23 @@ def leg_ats(args, torch, dev, stream, flush):
     ms_full = _timed(torch, lambda: (s.set_levels(h.lmin, h.lmax, ijk, base), s.solve(out=outs[h.lmin])), K, 2, stream)
     s.sync()
     updated = sum(sum(h.n(l) for l in range(lo, h.lmax + 1)) for lo in sched)
+    # accuracy of the mixed, FP32-output solve against an FP64 solve of the same masses
+    s.set_levels(h.lmin, h.lmax, ijk, base)
+    mp, ma = s.solve(out=outs[h.lmin])
+    ref = fmm.Solver(P_ORDER, "fp64")
+    ref.set_levels(h.lmin, h.lmax, ijk, base)
+    rp, ra = ref.solve()
+    ref.sync()
+    s.sync()
+    num = sum(float(((ma[l].double() - ra[l]) ** 2).sum()) for l in ra)
+    den = sum(float((ra[l] ** 2).sum()) for l in ra)
+    err_ats = float(np.sqrt(num / den))
+    del ref
     res = {"workload": h.name + ", p=6 mixed, FP32 outputs", "cells": h.n_cells,
            "levels": [h.n(l) for l in h.levels], "schedule_lo": sched,
            "value": updated / (ms_step * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms_step,
            "cell_updates_per_coarse_step": updated, "full_rebuild_and_solve_ms": ms_full,
-           "tuning": tuning, "generation_s": gen_s,
+           "tuning": tuning, "generation_s": gen_s, "rel_rms_accel_mixed_vs_fp64": err_ats,
            "step": "per solve of the schedule: fmm_set_levels(lo) with perturbed masses + fmm_solve(lo)"}
     del s
     return res
