@@ -29,6 +29,29 @@ enum : unsigned {
 // (the finest level with an error names the cause: errors propagate upwards).
 constexpr int kErrWords = kMaxLevel + 2;
 
+// Programmatic dependent launch: kernels launched with launch_pdl may start
+// while the previous kernel on the stream drains; each one waits for it
+// (griddepcontrol.wait) before touching memory it produced, and lets its own
+// successor start early.  Both instructions are no-ops in a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Sign of prod_{i: e_i = 1} s_i for child c, s_i = +1 if bit i of c is set
 // (child in the upper half along axis i) else -1.
 __host__ __device__ inline int child_sign(int c, int e) {

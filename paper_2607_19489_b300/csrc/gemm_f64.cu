@@ -35,6 +35,8 @@ struct F64Params {
 };
 
 __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double As[TM][KC];
   __shared__ int32_t src[TM][26];
   const int n = blockIdx.y * 256 + threadIdx.x;
@@ -121,6 +123,8 @@ void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream
   P.L = (mode == kModeM2L) ? (double*)R.L.ptr : nullptr;
   dim3 grid((unsigned)((nr + TM - 1) / TM), (unsigned)((op.N + 255) / 256));
   ++c->n_launch;
+  // a normal launch: this long kernel shares the SMs with the other branch of the
+  // solve, and early-launched waiting blocks of a successor would take its slots
   k_gemm_f64<<<grid, 256, 0, st>>>(P);
 }
 

@@ -189,6 +189,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  pdl_wait();  // rows, neighbour tables and multipoles come from earlier kernels
+  pdl_trigger();
 
   if (warp < 4) {
     // ---------------- A gather (one row per thread) ----------------
@@ -439,8 +441,8 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.err = c->d_err;
   dim3 grid((unsigned)tiles, (unsigned)op.ntile, (unsigned)nz);
   ++c->n_launch;
-  k_gemm_tc<<<grid, THREADS, smem_bytes(op.BN), st>>>(*(const CUtensorMap*)op.tmap_hi,
-                                                       *(const CUtensorMap*)op.tmap_lo, P);
+  launch_pdl(k_gemm_tc, grid, THREADS, smem_bytes(op.BN), st, *(const CUtensorMap*)op.tmap_hi,
+             *(const CUtensorMap*)op.tmap_lo, P);
 }
 
 }  // namespace fmm

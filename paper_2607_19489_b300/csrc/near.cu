@@ -119,6 +119,8 @@ __host__ __device__ constexpr int gidx(int a, int b, int c) {
 // PC > 0: expansion order known at compile time (the L2P loops unroll); 0: runtime P.p.
 template <typename T, int OPB, int PC>
 __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearParams P) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ T s_m[OPB][216];
   __shared__ T s_L[OPB][kNcMax];          // local expansion of the oct's level l-2 box
   __shared__ int32_t s_nb[OPB][28];        // the 27 neighbour slots of the oct
@@ -361,6 +363,8 @@ struct Vec4<double> {
 // through shared memory at the end.
 template <typename T>
 __global__ void __launch_bounds__(256) k_near_m2p(const __grid_constant__ NearM2PParams P) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int16_t s_list[216];
   __shared__ int s_cnt;
   __shared__ int32_t s_nb[27];
@@ -483,11 +487,11 @@ namespace {
 template <typename T, int OPB>
 void near_dispatch(int p, unsigned blocks, cudaStream_t st, const NearParams& P) {
   if (p == 4)
-    k_near<T, OPB, 4><<<blocks, 8 * OPB, 0, st>>>(P);
+    launch_pdl(k_near<T, OPB, 4>, blocks, 8 * OPB, 0, st, P);
   else if (p == 6)
-    k_near<T, OPB, 6><<<blocks, 8 * OPB, 0, st>>>(P);
+    launch_pdl(k_near<T, OPB, 6>, blocks, 8 * OPB, 0, st, P);
   else
-    k_near<T, OPB, 0><<<blocks, 8 * OPB, 0, st>>>(P);
+    launch_pdl(k_near<T, OPB, 0>, blocks, 8 * OPB, 0, st, P);
 }
 
 }  // namespace
@@ -584,9 +588,9 @@ void launch_near_m2p(Ctx* c, int lo, cudaStream_t st) {
     if (!blocks) continue;
     ++c->n_launch;
     if (f64)
-      k_near_m2p<double><<<(unsigned)blocks, 256, 0, st>>>(P);
+      launch_pdl(k_near_m2p<double>, (unsigned)blocks, 256, 0, st, P);
     else
-      k_near_m2p<float><<<(unsigned)blocks, 256, 0, st>>>(P);
+      launch_pdl(k_near_m2p<float>, (unsigned)blocks, 256, 0, st, P);
   }
 }
 

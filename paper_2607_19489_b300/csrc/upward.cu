@@ -69,6 +69,8 @@ __device__ __forceinline__ void sign_transform_back(T x[8]) {
 template <typename TMono>
 __global__ void k_leaf_mono(int64_t ncell, const int32_t* __restrict__ cell_child, const double* __restrict__ mass,
                             TMono* __restrict__ mono) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ncell) return;
   int32_t ch = cell_child[i];
@@ -86,6 +88,8 @@ __global__ void __launch_bounds__(256) k_leaf_rows(int64_t n, int nc, const int3
                                                    const int32_t* __restrict__ cell_child,
                                                    const double* __restrict__ mass, Tout* __restrict__ M,
                                                    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n) return;
@@ -123,6 +127,8 @@ __global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
     __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono, const int* __restrict__ poff,
     const int* __restrict__ pg, const int* __restrict__ pe, const Tacc* __restrict__ pc,
     const Tacc* __restrict__ w0, const int* __restrict__ e0) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int W = M2MWarps<Tacc>::kWarps;
   __shared__ Tacc smem[W][8 * kNcMax];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -200,6 +206,8 @@ __global__ void __launch_bounds__(128) k_m2m_block(
     __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono,
     const int* __restrict__ poff, const int* __restrict__ pg, const int* __restrict__ pe,
     const double* __restrict__ pc) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char dsm[];
   double* S = (double*)dsm;                   // [8][nc]
   double* cf = S + 8 * nc;                    // [npairs]
@@ -252,6 +260,8 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
                                                  double* __restrict__ L, float* __restrict__ Lf,
                                                  const int* __restrict__ poff8,
                                                  const int* __restrict__ pg, const double* __restrict__ pc) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char dsm[];
   double* Lp = (double*)dsm;            // [nc]
   double* cf = Lp + nc;                 // [npairs]
@@ -309,9 +319,9 @@ void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {
   const bool f64 = c->cfg.precision == FMM_FP64;
   ++c->n_launch;
   if (f64)
-    k_leaf_mono<double><<<g, 256, 0, st>>>(n, cc, mass, (double*)T.mono.ptr);
+    launch_pdl(k_leaf_mono<double>, g, 256, 0, st, n, cc, mass, (double*)T.mono.ptr);
   else
-    k_leaf_mono<float><<<g, 256, 0, st>>>(n, cc, mass, (float*)T.mono.ptr);
+    launch_pdl(k_leaf_mono<float>, g, 256, 0, st, n, cc, mass, (float*)T.mono.ptr);
   if (l == c->lmax || !T.n_irows) return;  // no coefficient rows at the finest level
   const unsigned gr = (unsigned)((T.n_irows * 32 + 255) / 256);
   const int32_t* ir = (const int32_t*)T.irows.ptr;
@@ -319,10 +329,10 @@ void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {
   __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
   ++c->n_launch;
   if (T.m_is_f64)
-    k_leaf_rows<double><<<gr, 256, 0, st>>>(T.n_irows, c->tab.nc, ir, cc, mass, (double*)T.M.ptr,
+    launch_pdl(k_leaf_rows<double>, gr, 256, 0, st, T.n_irows, c->tab.nc, ir, cc, mass, (double*)T.M.ptr,
                                             f64 ? nullptr : hi, f64 ? nullptr : lo);
   else
-    k_leaf_rows<float><<<gr, 256, 0, st>>>(T.n_irows, c->tab.nc, ir, cc, mass, (float*)T.M.ptr, hi, lo);
+    launch_pdl(k_leaf_rows<float>, gr, 256, 0, st, T.n_irows, c->tab.nc, ir, cc, mass, (float*)T.M.ptr, hi, lo);
 }
 
 void launch_upward(Ctx* c, int b, cudaStream_t st, const int32_t* octs, int64_t n_octs) {
@@ -349,20 +359,20 @@ void launch_upward(Ctx* c, int b, cudaStream_t st, const int32_t* octs, int64_t 
   const int np = (int)c->tab.m2m_g.size();
   const size_t smb = m2m_block_smem(nc, np);
   if (f64) {
-    k_m2m_block<double, double, double><<<(unsigned)n, 128, smb, st>>>(octs, nc, np, par, ccn, (const double*)N.M.ptr, mn,
+    launch_pdl(k_m2m_block<double, double, double>, (unsigned)n, 128, smb, st, octs, nc, np, par, ccn, (const double*)N.M.ptr, mn,
                                                                      (double*)T.M.ptr, hi, lo, (double*)T.mono.ptr,
                                                                      poff, pg, pe, pc);
   } else if (T.m_is_f64) {  // mixed path, top of the tree: FP64 shifts
     if (N.m_is_f64)
-      k_m2m_block<double, double, float><<<(unsigned)n, 128, smb, st>>>(octs, nc, np, par, ccn, (const double*)N.M.ptr, mn,
+      launch_pdl(k_m2m_block<double, double, float>, (unsigned)n, 128, smb, st, octs, nc, np, par, ccn, (const double*)N.M.ptr, mn,
                                                                       (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
                                                                       poff, pg, pe, pc);
     else
-      k_m2m_block<float, double, float><<<(unsigned)n, 128, smb, st>>>(octs, nc, np, par, ccn, (const float*)N.M.ptr, mn,
+      launch_pdl(k_m2m_block<float, double, float>, (unsigned)n, 128, smb, st, octs, nc, np, par, ccn, (const float*)N.M.ptr, mn,
                                                                      (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
                                                                      poff, pg, pe, pc);
   } else {
-    k_m2m<float, float, float, float><<<g32, t32, 0, st>>>(n, octs, nc, par, ccn, (const float*)N.M.ptr, mn,
+    launch_pdl(k_m2m<float, float, float, float>, g32, t32, 0, st, n, octs, nc, par, ccn, (const float*)N.M.ptr, mn,
                                                            (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg,
                                                            pe, (const float*)c->d_m2m_c32.ptr,
                                                            (const float*)c->d_m2m_w0_32.ptr, e0);
@@ -378,7 +388,7 @@ void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t
   if (!nrows) return;
   ++c->n_launch;
   const int np = (int)c->tab.l2l_g.size();
-  k_l2l_add<<<(unsigned)nrows, 128, l2l_smem(c->tab.nc, np), st>>>(
+  launch_pdl(k_l2l_add, (unsigned)nrows, 128, l2l_smem(c->tab.nc, np), st,
       c->tab.nc, np, rows, (const int32_t*)T.oct_parent.ptr, (const int32_t*)T.slotL.ptr,
       b >= 3 ? (const int32_t*)c->lev[b - 1].slotL.ptr : nullptr, b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
       c->cfg.precision == FMM_FP64 ? nullptr : (float*)T.Lm.ptr, (double*)T.L.ptr, (float*)T.Lf.ptr,
