@@ -490,6 +490,7 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
     c->aux_stream = nullptr;  // one stream then: the solve stays correct, only serial
   }
   fmm_status s = near_init(c);
+  if (s == FMM_OK) s = upward_init(c);
   if (s == FMM_OK) s = acquire_tables(c);
   if (s != FMM_OK) {
     fmm_destroy(c);

@@ -200,6 +200,7 @@ fmm_status tree_prepare(Ctx* c);                 // oct counts, allocation (host
 fmm_status tree_enqueue(Ctx* c, cudaStream_t st);  // device work, capturable
 fmm_status tree_finish(Ctx* c, cudaStream_t st);   // the one synchronisation
 // upward.cu
+fmm_status upward_init(Ctx* c);
 void launch_mono_leaves(Ctx* c, int level, cudaStream_t st);
 // octs / rows: optional lists restricting the pass (null: the full level)
 void launch_upward(Ctx* c, int level, cudaStream_t st, const int32_t* octs = nullptr, int64_t n_octs = 0);

@@ -35,8 +35,7 @@ struct F64Params {
 };
 
 __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
-  pdl_wait();
-  pdl_trigger();
+  pdl_wait();  // no early trigger: a long kernel sharing the SMs with the other branch
   __shared__ double As[TM][KC];
   __shared__ int32_t src[TM][26];
   const int n = blockIdx.y * 256 + threadIdx.x;

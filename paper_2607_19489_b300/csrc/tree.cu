@@ -264,6 +264,7 @@ struct ListLevel {
   const int32_t* nbr;
   int32_t* out[4];  // rows, tgt, rowsL, irows
   uint8_t* leafmask;
+  const uint8_t* leafmask_next;  // level + 1 (or null)
   int32_t* slotL;    // [n_oct]: position in rowsL or -1
   int want_rowsL, want_irows;
 };
@@ -280,24 +281,33 @@ __device__ __forceinline__ int list_level(const ListParams& P, int64_t blk) {
   return k;
 }
 
-__device__ __forceinline__ unsigned oct_list_flags(const ListLevel& L, int64_t o, uint8_t* leafmask_out) {
-  int refined = 0, leaf = 0, mask = 0, grand = 0;
-  for (int c = 0; c < 8; ++c) {
-    const int32_t ch = L.cell_child[o * 8 + c];
-    refined |= ch >= 0;
-    leaf |= ch < 0;
-    mask |= (ch < 0) << c;
-    if (L.want_rowsL && ch >= 0 && ch < L.n_oct_next)
-      for (int cc = 0; cc < 8 && !grand; ++cc) grand |= L.cell_child_next[(int64_t)ch * 8 + cc] >= 0;
-  }
+// Leaf masks of every oct of every level (bit c: cell c is a leaf); an oct
+// holds a refined cell iff its mask is not 0xFF.  Read by the list flags below.
+__global__ void __launch_bounds__(kListBlock) k_leafmasks(const __grid_constant__ ListParams P) {
+  const int64_t blk = blockIdx.x;
+  const ListLevel& L = P.lev[list_level(P, blk)];
+  const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
+  if (o >= L.n_oct) return;
+  int mask = 0;
+  for (int c = 0; c < 8; ++c) mask |= (L.cell_child[o * 8 + c] < 0) << c;
+  L.leafmask[o] = (uint8_t)mask;
+}
+
+__device__ __forceinline__ unsigned oct_list_flags(const ListLevel& L, int64_t o) {
+  const unsigned mask = L.leafmask[o];
+  const int leaf = mask != 0, refined = mask != 0xFFu;
+  int grand = 0;
+  if (L.want_rowsL && refined)
+    for (int c = 0; c < 8 && !grand; ++c) {
+      const int32_t ch = L.cell_child[o * 8 + c];
+      if (ch >= 0 && ch < L.n_oct_next) grand |= L.leafmask_next[ch] != 0xFFu;
+    }
   int near_ref = 0;
   if (L.want_irows && leaf)
     for (int q = 0; q < 27 && !near_ref; ++q) {
       const int32_t nb = L.nbr[o * 27 + q];
-      if (nb < 0 || nb >= L.n_oct) continue;
-      for (int c = 0; c < 8; ++c) near_ref |= L.cell_child[(int64_t)nb * 8 + c] >= 0;
+      if (nb >= 0 && nb < L.n_oct) near_ref |= L.leafmask[nb] != 0xFFu;
     }
-  if (leafmask_out) *leafmask_out = (uint8_t)mask;
   return (unsigned)refined | ((unsigned)leaf << 1) | ((unsigned)grand << 2) | ((unsigned)(leaf && near_ref) << 3);
 }
 
@@ -308,7 +318,7 @@ __global__ void __launch_bounds__(kListBlock) k_lists_count(const __grid_constan
   const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
   unsigned f = 0;
   if (o < L.n_oct) {
-    f = oct_list_flags(L, o, L.leafmask + o);
+    f = oct_list_flags(L, o);
     L.slotL[o] = -1;
   }
   flags[blk * kListBlock + threadIdx.x] = (uint8_t)f;
@@ -619,6 +629,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
       L.out[2] = (int32_t*)T.rowsL.ptr;
       L.out[3] = (int32_t*)T.irows.ptr;
       L.leafmask = (uint8_t*)T.leafmask.ptr;
+      L.leafmask_next = l < lmax ? (const uint8_t*)c->lev[l + 1].leafmask.ptr : nullptr;
       L.slotL = (int32_t*)T.slotL.ptr;
       L.want_rowsL = l + 2 <= lmax;
       L.want_irows = l >= lmin;
@@ -628,7 +639,8 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     uint8_t* fl = (uint8_t*)c->flags.ptr;            // nb * kListBlock bytes
     int32_t* blk_counts = (int32_t*)c->scan.ptr;     // nb * 4
     int32_t* blk_off = blk_counts + nb * 4;          // nb * 4
-    c->n_launch += 3;
+    c->n_launch += 4;
+    k_leafmasks<<<(unsigned)nb, kListBlock, 0, st>>>(P);
     k_lists_count<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_counts);
     k_lists_scan<<<(unsigned)(4 * P.nlev), 1024, 0, st>>>(P, blk_counts, blk_off, d_counts);
     k_lists_write<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_off);

@@ -107,76 +107,88 @@ __global__ void __launch_bounds__(256) k_leaf_rows(int64_t n, int nc, const int3
   }
 }
 
-// M2M: one warp per oct of level b+1, i.e. per refined cell of level b.
-// An oct whose eight cells are all leaves (the bulk of a refined region's
-// parent level) has point-mass children only: after the sign transform over
-// the children only gamma = 0 survives, so each output is one product
+// M2M in FP32 (box levels above the FP64 top of the tree): one warp per oct
+// of level b+1, i.e. per refined cell of level b, eight warps per block.  An
+// oct whose eight cells are all leaves (the bulk of a refined region's parent
+// level) has point-mass children only: after the sign transform over the
+// children only gamma = 0 survives, so each output is one product
 // w0[alpha] * S[e0[alpha]] with S held in lanes 0..7.  Other octs stage the
-// children's coefficients in the warp's slice of shared memory, transform
-// them in place and run the short per-alpha sums.
-template <typename Tacc>
-struct M2MWarps {
-  static constexpr int kWarps = sizeof(Tacc) == 8 ? 4 : 8;  // 8 * kNcMax * kWarps * size <= 48 KB
-};
+// children's coefficients in the warp's slice of shared memory, transform them
+// in place and run the per-alpha sums over pair tables that the block stages
+// once (only when one of its warps needs them).  Dynamic shared memory:
+// m2m_smem.
+constexpr int kM2MWarps = 8;
 
-template <typename Tin, typename Tacc, typename Tout, typename TMono>
-__global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
-    int64_t n_oct_next, const int32_t* __restrict__ octs, int nc, const int32_t* __restrict__ oct_parent_next,
-    const int32_t* __restrict__ cell_child_next, const Tin* __restrict__ Mnext,
-    const double* __restrict__ mass_next, Tout* __restrict__ Mout, __nv_bfloat16* __restrict__ hi,
-    __nv_bfloat16* __restrict__ lo, TMono* __restrict__ mono, const int* __restrict__ poff,
-    const int* __restrict__ pg, const int* __restrict__ pe, const Tacc* __restrict__ pc,
-    const Tacc* __restrict__ w0, const int* __restrict__ e0) {
+inline size_t m2m_smem(int nc, int npairs) {
+  return (size_t)npairs * 8 + (size_t)(nc + 1) * 4 + kM2MWarps * 8 * 4 + (size_t)kM2MWarps * 8 * nc * 4;
+}
+
+__global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
+    int64_t n_oct_next, const int32_t* __restrict__ octs, int nc, int npairs,
+    const int32_t* __restrict__ oct_parent_next, const int32_t* __restrict__ cell_child_next,
+    const float* __restrict__ Mnext, const double* __restrict__ mass_next, float* __restrict__ Mout,
+    __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, float* __restrict__ mono,
+    const int* __restrict__ poff, const int* __restrict__ pg, const int* __restrict__ pe,
+    const float* __restrict__ pc, const float* __restrict__ w0, const int* __restrict__ e0) {
   pdl_wait();
   pdl_trigger();
-  constexpr int W = M2MWarps<Tacc>::kWarps;
-  __shared__ Tacc smem[W][8 * kNcMax];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float* cf = (float*)dsm;                   // [npairs] coefficients
+  int* gx = (int*)(cf + npairs);             // [npairs] gamma + nc * e
+  int* off = gx + npairs;                    // [nc + 1]
+  int* ccs = off + nc + 1;                   // [warps][8] children of each warp's oct
+  float* Sall = (float*)(ccs + 8 * kM2MWarps);  // [warps][8 * nc]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * W + warp;
-  if (i >= n_oct_next) return;  // warp-uniform; no block-wide barrier below
-  const int64_t o = octs ? octs[i] : i;
-  const int64_t cell = oct_parent_next[o];
+  const int64_t i = (int64_t)blockIdx.x * kM2MWarps + warp;
+  const bool valid = i < n_oct_next;
+  const int64_t o = valid ? (octs ? octs[i] : i) : 0;
+  const int64_t cell = valid ? oct_parent_next[o] : 0;
   const int64_t c0 = o * 8;
-  const int32_t cc = lane < 8 ? cell_child_next[c0 + lane] : -1;
+  const int32_t cc = (valid && lane < 8) ? cell_child_next[c0 + lane] : -1;
   const unsigned full = 0xffffffffu;
-  if (__all_sync(full, cc < 0)) {
-    Tacc m = lane < 8 ? (Tacc)mass_next[-1 - (int64_t)cc] : (Tacc)0;
+  const bool leaf_only = __all_sync(full, cc < 0);
+  if (__syncthreads_or(valid && !leaf_only)) {  // block-uniform: stage the pair tables
+    for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
+      cf[j] = pc[j];
+      gx[j] = pg[j] + nc * pe[j];
+    }
+    for (int k = threadIdx.x; k <= nc; k += blockDim.x) off[k] = poff[k];
+    __syncthreads();
+  }
+  if (!valid) return;  // warp-uniform; no block-wide barrier below
+  if (leaf_only) {
+    float m = lane < 8 ? (float)mass_next[-1 - (int64_t)cc] : 0.0f;
 #pragma unroll
     for (int axis = 0; axis < 3; ++axis) {  // S_e over lanes 0..7, as sign_transform
-      const Tacc other = __shfl_xor_sync(full, m, 1 << axis);
+      const float other = __shfl_xor_sync(full, m, 1 << axis);
       m = (lane & (1 << axis)) ? m - other : m + other;
     }
     for (int kb = 0; kb < nc; kb += 32) {
       const int k = kb + lane;
       const int e = k < nc ? e0[k] : 0;
-      const Tacc s = __shfl_sync(full, m, e);
+      const float sv = __shfl_sync(full, m, e);
       if (k < nc) {
-        const Tout v = (Tout)(w0[k] * s);
+        const float v = w0[k] * sv;
         Mout[cell * nc + k] = v;
         if (hi) split_bf16(v, hi[cell * nc + k], lo[cell * nc + k]);
-        if (k == 0) mono[cell] = (TMono)v;
+        if (k == 0) mono[cell] = v;
       }
     }
     return;
   }
-  Tacc* S = smem[warp];
-  for (int base = 0; base < 8 * nc; base += 32) {
-    const int idx = base + lane;
-    const int c = min(idx / nc, 7);
-    const int32_t ch = __shfl_sync(full, cc, c);
-    if (idx < 8 * nc) {
-      const int g = idx - c * nc;
-      Tacc v;
-      if (ch < 0)
-        v = (g == 0) ? (Tacc)mass_next[-1 - (int64_t)ch] : (Tacc)0;
-      else
-        v = (Tacc)Mnext[(c0 + c) * nc + g];
-      S[idx] = v;
-    }
+  int* wcc = ccs + 8 * warp;
+  float* S = Sall + (size_t)warp * 8 * nc;
+  if (lane < 8) wcc[lane] = cc;
+  __syncwarp();
+#pragma unroll 4
+  for (int idx = lane; idx < 8 * nc; idx += 32) {
+    const int c = idx / nc, g = idx - c * nc;
+    const int32_t ch = wcc[c];
+    S[idx] = ch < 0 ? (g == 0 ? (float)mass_next[-1 - (int64_t)ch] : 0.0f) : Mnext[(c0 + c) * nc + g];
   }
   __syncwarp();
   for (int g = lane; g < nc; g += 32) {
-    Tacc x[8];
+    float x[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) x[c] = S[c * nc + g];
     sign_transform(x);
@@ -185,12 +197,11 @@ __global__ void __launch_bounds__(32 * M2MWarps<Tacc>::kWarps) k_m2m(
   }
   __syncwarp();
   for (int k = lane; k < nc; k += 32) {
-    Tacc out = 0;
-    for (int j = poff[k]; j < poff[k + 1]; ++j) out += pc[j] * S[pe[j] * nc + pg[j]];
-    const Tout v = (Tout)out;
-    Mout[cell * nc + k] = v;
-    if (hi) split_bf16(v, hi[cell * nc + k], lo[cell * nc + k]);
-    if (k == 0) mono[cell] = (TMono)v;
+    float out = 0;
+    for (int j = off[k]; j < off[k + 1]; ++j) out += cf[j] * S[gx[j]];
+    Mout[cell * nc + k] = out;
+    if (hi) split_bf16(out, hi[cell * nc + k], lo[cell * nc + k]);
+    if (k == 0) mono[cell] = out;
   }
 }
 
@@ -309,6 +320,17 @@ inline size_t l2l_smem(int nc, int npairs) { return (size_t)nc * 8 + (size_t)npa
 
 }  // namespace
 
+// Kernel attributes set once per context creation (not inside a stream capture):
+// the FP32 M2M needs more than 48 KB of dynamic shared memory at p = 8.
+fmm_status upward_init(Ctx* c) {
+  cudaError_t e = cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2m_smem(165, 3003));
+  if (e != cudaSuccess) {
+    c->last_error = std::string("upward_init: ") + cudaGetErrorString(e);
+    return FMM_ERR_CUDA;
+  }
+  return FMM_OK;
+}
+
 void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {
   LevelTree& T = c->lev[l];
   int64_t n = 8 * T.n_oct;
@@ -353,8 +375,7 @@ void launch_upward(Ctx* c, int b, cudaStream_t st, const int32_t* octs, int64_t 
   const double* mn = (const double*)N.mass.ptr;
   __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
   __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
-  const unsigned g32 = (unsigned)((n + M2MWarps<float>::kWarps - 1) / M2MWarps<float>::kWarps);
-  constexpr int t32 = 32 * M2MWarps<float>::kWarps;
+  const unsigned g32 = (unsigned)((n + kM2MWarps - 1) / kM2MWarps);
   ++c->n_launch;
   const int np = (int)c->tab.m2m_g.size();
   const size_t smb = m2m_block_smem(nc, np);
@@ -372,10 +393,10 @@ void launch_upward(Ctx* c, int b, cudaStream_t st, const int32_t* octs, int64_t 
                                                                      (double*)T.M.ptr, hi, lo, (float*)T.mono.ptr,
                                                                      poff, pg, pe, pc);
   } else {
-    launch_pdl(k_m2m<float, float, float, float>, g32, t32, 0, st, n, octs, nc, par, ccn, (const float*)N.M.ptr, mn,
-                                                           (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg,
-                                                           pe, (const float*)c->d_m2m_c32.ptr,
-                                                           (const float*)c->d_m2m_w0_32.ptr, e0);
+    const size_t sm32 = m2m_smem(nc, np);
+    launch_pdl(k_m2m, g32, 32 * kM2MWarps, sm32, st, n, octs, nc, np, par, ccn, (const float*)N.M.ptr, mn,
+               (float*)T.M.ptr, hi, lo, (float*)T.mono.ptr, poff, pg, pe, (const float*)c->d_m2m_c32.ptr,
+               (const float*)c->d_m2m_w0_32.ptr, e0);
   }
 }
 
