@@ -530,6 +530,16 @@ def leg_ats(args, torch, dev, stream, flush):
 
     K = max(3, min(args.steps // 40, 10))
     ms_step = _timed(torch, coarse_step, K, 3, stream)
+    # one more coarse step with an event pair around every solve of the schedule
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(sched) + 1)]
+    evs[0].record(stream)
+    for i, (lo, ms) in enumerate(zip(sched, pert)):
+        s.set_levels(h.lmin, h.lmax, ijk[lo - h.lmin:], ms, lo=lo)
+        s.solve(lo, out=outs[lo])
+        evs[i + 1].record(stream)
+    evs[-1].synchronize()
+    per_solve = [{"lo": lo, "ms": evs[i].elapsed_time(evs[i + 1]),
+                  "cells": sum(h.n(l) for l in range(lo, h.lmax + 1))} for i, lo in enumerate(sched)]
     s.set_levels(h.lmin, h.lmax, ijk, base)
     ms_full = _timed(torch, lambda: (s.set_levels(h.lmin, h.lmax, ijk, base), s.solve(out=outs[h.lmin])), K, 2, stream)
     s.sync()
@@ -549,6 +559,7 @@ def leg_ats(args, torch, dev, stream, flush):
     res = {"workload": h.name + ", p=6 mixed, FP32 outputs", "cells": h.n_cells,
            "levels": [h.n(l) for l in h.levels], "schedule_lo": sched,
            "value": updated / (ms_step * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms_step,
+           "per_solve": per_solve,
            "cell_updates_per_coarse_step": updated, "full_rebuild_and_solve_ms": ms_full,
            "tuning": tuning, "generation_s": gen_s, "rel_rms_accel_mixed_vs_fp64": err_ats,
            "step": "per solve of the schedule: fmm_set_levels(lo) with perturbed masses + fmm_solve(lo)"}
