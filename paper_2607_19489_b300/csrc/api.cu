@@ -1173,7 +1173,7 @@ void fmm_destroy(fmm_ctx* c) {
   drop_batch_graphs_of(c);
   release_tables(c);
   for (auto& T : c->lev) {
-    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.ancflag, &T.tgt, &T.ijk,
+    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.tgt, &T.ijk,
                       &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc})
       buf_free(c, *b);
   }
@@ -1183,7 +1183,7 @@ void fmm_destroy(fmm_ctx* c) {
                     &c->d_l2lT_c, &c->d_m2pT, &c->d_m2lT, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
-                    &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->out_stage, &c->in_stage})
+                    &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->anc_flags, &c->out_stage, &c->in_stage})
     buf_free(c, *b);
   if (c->d_err) cudaFree(c->d_err);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);

@@ -25,9 +25,13 @@ enum : unsigned {
   kErrTimeout = 32u,
   kErrStructure = 64u,  // a partial update changed the cells of its lowest level
 };
-// Device error words: [0] solves (timeouts), [1 + l] the tree build of level l
-// (the finest level with an error names the cause: errors propagate upwards).
-constexpr int kErrWords = kMaxLevel + 2;
+// Device error words: [0] solves (timeouts), [1 + l] the sorted pass of level l,
+// [kErrNbr0 + l] the neighbour tables of level l.  The sorted passes see the
+// input itself; the neighbour stage reads the links the passes wrote, so its
+// words name the cause only when every pass was clean.  Within each group the
+// finest level with an error names the cause (errors propagate upwards).
+constexpr int kErrNbr0 = kMaxLevel + 2;
+constexpr int kErrWords = kErrNbr0 + kMaxLevel + 1;
 
 // Programmatic dependent launch: kernels launched with launch_pdl may start
 // while the previous kernel on the stream drains; each one waits for it
@@ -92,7 +96,7 @@ struct LevelTree {
   DevBuf srcP, srcL;     // int32: octs read by M2P rows / by M2L rows of this level
   int64_t n_srcP = 0, n_srcL = 0;
   // incremental solves: octs with a descendant at level Ctx::anc_d (ancestor lists)
-  DevBuf anc, ancflag;   // int32 [n_anc], uint8 [n_oct]
+  DevBuf anc;           // int32 [n_anc]
   int64_t n_anc = 0;
   // inputs kept for adaptive time stepping (replaced by set_levels)
   DevBuf ijk;            // int32 [n_leaf][3]
@@ -137,6 +141,7 @@ struct Ctx {
   GemmOperand op_m2p, op_m2l;
   // scratch
   DevBuf sort_tmp, keys_a, keys_b, vals_a, vals_b, flags, scan, err_word, counter;
+  DevBuf anc_flags;     // uint8: one visited flag per oct of levels 1..anc_req-1 (ancestor walks)
   DevBuf out_stage;     // device staging for host outputs
   DevBuf in_stage;      // device staging for host inputs
   unsigned* d_err = nullptr;

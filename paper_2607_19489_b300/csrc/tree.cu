@@ -20,7 +20,6 @@
 // bits, every kernel bounds-checks the indices it follows, and one
 // synchronisation at the end reads the error word and the list lengths.
 #include <cub/cub.cuh>
-#include <thrust/iterator/counting_iterator.h>
 
 #include "fmm_internal.cuh"
 
@@ -389,18 +388,34 @@ __global__ void __launch_bounds__(kListBlock) k_lists_write(const __grid_constan
   }
 }
 
-// Octs of level b with a descendant at level d: for b = d-1 the octs holding a
-// refined cell, above that the octs with a cell whose child oct is flagged.
-__global__ void k_anc_flags(int64_t n_oct, const int32_t* __restrict__ cc, const uint8_t* __restrict__ next,
-                            int64_t n_next, uint8_t* __restrict__ out) {
+// Ancestor lists of level d: the octs of each level b < d with a descendant
+// oct at level d.  Every level-d oct walks up its parent chain; the first
+// walker to reach an oct sets its visited flag, appends it to its level's
+// list and goes on, later walkers stop there.  Work is proportional to the
+// ancestors, not to the octs of the coarser levels.
+struct AncParams {
+  int d;
+  int64_t n_oct[kMaxLevel + 1];
+  int64_t flag_off[kMaxLevel + 1];  // byte offset of level b's flags (multiple of 4)
+  const int32_t* oct_parent[kMaxLevel + 1];
+  int32_t* anc[kMaxLevel + 1];
+  uint8_t* flags;
+  int32_t* counts;  // [b]: length of level b's list
+};
+
+__global__ void k_anc_walk(const __grid_constant__ AncParams A, int64_t n_oct_d) {
   const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (o >= n_oct) return;
-  uint8_t f = 0;
-  for (int c = 0; c < 8; ++c) {
-    const int32_t ch = cc[o * 8 + c];
-    if (ch >= 0 && ch < n_next) f |= next ? next[ch] : (uint8_t)1;
+  if (o >= n_oct_d) return;
+  int32_t cur = (int32_t)o;
+  for (int l = A.d; l >= 2; --l) {
+    const int32_t up = A.oct_parent[l][cur] >> 3;
+    if (up < 0 || up >= A.n_oct[l - 1]) return;
+    unsigned int* word = (unsigned int*)(A.flags + A.flag_off[l - 1] + (up & ~3));
+    const unsigned int bit = 1u << (8 * (up & 3));
+    if (atomicOr(word, bit) & bit) return;
+    A.anc[l - 1][atomicAdd(A.counts + (l - 1), 1)] = up;
+    cur = up;
   }
-  out[o] = f;
 }
 
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
@@ -481,7 +496,11 @@ fmm_status tree_prepare(Ctx* c) {
     CK(buf_ensure(c, T.leafmask, T.n_oct));
     CK(buf_ensure(c, T.slotL, T.n_oct * 4));
     CK(buf_ensure(c, T.anc, T.n_oct * 4));
-    CK(buf_ensure(c, T.ancflag, T.n_oct));
+  }
+  {
+    int64_t nf = 4;
+    for (int b = 1; b < c->anc_req && b <= lmax; ++b) nf += (c->lev[b].n_oct + 3) & ~(int64_t)3;
+    CK(buf_ensure(c, c->anc_flags, nf));
   }
   CK(buf_ensure(c, c->lev[0].cell_child, 32));
   CK(buf_ensure(c, c->keys_a, nmax * 8));
@@ -493,16 +512,9 @@ fmm_status tree_prepare(Ctx* c) {
   CK(buf_ensure(c, c->flags, std::max<int64_t>(nmax * 8, list_blocks * kListBlock)));
   CK(buf_ensure(c, c->scan, std::max<int64_t>(nmax * 4, list_blocks * 32)));
   CK(buf_ensure(c, c->counter, 5 * 4 * (lmax + 2)));
-  // CUB temporary storage for the largest sort, scan and select of this build
+  // CUB temporary storage for the largest sort and scan of this build
   size_t tmp_max = 0;
   {
-    int64_t omax = 1;
-    for (int l = 1; l <= lmax; ++l) omax = std::max<int64_t>(omax, c->lev[l].n_oct);
-    size_t t = 0;
-    thrust::counting_iterator<int32_t> it(0);
-    CK(cub::DeviceSelect::Flagged(nullptr, t, it, (const uint8_t*)nullptr, (int32_t*)nullptr, (int32_t*)nullptr,
-                                  (int)omax));
-    tmp_max = t;
     for (int l = lo; l <= lmax; ++l) {
       const int n = (int)(8 * c->lev[l].n_oct);
       size_t t = 0;
@@ -524,7 +536,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
   const int lmin = c->lmin, lmax = c->lmax;
   const int lo = c->tree_lo;
   const bool partial = lo > lmin;
-  unsigned* err0 = c->d_err + 1;  // err0[l]: errors found while building level l
+  unsigned* err0 = c->d_err + 1;  // err0[l]: errors found by the sorted pass of level l
   int32_t* d_counts = (int32_t*)c->counter.ptr;  // [5][lmax+2]: rows, tgt, rowsL, irows, anc
   CK(cudaMemsetAsync(err0, 0, (kErrWords - 1) * sizeof(unsigned), st));
   CK(cudaMemsetAsync(d_counts, 0, 5 * 4 * (lmax + 2), st));
@@ -605,19 +617,21 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     const int64_t n_up = c->lev[l - 1].n_oct;
     ++c->n_launch;
     k_nbr<<<nblk(T.n_oct * 27), 256, 0, st>>>(l, T.n_oct, n_up, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
-                                              (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr, err0 + l);
+                                              (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr,
+                                              c->d_err + kErrNbr0 + l);
   }
-  // ---- row lists ------------------------------------------------------------
+  // ---- row lists (a partial build changes the lists of levels lo-1..lmax only) ----
+  const int list0 = partial ? lo - 1 : 1;
   {
     const int stride = lmax + 2;
     ListParams P{};
-    P.nlev = lmax;
-    P.level0 = 1;
+    P.nlev = lmax - list0 + 1;
+    P.level0 = list0;
     P.stride = stride;
     int64_t nb = 0;
-    for (int l = 1; l <= lmax; ++l) {
+    for (int l = list0; l <= lmax; ++l) {
       LevelTree& T = c->lev[l];
-      ListLevel& L = P.lev[l - 1];
+      ListLevel& L = P.lev[l - list0];
       L.n_oct = T.n_oct;
       L.n_oct_next = l < lmax ? c->lev[l + 1].n_oct : 0;
       L.blk0 = nb;
@@ -648,25 +662,31 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
   // ---- ancestor lists of level anc_req (incremental solves) ------------------------
   const int d = c->anc_req;
   if (d > lmin && d <= lmax) {
-    thrust::counting_iterator<int32_t> it(0);
-    for (int b = d - 1; b >= 1; --b) {
+    AncParams A{};
+    A.d = d;
+    int64_t off = 0;
+    for (int b = 1; b < d; ++b) {
       LevelTree& B = c->lev[b];
-      ++c->n_launch;
-      k_anc_flags<<<nblk(B.n_oct), 256, 0, st>>>(B.n_oct, (const int32_t*)B.cell_child.ptr,
-                                                 b == d - 1 ? nullptr : (const uint8_t*)c->lev[b + 1].ancflag.ptr,
-                                                 c->lev[b + 1].n_oct, (uint8_t*)B.ancflag.ptr);
-      size_t tmp = c->sort_tmp.bytes;
-      ++c->n_cub;
-      CK(cub::DeviceSelect::Flagged(c->sort_tmp.ptr, tmp, it, (const uint8_t*)B.ancflag.ptr, (int32_t*)B.anc.ptr,
-                                    d_counts + 4 * (lmax + 2) + b, (int)B.n_oct, st));
+      A.flag_off[b] = off;
+      A.n_oct[b] = B.n_oct;
+      off += (B.n_oct + 3) & ~(int64_t)3;  // 4-byte aligned: the walk sets flags with word atomics
+      A.oct_parent[b + 1] = (const int32_t*)c->lev[b + 1].oct_parent.ptr;
+      A.anc[b] = (int32_t*)B.anc.ptr;
     }
+    A.flags = (uint8_t*)c->anc_flags.ptr;
+    A.counts = d_counts + 4 * (lmax + 2);
+    CK(cudaMemsetAsync(A.flags, 0, off, st));
+    ++c->n_launch;
+    k_anc_walk<<<nblk(c->lev[d].n_oct), 256, 0, st>>>(A, c->lev[d].n_oct);
   }
   return FMM_OK;
 }
 
 // The one synchronisation of a tree build: error words and list lengths.  An
 // invalid level also corrupts the levels above it (their keys come from its
-// octs), so the finest level with an error names the cause.
+// octs), so the finest level with an error names the cause; errors of the
+// sorted passes come before those of the neighbour stage, which reads their
+// output.
 fmm_status tree_finish(Ctx* c, cudaStream_t st) {
   const int lmin = c->lmin, lmax = c->lmax;
   const int stride = lmax + 2;
@@ -676,23 +696,28 @@ fmm_status tree_finish(Ctx* c, cudaStream_t st) {
   unsigned ev[kErrWords] = {};
   CK(cudaMemcpyAsync(ev, c->d_err, kErrWords * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  for (int l = lmax; l >= 1; --l) {
-    const unsigned e = ev[1 + l] | c->tree_host_err[l];
-    const fmm_status s = err_to_status(e);
-    if (s != FMM_OK) {
-      c->last_error = (e & kErrStructure)
-                          ? "tree: a partial update changed the cells of its lowest level; update from one level coarser"
-                          : "tree: invalid hierarchy at level " + std::to_string(l) + " (error bits " + std::to_string(e) +
-                                ")";
-      return s;
+  for (int group = 0; group < 2; ++group) {
+    for (int l = lmax; l >= 1; --l) {
+      const unsigned e = group == 0 ? ev[1 + l] | c->tree_host_err[l] : ev[kErrNbr0 + l];
+      const fmm_status s = err_to_status(e);
+      if (s != FMM_OK) {
+        c->last_error = (e & kErrStructure)
+                            ? "tree: a partial update changed the cells of its lowest level; update from one level coarser"
+                            : "tree: invalid hierarchy at level " + std::to_string(l) + " (error bits " +
+                                  std::to_string(e) + ")";
+        return s;
+      }
     }
   }
+  const int list0 = c->tree_lo > lmin ? c->tree_lo - 1 : 1;  // the levels whose lists were rebuilt
   for (int l = 1; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
-    T.n_rows = counts[0 * stride + l];
-    T.n_tgt = counts[1 * stride + l];
-    T.n_rowsL = (l + 2 <= lmax) ? counts[2 * stride + l] : 0;
-    T.n_irows = (l >= lmin) ? counts[3 * stride + l] : 0;
+    if (l >= list0) {
+      T.n_rows = counts[0 * stride + l];
+      T.n_tgt = counts[1 * stride + l];
+      T.n_rowsL = (l + 2 <= lmax) ? counts[2 * stride + l] : 0;
+      T.n_irows = (l >= lmin) ? counts[3 * stride + l] : 0;
+    }
     T.n_anc = (l < c->anc_req) ? counts[4 * stride + l] : 0;
   }
   return FMM_OK;
