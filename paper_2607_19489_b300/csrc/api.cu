@@ -635,13 +635,16 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // update of levels d..lmax only the cells with descendants at level d change
   // (multipoles are totals over the finer levels): M2M runs on all octs of
   // levels >= d and on the ancestor octs above; with no change it is skipped.
+  // Nothing reads the multipoles of level 1: its cells are never leaves (lmin
+  // >= 2), and M2L (box levels >= 2) and M2P (the 26 neighbour octs of the one
+  // level-1 oct lie outside the box) have no level-1 sources.
   if (d <= lmin || (d <= lmax && c->anc_d != d)) {
     for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
-    for (int b = lmax - 1; b >= 1; --b) launch_upward(c, b, st);
+    for (int b = lmax - 1; b >= 2; --b) launch_upward(c, b, st);
   } else if (d <= lmax) {
     for (int l = d; l <= lmax; ++l) launch_mono_leaves(c, l, st);
     for (int b = lmax - 1; b >= d - 1; --b) launch_upward(c, b, st);
-    for (int b = d - 2; b >= 1; --b)
+    for (int b = d - 2; b >= 2; --b)
       launch_upward(c, b, st, (const int32_t*)c->lev[b + 1].anc.ptr, c->lev[b + 1].n_anc);
   }
   stage_event(c, 1, st);

@@ -9,10 +9,10 @@
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
 //
 // Per CTA: 128 rows x BN columns, accumulator in tensor memory (TMEM).
-//   warps 0-3  gather A rows with cp.async into 128B-swizzled shared memory
+//   warps 0-3  gather A rows with cp.async into 64B-swizzled shared memory
 //              (the rows are neighbour octs, so TMA tiles cannot fetch them),
 //              then run the epilogue (tcgen05.ld, scatter-add to the targets)
-//   warp 4     allocates TMEM and loads B tiles with TMA (SWIZZLE_128B)
+//   warp 4     allocates TMEM and loads B tiles with TMA (SWIZZLE_64B)
 //   warp 5     one thread issues tcgen05.mma (M=128, N=BN, K=16) per slice
 // Split-K over grid.z; partial sums are added with atomics.  Every wait on an
 // mbarrier is bounded by a wall-clock limit; on expiry the CTA latches
@@ -193,7 +193,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   pdl_trigger();
 
   if (warp < 4) {
-    // ---------------- A gather (one row per thread) ----------------
+    // ---------------- A gather ----------------
+    // Thread t owns row t for the epilogue (TMEM lane t) and writes that row's
+    // neighbour table.  The copies are spread differently: four lanes fetch the
+    // four 16-byte chunks of one row's 64-byte slice, eight rows per
+    // instruction, so every 32-byte sector is requested once and whole.
     const int t = threadIdx.x;
     int si = 0;
     while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].tile0) ++si;
@@ -201,49 +205,57 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int64_t row_idx = (int64_t)(blockIdx.x - S.tile0) * BM + t;
     const bool valid = row_idx < S.nrows;
     const int32_t roct = valid ? S.rows[row_idx] : 0;
-    int32_t* myn = s_nbr + t * kNbrStride;  // read by this thread only
+    int32_t* myn = s_nbr + t * kNbrStride;
     for (int q = 0; q < 26; ++q) myn[q] = valid ? S.nbr[(int64_t)roct * 27 + c_nbr26[q]] : -1;
-    const uint32_t myn_s = smem_u32(myn);  // read back with ld.shared (a plain pointer would be generic)
-    const uint32_t ahi0 = smem_u32(Ahi) + t * (BK * 2), alo0 = smem_u32(Alo) + t * (BK * 2);
+    __syncwarp();  // each warp gathers its own 32 rows and reads their tables below
+    const int jj = lane & 3;  // 16-byte chunk within the row slice
+    uint32_t nbr_s[4], dst[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = warp * 32 + i * 8 + (lane >> 2);
+      nbr_s[i] = smem_u32(s_nbr + r * kNbrStride);  // read back with ld.shared (a plain pointer would be generic)
+      dst[i] = (uint32_t)(r * (BK * 2)) + (uint32_t)((jj ^ ((r >> 1) & 3)) << 4);
+    }
+    const uint32_t ahi0 = smem_u32(Ahi), alo0 = smem_u32(Alo);
+    // Up to three stages of copies in flight: after committing stage it, wait
+    // for stage it-2 and mark it full.
+    constexpr int kInFlight = 2;
     bool ok = true;
     for (int it = 0; it < nit && ok; ++it) {
       const int s = it % STAGES;
       if (it >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, abort);
       if (!ok) break;
-      const int k0 = (kc_begin + it) * BK;
-      const int qi0 = k0 / P.KQ;  // a BK-wide slice spans at most two offset segments
-      const int kb = (qi0 + 1) * P.KQ;
+      const int k = (kc_begin + it) * BK + 8 * jj;  // 8 elements never straddle an offset segment (KQ % 8 == 0)
+      int qi = -1, off = 0;
+      if (k < P.Kvalid) {
+        qi = k / P.KQ;
+        off = k - qi * P.KQ;
+      }
 #pragma unroll
-      for (int j = 0; j < BK / 8; ++j) {
-        const int k = k0 + 8 * j;
+      for (int i = 0; i < 4; ++i) {
         int32_t src = -1;
-        int off = 0;
-        if (k < P.Kvalid) {
-          const int qi = (k >= kb) ? qi0 + 1 : qi0;
-          off = k - qi * P.KQ;
-          asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
-        }
-        const uint32_t sw = (uint32_t)((j ^ ((t >> 1) & 3)) << 4);
+        if (qi >= 0) asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(nbr_s[i] + 4 * qi));
         const __nv_bfloat16* gh = src >= 0 ? S.Ahi + (int64_t)src * P.KQ + off : S.Ahi;
         const __nv_bfloat16* gl = src >= 0 ? S.Alo + (int64_t)src * P.KQ + off : S.Alo;
         const uint32_t sz = src >= 0 ? 16u : 0u;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(ahi0 + s * a_bytes + sw), "l"(gh),
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(ahi0 + s * a_bytes + dst[i]), "l"(gh),
                      "r"(sz)
                      : "memory");
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(alo0 + s * a_bytes + sw), "l"(gl),
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(alo0 + s * a_bytes + dst[i]), "l"(gl),
                      "r"(sz)
                      : "memory");
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
-      if (it > 0) {
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      if (it >= kInFlight) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(kInFlight) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(full0 + 8 * ((it - 1) % STAGES));
+        mbar_arrive(full0 + 8 * ((it - kInFlight) % STAGES));
       }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (ok && nit > 0) mbar_arrive(full0 + 8 * ((nit - 1) % STAGES));
+    if (ok)  // the stages committed but not yet marked full
+      for (int r = max(0, nit - kInFlight); r < nit; ++r) mbar_arrive(full0 + 8 * (r % STAGES));
 
     // ---------------- epilogue ----------------
     bool have = ok && nit > 0 && mbar_wait(done, 0, abort);
