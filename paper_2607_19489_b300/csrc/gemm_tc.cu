@@ -8,12 +8,18 @@
 // Each operand is split x = hi + lo with hi, lo in BF16; the product keeps
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
 //
-// Per CTA: 128 rows x BN columns, accumulator in tensor memory (TMEM).
-//   warps 0-3  gather A rows with cp.async into 64B-swizzled shared memory
-//              (the rows are neighbour octs, so TMA tiles cannot fetch them),
-//              then run the epilogue (tcgen05.ld, scatter-add to the targets)
-//   warp 4     allocates TMEM and loads B tiles with TMA (SWIZZLE_64B)
-//   warp 5     one thread issues tcgen05.mma (M=128, N=BN, K=16) per slice
+// Per CTA: 128 rows x BN columns.  Tensor memory (TMEM, 512 columns) holds the
+// FP32 accumulator (columns 0..255) and SA stages of the A operand (columns
+// 256..511, 32 per stage: the hi and lo halves of a BK-wide slice of every
+// row, two bf16 per column); the MMA reads A from TMEM and B from shared memory.
+//   warps 0-15   producers: the rows are neighbour octs (no TMA tile fetches
+//                them), so thread t of warp w loads row 32 (w % 4) + t, i.e.
+//                its own TMEM lane, with vector loads and tcgen05.st; the four
+//                warps of a lane quarter take every fourth stage, so four
+//                stages of loads are in flight per quarter.  Warps 0-3 then
+//                run the epilogue (tcgen05.ld, scatter-add to the targets).
+//   warp 16      allocates TMEM and loads B tiles with TMA (SWIZZLE_64B)
+//   warp 17      one thread issues tcgen05.mma (M=128, N=BN, K=16) per slice
 // Split-K over grid.z; partial sums are added with atomics.  Every wait on an
 // mbarrier is bounded by a wall-clock limit; on expiry the CTA latches
 // kErrTimeout, skips the remaining work and still frees its TMEM.
@@ -26,10 +32,17 @@ namespace fmm {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 32;  // bf16 elements per row per stage = 64 bytes (64-byte swizzle)
-constexpr int STAGES = 4;
+constexpr int BK = 32;  // bf16 elements per row per stage = 64 bytes (64-byte swizzle for B)
+constexpr int SB = 6;   // B stages (shared memory)
+constexpr int SA = 8;   // A stages (TMEM, 32 columns each)
+constexpr int kPhases = 4;                    // producer warps per TMEM lane quarter
+constexpr int kProducerWarps = 4 * kPhases;
+constexpr int kWarpTma = kProducerWarps;      // also allocates TMEM
+constexpr int kWarpMma = kProducerWarps + 1;
+constexpr int THREADS = 32 * (kProducerWarps + 2);
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAcol0 = 256;              // first A column
 constexpr int kNbrStride = 27;  // shared-memory row stride of the per-row neighbour table
-constexpr int THREADS = 192;
 constexpr int kMaxSeg = 24;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
@@ -44,6 +57,7 @@ struct TcSeg {
   const int32_t* nbr;
   const int32_t* cell_child_rows;  // M2P: cell_child of the row level
   const int32_t* cell_child_tgt;   // M2P: cell_child of the target level (refined targets get nothing)
+  const uint8_t* leafmask_tgt;     // M2P: leaf masks of the target level (or null: use cell_child_tgt)
   const int32_t* slot;             // M2L: local-expansion slot of each row oct
   float* out;                      // M2P: [cells of target level][4]; M2L: [slot*8 + cell][nc]
   int nrows;
@@ -57,6 +71,7 @@ struct TcParams {
   int Kvalid;      // 26 * KQ
   int nchunks;     // Kpad / BK
   int chunks_per_split;
+  int v8;          // rows load in 32-byte pieces (KQ % 16 == 0 and 32-byte aligned sources)
   int BN, N, nc, mode;
   unsigned* err;
 };
@@ -125,11 +140,33 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+// D (TMEM) += A (TMEM: 128 lanes x 8 columns = 16 bf16 per row) * B (shared memory)
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                            uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// 16 consecutive columns of this warp's 32 TMEM lanes, one register per lane and column
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void ld_nc_v4(const void* p, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "l"(p));
+}
+// 32 bytes (one sector) per thread; p must be 32-byte aligned
+__device__ __forceinline__ void ld_nc_v8(const void* p, uint32_t* v) {
+  asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "l"(p));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -152,14 +189,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   // 1024-byte aligned carve-up
   uintptr_t base = ((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023;
   unsigned char* sm = (unsigned char*)base;
-  const int a_bytes = BM * BK * 2;        // 16 KB
-  const int b_bytes = P.BN * BK * 2;      // BN * 128
-  unsigned char* Ahi = sm;
-  unsigned char* Alo = Ahi + STAGES * a_bytes;
-  unsigned char* Bhi = Alo + STAGES * a_bytes;
-  unsigned char* Blo = Bhi + STAGES * b_bytes;
-  uint64_t* bars = (uint64_t*)(Blo + STAGES * b_bytes);  // full[S], empty[S], done
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  const int b_bytes = P.BN * BK * 2;  // BN * 64
+  unsigned char* Bhi = sm;
+  unsigned char* Blo = Bhi + SB * b_bytes;
+  uint64_t* bars = (uint64_t*)(Blo + SB * b_bytes);  // fullA[SA], emptyA[SA], fullB[SB], emptyB[SB], done
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * SA + 2 * SB + 1);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
   int32_t* s_nbr = (int32_t*)(tmem_slot + 4);  // [BM][kNbrStride] source octs of each row
 
@@ -167,21 +201,26 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int kc_begin = blockIdx.z * P.chunks_per_split;
   const int kc_end = min(P.nchunks, kc_begin + P.chunks_per_split);
   const int nit = max(0, kc_end - kc_begin);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  const uint32_t fullA0 = smem_u32(bars), emptyA0 = smem_u32(bars + SA);
+  const uint32_t fullB0 = smem_u32(bars + 2 * SA), emptyB0 = smem_u32(bars + 2 * SA + SB);
+  const uint32_t done = smem_u32(bars + 2 * SA + 2 * SB);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full0 + 8 * s, 129);  // 128 gathering threads + 1 TMA arrive
-      mbar_init(empty0 + 8 * s, 1);   // tcgen05.commit
+    for (int s = 0; s < SA; ++s) {
+      mbar_init(fullA0 + 8 * s, 128);  // the 32 x 4 producer threads of the stage
+      mbar_init(emptyA0 + 8 * s, 1);   // tcgen05.commit
+    }
+    for (int s = 0; s < SB; ++s) {
+      mbar_init(fullB0 + 8 * s, 1);    // TMA arrive + transaction bytes
+      mbar_init(emptyB0 + 8 * s, 1);   // tcgen05.commit
     }
     mbar_init(done, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const uint32_t ncols = P.BN <= 32 ? 32 : (P.BN <= 64 ? 64 : (P.BN <= 128 ? 128 : 256));
-  if (warp == 4) {
+  if (warp == kWarpTma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(ncols)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -192,124 +231,158 @@ __global__ void __launch_bounds__(THREADS, 1)
   pdl_wait();  // rows, neighbour tables and multipoles come from earlier kernels
   pdl_trigger();
 
-  if (warp < 4) {
-    // ---------------- A gather ----------------
-    // Thread t owns row t for the epilogue (TMEM lane t) and writes that row's
-    // neighbour table.  The copies are spread differently: four lanes fetch the
-    // four 16-byte chunks of one row's 64-byte slice, eight rows per
-    // instruction, so every 32-byte sector is requested once and whole.
-    const int t = threadIdx.x;
+  if (warp < kProducerWarps) {
+    // ---------------- A rows into TMEM ----------------
+    const int q = warp & 3;             // lane quarter: rows 32 q .. 32 q + 31
+    const int t = 32 * q + lane;        // this thread's row (TMEM lane)
     int si = 0;
     while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].tile0) ++si;
     const TcSeg& S = P.seg[si];
     const int64_t row_idx = (int64_t)(blockIdx.x - S.tile0) * BM + t;
     const bool valid = row_idx < S.nrows;
     const int32_t roct = valid ? S.rows[row_idx] : 0;
-    int32_t* myn = s_nbr + t * kNbrStride;
-    for (int q = 0; q < 26; ++q) myn[q] = valid ? S.nbr[(int64_t)roct * 27 + c_nbr26[q]] : -1;
-    __syncwarp();  // each warp gathers its own 32 rows and reads their tables below
-    const int jj = lane & 3;  // 16-byte chunk within the row slice
-    uint32_t nbr_s[4], dst[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = warp * 32 + i * 8 + (lane >> 2);
-      nbr_s[i] = smem_u32(s_nbr + r * kNbrStride);  // read back with ld.shared (a plain pointer would be generic)
-      dst[i] = (uint32_t)(r * (BK * 2)) + (uint32_t)((jj ^ ((r >> 1) & 3)) << 4);
+    if (warp < 4) {
+      int32_t* myn = s_nbr + t * kNbrStride;
+      for (int qq = 0; qq < 26; ++qq) myn[qq] = valid ? S.nbr[(int64_t)roct * 27 + c_nbr26[qq]] : -1;
     }
-    const uint32_t ahi0 = smem_u32(Ahi), alo0 = smem_u32(Alo);
-    // Up to three stages of copies in flight: after committing stage it, wait
-    // for stage it-2 and mark it full.
-    constexpr int kInFlight = 2;
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kProducerWarps) : "memory");  // tables of all rows written
+    const uint32_t myn_s = smem_u32(s_nbr + t * kNbrStride);  // read back with ld.shared
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);   // this warp's lanes, column 0
     bool ok = true;
-    for (int it = 0; it < nit && ok; ++it) {
-      const int s = it % STAGES;
-      if (it >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, abort);
+    for (int it = warp >> 2; it < nit && ok; it += kPhases) {
+      const int s = it % SA;
+      if (it >= SA) ok = mbar_wait(emptyA0 + 8 * s, ((it / SA) - 1) & 1, abort);
       if (!ok) break;
-      const int k = (kc_begin + it) * BK + 8 * jj;  // 8 elements never straddle an offset segment (KQ % 8 == 0)
-      int qi = -1, off = 0;
-      if (k < P.Kvalid) {
-        qi = k / P.KQ;
-        off = k - qi * P.KQ;
-      }
+      const int k0 = (kc_begin + it) * BK;
+      uint32_t hv[16], lv[16];
+      if (P.v8) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        int32_t src = -1;
-        if (qi >= 0) asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(nbr_s[i] + 4 * qi));
-        const __nv_bfloat16* gh = src >= 0 ? S.Ahi + (int64_t)src * P.KQ + off : S.Ahi;
-        const __nv_bfloat16* gl = src >= 0 ? S.Alo + (int64_t)src * P.KQ + off : S.Alo;
-        const uint32_t sz = src >= 0 ? 16u : 0u;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(ahi0 + s * a_bytes + dst[i]), "l"(gh),
-                     "r"(sz)
-                     : "memory");
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(alo0 + s * a_bytes + dst[i]), "l"(gl),
-                     "r"(sz)
-                     : "memory");
+        for (int j = 0; j < BK / 16; ++j) {  // 16 bf16 (32 bytes) never straddle an offset segment (KQ % 16 == 0)
+          const int k = k0 + 16 * j;
+          int32_t src = -1;
+          int off = 0;
+          if (k < P.Kvalid) {
+            const int qi = k / P.KQ;
+            off = k - qi * P.KQ;
+            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
+          }
+          if (src >= 0) {
+            ld_nc_v8(S.Ahi + (int64_t)src * P.KQ + off, hv + 8 * j);
+            ld_nc_v8(S.Alo + (int64_t)src * P.KQ + off, lv + 8 * j);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) hv[8 * j + u] = lv[8 * j + u] = 0u;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < BK / 8; ++j) {  // 8 bf16 (16 bytes) never straddle an offset segment (KQ % 8 == 0)
+          const int k = k0 + 8 * j;
+          int32_t src = -1;
+          int off = 0;
+          if (k < P.Kvalid) {
+            const int qi = k / P.KQ;
+            off = k - qi * P.KQ;
+            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
+          }
+          if (src >= 0) {
+            ld_nc_v4(S.Ahi + (int64_t)src * P.KQ + off, hv[4 * j], hv[4 * j + 1], hv[4 * j + 2], hv[4 * j + 3]);
+            ld_nc_v4(S.Alo + (int64_t)src * P.KQ + off, lv[4 * j], lv[4 * j + 1], lv[4 * j + 2], lv[4 * j + 3]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) hv[4 * j + u] = lv[4 * j + u] = 0u;
+          }
+        }
       }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      if (it >= kInFlight) {
-        asm volatile("cp.async.wait_group %0;" ::"n"(kInFlight) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(full0 + 8 * ((it - kInFlight) % STAGES));
-      }
+      const uint32_t col = kAcol0 + 32u * (uint32_t)s;
+      tmem_st16(tl + col, hv);
+      tmem_st16(tl + col + 16, lv);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(fullA0 + 8 * s);
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (ok)  // the stages committed but not yet marked full
-      for (int r = max(0, nit - kInFlight); r < nit; ++r) mbar_arrive(full0 + 8 * (r % STAGES));
 
-    // ---------------- epilogue ----------------
-    bool have = ok && nit > 0 && mbar_wait(done, 0, abort);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int nchunk = P.BN / 32;
-    for (int j = 0; j < nchunk; ++j) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 32);
-      TMEM_LD32(taddr, v);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (!have || !valid) continue;
-      const int n0 = blockIdx.y * P.BN + j * 32;
+    if (warp < 4) {
+      // ---------------- epilogue ----------------
+      // Everything the scatter needs is loaded before the accumulator is ready:
+      // M2P: the child oct under each of the row's cells and which of its cells
+      // are leaves (targets); M2L: the row's local-expansion slot.
+      const int nchunk = P.BN / 32;
+      int32_t ch[8];
+      uint32_t tmask[8];
+      int64_t slot = 0;
       if (P.mode == kModeM2P) {
-        const int f = n0 >> 5;
-        const int32_t ch = S.cell_child_rows[(int64_t)roct * 8 + f];
-        if (ch >= 0) {
-          float* dst = S.out + (int64_t)ch * 32;
-          const int32_t* cct = S.cell_child_tgt + (int64_t)ch * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          ch[j] = -1;
+          const int f = (blockIdx.y * P.BN + j * 32) >> 5;
+          if (valid && j < nchunk && f < 8) ch[j] = S.cell_child_rows[(int64_t)roct * 8 + f];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          tmask[j] = 0;
+          if (ch[j] >= 0) {
+            if (S.leafmask_tgt) {
+              tmask[j] = S.leafmask_tgt[ch[j]];
+            } else {
+              for (int u = 0; u < 8; ++u) tmask[j] |= (uint32_t)(S.cell_child_tgt[(int64_t)ch[j] * 8 + u] < 0) << u;
+            }
+          }
+        }
+      } else if (valid) {
+        slot = S.slot[roct];
+      }
+      bool have = ok && nit > 0 && mbar_wait(done, 0, abort);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (j >= nchunk) break;
+        uint32_t v[32];
+        const uint32_t taddr = tl + (uint32_t)(j * 32);
+        TMEM_LD32(taddr, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!have || !valid) continue;
+        const int n0 = blockIdx.y * P.BN + j * 32;
+        if (P.mode == kModeM2P) {
+          if (ch[j] >= 0) {
+            float* dst = S.out + (int64_t)ch[j] * 32;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if ((tmask[j] >> u) & 1)  // leaf targets only: the accumulator of refined cells stays zero
+                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * u),
+                             "f"(__uint_as_float(v[4 * u])), "f"(__uint_as_float(v[4 * u + 1])),
+                             "f"(__uint_as_float(v[4 * u + 2])), "f"(__uint_as_float(v[4 * u + 3]))
+                             : "memory");
+          }
+        } else {
+          float* dst = S.out + slot * 8 * P.nc + n0;
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (cct[u] < 0)  // leaf targets only: the accumulator of refined cells stays zero
+            if (n0 + 4 * u < P.N)
               asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * u),
                            "f"(__uint_as_float(v[4 * u])), "f"(__uint_as_float(v[4 * u + 1])),
                            "f"(__uint_as_float(v[4 * u + 2])), "f"(__uint_as_float(v[4 * u + 3]))
                            : "memory");
         }
-      } else {
-        float* dst = S.out + (int64_t)S.slot[roct] * 8 * P.nc + n0;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (n0 + 4 * u < P.N)
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * u),
-                         "f"(__uint_as_float(v[4 * u])), "f"(__uint_as_float(v[4 * u + 1])),
-                         "f"(__uint_as_float(v[4 * u + 2])), "f"(__uint_as_float(v[4 * u + 3]))
-                         : "memory");
       }
     }
-  } else if (warp == 4) {
+  } else if (warp == kWarpTma) {
     // ---------------- B tiles by TMA ----------------
     if (lane == 0) {
       bool ok = true;
       for (int it = 0; it < nit && ok; ++it) {
-        const int s = it % STAGES;
-        if (it >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((it / STAGES) - 1) & 1, abort);
+        const int s = it % SB;
+        if (it >= SB) ok = mbar_wait(emptyB0 + 8 * s, ((it / SB) - 1) & 1, abort);
         if (!ok) break;
         const int k0 = (kc_begin + it) * BK;
         const int n0 = blockIdx.y * P.BN;
-        mbar_arrive_tx(full0 + 8 * s, 2u * (uint32_t)b_bytes);
-        tma_load_2d(smem_u32(Bhi + s * b_bytes), &tm_hi, k0, n0, full0 + 8 * s);
-        tma_load_2d(smem_u32(Blo + s * b_bytes), &tm_lo, k0, n0, full0 + 8 * s);
+        mbar_arrive_tx(fullB0 + 8 * s, 2u * (uint32_t)b_bytes);
+        tma_load_2d(smem_u32(Bhi + s * b_bytes), &tm_hi, k0, n0, fullB0 + 8 * s);
+        tma_load_2d(smem_u32(Blo + s * b_bytes), &tm_lo, k0, n0, fullB0 + 8 * s);
       }
     }
     __syncwarp();
-  } else {
+  } else if (warp == kWarpMma) {
     // ---------------- MMA issue ----------------
     if (lane == 0) {
       // kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = BN
@@ -317,23 +390,24 @@ __global__ void __launch_bounds__(THREADS, 1)
                              ((uint32_t)(BM >> 4) << 24);
       bool ok = true;
       for (int it = 0; it < nit && ok; ++it) {
-        const int s = it % STAGES;
-        ok = mbar_wait(full0 + 8 * s, (it / STAGES) & 1, abort);
+        const int sa = it % SA, sb = it % SB;
+        ok = mbar_wait(fullA0 + 8 * sa, (it / SA) & 1, abort) && mbar_wait(fullB0 + 8 * sb, (it / SB) & 1, abort);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = smem_u32(Ahi + s * a_bytes), al = smem_u32(Alo + s * a_bytes);
-        const uint32_t bh = smem_u32(Bhi + s * b_bytes), bl = smem_u32(Blo + s * b_bytes);
+        const uint32_t acol = tmem + kAcol0 + 32u * (uint32_t)sa;  // hi at +0, lo at +16
+        const uint32_t bh = smem_u32(Bhi + sb * b_bytes), bl = smem_u32(Blo + sb * b_bytes);
 #pragma unroll
         for (int part = 0; part < 3; ++part) {
-          const uint32_t a = (part == 2) ? al : ah;
+          const uint32_t a = (part == 2) ? acol + 16 : acol;
           const uint32_t b = (part == 1) ? bl : bh;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t accum = (it | part | kk) != 0;
-            mma_bf16(tmem, sdesc_sw64(a + kk * 32), sdesc_sw64(b + kk * 32), idesc, accum);
+            mma_bf16_ta(tmem, a + 8 * kk, sdesc_sw64(b + kk * 32), idesc, accum);
           }
         }
-        mma_commit(empty0 + 8 * s);
+        mma_commit(emptyA0 + 8 * sa);
+        mma_commit(emptyB0 + 8 * sb);
       }
       if (ok && nit > 0) mma_commit(done);
     }
@@ -342,9 +416,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (*abort && threadIdx.x == 0) atomicOr(P.err, kErrTimeout);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 4) {
+  if (warp == kWarpTma) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
@@ -362,7 +436,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 size_t smem_bytes(int BN) {
-  return 1024 + STAGES * (2 * BM * BK * 2 + 2 * BN * BK * 2) + (2 * STAGES + 1) * 8 + 16 + BM * kNbrStride * 4;
+  return 1024 + SB * (2 * BN * BK * 2) + (2 * SA + 2 * SB + 1) * 8 + 16 + BM * kNbrStride * 4;
 }
 
 // split-K factor minimising waves x chunks per CTA
@@ -418,6 +492,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   TcParams P;
   int tiles = 0;
   P.nseg = 0;
+  P.v8 = op.kseg % 16 == 0;
   for (int i = 0; i < nlev && P.nseg < kMaxSeg; ++i) {
     const int lr = levels[i];  // row level
     LevelTree& R = c->lev[lr];
@@ -430,12 +505,14 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
     S.Alo = (const __nv_bfloat16*)R.Mlo.ptr;
     S.rows = (rows && rows[i]) ? rows[i] : (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
     S.cell_child_tgt = (mode == kModeM2P) ? (const int32_t*)c->lev[lr + 1].cell_child.ptr : nullptr;
+    S.leafmask_tgt = (mode == kModeM2P) ? (const uint8_t*)c->lev[lr + 1].leafmask.ptr : nullptr;
     S.slot = (const int32_t*)R.slotL.ptr;
     S.nbr = (const int32_t*)R.nbr.ptr;
     S.cell_child_rows = (const int32_t*)R.cell_child.ptr;
     S.out = (mode == kModeM2P) ? (float*)c->lev[lr + 1].acc.ptr : (float*)R.Lm.ptr;
     S.nrows = (int)nr;
     S.tile0 = tiles;
+    if ((uintptr_t)S.Ahi % 32 || (uintptr_t)S.Alo % 32) P.v8 = 0;
     tiles += (int)((nr + BM - 1) / BM);
   }
   if (!tiles) return;
