@@ -66,6 +66,26 @@ __device__ __forceinline__ void sign_transform_back(T x[8]) {
 }
 
 // Leaf cells of one level: monopole = mass.
+// Block-wide copies of translation tables into shared memory with every load
+// of a batch in flight before the first store: these small kernels are bound
+// by memory latency, and a plain strided loop pays one round trip per stride.
+template <int U, typename T, typename F>
+__device__ __forceinline__ void stage_block(int n, F&& load, T* dst) {
+  for (int base = 0; base < n; base += U * (int)blockDim.x) {
+    T r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = base + u * (int)blockDim.x + (int)threadIdx.x;
+      if (j < n) r[u] = load(j);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = base + u * (int)blockDim.x + (int)threadIdx.x;
+      if (j < n) dst[j] = r[u];
+    }
+  }
+}
+
 template <typename TMono>
 __global__ void k_leaf_mono(int64_t ncell, const int32_t* __restrict__ cell_child, const double* __restrict__ mass,
                             TMono* __restrict__ mono) {
@@ -148,15 +168,22 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
   const unsigned full = 0xffffffffu;
   const bool leaf_only = __all_sync(full, cc < 0);
   if (__syncthreads_or(valid && !leaf_only)) {  // block-uniform: stage the pair tables
-    for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
-      cf[j] = pc[j];
-      gx[j] = pg[j] + nc * pe[j];
-    }
-    for (int k = threadIdx.x; k <= nc; k += blockDim.x) off[k] = poff[k];
+    stage_block<4>(npairs, [&](int j) { return pc[j]; }, cf);
+    stage_block<4>(npairs, [&](int j) { return pg[j] + nc * pe[j]; }, gx);
+    stage_block<1>(nc + 1, [&](int j) { return poff[j]; }, off);
     __syncthreads();
   }
   if (!valid) return;  // warp-uniform; no block-wide barrier below
   if (leaf_only) {
+    // table entries first (independent of the masses), all loads in flight together
+    int ek[4];
+    float wk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = 32 * u + lane;
+      ek[u] = k < nc ? e0[k] : 0;
+      wk[u] = k < nc ? w0[k] : 0.0f;
+    }
     float m = lane < 8 ? (float)mass_next[-1 - (int64_t)cc] : 0.0f;
 #pragma unroll
     for (int axis = 0; axis < 3; ++axis) {  // S_e over lanes 0..7, as sign_transform
@@ -165,10 +192,11 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
     }
     for (int kb = 0; kb < nc; kb += 32) {
       const int k = kb + lane;
-      const int e = k < nc ? e0[k] : 0;
+      const int u = kb >> 5;
+      const int e = u < 4 ? ek[u] : (k < nc ? e0[k] : 0);
       const float sv = __shfl_sync(full, m, e);
       if (k < nc) {
-        const float v = w0[k] * sv;
+        const float v = (u < 4 ? wk[u] : w0[k]) * sv;
         Mout[cell * nc + k] = v;
         if (hi) split_bf16(v, hi[cell * nc + k], lo[cell * nc + k]);
         if (k == 0) mono[cell] = v;
@@ -180,11 +208,23 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
   float* S = Sall + (size_t)warp * 8 * nc;
   if (lane < 8) wcc[lane] = cc;
   __syncwarp();
-#pragma unroll 4
-  for (int idx = lane; idx < 8 * nc; idx += 32) {
-    const int c = idx / nc, g = idx - c * nc;
-    const int32_t ch = wcc[c];
-    S[idx] = ch < 0 ? (g == 0 ? (float)mass_next[-1 - (int64_t)ch] : 0.0f) : Mnext[(c0 + c) * nc + g];
+  // the children's rows: every load of a batch in flight before the first store
+  for (int base = 0; base < 8 * nc; base += 32 * 12) {
+    float r[12];
+#pragma unroll
+    for (int u = 0; u < 12; ++u) {
+      const int idx = base + 32 * u + lane;
+      if (idx < 8 * nc) {
+        const int c = idx / nc, g = idx - c * nc;
+        const int32_t ch = wcc[c];
+        r[u] = ch < 0 ? (g == 0 ? (float)mass_next[-1 - (int64_t)ch] : 0.0f) : Mnext[(c0 + c) * nc + g];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 12; ++u) {
+      const int idx = base + 32 * u + lane;
+      if (idx < 8 * nc) S[idx] = r[u];
+    }
   }
   __syncwarp();
   for (int g = lane; g < nc; g += 32) {
@@ -227,16 +267,17 @@ __global__ void __launch_bounds__(128) k_m2m_block(
   const int64_t o = octs ? octs[blockIdx.x] : blockIdx.x;
   const int64_t cell = oct_parent_next[o];
   const int64_t c0 = o * 8;
-  for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
-    cf[j] = pc[j];
-    gx[j] = pg[j] + nc * pe[j];
-  }
-  for (int k = threadIdx.x; k <= nc; k += blockDim.x) off[k] = poff[k];
-  for (int idx = threadIdx.x; idx < 8 * nc; idx += blockDim.x) {
+  __shared__ int32_t ccs[8];
+  if (threadIdx.x < 8) ccs[threadIdx.x] = cell_child_next[c0 + threadIdx.x];
+  stage_block<8>(npairs, [&](int j) { return pc[j]; }, cf);
+  stage_block<8>(npairs, [&](int j) { return pg[j] + nc * pe[j]; }, gx);
+  stage_block<1>(nc + 1, [&](int j) { return poff[j]; }, off);
+  __syncthreads();
+  stage_block<6>(8 * nc, [&](int idx) {
     const int c = idx / nc, g = idx - c * nc;
-    const int32_t cc = cell_child_next[c0 + c];
-    S[idx] = cc < 0 ? (g == 0 ? mass_next[-1 - (int64_t)cc] : 0.0) : (double)Mnext[(c0 + c) * nc + g];
-  }
+    const int32_t cc = ccs[c];
+    return cc < 0 ? (g == 0 ? mass_next[-1 - (int64_t)cc] : 0.0) : (double)Mnext[(c0 + c) * nc + g];
+  }, S);
   __syncthreads();
   for (int g = threadIdx.x; g < nc; g += blockDim.x) {
     double x[8];
@@ -283,12 +324,10 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
   if (Lup) {
     const int32_t par = oct_parent[o];
     const int64_t sp = (int64_t)slot_up[par >> 3] * 8 + (par & 7);
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) Lp[k] = Lup[sp * nc + k];
-    for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
-      cf[j] = pc[j];
-      gg[j] = pg[j];
-    }
-    for (int k = threadIdx.x; k <= 8 * nc; k += blockDim.x) off[k] = poff8[k];
+    stage_block<2>(nc, [&](int k) { return Lup[sp * nc + k]; }, Lp);
+    stage_block<8>(npairs, [&](int j) { return pc[j]; }, cf);
+    stage_block<8>(npairs, [&](int j) { return pg[j]; }, gg);
+    stage_block<6>(8 * nc + 1, [&](int k) { return poff8[k]; }, off);
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nc; b += blockDim.x) {
