@@ -624,6 +624,12 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
   return FMM_OK;
 }
 
+// SMs left to the L2L chain and the near-field M2P while the bottom M2P runs
+#ifndef FMM_M2P_SIDE_SMS
+#define FMM_M2P_SIDE_SMS 40
+#endif
+constexpr int kM2PSideSMs = FMM_M2P_SIDE_SMS;
+
 // The device work of one solve (no host synchronisation, no allocation).
 static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* dacc, cudaStream_t st) {
   if (lo > c->lmax) return FMM_OK;  // only empty levels
@@ -679,7 +685,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
     }
   };
   // 3a. bottom intermediate field: M2P from level l-1 cells
-  auto m2p = [&](cudaStream_t s2) {
+  auto m2p = [&](cudaStream_t s2, int sm_budget) {
     std::vector<int> lv;
     for (int l = lo; l <= lmax; ++l) {
       if (!c->lev[l].n_leaf) continue;
@@ -688,20 +694,22 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
       else
         lv.push_back(l - 1);
     }
-    if (!f64 && !lv.empty()) launch_gemm_tc(c, c->op_m2p, kModeM2P, lv.data(), (int)lv.size(), s2);
+    if (!f64 && !lv.empty())
+      launch_gemm_tc(c, c->op_m2p, kModeM2P, lv.data(), (int)lv.size(), s2, nullptr, nullptr, sm_budget);
   };
   // The bottom field needs only the multipoles, so it runs on a second branch
-  // beside the downward pass.  Mixed: the two tcgen05 contractions each fill the
-  // SMs' shared memory, so M2L goes first, then M2P overlaps the latency-bound
-  // L2L chain and the near-field M2P (both add atomically into the zeroed
-  // accumulator).  FP64: the DFMA contractions share SMs, so the fork comes
-  // right after the upward pass; the FP64 M2P assigns the accumulator, so the
-  // near-field M2P follows it.  With stage timing on, everything stays in order.
+  // beside the downward pass.  Mixed: a tcgen05 CTA fills an SM's shared
+  // memory, so M2L goes first; then M2P, split over all but kM2PSideSMs SMs,
+  // overlaps the latency-bound L2L chain and the near-field M2P on the rest
+  // (both add atomically into the zeroed accumulator).  FP64: the DFMA
+  // contractions share SMs, so the fork comes right after the upward pass; the
+  // FP64 M2P assigns the accumulator, so the near-field M2P follows it.  With
+  // stage timing on, everything stays in order.
   if (!c->timing && c->aux_stream) {
     if (!f64) m2l_tc(st);
     CKS(cudaEventRecord(c->ev_fork, st));
     CKS(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
-    m2p(c->aux_stream);
+    m2p(c->aux_stream, dl.empty() ? 0 : std::max(1, c->num_sms - kM2PSideSMs));
     if (f64) launch_near_m2p(c, lo, c->aux_stream);
     CKS(cudaEventRecord(c->ev_join, c->aux_stream));
     l2l_chain(st);
@@ -711,7 +719,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
     if (!f64) m2l_tc(st);
     l2l_chain(st);
     stage_event(c, 2, st);
-    m2p(st);
+    m2p(st, 0);
     stage_event(c, 3, st);  // the near-field stage starts here
     launch_near_m2p(c, lo, st);
   }

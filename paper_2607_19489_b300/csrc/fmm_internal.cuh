@@ -215,9 +215,11 @@ void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int level_rows, cu
                      const int32_t* rows = nullptr, int64_t nrows = 0);
 // gemm_tc.cu
 fmm_status make_tensor_maps(Ctx* c, GemmOperand& op);
-// rows[i] / nrows[i]: optional per-level row lists (null: the level's full list)
+// rows[i] / nrows[i]: optional per-level row lists (null: the level's full list);
+// sm_budget: SMs the split-K factor may fill (0: all; fewer leave room for
+// kernels running beside it)
 void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* row_levels, int nlev, cudaStream_t st,
-                    const int32_t* const* rows = nullptr, const int64_t* nrows = nullptr);
+                    const int32_t* const* rows = nullptr, const int64_t* nrows = nullptr, int sm_budget = 0);
 // near.cu
 fmm_status near_init(Ctx* c);
 void launch_near_m2p(Ctx* c, int lo, cudaStream_t st);

@@ -488,7 +488,7 @@ fmm_status make_tensor_maps(Ctx* c, GemmOperand& op) {
 }
 
 void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, int nlev, cudaStream_t st,
-                    const int32_t* const* rows, const int64_t* nrows) {
+                    const int32_t* const* rows, const int64_t* nrows, int sm_budget) {
   TcParams P;
   int tiles = 0;
   P.nseg = 0;
@@ -520,7 +520,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.Kvalid = op.K;
   P.nchunks = op.Kpad / BK;
   const int tuned = c->tune_split[mode == kModeM2P ? 0 : 1];
-  const int split = tuned > 0 ? std::min(tuned, P.nchunks) : choose_split(tiles * op.ntile, P.nchunks, c->num_sms);
+  const int split = tuned > 0 ? std::min(tuned, P.nchunks) : choose_split(tiles * op.ntile, P.nchunks, sm_budget > 0 ? sm_budget : c->num_sms);
   P.chunks_per_split = (P.nchunks + split - 1) / split;
   const int nz = (P.nchunks + P.chunks_per_split - 1) / P.chunks_per_split;
   P.BN = op.BN;
