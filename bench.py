@@ -48,7 +48,7 @@ WORKLOAD = "two-level AMR 64^3 + 32^3 refined block, Plummer a=0.05 + lognormal 
 RECORDED_PEAKS = {"hbm_gbs": 6513.0, "bf16_tflops": 1786.0, "bf16_tflops_sustained": 1405.0}
 NC = (P_ORDER + 1) * (P_ORDER + 2) * (P_ORDER + 3) // 6
 # DRAM bytes of one M2P launch (k_gemm_tc) of the headline workload, from ncu
-M2P_TRAFFIC_BYTES = 38_123_264
+M2P_TRAFFIC_BYTES = 37_020_416
 
 
 def load_peaks():
@@ -325,7 +325,8 @@ def gpu_arm(args, rank, world, local):
         "unit": "TFLOP/s",
         "traffic": M2P_TRAFFIC_BYTES,
         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one M2P launch of this workload "
-                        "(ncu, profiles/k_gemm_tc_two_level_64c_32c_p6.md); algorithmic ~38 MB",
+                        "(ncu, profiles/k_gemm_tc_two_level_64c_32c_p6.md: the forked launch, split-K 3; the "
+                        "stage time is the in-order launch, split-K 4, same kernel and operands); algorithmic ~38 MB",
         "peak_note": f"{peak_src} bf16 dense sustained / 3 (three bf16 products per split-BF16 product); "
                      "achieved counts useful flops 2*189*4*ncoef per target cell",
         "stage_ms": stage["m2p"],
