@@ -142,6 +142,8 @@ struct Ctx {
   // scratch
   DevBuf sort_tmp, keys_a, keys_b, vals_a, vals_b, flags, scan, err_word, counter;
   DevBuf anc_flags;     // uint8: one visited flag per oct of levels 1..anc_req-1 (ancestor walks)
+  std::vector<int64_t> cub_sig;  // sorted levels and their sizes of the last CUB size query
+  size_t cub_tmp = 0;            // and its answer (bytes of sort_tmp needed)
   DevBuf out_stage;     // device staging for host outputs
   DevBuf in_stage;      // device staging for host inputs
   unsigned* d_err = nullptr;

@@ -512,9 +512,13 @@ fmm_status tree_prepare(Ctx* c) {
   CK(buf_ensure(c, c->flags, std::max<int64_t>(nmax * 8, list_blocks * kListBlock)));
   CK(buf_ensure(c, c->scan, std::max<int64_t>(nmax * 4, list_blocks * 32)));
   CK(buf_ensure(c, c->counter, 5 * 4 * (lmax + 2)));
-  // CUB temporary storage for the largest sort and scan of this build
-  size_t tmp_max = 0;
-  {
+  // CUB temporary storage for the largest sort and scan of this build.  The size
+  // queries are host work repeated on every call, so their answer is kept for
+  // as long as the sorted levels and their sizes stay the same.
+  std::vector<int64_t> sig = {lo, lmax};
+  for (int l = lo; l <= lmax; ++l) sig.push_back(c->lev[l].n_oct);
+  if (sig != c->cub_sig) {
+    size_t tmp_max = 0;
     for (int l = lo; l <= lmax; ++l) {
       const int n = (int)(8 * c->lev[l].n_oct);
       size_t t = 0;
@@ -525,8 +529,10 @@ fmm_status tree_prepare(Ctx* c) {
       CK(cub::DeviceScan::InclusiveSum(nullptr, t, (int32_t*)nullptr, (int32_t*)nullptr, n));
       tmp_max = std::max(tmp_max, t);
     }
+    c->cub_sig = sig;
+    c->cub_tmp = tmp_max;
   }
-  CK(buf_ensure(c, c->sort_tmp, tmp_max));
+  CK(buf_ensure(c, c->sort_tmp, c->cub_tmp));
   return FMM_OK;
 }
 
