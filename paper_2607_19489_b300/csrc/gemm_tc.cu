@@ -33,7 +33,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 32;  // bf16 elements per row per stage = 64 bytes (64-byte swizzle for B)
-constexpr int SB = 6;   // B stages (shared memory)
+constexpr int SB = 4;   // B stages (shared memory; the rest of the SM's 256 KB serves as L1 for the rows)
 constexpr int SA = 8;   // A stages (TMEM, 32 columns each)
 constexpr int kPhases = 4;                    // producer warps per TMEM lane quarter
 constexpr int kProducerWarps = 4 * kPhases;
@@ -72,9 +72,22 @@ struct TcParams {
   int nchunks;     // Kpad / BK
   int chunks_per_split;
   int v8;          // rows load in 32-byte pieces (KQ % 16 == 0 and 32-byte aligned sources)
+  int kq_chunks;   // > 0: K slices visited slice-major (KQ / BK slices per offset, all 26 offsets of a
+                   // slice in a row) so a source row slice is re-read from L1; 0: in K order
   int BN, N, nc, mode;
   unsigned* err;
 };
+
+// First K index of the it-th slice a CTA visits.  Slice-major order (slice c of
+// every neighbour offset q before slice c + 1) keeps the rows one slice needs,
+// about the distinct neighbour octs of the tile, in L1 across the 26 offsets.
+__device__ __forceinline__ int slice_k0(int kq_chunks, int KQ, int it) {
+  if (kq_chunks > 0) {
+    const int c = it / 26, q = it - 26 * c;
+    return q * KQ + c * BK;
+  }
+  return it * BK;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -253,7 +266,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int s = it % SA;
       if (it >= SA) ok = mbar_wait(emptyA0 + 8 * s, ((it / SA) - 1) & 1, abort);
       if (!ok) break;
-      const int k0 = (kc_begin + it) * BK;
+      const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
       uint32_t hv[16], lv[16];
       if (P.v8) {
 #pragma unroll
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int s = it % SB;
         if (it >= SB) ok = mbar_wait(emptyB0 + 8 * s, ((it / SB) - 1) & 1, abort);
         if (!ok) break;
-        const int k0 = (kc_begin + it) * BK;
+        const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
         const int n0 = blockIdx.y * P.BN;
         mbar_arrive_tx(fullB0 + 8 * s, 2u * (uint32_t)b_bytes);
         tma_load_2d(smem_u32(Bhi + s * b_bytes), &tm_hi, k0, n0, fullB0 + 8 * s);
@@ -519,6 +532,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.KQ = op.kseg;
   P.Kvalid = op.K;
   P.nchunks = op.Kpad / BK;
+  P.kq_chunks = (op.kseg % BK == 0 && op.Kpad == 26 * op.kseg) ? op.kseg / BK : 0;
   const int tuned = c->tune_split[mode == kModeM2P ? 0 : 1];
   const int split = tuned > 0 ? std::min(tuned, P.nchunks) : choose_split(tiles * op.ntile, P.nchunks, sm_budget > 0 ? sm_budget : c->num_sms);
   P.chunks_per_split = (P.nchunks + split - 1) / split;
