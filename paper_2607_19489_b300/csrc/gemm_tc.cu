@@ -20,6 +20,10 @@
 //                run the epilogue (tcgen05.ld, scatter-add to the targets).
 //   warp 16      allocates TMEM and loads B tiles with TMA (SWIZZLE_64B)
 //   warp 17      one thread issues tcgen05.mma (M=128, N=BN, K=16) per slice
+// K is visited slice-major when the offset segment is a whole number of
+// slices: one BK-wide slice of all 26 offsets, then the next.  A tile's rows
+// then re-read the row slices of the same few hundred neighbour octs across the
+// 26 offsets, and the shared memory left unused (4 B stages) keeps them in L1.
 // Split-K over grid.z; partial sums are added with atomics.  Every wait on an
 // mbarrier is bounded by a wall-clock limit; on expiry the CTA latches
 // kErrTimeout, skips the remaining work and still frees its TMEM.
