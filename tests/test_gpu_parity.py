@@ -104,6 +104,19 @@ def test_mixed_matches_oracle(name, p):
     assert rel_rms(gp, rp) <= MIXED_TOL
 
 
+@pytest.mark.parametrize("name", ["amr_3_5", "twolevel16"])
+@pytest.mark.parametrize("p", [2, 3, 5, 8])
+def test_mixed_other_orders_match_oracle(name, p):
+    """The tensor-core contraction picks its row-load width and its K order from
+    the offset segment 8 ncoef(p): p = 2 (80), 3 (160), 5 (448) and 8 (1320)
+    reach the combinations that p = 4 (280) and 6 (672) do not."""
+    h = CASES[name]
+    rp, ra = oracle.solve(h, p)
+    gp, ga = run(h, p, "mixed")
+    assert rel_rms(ga, ra) <= MIXED_TOL
+    assert rel_rms(gp, rp) <= MIXED_TOL
+
+
 def test_unigrid32_p4_fp64_full():
     # 32^3 Plummer, p = 4, FP64 path on every cell
     h = W.unigrid_plummer(5)
