@@ -52,7 +52,7 @@ M2P_TRAFFIC_BYTES = 37_012_992
 
 
 def load_peaks():
-    for path in (os.path.join(ROOT, "MEASURED_PEAKS.json"), "/root/repo/MEASURED_PEAKS.json"):
+    for path in (os.path.join(ROOT, "MEASURED_PEAKS.json"),):
         if os.path.exists(path):
             with open(path) as f:
                 d = json.load(f)
