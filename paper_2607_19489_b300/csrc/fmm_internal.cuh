@@ -70,6 +70,8 @@ struct DevBuf {
 
 struct Ctx;
 cudaError_t buf_ensure(Ctx* c, DevBuf& b, size_t bytes);
+// true for device (or managed) memory; cudaPointerGetAttributes allocates nothing
+bool is_device_ptr(const void* p);
 
 // Device-resident tree of one level.
 struct LevelTree {

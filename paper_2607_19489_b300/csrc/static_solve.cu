@@ -119,7 +119,11 @@ using namespace fmm;
 extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n, const int32_t* ijk,
                                                const double* mass, void* phi, void* accel, void* stream) {
   Ctx* c = reinterpret_cast<Ctx*>(cx);
-  if (!c || !ijk || !mass || !phi || !accel) return FMM_ERR_ARG;
+  if (!c) return FMM_ERR_ARG;
+  if (!ijk || !mass || !phi || !accel) {
+    c->last_error = "fmm_solve_unigrid_static: a NULL pointer";
+    return FMM_ERR_ARG;
+  }
   if (level < 2 || level > kStaticMaxLevel) {
     c->last_error = "fmm_solve_unigrid_static: level must be 2..4 (at most 16^3 cells)";
     return FMM_ERR_ARG;
@@ -135,7 +139,17 @@ extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
+    c->last_error = "fmm_solve_unigrid_static: no current CUDA device";
     return FMM_ERR_CUDA;
+  }
+  if (dev != c->device) {  // the context's tables live on its own device
+    c->last_error = "fmm_solve_unigrid_static: the current device is not the context's device";
+    return FMM_ERR_ARG;
+  }
+  // the kernels read and write these directly: a host pointer would be an illegal access
+  if (!is_device_ptr(ijk) || !is_device_ptr(mass) || !is_device_ptr(phi) || !is_device_ptr(accel)) {
+    c->last_error = "fmm_solve_unigrid_static: ijk, mass, phi and accel must be device pointers";
+    return FMM_ERR_ARG;
   }
   if (!g_scratch_dev[dev]) {  // once per device, with that device current
     void* p = nullptr;
@@ -222,9 +236,18 @@ extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n
     c->last_error = std::string("fmm_solve_unigrid_static: ") + cudaGetErrorString(e);
     return FMM_ERR_CUDA;
   }
-  if (status & kErrOutOfBox) return FMM_ERR_OUT_OF_BOX;
-  if (status & kErrNonFinite) return FMM_ERR_NONFINITE;
-  if (status & kErrDuplicate) return FMM_ERR_DUPLICATE;
+  if (status & kErrOutOfBox) {
+    c->last_error = "fmm_solve_unigrid_static: a cell index outside [0, 2^level)";
+    return FMM_ERR_OUT_OF_BOX;
+  }
+  if (status & kErrNonFinite) {
+    c->last_error = "fmm_solve_unigrid_static: a mass is NaN or infinite";
+    return FMM_ERR_NONFINITE;
+  }
+  if (status & kErrDuplicate) {
+    c->last_error = "fmm_solve_unigrid_static: a cell given twice";
+    return FMM_ERR_DUPLICATE;
+  }
 
   // ---- the solve, on the view (the context's own hierarchy is put back after) ----
   LevelTree saved[kStaticMaxLevel + 1];

@@ -267,7 +267,19 @@ class Solver:
 
     def solve_unigrid_static(self, level: int, ijk, mass, phi, accel, stream=None):
         """Unigrid solve (level 2..4) that allocates no device memory; all arguments are
-        device tensors (see fmm_solve_unigrid_static in include/fmm.h)."""
+        contiguous CUDA tensors: ijk int32 [n, 3], mass float64 [n], phi [n] and accel
+        [n, 3] in the output dtype of this solver (see fmm_solve_unigrid_static in
+        include/fmm.h).  Anything else is rejected here, before the library is called."""
+        import torch
+        n = int(ijk.shape[0]) if hasattr(ijk, "shape") and len(ijk.shape) else -1
+        out_dt = torch.float32 if self.out_fp32 else torch.float64
+        want = ((ijk, torch.int32, (n, 3)), (mass, torch.float64, (n,)), (phi, out_dt, (n,)),
+                (accel, out_dt, (n, 3)))
+        for name, (t, dt, shape) in zip(("ijk", "mass", "phi", "accel"), want):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and tuple(t.shape) == shape
+                    and t.is_contiguous()):
+                raise FMMError(-1, f"solve_unigrid_static: {name} must be a contiguous CUDA tensor of dtype "
+                                   f"{dt} and shape {shape}")
         rc = lib().fmm_solve_unigrid_static(self._h, level, int(ijk.shape[0]), _data_ptr(ijk), _data_ptr(mass),
                                             _data_ptr(phi), _data_ptr(accel), _stream_ptr(stream))
         self._check(rc, "fmm_solve_unigrid_static")

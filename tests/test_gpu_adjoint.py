@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from paper_2607_19489_b300 import workloads as W
+from _parity import ORACLE_FP64, check_arrays
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +77,7 @@ def test_adjoint_is_the_oracle_transpose(boxes, lo_off):
     gp, ga = cotangents(h, lo, seed=11)
     ref = oracle_transpose(h, 4, gp, ga, lo)
     got, _ = gpu_adjoint(h, 4, gp, ga, lo)
-    assert rel_rms(got, ref) <= 1e-10
+    check_arrays(got, ref, ORACLE_FP64, "adjoint vs the oracle's transpose")
 
 
 @pytest.mark.parametrize("name", ["random_amr", "two_level16", "nested_p6"])

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_2607_19489_b300 import workloads as W
+from _parity import ORACLE_FP64, SELF_MIXED, check, oracle_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -17,12 +18,6 @@ def _np(out):
     torch.cuda.synchronize()
     phi, acc = out
     return {l: phi[l].double().cpu().numpy() for l in phi}, {l: acc[l].double().cpu().numpy() for l in acc}
-
-
-def _rel(got, ref):
-    num = sum(((got[l] - ref[l]) ** 2).sum() for l in ref)
-    den = sum((ref[l] ** 2).sum() for l in ref)
-    return float(np.sqrt(num / den))
 
 
 def small_batch(n=6, seed=3):
@@ -43,8 +38,7 @@ def test_fp64_batch_matches_oracle():
     for h, out in zip(hs, outs):
         got_p, got_a = _np(out)
         ref_p, ref_a = oracle.solve(h, 4)
-        assert _rel(got_a, ref_a) <= 1e-10
-        assert _rel(got_p, ref_p) <= 1e-10
+        check(got_p, got_a, ref_p, ref_a, ORACLE_FP64, "fp64 batch", h=h)
 
 
 @pytest.mark.parametrize("p", [4, 6])
@@ -63,8 +57,7 @@ def test_mixed_batch_matches_own_solves(p):
         s.sync()
     for o, ref in zip(outs, own):  # same kernels; atomics may add in another order
         got_p, got_a = _np(o)
-        assert _rel(got_a, ref[1]) <= 1e-5
-        assert _rel(got_p, ref[0]) <= 1e-5
+        check(got_p, got_a, ref[0], ref[1], SELF_MIXED, f"mixed batch p={p} vs own solve")
 
 
 def test_batch_follows_hierarchy_changes_and_subcycles():
@@ -86,7 +79,7 @@ def test_batch_follows_hierarchy_changes_and_subcycles():
     for h, lo, out in zip(hs, los, outs):
         got_p, got_a = _np(out)
         ref_p, ref_a = oracle.solve(h, 4, lo=lo)
-        assert _rel(got_a, ref_a) <= 1e-10
+        check(got_p, got_a, ref_p, ref_a, ORACLE_FP64, f"fp64 batch lo={lo}", h=h)
 
 
 def test_autotune_keeps_results():
@@ -100,14 +93,14 @@ def test_autotune_keeps_results():
     after = _np(s.solve())
     s.sync()
     # another split-K factor sums the FP32 partial products in another order
-    assert _rel(after[1], before[1]) <= 1e-5
+    check(after[0], after[1], before[0], before[1], SELF_MIXED, "after autotune")
     s2 = fmm.Solver(6, "mixed")
     s2.set_hierarchy(h)
     s2.set_tuning(t)
     assert s2.tuning() == t
     again = _np(s2.solve())
     s2.sync()
-    assert _rel(again[1], before[1]) <= 1e-5
+    check(again[0], again[1], before[0], before[1], SELF_MIXED, "tuning set on another context")
 
 
 def test_shared_tables_survive_their_creator():
@@ -124,14 +117,14 @@ def test_shared_tables_survive_their_creator():
         s.set_hierarchy(h)
         got_p, got_a = _np(s.solve())
         s.sync()
-        assert _rel(got_a, ref_a) <= 1e-10
+        check(got_p, got_a, ref_p, ref_a, ORACLE_FP64, "shared tables", h=h)
     del others
     gc.collect()
     s = fmm.Solver(4, "fp64")
     s.set_hierarchy(h)
     got_p, got_a = _np(s.solve())
     s.sync()
-    assert _rel(got_a, ref_a) <= 1e-10
+    check(got_p, got_a, ref_p, ref_a, ORACLE_FP64, "tables rebuilt", h=h)
 
 
 def test_trailing_empty_levels():
@@ -141,14 +134,15 @@ def test_trailing_empty_levels():
     e = W.Hierarchy(h.lmin, h.lmax + 2, [a for a in h.ijk] + [np.zeros((0, 3), np.int32)] * 2,
                     [m for m in h.mass] + [np.zeros(0)] * 2, "with empty levels")
     ref_p, ref_a = oracle.solve(h, 4)
-    for precision, tol in (("fp64", 1e-10), ("mixed", 1e-4)):
+    for precision in ("fp64", "mixed"):
         s = fmm.Solver(4, precision)
         s.set_hierarchy(e)
         phi, acc = s.solve()
         s.sync()
         assert acc[e.lmax].shape[0] == 0
         got_p, got_a = _np((phi, acc))
-        assert _rel({l: got_a[l] for l in h.levels}, ref_a) <= tol
+        check({l: got_p[l] for l in h.levels}, {l: got_a[l] for l in h.levels}, ref_p, ref_a,
+              oracle_tol(precision), f"trailing empty levels {precision}", h=h)
         assert s.tree_counts()[e.lmax] == 0
         phi2, acc2 = s.solve(lo=e.lmax)  # a subcycle of an empty level: nothing to do
         s.sync()

@@ -2,9 +2,11 @@
 
 Each test ties one part of the oracle to something fixed outside it: closed
 forms of the derivatives of 1/r and the Legendre identity, the M2M and L2L
-exactness identities, analytic truncation behaviour, the O(N^2) direct sum,
-linearity, mirror symmetry, the exact antisymmetry of nearest-field pairs
-(Sec. 3.2) and the graded-octree validation rules.
+exactness identities, analytic truncation behaviour, the O(N^2) direct sum
+(including the full 32^3 unigrid), the closed-form potential of a smooth
+sphere with O(h^2) convergence, linearity, mirror, axis-permutation and shift
+symmetries, the exact antisymmetry of nearest-field pairs (Sec. 3.2) and the
+graded-octree validation rules.
 """
 import os
 
@@ -212,6 +214,112 @@ def test_amr_converges_to_direct_sum():
     errs = [_solve_vs_direct(h, p)[0] for p in (2, 4, 6, 8)]
     assert all(errs[i] > errs[i + 1] for i in range(3))
     assert errs[-1] < 1e-4
+
+
+def test_config1_unigrid32_converges_to_direct_sum():
+    """The 32^3 Plummer unigrid (a = 0.1, 1 % noise) against its O(N^2) direct sum
+    over all 32 768 cells at p = 2, 4, 6.  The truncation error falls by more than
+    3x per two orders (measured 4.6e-2, 7.2e-3, 1.6e-3 in accel; 4.9e-3, 5.8e-4,
+    1.2e-4 in phi): a dropped or doubled region would leave a floor instead."""
+    h = W.unigrid_plummer(5)
+    errs = [_solve_vs_direct(h, p) for p in (2, 4, 6)]
+    ea = [e[0] for e in errs]
+    ep = [e[1] for e in errs]
+    assert ea[0] > 3 * ea[1] and ea[1] > 3 * ea[2], ea
+    assert ep[0] > 3 * ep[1] and ep[1] > 3 * ep[2], ep
+    assert ea[2] < 2.5e-3 and ep[2] < 2e-4
+
+
+def _smooth_sphere(level, R=0.3, centre=0.5):
+    """Unigrid sampling of rho = (1 - r^2/R^2)^2 (r < R) at cell centres, mass =
+    rho h^3 (no renormalisation), and the closed-form potential and acceleration of
+    the continuous density: for r < R, with s the radius,
+      phi(r) = -4 pi [ (1/r) int_0^r rho s^2 ds + int_r^R rho s ds ]
+             = -4 pi [ r^2/3 - 2 r^4/(5 R^2) + r^6/(7 R^4) + (R^2/6)(1 - r^2/R^2)^3 ],
+      M(<r)  = 4 pi [ r^3/3 - 2 r^5/(5 R^2) + r^7/(7 R^4) ],   accel = -M(<r) x / r^3,
+    and -M/r, -M x/r^3 outside with M = 4 pi R^3 8/105 (Newton's shell theorem).
+    The density is C^1 at r = R, so midpoint sampling converges as O(h^2)."""
+    n = 2 ** level
+    g = np.stack(np.meshgrid(*(np.arange(n),) * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.int32)
+    x = (g + 0.5) / n
+    d = x - centre
+    r = np.linalg.norm(d, axis=1)
+    rho = np.where(r < R, (1 - r ** 2 / R ** 2) ** 2, 0.0)
+    h = W.Hierarchy(level, level, [g], [rho / n ** 3], "smooth sphere")
+    M = 4 * np.pi * R ** 3 * 8 / 105
+    inside = r < R
+    phi = np.where(inside, -4 * np.pi * (r ** 2 / 3 - 2 * r ** 4 / (5 * R ** 2) + r ** 6 / (7 * R ** 4)
+                                         + (R ** 2 / 6) * (1 - r ** 2 / R ** 2) ** 3), -M / r)
+    menc = np.where(inside, 4 * np.pi * (r ** 3 / 3 - 2 * r ** 5 / (5 * R ** 2) + r ** 7 / (7 * R ** 4)), M)
+    acc = -(menc / r ** 3)[:, None] * d
+    return h, r, phi, acc
+
+
+def test_smooth_sphere_closed_form_converges_as_h2():
+    # phi and accel of the FMM (p = 8) against the continuum closed form on 8^3,
+    # 16^3 and 32^3: the error is discretisation-limited and must fall ~4x per
+    # refinement (measured ratios 3.7-4.0); a wrong G, sign, scale or missing
+    # region would not converge to the closed form at all.
+    ep, ea = [], []
+    for level in (3, 4, 5):
+        h, r, phi_x, acc_x = _smooth_sphere(level)
+        idx = np.where(r < 0.45)[0]
+        idx = idx[np.linspace(0, idx.size - 1, min(idx.size, 3000)).astype(np.int64)]
+        phi, a = oracle.solve(h, 8, sel={level: idx})
+        ep.append(rel_rms(phi[level], phi_x[idx]))
+        ea.append(rel_rms(a[level], acc_x[idx]))
+    for e in (ep, ea):
+        assert e[0] / e[1] > 3.5 and e[1] / e[2] > 3.5, (ep, ea)
+    assert ep[2] < 8e-3 and ea[2] < 9e-3
+
+
+def test_axis_permutation():
+    # (i, j, k) -> (j, k, i): every operator treats the axes alike, so the outputs
+    # are the permuted outputs to rounding
+    h = W.random_amr(3, 5, seed=13)
+    perm = [1, 2, 0]
+    m = h.copy()
+    for k in range(len(h.levels)):
+        m.ijk[k] = np.ascontiguousarray(h.ijk[k][:, perm])
+    phi, a = oracle.solve(h, 5)
+    phim, am = oracle.solve(m, 5)
+    for l in h.levels:
+        if a[l].size == 0:
+            continue
+        np.testing.assert_allclose(phim[l], phi[l], rtol=1e-12)
+        np.testing.assert_allclose(am[l], a[l][:, perm], rtol=1e-10, atol=1e-11 * np.abs(a[l]).max())
+
+
+def test_shift_by_a_level1_box():
+    # Mass confined to the octant x < 1/2 of a 16^3 base with a refined block, then
+    # the same masses and block moved by half the box along x.  Boxes of every
+    # level >= 1 map onto boxes, so every interaction list maps onto itself and the
+    # occupied cells get the same outputs to rounding (zero masses elsewhere).
+    lmin, lmax = 4, 5
+    outs = []
+    for sx in (0, 8):
+        refined = W.nested_boxes(lmin, [((2 + sx, 2, 3), (6 + sx, 6, 7))])
+        leaves = W.leaves_from_refined(lmin, lmax, refined)
+        h = W.Hierarchy(lmin, lmax, name="shifted")
+        occ = []
+        for k, c in enumerate(leaves):
+            l = lmin + k
+            c = np.ascontiguousarray(c, dtype=np.int32)
+            shift = sx << k
+            local = c - np.array([shift, 0, 0])
+            inside = (local[:, 0] >= 0) & (local[:, 0] < (8 << k))
+            key = local[:, 0] * 10 ** 6 + local[:, 1] * 10 ** 3 + local[:, 2]
+            mass = np.where(inside, 1.0 + W.uniform(3, 40 + k, np.abs(key) % 4099), 0.0) * 8.0 ** (-l)
+            h.ijk.append(c)
+            h.mass.append(mass)
+            order = np.where(inside)[0][np.argsort(key[inside])]
+            occ.append(order)
+        phi, a = oracle.solve(h, 4)
+        outs.append([(phi[lmin + k][o], a[lmin + k][o]) for k, o in enumerate(occ)])
+    for (p0, a0), (p1, a1) in zip(*outs):
+        assert p0.size > 0
+        np.testing.assert_allclose(p1, p0, rtol=1e-12)
+        np.testing.assert_allclose(a1, a0, rtol=1e-10, atol=1e-11 * np.abs(a0).max())
 
 
 def test_point_mass():
