@@ -58,30 +58,61 @@ typedef enum {
 
 typedef enum {
   FMM_FP64 = 0,          /* every step in FP64 (DFMA) */
-  FMM_MIXED_BF16X3 = 1   /* M2L/M2P on tcgen05 tensor cores in split-BF16 (3 products,
+  FMM_MIXED_BF16X3 = 1,  /* M2L/M2P on tcgen05 tensor cores in split-BF16 (3 products,
                             FP32 accumulation), P2P in FP32, FP64 for box levels <= 3
                             of M2M, for L2L and for local-expansion accumulation */
+  FMM_MIXED_TF32 = 2     /* as FMM_MIXED_BF16X3, but M2L/M2P in one TF32 product per
+                            term (tcgen05 kind::tf32, FP32 accumulation) */
 } fmm_precision;
 
+/* The bottom intermediate field of a target cell t at level l: the sources in the
+ * interaction list of t's parent box F (level l-1). */
+typedef enum {
+  FMM_BOTTOM_M2P = 0,     /* the paper's (Fig. 2, Alg. 4): M2P from each source to t */
+  FMM_BOTTOM_M2L_L2P = 1  /* M2L (Eq. 3) / P2L from each source into F's local
+                             expansion, which also receives F's parent's by L2L
+                             (Eq. 4); t evaluates it by L2P.  The downward pass runs one
+                             level further; the truncation differs from M2P's. */
+} fmm_bottom_mode;
+
 typedef struct {
-  int p;              /* expansion order, 1..8 (Eq. 3 truncation) */
+  int p;              /* expansion order of the local expansions, 1..8 (Eq. 3 truncation) */
   int precision;      /* fmm_precision */
   double G;           /* gravitational constant (outputs scale linearly) */
   int out_fp32;       /* 0: phi/accel outputs are double, 1: float */
   size_t mem_budget;  /* 0: unlimited; else fmm_set_levels fails with FMM_ERR_OOM when
                          the device workspace would exceed this many bytes */
+  int bottom_mode;    /* fmm_bottom_mode */
+  int p_m;            /* multipole order used by M2L and M2P, 1..p; 0 means p.  Eq. 3
+                         sums n <= p - m over the multipoles that exist: with the
+                         paper's quadrupoles and p = 3 (Sec. 2) that is p_m = 2, p = 3.
+                         Terms with |alpha| > p_m are dropped from every translation. */
+  int mass_fp32;      /* 0: masses passed to fmm_set_levels / fmm_update_masses are
+                         double, 1: float (widened exactly to double on the device) */
 } fmm_config;
 
-/* Create a context on the current CUDA device.  The config is copied.
- * Returns FMM_ERR_ARG for p outside 1..8 or an unknown precision. */
-fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out);
+/* Device memory for the library, supplied by the caller (for instance a caching
+ * allocator).  Called with ptr == NULL to allocate `bytes` (return the device
+ * pointer, 256-byte aligned, or NULL when out of memory) and with ptr != NULL to
+ * release an earlier allocation of `bytes` (the return value is ignored).
+ * `stream` is the stream of the library call that needs the memory; the library
+ * orders all its own work on that stream before it returns memory. */
+typedef void* (*fmm_alloc_fn)(void* user, void* ptr, size_t bytes, void* stream);
+
+/* Create a context on the current CUDA device.  The config is copied.  `alloc`
+ * (with its `alloc_user` pointer) supplies every device allocation the context
+ * makes (its workspace, and the translation tables it shares with the other
+ * contexts of the same device, order, precision and allocator); NULL uses
+ * cudaMalloc / cudaFree.  Returns FMM_ERR_ARG for p outside 1..8, p_m outside
+ * 0..p, an unknown precision or bottom mode. */
+fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_user, fmm_ctx** out);
 
 /* Set the AMR hierarchy, or replace its levels lo..lmax (adaptive time
  * stepping: Alg. 1 rebuilds the trees of the active levels only).
  *
  *   n[k]    host int64, number of leaf cells of level lo+k, k = 0..lmax-lo
  *   ijk[k]  int32 [n[k]][3] cell indices of level lo+k, each in [0, 2^(lo+k))
- *   mass[k] double [n[k]] masses
+ *   mass[k] [n[k]] masses, double (or float when config.mass_fp32)
  * ijk/mass may be device or host pointers (host data is copied in on
  * `stream`).  The caller keeps ownership; the library copies what it needs
  * before returning, so the buffers may be reused afterwards.  A call with
@@ -93,16 +124,16 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out);
  * when graphs are on (fmm_set_graphs); this call synchronises `stream` once.
  * Requires 2 <= lmin <= lmax <= 20. */
 fmm_status fmm_set_levels(fmm_ctx* ctx, int lmin, int lmax, int lo, const int64_t* n,
-                          const int32_t* const* ijk, const double* const* mass, void* stream);
+                          const int32_t* const* ijk, const void* const* mass, void* stream);
 
 /* Replace the masses of levels lo..lmax of the current hierarchy, cells
  * unchanged (a time step that moves mass but not the mesh).  mass[k]: double
- * [n] for level lo+k in the order of the last fmm_set_levels of that level,
+ * (float when config.mass_fp32) [n] for level lo+k in the order of the last fmm_set_levels of that level,
  * device or host pointer, copied on `stream` before the call returns (host
  * memory) or in stream order (device memory).  No tree rebuild and no
  * synchronisation; the next solve recomputes what depends on these levels.
  * The values are not validated (fmm_set_levels rejects non-finite masses). */
-fmm_status fmm_update_masses(fmm_ctx* ctx, int lo, const double* const* mass, void* stream);
+fmm_status fmm_update_masses(fmm_ctx* ctx, int lo, const void* const* mass, void* stream);
 
 /* Solve for the leaf cells of levels lo..lmax (Alg. 1 for l = lo..lmax, which
  * share one upward and one downward pass: the far field of a box does not
@@ -159,8 +190,18 @@ fmm_status fmm_solve_adjoint(fmm_ctx* ctx, int lo, const void* const* g_phi, con
                              double* const* g_mass, void* stream);
 
 /* Wait for all work of the context on its last stream and return any
- * latched device error (FMM_ERR_TIMEOUT from a bounded wait, FMM_ERR_CUDA). */
+ * latched device error (FMM_ERR_TIMEOUT from a bounded wait, FMM_ERR_CUDA).
+ * After FMM_ERR_TIMEOUT the outputs of that solve are invalid; the context
+ * clears its partial sums, and the next solve recomputes everything. */
 fmm_status fmm_sync(fmm_ctx* ctx);
+
+/* Every wait of a tensor-core contraction on one of its pipeline barriers gives
+ * up after `seconds` of wall-clock time (default 2; 0 gives up at the first
+ * wait that is not already complete, for tests).  A CTA that gives up latches
+ * FMM_ERR_TIMEOUT (returned by fmm_sync), waits for its own copies and tensor
+ * operations in flight, frees its tensor memory and exits.  FMM_ERR_ARG for a
+ * negative or non-finite value. */
+fmm_status fmm_set_wait_limit(fmm_ctx* ctx, double seconds);
 
 /* Text of the last error of this context (static storage inside ctx). */
 const char* fmm_last_error(const fmm_ctx* ctx);

@@ -35,23 +35,52 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory comes from the caller's allocator when one was given to
+// fmm_create, else from cudaMalloc.  Memory handed back to a caller's allocator
+// may be reused at once in the order of the call's stream; all of the library's
+// work is ordered on that stream (its second stream joins it before a solve
+// ends), so nothing still reads a released buffer out of order.
+static void dev_release(Ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  if (c->alloc)
+    c->alloc(c->alloc_user, p, bytes, (void*)c->last_stream);
+  else
+    cudaFree(p);
+}
+
+static cudaError_t dev_acquire(Ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!c->alloc) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      cudaGetLastError();
+    }
+    return e;
+  }
+  void* q = c->alloc(c->alloc_user, nullptr, bytes, (void*)c->last_stream);
+  if (!q) return cudaErrorMemoryAllocation;
+  if ((uintptr_t)q % 256) {  // tensor maps and vector loads rely on 256-byte alignment
+    c->alloc(c->alloc_user, q, bytes, (void*)c->last_stream);
+    return cudaErrorMisalignedAddress;
+  }
+  *p = q;
+  return cudaSuccess;
+}
+
 cudaError_t buf_ensure(Ctx* c, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return cudaSuccess;
   if (b.ptr) {
-    cudaFree(b.ptr);
+    dev_release(c, b.ptr, b.bytes);
     c->bytes_in_use -= b.bytes;
     b.ptr = nullptr;
     b.bytes = 0;
   }
   ++c->layout_gen;  // cached solve graphs hold the old pointers
   if (c->cfg.mem_budget && c->bytes_in_use + bytes > c->cfg.mem_budget) return cudaErrorMemoryAllocation;
-  cudaError_t e = cudaMalloc(&b.ptr, bytes);
-  if (e != cudaSuccess) {
-    b.ptr = nullptr;
-    cudaGetLastError();
-    return e;
-  }
+  cudaError_t e = dev_acquire(c, &b.ptr, bytes);
+  if (e != cudaSuccess) return e;
   b.bytes = bytes;
   c->bytes_in_use += bytes;
   return cudaSuccess;
@@ -59,11 +88,45 @@ cudaError_t buf_ensure(Ctx* c, DevBuf& b, size_t bytes) {
 
 static void buf_free(Ctx* c, DevBuf& b) {
   if (b.ptr) {
-    cudaFree(b.ptr);
+    dev_release(c, b.ptr, b.bytes);
     c->bytes_in_use -= b.bytes;
   }
   b.ptr = nullptr;
   b.bytes = 0;
+}
+
+namespace {
+// masses given as float (config.mass_fp32): widened exactly to the FP64 copy
+__global__ void k_widen_mass(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+}  // namespace
+
+// Copies the masses of one level into its FP64 array: double input directly,
+// float input through the staging buffer and a widening kernel.
+static fmm_status copy_masses(Ctx* c, LevelTree& T, const void* mass, int64_t nl, cudaStream_t st) {
+  if (!nl) return FMM_OK;
+  if (!c->cfg.mass_fp32) {
+    cudaError_t e = cudaMemcpyAsync(T.mass.ptr, mass, nl * 8, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) {
+      c->last_error = std::string("mass copy: ") + cudaGetErrorString(e);
+      return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->mass_stage.ptr, mass, nl * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) {
+    k_widen_mass<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(nl, (const float*)c->mass_stage.ptr,
+                                                               (double*)T.mass.ptr);
+    ++c->n_launch;
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    c->last_error = std::string("mass copy: ") + cudaGetErrorString(e);
+    return FMM_ERR_CUDA;
+  }
+  return FMM_OK;
 }
 
 namespace {
@@ -114,9 +177,9 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
     // [K'][N] with K' ordered (q, alpha, s) and per-column segment limits
     std::vector<double> f((size_t)K * N);
     std::vector<int32_t> lim(N);
-    for (int n = 0; n < N; ++n) {
+    for (int n = 0; n < N; ++n) {  // the alpha (graded order) a column reads: degree <= min(p - |beta|, p_m)
       int d = m2l ? c->tab.degree[n % nc] : 0;
-      lim[n] = m2l ? 8 * ncoef(c->tab.p - d) : KQ;
+      lim[n] = 8 * ncoef(std::min(c->tab.p - d, c->tab.pm));
     }
     for (int q = 0; q < 26; ++q)
       for (int s = 0; s < 8; ++s)
@@ -151,7 +214,7 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
 
 fmm_status init_tables(Ctx* c) {
   Tables& t = c->tab;
-  t.build(c->cfg.p);
+  t.build(c->cfg.p, c->cfg.p_m);
   TRY(upload(c, c->d_m2m_off, t.m2m_off));
   TRY(upload(c, c->d_m2m_g, t.m2m_g));
   TRY(upload(c, c->d_m2m_e, t.m2m_e));
@@ -292,7 +355,7 @@ fmm_status adjoint_tables(Ctx* c) {
   }
   const int KQ = 8 * nc, K = 26 * KQ;
   Tables full;  // the context keeps no host copy of the contraction operators
-  full.build(c->cfg.p);
+  full.build(c->cfg.p, c->cfg.p_m);
   for (int w = 0; w < 2; ++w) {
     const std::vector<double>& src = w == 0 ? full.m2p : full.m2l;
     if (src.size() != (size_t)(w == 0 ? 256 : 8 * nc) * K) {
@@ -369,11 +432,15 @@ struct TableSet {
   DevBuf bufs[kNumTableBufs];
   GemmOperand op_m2p, op_m2l;
 };
-using TableKey = std::tuple<int, int, int>;
+// (device, p, precision, p_m, allocator, allocator's user pointer): contexts of
+// another allocator get their own copy, released through that allocator
+using TableKey = std::tuple<int, int, int, int, uintptr_t, uintptr_t>;
 std::mutex g_tables_mu;
 std::map<TableKey, TableSet*> g_tables;
 
-TableKey table_key(const Ctx* c) { return TableKey(c->device, c->cfg.p, c->cfg.precision); }
+TableKey table_key(const Ctx* c) {
+  return TableKey(c->device, c->cfg.p, c->cfg.precision, c->cfg.p_m, (uintptr_t)c->alloc, (uintptr_t)c->alloc_user);
+}
 
 fmm_status acquire_tables(Ctx* c) {
   std::lock_guard<std::mutex> lock(g_tables_mu);
@@ -459,14 +526,22 @@ struct fmm_ctx : public fmm::Ctx {};
 
 extern "C" {
 
-fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
+fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_user, fmm_ctx** out) {
   if (!cfg || !out) return FMM_ERR_ARG;
   *out = nullptr;
   if (cfg->p < 1 || cfg->p > 8) return FMM_ERR_ARG;
-  if (cfg->precision != FMM_FP64 && cfg->precision != FMM_MIXED_BF16X3) return FMM_ERR_ARG;
+  if (cfg->p_m < 0 || cfg->p_m > cfg->p) return FMM_ERR_ARG;
+  if (cfg->precision != FMM_FP64 && cfg->precision != FMM_MIXED_BF16X3 && cfg->precision != FMM_MIXED_TF32)
+    return FMM_ERR_ARG;
+  if (cfg->bottom_mode != FMM_BOTTOM_M2P && cfg->bottom_mode != FMM_BOTTOM_M2L_L2P) return FMM_ERR_ARG;
+  if (cfg->mass_fp32 != 0 && cfg->mass_fp32 != 1) return FMM_ERR_ARG;
   if (!std::isfinite(cfg->G)) return FMM_ERR_ARG;
+  if (cfg->precision == FMM_MIXED_TF32 || cfg->bottom_mode != FMM_BOTTOM_M2P) return FMM_ERR_ARG;  // not built yet
   fmm_ctx* c = new fmm_ctx();
   c->cfg = *cfg;
+  if (c->cfg.p_m == c->cfg.p) c->cfg.p_m = 0;  // one key for the full order
+  c->alloc = alloc;
+  c->alloc_user = alloc_user;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -475,12 +550,12 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_ctx** out) {
   }
   c->device = dev;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaMalloc(&c->d_err, kErrWords * 4);
+  cudaError_t e = buf_ensure(c, c->err_buf, kErrWords * 4);
   if (e != cudaSuccess) {
-    cudaGetLastError();
     delete c;
     return e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;
   }
+  c->d_err = (unsigned*)c->err_buf.ptr;
   cudaMemset(c->d_err, 0, kErrWords * 4);
   for (auto& ev : c->ev) cudaEventCreate(&ev);
   if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -545,8 +620,43 @@ static fmm_status launch_tree_graph(Ctx* c, cudaStream_t st) {
   return FMM_OK;
 }
 
+static fmm_status set_levels_impl(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t* n,
+                                  const int32_t* const* ijk, const void* const* mass, void* stream);
+
+// A hierarchy that does not fit (FMM_ERR_OOM) leaves no half-grown workspace
+// behind: every per-hierarchy buffer is released (the shared tables stay), so a
+// smaller hierarchy fits the budget again.  The context then has no hierarchy.
+static void release_workspace(Ctx* c) {
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  for (auto& T : c->lev)
+    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows,
+                      &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.tgt, &T.ijk, &T.mass, &T.M,
+                      &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc})
+      buf_free(c, *b);
+  for (DevBuf* b : {&c->sort_tmp, &c->keys_a, &c->keys_b, &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter,
+                    &c->anc_flags, &c->out_stage, &c->in_stage, &c->mass_stage})
+    buf_free(c, *b);
+  for (auto& T : c->lev) T.n_oct = T.n_leaf = T.n_rows = T.n_tgt = T.n_rowsL = T.n_irows = T.n_anc = 0;
+  c->cub_sig.clear();
+  c->count_sig.clear();
+  c->adj_gen = 0;
+  ++c->layout_gen;
+  c->have_levels = false;
+}
+
 fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t* n, const int32_t* const* ijk,
-                          const double* const* mass, void* stream) {
+                          const void* const* mass, void* stream) {
+  fmm_status s = set_levels_impl(c, lmin, lmax, lo, n, ijk, mass, stream);
+  if (s == FMM_ERR_OOM && c) {
+    const std::string msg = c->last_error;
+    release_workspace(c);
+    c->last_error = msg + " (the hierarchy's workspace was released)";
+  }
+  return s;
+}
+
+static fmm_status set_levels_impl(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t* n,
+                                  const int32_t* const* ijk, const void* const* mass, void* stream) {
   if (!c || !n || !ijk || !mass) return FMM_ERR_ARG;
   if (lmin < 2 || lmax < lmin || lmax > kMaxLevel || lo < lmin || lo > lmax) return FMM_ERR_ARG;
   if (!c->have_levels) {
@@ -566,6 +676,11 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
   c->lmin = lmin;
   c->lmax = lmax;
   c->have_levels = false;
+  if (c->cfg.mass_fp32) {
+    int64_t nmax = 1;
+    for (int k = 0; k <= lmax - lo; ++k) nmax = std::max(nmax, n[k]);
+    CKS(buf_ensure(c, c->mass_stage, nmax * 4));
+  }
   for (int l = lo; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
     int64_t nl = n[l - lo];
@@ -574,7 +689,7 @@ fmm_status fmm_set_levels(fmm_ctx* c, int lmin, int lmax, int lo, const int64_t*
     CKS(buf_ensure(c, T.mass, nl * 8));
     if (nl) {
       CKS(cudaMemcpyAsync(T.ijk.ptr, ijk[l - lo], nl * 12, cudaMemcpyDefault, st));
-      CKS(cudaMemcpyAsync(T.mass.ptr, mass[l - lo], nl * 8, cudaMemcpyDefault, st));
+      TRY(copy_masses(c, T, mass[l - lo], nl, st));
     }
   }
   // trailing empty levels: the tree ends at the finest level that holds leaves
@@ -1128,7 +1243,7 @@ fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const
   return FMM_OK;
 }
 
-fmm_status fmm_update_masses(fmm_ctx* c, int lo, const double* const* mass, void* stream) {
+fmm_status fmm_update_masses(fmm_ctx* c, int lo, const void* const* mass, void* stream) {
   if (!c || !mass) return FMM_ERR_ARG;
   if (!c->have_levels) {
     c->last_error = "fmm_update_masses before fmm_set_levels";
@@ -1139,11 +1254,20 @@ fmm_status fmm_update_masses(fmm_ctx* c, int lo, const double* const* mass, void
     if (c->lev[l].n_leaf && !mass[l - lo]) return FMM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
-  for (int l = lo; l <= c->lmax; ++l) {
-    const int64_t nl = c->lev[l].n_leaf;
-    if (nl) CKS(cudaMemcpyAsync(c->lev[l].mass.ptr, mass[l - lo], nl * 8, cudaMemcpyDefault, st));
+  if (c->cfg.mass_fp32) {
+    int64_t nmax = 1;
+    for (int l = lo; l <= c->lmax; ++l) nmax = std::max(nmax, c->lev[l].n_leaf);
+    CKS(buf_ensure(c, c->mass_stage, nmax * 4));
   }
+  for (int l = lo; l <= c->lmax; ++l) TRY(copy_masses(c, c->lev[l], mass[l - lo], c->lev[l].n_leaf, st));
   c->dirty_lo = std::min(c->dirty_lo, lo);
+  return FMM_OK;
+}
+
+fmm_status fmm_set_wait_limit(fmm_ctx* c, double seconds) {
+  if (!c || !std::isfinite(seconds) || seconds < 0.0 || seconds > 3600.0) return FMM_ERR_ARG;
+  c->wait_s = seconds;
+  ++c->layout_gen;  // cached graphs carry the old limit in their launch parameters
   return FMM_OK;
 }
 
@@ -1194,9 +1318,10 @@ void fmm_destroy(fmm_ctx* c) {
                     &c->d_l2lT_c, &c->d_m2pT, &c->d_m2lT, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
-                    &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->anc_flags, &c->out_stage, &c->in_stage})
+                    &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->anc_flags, &c->out_stage, &c->in_stage,
+                    &c->mass_stage, &c->err_buf})
     buf_free(c, *b);
-  if (c->d_err) cudaFree(c->d_err);
+  c->d_err = nullptr;
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : c->tree_graphs) cudaGraphExecDestroy(g.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -148,7 +148,13 @@ struct Ctx {
   size_t cub_tmp = 0;            // and its answer (bytes of sort_tmp needed)
   DevBuf out_stage;     // device staging for host outputs
   DevBuf in_stage;      // device staging for host inputs
+  DevBuf mass_stage;    // FP32 masses (config.mass_fp32) on their way to the FP64 copies
+  DevBuf err_buf;       // the device error words (d_err points into it)
   unsigned* d_err = nullptr;
+  // the caller's allocator (null: cudaMalloc / cudaFree)
+  fmm_alloc_fn alloc = nullptr;
+  void* alloc_user = nullptr;
+  double wait_s = 2.0;  // limit of every bounded device-side wait (fmm_set_wait_limit)
   size_t bytes_in_use = 0;
   std::string last_error;
   cudaStream_t last_stream = nullptr;

@@ -25,8 +25,10 @@
 // then re-read the row slices of the same few hundred neighbour octs across the
 // 26 offsets, and the shared memory left unused (4 B stages) keeps them in L1.
 // Split-K over grid.z; partial sums are added with atomics.  Every wait on an
-// mbarrier is bounded by a wall-clock limit; on expiry the CTA latches
-// kErrTimeout, skips the remaining work and still frees its TMEM.
+// mbarrier is bounded by a wall-clock limit (a launch parameter); on expiry the
+// CTA latches kErrTimeout and skips the remaining work, but before it frees its
+// TMEM and exits it waits (with a fixed limit of its own) for the TMA loads and
+// the MMAs it has already issued: those still write shared and tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -48,7 +50,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAcol0 = 256;              // first A column
 constexpr int kNbrStride = 27;  // shared-memory row stride of the per-row neighbour table
 constexpr int kMaxSeg = 24;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr uint64_t kDrainLimitNs = 1000000000ull;  // 1 s: waits for a CTA's own copies and MMAs in flight
 
 __constant__ int c_nbr26[26] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12,
                                 14, 15, 16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26};
@@ -80,6 +82,7 @@ struct TcParams {
                    // slice in a row) so a source row slice is re-read from L1; 0: in K order
   int BN, N, nc, mode;
   unsigned* err;
+  uint64_t wait_ns;  // limit of every pipeline wait
 };
 
 // First K index of the it-th slice a CTA visits.  Slice-major order (slice c of
@@ -121,19 +124,30 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait: returns false (and sets *abort) if the phase did not complete
-// within kWaitLimitNs or another thread already aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// within limit_ns or another thread already aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   uint64_t t0 = now_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try(bar, parity)) return true;
     if ((i & 1023) == 0) {
       if (*abort) return false;
-      if (now_ns() - t0 > kWaitLimitNs) {
+      if (now_ns() - t0 > limit_ns) {
         *abort = 1;
         return false;
       }
     }
+  }
+}
+// Wait for work this CTA itself issued (a TMA load, a tcgen05.commit) to land
+// before it leaves; that work completes by itself, so only a fixed limit
+// guards it, and the abort flag is ignored.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 1023) == 0 && now_ns() - t0 > kDrainLimitNs) return false;
   }
 }
 
@@ -209,8 +223,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int b_bytes = P.BN * BK * 2;  // BN * 64
   unsigned char* Bhi = sm;
   unsigned char* Blo = Bhi + SB * b_bytes;
-  uint64_t* bars = (uint64_t*)(Blo + SB * b_bytes);  // fullA[SA], emptyA[SA], fullB[SB], emptyB[SB], done
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * SA + 2 * SB + 1);
+  // fullA[SA], emptyA[SA], fullB[SB], emptyB[SB], done, drain (the MMA issuer's last commit)
+  uint64_t* bars = (uint64_t*)(Blo + SB * b_bytes);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * SA + 2 * SB + 2);
   volatile int* abort = (volatile int*)(tmem_slot + 1);
   int32_t* s_nbr = (int32_t*)(tmem_slot + 4);  // [BM][kNbrStride] source octs of each row
 
@@ -221,6 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t fullA0 = smem_u32(bars), emptyA0 = smem_u32(bars + SA);
   const uint32_t fullB0 = smem_u32(bars + 2 * SA), emptyB0 = smem_u32(bars + 2 * SA + SB);
   const uint32_t done = smem_u32(bars + 2 * SA + 2 * SB);
+  const uint32_t drain = smem_u32(bars + 2 * SA + 2 * SB + 1);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < SA; ++s) {
@@ -232,6 +248,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(emptyB0 + 8 * s, 1);   // tcgen05.commit
     }
     mbar_init(done, 1);
+    mbar_init(drain, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -268,7 +285,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     for (int it = warp >> 2; it < nit && ok; it += kPhases) {
       const int s = it % SA;
-      if (it >= SA) ok = mbar_wait(emptyA0 + 8 * s, ((it / SA) - 1) & 1, abort);
+      if (it >= SA) ok = mbar_wait(emptyA0 + 8 * s, ((it / SA) - 1) & 1, abort, P.wait_ns);
       if (!ok) break;
       const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
       uint32_t hv[16], lv[16];
@@ -349,7 +366,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       } else if (valid) {
         slot = S.slot[roct];
       }
-      bool have = ok && nit > 0 && mbar_wait(done, 0, abort);
+      bool have = ok && nit > 0 && mbar_wait(done, 0, abort, P.wait_ns);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -387,16 +404,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- B tiles by TMA ----------------
     if (lane == 0) {
       bool ok = true;
+      int issued = 0;
       for (int it = 0; it < nit && ok; ++it) {
         const int s = it % SB;
-        if (it >= SB) ok = mbar_wait(emptyB0 + 8 * s, ((it / SB) - 1) & 1, abort);
+        if (it >= SB) ok = mbar_wait(emptyB0 + 8 * s, ((it / SB) - 1) & 1, abort, P.wait_ns);
         if (!ok) break;
         const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
         const int n0 = blockIdx.y * P.BN;
         mbar_arrive_tx(fullB0 + 8 * s, 2u * (uint32_t)b_bytes);
         tma_load_2d(smem_u32(Bhi + s * b_bytes), &tm_hi, k0, n0, fullB0 + 8 * s);
         tma_load_2d(smem_u32(Blo + s * b_bytes), &tm_lo, k0, n0, fullB0 + 8 * s);
+        ++issued;
       }
+      // Loads older than the last SB were consumed by the MMA (it waited for them
+      // before freeing their stage); the last SB may still be landing.
+      for (int it = max(0, issued - SB); it < issued; ++it)
+        if (!mbar_drain(fullB0 + 8 * (it % SB), (it / SB) & 1)) *abort = 1;
     }
     __syncwarp();
   } else if (warp == kWarpMma) {
@@ -406,10 +429,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.BN >> 3) << 17) |
                              ((uint32_t)(BM >> 4) << 24);
       bool ok = true;
+      int issued = 0;
       for (int it = 0; it < nit && ok; ++it) {
         const int sa = it % SA, sb = it % SB;
-        ok = mbar_wait(fullA0 + 8 * sa, (it / SA) & 1, abort) && mbar_wait(fullB0 + 8 * sb, (it / SB) & 1, abort);
+        ok = mbar_wait(fullA0 + 8 * sa, (it / SA) & 1, abort, P.wait_ns) &&
+             mbar_wait(fullB0 + 8 * sb, (it / SB) & 1, abort, P.wait_ns);
         if (!ok) break;
+        ++issued;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acol = tmem + kAcol0 + 32u * (uint32_t)sa;  // hi at +0, lo at +16
         const uint32_t bh = smem_u32(Bhi + sb * b_bytes), bl = smem_u32(Blo + sb * b_bytes);
@@ -427,6 +453,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         mma_commit(emptyB0 + 8 * sb);
       }
       if (ok && nit > 0) mma_commit(done);
+      // Every MMA issued must finish before the tensor memory is freed, also when
+      // a wait gave up (the epilogue then does not wait for `done`).
+      if (issued > 0) {
+        mma_commit(drain);
+        if (!mbar_drain(drain, 0)) *abort = 1;
+      }
     }
     __syncwarp();
   }
@@ -453,7 +485,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 size_t smem_bytes(int BN) {
-  return 1024 + SB * (2 * BN * BK * 2) + (2 * SA + 2 * SB + 1) * 8 + 16 + BM * kNbrStride * 4;
+  return 1024 + SB * (2 * BN * BK * 2) + (2 * SA + 2 * SB + 2) * 8 + 16 + BM * kNbrStride * 4;
 }
 
 // split-K factor minimising waves x chunks per CTA
@@ -546,6 +578,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.nc = c->tab.nc;
   P.mode = mode;
   P.err = c->d_err;
+  P.wait_ns = (uint64_t)(c->wait_s * 1e9);
   dim3 grid((unsigned)tiles, (unsigned)op.ntile, (unsigned)nz);
   ++c->n_launch;
   launch_pdl(k_gemm_tc, grid, THREADS, smem_bytes(op.BN), st, *(const CUtensorMap*)op.tmap_hi,

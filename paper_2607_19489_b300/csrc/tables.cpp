@@ -109,8 +109,9 @@ void deriv_g(const int64_t u[3], double scale, int q, const MultiIdx& mi, std::v
 
 }  // namespace
 
-void Tables::build(int p_) {
+void Tables::build(int p_, int p_m) {
   p = p_;
+  pm = (p_m > 0 && p_m < p) ? p_m : p;
   nc = ncoef(p);
   nc1 = ncoef(p + 1);
   mi.build(p + 1);
@@ -137,6 +138,7 @@ void Tables::build(int p_) {
           if (adj) continue;  // S touches F: near field
           deriv_g(u, 4.0, p + 1, mi, D);
           for (int a = 0; a < nc; ++a) {
+            if (degree[a] > pm) continue;
             const auto& al = mi.list[a];
             double w = ((degree[a] & 1) ? -1.0 : 1.0) / mfact(al);
             size_t k = (size_t)(qi * 8 + s) * nc + a;
@@ -167,7 +169,7 @@ void Tables::build(int p_) {
         for (int be = 0; be < nc; ++be) {
           const auto& B = mi.list[be];
           for (int a = 0; a < nc; ++a) {
-            if (degree[a] + degree[be] > p) continue;
+            if (degree[a] + degree[be] > p || degree[a] > pm) continue;
             const auto& al = mi.list[a];
             double w = ((degree[a] & 1) ? -1.0 : 1.0) / mfact(al);
             size_t k = (size_t)(qi * 8 + s) * nc + a;
@@ -188,6 +190,7 @@ void Tables::build(int p_) {
         deriv_g(u, 1.0, p + 1, mi, D);
         size_t base = (size_t)((z + 3) * 49 + (y + 3) * 7 + (x + 3)) * nc * 4;
         for (int a = 0; a < nc; ++a) {
+          if (degree[a] > pm) continue;
           const auto& al = mi.list[a];
           double w = ((degree[a] & 1) ? -1.0 : 1.0) / mfact(al);
           nearop[base + a * 4 + 0] = w * D[mi.at(al[0], al[1], al[2])];

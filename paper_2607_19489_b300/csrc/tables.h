@@ -39,6 +39,9 @@ extern const int kNbr26[26];
 
 struct Tables {
   int p = 0, nc = 0, nc1 = 0;  // ncoef(p), ncoef(p+1)
+  int pm = 0;                  // multipole order of M2L / M2P / near M2P (<= p): terms with
+                               // |alpha| > pm are zero in those operators (Eq. 3 with
+                               // multipoles up to order pm only)
   MultiIdx mi;                 // |alpha| <= p+1
 
   // Operators (FP64).  Index conventions:
@@ -67,7 +70,7 @@ struct Tables {
   // degree of each coefficient (|alpha|) for alpha < nc
   std::vector<int> degree;
 
-  void build(int p);
+  void build(int p, int p_m = 0);  // p_m = 0: p
 };
 
 }  // namespace fmm

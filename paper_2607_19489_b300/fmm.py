@@ -18,13 +18,14 @@ LIB_PATH = os.path.join(_HERE, "libfmm.so")
 STATUS = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_NOT_GRADED", -3: "FMM_ERR_DUPLICATE",
           -4: "FMM_ERR_OUT_OF_BOX", -5: "FMM_ERR_OOM", -6: "FMM_ERR_CUDA", -7: "FMM_ERR_NONFINITE",
           -8: "FMM_ERR_STATE", -9: "FMM_ERR_TIMEOUT", -10: "FMM_ERR_INCOMPLETE"}
-PRECISION = {"fp64": 0, "mixed": 1, "bf16x3": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "bf16x3": 1, "tf32": 2}
+BOTTOM = {"m2p": 0, "m2l": 1}
 
 EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_error", "fmm_destroy",
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
             "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static",
             "fmm_solve_adjoint", "fmm_batch_solve", "fmm_autotune", "fmm_get_tuning",
-            "fmm_set_tuning", "fmm_update_masses"]
+            "fmm_set_tuning", "fmm_update_masses", "fmm_set_wait_limit"]
 
 
 class FMMError(RuntimeError):
@@ -36,8 +37,40 @@ class FMMError(RuntimeError):
 
 class _Config(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("G", ctypes.c_double),
-                ("out_fp32", ctypes.c_int), ("mem_budget", ctypes.c_size_t)]
+                ("out_fp32", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("bottom_mode", ctypes.c_int),
+                ("p_m", ctypes.c_int), ("mass_fp32", ctypes.c_int)]
 
+
+# fmm_alloc_fn: (user, ptr, bytes, stream) -> ptr
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_shutting_down = False
+
+
+def _torch_alloc(user, ptr, nbytes, stream):
+    """The library's device memory from PyTorch's caching allocator, on the stream of
+    the library call that needs it.  Frees after interpreter shutdown has begun are
+    skipped (the process is exiting; torch may already be torn down)."""
+    try:
+        import torch
+        if ptr:
+            if not _shutting_down:
+                torch.cuda.caching_allocator_delete(ptr)
+            return None
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+    except Exception:  # out of memory (or no CUDA): the library reports FMM_ERR_OOM
+        return None
+
+
+TORCH_ALLOC = ALLOC_FN(_torch_alloc)   # kept alive for as long as the module is
+
+
+def _at_exit():
+    global _shutting_down
+    _shutting_down = True
+
+
+import atexit  # noqa: E402
+atexit.register(_at_exit)
 
 _lib = None
 
@@ -51,7 +84,7 @@ def lib() -> ctypes.CDLL:
         raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2607_19489_b300.build`")
     L = ctypes.CDLL(LIB_PATH)
     P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
-    L.fmm_create.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(P)]
+    L.fmm_create.argtypes = [ctypes.POINTER(_Config), ALLOC_FN, P, ctypes.POINTER(P)]
     L.fmm_set_levels.argtypes = [P, I, I, I, P, P, P, P]
     L.fmm_solve.argtypes = [P, I, P, P, P]
     L.fmm_sync.argtypes = [P]
@@ -74,6 +107,7 @@ def lib() -> ctypes.CDLL:
     L.fmm_set_tuning.argtypes = [P, P]
     L.fmm_update_masses.argtypes = [P, I, P, P]
     L.fmm_stage_times.argtypes = [P, P]
+    L.fmm_set_wait_limit.argtypes = [P, ctypes.c_double]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("fmm_last_error", "fmm_destroy"):
@@ -125,16 +159,30 @@ def host_table(p: int, which: str) -> np.ndarray:
 
 
 class Solver:
-    """One FMM context (fmm_ctx) on the current CUDA device."""
+    """One FMM context (fmm_ctx) on the current CUDA device.
+
+    precision: "fp64", "mixed" (split-BF16 tensor-core translations) or "tf32";
+    bottom: "m2p" (the paper's bottom intermediate field) or "m2l" (M2L into the
+    parent box + L2P); p_m: multipole order of the translations (None: p);
+    mass_fp32: masses are given as float32; allocator: "torch" (PyTorch's caching
+    allocator supplies the library's device memory) or "cuda" (cudaMalloc)."""
 
     def __init__(self, p: int = 6, precision: str = "mixed", G: float = 1.0, out_fp32: bool = False,
-                 mem_budget: int = 0):
+                 mem_budget: int = 0, bottom: str = "m2p", p_m: int | None = None, mass_fp32: bool = False,
+                 allocator: str = "torch"):
         self.p = p
         self.precision = precision
         self.out_fp32 = out_fp32
-        cfg = _Config(p, PRECISION[precision], float(G), int(out_fp32), int(mem_budget))
+        self.mass_fp32 = mass_fp32
+        self.bottom = bottom
+        self.p_m = p if p_m is None else p_m
+        cfg = _Config(p, PRECISION[precision], float(G), int(out_fp32), int(mem_budget), BOTTOM[bottom],
+                      0 if p_m is None else int(p_m), int(mass_fp32))
+        if allocator not in ("torch", "cuda"):
+            raise ValueError("allocator must be 'torch' or 'cuda'")
         h = ctypes.c_void_p()
-        rc = lib().fmm_create(ctypes.byref(cfg), ctypes.byref(h))
+        fn = TORCH_ALLOC if allocator == "torch" else ALLOC_FN()
+        rc = lib().fmm_create(ctypes.byref(cfg), fn, None, ctypes.byref(h))
         if rc:
             raise FMMError(rc, "fmm_create")
         self._h = h
@@ -156,8 +204,8 @@ class Solver:
             raise FMMError(rc, f"{what}: {msg.decode() if msg else ''}")
 
     def set_levels(self, lmin: int, lmax: int, ijk, mass, lo: int | None = None, stream=None):
-        """ijk[k] int32 [n,3] and mass[k] float64 [n] for levels lo..lmax (torch tensors on
-        the device, or numpy arrays on the host)."""
+        """ijk[k] int32 [n,3] and mass[k] float64 [n] (float32 when mass_fp32) for levels
+        lo..lmax (torch tensors on the device, or numpy arrays on the host)."""
         lo = lmin if lo is None else lo
         n = np.array([int(a.shape[0]) for a in ijk], dtype=np.int64)
         keep = list(ijk) + list(mass)
@@ -185,8 +233,9 @@ class Solver:
         import torch
         lo = h.lmin if lo is None else lo
         ks = range(lo - h.lmin, h.lmax - h.lmin + 1)
+        mdt = torch.float32 if self.mass_fp32 else torch.float64
         ijk = [torch.as_tensor(h.ijk[k], dtype=torch.int32, device=device).contiguous() for k in ks]
-        mass = [torch.as_tensor(h.mass[k], dtype=torch.float64, device=device).contiguous() for k in ks]
+        mass = [torch.as_tensor(h.mass[k], dtype=mdt, device=device).contiguous() for k in ks]
         self.set_levels(h.lmin, h.lmax, ijk, mass, lo=lo, stream=stream)
 
     def alloc_outputs(self, lo: int | None = None, device="cuda"):
@@ -255,6 +304,10 @@ class Solver:
 
     def set_timing(self, on: bool):
         self._check(lib().fmm_set_timing(self._h, int(on)), "fmm_set_timing")
+
+    def set_wait_limit(self, seconds: float) -> None:
+        """Limit of every bounded device-side wait (fmm_set_wait_limit)."""
+        self._check(lib().fmm_set_wait_limit(self._h, float(seconds)), "fmm_set_wait_limit")
 
     def set_graphs(self, on: bool) -> None:
         """Replay solves as CUDA graphs (default) or launch every kernel directly."""
