@@ -27,6 +27,15 @@
 //   * M2L at box levels 2..l-2, L2P from the level l-2 box, M2P at level l-1;
 //   * self-interaction excluded; targets are leaf cells only; isolated
 //     boundaries (nothing outside the unit box).
+// Two options beside the paper's defaults:
+//   * multipole order p_m <= p: Eq. 3 sums n <= p - m over the multipoles that
+//     exist; the paper's quadrupoles with p = 3 are p_m = 2.  M2L keeps
+//     |alpha| <= p_m and |alpha| + |beta| <= p, M2P keeps |alpha| <= p_m;
+//   * bottom mode 1: the sources of the interaction list of the target's parent
+//     box F (level l-1) reach the target through F's local expansion (M2L / P2L
+//     into F, which also receives L2L from its parent, then L2P), instead of
+//     M2P / P2P to the target (Fig. 2, Alg. 4).  The downward pass then runs to
+//     box level l-1 and the far field is the L2P of F.
 //
 // Parity status: pinned by the tests in tests/test_oracle_*.py against the
 // O(N^2) direct sum (exact agreement where the FMM has no far field, error
@@ -207,9 +216,10 @@ struct DCache {
 // Expansion operators, each written from its equation.  Coordinates physical.
 struct Ops {
   int p;
+  int pm;          // multipole order of M2L and M2P (<= p)
   MultiIndex mi;   // |alpha| <= p
   MultiIndex mi1;  // |alpha| <= p+1 (matches g_der.mi prefix)
-  explicit Ops(int p_) : p(p_) {
+  explicit Ops(int p_, int pm_ = 0) : p(p_), pm(pm_ > 0 && pm_ < p_ ? pm_ : p_) {
     mi.build(p);
     mi1.build(p + 1);
   }
@@ -237,14 +247,14 @@ struct Ops {
       Mp[k] += s;
     }
   }
-  // Eq. (3): L_beta += sum_{|alpha|<=p-|beta|} (-1)^|alpha|/alpha! D_{alpha+beta}(c_t - c_s) M_alpha
+  // Eq. (3): L_beta += sum_{|alpha|<=p-|beta|, |alpha|<=pm} (-1)^|alpha|/alpha! D_{alpha+beta}(c_t - c_s) M_alpha
   void m2l(const Vec& M, const Vec& D, Vec& L) const {
     for (int kb = 0; kb < n(); ++kb) {
       const I3& b = mi.list[kb];
       double s = 0.0;
       for (int ka = 0; ka < n(); ++ka) {
         const I3& a = mi.list[ka];
-        if (deg(a) + deg(b) > p) continue;
+        if (deg(a) + deg(b) > p || deg(a) > pm) continue;
         double sg = (deg(a) % 2) ? -1.0 : 1.0;
         s += sg / mfact(a) * D[mi1.at(a[0] + b[0], a[1] + b[1], a[2] + b[2])] * M[ka];
       }
@@ -284,11 +294,12 @@ struct Ops {
       }
     }
   }
-  // M2P: phi = sum_{|alpha|<=p} (-1)^|alpha|/alpha! D_alpha(x - c) M_alpha;
+  // M2P: phi = sum_{|alpha|<=pm} (-1)^|alpha|/alpha! D_alpha(x - c) M_alpha;
   // d phi/dx_i uses D_{alpha+e_i}.  D must hold |gamma| <= p+1.
   void m2p(const Vec& M, const Vec& D, double* phi, double* grad) const {
     for (int k = 0; k < n(); ++k) {
       const I3& a = mi.list[k];
+      if (deg(a) > pm) continue;
       double w = ((deg(a) % 2) ? -1.0 : 1.0) / mfact(a) * M[k];
       *phi += w * D[mi1.at(a[0], a[1], a[2])];
       grad[0] += w * D[mi1.at(a[0] + 1, a[1], a[2])];
@@ -441,10 +452,11 @@ Tree build_tree(const Hier& H, const Ops& op, int j) {
 struct Solver {
   const Hier& H;
   int p;
+  int bottom;               // 0: M2P bottom intermediate field (paper); 1: M2L into F + L2P
   Ops op;
   std::vector<Tree> trees;  // indexed by AMR level j
 
-  Solver(const Hier& h, int p_) : H(h), p(p_), op(p_) {
+  Solver(const Hier& h, int p_, int pm = 0, int bottom_ = 0) : H(h), p(p_), bottom(bottom_), op(p_, pm) {
     ensure_derivs(p + 1);
     trees.resize(H.lmax + 1);
     for (int j = H.lmin; j <= H.lmax; ++j) trees[j] = build_tree(H, op, j);
@@ -495,22 +507,24 @@ struct Solver {
   }
 
   // MultipoleToLocal (Alg. 3) for target level l: L at every level-b ancestor
-  // (b = 2..l-2) of a level-l leaf.  Level 0 and 1 boxes have empty
-  // interaction lists, so the first local expansion is at box level 2.
+  // (b = 2..top) of a level-l leaf, top = l-2 (bottom mode 1: l-1, the
+  // parent box F itself).  Level 0 and 1 boxes have empty interaction lists,
+  // so the first local expansion is at box level 2.
   std::vector<Grid> downward(int l, const std::vector<Grid>& mt, int nthreads) const {
     std::vector<Grid> L(l + 1);
-    if (l - 2 < 2) return L;
+    const int top = bottom ? l - 1 : l - 2;
+    if (top < 2) return L;
     // boxes that need L: ancestors of level-l leaves
     std::vector<std::set<I3>> need(l + 1);
     for (const auto& kv : H.leaf[l]) {
       I3 c = kv.first;
       for (int b = l - 1; b >= 2; --b) {
         c = parent_of(c);
-        if (b <= l - 2) need[b].insert(c);
+        if (b <= top) need[b].insert(c);
       }
     }
     int nc = op.n();
-    for (int b = 2; b <= l - 2; ++b) {
+    for (int b = 2; b <= top; ++b) {
       std::vector<I3> boxes(need[b].begin(), need[b].end());
       std::vector<Vec> res(boxes.size(), Vec(nc, 0.0));
 #pragma omp parallel num_threads(nthreads)
@@ -556,14 +570,22 @@ struct Solver {
     double xt[3];
     centre(t, l, xt);
     I3 F = parent_of(t);
-    // far field: local expansion of the level l-2 box
-    if (l - 2 >= 2) {
+    if (bottom) {
+      // bottom mode 1: far and intermediate fields both from F's local expansion
+      if (l - 1 >= 2) {
+        double c[3];
+        centre(F, l - 1, c);
+        op.l2p(L[l - 1].at(F), c, xt, phi, grad);
+      }
+    } else if (l - 2 >= 2) {
+      // far field: local expansion of the level l-2 box
       I3 G2 = parent_of(F);
       double c[3];
       centre(G2, l - 2, c);
       op.l2p(L[l - 2].at(G2), c, xt, phi, grad);
     }
-    // intermediate field: interaction list of F at level l-1
+    // intermediate field: interaction list of F at level l-1 (bottom mode 0)
+    if (!bottom)
     for (const I3& S : ilist(F, l - 1)) {
       double cS[3], R[3];
       centre(S, l - 1, cS);
@@ -635,16 +657,17 @@ extern "C" {
 // n_sel == NULL means all leaves.  phi[l-lmin] (double[n_sel]) and
 // acc[l-lmin] (double[n_sel][3]) receive G*phi and -G*grad phi.  Returns 0 or a
 // negative validation code.
+// p_m: multipole order of M2L / M2P (0: p); bottom: 0 = M2P, 1 = M2L + L2P.
 int oracle_fmm_solve(int lmin, int lmax, const int64_t* n, const int32_t* const* ijk,
-                     const double* const* mass, int p, double G, int lo,
+                     const double* const* mass, int p, double G, int p_m, int bottom, int lo,
                      const int64_t* n_sel, const int64_t* const* sel, double* const* phi,
                      double* const* acc, int nthreads) {
-  if (p < 1 || p > 12 || nthreads < 1) return ORC_ERR_ARG;
+  if (p < 1 || p > 12 || nthreads < 1 || p_m < 0 || p_m > p || (bottom != 0 && bottom != 1)) return ORC_ERR_ARG;
   Hier H;
   int rc = H.build(lmin, lmax, n, ijk, mass);
   if (rc) return rc;
   if (lo < lmin || lo > lmax) return ORC_ERR_ARG;
-  Solver S(H, p);
+  Solver S(H, p, p_m, bottom);
   for (int l = lo; l <= lmax; ++l) {
     int64_t nt = n_sel ? n_sel[l - lmin] : n[l - lmin];
     if (nt == 0) continue;

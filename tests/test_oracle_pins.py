@@ -4,8 +4,9 @@ Each test ties one part of the oracle to something fixed outside it: closed
 forms of the derivatives of 1/r and the Legendre identity, the M2M and L2L
 exactness identities, analytic truncation behaviour, the O(N^2) direct sum
 (including the full 32^3 unigrid), the closed-form potential of a smooth
-sphere with O(h^2) convergence, linearity, mirror, axis-permutation and shift
-symmetries, the exact antisymmetry of nearest-field pairs (Sec. 3.2) and the
+sphere with O(h^2) convergence, the M2L + L2P bottom mode and the multipole
+order p_m (Eq. 3 over the multipoles that exist), linearity, mirror,
+axis-permutation and shift symmetries, the exact antisymmetry of nearest-field pairs (Sec. 3.2) and the
 graded-octree validation rules.
 """
 import os
@@ -320,6 +321,84 @@ def test_shift_by_a_level1_box():
         assert p0.size > 0
         np.testing.assert_allclose(p1, p0, rtol=1e-12)
         np.testing.assert_allclose(a1, a0, rtol=1e-10, atol=1e-11 * np.abs(a0).max())
+
+
+def _errs_vs_direct(h, ps, **kw):
+    phid, ad = oracle.direct(h)
+    out = []
+    for p in ps:
+        phi, a = oracle.solve(h, p, **kw)
+        A = np.concatenate([a[l] for l in h.levels])
+        AD = np.concatenate([ad[l] for l in h.levels])
+        out.append(rel_rms(A, AD))
+    return out
+
+
+def test_bottom_mode_m2l_converges_to_direct_sum():
+    # Bottom mode 1 (the sources of ilist(F) reach the target through F's local
+    # expansion): no region may be dropped or doubled, so the error against the
+    # direct sum falls monotonically with p on a unigrid and on random AMR (with
+    # coarse leaves in the interaction lists, which go through P2L), and is exact
+    # where there is no far field.
+    e = _errs_vs_direct(W.unigrid_plummer(2, seed=5), [4], bottom="m2l")
+    assert e[0] < 1e-14
+    for h, floor in ((W.unigrid_plummer(4), 5e-4), (W.random_amr(3, 5, seed=7), 1e-4)):
+        errs = _errs_vs_direct(h, (2, 4, 6, 8), bottom="m2l")
+        assert all(errs[i] > 1.5 * errs[i + 1] for i in range(3)), errs
+        assert errs[-1] < floor, errs
+
+
+def test_bottom_modes_agree_as_p_grows():
+    # M2P and M2L + L2P truncate differently but converge to the same sum
+    h = W.random_amr(3, 5, seed=13)
+    d = []
+    for p in (2, 4, 6, 8):
+        _, a0 = oracle.solve(h, p)
+        _, a1 = oracle.solve(h, p, bottom="m2l")
+        d.append(rel_rms(np.concatenate([a1[l] for l in h.levels]), np.concatenate([a0[l] for l in h.levels])))
+    assert all(d[i] > 1.5 * d[i + 1] for i in range(3)), d
+    assert d[0] > 1e-4   # the modes are not the same computation
+
+
+def test_bottom_mode_m2l_mirror_symmetry():
+    h = W.random_amr(3, 5, seed=13)
+    m = h.copy()
+    for k, l in enumerate(h.levels):
+        m.ijk[k] = h.ijk[k].copy()
+        m.ijk[k][:, 2] = (1 << l) - 1 - h.ijk[k][:, 2]
+    phi, a = oracle.solve(h, 4, bottom="m2l")
+    phim, am = oracle.solve(m, 4, bottom="m2l")
+    for l in h.levels:
+        if a[l].size == 0:
+            continue
+        tol = 1e-10 * np.abs(a[l]).max()
+        np.testing.assert_allclose(phim[l], phi[l], rtol=1e-12)
+        np.testing.assert_allclose(am[l][:, 2], -a[l][:, 2], rtol=1e-10, atol=tol)
+        np.testing.assert_allclose(am[l][:, :2], a[l][:, :2], rtol=1e-10, atol=tol)
+
+
+def test_multipole_order_drops_exactly_the_higher_multipoles():
+    # Eq. 3 with multipoles up to order p_m only.  On a uniform unigrid every FMM
+    # box is filled symmetrically about its centre, so all its odd moments vanish:
+    # (p, p_m) = (3, 2) and (5, 4) must equal p_m = p exactly, while (4, 3) drops
+    # the non-zero fourth moments and must differ, as must (3, 2) on a Plummer field.
+    h = W.unigrid_plummer(4)
+    u = h.copy()
+    u.mass = [np.full_like(h.mass[0], 1.0 / h.mass[0].size)]
+    for p, pm, same in ((3, 2, True), (5, 4, True), (4, 3, False)):
+        pa, aa = oracle.solve(u, p, p_m=pm)
+        pb, ab = oracle.solve(u, p)
+        if same:
+            assert np.array_equal(aa[4], ab[4]) and np.array_equal(pa[4], pb[4]), (p, pm)
+        else:
+            assert rel_rms(aa[4], ab[4]) > 1e-5, (p, pm)
+    _, a32 = oracle.solve(h, 3, p_m=2)
+    _, a33 = oracle.solve(h, 3)
+    assert rel_rms(a32[4], a33[4]) > 1e-4
+    # and the paper's (p_m, p) = (2, 3) converges to the direct sum like p = 3 does
+    e32 = _errs_vs_direct(h, [3], p_m=2)[0]
+    e2, e3 = _errs_vs_direct(h, [2, 3])
+    assert e3 < e32 < 1.1 * e3 < e2
 
 
 def test_point_mass():
