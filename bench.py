@@ -47,8 +47,20 @@ WORKLOAD = "two-level AMR 64^3 + 32^3 refined block, Plummer a=0.05 + lognormal 
 # MEASURED_PEAKS.json, when present, takes precedence.
 RECORDED_PEAKS = {"hbm_gbs": 6513.0, "bf16_tflops": 1786.0, "bf16_tflops_sustained": 1405.0}
 NC = (P_ORDER + 1) * (P_ORDER + 2) * (P_ORDER + 3) // 6
-# DRAM bytes of one M2P launch (k_gemm_tc) of the headline workload, from ncu
-M2P_TRAFFIC_BYTES = 37_012_992
+# DRAM bytes (read + write) of the stage-timed M2P launch (k_gemm_tc, in-order
+# solve, split-K from the built-in heuristic) of the headline workload, from one
+# ncu capture of that launch shape; None until captured for the current kernel.
+M2P_TRAFFIC_BYTES = None
+# FP32 work per P2P interaction, the usual count for a softened-free gravity
+# pair (3 differences, r^2, rsqrt ~4, m/r, m/r^3, 4 accumulations)
+FLOP_PER_PAIR = 20
+
+
+# FP32 / FP64 / MUFU throughput of the B300s, probed once with
+# register-only FFMA, DFMA and rsqrt chains over 148 x 8 blocks of 256 threads
+# (CUDA events, best of 5); MEASURED_PEAKS.json carries no FP32 figure.
+PROBED_PEAKS = {"ffma_tflops": 70.0, "dfma_tflops": 1.12, "rsqrt_tops": 4.4,
+                "note": "probed FP32 FFMA peak (register-only FFMA chains, 148 x 8 x 256 threads, CUDA events)"}
 
 
 def load_peaks():
@@ -165,6 +177,112 @@ def make_workload(name: str = "two_level"):
     return W.two_level_plummer() if name == "two_level" else W.unigrid_plummer(4)
 
 
+# ---------------------------------------------------------------------------- work counts
+
+_OFF6 = np.array([[x, y, z] for z in range(-2, 4) for y in range(-2, 4) for x in range(-2, 4)], np.int64)
+
+
+def _keys(c, level):
+    c = np.asarray(c, np.int64)
+    return c[..., 0] + (c[..., 1] << level) + (c[..., 2] << (2 * level))
+
+
+class _CellSet:
+    """Membership of level-l cell keys: a dense bitmap up to level 8, else a sorted array."""
+
+    def __init__(self, keys, level):
+        self.dense = level <= 8
+        if self.dense:
+            self.map = np.zeros(1 << (3 * level), bool)
+            self.map[keys] = True
+        else:
+            self.keys = np.sort(keys)
+
+    def test(self, q):
+        """q: keys, -1 where invalid."""
+        if self.dense:
+            return self.map[np.maximum(q, 0)] & (q >= 0)
+        if self.keys.size == 0:
+            return np.zeros(q.shape, bool)
+        i = np.searchsorted(self.keys, q).clip(0, self.keys.size - 1)
+        return self.keys[i] == q
+
+
+def _member(cells, q):
+    return cells.test(q)
+
+
+def work_counts(h, chunk: int = 8192) -> dict:
+    """The method's own interaction counts for the leaf targets of a hierarchy
+    (Fig. 2): M2P (source box, target) pairs of the bottom intermediate field, P2P
+    pairs (level-l leaves of the 3^3 neighbour octs, coarse leaves once each, and
+    the coarse leaves of the interaction list), nearest-field children, and
+    near-field M2P pairs.  Bookkeeping for the roofline, on the host."""
+    lv = list(h.levels)
+    leaves, refined = {}, {}
+    for k, l in enumerate(lv):
+        leaves[l] = np.sort(_keys(h.ijk[k], l))
+    cells_next = None
+    for l in range(h.lmax, 0, -1):  # refined cells: parents of the next level's cells
+        if cells_next is None:
+            refined[l] = np.zeros(0, np.int64)
+        else:
+            refined[l] = np.unique(_keys(cells_next >> 1, l))
+        k = l - h.lmin
+        mine = h.ijk[k].astype(np.int64) if 0 <= k < len(lv) else np.zeros((0, 3), np.int64)
+        ref_cells = np.stack([refined[l] & ((1 << l) - 1), (refined[l] >> l) & ((1 << l) - 1),
+                              refined[l] >> (2 * l)], 1) if refined[l].size else np.zeros((0, 3), np.int64)
+        cells_next = np.concatenate([mine, ref_cells]) if (mine.size or ref_cells.size) else None
+    for l in range(0, h.lmin):
+        leaves[l] = np.zeros(0, np.int64)
+    # octs (keyed by their parent cell) holding a refined cell, per level
+    m2p_rows = {l: np.unique(np.stack([v & ((1 << l) - 1), (v >> l) & ((1 << l) - 1), v >> (2 * l)], 1) >> 1,
+                             axis=0).shape[0] if v.size else 0 for l, v in refined.items()}
+    leaves = {l: _CellSet(v, l) for l, v in leaves.items()}
+    refined = {l: _CellSet(v, l) for l, v in refined.items()}
+    empty = _CellSet(np.zeros(0, np.int64), 0)
+    out = {"targets": 0, "m2p_pairs": 0, "p2p_pairs": 0, "nearest_pairs": 0, "near_m2p_pairs": 0,
+           "m2p_rows": m2p_rows}
+    child = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], np.int64)
+    for k, l in enumerate(lv):
+        T = h.ijk[k].astype(np.int64)
+        out["targets"] += T.shape[0]
+        n_up = 1 << (l - 1)
+        # everything but the self term and the touching test depends on the parent
+        # box F only: count per F, weighted by its number of targets
+        fk, inv, n_t = np.unique(_keys(T >> 1, l - 1), return_inverse=True, return_counts=True)
+        Fs = np.stack([fk & (n_up - 1), (fk >> (l - 1)) & (n_up - 1), fk >> (2 * (l - 1))], 1)
+        tmask = np.zeros((fk.size, 8), bool)  # which children of F are targets
+        tmask[inv.reshape(-1), (T[:, 0] & 1) | ((T[:, 1] & 1) << 1) | ((T[:, 2] & 1) << 2)] = True
+        for i0 in range(0, fk.size, chunk):
+            F = Fs[i0:i0 + chunk]
+            nt = n_t[i0:i0 + chunk]
+            # bottom intermediate field: interaction list of F at level l-1
+            S = 2 * (F >> 1)[:, None, :] + _OFF6[None]
+            ok = ((S >= 0) & (S < n_up)).all(-1) & (np.abs(S - F[:, None, :]).max(-1) > 1)
+            sk = np.where(ok, _keys(np.clip(S, 0, n_up - 1), l - 1), -1)
+            out["m2p_pairs"] += int((nt * _member(refined[l - 1], sk).sum(1)).sum())
+            out["p2p_pairs"] += int((nt * _member(leaves.get(l - 1, empty), sk).sum(1)).sum())
+            # near field: the level-l positions of F's 3^3 neighbour octs
+            P = 2 * F[:, None, :] + _OFF6[None]
+            inb = ((P >= 0) & (P < (1 << l))).all(-1)
+            pk = np.where(inb, _keys(np.clip(P, 0, (1 << l) - 1), l), -1)
+            n_leaf = _member(leaves[l], pk).sum(1)
+            nk = np.where(inb, _keys(np.clip(P >> 1, 0, n_up - 1), l - 1), -1)
+            n_coarse = _member(leaves.get(l - 1, empty), nk).sum(1) // 8
+            out["p2p_pairs"] += int((nt * (n_leaf - 1 + n_coarse)).sum())  # every target skips itself
+            is_ref = _member(refined[l], pk)
+            iface = np.where(is_ref.any(1))[0]
+            if iface.size:  # touching refined cells: nearest field; the others: near-field M2P
+                t = 2 * F[iface][:, None, :] + child[None]                      # [f, 8, 3]
+                touch = np.abs(P[iface][:, None, :, :] - t[:, :, None, :]).max(-1) <= 1  # [f, 8, 216]
+                rt = (touch & is_ref[iface][:, None, :]).sum(-1)                 # [f, 8]
+                tm = tmask[i0:i0 + chunk][iface]
+                out["nearest_pairs"] += 8 * int((rt * tm).sum())
+                out["near_m2p_pairs"] += int(((is_ref[iface].sum(1)[:, None] - rt) * tm).sum())
+    return out
+
+
 def rel_rms(a: dict, b: dict) -> float:
     num = sum(float(((a[l] - b[l]) ** 2).sum()) for l in b)
     den = sum(float((b[l] ** 2).sum()) for l in b)
@@ -231,7 +349,7 @@ def gpu_arm(args, rank, world, local):
         return s, out
 
     mixed, out_m = make("mixed")
-    fp64, out_d = make("fp64")
+    fp64, out_d = make("fp64") if not args.quick else (None, None)
 
     def step_mixed():
         mixed.set_levels(h.lmin, h.lmax, ijk, mass)
@@ -245,17 +363,19 @@ def gpu_arm(args, rank, world, local):
         fp64.solve(out=out_d)
 
     # accuracy of the mixed path against the FP64 GPU path (which matches the oracle to 1e-10)
-    step_mixed()
-    step_fp64()
-    torch.cuda.synchronize()
-    mixed.sync()
-    fp64.sync()
-    am = {l: out_m[1][l].cpu().numpy() for l in h.levels}
-    ad = {l: out_d[1][l].cpu().numpy() for l in h.levels}
-    pm = {l: out_m[0][l].cpu().numpy() for l in h.levels}
-    pd = {l: out_d[0][l].cpu().numpy() for l in h.levels}
-    err_acc = rel_rms(am, ad)
-    err_phi = rel_rms(pm, pd)
+    err_acc = err_phi = None
+    if fp64 is not None:
+        step_mixed()
+        step_fp64()
+        torch.cuda.synchronize()
+        mixed.sync()
+        fp64.sync()
+        am = {l: out_m[1][l].cpu().numpy() for l in h.levels}
+        ad = {l: out_d[1][l].cpu().numpy() for l in h.levels}
+        pm = {l: out_m[0][l].cpu().numpy() for l in h.levels}
+        pd = {l: out_d[0][l].cpu().numpy() for l in h.levels}
+        err_acc = rel_rms(am, ad)
+        err_phi = rel_rms(pm, pd)
 
     barrier(dist)
     launches0 = mixed.stats()["launches"]
@@ -269,9 +389,10 @@ def gpu_arm(args, rank, world, local):
     t_solve = timed_after(torch, lambda: mixed.update_masses(mass), step_mixed_solve_only,
                           args.steps, 3, stream, flush)
     k64 = max(3, min(args.steps, 5))
-    t_fp64 = timed_steps(torch, step_fp64, k64, 3, stream, flush)
+    t_fp64 = timed_steps(torch, step_fp64, k64, 3, stream, flush) if fp64 is not None else [float("nan")]
     mixed.sync()
-    fp64.sync()
+    if fp64 is not None:
+        fp64.sync()
     barrier(dist)
 
     ms_mixed = reduce_max(statistics.mean(t_mixed), dist, dev)
@@ -282,7 +403,7 @@ def gpu_arm(args, rank, world, local):
 
     # per-stage device times of the solve (events inside the library, on this stream)
     mixed.set_timing(True)
-    stage = {k: 0.0 for k in ("upward", "downward", "m2p", "near")}
+    stage = {k: 0.0 for k in ("upward", "downward", "m2p", "near_m2p", "near")}
     reps = max(3, args.steps)
     for _ in range(reps):
         flush.zero_()
@@ -307,31 +428,14 @@ def gpu_arm(args, rank, world, local):
         e2e_solver.set_levels(h.lmin, h.lmax, np_ijk, np_mass)
         e2e_solver.solve(out=np_out)
 
-    t_e2e = timed_steps(torch, step_e2e, args.steps, 3, stream, flush)
+    t_e2e = timed_steps(torch, step_e2e, args.steps if not args.quick else 3, 3, stream, flush)
     e2e_solver.sync()
     ms_e2e = reduce_max(statistics.mean(t_e2e), dist, dev)
     h2d = sum(a.nbytes for a in np_ijk) + sum(m.nbytes for m in np_mass)
     d2h = sum(v.nbytes for v in np_out[0].values()) + sum(v.nbytes for v in np_out[1].values())
 
     peaks, peak_src = load_peaks()
-    n_tgt = n_cells
-    m2p_useful = 2.0 * 189 * 4 * NC * n_tgt                       # per solve (all target levels)
-    rows = sum(int(mixed.tree_counts()[l - 1]) for l in h.levels)  # upper bound on M2P rows
-    roofline = {
-        "kernel": "k_gemm_tc (bottom M2P, split-BF16 x3 on tcgen05)",
-        "bound": "tensor",
-        "achieved": m2p_useful / (stage["m2p"] * 1e-3) / 1e12,
-        "peak": peaks["bf16_tflops_sustained"] / 3.0,
-        "unit": "TFLOP/s",
-        "traffic": M2P_TRAFFIC_BYTES,
-        "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one M2P launch of this workload "
-                        "(ncu, profiles/k_gemm_tc_two_level_64c_32c_p6.md: the forked launch, split-K 3; the "
-                        "stage time is the in-order launch, split-K 4, same kernel and operands); algorithmic ~38 MB",
-        "peak_note": f"{peak_src} bf16 dense sustained / 3 (three bf16 products per split-BF16 product); "
-                     "achieved counts useful flops 2*189*4*ncoef per target cell",
-        "stage_ms": stage["m2p"],
-    }
-    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    roofline, kernels = rooflines(h, stage, peaks, peak_src)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -349,10 +453,11 @@ def gpu_arm(args, rank, world, local):
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
         "gpu_launches": int(launches1 - launches0),
         "roofline": roofline,
+        "kernels": kernels,
         "clocks": clocks,
     }
     del mixed, fp64, e2e_solver
-    legs = [x for x in args.legs.split(",") if x and x != "none"]
+    legs = [x for x in args.legs.split(",") if x and x != "none"] if not args.quick else []
     for name in legs:
         fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats}.get(name)
         if fn is None:
@@ -362,12 +467,88 @@ def gpu_arm(args, rank, world, local):
         except Exception as e:  # an extra workload never hides the headline
             line[name] = {"error": f"{type(e).__name__}: {e}"}
         torch.cuda.empty_cache()
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and not args.quick:
         line["cpu_baseline"] = cpu_baseline(h, per_level=args.cpu_sample)
     if rank == 0:
         print(json.dumps(line))
     barrier(dist)
-    del rows
+
+
+def rooflines(h, stage, peaks, peak_src):
+    """Roofline of the dominant kernel (the bottom M2P contraction) and of the
+    other stages, from the method's own work on this hierarchy (work_counts) and
+    the per-stage CUDA-event times of an in-order solve."""
+    w = work_counts(h)
+    kq = 8 * NC
+    # M2P row tiles: per target level l, 128-row tiles over the octs of level l-1
+    # holding a refined cell
+    issued_mac = sum(-(-w["m2p_rows"][l - 1] // 128) * 128 for l in h.levels if h.n(l)) * 26 * kq * 256 * 3
+    useful = 2.0 * 4 * NC * w["m2p_pairs"]
+    t = stage["m2p"] * 1e-3
+    peak = peaks["bf16_tflops"] / 3.0
+    roof = {
+        "kernel": "k_gemm_tc (bottom M2P, split-BF16 x3 on tcgen05)",
+        "bound": "tensor",
+        "achieved": useful / t / 1e12,
+        "peak": peak,
+        "unit": "TFLOP/s",
+        "frac": useful / t / 1e12 / peak,
+        "traffic": M2P_TRAFFIC_BYTES,
+        "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of the stage-timed M2P launch of this "
+                        "workload, one ncu capture (null until captured for this kernel); algorithmic: the "
+                        "operator hi+lo (17.9 MB), the gathered multipole rows and the accumulator",
+        "peak_note": f"{peak_src} bf16 dense burst / 3 (three bf16 products per split-BF16 product; the kernel is "
+                     "timed alone by stage events); useful flops = 2 * 4 * ncoef per (source box, target) pair "
+                     f"of the method, {w['m2p_pairs']} pairs = {w['m2p_pairs'] / w['targets']:.1f} sources per target",
+        "issued_bf16_tflops": 2.0 * issued_mac / t / 1e12,
+        "issued_note": "MACs the contraction issues: 128-row tiles x 26 offsets x 8 ncoef x 256 columns x 3 "
+                       "products (dense blocks, zero near-neighbour blocks included)",
+        "stage_ms": stage["m2p"],
+    }
+    kern = {"work": w, "flop_per_pair": FLOP_PER_PAIR}
+    fp32 = PROBED_PEAKS["ffma_tflops"]
+    p2p = w["p2p_pairs"] + w["nearest_pairs"]
+    if stage.get("near"):
+        fl = FLOP_PER_PAIR * p2p + 2.0 * 4 * NC * w["targets"]   # P2P + nearest + L2P
+        kern["near"] = {"kernel": "k_near (P2P, nearest field, L2P, scatter)", "bound": "fp32",
+                        "achieved_tflops": fl / (stage["near"] * 1e-3) / 1e12, "peak_tflops": fp32,
+                        "frac": fl / (stage["near"] * 1e-3) / 1e12 / fp32, "ms": stage["near"],
+                        "peak_note": PROBED_PEAKS["note"]}
+    if stage.get("near_m2p"):
+        fl = 2.0 * 4 * NC * w["near_m2p_pairs"]
+        kern["near_m2p"] = {"kernel": "k_near_m2p", "bound": "fp32", "achieved_tflops": fl / (stage["near_m2p"] * 1e-3) / 1e12,
+                            "peak_tflops": fp32, "frac": fl / (stage["near_m2p"] * 1e-3) / 1e12 / fp32,
+                            "ms": stage["near_m2p"]}
+    if stage.get("upward"):
+        # algorithmic bytes of P2M + M2M: each leaf mass read once (8 B), each cell's
+        # total mass written (4 B), each refined cell's multipole row written once in
+        # FP32 + bf16 hi + lo (8 B per coefficient) and read once by its parent (4 B)
+        n_leaf = sum(h.n(l) for l in h.levels)
+        n_ref = sum(np.unique(_keys(h.ijk[k].astype(np.int64) >> 1, l - 1)).size for k, l in enumerate(h.levels))
+        nbytes = 12 * n_leaf + 4 * n_ref + 12 * NC * n_ref
+        kern["upward"] = {"kernels": "k_leaf_mono, k_leaf_rows, k_m2m, k_m2m_block", "bound": "hbm",
+                          "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (stage["upward"] * 1e-3) / 1e9,
+                          "peak_gbs": peaks["hbm_gbs"], "frac": nbytes / (stage["upward"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                          "ms": stage["upward"]}
+    return roof, kern
+
+
+def profile_solves(args):
+    """In-order, stage-timed solves of the headline hierarchy, for ncu: each solve
+    launches k_gemm_tc twice (M2L of every box level, then the bottom M2P)."""
+    import torch
+    from paper_2607_19489_b300 import fmm
+    h = make_workload(args.workload)
+    s = fmm.Solver(P_ORDER, "mixed")
+    s.set_hierarchy(h)
+    out = s.alloc_outputs()
+    s.set_timing(True)
+    for _ in range(args.profile_solves):
+        s.update_masses([torch.as_tensor(m, device="cuda") for m in h.mass])
+        s.solve(out=out)
+        s.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solves": args.profile_solves, "stages_ms": s.stage_times()}))
 
 
 # ---------------------------------------------------------------------------- extra workloads
@@ -622,12 +803,20 @@ def main():
                     help="adjoint leg: central finite differences on this many seeded cells (2 FP64 solves each)")
     ap.add_argument("--legs", default="batched,adjoint,ats",
                     help="extra workloads reported beside the headline (comma list, or 'none')")
+    ap.add_argument("--quick", action="store_true",
+                    help="the mixed headline and its stage times only (no FP64 arm, e2e, legs or CPU baseline)")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="for profilers: set the headline hierarchy, then run this many in-order, stage-timed mixed "
+                         "solves (the launch shapes the roofline times) and exit without a JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.profile_solves:
+        profile_solves(args)
         return
     gpu_arm(args, rank, world, local)
 

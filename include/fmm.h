@@ -279,12 +279,13 @@ fmm_status fmm_stats(const fmm_ctx* ctx, int64_t* out4);
 fmm_status fmm_set_graphs(fmm_ctx* ctx, int on);
 
 /* Per-stage device times (ms) of the last solve when timing is enabled with
- * fmm_set_timing(ctx, 1): upward, downward, m2p (the bottom M2P contraction),
- * near (near-field M2P, P2P, L2P, scatter) (4 doubles).  With timing on the
- * stages run one after the other on one stream; otherwise the bottom M2P runs
- * beside the downward pass. */
+ * fmm_set_timing(ctx, 1), 5 doubles: upward (P2M, M2M), downward (M2L, L2L),
+ * m2p (the bottom M2P contraction; 0 in bottom mode 1), near-field M2P, near
+ * field (P2P, nearest field, L2P, scatter).  With timing on the stages run one
+ * after the other on one stream; otherwise the bottom M2P runs beside the
+ * downward pass. */
 fmm_status fmm_set_timing(fmm_ctx* ctx, int on);
-fmm_status fmm_stage_times(const fmm_ctx* ctx, double* ms4);
+fmm_status fmm_stage_times(const fmm_ctx* ctx, double* ms5);
 
 #ifdef __cplusplus
 }

@@ -286,7 +286,7 @@ fmm_status size_expansions(Ctx* c, cudaStream_t st) {
 fmm_status size_locals(Ctx* c, cudaStream_t st) {
   const int nc = c->tab.nc;
   const bool f64 = c->cfg.precision == FMM_FP64;
-  for (int l = 2; l <= c->lmax - 2; ++l) {
+  for (int l = 2; l <= top_local_level(c); ++l) {
     LevelTree& T = c->lev[l];
     const int64_t nrow = 8 * std::max<int64_t>(T.n_rowsL, 1);
     CKS(buf_ensure(c, T.L, nrow * nc * 8));
@@ -536,7 +536,7 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_use
   if (cfg->bottom_mode != FMM_BOTTOM_M2P && cfg->bottom_mode != FMM_BOTTOM_M2L_L2P) return FMM_ERR_ARG;
   if (cfg->mass_fp32 != 0 && cfg->mass_fp32 != 1) return FMM_ERR_ARG;
   if (!std::isfinite(cfg->G)) return FMM_ERR_ARG;
-  if (cfg->precision == FMM_MIXED_TF32 || cfg->bottom_mode != FMM_BOTTOM_M2P) return FMM_ERR_ARG;  // not built yet
+  if (cfg->precision == FMM_MIXED_TF32) return FMM_ERR_ARG;  // not built yet
   fmm_ctx* c = new fmm_ctx();
   c->cfg = *cfg;
   if (c->cfg.p_m == c->cfg.p) c->cfg.p_m = 0;  // one key for the full order
@@ -769,21 +769,24 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
       launch_upward(c, b, st, (const int32_t*)c->lev[b + 1].anc.ptr, c->lev[b + 1].n_anc);
   }
   stage_event(c, 1, st);
-  // 2. downward over box levels 2..lmax-2: L = L2L(parent) + M2L.  For targets
-  // at levels >= lo > lmin, the levels b <= lo-3 only feed the L2L chain of the
-  // ancestors of level lo: their ancestor lists replace the full row lists.
+  // 2. downward over box levels 2..top (top = lmax-2, or lmax-1 in bottom mode
+  // 1): L = L2L(parent) + M2L.  For targets at levels >= lo > lmin, the levels
+  // b <= lo-3 (lo-2 in mode 1) only feed the L2L chain of the ancestors of
+  // level lo: their ancestor lists replace the full row lists.
+  const int m1 = c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P;
+  const int top = top_local_level(c);
   const bool restrict_dn = lo > lmin && c->anc_d == lo;
   std::vector<const int32_t*> drows(lmax + 1, nullptr);
   std::vector<int64_t> dn(lmax + 1, 0);
-  for (int b = 2; b <= lmax - 2; ++b)
-    if (restrict_dn && b <= lo - 3) {
+  for (int b = 2; b <= top; ++b)
+    if (restrict_dn && b <= lo - 3 + m1) {
       drows[b] = (const int32_t*)c->lev[b].anc.ptr;
       dn[b] = c->lev[b].n_anc;
     }
   std::vector<int> dl;  // box levels with M2L rows
   std::vector<const int32_t*> dr;
   std::vector<int64_t> dnr;
-  for (int b = 2; b <= lmax - 2; ++b) {
+  for (int b = 2; b <= top; ++b) {
     if (drows[b] && !dn[b]) continue;
     dl.push_back(b);
     dr.push_back(drows[b]);
@@ -799,8 +802,10 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
       if (f64) launch_gemm_f64(c, c->op_m2l, kModeM2L, dl[i], s2, dr[i], dnr[i]);
     }
   };
-  // 3a. bottom intermediate field: M2P from level l-1 cells
+  // 3a. bottom intermediate field: M2P from level l-1 cells (bottom mode 1: in
+  // the local expansions already)
   auto m2p = [&](cudaStream_t s2, int sm_budget) {
+    if (m1) return;
     std::vector<int> lv;
     for (int l = lo; l <= lmax; ++l) {
       if (!c->lev[l].n_leaf) continue;
@@ -835,12 +840,13 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
     l2l_chain(st);
     stage_event(c, 2, st);
     m2p(st, 0);
-    stage_event(c, 3, st);  // the near-field stage starts here
+    stage_event(c, 3, st);
     launch_near_m2p(c, lo, st);
+    stage_event(c, 4, st);
   }
   // 3b. near / nearest / far fields and the scatter, all target levels in one launch
   launch_near(c, lo, dphi + lo, dacc + lo, c->cfg.out_fp32, st);
-  stage_event(c, 4, st);
+  stage_event(c, 5, st);
   return FMM_OK;
 }
 
@@ -1140,7 +1146,7 @@ fmm_status fmm_autotune(fmm_ctx* c, int lo, void* stream) {
   };
   if (c->cfg.precision != FMM_FP64) {
     const std::vector<int> splits = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24};
-    tune(&c->tune_split[0], splits);
+    if (c->cfg.bottom_mode == FMM_BOTTOM_M2P) tune(&c->tune_split[0], splits);  // mode 1 runs no M2P
     tune(&c->tune_split[1], splits);
     tune(&c->tune_opb, {16, 8, 4});
   } else {
@@ -1184,6 +1190,10 @@ fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const
   }
   if (c->cfg.precision != FMM_FP64) {
     c->last_error = "fmm_solve_adjoint needs an FMM_FP64 context";
+    return FMM_ERR_ARG;
+  }
+  if (c->cfg.bottom_mode != FMM_BOTTOM_M2P) {
+    c->last_error = "fmm_solve_adjoint: the transposed chain follows the paper's bottom M2P only";
     return FMM_ERR_ARG;
   }
   if (lo < c->lmin || lo > c->lmax_user) return FMM_ERR_ARG;
@@ -1277,7 +1287,7 @@ fmm_status fmm_sync(fmm_ctx* c) {
   unsigned e = 0;
   CKS(cudaMemcpy(&e, c->d_err, 4, cudaMemcpyDeviceToHost));
   if (c->timing) {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
       float ms = 0;
       cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
       c->stage_ms[i] = ms;
@@ -1291,7 +1301,7 @@ fmm_status fmm_sync(fmm_ctx* c) {
     if (c->have_levels) {
       for (int l = c->lmin; l <= c->lmax; ++l)
         if (c->lev[l].acc.ptr) cudaMemset(c->lev[l].acc.ptr, 0, c->lev[l].acc.bytes);
-      for (int l = 2; l <= c->lmax - 2; ++l)
+      for (int l = 2; l <= top_local_level(c); ++l)
         if (c->lev[l].Lm.ptr) cudaMemset(c->lev[l].Lm.ptr, 0, c->lev[l].Lm.bytes);
       c->dirty_lo = c->lmin;
     }
@@ -1421,9 +1431,9 @@ fmm_status fmm_set_timing(fmm_ctx* c, int on) {
   return FMM_OK;
 }
 
-fmm_status fmm_stage_times(const fmm_ctx* c, double* ms4) {
-  if (!c || !ms4) return FMM_ERR_ARG;
-  for (int i = 0; i < 4; ++i) ms4[i] = c->stage_ms[i];
+fmm_status fmm_stage_times(const fmm_ctx* c, double* ms5) {
+  if (!c || !ms5) return FMM_ERR_ARG;
+  for (int i = 0; i < 5; ++i) ms5[i] = c->stage_ms[i];
   return FMM_OK;
 }
 

@@ -108,7 +108,8 @@ struct LevelTree {
                          // refined cells and of the leaves in interface octs (irows)
   DevBuf Mhi, Mlo;       // bf16 [8 n_oct][nc] (mixed path GEMM operands)
   DevBuf mono;           // [8 n_oct] total mass per cell (double or float)
-  DevBuf L;              // double [8 n_rowsL][nc] local expansions (levels 2..lmax-2), by slot
+  DevBuf L;              // double [8 n_rowsL][nc] local expansions (levels 2..lmax-2, or
+                         // 2..lmax-1 in bottom mode 1), by slot
   DevBuf Lf;             // float [8 n_rowsL][nc] FP32 copy of L read by the mixed near field
   DevBuf Lm;             // float [8 n_rowsL][nc] this level's M2L sum (mixed path), by slot;
                          // zero between solves (the L2L step clears what it consumes)
@@ -161,8 +162,8 @@ struct Ctx {
   int device = 0;
   int num_sms = 148;
   bool timing = false;
-  cudaEvent_t ev[5] = {};
-  double stage_ms[4] = {0, 0, 0, 0};
+  cudaEvent_t ev[6] = {};
+  double stage_ms[5] = {0, 0, 0, 0, 0};  // upward, downward, m2p, near-field M2P, near field
   bool tables_on_device = false;
   int64_t n_launch = 0, n_cub = 0, n_solve = 0, n_set = 0;
   // CUDA graphs of fmm_solve's device work, keyed by (layout generation, lo,
@@ -243,5 +244,11 @@ void launch_adjoint(Ctx* c, int lo, const void* const* g_phi, const void* const*
                     cudaStream_t st);
 
 enum { kModeM2P = 0, kModeM2L = 1 };
+
+// Highest box level holding local expansions: lmax-2 (the paper's bottom
+// M2P), lmax-1 with bottom mode 1 (M2L into the parent box, then L2P).
+inline int top_local_level(const Ctx* c) {
+  return c->lmax - 2 + (c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P ? 1 : 0);
+}
 
 }  // namespace fmm

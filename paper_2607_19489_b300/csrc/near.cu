@@ -21,8 +21,8 @@
 // entries, which only occur next to coarse-fine interfaces; the 27 rounds of
 // source loads are independent, so they are issued back to back.  The P2P
 // loop is then branch-free except for the self term.  The local expansion of
-// the oct's level l-2 box is staged too and evaluated directly,
-// phi = sum_beta L_beta rho^beta / beta!.
+// the oct's level l-2 box (bottom mode 1: of its parent box, level l-1) is
+// staged too and evaluated directly, phi = sum_beta L_beta rho^beta / beta!.
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -91,8 +91,9 @@ struct NearSeg {
   const void* mono_l;         // level l
   const void* mono_dn;        // level l+1
   const void* M_l;            // multipoles of level l cells
-  const void* L2;             // local expansions of level l-2 (or null), by slot, in T
-  const int32_t* slot2;       // local-expansion slot of each level l-2 oct
+  const void* L2;             // local expansions of level l-2 (bottom mode 1: l-1), or null,
+                              // by slot, in T
+  const int32_t* slot2;       // local-expansion slot of each oct of that level
   void* acc;                  // M2P results for level l cells [cells][4]; cleared after reading
   void* phi;
   void* accel;
@@ -106,6 +107,7 @@ struct NearSeg {
 struct NearParams {
   NearSeg seg[kMaxNearSeg];
   int nseg, nc, p, out_fp32;
+  int bottom1;                // bottom mode 1: far field from the parent box (level l-1)
   const void* nearop;         // [343][nc][4]
   double G;
 };
@@ -158,7 +160,9 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
       s_m[g][s] = m;
     }
     if (S.L2) {
-      const int32_t G2 = S.par_up[S.par_l[o] >> 3];
+      // the box whose expansion the oct's cells evaluate: their grandparent cell
+      // (level l-2), or in bottom mode 1 their parent cell F (level l-1)
+      const int32_t G2 = P.bottom1 ? S.par_l[o] : S.par_up[S.par_l[o] >> 3];
       const int64_t sl = (int64_t)S.slot2[G2 >> 3] * 8 + (G2 & 7);
       for (int b = tp; b < P.nc; b += 8) s_L[g][b] = ((const T*)S.L2)[sl * P.nc + b];
     }
@@ -245,11 +249,13 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
   T pl = 0, xl = 0, yl = 0, zl = 0;
   if (S.L2) {
     // phi = sum_beta L_beta rho^beta / beta!, grad_i = sum_gamma L_{gamma+e_i} rho^gamma / gamma!,
-    // rho = target - box centre in units of the level l-2 box
-    const int fpos = S.par_l[o] & 7;
-    const T rx = (T)(2 * (fpos & 1) + tbx) * (T)0.25 - (T)0.375;
-    const T ry = (T)(2 * ((fpos >> 1) & 1) + tby) * (T)0.25 - (T)0.375;
-    const T rz = (T)(2 * ((fpos >> 2) & 1) + tbz) * (T)0.25 - (T)0.375;
+    // rho = target - box centre in units of the level l-2 box (mode 1: of the
+    // level l-1 box, where the target sits at +-1/4)
+    const int fpos = P.bottom1 ? 0 : (S.par_l[o] & 7);
+    const T q = P.bottom1 ? (T)0.5 : (T)0.25, q0 = P.bottom1 ? (T)0.25 : (T)0.375;
+    const T rx = (T)(2 * (fpos & 1) + tbx) * q - q0;
+    const T ry = (T)(2 * ((fpos >> 1) & 1) + tby) * q - q0;
+    const T rz = (T)(2 * ((fpos >> 2) & 1) + tbz) * q - q0;
     // s_L indexed directly (a plain pointer into it compiles to generic loads)
     if constexpr (PC > 0) {
       T xa = 1;
@@ -295,7 +301,9 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     }
     }
   }
-  // level-l units: the M2P sum is in level l-1 units, the local expansion in level l-2 units
+  // level-l units: the M2P sum is in level l-1 units, the local expansion in level l-2
+  // units (mode 1: l-1)
+  const T fl1 = P.bottom1 ? (T)0.5 : (T)0.25, fl2 = P.bottom1 ? (T)0.25 : (T)0.0625;
   T s1, s2;
   if constexpr (sizeof(T) == 4) {
     s1 = S.s1f;
@@ -304,10 +312,10 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     s1 = S.s1;
     s2 = S.s2;
   }
-  const T ph = s1 * (phi + (T)0.5 * pm + (T)0.25 * pl);
-  const T gx = s2 * (ax + (T)0.25 * xm + (T)0.0625 * xl);
-  const T gy = s2 * (ay + (T)0.25 * ym + (T)0.0625 * yl);
-  const T gz = s2 * (az + (T)0.25 * zm + (T)0.0625 * zl);
+  const T ph = s1 * (phi + (T)0.5 * pm + fl1 * pl);
+  const T gx = s2 * (ax + (T)0.25 * xm + fl2 * xl);
+  const T gy = s2 * (ay + (T)0.25 * ym + fl2 * yl);
+  const T gz = s2 * (az + (T)0.25 * zm + fl2 * zl);
   const int64_t li = -1 - (int64_t)self;
   if (P.out_fp32) {
     ((float*)S.phi)[li] = (float)ph;
@@ -515,6 +523,8 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
     P.out_fp32 = out_fp32;
     P.nearop = f64 ? c->d_near64.ptr : c->d_near32.ptr;
     P.G = c->cfg.G;
+    P.bottom1 = c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P;
+    const int dl = P.bottom1 ? 1 : 2;  // level difference to the box of the far field
     int blocks = 0;
     for (; l <= c->lmax && P.nseg < kMaxNearSeg; ++l) {
       LevelTree& T = c->lev[l];
@@ -530,8 +540,8 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
       S.mono_dn = (l < c->lmax) ? c->lev[l + 1].mono.ptr : nullptr;
       S.M_l = T.M.ptr;
       S.M_l_f64 = T.m_is_f64 ? 1 : 0;
-      S.L2 = (l - 2 >= 2) ? (f64 ? c->lev[l - 2].L.ptr : c->lev[l - 2].Lf.ptr) : nullptr;
-      S.slot2 = (l - 2 >= 2) ? (const int32_t*)c->lev[l - 2].slotL.ptr : nullptr;
+      S.L2 = (l - dl >= 2) ? (f64 ? c->lev[l - dl].L.ptr : c->lev[l - dl].Lf.ptr) : nullptr;
+      S.slot2 = (l - dl >= 2) ? (const int32_t*)c->lev[l - dl].slotL.ptr : nullptr;
       S.acc = T.acc.ptr;
       S.phi = phi[l - lo];
       S.accel = accel[l - lo];

@@ -246,7 +246,9 @@ __global__ void k_nbr(int level, int64_t n_oct, int64_t n_oct_up, const int32_t*
 //   rows  (bit 0): the oct holds a refined cell (its M2M output / M2P row);
 //   tgt   (bit 1): the oct holds a leaf (a target oct);
 //   rowsL (bit 2): a cell of the oct has grandchildren (it needs a local
-//                  expansion), levels 1..lmax-2;
+//                  expansion), levels 1..lmax-2; in bottom mode 1 (M2L + L2P)
+//                  a cell of the oct is refined (its children evaluate its local
+//                  expansion), levels 1..lmax-1;
 //   irows (bit 3): the oct holds a leaf and one of its 3^3 neighbour octs holds
 //                  a refined cell (near-field M2P / nearest field), levels
 //                  lmin..lmax.
@@ -266,6 +268,7 @@ struct ListLevel {
   const uint8_t* leafmask_next;  // level + 1 (or null)
   int32_t* slotL;    // [n_oct]: position in rowsL or -1
   int want_rowsL, want_irows;
+  int rowsL_refined;  // bottom mode 1: rowsL holds the octs with a refined cell
 };
 
 struct ListParams {
@@ -296,7 +299,8 @@ __device__ __forceinline__ unsigned oct_list_flags(const ListLevel& L, int64_t o
   const unsigned mask = L.leafmask[o];
   const int leaf = mask != 0, refined = mask != 0xFFu;
   int grand = 0;
-  if (L.want_rowsL && refined)
+  if (L.want_rowsL && refined && L.rowsL_refined) grand = 1;
+  if (L.want_rowsL && refined && !L.rowsL_refined)
     for (int c = 0; c < 8 && !grand; ++c) {
       const int32_t ch = L.cell_child[o * 8 + c];
       if (ch >= 0 && ch < L.n_oct_next) grand |= L.leafmask_next[ch] != 0xFFu;
@@ -628,6 +632,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
   }
   // ---- row lists (a partial build changes the lists of levels lo-1..lmax only) ----
   const int list0 = partial ? lo - 1 : 1;
+  const int m1 = c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P;  // local expansions down to level lmax-1
   {
     const int stride = lmax + 2;
     ListParams P{};
@@ -651,7 +656,8 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
       L.leafmask = (uint8_t*)T.leafmask.ptr;
       L.leafmask_next = l < lmax ? (const uint8_t*)c->lev[l + 1].leafmask.ptr : nullptr;
       L.slotL = (int32_t*)T.slotL.ptr;
-      L.want_rowsL = l + 2 <= lmax;
+      L.want_rowsL = l + 2 - m1 <= lmax;
+      L.rowsL_refined = m1;
       L.want_irows = l >= lmin;
       nb += (T.n_oct + kListBlock - 1) / kListBlock;
     }
@@ -716,12 +722,13 @@ fmm_status tree_finish(Ctx* c, cudaStream_t st) {
     }
   }
   const int list0 = c->tree_lo > lmin ? c->tree_lo - 1 : 1;  // the levels whose lists were rebuilt
+  const int m1 = c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P;
   for (int l = 1; l <= lmax; ++l) {
     LevelTree& T = c->lev[l];
     if (l >= list0) {
       T.n_rows = counts[0 * stride + l];
       T.n_tgt = counts[1 * stride + l];
-      T.n_rowsL = (l + 2 <= lmax) ? counts[2 * stride + l] : 0;
+      T.n_rowsL = (l + 2 - m1 <= lmax) ? counts[2 * stride + l] : 0;
       T.n_irows = (l >= lmin) ? counts[3 * stride + l] : 0;
     }
     T.n_anc = (l < c->anc_req) ? counts[4 * stride + l] : 0;

@@ -314,9 +314,9 @@ class Solver:
         self._check(lib().fmm_set_graphs(self._h, int(on)), "fmm_set_graphs")
 
     def stage_times(self):
-        out = np.zeros(4)
+        out = np.zeros(5)
         self._check(lib().fmm_stage_times(self._h, out.ctypes.data), "fmm_stage_times")
-        return dict(zip(["upward", "downward", "m2p", "near"], out.tolist()))
+        return dict(zip(["upward", "downward", "m2p", "near_m2p", "near"], out.tolist()))
 
     def solve_unigrid_static(self, level: int, ijk, mass, phi, accel, stream=None):
         """Unigrid solve (level 2..4) that allocates no device memory; all arguments are

@@ -23,10 +23,10 @@ def _torch():
     return torch
 
 
-def run(h, p, precision, lo=None, out_fp32=False, sel=None):
+def run(h, p, precision, lo=None, out_fp32=False, sel=None, **kw):
     from paper_2607_19489_b300 import fmm
     torch = _torch()
-    s = fmm.Solver(p, precision, out_fp32=out_fp32)
+    s = fmm.Solver(p, precision, out_fp32=out_fp32, **kw)
     s.set_hierarchy(h)
     phi, acc = s.solve(lo)
     torch.cuda.synchronize()
@@ -154,6 +154,69 @@ def test_twolevel64_p6_sampled(precision):
     rp, ra = oracle.solve(h, 6, sel=sel)
     gp, ga = run(h, 6, precision, sel=sel)
     check(gp, ga, rp, ra, oracle_tol(precision), f"64^3+32^3 p=6 {precision}", h=h, sel=sel)
+
+
+@pytest.mark.parametrize("name", ["unigrid16", "amr_3_5", "amr_3_5b", "twolevel16", "empty_base", "tiny4"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bottom_mode_m2l_matches_oracle(name, precision):
+    """Bottom mode 1 (M2L into the parent box + L2P): the downward pass runs to
+    level lmax-1 and no M2P is launched."""
+    h = CASES[name]
+    for p in (4, 6):
+        rp, ra = oracle.solve(h, p, bottom="m2l")
+        gp, ga = run(h, p, precision, bottom="m2l")
+        check(gp, ga, rp, ra, oracle_tol(precision), f"{name} p={p} {precision} bottom m2l", h=h)
+
+
+@pytest.mark.parametrize("p,pm", [(3, 2), (6, 4), (8, 5)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multipole_order_matches_oracle(p, pm, precision):
+    """(p_m, p) = (2, 3) is the paper's quadrupole configuration."""
+    for name in ("amr_3_5", "twolevel16"):
+        h = CASES[name]
+        rp, ra = oracle.solve(h, p, p_m=pm)
+        gp, ga = run(h, p, precision, p_m=pm)
+        check(gp, ga, rp, ra, oracle_tol(precision), f"{name} p={p} p_m={pm} {precision}", h=h)
+    h = CASES["amr_3_5"]
+    rp, ra = oracle.solve(h, p, p_m=pm, bottom="m2l")
+    gp, ga = run(h, p, precision, p_m=pm, bottom="m2l")
+    check(gp, ga, rp, ra, oracle_tol(precision), f"amr p={p} p_m={pm} {precision} bottom m2l", h=h)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_twolevel64_p6_bottom_m2l_sampled(precision):
+    h = W.two_level_plummer()
+    sel = _sample(h, 800, 78)
+    c = h.ijk[0]
+    ring = np.where((np.abs(c - 31.5).max(1) >= 8) & (np.abs(c - 31.5).max(1) <= 10))[0]
+    sel[6] = np.unique(np.concatenate([sel[6], ring[::11]]))
+    rp, ra = oracle.solve(h, 6, sel=sel, bottom="m2l")
+    gp, ga = run(h, 6, precision, sel=sel, bottom="m2l")
+    check(gp, ga, rp, ra, oracle_tol(precision), f"64^3+32^3 p=6 {precision} bottom m2l", h=h, sel=sel)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bottom_mode_m2l_subcycles_match_oracle(precision):
+    """Partial rebuilds and fine-level-only solves in bottom mode 1 (the downward
+    pass then keeps the ancestor lists up to level lo-2)."""
+    from paper_2607_19489_b300 import fmm
+    torch = _torch()
+    h = CASES["amr_3_5"]
+    s = fmm.Solver(6, precision, bottom="m2l")
+    s.set_hierarchy(h)
+    s.solve()
+    for lo in (4, 5):
+        h2 = h.copy()
+        for k in range(lo - h.lmin, len(h.mass)):
+            h2.mass[k] = h.mass[k] * (1.0 + 1e-3 * (2 * W.uniform(4, 70 + k + lo, np.arange(h.mass[k].size)) - 1))
+        s.set_hierarchy(h2, lo=lo)
+        phi, acc = s.solve(lo)
+        torch.cuda.synchronize()
+        s.sync()
+        rp, ra = oracle.solve(h2, 6, lo=lo, bottom="m2l")
+        check({l: phi[l].cpu().numpy() for l in phi}, {l: acc[l].cpu().numpy() for l in acc}, rp, ra,
+              oracle_tol(precision), f"bottom m2l subcycle lo={lo} {precision}", h=h2)
+        h = h2
 
 
 def test_caller_order_is_kept():
