@@ -459,7 +459,7 @@ def gpu_arm(args, rank, world, local):
     del mixed, fp64, e2e_solver
     legs = [x for x in args.legs.split(",") if x and x != "none"] if not args.quick else []
     for name in legs:
-        fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats}.get(name)
+        fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats, "sweep": leg_sweep}.get(name)
         if fn is None:
             continue
         try:
@@ -565,6 +565,64 @@ def _timed(torch, fn, K, W, stream):
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / K
+
+
+def leg_sweep(args, torch, dev, stream, flush):
+    """Speed against accuracy (a Pareto table): the bottom intermediate field (M2P
+    as in the paper, or M2L into the parent box + L2P), the orders (p_m, p) = (2, 3)
+    (the paper's quadrupoles), (4, 4), (6, 6), (8, 8), and the precision (FP64,
+    split-BF16, TF32), on the 32^3 Plummer unigrid and the two-level 64^3 + 32^3
+    hierarchy.  Each entry: cell-updates/s of fmm_set_levels + fmm_solve, and the
+    relative RMS error against the exact sum (fmm_direct_sum, FP64) on all cells
+    (32^3) or 4096 seeded cells per level (64^3 + 32^3)."""
+    from paper_2607_19489_b300 import fmm, workloads as W
+    cfgs = [("unigrid 32^3 Plummer a=0.1, 1% noise", W.unigrid_plummer(5), None),
+            ("two-level 64^3 + 32^3 Plummer a=0.05, lognormal 0.3", W.two_level_plummer(), 4096)]
+    orders = [(3, 2), (4, 4), (6, 6), (8, 8)]
+    keep = {}   # one context per (p, p_m, precision) keeps its shared tables alive
+    rows = []
+    t0 = time.perf_counter()
+    for cname, h, nsample in cfgs:
+        ijk = [torch.as_tensor(a, device=dev).contiguous() for a in h.ijk]
+        mass = [torch.as_tensor(m, device=dev).contiguous() for m in h.mass]
+        ref = fmm.Solver(4, "fp64")
+        ref.set_levels(h.lmin, h.lmax, ijk, mass)
+        sel = {l: (torch.arange(h.n(l), device=dev) if nsample is None else
+                   torch.as_tensor(np.unique((W.uniform(61, l, np.arange(nsample)) * h.n(l)).astype(np.int64)),
+                                   device=dev)) for l in h.levels}
+        direct = {l: ref.direct_sum(l, sel[l]) for l in h.levels}
+        ref.sync()
+        for p, pm in orders:
+            for prec in ("fp64", "mixed", "tf32"):
+                for bottom in ("m2p", "m2l"):
+                    s = fmm.Solver(p, prec, p_m=pm, bottom=bottom)
+                    keep.setdefault((p, pm, prec), s)
+                    out = s.alloc_outputs(device=dev)
+
+                    def step():
+                        s.set_levels(h.lmin, h.lmax, ijk, mass)
+                        s.solve(out=out)
+
+                    K = 2 if prec == "fp64" else 10
+                    ms = _timed(torch, step, K, 2, stream)
+                    s.sync()
+                    num_a = den_a = num_p = den_p = 0.0
+                    for l in h.levels:
+                        ga = out[1][l][sel[l]].double()
+                        gp = out[0][l][sel[l]].double()
+                        num_a += float(((ga - direct[l][1]) ** 2).sum())
+                        den_a += float((direct[l][1] ** 2).sum())
+                        num_p += float(((gp - direct[l][0]) ** 2).sum())
+                        den_p += float((direct[l][0] ** 2).sum())
+                    rows.append({"config": cname, "p": p, "p_m": pm, "bottom": bottom, "precision": prec,
+                                 "cells": h.n_cells, "ms": ms, "value": h.n_cells / (ms * 1e-3),
+                                 "rel_rms_accel_vs_direct": float(np.sqrt(num_a / den_a)),
+                                 "rel_rms_phi_vs_direct": float(np.sqrt(num_p / den_p))})
+                    del s, out
+        del ref
+    del keep
+    return {"unit": UNIT, "step": "fmm_set_levels + fmm_solve (inputs resident)", "runs": rows,
+            "reference": "fmm_direct_sum (FP64 exact sum) on the listed cells", "wall_s": time.perf_counter() - t0}
 
 
 def leg_batched(args, torch, dev, stream, flush):
@@ -801,7 +859,7 @@ def main():
                     help="two_level: the measured configuration; unigrid16: a small check of the launch paths")
     ap.add_argument("--fd-cells", type=int, default=0,
                     help="adjoint leg: central finite differences on this many seeded cells (2 FP64 solves each)")
-    ap.add_argument("--legs", default="batched,adjoint,ats",
+    ap.add_argument("--legs", default="sweep,batched,adjoint,ats",
                     help="extra workloads reported beside the headline (comma list, or 'none')")
     ap.add_argument("--quick", action="store_true",
                     help="the mixed headline and its stage times only (no FP64 arm, e2e, legs or CPU baseline)")

@@ -231,6 +231,18 @@ void fmm_destroy(fmm_ctx* ctx);
 fmm_status fmm_solve_unigrid_static(fmm_ctx* ctx, int level, int64_t n, const int32_t* ijk,
                                     const double* mass, void* phi, void* accel, void* stream);
 
+/* The exact sum the FMM approximates (Sec. 2; the reference of the accuracy
+ * checks of Sec. 4): phi and accel of selected leaf cells of `level` from every
+ * leaf cell of the current hierarchy, G sum_{j != i} m_j g(x_i - x_j) and its
+ * negative gradient, in FP64, O(n_sel x cells) work on the device.
+ *   sel    DEVICE int64 [n_sel], indices into the level's cells in the order of
+ *          the last fmm_set_levels of that level (an index outside gives NaN)
+ *   phi    DEVICE double [n_sel];  accel  DEVICE double [n_sel][3]
+ * Asynchronous on `stream`.  FMM_ERR_STATE before fmm_set_levels, FMM_ERR_ARG
+ * for a level outside lmin..lmax, n_sel < 0 or non-device pointers. */
+fmm_status fmm_direct_sum(fmm_ctx* ctx, int level, int64_t n_sel, const int64_t* sel, double* phi,
+                          double* accel, void* stream);
+
 /* ---- introspection (tests and tools) ---------------------------------- */
 
 /* Number of octs per level l = 0..lmax (n_oct[0] = 0) of the current tree. */

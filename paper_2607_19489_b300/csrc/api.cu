@@ -165,6 +165,15 @@ inline float bf16_val(uint16_t b) {
   std::memcpy(&f, &u, 4);
   return f;
 }
+// FP32 rounded to TF32 (10 explicit mantissa bits) to nearest, ties away from
+// zero: add half of the last kept unit to the magnitude, then drop the 13 bits
+inline float tf32_round(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x1000u) & 0xFFFFE000u;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
 
 // Build the device copies of one contraction operator.  `src` is [N][K] with
 // K ordered (q, s, alpha).
@@ -198,6 +207,13 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
   op.BN = ((N + op.ntile - 1) / op.ntile + 31) / 32 * 32;  // the epilogue reads 32 columns at a time
   op.Npad = op.ntile * op.BN;
   op.Kpad = (K + 63) / 64 * 64;
+  if (c->cfg.precision == FMM_MIXED_TF32) {  // one FP32 operand, rounded to TF32
+    std::vector<float> f((size_t)op.Npad * op.Kpad, 0.0f);
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < K; ++k) f[(size_t)n * op.Kpad + k] = tf32_round((float)src[(size_t)n * K + k]);
+    TRY(upload(c, op.hi, f));
+    return make_tensor_maps(c, op);
+  }
   std::vector<uint16_t> hi((size_t)op.Npad * op.Kpad, 0), lo((size_t)op.Npad * op.Kpad, 0);
   for (int n = 0; n < N; ++n)
     for (int k = 0; k < K; ++k) {
@@ -269,7 +285,9 @@ fmm_status size_expansions(Ctx* c, cudaStream_t st) {
     CKS(buf_ensure(c, T.mono, ncell * 8));
     if (l < c->lmax) {
       CKS(buf_ensure(c, T.M, ncell * nc * (T.m_is_f64 ? 8 : 4)));
-      if (!f64) {
+      if (c->cfg.precision == FMM_MIXED_TF32) {
+        CKS(buf_ensure(c, T.Mhi, ncell * nc * 4));  // FP32 operand rows (TF32-rounded)
+      } else if (!f64) {
         CKS(buf_ensure(c, T.Mhi, ncell * nc * 2));
         CKS(buf_ensure(c, T.Mlo, ncell * nc * 2));
       }
@@ -536,7 +554,6 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_use
   if (cfg->bottom_mode != FMM_BOTTOM_M2P && cfg->bottom_mode != FMM_BOTTOM_M2L_L2P) return FMM_ERR_ARG;
   if (cfg->mass_fp32 != 0 && cfg->mass_fp32 != 1) return FMM_ERR_ARG;
   if (!std::isfinite(cfg->G)) return FMM_ERR_ARG;
-  if (cfg->precision == FMM_MIXED_TF32) return FMM_ERR_ARG;  // not built yet
   fmm_ctx* c = new fmm_ctx();
   c->cfg = *cfg;
   if (c->cfg.p_m == c->cfg.p) c->cfg.p_m = 0;  // one key for the full order

@@ -6,7 +6,11 @@
 // 8 cells and the multipole coefficients, and B is the translation operator
 // (translation invariant, so one table serves every oct and every level).
 // Each operand is split x = hi + lo with hi, lo in BF16; the product keeps
-// hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
+// hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).  In TF32
+// precision each operand is one FP32 value rounded to TF32 and each product is
+// one kind::tf32 MMA (K = 8): the A stage then holds 32 FP32 values per row
+// (32 TMEM columns, as hi + lo do) and the B stage one 128-byte-swizzled tile
+// of BN rows x 32 FP32 (the bytes of the hi and lo tiles together).
 //
 // Per CTA: 128 rows x BN columns.  Tensor memory (TMEM, 512 columns) holds the
 // FP32 accumulator (columns 0..255) and SA stages of the A operand (columns
@@ -83,6 +87,7 @@ struct TcParams {
   int BN, N, nc, mode;
   unsigned* err;
   uint64_t wait_ns;  // limit of every pipeline wait
+  int tf32;          // 1: FP32 operands (Ahi as float), kind::tf32; 0: split-BF16, kind::f16
 };
 
 // First K index of the it-th slice a CTA visits.  Slice-major order (slice c of
@@ -125,12 +130,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait: returns false (and sets *abort) if the phase did not complete
 // within limit_ns or another thread already aborted.
+// A try_wait may itself suspend the thread for a while, so the clock is read
+// on the first retry too, not only every 1024 retries.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   uint64_t t0 = now_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try(bar, parity)) return true;
-    if ((i & 1023) == 0) {
+    if ((i & 1023) == 0 || i == 1) {
       if (*abort) return false;
       if (now_ns() - t0 > limit_ns) {
         *abort = 1;
@@ -163,6 +170,17 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
   return d;
 }
 
+// K-major FP32 tile, rows of BK fp32 (128 B), 128-byte swizzle: 8 rows form a 1024 B atom.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                  // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -177,6 +195,15 @@ __device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, ui
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// D (TMEM) += A (TMEM: 128 lanes x 8 columns = 8 tf32 per row) * B (shared memory)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                            uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
       "r"(tmem_a), "l"(b), "r"(idesc), "r"(accum));
 }
 
@@ -289,7 +316,28 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!ok) break;
       const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
       uint32_t hv[16], lv[16];
-      if (P.v8) {
+      if (P.tf32) {
+        // 32 FP32 per row: columns 0..15 take k0..k0+15, columns 16..31 take k0+16..k0+31
+        const float* A = reinterpret_cast<const float*>(S.Ahi);
+#pragma unroll
+        for (int j = 0; j < BK / 8; ++j) {  // 8 fp32 (32 bytes) never straddle an offset segment (KQ % 8 == 0)
+          const int k = k0 + 8 * j;
+          uint32_t* dst = j < 2 ? hv + 8 * j : lv + 8 * (j - 2);
+          int32_t src = -1;
+          int off = 0;
+          if (k < P.Kvalid) {
+            const int qi = k / P.KQ;
+            off = k - qi * P.KQ;
+            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
+          }
+          if (src >= 0) {
+            ld_nc_v8(A + (int64_t)src * P.KQ + off, dst);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) dst[u] = 0u;
+          }
+        }
+      } else if (P.v8) {
 #pragma unroll
         for (int j = 0; j < BK / 16; ++j) {  // 16 bf16 (32 bytes) never straddle an offset segment (KQ % 16 == 0)
           const int k = k0 + 16 * j;
@@ -412,8 +460,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
         const int n0 = blockIdx.y * P.BN;
         mbar_arrive_tx(fullB0 + 8 * s, 2u * (uint32_t)b_bytes);
-        tma_load_2d(smem_u32(Bhi + s * b_bytes), &tm_hi, k0, n0, fullB0 + 8 * s);
-        tma_load_2d(smem_u32(Blo + s * b_bytes), &tm_lo, k0, n0, fullB0 + 8 * s);
+        if (P.tf32) {  // one FP32 tile per stage, laid over the hi and lo regions
+          tma_load_2d(smem_u32(Bhi + s * 2 * b_bytes), &tm_hi, k0, n0, fullB0 + 8 * s);
+        } else {
+          tma_load_2d(smem_u32(Bhi + s * b_bytes), &tm_hi, k0, n0, fullB0 + 8 * s);
+          tma_load_2d(smem_u32(Blo + s * b_bytes), &tm_lo, k0, n0, fullB0 + 8 * s);
+        }
         ++issued;
       }
       // Loads older than the last SB were consumed by the MMA (it waited for them
@@ -425,8 +477,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == kWarpMma) {
     // ---------------- MMA issue ----------------
     if (lane == 0) {
-      // kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = BN
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P.BN >> 3) << 17) |
+      // kind::f16, D = F32, A = B = BF16 (format 1), or kind::tf32, A = B = TF32 (format 2);
+      // both K-major, M = 128, N = BN
+      const uint32_t fmt = P.tf32 ? 2u : 1u;
+      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(P.BN >> 3) << 17) |
                              ((uint32_t)(BM >> 4) << 24);
       bool ok = true;
       int issued = 0;
@@ -438,15 +492,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         ++issued;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acol = tmem + kAcol0 + 32u * (uint32_t)sa;  // hi at +0, lo at +16
-        const uint32_t bh = smem_u32(Bhi + sb * b_bytes), bl = smem_u32(Blo + sb * b_bytes);
+        if (P.tf32) {
+          const uint32_t b = smem_u32(Bhi + sb * 2 * b_bytes);
 #pragma unroll
-        for (int part = 0; part < 3; ++part) {
-          const uint32_t a = (part == 2) ? acol + 16 : acol;
-          const uint32_t b = (part == 1) ? bl : bh;
+          for (int kk = 0; kk < BK / 8; ++kk)  // K = 8 per MMA: 8 TMEM columns, 32 bytes of each B row
+            mma_tf32_ta(tmem, acol + 8 * kk, sdesc_sw128(b + kk * 32), idesc, (it | kk) != 0);
+        } else {
+          const uint32_t bh = smem_u32(Bhi + sb * b_bytes), bl = smem_u32(Blo + sb * b_bytes);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t accum = (it | part | kk) != 0;
-            mma_bf16_ta(tmem, a + 8 * kk, sdesc_sw64(b + kk * 32), idesc, accum);
+          for (int part = 0; part < 3; ++part) {
+            const uint32_t a = (part == 2) ? acol + 16 : acol;
+            const uint32_t b = (part == 1) ? bl : bh;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t accum = (it | part | kk) != 0;
+              mma_bf16_ta(tmem, a + 8 * kk, sdesc_sw64(b + kk * 32), idesc, accum);
+            }
           }
         }
         mma_commit(emptyA0 + 8 * sa);
@@ -513,15 +574,19 @@ fmm_status make_tensor_maps(Ctx* c, GemmOperand& op) {
     c->last_error = "cuTensorMapEncodeTiled unavailable";
     return FMM_ERR_CUDA;
   }
+  // split-BF16: two maps of bf16 [Npad][Kpad], 64-byte swizzle (BK bf16 = 64 B per row);
+  // TF32: one map of fp32 [Npad][Kpad], 128-byte swizzle (BK fp32 = 128 B per row)
+  const bool tf32 = c->cfg.precision == FMM_MIXED_TF32;
   cuuint64_t dims[2] = {(cuuint64_t)op.Kpad, (cuuint64_t)op.Npad};
-  cuuint64_t strides[1] = {(cuuint64_t)op.Kpad * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)op.Kpad * (tf32 ? 4 : 2)};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)op.BN};
   cuuint32_t es[2] = {1, 1};
   for (int w = 0; w < 2; ++w) {
-    void* g = w == 0 ? op.hi.ptr : op.lo.ptr;
+    void* g = (w == 0 || tf32) ? op.hi.ptr : op.lo.ptr;
     CUtensorMap* tm = (CUtensorMap*)(w == 0 ? op.tmap_hi : op.tmap_lo);
-    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+    CUresult r = enc(tm, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g, dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     tf32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       c->last_error = "cuTensorMapEncodeTiled failed: " + std::to_string((int)r);
@@ -579,6 +644,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.mode = mode;
   P.err = c->d_err;
   P.wait_ns = (uint64_t)(c->wait_s * 1e9);
+  P.tf32 = c->cfg.precision == FMM_MIXED_TF32;
   dim3 grid((unsigned)tiles, (unsigned)op.ntile, (unsigned)nz);
   ++c->n_launch;
   launch_pdl(k_gemm_tc, grid, THREADS, smem_bytes(op.BN), st, *(const CUtensorMap*)op.tmap_hi,

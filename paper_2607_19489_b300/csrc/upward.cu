@@ -28,11 +28,22 @@ namespace {
 
 constexpr int kNcMax = 168;  // ncoef(8) = 165
 
+// One coefficient of a contraction operand row: split-BF16 (hi + lo) for the
+// kind::f16 contraction, or, when lo is null (TF32 precision), the value
+// rounded to nearest TF32 (10 mantissa bits) and stored as FP32 in hi's
+// buffer, which then holds 4 bytes per coefficient.
 template <typename T>
-__device__ __forceinline__ void split_bf16(T v, __nv_bfloat16& h, __nv_bfloat16& l) {
-  float f = (float)v;
-  h = __float2bfloat16_rn(f);
-  l = __float2bfloat16_rn(f - __bfloat162float(h));
+__device__ __forceinline__ void put_operand(T v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
+  const float f = (float)v;
+  if (lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(f - __bfloat162float(h));
+  } else {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+    reinterpret_cast<float*>(hi)[i] = __uint_as_float(r);
+  }
 }
 
 // x[c] -> S[e] = sum_c sign(c, e) x[c]: per axis, (a, b) -> (a + b, b - a).
@@ -122,7 +133,7 @@ __global__ void __launch_bounds__(256) k_leaf_rows(int64_t n, int nc, const int3
     for (int k = lane; k < nc; k += 32) {
       const Tout v = k == 0 ? m : (Tout)0;
       M[row + k] = v;
-      if (hi) split_bf16(v, hi[row + k], lo[row + k]);
+      if (hi) put_operand(v, hi, lo, row + k);
     }
   }
 }
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
       if (k < nc) {
         const float v = (u < 4 ? wk[u] : w0[k]) * sv;
         Mout[cell * nc + k] = v;
-        if (hi) split_bf16(v, hi[cell * nc + k], lo[cell * nc + k]);
+        if (hi) put_operand(v, hi, lo, cell * nc + k);
         if (k == 0) mono[cell] = v;
       }
     }
@@ -240,7 +251,7 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
     float out = 0;
     for (int j = off[k]; j < off[k + 1]; ++j) out += cf[j] * S[gx[j]];
     Mout[cell * nc + k] = out;
-    if (hi) split_bf16(out, hi[cell * nc + k], lo[cell * nc + k]);
+    if (hi) put_operand(out, hi, lo, cell * nc + k);
     if (k == 0) mono[cell] = out;
   }
 }
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(128) k_m2m_block(
     for (int j = off[k]; j < off[k + 1]; ++j) v += cf[j] * S[gx[j]];
     const Tout w = (Tout)v;
     Mout[cell * nc + k] = w;
-    if (hi) split_bf16(w, hi[cell * nc + k], lo[cell * nc + k]);
+    if (hi) put_operand(w, hi, lo, cell * nc + k);
     if (k == 0) mono[cell] = (TMono)w;
   }
 }
@@ -387,7 +398,8 @@ void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {
   const unsigned gr = (unsigned)((T.n_irows * 32 + 255) / 256);
   const int32_t* ir = (const int32_t*)T.irows.ptr;
   __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
-  __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
+  // TF32 precision: one FP32 (TF32-rounded) operand per coefficient in Mhi, no lo half
+  __nv_bfloat16* lo = c->cfg.precision == FMM_MIXED_TF32 ? nullptr : (__nv_bfloat16*)T.Mlo.ptr;
   ++c->n_launch;
   if (T.m_is_f64)
     launch_pdl(k_leaf_rows<double>, gr, 256, 0, st, T.n_irows, c->tab.nc, ir, cc, mass, (double*)T.M.ptr,
@@ -413,7 +425,7 @@ void launch_upward(Ctx* c, int b, cudaStream_t st, const int32_t* octs, int64_t 
   const int32_t* ccn = (const int32_t*)N.cell_child.ptr;
   const double* mn = (const double*)N.mass.ptr;
   __nv_bfloat16* hi = (__nv_bfloat16*)T.Mhi.ptr;
-  __nv_bfloat16* lo = (__nv_bfloat16*)T.Mlo.ptr;
+  __nv_bfloat16* lo = c->cfg.precision == FMM_MIXED_TF32 ? nullptr : (__nv_bfloat16*)T.Mlo.ptr;
   const unsigned g32 = (unsigned)((n + kM2MWarps - 1) / kM2MWarps);
   ++c->n_launch;
   const int np = (int)c->tab.m2m_g.size();

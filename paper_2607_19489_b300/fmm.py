@@ -25,7 +25,7 @@ EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_e
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
             "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static",
             "fmm_solve_adjoint", "fmm_batch_solve", "fmm_autotune", "fmm_get_tuning",
-            "fmm_set_tuning", "fmm_update_masses", "fmm_set_wait_limit"]
+            "fmm_set_tuning", "fmm_update_masses", "fmm_set_wait_limit", "fmm_direct_sum"]
 
 
 class FMMError(RuntimeError):
@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
     L.fmm_update_masses.argtypes = [P, I, P, P]
     L.fmm_stage_times.argtypes = [P, P]
     L.fmm_set_wait_limit.argtypes = [P, ctypes.c_double]
+    L.fmm_direct_sum.argtypes = [P, I, I64, P, P, P, P]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("fmm_last_error", "fmm_destroy"):
@@ -304,6 +305,21 @@ class Solver:
 
     def set_timing(self, on: bool):
         self._check(lib().fmm_set_timing(self._h, int(on)), "fmm_set_timing")
+
+    def direct_sum(self, level: int, sel=None, stream=None):
+        """The exact sum (no FMM) at the given cells of `level` (indices into that level's
+        input order; None: all of them): (phi, accel) float64 CUDA tensors."""
+        import torch
+        if sel is None:
+            sel = torch.arange(self.n[level], dtype=torch.int64, device="cuda")
+        sel = torch.as_tensor(sel, dtype=torch.int64, device="cuda").contiguous()
+        n = int(sel.numel())
+        phi = torch.empty(n, dtype=torch.float64, device="cuda")
+        acc = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+        rc = lib().fmm_direct_sum(self._h, level, n, sel.data_ptr() if n else None, phi.data_ptr() if n else None,
+                                  acc.data_ptr() if n else None, _stream_ptr(stream))
+        self._check(rc, "fmm_direct_sum")
+        return phi, acc
 
     def set_wait_limit(self, seconds: float) -> None:
         """Limit of every bounded device-side wait (fmm_set_wait_limit)."""

@@ -219,6 +219,26 @@ def test_bottom_mode_m2l_subcycles_match_oracle(precision):
         h = h2
 
 
+@pytest.mark.parametrize("name", ["unigrid16", "amr_3_5", "twolevel16", "empty_base"])
+@pytest.mark.parametrize("p", [2, 4, 5, 6, 8])
+def test_tf32_matches_oracle(name, p):
+    """M2L and M2P in one TF32 product per term (tcgen05 kind::tf32), both row
+    orders of the contraction (K order at p = 2, 4, 5, 8; slice-major at 6)."""
+    h = CASES[name]
+    rp, ra = oracle.solve(h, p)
+    gp, ga = run(h, p, "tf32")
+    check(gp, ga, rp, ra, ORACLE_MIXED, f"{name} p={p} tf32", h=h)
+
+
+@pytest.mark.parametrize("bottom", ["m2p", "m2l"])
+def test_twolevel64_p6_tf32_sampled(bottom):
+    h = W.two_level_plummer()
+    sel = _sample(h, 800, 79)
+    rp, ra = oracle.solve(h, 6, sel=sel, bottom=bottom)
+    gp, ga = run(h, 6, "tf32", sel=sel, bottom=bottom)
+    check(gp, ga, rp, ra, ORACLE_MIXED, f"64^3+32^3 p=6 tf32 bottom {bottom}", h=h, sel=sel)
+
+
 def test_caller_order_is_kept():
     h = CASES["amr_3_5"]
     hp = W.permute(h, seed=5)
