@@ -43,8 +43,8 @@ def lib():
         P = ctypes.c_void_p
         i64 = ctypes.c_int64
         L.oracle_fmm_solve.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int,
-                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P,
-                                       ctypes.c_int]
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P,
+                                       P, ctypes.c_int]
         L.oracle_direct_sum.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_double,
                                         ctypes.c_int, P, P, P, P, ctypes.c_int]
         L.oracle_tree.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P]
@@ -117,15 +117,28 @@ def _call(fn, h, lo, sel, extra_front, threads):
 
 
 def solve(h, p: int, G: float = 1.0, lo: int | None = None, sel: dict | None = None,
-          threads: int | None = None, p_m: int | None = None, bottom: str = "m2p"):
+          threads: int | None = None, p_m: int | None = None, bottom: str = "m2p",
+          vel: list | None = None, dt: list | None = None):
     """FMM potential and acceleration of the leaf cells of levels lo..lmax.
 
     sel maps level -> indices into that level's leaf list (None: all leaves).
     p_m: multipole order of M2L / M2P (None: p); bottom: "m2p" (the paper's bottom
     intermediate field) or "m2l" (M2L into the parent box, then L2P).
+    vel[k] ([n, 3] velocities of level lmin+k) and dt[k] (time since level lmin+k was
+    set): drift the multipoles of the stale trees below lo.
     Returns (phi, acc) dicts keyed by level."""
     mode = {"m2p": 0, "m2l": 1}[bottom]
-    return _call(lib().oracle_fmm_solve, h, lo, sel, (p, G, 0 if p_m is None else p_m, mode), threads)
+    keep = None
+    if vel is not None and dt is not None:
+        keep = [np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3) for v in vel]
+        t_vel = _ptr_array(keep)
+        t_dt = np.ascontiguousarray(dt, dtype=np.float64)
+        extra = (p, G, 0 if p_m is None else p_m, mode, t_vel, _ptr(t_dt))
+    else:
+        extra = (p, G, 0 if p_m is None else p_m, mode, None, None)
+    out = _call(lib().oracle_fmm_solve, h, lo, sel, extra, threads)
+    del keep
+    return out
 
 
 def direct(h, G: float = 1.0, lo: int | None = None, sel: dict | None = None,

@@ -36,6 +36,13 @@
 //     into F, which also receives L2L from its parent, then L2P), instead of
 //     M2P / P2P to the target (Fig. 2, Alg. 4).  The downward pass then runs to
 //     box level l-1 and the far field is the L2P of F.
+//   * multipole drifting (Sec. 4 names it as future work, after SWIFT): in a
+//     solve from level lo, every box of a stale tree T_j (j < lo) is moved by
+//     the centre-of-mass velocity of T_j's cells inside it times dt[j], the time
+//     since level j was last set: its moments about the box centre c become the
+//     moments of the moved mass, i.e. the moments about c - d (the shift of
+//     Eq. 2 with displacement d).  Cells used as point masses (P2P, P2L) stay
+//     at their centres.
 //
 // Parity status: pinned by the tests in tests/test_oracle_*.py against the
 // O(N^2) direct sum (exact agreement where the FMM has no far field, error
@@ -462,6 +469,38 @@ struct Solver {
     for (int j = H.lmin; j <= H.lmax; ++j) trees[j] = build_tree(H, op, j);
   }
 
+  // Multipole drifting of the stale trees j < lo (see the header): vel[j] holds
+  // the velocity of each leaf of level j (input order), dt[j - lmin] the time
+  // since level j was set.  Boxes whose tree mass is zero are not moved.
+  void drift(int lo, const double* const* vel, const double* dt) {
+    for (int j = H.lmin; j < lo && j <= H.lmax; ++j) {
+      const double tj = dt[j - H.lmin];
+      if (tj == 0.0 || !vel[j - H.lmin]) continue;
+      for (int f = 1; f < j; ++f) {
+        std::map<I3, std::array<double, 4>> mp;  // box -> (mass, momentum) of tree j
+        for (const auto& kv : H.leaf[j]) {
+          I3 b = kv.first;
+          for (int s = j; s > f; --s) b = parent_of(b);
+          const double m = H.mass[j][kv.second];
+          const double* v = vel[j - H.lmin] + 3 * kv.second;
+          auto& a = mp[b];
+          a[0] += m;
+          for (int i = 0; i < 3; ++i) a[1 + i] += m * v[i];
+        }
+        for (auto& kv : trees[j][f]) {
+          auto it = mp.find(kv.first);
+          if (it == mp.end() || it->second[0] == 0.0) continue;
+          double c[3], cd[3];
+          centre(kv.first, f, c);
+          for (int i = 0; i < 3; ++i) cd[i] = c[i] - it->second[1 + i] / it->second[0] * tj;
+          Vec out(op.n(), 0.0);
+          op.m2m(kv.second, c, cd, out);  // moments about c - d of the unmoved mass
+          kv.second = out;
+        }
+      }
+    }
+  }
+
   // RebuildMergedTree of Alg. 1: merged[f][box] = sum_{j>=l+1} M_{j;f}[box].
   std::vector<Grid> merged_tree(int l) const {
     std::vector<Grid> mt(H.lmax + 1);
@@ -658,8 +697,11 @@ extern "C" {
 // acc[l-lmin] (double[n_sel][3]) receive G*phi and -G*grad phi.  Returns 0 or a
 // negative validation code.
 // p_m: multipole order of M2L / M2P (0: p); bottom: 0 = M2P, 1 = M2L + L2P.
+// vel (per level, double [n][3], or NULL) and dt (per level, or NULL): drift
+// the multipoles of the stale trees j < lo (see Solver::drift).
 int oracle_fmm_solve(int lmin, int lmax, const int64_t* n, const int32_t* const* ijk,
-                     const double* const* mass, int p, double G, int p_m, int bottom, int lo,
+                     const double* const* mass, int p, double G, int p_m, int bottom,
+                     const double* const* vel, const double* dt, int lo,
                      const int64_t* n_sel, const int64_t* const* sel, double* const* phi,
                      double* const* acc, int nthreads) {
   if (p < 1 || p > 12 || nthreads < 1 || p_m < 0 || p_m > p || (bottom != 0 && bottom != 1)) return ORC_ERR_ARG;
@@ -668,6 +710,7 @@ int oracle_fmm_solve(int lmin, int lmax, const int64_t* n, const int32_t* const*
   if (rc) return rc;
   if (lo < lmin || lo > lmax) return ORC_ERR_ARG;
   Solver S(H, p, p_m, bottom);
+  if (vel && dt) S.drift(lo, vel, dt);
   for (int l = lo; l <= lmax; ++l) {
     int64_t nt = n_sel ? n_sel[l - lmin] : n[l - lmin];
     if (nt == 0) continue;
