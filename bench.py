@@ -459,7 +459,8 @@ def gpu_arm(args, rank, world, local):
     del mixed, fp64, e2e_solver
     legs = [x for x in args.legs.split(",") if x and x != "none"] if not args.quick else []
     for name in legs:
-        fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats, "sweep": leg_sweep}.get(name)
+        fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats, "sweep": leg_sweep,
+              "binary": leg_binary}.get(name)
         if fn is None:
             continue
         try:
@@ -597,6 +598,7 @@ def leg_sweep(args, torch, dev, stream, flush):
                 for bottom in ("m2p", "m2l"):
                     s = fmm.Solver(p, prec, p_m=pm, bottom=bottom)
                     keep.setdefault((p, pm, prec), s)
+                    s.set_levels(h.lmin, h.lmax, ijk, mass)
                     out = s.alloc_outputs(device=dev)
 
                     def step():
@@ -623,6 +625,28 @@ def leg_sweep(args, torch, dev, stream, flush):
     del keep
     return {"unit": UNIT, "step": "fmm_set_levels + fmm_solve (inputs resident)", "runs": rows,
             "reference": "fmm_direct_sum (FP64 exact sum) on the listed cells", "wall_s": time.perf_counter() - t0}
+
+
+def leg_binary(args, torch, dev, stream, flush):
+    """The paper's binary orbit test (Sec. 4, Figs. 5-6): two point masses (GM = 0.01
+    each, separation 0.15) deposited by CIC on a grid with lmin = 6 and lmax = 6, 7, 8
+    that follows them (nexpand = 2), fixed-step kick-drift-kick leapfrog to t = 8
+    (about three orbits), p = 6 mixed; the diagnostics of Fig. 6 at t = 8."""
+    from paper_2607_19489_b300 import binary
+    runs = []
+    for lmax in (6, 7, 8):
+        b = binary.Binary(lmin=6, lmax=lmax, p=P_ORDER, precision="mixed", nexpand=2)
+        period = 2 * np.pi / b.omega
+        t0 = time.perf_counter()
+        d = b.run(8.0, period / 200)
+        d.update({"lmin": 6, "lmax": lmax, "dt": period / 200, "wall_s": time.perf_counter() - t0,
+                  "ms_per_step_wall": 1e3 * (time.perf_counter() - t0) / d["solves"]})
+        runs.append(d)
+        del b
+    return {"workload": "binary orbit, GM = 0.01 each, separation 0.15, CIC, nexpand = 2, KDK leapfrog, "
+                        "p=6 mixed", "runs": runs,
+            "step": "per solve: grid around the particles (host), CIC deposit, fmm_set_levels + fmm_solve, "
+                    "CIC interpolation"}
 
 
 def leg_batched(args, torch, dev, stream, flush):
@@ -859,7 +883,7 @@ def main():
                     help="two_level: the measured configuration; unigrid16: a small check of the launch paths")
     ap.add_argument("--fd-cells", type=int, default=0,
                     help="adjoint leg: central finite differences on this many seeded cells (2 FP64 solves each)")
-    ap.add_argument("--legs", default="sweep,batched,adjoint,ats",
+    ap.add_argument("--legs", default="sweep,batched,adjoint,ats,binary",
                     help="extra workloads reported beside the headline (comma list, or 'none')")
     ap.add_argument("--quick", action="store_true",
                     help="the mixed headline and its stage times only (no FP64 arm, e2e, legs or CPU baseline)")

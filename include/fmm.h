@@ -135,6 +135,27 @@ fmm_status fmm_set_levels(fmm_ctx* ctx, int lmin, int lmax, int lo, const int64_
  * The values are not validated (fmm_set_levels rejects non-finite masses). */
 fmm_status fmm_update_masses(fmm_ctx* ctx, int lo, const void* const* mass, void* stream);
 
+/* Multipole drifting of stale trees (Sec. 4 names it as future work, after
+ * SWIFT).  In a solve from level lo > lmin the trees of levels j < lo are stale:
+ * their multipoles hold the masses last given to those levels.  With drifting
+ * on, every box of such a tree at box level >= 2 is moved by d = v dt[j], v the
+ * centre-of-mass velocity of the tree's cells inside the box: its moments about
+ * the box centre become those of the moved mass (the shift of Eq. 2).  Cells
+ * used as point masses (P2P, P2L) stay at their centres.
+ *
+ * fmm_set_velocities: vel[k] double [n][3], velocity of each leaf of level lo+k
+ * in the order of the last fmm_set_levels of that level, device or host
+ * pointer, copied on `stream`.  fmm_set_levels of a level invalidates its
+ * velocities; a drifting solve that needs them returns FMM_ERR_STATE.
+ *
+ * fmm_set_drift: dt[k], k = 0..n-1 with n = lmax - lmin + 1: the time elapsed
+ * since level lmin+k was set (only levels below a solve's lo are drifted); NULL
+ * turns drifting off.  A drifting solve recomputes every multipole from the
+ * masses (a full upward pass) before it adds the drift; the first call after a
+ * new hierarchy sizes the drift scratch (the solves then allocate nothing). */
+fmm_status fmm_set_velocities(fmm_ctx* ctx, int lo, const double* const* vel, void* stream);
+fmm_status fmm_set_drift(fmm_ctx* ctx, const double* dt, int n);
+
 /* Solve for the leaf cells of levels lo..lmax (Alg. 1 for l = lo..lmax, which
  * share one upward and one downward pass: the far field of a box does not
  * depend on the target level).  phi[k] / accel[k] receive level lo+k in the

@@ -648,7 +648,7 @@ static void release_workspace(Ctx* c) {
   for (auto& T : c->lev)
     for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows,
                       &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.tgt, &T.ijk, &T.mass, &T.M,
-                      &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc})
+                      &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc, &T.vel, &T.dS, &T.dQ})
       buf_free(c, *b);
   for (DevBuf* b : {&c->sort_tmp, &c->keys_a, &c->keys_b, &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter,
                     &c->anc_flags, &c->out_stage, &c->in_stage, &c->mass_stage})
@@ -702,6 +702,7 @@ static fmm_status set_levels_impl(fmm_ctx* c, int lmin, int lmax, int lo, const 
     LevelTree& T = c->lev[l];
     int64_t nl = n[l - lo];
     T.n_leaf = nl;
+    T.vel_valid = false;  // the cells may have changed: fmm_set_velocities again
     CKS(buf_ensure(c, T.ijk, nl * 12));
     CKS(buf_ensure(c, T.mass, nl * 8));
     if (nl) {
@@ -741,6 +742,7 @@ static fmm_status set_levels_impl(fmm_ctx* c, int lmin, int lmax, int lo, const 
   }
   c->anc_d = c->anc_req;
   TRY(size_locals(c, st));
+  if (!c->drift_dt.empty()) TRY(drift_prepare(c));
   {  // list lengths decide grid sizes: a change retires the cached solve graphs
     std::vector<int64_t> sig = {c->lmin, c->lmax};
     for (int l = 0; l <= c->lmax; ++l) {
@@ -776,9 +778,13 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // Nothing reads the multipoles of level 1: its cells are never leaves (lmin
   // >= 2), and M2L (box levels >= 2) and M2P (the 26 neighbour octs of the one
   // level-1 oct lie outside the box) have no level-1 sources.
-  if (d <= lmin || (d <= lmax && c->anc_d != d)) {
+  // A drifting solve recomputes every total from the masses, then adds the
+  // drift of each stale tree (corrections must not stack from solve to solve).
+  const bool drift = drift_active(c, lo);
+  if (d <= lmin || (d <= lmax && c->anc_d != d) || drift) {
     for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
     for (int b = lmax - 1; b >= 2; --b) launch_upward(c, b, st);
+    if (drift) launch_drift(c, lo, st);
   } else if (d <= lmax) {
     for (int l = d; l <= lmax; ++l) launch_mono_leaves(c, l, st);
     for (int b = lmax - 1; b >= d - 1; --b) launch_upward(c, b, st);
@@ -877,6 +883,12 @@ static fmm_status launch_solve_graph(Ctx* c, int lo, void* const* dphi, void* co
     key.push_back((uintptr_t)dphi[l]);
     key.push_back((uintptr_t)dacc[l]);
   }
+  if (drift_active(c, lo))  // the time steps are launch parameters of the drift kernels
+    for (double t : c->drift_dt) {
+      uint64_t bits;
+      std::memcpy(&bits, &t, 8);
+      key.push_back((uintptr_t)bits);
+    }
   Ctx::SolveGraph* g = nullptr;
   for (auto& e : c->graphs)
     if (e.key == key) g = &e;
@@ -922,6 +934,13 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
     return FMM_ERR_STATE;
   }
   if (lo < c->lmin || lo > c->lmax_user) return FMM_ERR_ARG;
+  const bool drift = drift_active(c, lo);
+  if (drift)
+    for (int j = c->lmin; j < lo && j <= c->lmax; ++j)
+      if (c->drift_dt[j - c->lmin] != 0.0 && c->lev[j].n_leaf && !c->lev[j].vel_valid) {
+        c->last_error = "fmm_solve: drifting level " + std::to_string(j) + " needs its velocities (fmm_set_velocities)";
+        return FMM_ERR_STATE;
+      }
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
   ++c->n_solve;
@@ -964,7 +983,9 @@ fmm_status fmm_solve(fmm_ctx* c, int lo, void* const* phi, void* const* accel, v
   } else {
     TRY(launch_solve_graph(c, lo, dphi.data(), dacc.data(), st));
   }
-  c->dirty_lo = Ctx::kClean;  // every multipole now matches the current masses
+  // every multipole now matches the current masses, unless drift corrections
+  // were added to them
+  c->dirty_lo = drift ? c->lmin : Ctx::kClean;
   CKS(cudaGetLastError());
   for (int l = lo; l <= c->lmax; ++l)
     if (host_out[l]) {
@@ -1091,7 +1112,7 @@ fmm_status fmm_batch_solve(fmm_ctx* const* ctxs, int nctx, const int* lo, void* 
     g->ctxs[i]->n_launch += g->launches[i];
     ++g->ctxs[i]->n_solve;
     g->ctxs[i]->last_stream = st;
-    g->ctxs[i]->dirty_lo = Ctx::kClean;
+    g->ctxs[i]->dirty_lo = drift_active(g->ctxs[i], lo[i]) ? g->ctxs[i]->lmin : Ctx::kClean;
   }
   return FMM_OK;
 }
@@ -1291,6 +1312,47 @@ fmm_status fmm_update_masses(fmm_ctx* c, int lo, const void* const* mass, void* 
   return FMM_OK;
 }
 
+fmm_status fmm_set_velocities(fmm_ctx* c, int lo, const double* const* vel, void* stream) {
+  if (!c || !vel) return FMM_ERR_ARG;
+  if (!c->have_levels) {
+    c->last_error = "fmm_set_velocities before fmm_set_levels";
+    return FMM_ERR_STATE;
+  }
+  if (lo < c->lmin || lo > c->lmax_user) return FMM_ERR_ARG;
+  for (int l = lo; l <= c->lmax; ++l)
+    if (c->lev[l].n_leaf && !vel[l - lo]) return FMM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  for (int l = lo; l <= c->lmax; ++l) {
+    LevelTree& T = c->lev[l];
+    const int64_t nl = T.n_leaf;
+    CKS(buf_ensure(c, T.vel, std::max<int64_t>(nl, 1) * 24));
+    if (nl) CKS(cudaMemcpyAsync(T.vel.ptr, vel[l - lo], nl * 24, cudaMemcpyDefault, st));
+    T.vel_valid = true;
+  }
+  return FMM_OK;
+}
+
+fmm_status fmm_set_drift(fmm_ctx* c, const double* dt, int n) {
+  if (!c) return FMM_ERR_ARG;
+  if (!dt) {
+    c->drift_dt.clear();
+    return FMM_OK;
+  }
+  if (!c->have_levels) {
+    c->last_error = "fmm_set_drift before fmm_set_levels";
+    return FMM_ERR_STATE;
+  }
+  if (n != c->lmax_user - c->lmin + 1) {
+    c->last_error = "fmm_set_drift: n must be lmax - lmin + 1";
+    return FMM_ERR_ARG;
+  }
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(dt[k])) return FMM_ERR_ARG;
+  c->drift_dt.assign(dt, dt + n);
+  return drift_prepare(c);
+}
+
 fmm_status fmm_set_wait_limit(fmm_ctx* c, double seconds) {
   if (!c || !std::isfinite(seconds) || seconds < 0.0 || seconds > 3600.0) return FMM_ERR_ARG;
   c->wait_s = seconds;
@@ -1336,7 +1398,7 @@ void fmm_destroy(fmm_ctx* c) {
   release_tables(c);
   for (auto& T : c->lev) {
     for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.tgt, &T.ijk,
-                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc})
+                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc, &T.vel, &T.dS, &T.dQ})
       buf_free(c, *b);
   }
   for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_off8, &c->d_l2l_g,
@@ -1346,7 +1408,7 @@ void fmm_destroy(fmm_ctx* c) {
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
                     &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->anc_flags, &c->out_stage, &c->in_stage,
-                    &c->mass_stage, &c->err_buf})
+                    &c->mass_stage, &c->err_buf, &c->d_alpha})
     buf_free(c, *b);
   c->d_err = nullptr;
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);

@@ -62,6 +62,24 @@ __host__ __device__ inline int child_sign(int c, int e) {
   return (__builtin_popcount(e & ~c & 7) & 1) ? -1 : 1;
 }
 
+// One coefficient of a contraction operand row: split-BF16 (hi + lo) for the
+// kind::f16 contraction, or, when lo is null (TF32 precision), the value
+// rounded to nearest TF32 (10 mantissa bits) and stored as FP32 in hi's
+// buffer, which then holds 4 bytes per coefficient.
+template <typename T>
+__device__ __forceinline__ void put_operand(T v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
+  const float f = (float)v;
+  if (lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(f - __bfloat162float(h));
+  } else {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+    reinterpret_cast<float*>(hi)[i] = __uint_as_float(r);
+  }
+}
+
 // A grow-only device allocation.
 struct DevBuf {
   void* ptr = nullptr;
@@ -103,6 +121,11 @@ struct LevelTree {
   // inputs kept for adaptive time stepping (replaced by set_levels)
   DevBuf ijk;            // int32 [n_leaf][3]
   DevBuf mass;           // double [n_leaf]
+  DevBuf vel;            // double [n_leaf][3] velocities (multipole drifting), input order
+  bool vel_valid = false;
+  // multipole drifting scratch: one stale tree's multipoles and (mass, momentum)
+  // per cell of this level, FP64 box units
+  DevBuf dS, dQ;
   // expansions (box units)
   DevBuf M;              // [8 n_oct][nc] double (FP64 path / top levels) or float; rows of
                          // refined cells and of the leaves in interface octs (irows)
@@ -156,6 +179,10 @@ struct Ctx {
   fmm_alloc_fn alloc = nullptr;
   void* alloc_user = nullptr;
   double wait_s = 2.0;  // limit of every bounded device-side wait (fmm_set_wait_limit)
+  // multipole drifting: dt per level lmin.. (empty: off), the multi-index
+  // components of each coefficient on the device
+  std::vector<double> drift_dt;
+  DevBuf d_alpha;
   size_t bytes_in_use = 0;
   std::string last_error;
   cudaStream_t last_stream = nullptr;
@@ -236,6 +263,11 @@ fmm_status near_init(Ctx* c);
 void launch_near_m2p(Ctx* c, int lo, cudaStream_t st);
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st);
 int near_opb(const Ctx* c);
+
+// drift.cu: true when a solve from lo drifts some stale tree; the device work
+bool drift_active(const Ctx* c, int lo);
+fmm_status drift_prepare(Ctx* c);  // scratch and tables (host, allocates)
+void launch_drift(Ctx* c, int lo, cudaStream_t st);
 
 // adjoint.cu
 void launch_adj_mark(Ctx* c, const int32_t* rows, int64_t nrows, const int32_t* nbr, int32_t* flags,

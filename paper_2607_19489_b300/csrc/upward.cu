@@ -28,23 +28,7 @@ namespace {
 
 constexpr int kNcMax = 168;  // ncoef(8) = 165
 
-// One coefficient of a contraction operand row: split-BF16 (hi + lo) for the
-// kind::f16 contraction, or, when lo is null (TF32 precision), the value
-// rounded to nearest TF32 (10 mantissa bits) and stored as FP32 in hi's
-// buffer, which then holds 4 bytes per coefficient.
-template <typename T>
-__device__ __forceinline__ void put_operand(T v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
-  const float f = (float)v;
-  if (lo) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(f);
-    hi[i] = h;
-    lo[i] = __float2bfloat16_rn(f - __bfloat162float(h));
-  } else {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
-    reinterpret_cast<float*>(hi)[i] = __uint_as_float(r);
-  }
-}
+
 
 // x[c] -> S[e] = sum_c sign(c, e) x[c]: per axis, (a, b) -> (a + b, b - a).
 template <typename T>

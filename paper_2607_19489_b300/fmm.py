@@ -25,7 +25,8 @@ EXPORTED = ["fmm_create", "fmm_set_levels", "fmm_solve", "fmm_sync", "fmm_last_e
             "fmm_tree_counts", "fmm_tree_export", "fmm_host_numerators", "fmm_host_table",
             "fmm_set_timing", "fmm_set_graphs", "fmm_stage_times", "fmm_stats", "fmm_solve_unigrid_static",
             "fmm_solve_adjoint", "fmm_batch_solve", "fmm_autotune", "fmm_get_tuning",
-            "fmm_set_tuning", "fmm_update_masses", "fmm_set_wait_limit", "fmm_direct_sum"]
+            "fmm_set_tuning", "fmm_update_masses", "fmm_set_wait_limit", "fmm_direct_sum",
+            "fmm_set_velocities", "fmm_set_drift"]
 
 
 class FMMError(RuntimeError):
@@ -109,6 +110,8 @@ def lib() -> ctypes.CDLL:
     L.fmm_stage_times.argtypes = [P, P]
     L.fmm_set_wait_limit.argtypes = [P, ctypes.c_double]
     L.fmm_direct_sum.argtypes = [P, I, I64, P, P, P, P]
+    L.fmm_set_velocities.argtypes = [P, I, P, P]
+    L.fmm_set_drift.argtypes = [P, P, I]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("fmm_last_error", "fmm_destroy"):
@@ -320,6 +323,23 @@ class Solver:
                                   acc.data_ptr() if n else None, _stream_ptr(stream))
         self._check(rc, "fmm_direct_sum")
         return phi, acc
+
+    def set_velocities(self, vel, lo: int | None = None, stream=None) -> None:
+        """Velocities [n, 3] (float64) of the leaves of levels lo..lmax, for drifting."""
+        lo = self.lmin if lo is None else lo
+        keep = [v if hasattr(v, "data_ptr") else np.ascontiguousarray(v, dtype=np.float64) for v in vel]
+        pv = _ptrs([_data_ptr(v) for v in keep])
+        rc = lib().fmm_set_velocities(self._h, lo, pv, _stream_ptr(stream))
+        del keep
+        self._check(rc, "fmm_set_velocities")
+
+    def set_drift(self, dt=None) -> None:
+        """dt[k]: time since level lmin+k was set (None: drifting off)."""
+        if dt is None:
+            self._check(lib().fmm_set_drift(self._h, None, 0), "fmm_set_drift")
+            return
+        d = np.ascontiguousarray(dt, dtype=np.float64)
+        self._check(lib().fmm_set_drift(self._h, d.ctypes.data, int(d.size)), "fmm_set_drift")
 
     def set_wait_limit(self, seconds: float) -> None:
         """Limit of every bounded device-side wait (fmm_set_wait_limit)."""
