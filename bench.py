@@ -593,6 +593,7 @@ def leg_sweep(args, torch, dev, stream, flush):
                                    device=dev)) for l in h.levels}
         direct = {l: ref.direct_sum(l, sel[l]) for l in h.levels}
         ref.sync()
+        fp64_out = {}
         for p, pm in orders:
             for prec in ("fp64", "mixed", "tf32"):
                 for bottom in ("m2p", "m2l"):
@@ -616,10 +617,19 @@ def leg_sweep(args, torch, dev, stream, flush):
                         den_a += float((direct[l][1] ** 2).sum())
                         num_p += float(((gp - direct[l][0]) ** 2).sum())
                         den_p += float((direct[l][0] ** 2).sum())
+                    got = {l: out[1][l][sel[l]].double() for l in h.levels}
+                    if prec == "fp64":
+                        fp64_out[(p, pm, bottom)] = got
+                    ref64 = fp64_out.get((p, pm, bottom))
+                    vs64 = None
+                    if ref64 is not None and prec != "fp64":
+                        vs64 = float(np.sqrt(sum(float(((got[l] - ref64[l]) ** 2).sum()) for l in h.levels) /
+                                             sum(float((ref64[l] ** 2).sum()) for l in h.levels)))
                     rows.append({"config": cname, "p": p, "p_m": pm, "bottom": bottom, "precision": prec,
                                  "cells": h.n_cells, "ms": ms, "value": h.n_cells / (ms * 1e-3),
                                  "rel_rms_accel_vs_direct": float(np.sqrt(num_a / den_a)),
-                                 "rel_rms_phi_vs_direct": float(np.sqrt(num_p / den_p))})
+                                 "rel_rms_phi_vs_direct": float(np.sqrt(num_p / den_p)),
+                                 "rel_rms_accel_vs_fp64": vs64})
                     del s, out
         del ref
     del keep

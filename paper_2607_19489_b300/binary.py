@@ -121,6 +121,11 @@ class Binary:
         _, acc = self.solver.solve()
         self.solves += 1
         a = acc[self.lmax][torch.as_tensor(idx.reshape(-1), device="cuda")].double().cpu().numpy().reshape(2, 8, 3)
+        if not np.isfinite(a).all():
+            bad = {l: int((~torch.isfinite(acc[l])).any(1).sum()) for l in acc}
+            raise FloatingPointError(f"non-finite acceleration at t = {self.t:.6f} (solve {self.solves}): stencil "
+                                     f"cells {np.argwhere(~np.isfinite(a).all(2)).tolist()}, non-finite cells per "
+                                     f"level {bad}, leaves per level {[len(q) for q in lev]}, x = {self.x.tolist()}")
         return (w[..., None] * a).sum(1)
 
     def run(self, t_end: float, dt: float) -> dict:

@@ -21,6 +21,14 @@ FLOOR = 1e-2
 # against the FP64 oracle
 ORACLE_FP64 = {"rms": 1e-10, "cell": 1e-9}
 ORACLE_MIXED = {"rms": 1e-4, "cell": 1e-3}
+# TF32: one product per term with 10-bit mantissas, each operand rounded by up to
+# 2^-11 (4.9e-4 relative), so a product carries up to ~1e-3 and, with
+# independent rounding over the terms, an RMS of ~3e-4 of the far-field part.
+# The relative RMS bar is that (measured 0.6-1.4e-4 on random AMR, under 1e-4 on
+# the two-level workload); a cell whose acceleration is a few times smaller than
+# the far-field terms summed into it (a partial cancellation, bounded below by
+# the 1 % floor) sees the per-term error amplified: the per-cell bar is 1e-2.
+ORACLE_TF32 = {"rms": 3e-4, "cell": 1e-2}
 # the same kernels run twice (another launch shape, another order of the FP32
 # atomic additions, graph vs direct launches)
 SELF_FP64 = {"rms": 1e-12, "cell": 1e-11}
@@ -28,7 +36,7 @@ SELF_MIXED = {"rms": 1e-5, "cell": 1e-4}
 
 
 def oracle_tol(precision: str) -> dict:
-    return ORACLE_FP64 if precision == "fp64" else ORACLE_MIXED
+    return {"fp64": ORACLE_FP64, "tf32": ORACLE_TF32}.get(precision, ORACLE_MIXED)
 
 
 def self_tol(precision: str) -> dict:

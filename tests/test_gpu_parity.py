@@ -227,7 +227,7 @@ def test_tf32_matches_oracle(name, p):
     h = CASES[name]
     rp, ra = oracle.solve(h, p)
     gp, ga = run(h, p, "tf32")
-    check(gp, ga, rp, ra, ORACLE_MIXED, f"{name} p={p} tf32", h=h)
+    check(gp, ga, rp, ra, oracle_tol("tf32"), f"{name} p={p} tf32", h=h)
 
 
 @pytest.mark.parametrize("bottom", ["m2p", "m2l"])
@@ -236,7 +236,7 @@ def test_twolevel64_p6_tf32_sampled(bottom):
     sel = _sample(h, 800, 79)
     rp, ra = oracle.solve(h, 6, sel=sel, bottom=bottom)
     gp, ga = run(h, 6, "tf32", sel=sel, bottom=bottom)
-    check(gp, ga, rp, ra, ORACLE_MIXED, f"64^3+32^3 p=6 tf32 bottom {bottom}", h=h, sel=sel)
+    check(gp, ga, rp, ra, oracle_tol("tf32"), f"64^3+32^3 p=6 tf32 bottom {bottom}", h=h, sel=sel)
 
 
 def test_caller_order_is_kept():
