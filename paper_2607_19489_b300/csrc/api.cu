@@ -293,9 +293,12 @@ fmm_status size_expansions(Ctx* c, cudaStream_t st) {
       }
     }
     if (l >= c->lmin) {
+      // a grown buffer may come back at the same address (a caching allocator
+      // reuses the block it was just given): compare sizes as well as pointers
       void* old = T.acc.ptr;
+      const size_t old_bytes = T.acc.bytes;
       CKS(buf_ensure(c, T.acc, ncell * 4 * (f64 ? 8 : 4)));
-      if (T.acc.ptr != old) CKS(cudaMemsetAsync(T.acc.ptr, 0, T.acc.bytes, st));
+      if (T.acc.ptr != old || T.acc.bytes != old_bytes) CKS(cudaMemsetAsync(T.acc.ptr, 0, T.acc.bytes, st));
     }
   }
   return FMM_OK;
@@ -310,8 +313,9 @@ fmm_status size_locals(Ctx* c, cudaStream_t st) {
     CKS(buf_ensure(c, T.L, nrow * nc * 8));
     if (!f64) {
       void* old = T.Lm.ptr;
+      const size_t old_bytes = T.Lm.bytes;
       CKS(buf_ensure(c, T.Lm, nrow * nc * 4));
-      if (T.Lm.ptr != old) CKS(cudaMemsetAsync(T.Lm.ptr, 0, T.Lm.bytes, st));
+      if (T.Lm.ptr != old || T.Lm.bytes != old_bytes) CKS(cudaMemsetAsync(T.Lm.ptr, 0, T.Lm.bytes, st));
       CKS(buf_ensure(c, T.Lf, nrow * nc * 4));
     }
   }
@@ -845,9 +849,10 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // memory, so M2L goes first; then M2P, split over all but kM2PSideSMs SMs,
   // overlaps the latency-bound L2L chain and the near-field M2P on the rest
   // (both add atomically into the zeroed accumulator).  FP64: the DFMA
-  // contractions share SMs, so the fork comes right after the upward pass; the
-  // FP64 M2P assigns the accumulator, so the near-field M2P follows it.  With
-  // stage timing on, everything stays in order.
+  // contractions share SMs, so the fork comes right after the upward pass, and
+  // the near-field M2P follows the FP64 M2P on the same branch (both add into
+  // the accumulator, zero between solves).  With stage timing on, everything
+  // stays in order.
   if (!c->timing && c->aux_stream) {
     if (!f64) m2l_tc(st);
     CKS(cudaEventRecord(c->ev_fork, st));
@@ -1282,6 +1287,9 @@ fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const
   }
   launch_adjoint(c, lo, dphi.data() + lo, dacc.data() + lo, c->cfg.out_fp32, st);
   c->dirty_lo = lmin;  // the expansion arrays now hold cotangents
+  // the M2P accumulators are zero between forward solves (the contractions add into them)
+  for (int l = lmin; l <= lmax; ++l)
+    if (c->lev[l].acc.ptr) CKS(cudaMemsetAsync(c->lev[l].acc.ptr, 0, c->lev[l].acc.bytes, st));
   CKS(cudaGetLastError());
   for (int l = lmin; l <= lmax; ++l) {
     const int64_t nl = c->lev[l].n_leaf;

@@ -8,7 +8,10 @@
 // cells (M2P: phi and accel).  The operator table is stored [K][N] with K
 // ordered (q, alpha, s) so that an output column with |beta| = d only visits
 // the prefix |alpha| <= p - d of each offset segment (the Eq. 3 truncation),
-// which skips the zeros of M2L entirely.
+// which skips the zeros of M2L entirely.  Small levels split the 26 offsets
+// over grid.z (partial sums added with FP64 atomics) so that every SM has work;
+// M2P adds only into leaf targets, whose accumulators are zero between solves
+// (the near-field kernel clears what it reads).
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -30,6 +33,8 @@ struct F64Params {
   int mode;
   double* acc;              // M2P: [cells of level l][4]
   const int32_t* cell_child_rows;
+  const int32_t* cell_child_tgt;  // M2P: cell_child of the target level (refined targets get nothing)
+  int q_per_split;          // neighbour offsets per grid.z slice
   double* L;                // M2L: [slot*8 + cell][nc]
   const int32_t* slot;      // M2L: local-expansion slot of each oct
 };
@@ -57,7 +62,8 @@ __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
   double acc[TM];
 #pragma unroll
   for (int r = 0; r < TM; ++r) acc[r] = 0.0;
-  for (int q = 0; q < 26; ++q) {
+  const int q_end = min(26, ((int)blockIdx.z + 1) * P.q_per_split);
+  for (int q = (int)blockIdx.z * P.q_per_split; q < q_end; ++q) {
     for (int k0 = 0; k0 < kmax; k0 += KC) {
       __syncthreads();
       for (int i = threadIdx.x; i < TM * KC; i += 256) {
@@ -89,10 +95,11 @@ __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
     if (P.mode == kModeM2P) {
       int f = n >> 5, t = (n >> 2) & 7, comp = n & 3;
       int32_t ch = P.cell_child_rows[(int64_t)o * 8 + f];
-      if (ch >= 0) P.acc[((int64_t)ch * 8 + t) * 4 + comp] = acc[r];
+      if (ch >= 0 && P.cell_child_tgt[(int64_t)ch * 8 + t] < 0)
+        atomicAdd(&P.acc[((int64_t)ch * 8 + t) * 4 + comp], acc[r]);
     } else {
       int b = n / P.nc, beta = n - b * P.nc;
-      P.L[((int64_t)P.slot[o] * 8 + b) * P.nc + beta] += acc[r];
+      atomicAdd(&P.L[((int64_t)P.slot[o] * 8 + b) * P.nc + beta], acc[r]);
     }
   }
 }
@@ -119,8 +126,14 @@ void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream
   P.mode = mode;
   P.acc = (mode == kModeM2P) ? (double*)c->lev[lr + 1].acc.ptr : nullptr;
   P.cell_child_rows = (const int32_t*)R.cell_child.ptr;
+  P.cell_child_tgt = (mode == kModeM2P) ? (const int32_t*)c->lev[lr + 1].cell_child.ptr : nullptr;
   P.L = (mode == kModeM2L) ? (double*)R.L.ptr : nullptr;
-  dim3 grid((unsigned)((nr + TM - 1) / TM), (unsigned)((op.N + 255) / 256));
+  // split the 26 offsets until about two blocks per SM are in flight
+  const int64_t blocks2 = ((nr + TM - 1) / TM) * ((op.N + 255) / 256);
+  int split = (int)std::min<int64_t>(26, std::max<int64_t>(1, (2 * c->num_sms + blocks2 - 1) / blocks2));
+  P.q_per_split = (26 + split - 1) / split;
+  split = (26 + P.q_per_split - 1) / P.q_per_split;
+  dim3 grid((unsigned)((nr + TM - 1) / TM), (unsigned)((op.N + 255) / 256), (unsigned)split);
   ++c->n_launch;
   // a normal launch: this long kernel shares the SMs with the other branch of the
   // solve, and early-launched waiting blocks of a successor would take its slots

@@ -370,12 +370,15 @@ extern __shared__ __align__(16) float lat_f[];  // dynamic shared memory, seen a
 extern __shared__ __align__(16) int32_t lat_i[];  // ... as ints
 extern __shared__ __align__(16) uint8_t lat_u8[];  // ... as bytes
 
-// Offsets (in 4-byte words) of the shared arrays; nc runtime.
+// Offsets (in 4-byte words) of the shared arrays; nc runtime.  The local
+// expansions' rows are nc | 1 apart: an odd stride keeps the 32 lanes (one row
+// each) in distinct banks.
 struct LatLayout {
-  int L, nb, oct, nspec, lslot, spec_bytes;
+  int L, Ls, nb, oct, nspec, lslot, spec_bytes;
   __host__ __device__ explicit LatLayout(int nc) {
     L = kLatOcts * kLatStride;        // masses [32][217]
-    nb = L + kLatOcts * nc;           // local expansions [32][nc]
+    Ls = nc | 1;                      // row stride of the local expansions
+    nb = L + kLatOcts * Ls;           // local expansions [32][nc | 1]
     oct = nb + kLatOcts * 27;         // neighbour octs [32][27]
     nspec = oct + kLatOcts;           // target octs [32]
     lslot = nspec + kLatOcts;         // counts of special sources [32]
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(256, 4) k_near_lat(const __grid_constant__ Nea
   for (int i = threadIdx.x; i < kLatOcts * nc; i += blockDim.x) {
     const int k = i / nc, b = i - nc * k;
     const int32_t sl = lat_i[Y.lslot + k];
-    lat_f[Y.L + i] = sl >= 0 ? ((const float*)S.L2)[(int64_t)sl * nc + b] : 0.f;
+    lat_f[Y.L + k * Y.Ls + b] = sl >= 0 ? ((const float*)S.L2)[(int64_t)sl * nc + b] : 0.f;
   }
   __syncthreads();
   // ---- warp t: position t of the lane's oct
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(256, 4) k_near_lat(const __grid_constant__ Nea
     const float rx = (float)(2 * (fpos & 1) + tbx) * q - q0;
     const float ry = (float)(2 * ((fpos >> 1) & 1) + tby) * q - q0;
     const float rz = (float)(2 * ((fpos >> 2) & 1) + tbz) * q - q0;
-    const int Lb = Y.L + lane * nc;
+    const int Lb = Y.L + lane * Y.Ls;
     if constexpr (PC > 0) {
       float xa = 1.f;
 #pragma unroll

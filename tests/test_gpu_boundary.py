@@ -145,3 +145,27 @@ def test_bounded_wait_runs_out_and_the_context_recovers():
     check(got_p, got_a, ref_p, ref_a, ORACLE_MIXED, "after a timeout", h=h)
     with pytest.raises(fmm.FMMError):
         s.set_wait_limit(-1.0)
+
+
+def test_recycled_memory_from_the_caching_allocator():
+    """Memory handed back by PyTorch's caching allocator is not cleared: fill its
+    cache with NaN blocks before each growth of the hierarchy; every buffer the
+    library reads before writing (the accumulators that are zero between solves)
+    must be cleared by the library itself, also when a grown buffer comes back at
+    its old address."""
+    import torch
+    from paper_2607_19489_b300 import fmm
+    hs = [W.two_level_plummer(base=3, lo=2, hi=6, seed=2), W.random_amr(3, 5, seed=13),
+          W.two_level_plummer(base=4, lo=4, hi=12, seed=3), W.two_level_plummer(base=5, lo=12, hi=20, seed=3)]
+    for precision in ("mixed", "fp64"):
+        s = fmm.Solver(6, precision)
+        for k, h in enumerate(hs):
+            junk = [torch.full((n,), float("nan"), device="cuda") for n in (1 << 12, 1 << 15, 1 << 18, 1 << 21, 1 << 23)]
+            del junk
+            s.set_hierarchy(h)
+            for rep in range(2):
+                got = _np(*s.solve())
+                s.sync()
+            ref_p, ref_a = oracle.solve(h, 6)
+            tol = {"rms": 1e-10, "cell": 1e-9} if precision == "fp64" else ORACLE_MIXED
+            check(*got, ref_p, ref_a, tol, f"recycled memory {precision} hierarchy {k}", h=h)
