@@ -1190,7 +1190,8 @@ fmm_status fmm_autotune(fmm_ctx* c, int lo, void* stream) {
   if (c->cfg.precision != FMM_FP64) {
     const std::vector<int> splits = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24};
     if (c->cfg.bottom_mode == FMM_BOTTOM_M2P) tune(&c->tune_split[0], splits);  // mode 1 runs no M2P
-    tune(&c->tune_split[1], splits);  // the FP32 near-field kernel has one shape (32 octs per block)
+    tune(&c->tune_split[1], splits);
+    tune(&c->tune_opb, {16, 8, 4});
   } else {
     tune(&c->tune_opb, {8, 4});
   }

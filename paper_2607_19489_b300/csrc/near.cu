@@ -120,6 +120,57 @@ __host__ __device__ constexpr int gidx(int a, int b, int c) {
   return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
 }
 
+// ---- FP32 lattice pairs with compile-time coefficients -------------------------
+// The 216 lattice sources of a target at position t of its oct sit at offsets
+// i - 2 - t (level-l cells, i = 0..5 per axis).  Mirroring an axis on which t's
+// bit is set maps the offset (i - 2) - 1 to -((5 - i) - 2): every position's
+// pair geometry is position 0's, read at mirrored source slots, with the
+// mirrored force components negated at the end.  One unrolled pair loop then
+// serves every position with position 0's coefficients (-1/r and d/r^3) as
+// compile-time constants: a pair costs an address add, one shared-memory load
+// and four FFMAs, and no reciprocal square root.
+__host__ __device__ constexpr double lat_sqrt(double n) {  // Newton's iteration for sqrt, n >= 1
+  double x = n;
+  for (int i = 0; i < 64; ++i) x = 0.5 * (x + n / x);
+  return x;
+}
+
+template <int S>  // lattice source S = ix + 6 iy + 36 iz, seen from position 0
+struct LatPair {
+  static constexpr int ix = S % 6, iy = (S / 6) % 6, iz = S / 36;
+  static constexpr int dx = ix - 2, dy = iy - 2, dz = iz - 2;
+  static constexpr int r2 = dx * dx + dy * dy + dz * dz;
+  static constexpr double ir = r2 ? 1.0 / lat_sqrt((double)r2) : 0.0;
+  static constexpr double ir3 = ir * ir * ir;
+  static constexpr float kp = (float)(-ir);
+  static constexpr float kx = (float)(dx * ir3), ky = (float)(dy * ir3), kz = (float)(dz * ir3);
+};
+
+// The pairs of one target, seen from position 0 through the mirrors of its own
+// position: load(slot) returns the mass at a lattice slot of the target's oct.
+// The row base (iy, iz) is added before the ix term so that six consecutive
+// pairs share it.
+template <int S, typename Load>
+__device__ __forceinline__ void lat_pair(const Load& load, const int (&AX)[6], const int (&AYZ)[36],
+                                         float (&a)[2][4]) {
+  using Q = LatPair<S>;
+  if constexpr (Q::r2 != 0) {  // the target itself is not a source
+    const float m = load(AYZ[Q::iy + 6 * Q::iz] + AX[Q::ix]);
+    float* r = a[S & 1];  // two accumulator sets: shorter FFMA dependency chains
+    r[0] = fmaf(m, Q::kp, r[0]);
+    r[1] = fmaf(m, Q::kx, r[1]);
+    r[2] = fmaf(m, Q::ky, r[2]);
+    r[3] = fmaf(m, Q::kz, r[3]);
+  }
+}
+
+template <typename Load, int... S>
+__device__ __forceinline__ void lat_all(std::integer_sequence<int, S...>, const Load& load, const int (&AX)[6],
+                                        const int (&AYZ)[36], float (&a)[2][4]) {
+  (lat_pair<S>(load, AX, AYZ, a), ...);
+}
+
+
 // PC > 0: expansion order known at compile time (the L2P loops unroll); 0: runtime P.p.
 template <typename T, int OPB, int PC>
 __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearParams P) {
@@ -181,6 +232,31 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
   // Source cell c of slot q has its lower corner at 2 dq + bits(c); relative to
   // the target that is i - 2 - t along each axis, i = 2 (dq+1) + bit in 0..5.
   // With both loops unrolled the six offsets per axis live in registers.
+  if constexpr (sizeof(T) == 4) {
+    // FP32: position 0's pairs at this position's mirrored slots, compile-time
+    // coefficients (see LatPair); slot of lattice index j = 2 q + bit per axis:
+    // 8 (9 qz + 3 qy + qx) + 4 bz + 2 by + bx
+    int AX[6], AYZ[36];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const int jx = tbx ? 5 - i : i;
+      AX[i] = 8 * (jx >> 1) + (jx & 1);
+    }
+#pragma unroll
+    for (int iz = 0; iz < 6; ++iz)
+#pragma unroll
+      for (int iy = 0; iy < 6; ++iy) {
+        const int jy = tby ? 5 - iy : iy, jz = tbz ? 5 - iz : iz;
+        AYZ[iy + 6 * iz] = 24 * (jy >> 1) + 2 * (jy & 1) + 72 * (jz >> 1) + 4 * (jz & 1);
+      }
+    float a[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    auto load = [&](int slot) { return (float)s_m[g][slot]; };  // indexed directly: shared-memory loads
+    lat_all(std::make_integer_sequence<int, 216>{}, load, AX, AYZ, a);
+    phi = (T)(a[0][0] + a[1][0]);
+    ax = (T)(tbx ? -(a[0][1] + a[1][1]) : a[0][1] + a[1][1]);
+    ay = (T)(tby ? -(a[0][2] + a[1][2]) : a[0][2] + a[1][2]);
+    az = (T)(tbz ? -(a[0][3] + a[1][3]) : a[0][3] + a[1][3]);
+  } else {
   T X[6], Y[6], Z[6], X2[6], Y2[6], Z2[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -212,6 +288,7 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
       ay += mir3 * Y[iy];
       az += mir3 * Z[iz];
     }
+  }
   }
   // ---- coarse leaves and refined cells (coarse-fine interfaces only) ----
   const T* nearop = (const T*)P.nearop;
@@ -335,262 +412,6 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
 }
 
 
-// ---- FP32 near field: one warp per target position -----------------------------
-// The 216 lattice sources of a target at position t of its oct sit at offsets
-// i - 2 - t (level-l cells, i = 0..5 per axis).  Mirroring an axis on which t's
-// bit is set maps the offset (i - 2) - 1 to -((5 - i) - 2): every position's
-// pair geometry is position 0's, read at mirrored source slots, with the
-// mirrored force components negated at the end.  One unrolled pair loop then
-// serves every position, with position 0's coefficients (-1/r and d/r^3) as
-// compile-time constants: a pair costs an address add, one shared-memory load
-// and four FFMAs, and no reciprocal square root.  A block takes 32 target octs,
-// one per lane, and warp t computes position t of each; coarse leaves, refined
-// neighbours (nearest field), the M2P sums, L2P and the scatter are as in k_near.
-constexpr int kLatOcts = 32;
-constexpr int kLatStride = 217;  // odd row stride: the 32 lanes' rows start in distinct banks
-
-__host__ __device__ constexpr double lat_sqrt(double n) {  // Newton's iteration for sqrt, n >= 1
-  double x = n;
-  for (int i = 0; i < 64; ++i) x = 0.5 * (x + n / x);
-  return x;
-}
-
-template <int S>  // lattice source S = ix + 6 iy + 36 iz, seen from position 0
-struct LatPair {
-  static constexpr int ix = S % 6, iy = (S / 6) % 6, iz = S / 36;
-  static constexpr int dx = ix - 2, dy = iy - 2, dz = iz - 2;
-  static constexpr int r2 = dx * dx + dy * dy + dz * dz;
-  static constexpr double ir = r2 ? 1.0 / lat_sqrt((double)r2) : 0.0;
-  static constexpr double ir3 = ir * ir * ir;
-  static constexpr float kp = (float)(-ir);
-  static constexpr float kx = (float)(dx * ir3), ky = (float)(dy * ir3), kz = (float)(dz * ir3);
-};
-
-extern __shared__ __align__(16) float lat_f[];  // dynamic shared memory, seen as floats
-extern __shared__ __align__(16) int32_t lat_i[];  // ... as ints
-extern __shared__ __align__(16) uint8_t lat_u8[];  // ... as bytes
-
-// Offsets (in 4-byte words) of the shared arrays; nc runtime.  The local
-// expansions' rows are nc | 1 apart: an odd stride keeps the 32 lanes (one row
-// each) in distinct banks.
-struct LatLayout {
-  int L, Ls, nb, oct, nspec, lslot, spec_bytes;
-  __host__ __device__ explicit LatLayout(int nc) {
-    L = kLatOcts * kLatStride;        // masses [32][217]
-    Ls = nc | 1;                      // row stride of the local expansions
-    nb = L + kLatOcts * Ls;           // local expansions [32][nc | 1]
-    oct = nb + kLatOcts * 27;         // neighbour octs [32][27]
-    nspec = oct + kLatOcts;           // target octs [32]
-    lslot = nspec + kLatOcts;         // counts of special sources [32]
-    spec_bytes = 4 * (lslot + kLatOcts);  // byte offset of the special-source lists [32][216]
-  }
-  __host__ __device__ int bytes() const { return spec_bytes + kLatOcts * 216; }
-};
-
-template <int S>
-__device__ __forceinline__ void lat_pair(int base, const int (&AX)[6], const int (&AY)[6], const int (&AZ)[6],
-                                         float (&a)[2][4]) {
-  using Q = LatPair<S>;
-  if constexpr (Q::r2 != 0) {  // the target itself is not a source
-    const float m = lat_f[base + AX[Q::ix] + AY[Q::iy] + AZ[Q::iz]];
-    float* r = a[S & 1];  // two accumulator sets: shorter FFMA dependency chains
-    r[0] = fmaf(m, Q::kp, r[0]);
-    r[1] = fmaf(m, Q::kx, r[1]);
-    r[2] = fmaf(m, Q::ky, r[2]);
-    r[3] = fmaf(m, Q::kz, r[3]);
-  }
-}
-
-template <int... S>
-__device__ __forceinline__ void lat_all(std::integer_sequence<int, S...>, int base, const int (&AX)[6],
-                                        const int (&AY)[6], const int (&AZ)[6], float (&a)[2][4]) {
-  (lat_pair<S>(base, AX, AY, AZ, a), ...);
-}
-
-template <int PC>
-__global__ void __launch_bounds__(256, 4) k_near_lat(const __grid_constant__ NearParams P) {
-  pdl_wait();
-  pdl_trigger();
-  const LatLayout Y(P.nc);
-  const int nc = P.nc;
-  int si = 0;
-  while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].blk0) ++si;
-  const NearSeg& S = P.seg[si];
-  const int64_t g0 = (int64_t)(blockIdx.x - S.blk0) * kLatOcts;
-  // ---- the block's target octs, their neighbour octs and the box of their far field
-  if (threadIdx.x < kLatOcts) {
-    const int k = threadIdx.x;
-    const int64_t gi = g0 + k;
-    const int32_t o = gi < S.n_tgt ? S.tgt[gi] : -1;
-    lat_i[Y.oct + k] = o;
-    lat_i[Y.nspec + k] = 0;
-    int32_t sl = -1;
-    if (o >= 0 && S.L2) {
-      const int32_t G2 = P.bottom1 ? S.par_l[o] : S.par_up[S.par_l[o] >> 3];
-      sl = S.slot2[G2 >> 3] * 8 + (G2 & 7);
-    }
-    lat_i[Y.lslot + k] = sl;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kLatOcts * 27; i += blockDim.x) {
-    const int k = i / 27, q = i - 27 * k;
-    const int32_t o = lat_i[Y.oct + k];
-    lat_i[Y.nb + i] = o >= 0 ? S.nbr[(int64_t)o * 27 + q] : -1;
-  }
-  __syncthreads();
-  // ---- sources: level-l leaf masses (0 otherwise); coarse leaves and refined cells listed
-#pragma unroll 9
-  for (int j = 0; j < 27; ++j) {  // 32 octs x 216 slots = 27 rounds of 256
-    const int i = j * 256 + threadIdx.x;
-    const int k = i / 216, sl = i - 216 * k;
-    const int32_t nb = lat_i[Y.nb + k * 27 + (sl >> 3)];
-    float m = 0.f;
-    if (nb >= 0) {
-      const int64_t pc = (int64_t)nb * 8 + (sl & 7);
-      if (S.cc_l[pc] < 0)
-        m = ((const float*)S.mono_l)[pc];
-      else
-        lat_u8[Y.spec_bytes + k * 216 + atomicAdd(&lat_i[Y.nspec + k], 1)] = (uint8_t)sl;  // refined cell
-    } else if (nb <= -2 && (sl & 7) == 0) {
-      lat_u8[Y.spec_bytes + k * 216 + atomicAdd(&lat_i[Y.nspec + k], 1)] = (uint8_t)sl;  // a level l-1 leaf, once
-    }
-    lat_f[k * kLatStride + sl] = m;
-  }
-  for (int i = threadIdx.x; i < kLatOcts * nc; i += blockDim.x) {
-    const int k = i / nc, b = i - nc * k;
-    const int32_t sl = lat_i[Y.lslot + k];
-    lat_f[Y.L + k * Y.Ls + b] = sl >= 0 ? ((const float*)S.L2)[(int64_t)sl * nc + b] : 0.f;
-  }
-  __syncthreads();
-  // ---- warp t: position t of the lane's oct
-  const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int32_t o = lat_i[Y.oct + lane];
-  if (o < 0) return;
-  const int64_t cell = (int64_t)o * 8 + t;
-  const int32_t self = S.cc_l[cell];
-  if (self >= 0) return;  // refined: not a target of this level
-  const int tbx = t & 1, tby = (t >> 1) & 1, tbz = (t >> 2) & 1;
-  // slot of lattice index i = 2 q + bit per axis: slot = 8 (9 qz + 3 qy + qx) + 4 bz + 2 by + bx,
-  // read at the mirrored index 5 - i on the axes where t's bit is set
-  int AX[6], AY[6], AZ[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const int jx = tbx ? 5 - i : i, jy = tby ? 5 - i : i, jz = tbz ? 5 - i : i;
-    AX[i] = 8 * (jx >> 1) + (jx & 1);
-    AY[i] = 24 * (jy >> 1) + 2 * (jy & 1);
-    AZ[i] = 72 * (jz >> 1) + 4 * (jz & 1);
-  }
-  float a[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  lat_all(std::make_integer_sequence<int, 216>{}, lane * kLatStride, AX, AY, AZ, a);
-  float phi = a[0][0] + a[1][0];
-  float ax = a[0][1] + a[1][1], ay = a[0][2] + a[1][2], az = a[0][3] + a[1][3];
-  if (tbx) ax = -ax;
-  if (tby) ay = -ay;
-  if (tbz) az = -az;
-  // ---- coarse leaves and refined cells (coarse-fine interfaces only)
-  const float tx = (float)tbx, ty = (float)tby, tz = (float)tbz;
-  const float* nearop = (const float*)P.nearop;
-  (void)nearop;
-  const int nspec = lat_i[Y.nspec + lane];
-  for (int k = 0; k < nspec; ++k) {
-    const int s = lat_u8[Y.spec_bytes + lane * 216 + k];
-    const int32_t nb = lat_i[Y.nb + lane * 27 + (s >> 3)];
-    if (nb <= -2) {  // coarse leaf of level l-1: centre at 2 dq + 1
-      const float m = ((const float*)S.mono_up)[-2 - (int64_t)nb];
-      p2p<float>(m, c_src_pos[s][0] + 0.5f - tx, c_src_pos[s][1] + 0.5f - ty, c_src_pos[s][2] + 0.5f - tz, phi, ax,
-                 ay, az);
-      continue;
-    }
-    const int64_t pc = (int64_t)nb * 8 + (s & 7);
-    const int rx = (int)c_src_pos[s][0] - tbx;
-    const int ry = (int)c_src_pos[s][1] - tby;
-    const int rz = (int)c_src_pos[s][2] - tbz;
-    if (abs(rx) <= 1 && abs(ry) <= 1 && abs(rz) <= 1) {  // nearest field: the 8 children
-      const int32_t ch = S.cc_l[pc];
-      for (int kk = 0; kk < 8; ++kk) {
-        const float m = ((const float*)S.mono_dn)[(int64_t)ch * 8 + kk];
-        p2p<float>(m, (float)rx + (float)((kk & 1) * 2 - 1) * 0.25f, (float)ry + (float)(((kk >> 1) & 1) * 2 - 1) * 0.25f,
-                   (float)rz + (float)(((kk >> 2) & 1) * 2 - 1) * 0.25f, phi, ax, ay, az);
-      }
-    }
-    // refined cells not touching t: M2P, done beforehand by k_near_m2p into acc
-  }
-  // ---- bottom intermediate field (M2P sums) and far field (L2P)
-  float* accm = (float*)S.acc;
-  const float4 mv = *reinterpret_cast<const float4*>(accm + cell * 4);
-  *reinterpret_cast<float4*>(accm + cell * 4) = make_float4(0.f, 0.f, 0.f, 0.f);  // zero between solves
-  float pl = 0.f, xl = 0.f, yl = 0.f, zl = 0.f;
-  if (S.L2) {
-    const int fpos = P.bottom1 ? 0 : (S.par_l[o] & 7);
-    const float q = P.bottom1 ? 0.5f : 0.25f, q0 = P.bottom1 ? 0.25f : 0.375f;
-    const float rx = (float)(2 * (fpos & 1) + tbx) * q - q0;
-    const float ry = (float)(2 * ((fpos >> 1) & 1) + tby) * q - q0;
-    const float rz = (float)(2 * ((fpos >> 2) & 1) + tbz) * q - q0;
-    const int Lb = Y.L + lane * Y.Ls;
-    if constexpr (PC > 0) {
-      float xa = 1.f;
-#pragma unroll
-      for (int aa = 0; aa <= PC; ++aa) {
-        float xy = xa;
-#pragma unroll
-        for (int b = 0; aa + b <= PC; ++b) {
-          float m = xy;
-#pragma unroll
-          for (int cz = 0; aa + b + cz <= PC; ++cz) {
-            pl += lat_f[Lb + gidx(aa, b, cz)] * m;
-            if (aa + b + cz < PC) {
-              xl -= lat_f[Lb + gidx(aa + 1, b, cz)] * m;
-              yl -= lat_f[Lb + gidx(aa, b + 1, cz)] * m;
-              zl -= lat_f[Lb + gidx(aa, b, cz + 1)] * m;
-            }
-            m *= rz * (float)(1.0 / (cz + 1));
-          }
-          xy *= ry * (float)(1.0 / (b + 1));
-        }
-        xa *= rx * (float)(1.0 / (aa + 1));
-      }
-    } else {
-      const int p = P.p;
-      float xa = 1.f;
-      for (int aa = 0; aa <= p; ++aa) {
-        float xy = xa;
-        for (int b = 0; aa + b <= p; ++b) {
-          float m = xy;
-          for (int cz = 0; aa + b + cz <= p; ++cz) {
-            pl += lat_f[Lb + c_lut[aa][b][cz]] * m;
-            if (aa + b + cz < p) {
-              xl -= lat_f[Lb + c_lut[aa + 1][b][cz]] * m;
-              yl -= lat_f[Lb + c_lut[aa][b + 1][cz]] * m;
-              zl -= lat_f[Lb + c_lut[aa][b][cz + 1]] * m;
-            }
-            m *= rz * inv_k<float>(cz);
-          }
-          xy *= ry * inv_k<float>(b);
-        }
-        xa *= rx * inv_k<float>(aa);
-      }
-    }
-  }
-  const float fl1 = P.bottom1 ? 0.5f : 0.25f, fl2 = P.bottom1 ? 0.25f : 0.0625f;
-  const float ph = S.s1f * (phi + 0.5f * mv.x + fl1 * pl);
-  const float gx = S.s2f * (ax + 0.25f * mv.y + fl2 * xl);
-  const float gy = S.s2f * (ay + 0.25f * mv.z + fl2 * yl);
-  const float gz = S.s2f * (az + 0.25f * mv.w + fl2 * zl);
-  const int64_t li = -1 - (int64_t)self;
-  if (P.out_fp32) {
-    ((float*)S.phi)[li] = ph;
-    float* ap = (float*)S.accel + 3 * li;
-    ap[0] = gx;
-    ap[1] = gy;
-    ap[2] = gz;
-  } else {
-    ((double*)S.phi)[li] = widen(ph);
-    double* ap = (double*)S.accel + 3 * li;
-    ap[0] = widen(gx);
-    ap[1] = widen(gy);
-    ap[2] = widen(gz);
-  }
-}
 
 // Near-field M2P (Fig. 2: "M2P from the merged tree at FMM level l") for the
 // target octs that have refined cells among their 3^3 neighbour octs: one warp
@@ -742,11 +563,6 @@ fmm_status near_init(Ctx* c) {
     for (int i = 0; i < 3; ++i) pos[s][i] = (float)(2 * dq[i] + ((cc >> i) & 1));
   }
   cudaError_t e = cudaMemcpyToSymbol(c_src_pos, pos, sizeof(pos));
-  // the lattice kernel's shared memory exceeds the default 48 KB for larger orders
-  const int lat_max = LatLayout(kNcMax).bytes();
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_near_lat<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat_max);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_near_lat<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat_max);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_near_lat<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lat_max);
   if (e != cudaSuccess) {
     c->last_error = std::string("near_init: ") + cudaGetErrorString(e);
     return FMM_ERR_CUDA;
@@ -772,12 +588,12 @@ int near_opb(const Ctx* c) {
   const bool f64 = c->cfg.precision == FMM_FP64;
   const int o = c->tune_opb;
   if (f64) return (o == 4 || o == 8) ? o : 8;
-  return kLatOcts;  // FP32: the lattice kernel, 32 octs per block
+  return (o == 4 || o == 8 || o == 16) ? o : 16;
 }
 
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st) {
   const bool f64 = c->cfg.precision == FMM_FP64;
-  const int opb = near_opb(c);  // FP32: kLatOcts
+  const int opb = near_opb(c);
   int l = lo;
   while (l <= c->lmax) {  // up to kMaxNearSeg target levels per launch
     NearParams P;
@@ -826,13 +642,12 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
       else
         near_dispatch<double, 8>(p, (unsigned)blocks, st, P);
     } else {
-      const size_t smem = (size_t)LatLayout(P.nc).bytes();
-      if (p == 4)
-        launch_pdl(k_near_lat<4>, (unsigned)blocks, 256, smem, st, P);
-      else if (p == 6)
-        launch_pdl(k_near_lat<6>, (unsigned)blocks, 256, smem, st, P);
+      if (opb == 4)
+        near_dispatch<float, 4>(p, (unsigned)blocks, st, P);
+      else if (opb == 8)
+        near_dispatch<float, 8>(p, (unsigned)blocks, st, P);
       else
-        launch_pdl(k_near_lat<0>, (unsigned)blocks, 256, smem, st, P);
+        near_dispatch<float, 16>(p, (unsigned)blocks, st, P);
     }
   }
 }
