@@ -59,7 +59,7 @@ FLOP_PER_PAIR = 20
 # FP32 / FP64 / MUFU throughput of the B300s, probed once with
 # register-only FFMA, DFMA and rsqrt chains over 148 x 8 blocks of 256 threads
 # (CUDA events, best of 5); MEASURED_PEAKS.json carries no FP32 figure.
-PROBED_PEAKS = {"ffma_tflops": 70.0, "dfma_tflops": 1.12, "rsqrt_tops": 4.4,
+PROBED_PEAKS = {"ffma_tflops": 71.6, "dfma_tflops": 1.18, "rsqrt_tops": 4.69,
                 "note": "probed FP32 FFMA peak (register-only FFMA chains, 148 x 8 x 256 threads, CUDA events)"}
 
 

@@ -177,6 +177,15 @@ inline float tf32_round(float f) {
 
 // Build the device copies of one contraction operator.  `src` is [N][K] with
 // K ordered (q, s, alpha).
+//
+// Tensor-core layout.  K is reordered (q, alpha, s) to match the operand rows
+// (op_index), each offset segment padded to a whole number of kTcBK slices.
+// M2L keeps |alpha| + |beta| <= p (and |alpha| <= p_m; Eq. 3), so its columns
+// are ordered by |beta| descending, cell by cell within a degree: an N tile
+// whose lowest column degree is d needs only alpha of degree <= min(p - d,
+// p_m), a prefix of every segment, and the tiles of high degree (most of the
+// columns) read a few slices instead of all of them.  The M2L sums of a slot
+// are kept in this column order (colmap); M2P columns read every alpha <= p_m.
 fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& src, int N, bool m2l) {
   const int nc = c->tab.nc, KQ = 8 * nc, K = 26 * KQ;
   op.N = N;
@@ -203,26 +212,62 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
     op.ntile = (N + 255) / 256;
     return FMM_OK;
   }
-  op.ntile = (N + 255) / 256;
-  op.BN = ((N + op.ntile - 1) / op.ntile + 31) / 32 * 32;  // the epilogue reads 32 columns at a time
+  const int p = c->tab.p, pm = c->tab.pm;
+  // columns: order (new column -> source column) and the degree each keeps
+  std::vector<int> order(N);
+  std::vector<int> keep(N);  // alpha degrees <= keep[n] are read by column n
+  if (m2l) {
+    int n = 0;
+    for (int d = p; d >= 0; --d)
+      for (int b = 0; b < nc; ++b)
+        if (c->tab.degree[b] == d)
+          for (int s = 0; s < 8; ++s) {
+            order[n] = s * nc + b;
+            keep[n] = std::min(p - d, pm);
+            ++n;
+          }
+    std::vector<int32_t> colmap(N);
+    for (int j = 0; j < N; ++j) colmap[order[j]] = j;
+    TRY(upload(c, op.colmap, colmap));
+    op.BN = 96;  // finer tiles track the degree prefixes more closely
+  } else {
+    for (int n = 0; n < N; ++n) {
+      order[n] = n;
+      keep[n] = pm;
+    }
+    op.BN = ((N + 255) / 256 == 1) ? (N + 31) / 32 * 32 : 256;
+  }
+  op.ntile = (N + op.BN - 1) / op.BN;
   op.Npad = op.ntile * op.BN;
-  op.Kpad = (K + 63) / 64 * 64;
+  op.kqp = (KQ + kTcBK - 1) / kTcBK * kTcBK;
+  op.Kpad = 26 * op.kqp;
+  op.tile_slices.assign(op.ntile, 0);
+  for (int y = 0; y < op.ntile; ++y) {
+    int q = 0;
+    for (int n = y * op.BN; n < std::min(N, (y + 1) * op.BN); ++n) q = std::max(q, keep[n]);
+    op.tile_slices[y] = (8 * ncoef(q) + kTcBK - 1) / kTcBK;
+  }
+  // element (new column j, source K index (q, s, alpha)) -> (j, q kqp + alpha 8 + s)
+  auto each = [&](auto&& put) {
+    for (int j = 0; j < N; ++j)
+      for (int q = 0; q < 26; ++q)
+        for (int s = 0; s < 8; ++s)
+          for (int a = 0; a < nc; ++a)
+            put((size_t)j * op.Kpad + (size_t)q * op.kqp + a * 8 + s,
+                src[(size_t)order[j] * K + (size_t)(q * 8 + s) * nc + a]);
+  };
   if (c->cfg.precision == FMM_MIXED_TF32) {  // one FP32 operand, rounded to TF32
     std::vector<float> f((size_t)op.Npad * op.Kpad, 0.0f);
-    for (int n = 0; n < N; ++n)
-      for (int k = 0; k < K; ++k) f[(size_t)n * op.Kpad + k] = tf32_round((float)src[(size_t)n * K + k]);
+    each([&](size_t i, double v) { f[i] = tf32_round((float)v); });
     TRY(upload(c, op.hi, f));
     return make_tensor_maps(c, op);
   }
   std::vector<uint16_t> hi((size_t)op.Npad * op.Kpad, 0), lo((size_t)op.Npad * op.Kpad, 0);
-  for (int n = 0; n < N; ++n)
-    for (int k = 0; k < K; ++k) {
-      double v = src[(size_t)n * K + k];
-      uint16_t h = bf16_bits((float)v);
-      uint16_t l = bf16_bits((float)(v - (double)bf16_val(h)));
-      hi[(size_t)n * op.Kpad + k] = h;
-      lo[(size_t)n * op.Kpad + k] = l;
-    }
+  each([&](size_t i, double v) {
+    const uint16_t h = bf16_bits((float)v);
+    hi[i] = h;
+    lo[i] = bf16_bits((float)(v - (double)bf16_val(h)));
+  });
   TRY(upload(c, op.hi, hi));
   TRY(upload(c, op.lo, lo));
   return make_tensor_maps(c, op);
@@ -254,6 +299,7 @@ fmm_status init_tables(Ctx* c) {
   TRY(upload(c, c->d_l2l_g, t.l2l_g));
   TRY(upload(c, c->d_l2l_e, t.l2l_e));
   TRY(upload(c, c->d_l2l_c, t.l2l_c));
+  TRY(upload(c, c->d_l2l_c32, std::vector<float>(t.l2l_c.begin(), t.l2l_c.end())));
   if (c->cfg.precision == FMM_FP64) {
     TRY(upload(c, c->d_near64, t.nearop));
     TRY(upload(c, c->d_l2p64, t.l2p));
@@ -281,7 +327,10 @@ fmm_status size_expansions(Ctx* c, cudaStream_t st) {
   for (int l = 1; l <= c->lmax; ++l) {
     LevelTree& T = c->lev[l];
     const int64_t ncell = 8 * T.n_oct;
-    T.m_is_f64 = f64 || l <= kTopLevelFP64;
+    // the mixed paths keep FP32 multipoles at every level: they enter the
+    // contractions as split-BF16 or TF32 operands, and FP64 shifts at the top
+    // levels measured no more accurate (relative RMS 3.49e-6 either way)
+    T.m_is_f64 = f64;
     CKS(buf_ensure(c, T.mono, ncell * 8));
     if (l < c->lmax) {
       CKS(buf_ensure(c, T.M, ncell * nc * (T.m_is_f64 ? 8 : 4)));
@@ -310,7 +359,7 @@ fmm_status size_locals(Ctx* c, cudaStream_t st) {
   for (int l = 2; l <= top_local_level(c); ++l) {
     LevelTree& T = c->lev[l];
     const int64_t nrow = 8 * std::max<int64_t>(T.n_rowsL, 1);
-    CKS(buf_ensure(c, T.L, nrow * nc * 8));
+    if (f64) CKS(buf_ensure(c, T.L, nrow * nc * 8));  // the mixed paths keep the FP32 expansions only
     if (!f64) {
       void* old = T.Lm.ptr;
       const size_t old_bytes = T.Lm.bytes;
@@ -445,7 +494,7 @@ fmm_status adjoint_lists(Ctx* c, cudaStream_t st) {
 DevBuf Ctx::*const kTableBufs[] = {
     &Ctx::d_m2m_off, &Ctx::d_m2m_g,   &Ctx::d_m2m_e,    &Ctx::d_m2m_c,  &Ctx::d_m2m_c32, &Ctx::d_m2m_w0,
     &Ctx::d_m2m_w0_32, &Ctx::d_m2m_e0, &Ctx::d_l2l_off, &Ctx::d_l2l_off8, &Ctx::d_l2l_g, &Ctx::d_l2l_e,
-    &Ctx::d_l2l_c,   &Ctx::d_near64,  &Ctx::d_near32,   &Ctx::d_l2p64,  &Ctx::d_l2p32};
+    &Ctx::d_l2l_c,   &Ctx::d_l2l_c32, &Ctx::d_near64,  &Ctx::d_near32,   &Ctx::d_l2p64,  &Ctx::d_l2p32};
 constexpr int kNumTableBufs = sizeof(kTableBufs) / sizeof(kTableBufs[0]);
 
 struct TableSet {
@@ -500,7 +549,7 @@ void release_tables(Ctx* c) {
   TableSet* ts = it->second;
   if (--ts->refs > 0) {
     for (int i = 0; i < kNumTableBufs; ++i) c->*kTableBufs[i] = DevBuf();
-    for (GemmOperand* op : {&c->op_m2p, &c->op_m2l}) op->f64 = op->hi = op->lo = op->klimit = DevBuf();
+    for (GemmOperand* op : {&c->op_m2p, &c->op_m2l}) op->f64 = op->hi = op->lo = op->klimit = op->colmap = DevBuf();
   } else {
     g_tables.erase(it);
     delete ts;  // this context frees the buffers
@@ -651,7 +700,7 @@ static void release_workspace(Ctx* c) {
   if (c->last_stream) cudaStreamSynchronize(c->last_stream);
   for (auto& T : c->lev)
     for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows,
-                      &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.tgt, &T.ijk, &T.mass, &T.M,
+                      &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.lslot, &T.anc, &T.tgt, &T.ijk, &T.mass, &T.M,
                       &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc, &T.vel, &T.dS, &T.dQ})
       buf_free(c, *b);
   for (DevBuf* b : {&c->sort_tmp, &c->keys_a, &c->keys_b, &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter,
@@ -785,6 +834,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // A drifting solve recomputes every total from the masses, then adds the
   // drift of each stale tree (corrections must not stack from solve to solve).
   const bool drift = drift_active(c, lo);
+  if (!f64) launch_zero_lm(c, st);  // the M2L contraction adds into these sums
   if (d <= lmin || (d <= lmax && c->anc_d != d) || drift) {
     for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
     for (int b = lmax - 1; b >= 2; --b) launch_upward(c, b, st);
@@ -824,6 +874,10 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
     if (!dl.empty()) launch_gemm_tc(c, c->op_m2l, kModeM2L, dl.data(), (int)dl.size(), s2, dr.data(), dnr.data());
   };
   auto l2l_chain = [&](cudaStream_t s2) {
+    if (!f64) {  // one launch: each block recomputes its ancestors' expansions
+      if (!dl.empty()) launch_l2l_path(c, lo, s2);
+      return;
+    }
     for (size_t i = 0; i < dl.size(); ++i) {
       launch_l2l_add(c, dl[i], s2, dr[i], dnr[i]);
       if (f64) launch_gemm_f64(c, c->op_m2l, kModeM2L, dl[i], s2, dr[i], dnr[i]);
@@ -1405,15 +1459,15 @@ void fmm_destroy(fmm_ctx* c) {
   drop_batch_graphs_of(c);
   release_tables(c);
   for (auto& T : c->lev) {
-    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.anc, &T.tgt, &T.ijk,
+    for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.lslot, &T.anc, &T.tgt, &T.ijk,
                       &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc, &T.vel, &T.dS, &T.dQ})
       buf_free(c, *b);
   }
   for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_off8, &c->d_l2l_g,
-                    &c->d_l2l_e, &c->d_l2l_c, &c->d_m2m_c32, &c->d_m2m_w0, &c->d_m2m_w0_32, &c->d_m2m_e0,
+                    &c->d_l2l_e, &c->d_l2l_c, &c->d_l2l_c32, &c->d_m2m_c32, &c->d_m2m_w0, &c->d_m2m_w0_32, &c->d_m2m_e0,
                     &c->d_m2mT_off, &c->d_m2mT_a, &c->d_m2mT_c, &c->d_l2lT_off, &c->d_l2lT_b, &c->d_l2lT_e,
                     &c->d_l2lT_c, &c->d_m2pT, &c->d_m2lT, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
-                    &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.f64,
+                    &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.colmap, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
                     &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->anc_flags, &c->out_stage, &c->in_stage,
                     &c->mass_stage, &c->err_buf, &c->d_alpha})

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(128) k_drift_apply(int64_t ncell, int nc, doub
     }
     const TM v = (TM)((double)M[cell * nc + k] + fa * d);
     M[cell * nc + k] = v;
-    if (hi) put_operand(v, hi, lo, cell * nc + k);
+    if (hi) put_operand(v, hi, lo, op_index(cell, k, nc));
   }
 }
 

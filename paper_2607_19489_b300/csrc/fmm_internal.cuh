@@ -13,7 +13,6 @@
 namespace fmm {
 
 constexpr int kMaxLevel = 20;
-constexpr int kTopLevelFP64 = 3;  // mixed precision: box levels <= 3 use FP64 M2M
 
 // Error bits latched by kernels (atomicOr into DeviceState::err).
 enum : unsigned {
@@ -66,6 +65,15 @@ __host__ __device__ inline int child_sign(int c, int e) {
 // kind::f16 contraction, or, when lo is null (TF32 precision), the value
 // rounded to nearest TF32 (10 mantissa bits) and stored as FP32 in hi's
 // buffer, which then holds 4 bytes per coefficient.
+// Index of coefficient k of a cell in the contraction operand rows.  An oct's
+// eight cells form one row of 8 nc values, ordered (alpha, cell): the
+// coefficients of degree <= q then come first, 8 ncoef(q) of them, so an
+// output column that only reads those (M2L keeps |alpha| + |beta| <= p, Eq. 3)
+// needs a prefix of every row.
+__host__ __device__ __forceinline__ int64_t op_index(int64_t cell, int k, int nc) {
+  return (cell >> 3) * 8 * nc + (int64_t)k * 8 + (cell & 7);
+}
+
 template <typename T>
 __device__ __forceinline__ void put_operand(T v, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t i) {
   const float f = (float)v;
@@ -111,6 +119,9 @@ struct LevelTree {
   DevBuf leafmask;       // uint8 [n_oct]: bit c set when cell c of the oct is a leaf
   DevBuf slotL;          // int32 [n_oct]: position of the oct in rowsL (its local-expansion
                          // slot), -1 if it has none
+  DevBuf lslot;          // int32 [n_oct]: row of the local expansion the oct's cells evaluate
+                         // (8 slotL + cell of their level l-2 grandparent cell; bottom mode 1:
+                         // of their parent cell, level l-1), -1 where that level is below 2
   // adjoint (FP64): mass cotangents and the octs read by the contractions
   DevBuf gmass;          // double [n_leaf]
   DevBuf srcP, srcL;     // int32: octs read by M2P rows / by M2L rows of this level
@@ -141,6 +152,8 @@ struct LevelTree {
   bool m_is_f64 = true;
 };
 
+constexpr int kTcBK = 32;  // K slice of the tensor-core contraction (elements per operand row per stage)
+
 struct GemmOperand {  // one operator for the GEMM kernels
   int N = 0, K = 0;     // logical sizes
   int Npad = 0, Kpad = 0, BN = 0, ntile = 0;
@@ -150,6 +163,12 @@ struct GemmOperand {  // one operator for the GEMM kernels
   alignas(64) unsigned char tmap_lo[128];
   DevBuf klimit;        // int32 [N]: K entries per 26-offset segment to visit (FP64 kernel)
   int kseg = 0;         // entries per offset segment (8*nc)
+  // tensor-core layout: K ordered (q, alpha, s), each offset segment padded to
+  // kqp (a multiple of kTcBK); columns of N tile y read only the first
+  // tile_slices[y] slices of every segment (the coefficients they keep)
+  int kqp = 0;
+  std::vector<int> tile_slices;
+  DevBuf colmap;        // M2L, int32 [8 nc]: column (position in a slot's M2L sums) of (cell s, beta) at s nc + beta
 };
 
 struct Ctx {
@@ -162,7 +181,7 @@ struct Ctx {
   // device tables
   DevBuf d_m2m_off, d_m2m_g, d_m2m_e, d_m2m_c, d_m2m_c32;
   DevBuf d_m2m_w0, d_m2m_w0_32, d_m2m_e0;  // per alpha: the gamma = 0 pair (leaf-only octs)
-  DevBuf d_l2l_off, d_l2l_off8, d_l2l_g, d_l2l_e, d_l2l_c;
+  DevBuf d_l2l_off, d_l2l_off8, d_l2l_g, d_l2l_e, d_l2l_c, d_l2l_c32;
   DevBuf d_near64, d_near32, d_l2p64, d_l2p32;
   GemmOperand op_m2p, op_m2l;
   // scratch
@@ -248,6 +267,10 @@ void launch_mono_leaves(Ctx* c, int level, cudaStream_t st);
 // octs / rows: optional lists restricting the pass (null: the full level)
 void launch_upward(Ctx* c, int level, cudaStream_t st, const int32_t* octs = nullptr, int64_t n_octs = 0);
 void launch_l2l_add(Ctx* c, int level, cudaStream_t st, const int32_t* rows = nullptr, int64_t nrows = 0);
+// mixed paths: the whole L2L chain for the levels the near field of targets >= lo reads
+void launch_l2l_path(Ctx* c, int lo, cudaStream_t st);
+// mixed paths: clears the M2L sums of every level (before the contraction adds into them)
+void launch_zero_lm(Ctx* c, cudaStream_t st);
 // gemm_f64.cu
 void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st,
                      const int32_t* rows = nullptr, int64_t nrows = 0);

@@ -24,15 +24,22 @@
 //                run the epilogue (tcgen05.ld, scatter-add to the targets).
 //   warp 16      allocates TMEM and loads B tiles with TMA (SWIZZLE_64B)
 //   warp 17      one thread issues tcgen05.mma (M=128, N=BN, K=16) per slice
-// K is visited slice-major when the offset segment is a whole number of
-// slices: one BK-wide slice of all 26 offsets, then the next.  A tile's rows
-// then re-read the row slices of the same few hundred neighbour octs across the
-// 26 offsets, and the shared memory left unused (4 B stages) keeps them in L1.
-// Split-K over grid.z; partial sums are added with atomics.  Every wait on an
+// K is visited slice-major: one BK-wide slice of all 26 offsets, then the
+// next (each offset segment is padded to whole slices).  A tile's rows then
+// re-read the row slices of the same few hundred neighbour octs across the 26
+// offsets, and the shared memory left unused (4 B stages) keeps them in L1.
+// Within a segment K runs (alpha, cell), so the coefficients of low degree come
+// first; an N tile stops after the slices its columns keep (M2L: |alpha| <=
+// p - min |beta| of the tile).  Split-K: grid.y enumerates (N tile, K part)
+// pairs from a table, so tiles with few slices get no idle CTAs; partial sums
+// are added with atomics.  Every wait on an
 // mbarrier is bounded by a wall-clock limit (a launch parameter); on expiry the
 // CTA latches kErrTimeout and skips the remaining work, but before it frees its
 // TMEM and exits it waits (with a fixed limit of its own) for the TMA loads and
 // the MMAs it has already issued: those still write shared and tensor memory.
+#include <algorithm>
+#include <vector>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -42,7 +49,7 @@ namespace fmm {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 32;  // bf16 elements per row per stage = 64 bytes (64-byte swizzle for B)
+constexpr int BK = kTcBK;  // bf16 elements per row per stage = 64 bytes (64-byte swizzle for B)
 constexpr int SB = 4;   // B stages (shared memory; the rest of the SM's 256 KB serves as L1 for the rows)
 constexpr int SA = 8;   // A stages (TMEM, 32 columns each)
 constexpr int kPhases = 4;                    // producer warps per TMEM lane quarter
@@ -54,6 +61,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAcol0 = 256;              // first A column
 constexpr int kNbrStride = 27;  // shared-memory row stride of the per-row neighbour table
 constexpr int kMaxSeg = 24;
+constexpr int kMaxYZ = 64;  // (N tile, K part) pairs of one launch
 constexpr uint64_t kDrainLimitNs = 1000000000ull;  // 1 s: waits for a CTA's own copies and MMAs in flight
 
 __constant__ int c_nbr26[26] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12,
@@ -77,13 +85,14 @@ struct TcSeg {
 struct TcParams {
   TcSeg seg[kMaxSeg];
   int nseg;
-  int KQ;          // K per neighbour offset (8 * nc)
-  int Kvalid;      // 26 * KQ
-  int nchunks;     // Kpad / BK
+  int KQ;          // operand row length per neighbour offset (8 * nc)
+  int KQP;         // K per neighbour offset in the operator: KQ padded to whole slices
   int chunks_per_split;
   int v8;          // rows load in 32-byte pieces (KQ % 16 == 0 and 32-byte aligned sources)
-  int kq_chunks;   // > 0: K slices visited slice-major (KQ / BK slices per offset, all 26 offsets of a
-                   // slice in a row) so a source row slice is re-read from L1; 0: in K order
+  int nyz;                  // (N tile, K part) pairs on grid.y
+  uint16_t yz_tile[kMaxYZ];  // N tile of pair j
+  uint16_t yz_part[kMaxYZ];  // K part of pair j
+  uint16_t tile_chunks[kMaxYZ];  // slices the tile visits: 26 x the slices per segment it keeps
   int BN, N, nc, mode;
   unsigned* err;
   uint64_t wait_ns;  // limit of every pipeline wait
@@ -93,12 +102,9 @@ struct TcParams {
 // First K index of the it-th slice a CTA visits.  Slice-major order (slice c of
 // every neighbour offset q before slice c + 1) keeps the rows one slice needs,
 // about the distinct neighbour octs of the tile, in L1 across the 26 offsets.
-__device__ __forceinline__ int slice_k0(int kq_chunks, int KQ, int it) {
-  if (kq_chunks > 0) {
-    const int c = it / 26, q = it - 26 * c;
-    return q * KQ + c * BK;
-  }
-  return it * BK;
+__device__ __forceinline__ int slice_k0(int KQP, int it) {
+  const int c = it / 26, q = it - 26 * c;
+  return q * KQP + c * BK;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -257,8 +263,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   int32_t* s_nbr = (int32_t*)(tmem_slot + 4);  // [BM][kNbrStride] source octs of each row
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kc_begin = blockIdx.z * P.chunks_per_split;
-  const int kc_end = min(P.nchunks, kc_begin + P.chunks_per_split);
+  const int ytile = P.yz_tile[blockIdx.y];  // N tile
+  const int kc_begin = P.yz_part[blockIdx.y] * P.chunks_per_split;
+  const int kc_end = min((int)P.tile_chunks[blockIdx.y], kc_begin + P.chunks_per_split);
   const int nit = max(0, kc_end - kc_begin);
   const uint32_t fullA0 = smem_u32(bars), emptyA0 = smem_u32(bars + SA);
   const uint32_t fullB0 = smem_u32(bars + 2 * SA), emptyB0 = smem_u32(bars + 2 * SA + SB);
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int s = it % SA;
       if (it >= SA) ok = mbar_wait(emptyA0 + 8 * s, ((it / SA) - 1) & 1, abort, P.wait_ns);
       if (!ok) break;
-      const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
+      const int k0 = slice_k0(P.KQP, kc_begin + it);
       uint32_t hv[16], lv[16];
       if (P.tf32) {
         // 32 FP32 per row: columns 0..15 take k0..k0+15, columns 16..31 take k0+16..k0+31
@@ -325,10 +332,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint32_t* dst = j < 2 ? hv + 8 * j : lv + 8 * (j - 2);
           int32_t src = -1;
           int off = 0;
-          if (k < P.Kvalid) {
-            const int qi = k / P.KQ;
-            off = k - qi * P.KQ;
-            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
+          {  // the padding at the end of a segment reads as zeros
+            const int qi = k / P.KQP;
+            off = k - qi * P.KQP;
+            if (off < P.KQ) asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
           }
           if (src >= 0) {
             ld_nc_v8(A + (int64_t)src * P.KQ + off, dst);
@@ -343,10 +350,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int k = k0 + 16 * j;
           int32_t src = -1;
           int off = 0;
-          if (k < P.Kvalid) {
-            const int qi = k / P.KQ;
-            off = k - qi * P.KQ;
-            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
+          {  // the padding at the end of a segment reads as zeros
+            const int qi = k / P.KQP;
+            off = k - qi * P.KQP;
+            if (off < P.KQ) asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
           }
           if (src >= 0) {
             ld_nc_v8(S.Ahi + (int64_t)src * P.KQ + off, hv + 8 * j);
@@ -362,10 +369,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int k = k0 + 8 * j;
           int32_t src = -1;
           int off = 0;
-          if (k < P.Kvalid) {
-            const int qi = k / P.KQ;
-            off = k - qi * P.KQ;
-            asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
+          {  // the padding at the end of a segment reads as zeros
+            const int qi = k / P.KQP;
+            off = k - qi * P.KQP;
+            if (off < P.KQ) asm volatile("ld.shared.b32 %0, [%1];" : "=r"(src) : "r"(myn_s + 4 * qi));
           }
           if (src >= 0) {
             ld_nc_v4(S.Ahi + (int64_t)src * P.KQ + off, hv[4 * j], hv[4 * j + 1], hv[4 * j + 2], hv[4 * j + 3]);
@@ -397,7 +404,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           ch[j] = -1;
-          const int f = (blockIdx.y * P.BN + j * 32) >> 5;
+          const int f = (ytile * P.BN + j * 32) >> 5;
           if (valid && j < nchunk && f < 8) ch[j] = S.cell_child_rows[(int64_t)roct * 8 + f];
         }
 #pragma unroll
@@ -424,7 +431,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         TMEM_LD32(taddr, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (!have || !valid) continue;
-        const int n0 = blockIdx.y * P.BN + j * 32;
+        const int n0 = ytile * P.BN + j * 32;
         if (P.mode == kModeM2P) {
           if (ch[j] >= 0) {
             float* dst = S.out + (int64_t)ch[j] * 32;
@@ -457,8 +464,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int s = it % SB;
         if (it >= SB) ok = mbar_wait(emptyB0 + 8 * s, ((it / SB) - 1) & 1, abort, P.wait_ns);
         if (!ok) break;
-        const int k0 = slice_k0(P.kq_chunks, P.KQ, kc_begin + it);
-        const int n0 = blockIdx.y * P.BN;
+        const int k0 = slice_k0(P.KQP, kc_begin + it);
+        const int n0 = ytile * P.BN;
         mbar_arrive_tx(fullB0 + 8 * s, 2u * (uint32_t)b_bytes);
         if (P.tf32) {  // one FP32 tile per stage, laid over the hi and lo regions
           tma_load_2d(smem_u32(Bhi + s * 2 * b_bytes), &tm_hi, k0, n0, fullB0 + 8 * s);
@@ -549,18 +556,32 @@ size_t smem_bytes(int BN) {
   return 1024 + SB * (2 * BN * BK * 2) + (2 * SA + 2 * SB + 2) * 8 + 16 + BM * kNbrStride * 4;
 }
 
-// split-K factor minimising waves x chunks per CTA
-int choose_split(int tiles, int nchunks, int nsm) {
-  int best = 1;
+// Split-K: chunks per CTA minimising waves x chunks per CTA, for M tiles that
+// each run every N tile y over its own tile_chunks[y] slices.  `split` > 0
+// (the autotuner's choice) splits the longest tile in that many parts instead.
+int choose_chunks_per_split(int mtiles, const std::vector<int>& chunks, int nsm, int split) {
+  const int cmax = *std::max_element(chunks.begin(), chunks.end());
+  auto pairs = [&](int cps) {
+    int n = 0;
+    for (int ch : chunks) n += (ch + cps - 1) / cps;
+    return n;
+  };
+  if (split > 0) {
+    int cps = (cmax + split - 1) / split;
+    while (pairs(cps) > kMaxYZ) ++cps;
+    return cps;
+  }
+  int best = cmax;
   double best_t = 1e30;
-  for (int s = 1; s <= 32 && s <= nchunks; ++s) {
-    int cps = (nchunks + s - 1) / s;
-    int ctas = tiles * ((nchunks + cps - 1) / cps);
-    int waves = (ctas + nsm - 1) / nsm;
-    double t = (double)waves * (cps + 2);  // +2: pipeline fill and epilogue
+  for (int s = 1; s <= 32 && s <= cmax; ++s) {
+    const int cps = (cmax + s - 1) / s;
+    const int np = pairs(cps);
+    if (np > kMaxYZ) break;
+    const int waves = (mtiles * np + nsm - 1) / nsm;
+    const double t = (double)waves * (cps + 2);  // +2: pipeline fill and epilogue
     if (t < best_t - 1e-9) {
       best_t = t;
-      best = s;
+      best = cps;
     }
   }
   return best;
@@ -631,13 +652,19 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   }
   if (!tiles) return;
   P.KQ = op.kseg;
-  P.Kvalid = op.K;
-  P.nchunks = op.Kpad / BK;
-  P.kq_chunks = (op.kseg % BK == 0 && op.Kpad == 26 * op.kseg) ? op.kseg / BK : 0;
+  P.KQP = op.kqp;
+  std::vector<int> chunks(op.ntile);
+  for (int y = 0; y < op.ntile; ++y) chunks[y] = 26 * op.tile_slices[y];
   const int tuned = c->tune_split[mode == kModeM2P ? 0 : 1];
-  const int split = tuned > 0 ? std::min(tuned, P.nchunks) : choose_split(tiles * op.ntile, P.nchunks, sm_budget > 0 ? sm_budget : c->num_sms);
-  P.chunks_per_split = (P.nchunks + split - 1) / split;
-  const int nz = (P.nchunks + P.chunks_per_split - 1) / P.chunks_per_split;
+  P.chunks_per_split = choose_chunks_per_split(tiles, chunks, sm_budget > 0 ? sm_budget : c->num_sms, tuned);
+  P.nyz = 0;
+  for (int y = 0; y < op.ntile; ++y)
+    for (int z = 0; z * P.chunks_per_split < chunks[y]; ++z) {
+      P.yz_tile[P.nyz] = (uint16_t)y;
+      P.yz_part[P.nyz] = (uint16_t)z;
+      P.tile_chunks[P.nyz] = (uint16_t)chunks[y];
+      ++P.nyz;
+    }
   P.BN = op.BN;
   P.N = op.N;
   P.nc = c->tab.nc;
@@ -645,7 +672,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.err = c->d_err;
   P.wait_ns = (uint64_t)(c->wait_s * 1e9);
   P.tf32 = c->cfg.precision == FMM_MIXED_TF32;
-  dim3 grid((unsigned)tiles, (unsigned)op.ntile, (unsigned)nz);
+  dim3 grid((unsigned)tiles, (unsigned)P.nyz, 1u);
   ++c->n_launch;
   launch_pdl(k_gemm_tc, grid, THREADS, smem_bytes(op.BN), st, *(const CUtensorMap*)op.tmap_hi,
              *(const CUtensorMap*)op.tmap_lo, P);

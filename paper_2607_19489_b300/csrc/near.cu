@@ -18,11 +18,15 @@
 // target levels in one launch (a segment per level).  The 216 source cells of
 // an oct are staged once in shared memory: their masses (zero for anything
 // that is not a level-l leaf) and a short list of the coarse-leaf and refined
-// entries, which only occur next to coarse-fine interfaces; the 27 rounds of
-// source loads are independent, so they are issued back to back.  The P2P
-// loop is then branch-free except for the self term.  The local expansion of
-// the oct's level l-2 box (bottom mode 1: of its parent box, level l-1) is
-// staged too and evaluated directly, phi = sum_beta L_beta rho^beta / beta!.
+// entries, which only occur next to coarse-fine interfaces.  The kernel is
+// bound by the latency of its loads, so they are issued in as few dependent
+// rounds as possible: the tree data (target oct, its 27 neighbours, their leaf
+// masks, the row of its local expansion) before the wait on the previous
+// kernel, then every mass, the M2P accumulator and the local expansion at
+// once, each neighbour oct's eight masses with two 16-byte loads.  The P2P
+// loop is then branch-free.  The local expansion of the oct's level l-2 box
+// (bottom mode 1: of its parent box, level l-1) is evaluated directly,
+// phi = sum_beta L_beta rho^beta / beta!.
 #include <utility>
 
 #include "fmm_internal.cuh"
@@ -88,14 +92,14 @@ struct NearSeg {
   const int32_t* nbr;         // [oct][27] level l
   const int32_t* cc_l;        // cell_child level l
   const int32_t* par_l;       // oct_parent level l
-  const int32_t* par_up;      // oct_parent level l-1
   const void* mono_up;        // masses of level l-1 cells (in the kernel's precision)
   const void* mono_l;         // level l
   const void* mono_dn;        // level l+1
   const void* M_l;            // multipoles of level l cells
   const void* L2;             // local expansions of level l-2 (bottom mode 1: l-1), or null,
                               // by slot, in T
-  const int32_t* slot2;       // local-expansion slot of each oct of that level
+  const int32_t* lslot;       // [oct of level l]: row of L2 its cells evaluate, or -1
+  const uint8_t* leafmask;    // level l: bit c set when cell c of the oct is a leaf
   void* acc;                  // M2P results for level l cells [cells][4]; cleared after reading
   void* phi;
   void* accel;
@@ -151,11 +155,11 @@ struct LatPair {
 // The row base (iy, iz) is added before the ix term so that six consecutive
 // pairs share it.
 template <int S, typename Load>
-__device__ __forceinline__ void lat_pair(const Load& load, const int (&AX)[6], const int (&AYZ)[36],
-                                         float (&a)[2][4]) {
+__device__ __forceinline__ void lat_pair(const Load& load, const int (&AX)[6], const int (&AY)[6],
+                                         const int (&AZ)[6], float (&a)[2][4]) {
   using Q = LatPair<S>;
   if constexpr (Q::r2 != 0) {  // the target itself is not a source
-    const float m = load(AYZ[Q::iy + 6 * Q::iz] + AX[Q::ix]);
+    const float m = load((AY[Q::iy] + AZ[Q::iz]) + AX[Q::ix]);
     float* r = a[S & 1];  // two accumulator sets: shorter FFMA dependency chains
     r[0] = fmaf(m, Q::kp, r[0]);
     r[1] = fmaf(m, Q::kx, r[1]);
@@ -166,18 +170,43 @@ __device__ __forceinline__ void lat_pair(const Load& load, const int (&AX)[6], c
 
 template <typename Load, int... S>
 __device__ __forceinline__ void lat_all(std::integer_sequence<int, S...>, const Load& load, const int (&AX)[6],
-                                        const int (&AYZ)[36], float (&a)[2][4]) {
-  (lat_pair<S>(load, AX, AYZ, a), ...);
+                                        const int (&AY)[6], const int (&AZ)[6], float (&a)[2][4]) {
+  (lat_pair<S>(load, AX, AY, AZ, a), ...);
 }
 
 
 // PC > 0: expansion order known at compile time (the L2P loops unroll); 0: runtime P.p.
+// Eight consecutive values (one oct's cells) with 16-byte loads; p is 32-byte
+// aligned (an oct's row in a 256-byte aligned buffer).
+__device__ __forceinline__ void load8(const float* p, float (&m)[8]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w; m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+}
+__device__ __forceinline__ void load8(const double* p, double (&m)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = reinterpret_cast<const double2*>(p)[k];
+    m[2 * k] = a.x;
+    m[2 * k + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void load4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double& a, double& b, double& c, double& d) {
+  const double2 u = reinterpret_cast<const double2*>(p)[0], v = reinterpret_cast<const double2*>(p)[1];
+  a = u.x; b = u.y; c = v.x; d = v.y;
+}
+
+// FP32: 896 threads per SM (72 registers, no spills); 64 and 80 registers
+// measured the same on the 64^3 + 32^3 workload at p = 6.
 template <typename T, int OPB, int PC>
-__global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearParams P) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ T s_m[OPB][216];
-  __shared__ T s_L[OPB][kNcMax];          // local expansion of the oct's level l-2 box
+__global__ void __launch_bounds__(8 * OPB, sizeof(T) == 4 ? 112 / OPB : 1) k_near(const __grid_constant__ NearParams P) {
+  __shared__ __align__(16) T s_m[OPB][216];
+  // local expansion of the oct's level l-2 box (rows of ncoef(PC) when the order is fixed)
+  constexpr int kNcL = PC > 0 ? (PC + 1) * (PC + 2) * (PC + 3) / 6 : kNcMax;
+  __shared__ __align__(16) T s_L[OPB][kNcL];
   __shared__ int32_t s_nb[OPB][28];        // the 27 neighbour slots of the oct
   __shared__ uint8_t s_spec[OPB][216];     // source slots that are coarse leaves or refined cells
   __shared__ int s_nspec[OPB];
@@ -187,43 +216,70 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
   const int g = threadIdx.x >> 3, tp = threadIdx.x & 7;
   const int64_t gi = (int64_t)(blockIdx.x - S.blk0) * OPB + g;
   const bool oct_ok = gi < S.n_tgt;
+  // ---- tree data (written by the tree build, before this solve): read before
+  // the wait on the previous kernel, all in three dependent rounds ----
   const int32_t o = oct_ok ? S.tgt[gi] : 0;
-  if (tp == 0) s_nspec[g] = 0;
-  if (oct_ok)
-    for (int q = tp; q < 27; q += 8) s_nb[g][q] = S.nbr[(int64_t)o * 27 + q];
-  __syncthreads();
-  // ---- stage the 216 sources of this oct: thread tp takes cell tp of every slot ----
-  if (oct_ok) {
-#pragma unroll 9
-    for (int q = 0; q < 27; ++q) {
-      const int32_t nb = s_nb[g][q];
-      const int64_t pc = (int64_t)(nb >= 0 ? nb : 0) * 8 + tp;
-      const int32_t ch = S.cc_l[pc];
-      const T mm = ((const T*)S.mono_l)[pc];
-      const int s = q * 8 + tp;
-      T m = 0;
-      if (nb >= 0) {
-        if (ch < 0)
-          m = (T)mm;
-        else
-          s_spec[g][atomicAdd(&s_nspec[g], 1)] = (uint8_t)s;  // refined cell
-      } else if (nb <= -2 && tp == 0) {
-        s_spec[g][atomicAdd(&s_nspec[g], 1)] = (uint8_t)s;  // a level l-1 leaf, counted once
-      }
-      s_m[g][s] = m;
-    }
-    if (S.L2) {
-      // the box whose expansion the oct's cells evaluate: their grandparent cell
-      // (level l-2), or in bottom mode 1 their parent cell F (level l-1)
-      const int32_t G2 = P.bottom1 ? S.par_l[o] : S.par_up[S.par_l[o] >> 3];
-      const int64_t sl = (int64_t)S.slot2[G2 >> 3] * 8 + (G2 & 7);
-      for (int b = tp; b < P.nc; b += 8) s_L[g][b] = ((const T*)S.L2)[sl * P.nc + b];
-    }
+  const int64_t cell = (int64_t)o * 8 + tp;
+  // thread tp owns neighbour slots q = tp + 8 j (j < 4, q < 27)
+  int32_t nbq[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = tp + 8 * j;
+    nbq[j] = (oct_ok && q < 27) ? S.nbr[(int64_t)o * 27 + q] : -1;
   }
+  const int32_t self = oct_ok ? S.cc_l[cell] : 0;
+  const int32_t lrow = (oct_ok && S.L2) ? S.lslot[o] : -1;
+  const int fpos = (oct_ok && S.L2 && !P.bottom1) ? (S.par_l[o] & 7) : 0;
+  unsigned lm[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) lm[j] = nbq[j] >= 0 ? (unsigned)S.leafmask[nbq[j]] : 0xFFu;
+  // entries of the coarse-leaf / refined list: refined cells of each level-l
+  // neighbour oct, one per level l-1 leaf; placed by an exclusive scan over
+  // the oct's eight lanes (a fixed order)
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cnt += nbq[j] >= 0 ? 8 - __popc(lm[j]) : (nbq[j] <= -2 ? 1 : 0);
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d, 8);
+    if (tp >= d) incl += y;
+  }
+  int pos = incl - cnt;
+  if (tp == 7) s_nspec[g] = incl;
+  pdl_wait();
+  pdl_trigger();
+  // ---- masses, the M2P accumulator and the local expansion (this solve) ----
+  const T* mono_l = (const T*)S.mono_l;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = tp + 8 * j;
+    if (q >= 27) break;
+    const int32_t nb = nbq[j];
+    T m[8];
+    if (nb >= 0) {
+      load8(mono_l + (int64_t)nb * 8, m);
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        if ((lm[j] >> cc) & 1) continue;
+        m[cc] = (T)0;  // a refined cell: nearest field or near-field M2P
+        s_spec[g][pos++] = (uint8_t)(q * 8 + cc);
+      }
+    } else {
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) m[cc] = (T)0;
+      if (nb <= -2) s_spec[g][pos++] = (uint8_t)(q * 8);  // a level l-1 leaf, once
+    }
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) s_m[g][q * 8 + cc] = m[cc];
+    s_nb[g][q] = nb;
+  }
+  T pm = 0, xm = 0, ym = 0, zm = 0;
+  if (oct_ok && self < 0) load4((const T*)S.acc + cell * 4, pm, xm, ym, zm);
+  if (lrow >= 0)
+    for (int b = tp; b < P.nc; b += 8) s_L[g][b] = ((const T*)S.L2)[(int64_t)lrow * P.nc + b];
   __syncthreads();
   if (!oct_ok) return;
-  const int64_t cell = (int64_t)o * 8 + tp;
-  const int32_t self = S.cc_l[cell];
   if (self >= 0) return;  // refined: not a target of this level
   const int tbx = tp & 1, tby = (tp >> 1) & 1, tbz = (tp >> 2) & 1;
   const T tx = (T)tbx, ty = (T)tby, tz = (T)tbz;
@@ -236,22 +292,17 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
     // FP32: position 0's pairs at this position's mirrored slots, compile-time
     // coefficients (see LatPair); slot of lattice index j = 2 q + bit per axis:
     // 8 (9 qz + 3 qy + qx) + 4 bz + 2 by + bx
-    int AX[6], AYZ[36];
+    int AX[6], AY[6], AZ[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      const int jx = tbx ? 5 - i : i;
+      const int jx = tbx ? 5 - i : i, jy = tby ? 5 - i : i, jz = tbz ? 5 - i : i;
       AX[i] = 8 * (jx >> 1) + (jx & 1);
+      AY[i] = 24 * (jy >> 1) + 2 * (jy & 1);
+      AZ[i] = 72 * (jz >> 1) + 4 * (jz & 1);
     }
-#pragma unroll
-    for (int iz = 0; iz < 6; ++iz)
-#pragma unroll
-      for (int iy = 0; iy < 6; ++iy) {
-        const int jy = tby ? 5 - iy : iy, jz = tbz ? 5 - iz : iz;
-        AYZ[iy + 6 * iz] = 24 * (jy >> 1) + 2 * (jy & 1) + 72 * (jz >> 1) + 4 * (jz & 1);
-      }
     float a[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
     auto load = [&](int slot) { return (float)s_m[g][slot]; };  // indexed directly: shared-memory loads
-    lat_all(std::make_integer_sequence<int, 216>{}, load, AX, AYZ, a);
+    lat_all(std::make_integer_sequence<int, 216>{}, load, AX, AY, AZ, a);
     phi = (T)(a[0][0] + a[1][0]);
     ax = (T)(tbx ? -(a[0][1] + a[1][1]) : a[0][1] + a[1][1]);
     ay = (T)(tby ? -(a[0][2] + a[1][2]) : a[0][2] + a[1][2]);
@@ -319,18 +370,16 @@ __global__ void __launch_bounds__(8 * OPB) k_near(const __grid_constant__ NearPa
   }
   // ---- bottom intermediate field (M2P, level l-1 units) and far field (L2P, level l-2 units)
   T* acc = (T*)S.acc;
-  T pm = acc[cell * 4], xm = acc[cell * 4 + 1], ym = acc[cell * 4 + 2], zm = acc[cell * 4 + 3];
-  // the accumulator is zero between solves: the contractions add into it next time
+  // the accumulator (read above) is zero between solves: the contractions add into it next time
   acc[cell * 4] = (T)0;
   acc[cell * 4 + 1] = (T)0;
   acc[cell * 4 + 2] = (T)0;
   acc[cell * 4 + 3] = (T)0;
   T pl = 0, xl = 0, yl = 0, zl = 0;
-  if (S.L2) {
+  if (lrow >= 0) {
     // phi = sum_beta L_beta rho^beta / beta!, grad_i = sum_gamma L_{gamma+e_i} rho^gamma / gamma!,
     // rho = target - box centre in units of the level l-2 box (mode 1: of the
     // level l-1 box, where the target sits at +-1/4)
-    const int fpos = P.bottom1 ? 0 : (S.par_l[o] & 7);
     const T q = P.bottom1 ? (T)0.5 : (T)0.25, q0 = P.bottom1 ? (T)0.25 : (T)0.375;
     const T rx = (T)(2 * (fpos & 1) + tbx) * q - q0;
     const T ry = (T)(2 * ((fpos >> 1) & 1) + tby) * q - q0;
@@ -614,14 +663,14 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
       S.nbr = (const int32_t*)T.nbr.ptr;
       S.cc_l = (const int32_t*)T.cell_child.ptr;
       S.par_l = (const int32_t*)T.oct_parent.ptr;
-      S.par_up = (const int32_t*)c->lev[l - 1].oct_parent.ptr;
       S.mono_up = c->lev[l - 1].mono.ptr;
       S.mono_l = T.mono.ptr;
       S.mono_dn = (l < c->lmax) ? c->lev[l + 1].mono.ptr : nullptr;
       S.M_l = T.M.ptr;
       S.M_l_f64 = T.m_is_f64 ? 1 : 0;
       S.L2 = (l - dl >= 2) ? (f64 ? c->lev[l - dl].L.ptr : c->lev[l - dl].Lf.ptr) : nullptr;
-      S.slot2 = (l - dl >= 2) ? (const int32_t*)c->lev[l - dl].slotL.ptr : nullptr;
+      S.lslot = (const int32_t*)T.lslot.ptr;
+      S.leafmask = (const uint8_t*)T.leafmask.ptr;
       S.acc = T.acc.ptr;
       S.phi = phi[l - lo];
       S.accel = accel[l - lo];

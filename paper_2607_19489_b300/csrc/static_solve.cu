@@ -44,6 +44,8 @@ struct UnigridView {
   int32_t* oct_parent[kStaticMaxLevel + 1];
   int32_t* nbr[kStaticMaxLevel + 1];
   int32_t* iota;
+  uint8_t* leafmask;  // finest level: every cell a leaf
+  int32_t* lslot;     // finest level: local-expansion row of each oct's level L-2 grandparent cell
   unsigned* status;
   int level;
 };
@@ -75,7 +77,13 @@ __global__ void k_unigrid_tree(UnigridView V) {
       }
     }
   }
-  if (i < ((int64_t)1 << (3 * (L - 1)))) V.iota[i] = (int32_t)i;
+  if (i < ((int64_t)1 << (3 * (L - 1)))) {
+    V.iota[i] = (int32_t)i;
+    V.leafmask[i] = 0xFFu;
+    // oct i's parent cell is cell i of level L-1, whose parent is cell i >> 3 of
+    // level L-2; with one slot per oct (slotL = iota) that cell's row is i >> 3
+    V.lslot[i] = L - 2 >= 2 ? (int32_t)(i >> 3) : -1;
+  }
 }
 
 // Each input cell claims its slot of the finest level; a slot claimed twice or
@@ -215,6 +223,8 @@ extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n
     }
   }
   V.iota = (int32_t*)cv.take(((int64_t)1 << (3 * (L - 1))) * 4);
+  V.leafmask = (uint8_t*)cv.take((int64_t)1 << (3 * (L - 1)));
+  V.lslot = (int32_t*)cv.take(((int64_t)1 << (3 * (L - 1))) * 4);
   V.status = (unsigned*)cv.take(256);
   if (cv.off > kStaticBytes) {
     c->last_error = "fmm_solve_unigrid_static: static scratch too small for this order";
@@ -227,6 +237,9 @@ extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n
     set_buf(T.slotL, V.iota, T.n_oct * 4);  // every oct of a complete grid has its own slot
     set_buf(T.tgt, V.iota, T.n_oct * 4);
   }
+  // the near-field kernel reads these two tables of the target level
+  set_buf(view[L].leafmask, V.leafmask, view[L].n_oct);
+  set_buf(view[L].lslot, V.lslot, view[L].n_oct * 4);
 
   // ---- tree index and leaves ----
   const int64_t nmax = (int64_t)1 << (3 * L);

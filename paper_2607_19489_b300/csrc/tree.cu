@@ -38,6 +38,8 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 
 __global__ void k_leaf_keys(int64_t n, const int32_t* __restrict__ ijk, const double* __restrict__ mass,
                             int level, uint64_t* keys, int32_t* vals, unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int x = ijk[3 * i], y = ijk[3 * i + 1], z = ijk[3 * i + 2];
@@ -53,6 +55,8 @@ __global__ void k_leaf_keys(int64_t n, const int32_t* __restrict__ ijk, const do
 
 __global__ void k_refined_keys(int64_t n, const uint64_t* __restrict__ octkey_next, uint64_t* keys,
                                int32_t* vals) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   keys[i] = octkey_next[i];
@@ -60,6 +64,8 @@ __global__ void k_refined_keys(int64_t n, const uint64_t* __restrict__ octkey_ne
 }
 
 __global__ void k_oct_flags(int64_t n, const uint64_t* __restrict__ k, int32_t* flags, unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int f = 1;
@@ -79,6 +85,8 @@ __global__ void k_scatter_level(int64_t n, int64_t n_oct, const uint64_t* __rest
                                 const int32_t* __restrict__ v, const int32_t* __restrict__ scan, uint64_t* oct_key,
                                 int32_t* cell_child, int32_t* leaf_cell, int32_t* oct_parent_next,
                                 int64_t n_oct_next, int64_t n_leaf, int check_keys, unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t oct = scan[i] - 1;
@@ -116,6 +124,8 @@ __global__ void k_place_complete(int level, int64_t n_leaf, int64_t n_ref, int64
                                  const uint64_t* __restrict__ octkey_next, int32_t* __restrict__ cell_child,
                                  int32_t* __restrict__ leaf_cell, int32_t* __restrict__ oct_parent_next,
                                  unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_leaf + n_ref) return;
   uint64_t key;
@@ -168,6 +178,8 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {  // inverse of spread
 }
 
 __global__ void k_complete_levels(const __grid_constant__ CompleteLevels P) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= P.oct0[P.lmin + 1]) return;
   int l = 1;
@@ -193,6 +205,8 @@ __global__ void k_complete_levels(const __grid_constant__ CompleteLevels P) {
 __global__ void k_nbr(int level, int64_t n_oct, int64_t n_oct_up, const int32_t* __restrict__ oct_parent,
                       const int32_t* __restrict__ nbr_up, const int32_t* __restrict__ cell_child_up,
                       const int32_t* __restrict__ cell_child_here, int32_t* nbr, unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n_oct * 27) return;
   int64_t o = t / 27;
@@ -267,6 +281,13 @@ struct ListLevel {
   uint8_t* leafmask;
   const uint8_t* leafmask_next;  // level + 1 (or null)
   int32_t* slotL;    // [n_oct]: position in rowsL or -1
+  // local-expansion rows (k_lslots): lslot[o] = 8 slotL_far[G >> 3] + (G & 7), G the
+  // oct's ancestor cell at level l - dl (dl = 2, bottom mode 1: 1), or -1
+  const int32_t* oct_parent;     // level l
+  const int32_t* oct_parent_up;  // level l - 1 (dl = 2)
+  const int32_t* slotL_far;      // slotL of level l - dl, or null (no local expansion)
+  int32_t* lslot;
+  int64_t n_oct_up, n_oct_far;   // octs of levels l - 1 and l - dl
   int want_rowsL, want_irows;
   int rowsL_refined;  // bottom mode 1: rowsL holds the octs with a refined cell
 };
@@ -286,6 +307,8 @@ __device__ __forceinline__ int list_level(const ListParams& P, int64_t blk) {
 // Leaf masks of every oct of every level (bit c: cell c is a leaf); an oct
 // holds a refined cell iff its mask is not 0xFF.  Read by the list flags below.
 __global__ void __launch_bounds__(kListBlock) k_leafmasks(const __grid_constant__ ListParams P) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t blk = blockIdx.x;
   const ListLevel& L = P.lev[list_level(P, blk)];
   const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
@@ -316,6 +339,8 @@ __device__ __forceinline__ unsigned oct_list_flags(const ListLevel& L, int64_t o
 
 __global__ void __launch_bounds__(kListBlock) k_lists_count(const __grid_constant__ ListParams P, uint8_t* __restrict__ flags,
                                                             int32_t* __restrict__ blk_counts) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t blk = blockIdx.x;
   const ListLevel& L = P.lev[list_level(P, blk)];
   const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
@@ -335,6 +360,8 @@ __global__ void __launch_bounds__(kListBlock) k_lists_count(const __grid_constan
 __global__ void __launch_bounds__(1024) k_lists_scan(const __grid_constant__ ListParams P,
                                                      const int32_t* __restrict__ blk_counts,
                                                      int32_t* __restrict__ blk_off, int32_t* __restrict__ counts) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int32_t warp_sum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int li = blockIdx.x >> 2, k = blockIdx.x & 3;
@@ -370,6 +397,8 @@ __global__ void __launch_bounds__(1024) k_lists_scan(const __grid_constant__ Lis
 
 __global__ void __launch_bounds__(kListBlock) k_lists_write(const __grid_constant__ ListParams P, const uint8_t* __restrict__ flags,
                                                             const int32_t* __restrict__ blk_off) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int32_t warp_cnt[kListBlock / 32][4];
   const int64_t blk = blockIdx.x;
   const ListLevel& L = P.lev[list_level(P, blk)];
@@ -392,6 +421,31 @@ __global__ void __launch_bounds__(kListBlock) k_lists_write(const __grid_constan
   }
 }
 
+// The local-expansion row of every oct (the near-field kernel's far field),
+// read once per target oct instead of through the parent chain in its loop.
+// Runs before the build's errors are read: every link is checked against the
+// size of the level it points into, as in the list flags above (an invalid
+// hierarchy leaves -1 and is rejected afterwards).
+__global__ void __launch_bounds__(kListBlock) k_lslots(const __grid_constant__ ListParams P, int dl) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t blk = blockIdx.x;
+  const ListLevel& L = P.lev[list_level(P, blk)];
+  const int64_t o = (blk - L.blk0) * kListBlock + threadIdx.x;
+  if (o >= L.n_oct) return;
+  int32_t r = -1;
+  if (L.slotL_far) {
+    const int32_t par = L.oct_parent[o];
+    int32_t g = -1;
+    if (par >= 0 && par < 8 * L.n_oct_up) g = dl == 1 ? par : L.oct_parent_up[par >> 3];
+    if (g >= 0 && g < 8 * L.n_oct_far) {
+      const int32_t s = L.slotL_far[g >> 3];
+      r = s < 0 ? -1 : 8 * s + (g & 7);
+    }
+  }
+  L.lslot[o] = r;
+}
+
 // Ancestor lists of level d: the octs of each level b < d with a descendant
 // oct at level d.  Every level-d oct walks up its parent chain; the first
 // walker to reach an oct sets its visited flag, appends it to its level's
@@ -408,6 +462,8 @@ struct AncParams {
 };
 
 __global__ void k_anc_walk(const __grid_constant__ AncParams A, int64_t n_oct_d) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (o >= n_oct_d) return;
   int32_t cur = (int32_t)o;
@@ -499,6 +555,7 @@ fmm_status tree_prepare(Ctx* c) {
     CK(buf_ensure(c, T.irows, T.n_oct * 4));
     CK(buf_ensure(c, T.leafmask, T.n_oct));
     CK(buf_ensure(c, T.slotL, T.n_oct * 4));
+    CK(buf_ensure(c, T.lslot, T.n_oct * 4));
     CK(buf_ensure(c, T.anc, T.n_oct * 4));
   }
   {
@@ -563,10 +620,10 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     if (l == lmin && place_base) {
       CK(cudaMemsetAsync(T.cell_child.ptr, 0x80, T.n_oct * 32, st));
       ++c->n_launch;
-      k_place_complete<<<nblk(n), 256, 0, st>>>(l, T.n_leaf, n_ref, 8 * T.n_oct, (const int32_t*)T.ijk.ptr,
+      CK(launch_pdl(k_place_complete, nblk(n), 256, 0, st, l, T.n_leaf, n_ref, 8 * T.n_oct, (const int32_t*)T.ijk.ptr,
                                                 (const double*)T.mass.ptr,
                                                 n_ref ? (const uint64_t*)c->lev[l + 1].oct_key.ptr : nullptr,
-                                                (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next, err);
+                                                (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next, err));
       continue;
     }
     uint64_t* ka = (uint64_t*)c->keys_a.ptr;
@@ -575,13 +632,13 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     int32_t* vb = (int32_t*)c->vals_b.ptr;
     if (T.n_leaf) {
       ++c->n_launch;
-      k_leaf_keys<<<nblk(T.n_leaf), 256, 0, st>>>(T.n_leaf, (const int32_t*)T.ijk.ptr,
-                                                  (const double*)T.mass.ptr, l, ka, va, err);
+      CK(launch_pdl(k_leaf_keys, nblk(T.n_leaf), 256, 0, st, T.n_leaf, (const int32_t*)T.ijk.ptr,
+                                                  (const double*)T.mass.ptr, l, ka, va, err));
     }
     if (n_ref) {
       ++c->n_launch;
-      k_refined_keys<<<nblk(n_ref), 256, 0, st>>>(n_ref, (const uint64_t*)c->lev[l + 1].oct_key.ptr,
-                                                  ka + T.n_leaf, va + T.n_leaf);
+      CK(launch_pdl(k_refined_keys, nblk(n_ref), 256, 0, st, n_ref, (const uint64_t*)c->lev[l + 1].oct_key.ptr,
+                                                  ka + T.n_leaf, va + T.n_leaf));
     }
     size_t tmp = c->sort_tmp.bytes;
     ++c->n_cub;
@@ -589,14 +646,14 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     int32_t* flags = (int32_t*)c->flags.ptr;
     int32_t* scan = (int32_t*)c->scan.ptr;
     ++c->n_launch;
-    k_oct_flags<<<nblk(n), 256, 0, st>>>(n, kb, flags, err);
+    CK(launch_pdl(k_oct_flags, nblk(n), 256, 0, st, n, kb, flags, err));
     tmp = c->sort_tmp.bytes;
     ++c->n_cub;
     CK(cub::DeviceScan::InclusiveSum(c->sort_tmp.ptr, tmp, flags, scan, (int)n, st));
     ++c->n_launch;
-    k_scatter_level<<<nblk(n), 256, 0, st>>>(n, T.n_oct, kb, vb, scan, (uint64_t*)T.oct_key.ptr,
+    CK(launch_pdl(k_scatter_level, nblk(n), 256, 0, st, n, T.n_oct, kb, vb, scan, (uint64_t*)T.oct_key.ptr,
                                              (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next,
-                                             n_ref, T.n_leaf, partial && l == lo, err);
+                                             n_ref, T.n_leaf, partial && l == lo, err));
   }
   // ---- complete grids: levels 1..lmin-1, and the parents and neighbours of the
   // level-lmin octs (one launch); the root cell ------------------------------------
@@ -615,7 +672,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     }
     P.oct0[lmin + 1] = tot;
     ++c->n_launch;
-    k_complete_levels<<<nblk(tot), 256, 0, st>>>(P);
+    CK(launch_pdl(k_complete_levels, nblk(tot), 256, 0, st, P));
     CK(cudaMemsetAsync(c->lev[0].cell_child.ptr, 0, 4, st));
   }
   // ---- neighbour tables above the complete levels, top-down (levels below lo
@@ -626,9 +683,9 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     const int32_t* cc_up = (const int32_t*)c->lev[l - 1].cell_child.ptr;
     const int64_t n_up = c->lev[l - 1].n_oct;
     ++c->n_launch;
-    k_nbr<<<nblk(T.n_oct * 27), 256, 0, st>>>(l, T.n_oct, n_up, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
+    CK(launch_pdl(k_nbr, nblk(T.n_oct * 27), 256, 0, st, l, T.n_oct, n_up, (const int32_t*)T.oct_parent.ptr, nbr_up, cc_up,
                                               (const int32_t*)T.cell_child.ptr, (int32_t*)T.nbr.ptr,
-                                              c->d_err + kErrNbr0 + l);
+                                              c->d_err + kErrNbr0 + l));
   }
   // ---- row lists (a partial build changes the lists of levels lo-1..lmax only) ----
   const int list0 = partial ? lo - 1 : 1;
@@ -659,17 +716,24 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
       L.want_rowsL = l + 2 - m1 <= lmax;
       L.rowsL_refined = m1;
       L.want_irows = l >= lmin;
+      L.oct_parent = (const int32_t*)T.oct_parent.ptr;
+      L.oct_parent_up = l >= 2 ? (const int32_t*)c->lev[l - 1].oct_parent.ptr : nullptr;
+      L.slotL_far = l - (2 - m1) >= 2 ? (const int32_t*)c->lev[l - (2 - m1)].slotL.ptr : nullptr;
+      L.lslot = (int32_t*)T.lslot.ptr;
+      L.n_oct_up = l >= 2 ? c->lev[l - 1].n_oct : 0;
+      L.n_oct_far = l - (2 - m1) >= 1 ? c->lev[l - (2 - m1)].n_oct : 0;
       nb += (T.n_oct + kListBlock - 1) / kListBlock;
     }
     P.n_blocks = nb;
     uint8_t* fl = (uint8_t*)c->flags.ptr;            // nb * kListBlock bytes
     int32_t* blk_counts = (int32_t*)c->scan.ptr;     // nb * 4
     int32_t* blk_off = blk_counts + nb * 4;          // nb * 4
-    c->n_launch += 4;
-    k_leafmasks<<<(unsigned)nb, kListBlock, 0, st>>>(P);
-    k_lists_count<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_counts);
-    k_lists_scan<<<(unsigned)(4 * P.nlev), 1024, 0, st>>>(P, blk_counts, blk_off, d_counts);
-    k_lists_write<<<(unsigned)nb, kListBlock, 0, st>>>(P, fl, blk_off);
+    c->n_launch += 5;
+    CK(launch_pdl(k_leafmasks, (unsigned)nb, kListBlock, 0, st, P));
+    CK(launch_pdl(k_lists_count, (unsigned)nb, kListBlock, 0, st, P, fl, blk_counts));
+    CK(launch_pdl(k_lists_scan, (unsigned)(4 * P.nlev), 1024, 0, st, P, blk_counts, blk_off, d_counts));
+    CK(launch_pdl(k_lists_write, (unsigned)nb, kListBlock, 0, st, P, fl, blk_off));
+    CK(launch_pdl(k_lslots, (unsigned)nb, kListBlock, 0, st, P, 2 - m1));
   }
   // ---- ancestor lists of level anc_req (incremental solves) ------------------------
   const int d = c->anc_req;
@@ -689,7 +753,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
     A.counts = d_counts + 4 * (lmax + 2);
     CK(cudaMemsetAsync(A.flags, 0, off, st));
     ++c->n_launch;
-    k_anc_walk<<<nblk(c->lev[d].n_oct), 256, 0, st>>>(A, c->lev[d].n_oct);
+    CK(launch_pdl(k_anc_walk, nblk(c->lev[d].n_oct), 256, 0, st, A, c->lev[d].n_oct));
   }
   return FMM_OK;
 }

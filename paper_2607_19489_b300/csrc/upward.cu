@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_leaf_rows(int64_t n, int nc, const int3
     for (int k = lane; k < nc; k += 32) {
       const Tout v = k == 0 ? m : (Tout)0;
       M[row + k] = v;
-      if (hi) put_operand(v, hi, lo, row + k);
+      if (hi) put_operand(v, hi, lo, op_index(o * 8 + c, k, nc));
     }
   }
 }
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
       if (k < nc) {
         const float v = (u < 4 ? wk[u] : w0[k]) * sv;
         Mout[cell * nc + k] = v;
-        if (hi) put_operand(v, hi, lo, cell * nc + k);
+        if (hi) put_operand(v, hi, lo, op_index(cell, k, nc));
         if (k == 0) mono[cell] = v;
       }
     }
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
     float out = 0;
     for (int j = off[k]; j < off[k + 1]; ++j) out += cf[j] * S[gx[j]];
     Mout[cell * nc + k] = out;
-    if (hi) put_operand(out, hi, lo, cell * nc + k);
+    if (hi) put_operand(out, hi, lo, op_index(cell, k, nc));
     if (k == 0) mono[cell] = out;
   }
 }
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(128) k_m2m_block(
     for (int j = off[k]; j < off[k + 1]; ++j) v += cf[j] * S[gx[j]];
     const Tout w = (Tout)v;
     Mout[cell * nc + k] = w;
-    if (hi) put_operand(w, hi, lo, cell * nc + k);
+    if (hi) put_operand(w, hi, lo, op_index(cell, k, nc));
     if (k == 0) mono[cell] = (TMono)w;
   }
 }
@@ -296,7 +296,9 @@ __global__ void __launch_bounds__(128) k_m2m_block(
 inline size_t m2m_block_smem(int nc, int npairs) { return (size_t)8 * nc * 8 + (size_t)npairs * 12 + (nc + 1) * 4; }
 
 // Downward step for the row octs of level b: L = L2L(parent's L) + this level's
-// M2L sum (accumulated by the contraction in FP32, added here in FP64).
+// M2L sum (accumulated by the contraction in FP32, added here in FP64).  A
+// slot's M2L sums are in the contraction's column order: (cell c, beta) sits at
+// lmcol[c nc + beta].
 // One thread per output coefficient beta, all 8 children at once; the pair
 // tables and the parent's expansion are staged in shared memory (dynamic:
 // l2l_smem), since these small levels are latency-bound.
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
                                                  const int32_t* __restrict__ slot, const int32_t* __restrict__ slot_up,
                                                  const double* __restrict__ Lup, float* __restrict__ Lm,
                                                  double* __restrict__ L, float* __restrict__ Lf,
-                                                 const int* __restrict__ poff8,
+                                                 const int* __restrict__ lmcol, const int* __restrict__ poff8,
                                                  const int* __restrict__ pg, const double* __restrict__ pc) {
   pdl_wait();
   pdl_trigger();
@@ -339,10 +341,11 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
     for (int c = 0; c < 8; ++c) {
       const int64_t idx = (so * 8 + c) * nc + b;
       if (Lm) {
-        const double v = acc[c] + (double)Lm[idx];
+        const int64_t im = so * 8 * nc + lmcol[c * nc + b];
+        const double v = acc[c] + (double)Lm[im];
         L[idx] = v;
         Lf[idx] = (float)v;  // converted once here rather than by every target of the near field
-        Lm[idx] = 0.0f;      // the M2L contraction adds into a cleared slot next time
+        Lm[im] = 0.0f;       // the M2L contraction adds into a cleared slot next time
       } else {
         L[idx] = acc[c];
       }
@@ -352,12 +355,175 @@ __global__ void __launch_bounds__(128) k_l2l_add(int nc, int npairs, const int32
 
 inline size_t l2l_smem(int nc, int npairs) { return (size_t)nc * 8 + (size_t)npairs * 12 + (8 * nc + 1) * 4; }
 
+// Downward pass of the mixed paths in one launch.  Only the levels whose local
+// expansions the near field evaluates (target level minus 2; bottom mode 1:
+// minus 1) get blocks, one per row oct.  A block walks the path from its level-2
+// ancestor cell down to its own oct, L(cell_k) = L2L(L(cell_{k-1})) + M2L sum,
+// one cell per level, then all eight cells of its own oct.  L2L is exact, so
+// the result is the level-by-level chain's; the ancestors' expansions are
+// recomputed by every block that needs them instead of being handed down
+// between launches, which leaves one launch and no waits between blocks.  The
+// eight S_e sums of a step serve all children alike (see k_l2l_add); a path
+// step keeps one child, y = sum_e sign(c, e) S_e with
+// sign(c, e) = (-1)^popc(e & ~c) (the back transform of one output).  The M2L
+// sums are read, not cleared: k_zero_segments clears them before the next M2L.
+// FP32 throughout: the M2L sums come from the tensor-core contraction in FP32
+// and the near field evaluates an FP32 copy, and FP64 on this part runs about
+// two DFMA per clock per SM, which made the FP64 chain latency-bound on its
+// dependent pair sums; the output is the FP32 expansion the near field reads.
+struct L2LPathSeg {
+  const int32_t* rows;  // row octs of this level
+  int64_t n;
+  int blk0, level;
+};
+struct L2LPathParams {
+  L2LPathSeg seg[kMaxLevel];
+  int nseg, nc, npairs, max_level;
+  const int32_t* oct_parent[kMaxLevel + 1];
+  const int32_t* slotL[kMaxLevel + 1];
+  const float* Lm[kMaxLevel + 1];  // M2L sums, per slot in the contraction's column order (lmcol)
+  float* Lf[kMaxLevel + 1];
+  const int* lmcol;
+  const int* poff8;
+  const int* pg;
+  const float* pc;
+};
+
+constexpr int kPathThreads = 128;
+
+// S_e[beta] of the expansion Lp for one beta, all eight patterns
+__device__ __forceinline__ void l2l_sums(int beta, const float* Lp, const float* cf, const int* gg,
+                                         const int* off, float (&s)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    float v = 0.f;
+    for (int j = off[beta * 8 + e]; j < off[beta * 8 + e + 1]; ++j) v = fmaf(cf[j], Lp[gg[j]], v);
+    s[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant__ L2LPathParams P) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int nc = P.nc, np = P.npairs;
+  float* cf = (float*)dsm;                    // [np]
+  int* gg = (int*)(cf + np);                  // [np]
+  int* off = gg + np;                         // [8 nc + 1]
+  float* Lp = (float*)(off + 8 * nc + 1);     // [nc] expansion of the current path cell
+  float* Lmp = Lp + nc;                       // [max_level - 2][nc] M2L sums of the path cells
+  __shared__ int32_t s_row[kMaxLevel + 1];    // row (8 slot + cell) of the path cell at level k
+  __shared__ int s_pos[kMaxLevel + 1];        // its position in its oct
+  int si = 0;
+  while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].blk0) ++si;
+  const L2LPathSeg& S = P.seg[si];
+  const int b = S.level;
+  // tree data and tables (written before this solve): read before the wait
+  const int32_t o = S.rows[blockIdx.x - S.blk0];
+  const int64_t so = P.slotL[b][o];
+  if (threadIdx.x == 0) {
+    int32_t cell = b > 2 ? P.oct_parent[b][o] : 0;
+    for (int k = b - 1; k >= 2; --k) {
+      const int32_t oc = cell >> 3;
+      s_row[k] = P.slotL[k][oc] * 8 + (cell & 7);
+      s_pos[k] = cell & 7;
+      if (k > 2) cell = P.oct_parent[k][oc];
+    }
+  }
+  if (b > 2) {
+    stage_block<8>(np, [&](int j) { return P.pc[j]; }, cf);
+    stage_block<8>(np, [&](int j) { return P.pg[j]; }, gg);
+    stage_block<6>(8 * nc + 1, [&](int k) { return P.poff8[k]; }, off);
+  }
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  // the M2L sums: the path's (levels 2..b-1) to shared memory, the own oct's to registers
+  for (int k = 2; k < b; ++k)
+    for (int j = threadIdx.x; j < nc; j += kPathThreads)
+      Lmp[(k - 2) * nc + j] = P.Lm[k][(int64_t)(s_row[k] >> 3) * 8 * nc + __ldg(P.lmcol + (s_row[k] & 7) * nc + j)];
+  float own[2][8];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int beta = threadIdx.x + r * kPathThreads;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) own[r][c] = beta < nc ? P.Lm[b][so * 8 * nc + __ldg(P.lmcol + c * nc + beta)] : 0.f;
+  }
+  __syncthreads();
+  if (b > 2)
+    for (int j = threadIdx.x; j < nc; j += kPathThreads) Lp[j] = Lmp[j];  // level 2: the M2L sum alone
+  __syncthreads();
+  for (int k = 3; k < b; ++k) {
+    const unsigned nc_pos = ~(unsigned)s_pos[k] & 7u;
+    float v[2] = {0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int beta = threadIdx.x + r * kPathThreads;
+      if (beta >= nc) continue;
+      float s[8];
+      l2l_sums(beta, Lp, cf, gg, off, s);
+      float y = Lmp[(k - 2) * nc + beta];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) y += (__popc((unsigned)e & nc_pos) & 1) ? -s[e] : s[e];
+      v[r] = y;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int beta = threadIdx.x + r * kPathThreads;
+      if (beta < nc) Lp[beta] = v[r];
+    }
+    __syncthreads();
+  }
+  // the own oct: all eight cells
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int beta = threadIdx.x + r * kPathThreads;
+    if (beta >= nc) continue;
+    float acc[8];
+    if (b > 2) {
+      l2l_sums(beta, Lp, cf, gg, off, acc);
+      sign_transform_back(acc);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) P.Lf[b][(so * 8 + c) * nc + beta] = acc[c] + own[r][c];
+  }
+}
+
+inline size_t l2l_path_smem(int nc, int npairs, int max_level) {
+  return (size_t)npairs * 8 + (size_t)(8 * nc + 1) * 4 + (size_t)nc * 4 +
+         (size_t)std::max(max_level - 2, 0) * nc * 4;
+}
+
+// Clears float4 ranges of several buffers in one launch (the M2L sums of every
+// level before the contraction adds into them).
+struct ZeroSegs {
+  float4* p[kMaxLevel + 1];
+  int64_t end[kMaxLevel + 1];  // cumulative float4 counts
+  int n;
+};
+__global__ void k_zero_segments(const __grid_constant__ ZeroSegs Z) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t total = Z.end[Z.n - 1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (i >= Z.end[k]) ++k;
+    Z.p[k][i - (k ? Z.end[k - 1] : 0)] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
 }  // namespace
 
 // Kernel attributes set once per context creation (not inside a stream capture):
 // the FP32 M2M needs more than 48 KB of dynamic shared memory at p = 8.
 fmm_status upward_init(Ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2m_smem(165, 3003));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_l2l_path, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)l2l_path_smem(165, 3003, kMaxLevel));
+
   if (e != cudaSuccess) {
     c->last_error = std::string("upward_init: ") + cudaGetErrorString(e);
     return FMM_ERR_CUDA;
@@ -435,6 +601,56 @@ void launch_upward(Ctx* c, int b, cudaStream_t st, const int32_t* octs, int64_t 
   }
 }
 
+void launch_l2l_path(Ctx* c, int lo, cudaStream_t st) {
+  const int m1 = c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P;
+  const int top = top_local_level(c);
+  L2LPathParams P{};
+  int blocks = 0;
+  for (int b = std::max(2, lo - (2 - m1)); b <= top; ++b) {
+    LevelTree& T = c->lev[b];
+    if (!T.n_rowsL) continue;
+    L2LPathSeg& S = P.seg[P.nseg++];
+    S.rows = (const int32_t*)T.rowsL.ptr;
+    S.n = T.n_rowsL;
+    S.blk0 = blocks;
+    S.level = b;
+    blocks += (int)T.n_rowsL;
+    P.max_level = b;
+  }
+  if (!blocks) return;
+  for (int k = 2; k <= P.max_level; ++k) {
+    LevelTree& T = c->lev[k];
+    P.oct_parent[k] = (const int32_t*)T.oct_parent.ptr;
+    P.slotL[k] = (const int32_t*)T.slotL.ptr;
+    P.Lm[k] = (const float*)T.Lm.ptr;
+    P.Lf[k] = (float*)T.Lf.ptr;
+  }
+  P.nc = c->tab.nc;
+  P.npairs = (int)c->tab.l2l_g.size();
+  P.lmcol = (const int*)c->op_m2l.colmap.ptr;
+  P.poff8 = (const int*)c->d_l2l_off8.ptr;
+  P.pg = (const int*)c->d_l2l_g.ptr;
+  P.pc = (const float*)c->d_l2l_c32.ptr;
+  ++c->n_launch;
+  launch_pdl(k_l2l_path, (unsigned)blocks, kPathThreads, l2l_path_smem(P.nc, P.npairs, P.max_level), st, P);
+}
+
+void launch_zero_lm(Ctx* c, cudaStream_t st) {
+  ZeroSegs Z{};
+  int64_t tot = 0;
+  for (int b = 2; b <= top_local_level(c); ++b) {
+    LevelTree& T = c->lev[b];
+    if (!T.n_rowsL || !T.Lm.ptr) continue;
+    tot += 8 * T.n_rowsL * c->tab.nc / 4;  // 8 cells x nc floats: a multiple of 8 floats
+    Z.p[Z.n] = (float4*)T.Lm.ptr;
+    Z.end[Z.n++] = tot;
+  }
+  if (!tot) return;
+  ++c->n_launch;
+  const unsigned g = (unsigned)std::min<int64_t>((tot + 255) / 256, 4 * c->num_sms);
+  launch_pdl(k_zero_segments, g, 256, 0, st, Z);
+}
+
 void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t nrows) {
   LevelTree& T = c->lev[b];
   if (!rows) {
@@ -448,7 +664,7 @@ void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t
       c->tab.nc, np, rows, (const int32_t*)T.oct_parent.ptr, (const int32_t*)T.slotL.ptr,
       b >= 3 ? (const int32_t*)c->lev[b - 1].slotL.ptr : nullptr, b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
       c->cfg.precision == FMM_FP64 ? nullptr : (float*)T.Lm.ptr, (double*)T.L.ptr, (float*)T.Lf.ptr,
-      (const int*)c->d_l2l_off8.ptr, (const int*)c->d_l2l_g.ptr, (const double*)c->d_l2l_c.ptr);
+      (const int*)c->op_m2l.colmap.ptr, (const int*)c->d_l2l_off8.ptr, (const int*)c->d_l2l_g.ptr, (const double*)c->d_l2l_c.ptr);
 }
 
 }  // namespace fmm
