@@ -50,7 +50,7 @@ NC = (P_ORDER + 1) * (P_ORDER + 2) * (P_ORDER + 3) // 6
 # DRAM bytes (read + write) of the stage-timed M2P launch (k_gemm_tc, in-order
 # solve, split-K from the built-in heuristic) of the headline workload, from one
 # ncu capture of that launch shape; None until captured for the current kernel.
-M2P_TRAFFIC_BYTES = None
+M2P_TRAFFIC_BYTES = 37021952
 # FP32 work per P2P interaction, the usual count for a softened-free gravity
 # pair (3 differences, r^2, rsqrt ~4, m/r, m/r^3, 4 accumulations)
 FLOP_PER_PAIR = 20
@@ -747,29 +747,39 @@ def leg_adjoint(args, torch, dev, stream, flush):
     rhs = sum(float((gm[l] * mass[k]).sum()) for k, l in enumerate(h.levels))
     fd = None
     if args.fd_cells > 0:
+        # forward differences: the loss is linear in the masses, so
+        # (L(m + h e_i) - L(m)) / h = dL/dm_i with no truncation error, and a step
+        # of the whole box's mass (h = 1; cells hold ~1e-7) keeps rounding small
+        t_fd = time.perf_counter()
         n_all = sum(h.n(l) for l in h.levels)
         offs = np.cumsum([0] + [h.n(l) for l in h.levels])
         picks = np.unique((W.uniform(41, 1, np.arange(args.fd_cells)) * n_all).astype(np.int64))
+        step = 1.0
+        s.update_masses(mass)
+        s.solve(out=out)
+        s.sync()
+        l0 = sum(float((w[l] * out[1][l]).sum()) for l in h.levels)
         errs = []
         for g in picks:
             k = int(np.searchsorted(offs, g, side="right") - 1)
             j = int(g - offs[k])
-            vals = []
-            for sgn in (1, -1):
-                mp = [m.clone() for m in mass]
-                mp[k][j] += sgn * 1e-6
-                s.set_levels(h.lmin, h.lmax, ijk, mp)
-                s.solve(out=out)
-                s.sync()
-                vals.append(sum(float((w[l] * out[1][l]).sum()) for l in h.levels))
+            mp = [m.clone() for m in mass]
+            mp[k][j] += step
+            s.update_masses(mp)
+            s.solve(out=out)
+            s.sync()
+            l1 = sum(float((w[l] * out[1][l]).sum()) for l in h.levels)
             ad = float(gm[h.lmin + k][j])
-            errs.append(abs((vals[0] - vals[1]) / 2e-6 - ad) / max(abs(ad), 1e-300))
-        fd = {"cells": int(len(picks)), "h": 1e-6, "max_rel_err": float(max(errs))}
+            errs.append(abs((l1 - l0) / step - ad) / max(abs(ad), 1e-300))
+        s.update_masses(mass)
+        fd = {"cells": int(len(picks)), "h": step, "kind": "forward differences (exact for the linear map)",
+              "max_rel_err": float(max(errs)), "median_rel_err": float(np.median(errs)),
+              "wall_s": time.perf_counter() - t_fd}
     res = {"workload": "nested two-Plummer 128^3 + 2 refined levels (central 1/4 and 1/16 volumes), p=6 FP64",
            "finite_differences": fd,
            "cells": h.n_cells, "forward_ms": ms_fwd, "adjoint_ms": ms_adj, "adjoint_over_forward": ms_adj / ms_fwd,
            "dot_identity_rel": abs(lhs - rhs) / max(abs(lhs), 1e-300),
-           "check": "<w, accel(m)> = <dL/dm, m> (linear map); finite differences run in the GPU tests"}
+           "check": "<w, accel(m)> = <dL/dm, m> (linear map), and per-cell finite differences"}
     del s
     return res
 
@@ -814,6 +824,17 @@ def leg_ats(args, torch, dev, stream, flush):
     evs[-1].synchronize()
     per_solve = [{"lo": lo, "ms": evs[i].elapsed_time(evs[i + 1]),
                   "cells": sum(h.n(l) for l in range(lo, h.lmax + 1))} for i, lo in enumerate(sched)]
+    # in-order stage times of each kind of solve in the schedule (one rebuild + solve per lo)
+    s.set_timing(True)
+    stages = {}
+    for lo, ms in zip(sched, pert):
+        if lo in stages:
+            continue
+        s.set_levels(h.lmin, h.lmax, ijk[lo - h.lmin:], ms, lo=lo)
+        s.solve(lo, out=outs[lo])
+        s.sync()
+        stages[lo] = s.stage_times()
+    s.set_timing(False)
     s.set_levels(h.lmin, h.lmax, ijk, base)
     ms_full = _timed(torch, lambda: (s.set_levels(h.lmin, h.lmax, ijk, base), s.solve(out=outs[h.lmin])), K, 2, stream)
     s.sync()
@@ -833,7 +854,7 @@ def leg_ats(args, torch, dev, stream, flush):
     res = {"workload": h.name + ", p=6 mixed, FP32 outputs", "cells": h.n_cells,
            "levels": [h.n(l) for l in h.levels], "schedule_lo": sched,
            "value": updated / (ms_step * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms_step,
-           "per_solve": per_solve,
+           "per_solve": per_solve, "stages_ms_by_lo": {str(k): v for k, v in sorted(stages.items())},
            "cell_updates_per_coarse_step": updated, "full_rebuild_and_solve_ms": ms_full,
            "tuning": tuning, "generation_s": gen_s, "rel_rms_accel_mixed_vs_fp64": err_ats,
            "step": "per solve of the schedule: fmm_set_levels(lo) with perturbed masses + fmm_solve(lo)"}
@@ -891,8 +912,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="two_level", choices=sorted(WORKLOADS),
                     help="two_level: the measured configuration; unigrid16: a small check of the launch paths")
-    ap.add_argument("--fd-cells", type=int, default=0,
-                    help="adjoint leg: central finite differences on this many seeded cells (2 FP64 solves each)")
+    ap.add_argument("--fd-cells", type=int, default=100,
+                    help="adjoint leg: finite differences on this many seeded cells (one FP64 solve each)")
     ap.add_argument("--legs", default="sweep,batched,adjoint,ats,binary",
                     help="extra workloads reported beside the headline (comma list, or 'none')")
     ap.add_argument("--quick", action="store_true",
