@@ -342,8 +342,8 @@ def gpu_arm(args, rank, world, local):
     mass = [torch.as_tensor(m, device=dev).contiguous() for m in h.mass]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def make(precision):
-        s = fmm.Solver(P_ORDER, precision)
+    def make(precision, **kw):
+        s = fmm.Solver(P_ORDER, precision, **kw)
         s.set_levels(h.lmin, h.lmax, ijk, mass)
         out = s.alloc_outputs()
         return s, out
@@ -393,6 +393,23 @@ def gpu_arm(args, rank, world, local):
     mixed.sync()
     if fp64 is not None:
         fp64.sync()
+    # the option that keeps FP64 for the top-of-tree M2M and the L2L chain /
+    # local-expansion accumulation: same step, its time and accuracy
+    top64 = None
+    if fp64 is not None:
+        m64, out_t = make("mixed", fp64_top=True)
+
+        def step_top64():
+            m64.set_levels(h.lmin, h.lmax, ijk, mass)
+            m64.solve(out=out_t)
+
+        t_top = timed_steps(torch, step_top64, min(args.steps, 50), args.warmup, stream, flush)
+        m64.sync()
+        at = {l: out_t[1][l].cpu().numpy() for l in h.levels}
+        top64 = {"ms_per_step": statistics.mean(t_top), "value": world * n_cells / (statistics.mean(t_top) * 1e-3),
+                 "rel_rms_accel_vs_fp64": rel_rms(at, ad),
+                 "what": "config.fp64_top: FP64 M2M at box levels <= 3 and FP64 L2L / local-expansion accumulation"}
+        del m64
     barrier(dist)
 
     ms_mixed = reduce_max(statistics.mean(t_mixed), dist, dev)
@@ -445,6 +462,7 @@ def gpu_arm(args, rank, world, local):
                    "step": "fmm_set_levels (tree build) + fmm_solve", "l2": "flushed (256 MB write) before each step",
                    "parallelism": f"replicas x{world} (independent hierarchies)"},
         "fp64_gpu": {"value": value_fp64, "ms_per_step": ms_fp64, "speedup_mixed_over_fp64": value / value_fp64},
+        "mixed_fp64_top": top64,
         "accuracy": {"rel_rms_accel_mixed_vs_fp64": err_acc, "rel_rms_phi_mixed_vs_fp64": err_phi,
                      "bar": 1e-4},
         "solve_only": {"value": world * n_cells / (ms_solve * 1e-3), "ms": ms_solve},

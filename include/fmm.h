@@ -59,8 +59,9 @@ typedef enum {
 typedef enum {
   FMM_FP64 = 0,          /* every step in FP64 (DFMA) */
   FMM_MIXED_BF16X3 = 1,  /* M2L/M2P on tcgen05 tensor cores in split-BF16 (3 products,
-                            FP32 accumulation), P2P in FP32, FP64 for box levels <= 3
-                            of M2M, for L2L and for local-expansion accumulation */
+                            FP32 accumulation), everything else in FP32; with
+                            config.fp64_top the M2M of box levels <= 3 and the L2L
+                            chain with its local-expansion accumulation run in FP64 */
   FMM_MIXED_TF32 = 2     /* as FMM_MIXED_BF16X3, but M2L/M2P in one TF32 product per
                             term (tcgen05 kind::tf32, FP32 accumulation) */
 } fmm_precision;
@@ -89,6 +90,11 @@ typedef struct {
                          Terms with |alpha| > p_m are dropped from every translation. */
   int mass_fp32;      /* 0: masses passed to fmm_set_levels / fmm_update_masses are
                          double, 1: float (widened exactly to double on the device) */
+  int fp64_top;       /* mixed precisions: 1 keeps FP64 for the M2M of box levels <= 3
+                         and for the L2L chain and the accumulation of the local
+                         expansions; 0 runs them in FP32 (the default: on B300 the
+                         FP64 version costs ~20 % of a solve and, measured, gains no
+                         accuracy against the FP64 path).  Ignored by FMM_FP64. */
 } fmm_config;
 
 /* Device memory for the library, supplied by the caller (for instance a caching
@@ -184,12 +190,15 @@ fmm_status fmm_batch_solve(fmm_ctx* const* ctxs, int nctx, const int* lo, void* 
  * (mixed precision) and the target octs per block of the near-field kernel.
  * Synchronises `stream`.  The choices stay with the context (also for later
  * hierarchies) and are read back with fmm_get_tuning: out3 = {split M2P,
- * split M2L (0 = built-in heuristic), near-field octs per block}. */
+ * split M2L (0 = built-in heuristic), near-field octs per block}.  The split
+ * factors serve solves from the same lo only (a sub-cycle from a finer level
+ * has much smaller contractions and keeps the built-in choice); the
+ * octs-per-block choice serves every solve. */
 fmm_status fmm_autotune(fmm_ctx* ctx, int lo, void* stream);
 fmm_status fmm_get_tuning(const fmm_ctx* ctx, int* out3);
 /* Sets the same three values (for instance one autotuned context's choices on
- * the other contexts of a batch).  Unsupported octs-per-block values fall back
- * to the built-in choice. */
+ * the other contexts of a batch); values set here serve solves from every
+ * level.  Unsupported octs-per-block values fall back to the built-in choice. */
 fmm_status fmm_set_tuning(fmm_ctx* ctx, const int* in3);
 
 /* Adjoint of fmm_solve (not in the paper: the exact transpose of its linear

@@ -327,10 +327,7 @@ fmm_status size_expansions(Ctx* c, cudaStream_t st) {
   for (int l = 1; l <= c->lmax; ++l) {
     LevelTree& T = c->lev[l];
     const int64_t ncell = 8 * T.n_oct;
-    // the mixed paths keep FP32 multipoles at every level: they enter the
-    // contractions as split-BF16 or TF32 operands, and FP64 shifts at the top
-    // levels measured no more accurate (relative RMS 3.49e-6 either way)
-    T.m_is_f64 = f64;
+    T.m_is_f64 = f64 || (c->cfg.fp64_top && l <= kTopLevelFP64);
     CKS(buf_ensure(c, T.mono, ncell * 8));
     if (l < c->lmax) {
       CKS(buf_ensure(c, T.M, ncell * nc * (T.m_is_f64 ? 8 : 4)));
@@ -606,6 +603,7 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_use
     return FMM_ERR_ARG;
   if (cfg->bottom_mode != FMM_BOTTOM_M2P && cfg->bottom_mode != FMM_BOTTOM_M2L_L2P) return FMM_ERR_ARG;
   if (cfg->mass_fp32 != 0 && cfg->mass_fp32 != 1) return FMM_ERR_ARG;
+  if (cfg->fp64_top != 0 && cfg->fp64_top != 1) return FMM_ERR_ARG;
   if (!std::isfinite(cfg->G)) return FMM_ERR_ARG;
   fmm_ctx* c = new fmm_ctx();
   c->cfg = *cfg;
@@ -823,6 +821,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   const bool f64 = c->cfg.precision == FMM_FP64;
   const int lmin = c->lmin, lmax = c->lmax;
   const int d = c->dirty_lo;  // lowest level changed since the last upward pass
+  c->cur_lo = lo;
   stage_event(c, 0, st);
   // 1. upward: leaf monopoles, then M2M from the finest level up.  After an
   // update of levels d..lmax only the cells with descendants at level d change
@@ -834,22 +833,10 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // A drifting solve recomputes every total from the masses, then adds the
   // drift of each stale tree (corrections must not stack from solve to solve).
   const bool drift = drift_active(c, lo);
-  if (!f64) launch_zero_lm(c, st);  // the M2L contraction adds into these sums
-  if (d <= lmin || (d <= lmax && c->anc_d != d) || drift) {
-    for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
-    for (int b = lmax - 1; b >= 2; --b) launch_upward(c, b, st);
-    if (drift) launch_drift(c, lo, st);
-  } else if (d <= lmax) {
-    for (int l = d; l <= lmax; ++l) launch_mono_leaves(c, l, st);
-    for (int b = lmax - 1; b >= d - 1; --b) launch_upward(c, b, st);
-    for (int b = d - 2; b >= 2; --b)
-      launch_upward(c, b, st, (const int32_t*)c->lev[b + 1].anc.ptr, c->lev[b + 1].n_anc);
-  }
-  stage_event(c, 1, st);
-  // 2. downward over box levels 2..top (top = lmax-2, or lmax-1 in bottom mode
-  // 1): L = L2L(parent) + M2L.  For targets at levels >= lo > lmin, the levels
-  // b <= lo-3 (lo-2 in mode 1) only feed the L2L chain of the ancestors of
-  // level lo: their ancestor lists replace the full row lists.
+  // Rows of the downward pass over box levels 2..top (top = lmax-2, or lmax-1
+  // in bottom mode 1): L = L2L(parent) + M2L.  For targets at levels >= lo >
+  // lmin, the levels b <= lo-3 (lo-2 in mode 1) only feed the L2L chain of the
+  // ancestors of level lo: their ancestor lists replace the full row lists.
   const int m1 = c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P;
   const int top = top_local_level(c);
   const bool restrict_dn = lo > lmin && c->anc_d == lo;
@@ -869,6 +856,25 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
     dr.push_back(drows[b]);
     dnr.push_back(dn[b]);
   }
+  if (!f64) launch_zero_lm(c, dl, dr, dnr, st);  // the M2L contraction adds into these sums
+  if (d <= lmin || (d <= lmax && c->anc_d != d) || drift) {
+    for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
+    for (int b = lmax - 1; b >= 2; --b) launch_upward(c, b, st);
+    if (drift) launch_drift(c, lo, st);
+  } else if (d <= lmax) {
+    for (int l = d; l <= lmax; ++l) launch_mono_leaves(c, l, st);
+    for (int b = lmax - 1; b >= d - 1; --b) launch_upward(c, b, st);
+    // ancestors: one launch per level while the lists are long, then the rest
+    // of the chain in one block (each list at most two rounds of its warps;
+    // lists only shrink towards the root)
+    const int w = m2m_chain_warps(c);
+    int b = d - 2;
+    for (; b >= 2 && (w == 0 || c->lev[b + 1].n_anc > 2 * w); --b)
+      launch_upward(c, b, st, (const int32_t*)c->lev[b + 1].anc.ptr, c->lev[b + 1].n_anc);
+    if (b >= 2) launch_m2m_chain(c, b, st);
+  }
+  stage_event(c, 1, st);
+  // 2. downward (below): the M2L rows of each box level
   // M2L of all box levels: one tcgen05 launch (mixed), or per level (FP64)
   auto m2l_tc = [&](cudaStream_t s2) {
     if (!dl.empty()) launch_gemm_tc(c, c->op_m2l, kModeM2L, dl.data(), (int)dl.size(), s2, dr.data(), dnr.data());
@@ -1207,6 +1213,7 @@ fmm_status fmm_autotune(fmm_ctx* c, int lo, void* stream) {
   c->timing = false;
   const int anc_d = c->anc_d;
   c->anc_d = 0;  // time the full passes
+  c->tune_lo = lo;  // the split factors tuned here serve solves from lo
   cudaEvent_t e0, e1;
   CKS(cudaEventCreate(&e0));
   CKS(cudaEventCreate(&e1));
@@ -1245,9 +1252,7 @@ fmm_status fmm_autotune(fmm_ctx* c, int lo, void* stream) {
     const std::vector<int> splits = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24};
     if (c->cfg.bottom_mode == FMM_BOTTOM_M2P) tune(&c->tune_split[0], splits);  // mode 1 runs no M2P
     tune(&c->tune_split[1], splits);
-    tune(&c->tune_opb, {16, 8, 4});
-  } else {
-    tune(&c->tune_opb, {8, 4});
+    tune(&c->tune_opb, {16, 8});
   }
   c->n_launch = n0;  // tuning runs are not the caller's solves
   cudaEventDestroy(e0);
@@ -1265,6 +1270,7 @@ fmm_status fmm_set_tuning(fmm_ctx* c, const int* in3) {
   c->tune_split[0] = in3[0];
   c->tune_split[1] = in3[1];
   c->tune_opb = in3[2];
+  c->tune_lo = -1;
   ++c->layout_gen;
   return FMM_OK;
 }

@@ -152,6 +152,7 @@ struct LevelTree {
   bool m_is_f64 = true;
 };
 
+constexpr int kTopLevelFP64 = 3;  // mixed precisions with fp64_top: box levels <= 3 use FP64 M2M
 constexpr int kTcBK = 32;  // K slice of the tensor-core contraction (elements per operand row per stage)
 
 struct GemmOperand {  // one operator for the GEMM kernels
@@ -250,6 +251,8 @@ struct Ctx {
   bool use_graphs = true;
   // launch shapes picked by fmm_autotune (0: built-in choice)
   int tune_split[2] = {0, 0};  // split-K of the tcgen05 contraction, [kModeM2P], [kModeM2L]
+  int tune_lo = -1;            // solves from this level use tune_split (-1: every level)
+  int cur_lo = 0;              // lo of the solve being enqueued
   int tune_opb = 0;            // target octs per block of the near-field kernel
   // translation tables shared with other contexts of the same device, p and precision
   bool tables_shared = false;
@@ -267,10 +270,15 @@ void launch_mono_leaves(Ctx* c, int level, cudaStream_t st);
 // octs / rows: optional lists restricting the pass (null: the full level)
 void launch_upward(Ctx* c, int level, cudaStream_t st, const int32_t* octs = nullptr, int64_t n_octs = 0);
 void launch_l2l_add(Ctx* c, int level, cudaStream_t st, const int32_t* rows = nullptr, int64_t nrows = 0);
+// partial upward passes: the ancestor M2M of levels b_top..2 in one block (short lists only)
+int m2m_chain_warps(const Ctx* c);
+void launch_m2m_chain(Ctx* c, int b_top, cudaStream_t st);
 // mixed paths: the whole L2L chain for the levels the near field of targets >= lo reads
 void launch_l2l_path(Ctx* c, int lo, cudaStream_t st);
-// mixed paths: clears the M2L sums of every level (before the contraction adds into them)
-void launch_zero_lm(Ctx* c, cudaStream_t st);
+// mixed paths: clears the M2L sums of the rows the next M2L writes (levels[i],
+// rows[i] / nrows[i]; null rows: the level's full list)
+void launch_zero_lm(Ctx* c, const std::vector<int>& levels, const std::vector<const int32_t*>& rows,
+                    const std::vector<int64_t>& nrows, cudaStream_t st);
 // gemm_f64.cu
 void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int level_rows, cudaStream_t st,
                      const int32_t* rows = nullptr, int64_t nrows = 0);

@@ -152,14 +152,17 @@ struct LatPair {
 
 // The pairs of one target, seen from position 0 through the mirrors of its own
 // position: load(slot) returns the mass at a lattice slot of the target's oct.
-// The row base (iy, iz) is added before the ix term so that six consecutive
-// pairs share it.
-template <int S, typename Load>
-__device__ __forceinline__ void lat_pair(const Load& load, const int (&AX)[6], const int (&AY)[6],
-                                         const int (&AZ)[6], float (&a)[2][4]) {
+// The x mirror MX is the same for a whole warp (the threads are laid out so),
+// which makes the x part of every slot a compile-time offset from the row base
+// (iy, iz): one add per six pairs, the loads take immediate offsets.
+template <int MX, int S, typename Load>
+__device__ __forceinline__ void lat_pair(const Load& load, const int (&AY)[6], const int (&AZ)[6],
+                                         float (&a)[2][4]) {
   using Q = LatPair<S>;
   if constexpr (Q::r2 != 0) {  // the target itself is not a source
-    const float m = load((AY[Q::iy] + AZ[Q::iz]) + AX[Q::ix]);
+    constexpr int jx = MX ? 5 - Q::ix : Q::ix;
+    constexpr int ox = 8 * (jx >> 1) + (jx & 1);
+    const float m = load((AY[Q::iy] + AZ[Q::iz]) + ox);
     float* r = a[S & 1];  // two accumulator sets: shorter FFMA dependency chains
     r[0] = fmaf(m, Q::kp, r[0]);
     r[1] = fmaf(m, Q::kx, r[1]);
@@ -168,10 +171,10 @@ __device__ __forceinline__ void lat_pair(const Load& load, const int (&AX)[6], c
   }
 }
 
-template <typename Load, int... S>
-__device__ __forceinline__ void lat_all(std::integer_sequence<int, S...>, const Load& load, const int (&AX)[6],
-                                        const int (&AY)[6], const int (&AZ)[6], float (&a)[2][4]) {
-  (lat_pair<S>(load, AX, AY, AZ, a), ...);
+template <int MX, typename Load, int... S>
+__device__ __forceinline__ void lat_all(std::integer_sequence<int, S...>, const Load& load, const int (&AY)[6],
+                                        const int (&AZ)[6], float (&a)[2][4]) {
+  (lat_pair<MX, S>(load, AY, AZ, a), ...);
 }
 
 
@@ -199,32 +202,43 @@ __device__ __forceinline__ void load4(const double* p, double& a, double& b, dou
   a = u.x; b = u.y; c = v.x; d = v.y;
 }
 
-// FP32: 896 threads per SM (72 registers, no spills); 64 and 80 registers
-// measured the same on the 64^3 + 32^3 workload at p = 6.
+// Thread layout: a pair of warps serves 8 target octs, warp 2k + x holding the
+// targets at x-position x of octs 8k..8k+7, lane 4 m + 2 y + z the target at
+// (x, y, z) of oct 8k + m.  The x mirror of the pair loop is then uniform per
+// warp.  For staging, thread ts = 4 x + (lane & 3) of an oct (0..7) owns the
+// neighbour slots q = ts + 8 j; each half (x = 0, 1) keeps its own list of
+// coarse-leaf / refined entries.  OPB (octs per block) is 8 or 16.
+// FP32: 896 threads per SM.
 template <typename T, int OPB, int PC>
 __global__ void __launch_bounds__(8 * OPB, sizeof(T) == 4 ? 112 / OPB : 1) k_near(const __grid_constant__ NearParams P) {
+  static_assert(OPB % 8 == 0, "a warp pair serves eight octs");
   __shared__ __align__(16) T s_m[OPB][216];
   // local expansion of the oct's level l-2 box (rows of ncoef(PC) when the order is fixed)
   constexpr int kNcL = PC > 0 ? (PC + 1) * (PC + 2) * (PC + 3) / 6 : kNcMax;
   __shared__ __align__(16) T s_L[OPB][kNcL];
   __shared__ int32_t s_nb[OPB][28];        // the 27 neighbour slots of the oct
-  __shared__ uint8_t s_spec[OPB][216];     // source slots that are coarse leaves or refined cells
-  __shared__ int s_nspec[OPB];
+  constexpr int kSpecHalf = 15 * 8;        // a half owns at most 15 slots
+  __shared__ uint8_t s_spec[OPB][2][kSpecHalf];  // source slots that are coarse leaves or refined cells
+  __shared__ int s_nspec[OPB][2];
   int si = 0;
   while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].blk0) ++si;
   const NearSeg& S = P.seg[si];
-  const int g = threadIdx.x >> 3, tp = threadIdx.x & 7;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tbx = warp & 1, tby = (lane >> 1) & 1, tbz = lane & 1;
+  const int g = (warp >> 1) * 8 + (lane >> 2);  // oct in the block
+  const int tp = tbx + 2 * tby + 4 * tbz;       // target position in the oct
+  const int ts = 4 * tbx + (lane & 3);          // staging index in the oct
   const int64_t gi = (int64_t)(blockIdx.x - S.blk0) * OPB + g;
   const bool oct_ok = gi < S.n_tgt;
   // ---- tree data (written by the tree build, before this solve): read before
   // the wait on the previous kernel, all in three dependent rounds ----
   const int32_t o = oct_ok ? S.tgt[gi] : 0;
   const int64_t cell = (int64_t)o * 8 + tp;
-  // thread tp owns neighbour slots q = tp + 8 j (j < 4, q < 27)
+  // thread ts owns neighbour slots q = ts + 8 j (j < 4, q < 27)
   int32_t nbq[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int q = tp + 8 * j;
+    const int q = ts + 8 * j;
     nbq[j] = (oct_ok && q < 27) ? S.nbr[(int64_t)o * 27 + q] : -1;
   }
   const int32_t self = oct_ok ? S.cc_l[cell] : 0;
@@ -233,27 +247,27 @@ __global__ void __launch_bounds__(8 * OPB, sizeof(T) == 4 ? 112 / OPB : 1) k_nea
   unsigned lm[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) lm[j] = nbq[j] >= 0 ? (unsigned)S.leafmask[nbq[j]] : 0xFFu;
-  // entries of the coarse-leaf / refined list: refined cells of each level-l
+  // entries of the coarse-leaf / refined lists: refined cells of each level-l
   // neighbour oct, one per level l-1 leaf; placed by an exclusive scan over
-  // the oct's eight lanes (a fixed order)
+  // the half's four lanes (a fixed order)
   int cnt = 0;
 #pragma unroll
   for (int j = 0; j < 4; ++j) cnt += nbq[j] >= 0 ? 8 - __popc(lm[j]) : (nbq[j] <= -2 ? 1 : 0);
   int incl = cnt;
 #pragma unroll
-  for (int d = 1; d < 8; d <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, d, 8);
-    if (tp >= d) incl += y;
+  for (int d = 1; d < 4; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d, 4);
+    if ((lane & 3) >= d) incl += y;
   }
   int pos = incl - cnt;
-  if (tp == 7) s_nspec[g] = incl;
+  if ((lane & 3) == 3) s_nspec[g][tbx] = incl;
   pdl_wait();
   pdl_trigger();
   // ---- masses, the M2P accumulator and the local expansion (this solve) ----
   const T* mono_l = (const T*)S.mono_l;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int q = tp + 8 * j;
+    const int q = ts + 8 * j;
     if (q >= 27) break;
     const int32_t nb = nbq[j];
     T m[8];
@@ -263,12 +277,12 @@ __global__ void __launch_bounds__(8 * OPB, sizeof(T) == 4 ? 112 / OPB : 1) k_nea
       for (int cc = 0; cc < 8; ++cc) {
         if ((lm[j] >> cc) & 1) continue;
         m[cc] = (T)0;  // a refined cell: nearest field or near-field M2P
-        s_spec[g][pos++] = (uint8_t)(q * 8 + cc);
+        s_spec[g][tbx][pos++] = (uint8_t)(q * 8 + cc);
       }
     } else {
 #pragma unroll
       for (int cc = 0; cc < 8; ++cc) m[cc] = (T)0;
-      if (nb <= -2) s_spec[g][pos++] = (uint8_t)(q * 8);  // a level l-1 leaf, once
+      if (nb <= -2) s_spec[g][tbx][pos++] = (uint8_t)(q * 8);  // a level l-1 leaf, once
     }
 #pragma unroll
     for (int cc = 0; cc < 8; ++cc) s_m[g][q * 8 + cc] = m[cc];
@@ -277,11 +291,10 @@ __global__ void __launch_bounds__(8 * OPB, sizeof(T) == 4 ? 112 / OPB : 1) k_nea
   T pm = 0, xm = 0, ym = 0, zm = 0;
   if (oct_ok && self < 0) load4((const T*)S.acc + cell * 4, pm, xm, ym, zm);
   if (lrow >= 0)
-    for (int b = tp; b < P.nc; b += 8) s_L[g][b] = ((const T*)S.L2)[(int64_t)lrow * P.nc + b];
+    for (int b = ts; b < P.nc; b += 8) s_L[g][b] = ((const T*)S.L2)[(int64_t)lrow * P.nc + b];
   __syncthreads();
   if (!oct_ok) return;
   if (self >= 0) return;  // refined: not a target of this level
-  const int tbx = tp & 1, tby = (tp >> 1) & 1, tbz = (tp >> 2) & 1;
   const T tx = (T)tbx, ty = (T)tby, tz = (T)tbz;
   T phi = 0, ax = 0, ay = 0, az = 0;
   // ---- P2P with the level-l leaves of the 3^3 neighbour octs ----
@@ -292,17 +305,19 @@ __global__ void __launch_bounds__(8 * OPB, sizeof(T) == 4 ? 112 / OPB : 1) k_nea
     // FP32: position 0's pairs at this position's mirrored slots, compile-time
     // coefficients (see LatPair); slot of lattice index j = 2 q + bit per axis:
     // 8 (9 qz + 3 qy + qx) + 4 bz + 2 by + bx
-    int AX[6], AY[6], AZ[6];
+    int AY[6], AZ[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-      const int jx = tbx ? 5 - i : i, jy = tby ? 5 - i : i, jz = tbz ? 5 - i : i;
-      AX[i] = 8 * (jx >> 1) + (jx & 1);
+      const int jy = tby ? 5 - i : i, jz = tbz ? 5 - i : i;
       AY[i] = 24 * (jy >> 1) + 2 * (jy & 1);
       AZ[i] = 72 * (jz >> 1) + 4 * (jz & 1);
     }
     float a[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
     auto load = [&](int slot) { return (float)s_m[g][slot]; };  // indexed directly: shared-memory loads
-    lat_all(std::make_integer_sequence<int, 216>{}, load, AX, AY, AZ, a);
+    if (tbx)  // warp-uniform
+      lat_all<1>(std::make_integer_sequence<int, 216>{}, load, AY, AZ, a);
+    else
+      lat_all<0>(std::make_integer_sequence<int, 216>{}, load, AY, AZ, a);
     phi = (T)(a[0][0] + a[1][0]);
     ax = (T)(tbx ? -(a[0][1] + a[1][1]) : a[0][1] + a[1][1]);
     ay = (T)(tby ? -(a[0][2] + a[1][2]) : a[0][2] + a[1][2]);
@@ -342,10 +357,9 @@ __global__ void __launch_bounds__(8 * OPB, sizeof(T) == 4 ? 112 / OPB : 1) k_nea
   }
   }
   // ---- coarse leaves and refined cells (coarse-fine interfaces only) ----
-  const T* nearop = (const T*)P.nearop;
-  const int nspec = s_nspec[g];
+  const int nspec0 = s_nspec[g][0], nspec = nspec0 + s_nspec[g][1];
   for (int k = 0; k < nspec; ++k) {
-    const int s = s_spec[g][k];
+    const int s = k < nspec0 ? s_spec[g][0][k] : s_spec[g][1][k - nspec0];
     const int32_t nb = s_nb[g][s >> 3];
     if (nb <= -2) {  // coarse leaf of level l-1: centre at 2 dq + 1
       const T m = ((const T*)S.mono_up)[-2 - (int64_t)nb];
@@ -633,11 +647,11 @@ void near_dispatch(int p, unsigned blocks, cudaStream_t st, const NearParams& P)
 
 }  // namespace
 
-int near_opb(const Ctx* c) {
+int near_opb(const Ctx* c) {  // a pair of warps serves eight octs: 8 or 16 per block
   const bool f64 = c->cfg.precision == FMM_FP64;
   const int o = c->tune_opb;
-  if (f64) return (o == 4 || o == 8) ? o : 8;
-  return (o == 4 || o == 8 || o == 16) ? o : 16;
+  if (f64) return 8;
+  return (o == 8 || o == 16) ? o : 16;
 }
 
 void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_fp32, cudaStream_t st) {
@@ -686,14 +700,9 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
     ++c->n_launch;
     const int p = c->cfg.p;
     if (f64) {
-      if (opb == 4)
-        near_dispatch<double, 4>(p, (unsigned)blocks, st, P);
-      else
-        near_dispatch<double, 8>(p, (unsigned)blocks, st, P);
+      near_dispatch<double, 8>(p, (unsigned)blocks, st, P);
     } else {
-      if (opb == 4)
-        near_dispatch<float, 4>(p, (unsigned)blocks, st, P);
-      else if (opb == 8)
+      if (opb == 8)
         near_dispatch<float, 8>(p, (unsigned)blocks, st, P);
       else
         near_dispatch<float, 16>(p, (unsigned)blocks, st, P);

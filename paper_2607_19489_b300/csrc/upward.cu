@@ -295,6 +295,132 @@ __global__ void __launch_bounds__(128) k_m2m_block(
 
 inline size_t m2m_block_smem(int nc, int npairs) { return (size_t)8 * nc * 8 + (size_t)npairs * 12 + (nc + 1) * 4; }
 
+// The M2M chain of a partial upward pass (the ancestor octs of an updated
+// level), when every level's list is short: one block runs all those levels
+// in order, a barrier between levels, instead of one latency-bound launch per
+// level.  One warp per oct, as k_m2m's general path, with S in FP64 where the
+// output level keeps FP64 multipoles (the top of the tree) and FP32 below; the
+// pair tables are staged once.  A level's inputs that this block wrote one
+// level earlier are read at L2 (.cg) after the barrier.
+struct ChainLevel {            // M2M from the listed octs of level b+1 into their parents (level b)
+  const int32_t* octs;         // level b+1 octs (an ancestor list)
+  const int32_t* oct_parent;   // level b+1
+  const int32_t* cell_child;   // level b+1
+  const double* mass;          // level b+1 leaf masses
+  const void* Min;             // level b+1 rows (float, or double if in_f64)
+  void* Mout;                  // level b rows (float, or double if out_f64)
+  __nv_bfloat16* hi;           // level b operand rows, or null
+  __nv_bfloat16* lo;           // null for TF32
+  void* mono;                  // level b monopoles
+  int n, in_f64, out_f64;
+};
+struct ChainParams {
+  ChainLevel lev[kMaxLevel];
+  int nlev, nc, npairs;
+  const int* poff;
+  const int* pg;
+  const int* pe;
+  const double* pc;
+  const float* pc32;
+};
+
+inline size_t chain_smem(int nc, int npairs, int warps) {
+  return (size_t)npairs * 16 + (size_t)(nc + 1) * 4 + 16 + (size_t)warps * 8 * nc * 8;
+}
+constexpr size_t kChainSmemMax = 200 * 1024;
+
+template <typename TS>
+__device__ __forceinline__ TS chain_child(const ChainLevel& U, int nc, int64_t c0, const int32_t* wcc,
+                                          const double* wml, int idx) {
+  const int c = idx / nc, g = idx - c * nc;
+  const int64_t i = (c0 + c) * nc + g;
+  if (wcc[c] < 0) return g == 0 ? (TS)wml[c] : (TS)0;
+  return U.in_f64 ? (TS)__ldcg((const double*)U.Min + i) : (TS)__ldcg((const float*)U.Min + i);
+}
+
+// One general M2M of oct o (level b+1) into its parent by one warp; S: the
+// warp's [8][nc] staging area, in the output's precision.
+template <typename TS, typename TMono>
+__device__ __forceinline__ void chain_m2m(const ChainLevel& U, int nc, int64_t o, int lane, TS* S, int32_t* wcc,
+                                          double* wml, const int* off, const int* gx, const TS* cf) {
+  const int64_t cell = U.oct_parent[o];
+  const int64_t c0 = o * 8;
+  if (lane < 8) {
+    const int32_t ch = U.cell_child[c0 + lane];
+    wcc[lane] = ch;
+    wml[lane] = ch < 0 ? U.mass[-1 - (int64_t)ch] : 0.0;
+  }
+  __syncwarp();
+  for (int base = 0; base < 8 * nc; base += 32 * 8) {
+    TS r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + 32 * u + lane;
+      if (idx < 8 * nc) r[u] = chain_child<TS>(U, nc, c0, wcc, wml, idx);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + 32 * u + lane;
+      if (idx < 8 * nc) S[idx] = r[u];
+    }
+  }
+  __syncwarp();
+  for (int g = lane; g < nc; g += 32) {
+    TS x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = S[c * nc + g];
+    sign_transform(x);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) S[e * nc + g] = x[e];
+  }
+  __syncwarp();
+  for (int k = lane; k < nc; k += 32) {
+    TS out = 0;
+    for (int j = off[k]; j < off[k + 1]; ++j) out += cf[j] * S[gx[j]];
+    if (U.out_f64)
+      ((double*)U.Mout)[cell * nc + k] = (double)out;
+    else
+      ((float*)U.Mout)[cell * nc + k] = (float)out;
+    if (U.hi) put_operand(out, U.hi, U.lo, op_index(cell, k, nc));
+    if (k == 0) ((TMono*)U.mono)[cell] = (TMono)out;
+  }
+  __syncwarp();  // S and wcc are reused by the warp's next oct
+}
+
+template <typename TMono>
+__global__ void __launch_bounds__(1024) k_m2m_chain(const __grid_constant__ ChainParams P) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int nc = P.nc, np = P.npairs, warps = blockDim.x >> 5;
+  double* cf64 = (double*)dsm;            // [np]
+  float* cf32 = (float*)(cf64 + np);      // [np]
+  int* gx = (int*)(cf32 + np);            // [np]: gamma + nc * e
+  int* off = gx + np;                     // [nc + 1]
+  double* Sall = (double*)(((uintptr_t)(off + nc + 1) + 15) & ~(uintptr_t)15);  // [warps][8 nc]
+  __shared__ int32_t s_cc[32][8];
+  __shared__ double s_ml[32][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  stage_block<4>(np, [&](int j) { return P.pc[j]; }, cf64);
+  stage_block<4>(np, [&](int j) { return (float)P.pc[j]; }, cf32);
+  stage_block<4>(np, [&](int j) { return P.pg[j] + nc * P.pe[j]; }, gx);
+  stage_block<1>(nc + 1, [&](int j) { return P.poff[j]; }, off);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  for (int k = 0; k < P.nlev; ++k) {
+    const ChainLevel& U = P.lev[k];
+    for (int i = warp; i < U.n; i += warps) {
+      const int64_t o = U.octs[i];
+      if (U.out_f64)
+        chain_m2m<double, TMono>(U, nc, o, lane, Sall + (size_t)warp * 8 * nc, s_cc[warp], s_ml[warp], off, gx, cf64);
+      else
+        chain_m2m<float, TMono>(U, nc, o, lane, (float*)(Sall + (size_t)warp * 8 * nc), s_cc[warp], s_ml[warp], off,
+                                gx, cf32);
+    }
+    __threadfence_block();
+    __syncthreads();  // the next level reads these rows
+  }
+}
+
 // Downward step for the row octs of level b: L = L2L(parent's L) + this level's
 // M2L sum (accumulated by the contraction in FP32, added here in FP64).  A
 // slot's M2L sums are in the contraction's column order: (cell c, beta) sits at
@@ -366,11 +492,12 @@ inline size_t l2l_smem(int nc, int npairs) { return (size_t)nc * 8 + (size_t)npa
 // eight S_e sums of a step serve all children alike (see k_l2l_add); a path
 // step keeps one child, y = sum_e sign(c, e) S_e with
 // sign(c, e) = (-1)^popc(e & ~c) (the back transform of one output).  The M2L
-// sums are read, not cleared: k_zero_segments clears them before the next M2L.
-// FP32 throughout: the M2L sums come from the tensor-core contraction in FP32
-// and the near field evaluates an FP32 copy, and FP64 on this part runs about
-// two DFMA per clock per SM, which made the FP64 chain latency-bound on its
-// dependent pair sums; the output is the FP32 expansion the near field reads.
+// sums are read, not cleared: k_zero_rows clears them before the next M2L.
+// TA is the accumulation type: FP32 by default, FP64 with config.fp64_top (the
+// FP32 M2L sums are then added to the FP64 shifted parent).  Each (beta, e) sum
+// has a thread of its own: ~11 dependent pairs at p = 6 instead of the up to 84
+// a thread per beta chains (FP64 runs about two DFMA per clock per SM on B300).
+// Output: the FP32 expansion the near field reads.
 struct L2LPathSeg {
   const int32_t* rows;  // row octs of this level
   int64_t n;
@@ -386,38 +513,41 @@ struct L2LPathParams {
   const int* lmcol;
   const int* poff8;
   const int* pg;
-  const float* pc;
+  const void* pc;  // coefficients in TA
 };
 
-constexpr int kPathThreads = 128;
+constexpr int kPathThreads = 256;
 
-// S_e[beta] of the expansion Lp for one beta, all eight patterns
-__device__ __forceinline__ void l2l_sums(int beta, const float* Lp, const float* cf, const int* gg,
-                                         const int* off, float (&s)[8]) {
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    float v = 0.f;
-    for (int j = off[beta * 8 + e]; j < off[beta * 8 + e + 1]; ++j) v = fmaf(cf[j], Lp[gg[j]], v);
-    s[e] = v;
+// S[e][beta] of the expansion Lp for every (beta, e), one pair sum per thread
+template <typename TA>
+__device__ __forceinline__ void l2l_pattern_sums(int nc, const TA* Lp, const TA* cf, const int* gg,
+                                                 const int* off, TA* S) {
+  for (int i = threadIdx.x; i < 8 * nc; i += kPathThreads) {  // i = beta * 8 + e
+    TA v = 0;
+    const int j1 = off[i + 1];
+    for (int j = off[i]; j < j1; ++j) v = fma(cf[j], Lp[gg[j]], v);
+    S[(i & 7) * nc + (i >> 3)] = v;
   }
 }
 
+template <typename TA>
 __global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant__ L2LPathParams P) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int nc = P.nc, np = P.npairs;
-  float* cf = (float*)dsm;                    // [np]
-  int* gg = (int*)(cf + np);                  // [np]
+  TA* cf = (TA*)dsm;                          // [np]
+  TA* Lp = cf + np;                           // [nc] expansion of the current path cell
+  TA* S = Lp + nc;                            // [8][nc] pattern sums
+  int* gg = (int*)(S + 8 * nc);               // [np]
   int* off = gg + np;                         // [8 nc + 1]
-  float* Lp = (float*)(off + 8 * nc + 1);     // [nc] expansion of the current path cell
-  float* Lmp = Lp + nc;                       // [max_level - 2][nc] M2L sums of the path cells
+  float* Lmp = (float*)(off + 8 * nc + 1);    // [max_level - 2][nc] M2L sums of the path cells
   __shared__ int32_t s_row[kMaxLevel + 1];    // row (8 slot + cell) of the path cell at level k
   __shared__ int s_pos[kMaxLevel + 1];        // its position in its oct
   int si = 0;
   while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].blk0) ++si;
-  const L2LPathSeg& S = P.seg[si];
-  const int b = S.level;
+  const L2LPathSeg& Sg = P.seg[si];
+  const int b = Sg.level;
   // tree data and tables (written before this solve): read before the wait
-  const int32_t o = S.rows[blockIdx.x - S.blk0];
+  const int32_t o = Sg.rows[blockIdx.x - Sg.blk0];
   const int64_t so = P.slotL[b][o];
   if (threadIdx.x == 0) {
     int32_t cell = b > 2 ? P.oct_parent[b][o] : 0;
@@ -429,9 +559,9 @@ __global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant
     }
   }
   if (b > 2) {
-    stage_block<8>(np, [&](int j) { return P.pc[j]; }, cf);
+    stage_block<8>(np, [&](int j) { return ((const TA*)P.pc)[j]; }, cf);
     stage_block<8>(np, [&](int j) { return P.pg[j]; }, gg);
-    stage_block<6>(8 * nc + 1, [&](int k) { return P.poff8[k]; }, off);
+    stage_block<4>(8 * nc + 1, [&](int k) { return P.poff8[k]; }, off);
   }
   pdl_wait();
   pdl_trigger();
@@ -440,77 +570,72 @@ __global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant
   for (int k = 2; k < b; ++k)
     for (int j = threadIdx.x; j < nc; j += kPathThreads)
       Lmp[(k - 2) * nc + j] = P.Lm[k][(int64_t)(s_row[k] >> 3) * 8 * nc + __ldg(P.lmcol + (s_row[k] & 7) * nc + j)];
-  float own[2][8];
+  const int beta = threadIdx.x;  // nc <= 165 < kPathThreads
+  float own[8];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int beta = threadIdx.x + r * kPathThreads;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) own[r][c] = beta < nc ? P.Lm[b][so * 8 * nc + __ldg(P.lmcol + c * nc + beta)] : 0.f;
-  }
+  for (int c = 0; c < 8; ++c) own[c] = beta < nc ? P.Lm[b][so * 8 * nc + __ldg(P.lmcol + c * nc + beta)] : 0.f;
   __syncthreads();
-  if (b > 2)
-    for (int j = threadIdx.x; j < nc; j += kPathThreads) Lp[j] = Lmp[j];  // level 2: the M2L sum alone
+  if (b > 2 && beta < nc) Lp[beta] = (TA)Lmp[beta];  // level 2: the M2L sum alone
   __syncthreads();
   for (int k = 3; k < b; ++k) {
-    const unsigned nc_pos = ~(unsigned)s_pos[k] & 7u;
-    float v[2] = {0.f, 0.f};
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int beta = threadIdx.x + r * kPathThreads;
-      if (beta >= nc) continue;
-      float s[8];
-      l2l_sums(beta, Lp, cf, gg, off, s);
-      float y = Lmp[(k - 2) * nc + beta];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) y += (__popc((unsigned)e & nc_pos) & 1) ? -s[e] : s[e];
-      v[r] = y;
-    }
+    l2l_pattern_sums(nc, Lp, cf, gg, off, S);
     __syncthreads();
+    if (beta < nc) {
+      const unsigned nc_pos = ~(unsigned)s_pos[k] & 7u;
+      TA y = (TA)Lmp[(k - 2) * nc + beta];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int beta = threadIdx.x + r * kPathThreads;
-      if (beta < nc) Lp[beta] = v[r];
+      for (int e = 0; e < 8; ++e) y += (__popc((unsigned)e & nc_pos) & 1) ? -S[e * nc + beta] : S[e * nc + beta];
+      Lp[beta] = y;  // every thread has read Lp (barrier above) before it changes
     }
     __syncthreads();
   }
   // the own oct: all eight cells
+  TA acc[8];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int beta = threadIdx.x + r * kPathThreads;
-    if (beta >= nc) continue;
-    float acc[8];
-    if (b > 2) {
-      l2l_sums(beta, Lp, cf, gg, off, acc);
+  for (int c = 0; c < 8; ++c) acc[c] = 0;
+  if (b > 2) {
+    l2l_pattern_sums(nc, Lp, cf, gg, off, S);
+    __syncthreads();
+    if (beta < nc) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] = S[e * nc + beta];
       sign_transform_back(acc);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = 0.f;
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) P.Lf[b][(so * 8 + c) * nc + beta] = acc[c] + own[r][c];
   }
+  if (beta >= nc) return;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) P.Lf[b][(so * 8 + c) * nc + beta] = (float)(acc[c] + (TA)own[c]);
 }
 
+template <typename TA>
 inline size_t l2l_path_smem(int nc, int npairs, int max_level) {
-  return (size_t)npairs * 8 + (size_t)(8 * nc + 1) * 4 + (size_t)nc * 4 +
+  return (size_t)npairs * (sizeof(TA) + 4) + (size_t)nc * sizeof(TA) * 9 + (size_t)(8 * nc + 1) * 4 +
          (size_t)std::max(max_level - 2, 0) * nc * 4;
 }
 
-// Clears float4 ranges of several buffers in one launch (the M2L sums of every
-// level before the contraction adds into them).
-struct ZeroSegs {
-  float4* p[kMaxLevel + 1];
-  int64_t end[kMaxLevel + 1];  // cumulative float4 counts
-  int n;
+// Clears the M2L sums of the row octs the next M2L writes (their slots: 8 nc
+// floats each, 2 nc float4), all levels in one launch.
+struct ZeroRowsSeg {
+  const int32_t* rows;  // row octs of the level (the M2L's list)
+  const int32_t* slot;  // local-expansion slot of each oct of the level
+  float4* Lm;
+  int64_t end;          // cumulative float4 count up to and including this level
 };
-__global__ void k_zero_segments(const __grid_constant__ ZeroSegs Z) {
+struct ZeroRows {
+  ZeroRowsSeg seg[kMaxLevel + 1];
+  int n, nc;
+};
+__global__ void k_zero_rows(const __grid_constant__ ZeroRows Z) {
   pdl_wait();
   pdl_trigger();
-  const int64_t total = Z.end[Z.n - 1];
+  const int64_t total = Z.seg[Z.n - 1].end;
+  const int per = 2 * Z.nc;  // float4 per slot
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     int k = 0;
-    while (i >= Z.end[k]) ++k;
-    Z.p[k][i - (k ? Z.end[k - 1] : 0)] = make_float4(0.f, 0.f, 0.f, 0.f);
+    while (i >= Z.seg[k].end) ++k;
+    const int64_t u = i - (k ? Z.seg[k - 1].end : 0);
+    const int64_t r = u / per;
+    Z.seg[k].Lm[(int64_t)Z.seg[k].slot[Z.seg[k].rows[r]] * per + (u - r * per)] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -521,8 +646,15 @@ __global__ void k_zero_segments(const __grid_constant__ ZeroSegs Z) {
 fmm_status upward_init(Ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2m_smem(165, 3003));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_l2l_path, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)l2l_path_smem(165, 3003, kMaxLevel));
+    e = cudaFuncSetAttribute(k_l2l_path<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)l2l_path_smem<double>(165, 3003, kMaxLevel));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_l2l_path<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)l2l_path_smem<float>(165, 3003, kMaxLevel));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_m2m_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_m2m_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmemMax);
 
   if (e != cudaSuccess) {
     c->last_error = std::string("upward_init: ") + cudaGetErrorString(e);
@@ -630,25 +762,84 @@ void launch_l2l_path(Ctx* c, int lo, cudaStream_t st) {
   P.lmcol = (const int*)c->op_m2l.colmap.ptr;
   P.poff8 = (const int*)c->d_l2l_off8.ptr;
   P.pg = (const int*)c->d_l2l_g.ptr;
-  P.pc = (const float*)c->d_l2l_c32.ptr;
   ++c->n_launch;
-  launch_pdl(k_l2l_path, (unsigned)blocks, kPathThreads, l2l_path_smem(P.nc, P.npairs, P.max_level), st, P);
+  if (c->cfg.fp64_top) {
+    P.pc = c->d_l2l_c.ptr;
+    launch_pdl(k_l2l_path<double>, (unsigned)blocks, kPathThreads, l2l_path_smem<double>(P.nc, P.npairs, P.max_level),
+               st, P);
+  } else {
+    P.pc = c->d_l2l_c32.ptr;
+    launch_pdl(k_l2l_path<float>, (unsigned)blocks, kPathThreads, l2l_path_smem<float>(P.nc, P.npairs, P.max_level),
+               st, P);
+  }
 }
 
-void launch_zero_lm(Ctx* c, cudaStream_t st) {
-  ZeroSegs Z{};
+void launch_zero_lm(Ctx* c, const std::vector<int>& levels, const std::vector<const int32_t*>& rows,
+                    const std::vector<int64_t>& nrows, cudaStream_t st) {
+  ZeroRows Z{};
+  Z.nc = c->tab.nc;
   int64_t tot = 0;
-  for (int b = 2; b <= top_local_level(c); ++b) {
-    LevelTree& T = c->lev[b];
-    if (!T.n_rowsL || !T.Lm.ptr) continue;
-    tot += 8 * T.n_rowsL * c->tab.nc / 4;  // 8 cells x nc floats: a multiple of 8 floats
-    Z.p[Z.n] = (float4*)T.Lm.ptr;
-    Z.end[Z.n++] = tot;
+  for (size_t i = 0; i < levels.size(); ++i) {
+    LevelTree& T = c->lev[levels[i]];
+    const int32_t* r = rows[i] ? rows[i] : (const int32_t*)T.rowsL.ptr;
+    const int64_t n = rows[i] ? nrows[i] : T.n_rowsL;
+    if (!n || !T.Lm.ptr) continue;
+    tot += n * 2 * Z.nc;
+    ZeroRowsSeg& S = Z.seg[Z.n++];
+    S.rows = r;
+    S.slot = (const int32_t*)T.slotL.ptr;
+    S.Lm = (float4*)T.Lm.ptr;
+    S.end = tot;
   }
   if (!tot) return;
   ++c->n_launch;
   const unsigned g = (unsigned)std::min<int64_t>((tot + 255) / 256, 4 * c->num_sms);
-  launch_pdl(k_zero_segments, g, 256, 0, st, Z);
+  launch_pdl(k_zero_rows, g, 256, 0, st, Z);
+}
+
+int m2m_chain_warps(const Ctx* c) {
+  const int nc = c->tab.nc, np = (int)c->tab.m2m_g.size();
+  const size_t fixed = chain_smem(nc, np, 0);
+  const int w = fixed >= kChainSmemMax ? 0 : (int)((kChainSmemMax - fixed) / ((size_t)64 * nc));
+  return std::min(32, w);
+}
+
+void launch_m2m_chain(Ctx* c, int b_top, cudaStream_t st) {
+  const int nc = c->tab.nc;
+  const bool f64 = c->cfg.precision == FMM_FP64;
+  const bool tf32 = c->cfg.precision == FMM_MIXED_TF32;
+  ChainParams P{};
+  for (int b = b_top; b >= 2; --b) {
+    LevelTree& T = c->lev[b];
+    LevelTree& N = c->lev[b + 1];
+    if (!N.n_anc) continue;
+    ChainLevel& U = P.lev[P.nlev++];
+    U.octs = (const int32_t*)N.anc.ptr;
+    U.n = (int)N.n_anc;
+    U.oct_parent = (const int32_t*)N.oct_parent.ptr;
+    U.cell_child = (const int32_t*)N.cell_child.ptr;
+    U.mass = (const double*)N.mass.ptr;
+    U.Min = N.M.ptr;
+    U.in_f64 = N.m_is_f64 ? 1 : 0;
+    U.Mout = T.M.ptr;
+    U.out_f64 = T.m_is_f64 ? 1 : 0;
+    U.hi = f64 ? nullptr : (__nv_bfloat16*)T.Mhi.ptr;
+    U.lo = (f64 || tf32) ? nullptr : (__nv_bfloat16*)T.Mlo.ptr;
+    U.mono = T.mono.ptr;
+  }
+  if (!P.nlev) return;
+  P.nc = nc;
+  P.npairs = (int)c->tab.m2m_g.size();
+  P.poff = (const int*)c->d_m2m_off.ptr;
+  P.pg = (const int*)c->d_m2m_g.ptr;
+  P.pe = (const int*)c->d_m2m_e.ptr;
+  P.pc = (const double*)c->d_m2m_c.ptr;
+  const int w = m2m_chain_warps(c);
+  ++c->n_launch;
+  if (f64)
+    launch_pdl(k_m2m_chain<double>, 1u, 32u * w, chain_smem(nc, P.npairs, w), st, P);
+  else
+    launch_pdl(k_m2m_chain<float>, 1u, 32u * w, chain_smem(nc, P.npairs, w), st, P);
 }
 
 void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t nrows) {

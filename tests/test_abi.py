@@ -34,11 +34,12 @@ def test_create_rejects_bad_arguments_without_gpu():
     L = fmm.lib()
     h = ctypes.c_void_p()
     none = fmm.ALLOC_FN()
-    # (p, precision, bottom mode, p_m, mass_fp32)
-    for p, prec, bottom, pm, m32 in [(0, 0, 0, 0, 0), (9, 0, 0, 0, 0), (4, 7, 0, 0, 0), (4, 0, 2, 0, 0),
-                                     (4, 0, 0, 5, 0), (4, 0, 0, -1, 0), (4, 1, 0, 0, 2)]:
-        cfg = fmm._Config(p, prec, 1.0, 0, 0, bottom, pm, m32)
-        assert L.fmm_create(ctypes.byref(cfg), none, None, ctypes.byref(h)) == -1, (p, prec, bottom, pm, m32)
+    # (p, precision, bottom mode, p_m, mass_fp32, fp64_top)
+    for p, prec, bottom, pm, m32, t64 in [(0, 0, 0, 0, 0, 0), (9, 0, 0, 0, 0, 0), (4, 7, 0, 0, 0, 0),
+                                          (4, 0, 2, 0, 0, 0), (4, 0, 0, 5, 0, 0), (4, 0, 0, -1, 0, 0),
+                                          (4, 1, 0, 0, 2, 0), (4, 1, 0, 0, 0, 3)]:
+        cfg = fmm._Config(p, prec, 1.0, 0, 0, bottom, pm, m32, t64)
+        assert L.fmm_create(ctypes.byref(cfg), none, None, ctypes.byref(h)) == -1, (p, prec, bottom, pm, m32, t64)
     assert L.fmm_create(None, none, None, ctypes.byref(h)) == -1
     assert L.fmm_set_wait_limit(None, 1.0) == -1
     assert L.fmm_set_levels(None, 2, 3, 2, None, None, None, None) == -1

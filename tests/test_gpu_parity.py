@@ -230,6 +230,20 @@ def test_tf32_matches_oracle(name, p):
     check(gp, ga, rp, ra, oracle_tol("tf32"), f"{name} p={p} tf32", h=h)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "tf32"])
+@pytest.mark.parametrize("name,p", [("amr_3_5", 4), ("amr_3_5b", 6), ("twolevel16", 8), ("unigrid16", 6)])
+def test_fp64_top_matches_oracle(name, p, precision):
+    """config.fp64_top: FP64 M2M at box levels <= 3 and an FP64 L2L chain with
+    FP64 local-expansion accumulation, against the oracle; and against the
+    default FP32 version of the same context, which differs only by rounding."""
+    h = CASES[name]
+    rp, ra = oracle.solve(h, p)
+    gp, ga = run(h, p, precision, fp64_top=True)
+    check(gp, ga, rp, ra, oracle_tol(precision), f"{name} p={p} {precision} fp64_top", h=h)
+    fp, fa = run(h, p, precision)
+    check(gp, ga, fp, fa, {"rms": 1e-4, "cell": 1e-3}, f"{name} p={p} {precision} fp64_top vs FP32", h=h)
+
+
 @pytest.mark.parametrize("bottom", ["m2p", "m2l"])
 def test_twolevel64_p6_tf32_sampled(bottom):
     h = W.two_level_plummer()
