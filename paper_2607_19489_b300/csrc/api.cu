@@ -103,6 +103,64 @@ __global__ void k_widen_mass(int64_t n, const float* __restrict__ in, double* __
 }
 }  // namespace
 
+namespace {
+// The inputs of every level given by device pointers in one launch: cell
+// indices (ijk may be null: masses only) and masses, float masses widened.
+struct StageLevel {
+  const int32_t* ijk;
+  const void* mass;
+  int32_t* dijk;
+  double* dmass;
+  int64_t end;  // cumulative cell count up to and including this level
+};
+struct StageParams {
+  StageLevel lev[kMaxLevel + 1];
+  int nlev, mass_f32;
+};
+__global__ void k_stage_inputs(const __grid_constant__ StageParams P) {
+  const int64_t total = P.lev[P.nlev - 1].end;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (i >= P.lev[k].end) ++k;
+    const StageLevel& L = P.lev[k];
+    const int64_t j = i - (k ? P.lev[k - 1].end : 0);
+    if (L.ijk) {
+      L.dijk[3 * j] = L.ijk[3 * j];
+      L.dijk[3 * j + 1] = L.ijk[3 * j + 1];
+      L.dijk[3 * j + 2] = L.ijk[3 * j + 2];
+    }
+    L.dmass[j] = P.mass_f32 ? (double)((const float*)L.mass)[j] : ((const double*)L.mass)[j];
+  }
+}
+}  // namespace
+
+// Copies the inputs of levels lo..lo+nlev-1 into the context (ijk null: masses
+// only) with one kernel when every source is device memory; false when a source
+// is host memory (the caller then copies level by level).
+static bool stage_device_inputs(Ctx* c, int lo, int nlev, const int32_t* const* ijk, const void* const* mass,
+                                cudaStream_t st) {
+  StageParams P{};
+  P.mass_f32 = c->cfg.mass_fp32;
+  int64_t tot = 0;
+  for (int k = 0; k < nlev; ++k) {
+    LevelTree& T = c->lev[lo + k];
+    if (!T.n_leaf) continue;
+    if ((ijk && !is_device_ptr(ijk[k])) || !is_device_ptr(mass[k])) return false;
+    StageLevel& L = P.lev[P.nlev++];
+    L.ijk = ijk ? ijk[k] : nullptr;
+    L.mass = mass[k];
+    L.dijk = (int32_t*)T.ijk.ptr;
+    L.dmass = (double*)T.mass.ptr;
+    tot += T.n_leaf;
+    L.end = tot;
+  }
+  if (!tot) return true;
+  ++c->n_launch;
+  const unsigned g = (unsigned)std::min<int64_t>((tot + 255) / 256, 8 * c->num_sms);
+  k_stage_inputs<<<g, 256, 0, st>>>(P);
+  return cudaGetLastError() == cudaSuccess;
+}
+
 // Copies the masses of one level into its FP64 array: double input directly,
 // float input through the staging buffer and a widening kernel.
 static fmm_status copy_masses(Ctx* c, LevelTree& T, const void* mass, int64_t nl, cudaStream_t st) {
@@ -625,6 +683,12 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_use
   }
   c->d_err = (unsigned*)c->err_buf.ptr;
   cudaMemset(c->d_err, 0, kErrWords * 4);
+  if (cudaMallocHost((void**)&c->h_rb, Ctx::kReadbackBytes) != cudaSuccess) {
+    cudaGetLastError();
+    buf_free(c, c->err_buf);
+    delete c;
+    return FMM_ERR_OOM;
+  }
   for (auto& ev : c->ev) cudaEventCreate(&ev);
   if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -756,9 +820,16 @@ static fmm_status set_levels_impl(fmm_ctx* c, int lmin, int lmax, int lo, const 
     T.vel_valid = false;  // the cells may have changed: fmm_set_velocities again
     CKS(buf_ensure(c, T.ijk, nl * 12));
     CKS(buf_ensure(c, T.mass, nl * 8));
-    if (nl) {
-      CKS(cudaMemcpyAsync(T.ijk.ptr, ijk[l - lo], nl * 12, cudaMemcpyDefault, st));
-      TRY(copy_masses(c, T, mass[l - lo], nl, st));
+  }
+  if (!stage_device_inputs(c, lo, lmax - lo + 1, ijk, mass, st)) {
+    cudaGetLastError();
+    for (int l = lo; l <= lmax; ++l) {
+      LevelTree& T = c->lev[l];
+      const int64_t nl = T.n_leaf;
+      if (nl) {
+        CKS(cudaMemcpyAsync(T.ijk.ptr, ijk[l - lo], nl * 12, cudaMemcpyDefault, st));
+        TRY(copy_masses(c, T, mass[l - lo], nl, st));
+      }
     }
   }
   // trailing empty levels: the tree ends at the finest level that holds leaves
@@ -1375,7 +1446,10 @@ fmm_status fmm_update_masses(fmm_ctx* c, int lo, const void* const* mass, void* 
     for (int l = lo; l <= c->lmax; ++l) nmax = std::max(nmax, c->lev[l].n_leaf);
     CKS(buf_ensure(c, c->mass_stage, nmax * 4));
   }
-  for (int l = lo; l <= c->lmax; ++l) TRY(copy_masses(c, c->lev[l], mass[l - lo], c->lev[l].n_leaf, st));
+  if (!stage_device_inputs(c, lo, c->lmax - lo + 1, nullptr, mass, st)) {
+    cudaGetLastError();
+    for (int l = lo; l <= c->lmax; ++l) TRY(copy_masses(c, c->lev[l], mass[l - lo], c->lev[l].n_leaf, st));
+  }
   c->dirty_lo = std::min(c->dirty_lo, lo);
   return FMM_OK;
 }
@@ -1487,6 +1561,7 @@ void fmm_destroy(fmm_ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
+  if (c->h_rb) cudaFreeHost(c->h_rb);
   delete c;
 }
 

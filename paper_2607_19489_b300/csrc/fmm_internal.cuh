@@ -194,6 +194,10 @@ struct Ctx {
   DevBuf in_stage;      // device staging for host inputs
   DevBuf mass_stage;    // FP32 masses (config.mass_fp32) on their way to the FP64 copies
   DevBuf err_buf;       // the device error words (d_err points into it)
+  // pinned host copy of the tree build's list lengths and error words (one
+  // synchronisation per build reads them back)
+  static constexpr size_t kReadbackBytes = (size_t)5 * 4 * (kMaxLevel + 2) + (size_t)4 * kErrWords;
+  unsigned char* h_rb = nullptr;
   unsigned* d_err = nullptr;
   // the caller's allocator (null: cudaMalloc / cudaFree)
   fmm_alloc_fn alloc = nullptr;

@@ -767,10 +767,11 @@ fmm_status tree_finish(Ctx* c, cudaStream_t st) {
   const int lmin = c->lmin, lmax = c->lmax;
   const int stride = lmax + 2;
   int32_t* d_counts = (int32_t*)c->counter.ptr;
-  std::vector<int32_t> counts(5 * stride, 0);
-  CK(cudaMemcpyAsync(counts.data(), d_counts, 5 * 4 * stride, cudaMemcpyDeviceToHost, st));
-  unsigned ev[kErrWords] = {};
-  CK(cudaMemcpyAsync(ev, c->d_err, kErrWords * 4, cudaMemcpyDeviceToHost, st));
+  // both into the context's pinned buffer: asynchronous copies, one synchronisation
+  int32_t* counts = (int32_t*)c->h_rb;
+  const unsigned* ev = (const unsigned*)(c->h_rb + (size_t)5 * 4 * (kMaxLevel + 2));
+  CK(cudaMemcpyAsync(counts, d_counts, 5 * 4 * stride, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync((void*)ev, c->d_err, kErrWords * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   for (int group = 0; group < 2; ++group) {
     for (int l = lmax; l >= 1; --l) {
