@@ -154,6 +154,73 @@ __global__ void k_place_complete(int level, int64_t n_leaf, int64_t n_ref, int64
   if (atomicExch(cell_child + key, val) != kUnsetCell) atomicOr(err, kErrDuplicate);
 }
 
+// The level above a complete base level, without a sort: its octs are the
+// refined base cells in Morton order, so marking the parent of every entry
+// (leaf or refined cell) in a dense array over the 8^lmin base cells and
+// scanning it gives each oct its index; a cell then sits at 8 oct + (key & 7).
+// The result is the sorted pass's (same octs, cells, keys and maps).  Entries
+// are the level's leaves (i < n_leaf) and its refined cells (the octs of the
+// next level, whose keys are their parents' keys).
+__device__ __forceinline__ bool dense_key(int64_t i, int level, int64_t n_leaf, const int32_t* __restrict__ ijk,
+                                          const uint64_t* __restrict__ octkey_next, uint64_t& key) {
+  if (i < n_leaf) {
+    const int x = ijk[3 * i], y = ijk[3 * i + 1], z = ijk[3 * i + 2];
+    const int lim = 1 << level;
+    if (x < 0 || y < 0 || z < 0 || x >= lim || y >= lim || z >= lim) return false;
+    key = spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+  } else {
+    key = octkey_next[i - n_leaf];
+  }
+  return true;
+}
+
+__global__ void k_dense_mark(int level, int64_t n_leaf, int64_t n_ref, int64_t n_base,
+                             const int32_t* __restrict__ ijk, const double* __restrict__ mass,
+                             const uint64_t* __restrict__ octkey_next, int32_t* __restrict__ flags, unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_leaf + n_ref) return;
+  uint64_t key;
+  if (!dense_key(i, level, n_leaf, ijk, octkey_next, key)) {
+    atomicOr(err, kErrOutOfBox);
+    return;
+  }
+  if (i < n_leaf && !isfinite(mass[i])) atomicOr(err, kErrNonFinite);
+  if ((key >> 3) >= (uint64_t)n_base) {  // only after an invalid finer level
+    atomicOr(err, kErrIncomplete);
+    return;
+  }
+  flags[key >> 3] = 1;
+}
+
+__global__ void k_dense_place(int level, int64_t n_leaf, int64_t n_ref, int64_t n_base, int64_t n_oct,
+                              const int32_t* __restrict__ ijk, const uint64_t* __restrict__ octkey_next,
+                              const int32_t* __restrict__ scan, uint64_t* __restrict__ oct_key,
+                              int32_t* __restrict__ cell_child, int32_t* __restrict__ leaf_cell,
+                              int32_t* __restrict__ oct_parent_next, unsigned* err) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0 && scan[n_base - 1] != n_oct) atomicOr(err, kErrIncomplete);  // refined base cells != octs
+  if (i >= n_leaf + n_ref) return;
+  uint64_t key;
+  if (!dense_key(i, level, n_leaf, ijk, octkey_next, key) || (key >> 3) >= (uint64_t)n_base) return;  // flagged
+  const int64_t oct = (int64_t)scan[key >> 3] - 1;
+  if (oct < 0 || oct >= n_oct) {
+    atomicOr(err, kErrIncomplete);
+    return;
+  }
+  const int64_t cell = 8 * oct + (int64_t)(key & 7);
+  oct_key[oct] = key >> 3;  // every cell of the oct writes the same key
+  const int32_t val = i < n_leaf ? (int32_t)(-1 - i) : (int32_t)(i - n_leaf);
+  if (atomicExch(cell_child + cell, val) != kUnsetCell) atomicOr(err, kErrDuplicate);
+  if (i < n_leaf)
+    leaf_cell[i] = (int32_t)cell;
+  else
+    oct_parent_next[i - n_leaf] = (int32_t)cell;
+}
+
 // Levels 1..lmin (complete grids): oct o of level l sits under cell o of level
 // l-1, whose 27 neighbours are found by decoding o's Morton index; levels below
 // lmin are fully refined (the child oct of cell c is c).  One thread per oct of
@@ -624,6 +691,24 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
                                                 (const double*)T.mass.ptr,
                                                 n_ref ? (const uint64_t*)c->lev[l + 1].oct_key.ptr : nullptr,
                                                 (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next, err));
+      continue;
+    }
+    if (l == lmin + 1 && place_base) {  // the octs above the complete base level, unsorted
+      const int64_t nbase = 8 * c->lev[lmin].n_oct;
+      int32_t* flags = (int32_t*)c->flags.ptr;  // [8^lmin] refined base cells
+      int32_t* scan = (int32_t*)c->scan.ptr;
+      CK(cudaMemsetAsync(flags, 0, nbase * 4, st));
+      CK(cudaMemsetAsync(T.cell_child.ptr, 0x80, T.n_oct * 32, st));
+      const uint64_t* okn = n_ref ? (const uint64_t*)c->lev[l + 1].oct_key.ptr : nullptr;
+      c->n_launch += 2;
+      CK(launch_pdl(k_dense_mark, nblk(n), 256, 0, st, l, T.n_leaf, n_ref, nbase, (const int32_t*)T.ijk.ptr,
+                    (const double*)T.mass.ptr, okn, flags, err));
+      size_t tmp = c->sort_tmp.bytes;
+      ++c->n_cub;
+      CK(cub::DeviceScan::InclusiveSum(c->sort_tmp.ptr, tmp, flags, scan, (int)nbase, st));
+      CK(launch_pdl(k_dense_place, nblk(n), 256, 0, st, l, T.n_leaf, n_ref, nbase, T.n_oct,
+                    (const int32_t*)T.ijk.ptr, okn, (const int32_t*)scan, (uint64_t*)T.oct_key.ptr,
+                    (int32_t*)T.cell_child.ptr, (int32_t*)T.leaf_cell.ptr, par_next, err));
       continue;
     }
     uint64_t* ka = (uint64_t*)c->keys_a.ptr;

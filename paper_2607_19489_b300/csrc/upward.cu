@@ -107,17 +107,21 @@ __global__ void __launch_bounds__(256) k_leaf_rows(int64_t n, int nc, const int3
   pdl_trigger();
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= n) return;
+  if (w >= n) return;  // warp-uniform
   const int64_t o = irows[w];
+  // lanes 0..7 fetch the eight cells' links and masses together
+  const int32_t chl = lane < 8 ? cell_child[o * 8 + lane] : 0;
+  const double ml = (lane < 8 && chl < 0) ? mass[-1 - (int64_t)chl] : 0.0;
   for (int c = 0; c < 8; ++c) {
-    const int32_t ch = cell_child[o * 8 + c];
-    if (ch >= 0) continue;
-    const Tout m = (Tout)mass[-1 - (int64_t)ch];
+    const int32_t ch = __shfl_sync(0xffffffffu, chl, c);
+    const Tout m = (Tout)__shfl_sync(0xffffffffu, ml, c);
+    if (ch >= 0) continue;  // warp-uniform
     const int64_t row = (o * 8 + c) * nc;
+    const int64_t obase = op_index(o * 8 + c, 0, nc);
     for (int k = lane; k < nc; k += 32) {
       const Tout v = k == 0 ? m : (Tout)0;
       M[row + k] = v;
-      if (hi) put_operand(v, hi, lo, op_index(o * 8 + c, k, nc));
+      if (hi) put_operand(v, hi, lo, obase + 8 * k);
     }
   }
 }
