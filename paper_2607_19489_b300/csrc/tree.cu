@@ -385,22 +385,30 @@ __global__ void __launch_bounds__(kListBlock) k_leafmasks(const __grid_constant_
   L.leafmask[o] = (uint8_t)mask;
 }
 
+// The loops below have no early exit, so each one's loads are issued together
+// (one round of child links or neighbour indices, one round of leaf masks).
 __device__ __forceinline__ unsigned oct_list_flags(const ListLevel& L, int64_t o) {
   const unsigned mask = L.leafmask[o];
   const int leaf = mask != 0, refined = mask != 0xFFu;
   int grand = 0;
   if (L.want_rowsL && refined && L.rowsL_refined) grand = 1;
-  if (L.want_rowsL && refined && !L.rowsL_refined)
-    for (int c = 0; c < 8 && !grand; ++c) {
-      const int32_t ch = L.cell_child[o * 8 + c];
-      if (ch >= 0 && ch < L.n_oct_next) grand |= L.leafmask_next[ch] != 0xFFu;
-    }
+  if (L.want_rowsL && refined && !L.rowsL_refined) {
+    int32_t ch[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) ch[c] = L.cell_child[o * 8 + c];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (ch[c] >= 0 && ch[c] < L.n_oct_next) grand |= L.leafmask_next[ch[c]] != 0xFFu;
+  }
   int near_ref = 0;
-  if (L.want_irows && leaf)
-    for (int q = 0; q < 27 && !near_ref; ++q) {
-      const int32_t nb = L.nbr[o * 27 + q];
-      if (nb >= 0 && nb < L.n_oct) near_ref |= L.leafmask[nb] != 0xFFu;
-    }
+  if (L.want_irows && leaf) {
+    int32_t nb[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) nb[q] = L.nbr[o * 27 + q];
+#pragma unroll
+    for (int q = 0; q < 27; ++q)
+      if (nb[q] >= 0 && nb[q] < L.n_oct) near_ref |= L.leafmask[nb[q]] != 0xFFu;
+  }
   return (unsigned)refined | ((unsigned)leaf << 1) | ((unsigned)grand << 2) | ((unsigned)(leaf && near_ref) << 3);
 }
 
