@@ -289,10 +289,26 @@ def rel_rms(a: dict, b: dict) -> float:
     return float(np.sqrt(num / den))
 
 
+def host_warm(seconds: float = 1.0):
+    """Keeps the calling host core busy for a moment before a timed region.
+
+    Every step has host work between its device stages (the tree build's one
+    synchronisation, the solve's graph launch).  On the test machines a host
+    core that has idled, even for 0.1 s, runs that work several times slower
+    for the next few hundred milliseconds (the graph launch measured 0.08 ms
+    instead of 0.011 ms, the step 0.55 ms instead of 0.34 ms), and a busy-wait
+    of about a second restores it; steps in a steady loop never see it.  The
+    spin touches no GPU state."""
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        pass
+
+
 def timed_steps(torch, step, K, W, stream, flush):
     for _ in range(W):
         step()
     torch.cuda.synchronize()
+    host_warm()
     times = []
     for _ in range(K):
         flush.zero_()
@@ -313,6 +329,7 @@ def timed_after(torch, prepare, step, K, W, stream, flush):
         prepare()
         step()
     torch.cuda.synchronize()
+    host_warm()
     times = []
     for _ in range(K):
         flush.zero_()
@@ -576,6 +593,7 @@ def _timed(torch, fn, K, W, stream):
     for _ in range(W):
         fn()
     torch.cuda.synchronize()
+    host_warm()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -834,6 +852,7 @@ def leg_ats(args, torch, dev, stream, flush):
     ms_step = _timed(torch, coarse_step, K, 3, stream)
     # one more coarse step with an event pair around every solve of the schedule
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(sched) + 1)]
+    host_warm()
     evs[0].record(stream)
     for i, (lo, ms) in enumerate(zip(sched, pert)):
         s.set_levels(h.lmin, h.lmax, ijk[lo - h.lmin:], ms, lo=lo)

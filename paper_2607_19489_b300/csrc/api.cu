@@ -692,7 +692,8 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_use
   for (auto& ev : c->ev) cudaEventCreate(&ev);
   if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_sync, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     c->aux_stream = nullptr;  // one stream then: the solve stays correct, only serial
   }
@@ -1559,6 +1560,7 @@ void fmm_destroy(fmm_ctx* c) {
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_sync) cudaEventDestroy(c->ev_sync);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   if (c->h_rb) cudaFreeHost(c->h_rb);

@@ -252,6 +252,7 @@ struct Ctx {
   // the near field)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_sync = nullptr;  // the tree build's one synchronisation (polled, see tree_finish)
   bool use_graphs = true;
   // launch shapes picked by fmm_autotune (0: built-in choice)
   int tune_split[2] = {0, 0};  // split-K of the tcgen05 contraction, [kModeM2P], [kModeM2L]

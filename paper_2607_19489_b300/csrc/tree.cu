@@ -21,6 +21,8 @@
 // synchronisation at the end reads the error word and the list lengths.
 #include <cub/cub.cuh>
 
+#include <chrono>
+
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -865,7 +867,22 @@ fmm_status tree_finish(Ctx* c, cudaStream_t st) {
   const unsigned* ev = (const unsigned*)(c->h_rb + (size_t)5 * 4 * (kMaxLevel + 2));
   CK(cudaMemcpyAsync(counts, d_counts, 5 * 4 * stride, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync((void*)ev, c->d_err, kErrWords * 4, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  // The calling thread polls instead of blocking: a thread that sleeps in the
+  // wait can take far longer to wake than the build takes (a descheduled
+  // virtual CPU), and the device idles meanwhile.  Long waits fall back to a
+  // blocking wait after 20 ms.
+  CK(cudaEventRecord(c->ev_sync, st));
+  {
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaError_t q;
+    while ((q = cudaEventQuery(c->ev_sync)) == cudaErrorNotReady) {
+      if (std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(20)) {
+        q = cudaEventSynchronize(c->ev_sync);
+        break;
+      }
+    }
+    CK(q);
+  }
   for (int group = 0; group < 2; ++group) {
     for (int l = lmax; l >= 1; --l) {
       const unsigned e = group == 0 ? ev[1 + l] | c->tree_host_err[l] : ev[kErrNbr0 + l];
