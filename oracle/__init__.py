@@ -45,6 +45,8 @@ def lib():
         L.oracle_fmm_solve.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P,
                                        P, ctypes.c_int]
+        L.oracle_fmm_solve_dl2.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                           P, P, P, P, ctypes.c_int]
         L.oracle_direct_sum.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_double,
                                         ctypes.c_int, P, P, P, P, ctypes.c_int]
         L.oracle_tree.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P]
@@ -139,6 +141,20 @@ def solve(h, p: int, G: float = 1.0, lo: int | None = None, sel: dict | None = N
     out = _call(lib().oracle_fmm_solve, h, lo, sel, extra, threads)
     del keep
     return out
+
+
+def solve_dl2(h, p: int, G: float = 1.0, sel: dict | None = None, threads: int | None = None,
+              p_m: int | None = None):
+    """The Delta l = 2 variant (finest FMM box = 4^3 cells, near field = the
+    cells of the 3^3 neighbour boxes) on a single complete level h.lmin ==
+    h.lmax >= 3.  Returns (phi, acc) dicts keyed by level."""
+    if h.lmin != h.lmax:
+        raise OracleError(-1)
+
+    def fn(lmin, lmax, n, ijk, mass, p_, G_, pm_, lo, nsel, sel_, phi, acc, threads_):
+        return lib().oracle_fmm_solve_dl2(lmin, n, ijk, mass, p_, G_, pm_, nsel, sel_, phi, acc, threads_)
+
+    return _call(fn, h, None, sel, (p, G, 0 if p_m is None else p_m), threads)
 
 
 def direct(h, G: float = 1.0, lo: int | None = None, sel: dict | None = None,

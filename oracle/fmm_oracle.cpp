@@ -44,6 +44,16 @@
 //     Eq. 2 with displacement d).  Cells used as point masses (P2P, P2L) stay
 //     at their centres.
 //
+// A third option, for a single complete level only:
+//   * Delta l = 2 (the footnote of Sec. 2: Paper I's generalisation, tested
+//     there on unigrids; the paper keeps Delta l = 1 for AMR and ATS): the
+//     finest FMM box holds the 4^3 cells two levels up instead of an oct's
+//     2^3.  The downward pass stops at box level l-3 (far field = L2P of the
+//     level l-3 ancestor), the bottom intermediate field is the M2P from the
+//     interaction list of the target's level l-2 ancestor G, and the near field
+//     is the direct sum over the cells of G's 3^3 neighbours (12^3 = 1728
+//     cells less the target).
+//
 // Parity status: pinned by the tests in tests/test_oracle_*.py against the
 // O(N^2) direct sum (exact agreement where the FMM has no far field, error
 // falling with p elsewhere), closed forms of the derivatives of 1/r, the M2M
@@ -460,6 +470,7 @@ struct Solver {
   const Hier& H;
   int p;
   int bottom;               // 0: M2P bottom intermediate field (paper); 1: M2L into F + L2P
+  int delta = 1;            // levels between the cells and the finest FMM box (2: unigrids only)
   Ops op;
   std::vector<Tree> trees;  // indexed by AMR level j
 
@@ -551,7 +562,7 @@ struct Solver {
   // so the first local expansion is at box level 2.
   std::vector<Grid> downward(int l, const std::vector<Grid>& mt, int nthreads) const {
     std::vector<Grid> L(l + 1);
-    const int top = bottom ? l - 1 : l - 2;
+    const int top = bottom ? l - 1 : l - 1 - delta;
     if (top < 2) return L;
     // boxes that need L: ancestors of level-l leaves
     std::vector<std::set<I3>> need(l + 1);
@@ -603,9 +614,47 @@ struct Solver {
     return L;
   }
 
+  // PotentialEvaluation with Delta l = 2 on a single complete level l: the
+  // level l-2 ancestor G of the target is the finest FMM box.
+  void evaluate_dl2(int l, const I3& t, const std::vector<Grid>& L, DCache& dc, double* phi,
+                    double* grad) const {
+    double xt[3];
+    centre(t, l, xt);
+    const I3 G = parent_of(parent_of(t));
+    if (l - 3 >= 2) {  // far field: local expansion of G's parent (level l-3)
+      const I3 P = parent_of(G);
+      double c[3];
+      centre(P, l - 3, c);
+      op.l2p(L[l - 3].at(P), c, xt, phi, grad);
+    }
+    for (const I3& S : ilist(G, l - 2)) {  // intermediate field: M2P at level l-2
+      double cS[3], R[3];
+      centre(S, l - 2, cS);
+      for (int i = 0; i < 3; ++i) R[i] = xt[i] - cS[i];
+      if (const Vec* M = tree_box(l, l - 2, S)) op.m2p(*M, dc.get(R), phi, grad);
+    }
+    for (int dz = -1; dz <= 1; ++dz)  // near field: every cell of G's 3^3 neighbours
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const I3 N{G[0] + dx, G[1] + dy, G[2] + dz};
+          if (!inside(N, l - 2)) continue;
+          for (int k = 0; k < 64; ++k) {
+            const I3 C{4 * N[0] + (k & 3), 4 * N[1] + ((k >> 2) & 3), 4 * N[2] + (k >> 4)};
+            if (C == t) continue;
+            double cC[3];
+            centre(C, l, cC);
+            p2p(H.leaf_mass(l, C), cC, xt, phi, grad);
+          }
+        }
+  }
+
   // PotentialEvaluation (Alg. 4, with Fig. 2's list of sources) for one target.
   void evaluate(int l, const I3& t, const std::vector<Grid>& L, const std::vector<Grid>& mt,
                 DCache& dc, double* phi, double* grad) const {
+    if (delta == 2) {
+      evaluate_dl2(l, t, L, dc, phi, grad);
+      return;
+    }
     double xt[3];
     centre(t, l, xt);
     I3 F = parent_of(t);
@@ -699,17 +748,18 @@ extern "C" {
 // p_m: multipole order of M2L / M2P (0: p); bottom: 0 = M2P, 1 = M2L + L2P.
 // vel (per level, double [n][3], or NULL) and dt (per level, or NULL): drift
 // the multipoles of the stale trees j < lo (see Solver::drift).
-int oracle_fmm_solve(int lmin, int lmax, const int64_t* n, const int32_t* const* ijk,
-                     const double* const* mass, int p, double G, int p_m, int bottom,
-                     const double* const* vel, const double* dt, int lo,
-                     const int64_t* n_sel, const int64_t* const* sel, double* const* phi,
-                     double* const* acc, int nthreads) {
+static int solve_impl(int lmin, int lmax, const int64_t* n, const int32_t* const* ijk,
+                      const double* const* mass, int p, double G, int p_m, int bottom, int delta,
+                      const double* const* vel, const double* dt, int lo,
+                      const int64_t* n_sel, const int64_t* const* sel, double* const* phi,
+                      double* const* acc, int nthreads) {
   if (p < 1 || p > 12 || nthreads < 1 || p_m < 0 || p_m > p || (bottom != 0 && bottom != 1)) return ORC_ERR_ARG;
   Hier H;
   int rc = H.build(lmin, lmax, n, ijk, mass);
   if (rc) return rc;
   if (lo < lmin || lo > lmax) return ORC_ERR_ARG;
   Solver S(H, p, p_m, bottom);
+  S.delta = delta;
   if (vel && dt) S.drift(lo, vel, dt);
   for (int l = lo; l <= lmax; ++l) {
     int64_t nt = n_sel ? n_sel[l - lmin] : n[l - lmin];
@@ -732,6 +782,26 @@ int oracle_fmm_solve(int lmin, int lmax, const int64_t* n, const int32_t* const*
     }
   }
   return ORC_OK;
+}
+
+int oracle_fmm_solve(int lmin, int lmax, const int64_t* n, const int32_t* const* ijk,
+                     const double* const* mass, int p, double G, int p_m, int bottom,
+                     const double* const* vel, const double* dt, int lo,
+                     const int64_t* n_sel, const int64_t* const* sel, double* const* phi,
+                     double* const* acc, int nthreads) {
+  return solve_impl(lmin, lmax, n, ijk, mass, p, G, p_m, bottom, 1, vel, dt, lo, n_sel, sel, phi, acc, nthreads);
+}
+
+// The Delta l = 2 variant (see the header) on one complete level l = lmin =
+// lmax >= 3; arguments as oracle_fmm_solve without the bottom mode, drifting
+// and lo.
+int oracle_fmm_solve_dl2(int level, const int64_t* n, const int32_t* const* ijk, const double* const* mass,
+                         int p, double G, int p_m, const int64_t* n_sel, const int64_t* const* sel,
+                         double* const* phi, double* const* acc, int nthreads) {
+  if (level < 3) return ORC_ERR_ARG;
+  if (n[0] != ((int64_t)1 << (3 * level))) return ORC_ERR_INCOMPLETE;
+  return solve_impl(level, level, n, ijk, mass, p, G, p_m, 0, 2, nullptr, nullptr, level, n_sel, sel, phi, acc,
+                    nthreads);
 }
 
 // O(N^2) direct sum over all leaves of all levels (self term excluded), for
