@@ -95,6 +95,17 @@ typedef struct {
                          expansions; 0 runs them in FP32 (the default: on B300 the
                          FP64 version costs ~20 % of a solve and, measured, gains no
                          accuracy against the FP64 path).  Ignored by FMM_FP64. */
+  int delta_l;        /* levels between the cells and the finest FMM box: 1 (the
+                         paper's choice for AMR and ATS; 0 also means 1) or 2 (the
+                         generalisation of the footnote of Sec. 2, which Paper I
+                         tested on unigrids): the finest box is a 4^3 block of cells,
+                         the near field the cells of its 3^3 neighbour blocks (12^3
+                         cells), the bottom intermediate field the M2P from its
+                         interaction list and M2L stops one box level higher.  With 2,
+                         fmm_set_levels takes one complete level only (lmin == lmax
+                         >= 3; otherwise FMM_ERR_ARG) and the bottom mode must be
+                         FMM_BOTTOM_M2P; fmm_solve_adjoint and the static unigrid
+                         entry return FMM_ERR_ARG. */
 } fmm_config;
 
 /* Device memory for the library, supplied by the caller (for instance a caching
@@ -110,7 +121,8 @@ typedef void* (*fmm_alloc_fn)(void* user, void* ptr, size_t bytes, void* stream)
  * makes (its workspace, and the translation tables it shares with the other
  * contexts of the same device, order, precision and allocator); NULL uses
  * cudaMalloc / cudaFree.  Returns FMM_ERR_ARG for p outside 1..8, p_m outside
- * 0..p, an unknown precision or bottom mode. */
+ * 0..p, an unknown precision or bottom mode, or delta_l outside 0..2 (2 with
+ * bottom mode FMM_BOTTOM_M2L_L2P). */
 fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_user, fmm_ctx** out);
 
 /* Set the AMR hierarchy, or replace its levels lo..lmax (adaptive time

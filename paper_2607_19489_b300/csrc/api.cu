@@ -244,23 +244,26 @@ inline float tf32_round(float f) {
 // p_m), a prefix of every segment, and the tiles of high degree (most of the
 // columns) read a few slices instead of all of them.  The M2L sums of a slot
 // are kept in this column order (colmap); M2P columns read every alpha <= p_m.
-fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& src, int N, bool m2l) {
-  const int nc = c->tab.nc, KQ = 8 * nc, K = 26 * KQ;
+fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& src, int N, int kind) {
+  // kind: kOpM2P / kOpM2L (nc coefficients per source cell) or kOpP2P (the 8
+  // child masses of each source cell, all read)
+  const bool m2l = kind == kOpM2L;
+  const int nc = c->tab.nc, nsrc = kind == kOpP2P ? 8 : nc, KQ = 8 * nsrc, K = 26 * KQ;
   op.N = N;
   op.K = K;
   op.kseg = KQ;
+  // K entries of a segment that column n reads: alpha of degree <= min(p - |beta|,
+  // p_m) (M2L), <= p_m (M2P), every child (P2P)
+  auto keep_len = [&](int d) { return kind == kOpP2P ? KQ : 8 * ncoef(std::min(c->tab.p - d, c->tab.pm)); };
   if (c->cfg.precision == FMM_FP64) {
     // [K'][N] with K' ordered (q, alpha, s) and per-column segment limits
     std::vector<double> f((size_t)K * N);
     std::vector<int32_t> lim(N);
-    for (int n = 0; n < N; ++n) {  // the alpha (graded order) a column reads: degree <= min(p - |beta|, p_m)
-      int d = m2l ? c->tab.degree[n % nc] : 0;
-      lim[n] = 8 * ncoef(std::min(c->tab.p - d, c->tab.pm));
-    }
+    for (int n = 0; n < N; ++n) lim[n] = keep_len(m2l ? c->tab.degree[n % nc] : 0);
     for (int q = 0; q < 26; ++q)
       for (int s = 0; s < 8; ++s)
-        for (int a = 0; a < nc; ++a) {
-          size_t kin = (size_t)(q * 8 + s) * nc + a;
+        for (int a = 0; a < nsrc; ++a) {
+          size_t kin = (size_t)(q * 8 + s) * nsrc + a;
           size_t kout = (size_t)q * KQ + a * 8 + s;
           for (int n = 0; n < N; ++n) f[kout * N + n] = src[(size_t)n * K + kin];
         }
@@ -270,10 +273,10 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
     op.ntile = (N + 255) / 256;
     return FMM_OK;
   }
-  const int p = c->tab.p, pm = c->tab.pm;
-  // columns: order (new column -> source column) and the degree each keeps
+  const int p = c->tab.p;
+  // columns: order (new column -> source column) and the K entries of a segment each reads
   std::vector<int> order(N);
-  std::vector<int> keep(N);  // alpha degrees <= keep[n] are read by column n
+  std::vector<int> keep(N);
   if (m2l) {
     int n = 0;
     for (int d = p; d >= 0; --d)
@@ -281,7 +284,7 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
         if (c->tab.degree[b] == d)
           for (int s = 0; s < 8; ++s) {
             order[n] = s * nc + b;
-            keep[n] = std::min(p - d, pm);
+            keep[n] = keep_len(d);
             ++n;
           }
     std::vector<int32_t> colmap(N);
@@ -291,7 +294,7 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
   } else {
     for (int n = 0; n < N; ++n) {
       order[n] = n;
-      keep[n] = pm;
+      keep[n] = keep_len(0);
     }
     op.BN = ((N + 255) / 256 == 1) ? (N + 31) / 32 * 32 : 256;
   }
@@ -303,16 +306,16 @@ fmm_status build_operator(Ctx* c, GemmOperand& op, const std::vector<double>& sr
   for (int y = 0; y < op.ntile; ++y) {
     int q = 0;
     for (int n = y * op.BN; n < std::min(N, (y + 1) * op.BN); ++n) q = std::max(q, keep[n]);
-    op.tile_slices[y] = (8 * ncoef(q) + kTcBK - 1) / kTcBK;
+    op.tile_slices[y] = (q + kTcBK - 1) / kTcBK;
   }
   // element (new column j, source K index (q, s, alpha)) -> (j, q kqp + alpha 8 + s)
   auto each = [&](auto&& put) {
     for (int j = 0; j < N; ++j)
       for (int q = 0; q < 26; ++q)
         for (int s = 0; s < 8; ++s)
-          for (int a = 0; a < nc; ++a)
+          for (int a = 0; a < nsrc; ++a)
             put((size_t)j * op.Kpad + (size_t)q * op.kqp + a * 8 + s,
-                src[(size_t)order[j] * K + (size_t)(q * 8 + s) * nc + a]);
+                src[(size_t)order[j] * K + (size_t)(q * 8 + s) * nsrc + a]);
   };
   if (c->cfg.precision == FMM_MIXED_TF32) {  // one FP32 operand, rounded to TF32
     std::vector<float> f((size_t)op.Npad * op.Kpad, 0.0f);
@@ -366,11 +369,18 @@ fmm_status init_tables(Ctx* c) {
     TRY(upload(c, c->d_near32, nf));
     TRY(upload(c, c->d_l2p32, lf));
   }
-  TRY(build_operator(c, c->op_m2p, t.m2p, 256, false));
-  TRY(build_operator(c, c->op_m2l, t.m2l, 8 * t.nc, true));
+  TRY(build_operator(c, c->op_m2p, t.m2p, 256, kOpM2P));
+  TRY(build_operator(c, c->op_m2l, t.m2l, 8 * t.nc, kOpM2L));
+  if (c->cfg.delta_l == 2) {
+    t.build_dl2();
+    TRY(build_operator(c, c->op_m2p2, t.m2p2, 2048, kOpM2P));
+    TRY(build_operator(c, c->op_p2pr, t.p2pr, 256, kOpP2P));
+  }
   // the tables are only needed on the device from here on
   std::vector<double>().swap(t.m2p);
   std::vector<double>().swap(t.m2l);
+  std::vector<double>().swap(t.m2p2);
+  std::vector<double>().swap(t.p2pr);
   c->tables_on_device = true;
   return FMM_OK;
 }
@@ -394,6 +404,16 @@ fmm_status size_expansions(Ctx* c, cudaStream_t st) {
       } else if (!f64) {
         CKS(buf_ensure(c, T.Mhi, ncell * nc * 2));
         CKS(buf_ensure(c, T.Mlo, ncell * nc * 2));
+      }
+    }
+    if (c->cfg.delta_l == 2 && l == c->lmax - 1) {  // the 8 child masses of each cell
+      if (f64) {
+        CKS(buf_ensure(c, T.Chi, ncell * 8 * 8));
+      } else if (c->cfg.precision == FMM_MIXED_TF32) {
+        CKS(buf_ensure(c, T.Chi, ncell * 8 * 4));
+      } else {
+        CKS(buf_ensure(c, T.Chi, ncell * 8 * 2));
+        CKS(buf_ensure(c, T.Clo, ncell * 8 * 2));
       }
     }
     if (l >= c->lmin) {
@@ -556,16 +576,17 @@ struct TableSet {
   int refs = 0;
   Tables tab;
   DevBuf bufs[kNumTableBufs];
-  GemmOperand op_m2p, op_m2l;
+  GemmOperand op_m2p, op_m2l, op_m2p2, op_p2pr;
 };
-// (device, p, precision, p_m, allocator, allocator's user pointer): contexts of
-// another allocator get their own copy, released through that allocator
-using TableKey = std::tuple<int, int, int, int, uintptr_t, uintptr_t>;
+// (device, p, precision, p_m, Delta l, allocator, allocator's user pointer):
+// contexts of another allocator get their own copy, released through that allocator
+using TableKey = std::tuple<int, int, int, int, int, uintptr_t, uintptr_t>;
 std::mutex g_tables_mu;
 std::map<TableKey, TableSet*> g_tables;
 
 TableKey table_key(const Ctx* c) {
-  return TableKey(c->device, c->cfg.p, c->cfg.precision, c->cfg.p_m, (uintptr_t)c->alloc, (uintptr_t)c->alloc_user);
+  return TableKey(c->device, c->cfg.p, c->cfg.precision, c->cfg.p_m, c->cfg.delta_l, (uintptr_t)c->alloc,
+                  (uintptr_t)c->alloc_user);
 }
 
 fmm_status acquire_tables(Ctx* c) {
@@ -578,6 +599,8 @@ fmm_status acquire_tables(Ctx* c) {
     for (int i = 0; i < kNumTableBufs; ++i) c->*kTableBufs[i] = ts->bufs[i];
     c->op_m2p = ts->op_m2p;
     c->op_m2l = ts->op_m2l;
+    c->op_m2p2 = ts->op_m2p2;
+    c->op_p2pr = ts->op_p2pr;
     c->tables_on_device = true;
     c->tables_shared = true;
     return FMM_OK;
@@ -589,6 +612,8 @@ fmm_status acquire_tables(Ctx* c) {
   for (int i = 0; i < kNumTableBufs; ++i) ts->bufs[i] = c->*kTableBufs[i];
   ts->op_m2p = c->op_m2p;
   ts->op_m2l = c->op_m2l;
+  ts->op_m2p2 = c->op_m2p2;
+  ts->op_p2pr = c->op_p2pr;
   g_tables[table_key(c)] = ts;
   c->tables_shared = true;
   return FMM_OK;
@@ -604,7 +629,8 @@ void release_tables(Ctx* c) {
   TableSet* ts = it->second;
   if (--ts->refs > 0) {
     for (int i = 0; i < kNumTableBufs; ++i) c->*kTableBufs[i] = DevBuf();
-    for (GemmOperand* op : {&c->op_m2p, &c->op_m2l}) op->f64 = op->hi = op->lo = op->klimit = op->colmap = DevBuf();
+    for (GemmOperand* op : {&c->op_m2p, &c->op_m2l, &c->op_m2p2, &c->op_p2pr})
+      op->f64 = op->hi = op->lo = op->klimit = op->colmap = DevBuf();
   } else {
     g_tables.erase(it);
     delete ts;  // this context frees the buffers
@@ -662,10 +688,13 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_use
   if (cfg->bottom_mode != FMM_BOTTOM_M2P && cfg->bottom_mode != FMM_BOTTOM_M2L_L2P) return FMM_ERR_ARG;
   if (cfg->mass_fp32 != 0 && cfg->mass_fp32 != 1) return FMM_ERR_ARG;
   if (cfg->fp64_top != 0 && cfg->fp64_top != 1) return FMM_ERR_ARG;
+  if (cfg->delta_l < 0 || cfg->delta_l > 2) return FMM_ERR_ARG;
+  if (cfg->delta_l == 2 && cfg->bottom_mode != FMM_BOTTOM_M2P) return FMM_ERR_ARG;
   if (!std::isfinite(cfg->G)) return FMM_ERR_ARG;
   fmm_ctx* c = new fmm_ctx();
   c->cfg = *cfg;
   if (c->cfg.p_m == c->cfg.p) c->cfg.p_m = 0;  // one key for the full order
+  if (c->cfg.delta_l == 0) c->cfg.delta_l = 1;
   c->alloc = alloc;
   c->alloc_user = alloc_user;
   int dev = 0;
@@ -803,6 +832,10 @@ static fmm_status set_levels_impl(fmm_ctx* c, int lmin, int lmax, int lo, const 
   }
   for (int k = 0; k <= lmax - lo; ++k)
     if (n[k] < 0 || (n[k] > 0 && (!ijk[k] || !mass[k]))) return FMM_ERR_ARG;
+  if (c->cfg.delta_l == 2 && (lmin != lmax || lmin < 3)) {
+    c->last_error = "delta_l = 2 takes one complete level (lmin == lmax >= 3)";
+    return FMM_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
   ++c->n_set;
@@ -910,7 +943,9 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   // lmin, the levels b <= lo-3 (lo-2 in mode 1) only feed the L2L chain of the
   // ancestors of level lo: their ancestor lists replace the full row lists.
   const int m1 = c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P;
+  const bool dl2 = c->cfg.delta_l == 2;  // one level: lo == lmin, no stale trees
   const int top = top_local_level(c);
+  const int top_m2l = top_m2l_level(c);
   const bool restrict_dn = lo > lmin && c->anc_d == lo;
   std::vector<const int32_t*> drows(lmax + 1, nullptr);
   std::vector<int64_t> dn(lmax + 1, 0);
@@ -922,7 +957,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   std::vector<int> dl;  // box levels with M2L rows
   std::vector<const int32_t*> dr;
   std::vector<int64_t> dnr;
-  for (int b = 2; b <= top; ++b) {
+  for (int b = 2; b <= top_m2l; ++b) {
     if (drows[b] && !dn[b]) continue;
     dl.push_back(b);
     dr.push_back(drows[b]);
@@ -931,6 +966,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   if (!f64) launch_zero_lm(c, dl, dr, dnr, st);  // the M2L contraction adds into these sums
   if (d <= lmin || (d <= lmax && c->anc_d != d) || drift) {
     for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
+    if (dl2) launch_child_masses(c, st);
     for (int b = lmax - 1; b >= 2; --b) launch_upward(c, b, st);
     if (drift) launch_drift(c, lo, st);
   } else if (d <= lmax) {
@@ -951,20 +987,34 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   auto m2l_tc = [&](cudaStream_t s2) {
     if (!dl.empty()) launch_gemm_tc(c, c->op_m2l, kModeM2L, dl.data(), (int)dl.size(), s2, dr.data(), dnr.data());
   };
+  // Delta l = 2: the level lmax-2 expansions (read by the near field) are the
+  // L2L of lmax-3's, zero when lmax-3 < 2
   auto l2l_chain = [&](cudaStream_t s2) {
     if (!f64) {  // one launch: each block recomputes its ancestors' expansions
-      if (!dl.empty()) launch_l2l_path(c, lo, s2);
+      if (!dl.empty() || (dl2 && top >= 2)) launch_l2l_path(c, lo, s2);
       return;
     }
     for (size_t i = 0; i < dl.size(); ++i) {
       launch_l2l_add(c, dl[i], s2, dr[i], dnr[i]);
       if (f64) launch_gemm_f64(c, c->op_m2l, kModeM2L, dl[i], s2, dr[i], dnr[i]);
     }
+    if (dl2 && top >= 2) launch_l2l_add(c, top, s2);
   };
   // 3a. bottom intermediate field: M2P from level l-1 cells (bottom mode 1: in
   // the local expansions already)
   auto m2p = [&](cudaStream_t s2, int sm_budget) {
     if (m1) return;
+    if (dl2) {  // M2P from the level l-2 interaction list, P2P from the ring of level-l cells
+      const int l2 = lmax - 2, l1 = lmax - 1;
+      if (f64) {
+        launch_gemm_f64(c, c->op_m2p2, kModeM2P2, l2, s2);
+        launch_gemm_f64(c, c->op_p2pr, kModeP2PR, l1, s2);
+      } else {
+        launch_gemm_tc(c, c->op_m2p2, kModeM2P2, &l2, 1, s2, nullptr, nullptr, sm_budget);
+        launch_gemm_tc(c, c->op_p2pr, kModeP2PR, &l1, 1, s2, nullptr, nullptr, sm_budget);
+      }
+      return;
+    }
     std::vector<int> lv;
     for (int l = lo; l <= lmax; ++l) {
       if (!c->lev[l].n_leaf) continue;
@@ -1367,6 +1417,10 @@ fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const
     c->last_error = "fmm_solve_adjoint needs an FMM_FP64 context";
     return FMM_ERR_ARG;
   }
+  if (c->cfg.delta_l == 2) {
+    c->last_error = "fmm_solve_adjoint: delta_l = 1 only";
+    return FMM_ERR_ARG;
+  }
   if (c->cfg.bottom_mode != FMM_BOTTOM_M2P) {
     c->last_error = "fmm_solve_adjoint: the transposed chain follows the paper's bottom M2P only";
     return FMM_ERR_ARG;
@@ -1541,7 +1595,7 @@ void fmm_destroy(fmm_ctx* c) {
   release_tables(c);
   for (auto& T : c->lev) {
     for (DevBuf* b : {&T.oct_key, &T.oct_parent, &T.cell_child, &T.nbr, &T.leaf_cell, &T.rows, &T.rowsL, &T.irows, &T.leafmask, &T.gmass, &T.srcP, &T.srcL, &T.slotL, &T.lslot, &T.anc, &T.tgt, &T.ijk,
-                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc, &T.vel, &T.dS, &T.dQ})
+                      &T.mass, &T.M, &T.Mhi, &T.Mlo, &T.Chi, &T.Clo, &T.mono, &T.L, &T.Lf, &T.Lm, &T.acc, &T.vel, &T.dS, &T.dQ})
       buf_free(c, *b);
   }
   for (DevBuf* b : {&c->d_m2m_off, &c->d_m2m_g, &c->d_m2m_e, &c->d_m2m_c, &c->d_l2l_off, &c->d_l2l_off8, &c->d_l2l_g,
@@ -1549,7 +1603,9 @@ void fmm_destroy(fmm_ctx* c) {
                     &c->d_m2mT_off, &c->d_m2mT_a, &c->d_m2mT_c, &c->d_l2lT_off, &c->d_l2lT_b, &c->d_l2lT_e,
                     &c->d_l2lT_c, &c->d_m2pT, &c->d_m2lT, &c->d_near64, &c->d_near32, &c->d_l2p64, &c->d_l2p32,
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.colmap, &c->op_m2l.f64,
-                    &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
+                    &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->op_m2p2.f64, &c->op_m2p2.hi,
+                    &c->op_m2p2.lo, &c->op_m2p2.klimit, &c->op_p2pr.f64, &c->op_p2pr.hi, &c->op_p2pr.lo,
+                    &c->op_p2pr.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
                     &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->anc_flags, &c->out_stage, &c->in_stage,
                     &c->mass_stage, &c->err_buf, &c->d_alpha})
     buf_free(c, *b);

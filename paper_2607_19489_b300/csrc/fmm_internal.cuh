@@ -147,6 +147,9 @@ struct LevelTree {
   DevBuf Lf;             // float [8 n_rowsL][nc] FP32 copy of L read by the mixed near field
   DevBuf Lm;             // float [8 n_rowsL][nc] this level's M2L sum (mixed path), by slot;
                          // zero between solves (the L2L step clears what it consumes)
+  DevBuf Chi, Clo;       // Delta l = 2, level lmax-1: the 8 child masses of each cell as
+                         // contraction operand rows (bf16 hi/lo by op_index with nc = 8;
+                         // TF32: FP32 in Chi; FP64: double [cell][8] in Chi)
   DevBuf acc;            // [8 n_oct][4] M2P result (double or float), targets of this level;
                          // mixed path: zero between solves (the near field clears what it reads)
   bool m_is_f64 = true;
@@ -185,6 +188,7 @@ struct Ctx {
   DevBuf d_l2l_off, d_l2l_off8, d_l2l_g, d_l2l_e, d_l2l_c, d_l2l_c32;
   DevBuf d_near64, d_near32, d_l2p64, d_l2p32;
   GemmOperand op_m2p, op_m2l;
+  GemmOperand op_m2p2, op_p2pr;  // Delta l = 2: M2P from level l-2, P2P ring from level l-1
   // scratch
   DevBuf sort_tmp, keys_a, keys_b, vals_a, vals_b, flags, scan, err_word, counter;
   DevBuf anc_flags;     // uint8: one visited flag per oct of levels 1..anc_req-1 (ancestor walks)
@@ -311,12 +315,24 @@ void launch_adj_mark(Ctx* c, const int32_t* rows, int64_t nrows, const int32_t* 
 void launch_adjoint(Ctx* c, int lo, const void* const* g_phi, const void* const* g_accel, int in_fp32,
                     cudaStream_t st);
 
-enum { kModeM2P = 0, kModeM2L = 1 };
+// contraction modes: the bottom M2P (rows of level l-1, targets their
+// grandchildren), M2L, the Delta l = 2 M2P (rows of level l-2, targets three
+// levels down) and the Delta l = 2 near-field ring (P2P from child masses,
+// rows and targets as kModeM2P)
+enum { kModeM2P = 0, kModeM2L = 1, kModeM2P2 = 2, kModeP2PR = 3 };
+// operator kinds of build_operator
+enum { kOpM2P = 0, kOpM2L = 1, kOpP2P = 2 };
+
+// Delta l = 2: the 8 child masses of every cell of level lmax-1 as operand rows
+void launch_child_masses(Ctx* c, cudaStream_t st);
 
 // Highest box level holding local expansions: lmax-2 (the paper's bottom
 // M2P), lmax-1 with bottom mode 1 (M2L into the parent box, then L2P).
+// With Delta l = 2 the level lmax-2 expansions are the L2L of lmax-3's (the
+// near field reads them there) and M2L stops one level higher.
 inline int top_local_level(const Ctx* c) {
   return c->lmax - 2 + (c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P ? 1 : 0);
 }
+inline int top_m2l_level(const Ctx* c) { return top_local_level(c) - (c->cfg.delta_l == 2 ? 1 : 0); }
 
 }  // namespace fmm

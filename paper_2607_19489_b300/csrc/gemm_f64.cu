@@ -11,7 +11,10 @@
 // which skips the zeros of M2L entirely.  Small levels split the 26 offsets
 // over grid.z (partial sums added with FP64 atomics) so that every SM has work;
 // M2P adds only into leaf targets, whose accumulators are zero between solves
-// (the near-field kernel clears what it reads).
+// (the near-field kernel clears what it reads).  The Delta l = 2 variant
+// (footnote of Sec. 2) adds M2P from the level l-2 grid (2048 columns, the 512
+// level-l cells under a row oct) and the near-field ring (the sources are the
+// 8 child masses of each level l-1 cell: P2P as a contraction).
 #include "fmm_internal.cuh"
 
 namespace fmm {
@@ -33,6 +36,7 @@ struct F64Params {
   int mode;
   double* acc;              // M2P: [cells of level l][4]
   const int32_t* cell_child_rows;
+  const int32_t* cell_child_mid;  // M2P2: cell_child of the level between rows and targets
   const int32_t* cell_child_tgt;  // M2P: cell_child of the target level (refined targets get nothing)
   int q_per_split;          // neighbour offsets per grid.z slice
   double* L;                // M2L: [slot*8 + cell][nc]
@@ -92,7 +96,13 @@ __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
     int64_t ri = r0 + r;
     if (ri >= P.nrows) break;
     int32_t o = P.rows[ri];
-    if (P.mode == kModeM2P) {
+    if (P.mode == kModeM2P2) {
+      const int g = n >> 8, f = (n >> 5) & 7, t = (n >> 2) & 7, comp = n & 3;
+      const int32_t mid = P.cell_child_rows[(int64_t)o * 8 + g];
+      const int32_t ch = mid >= 0 ? P.cell_child_mid[(int64_t)mid * 8 + f] : -1;
+      if (ch >= 0 && P.cell_child_tgt[(int64_t)ch * 8 + t] < 0)
+        atomicAdd(&P.acc[((int64_t)ch * 8 + t) * 4 + comp], acc[r]);
+    } else if (P.mode != kModeM2L) {
       int f = n >> 5, t = (n >> 2) & 7, comp = n & 3;
       int32_t ch = P.cell_child_rows[(int64_t)o * 8 + f];
       if (ch >= 0 && P.cell_child_tgt[(int64_t)ch * 8 + t] < 0)
@@ -109,12 +119,15 @@ __global__ void __launch_bounds__(256) k_gemm_f64(F64Params P) {
 void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream_t st, const int32_t* rows,
                      int64_t nrows) {
   LevelTree& R = c->lev[lr];
-  // M2P: octs with a refined cell; M2L: octs with a cell that has grandchildren
-  const int64_t nr = rows ? nrows : ((mode == kModeM2P) ? R.n_rows : R.n_rowsL);
+  // M2P (and the Delta l = 2 modes): octs with a refined cell; M2L: octs with a
+  // cell that has grandchildren
+  const bool m2l = mode == kModeM2L;
+  const int lt = lr + (mode == kModeM2P2 ? 2 : 1);  // target level of the bottom modes
+  const int64_t nr = rows ? nrows : (m2l ? R.n_rowsL : R.n_rows);
   if (!nr) return;
   F64Params P;
-  P.M = (const double*)R.M.ptr;
-  P.rows = rows ? rows : (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
+  P.M = (const double*)(mode == kModeP2PR ? R.Chi.ptr : R.M.ptr);
+  P.rows = rows ? rows : (const int32_t*)(m2l ? R.rowsL.ptr : R.rows.ptr);
   P.slot = (const int32_t*)R.slotL.ptr;
   P.nrows = nr;
   P.nbr = (const int32_t*)R.nbr.ptr;
@@ -122,12 +135,13 @@ void launch_gemm_f64(Ctx* c, const GemmOperand& op, int mode, int lr, cudaStream
   P.klimit = (const int32_t*)op.klimit.ptr;
   P.KQ = op.kseg;
   P.N = op.N;
-  P.nc = c->tab.nc;
+  P.nc = mode == kModeP2PR ? 8 : c->tab.nc;
   P.mode = mode;
-  P.acc = (mode == kModeM2P) ? (double*)c->lev[lr + 1].acc.ptr : nullptr;
+  P.acc = m2l ? nullptr : (double*)c->lev[lt].acc.ptr;
   P.cell_child_rows = (const int32_t*)R.cell_child.ptr;
-  P.cell_child_tgt = (mode == kModeM2P) ? (const int32_t*)c->lev[lr + 1].cell_child.ptr : nullptr;
-  P.L = (mode == kModeM2L) ? (double*)R.L.ptr : nullptr;
+  P.cell_child_mid = mode == kModeM2P2 ? (const int32_t*)c->lev[lr + 1].cell_child.ptr : nullptr;
+  P.cell_child_tgt = m2l ? nullptr : (const int32_t*)c->lev[lt].cell_child.ptr;
+  P.L = m2l ? (double*)R.L.ptr : nullptr;
   // split the 26 offsets until about two blocks per SM are in flight
   const int64_t blocks2 = ((nr + TM - 1) / TM) * ((op.N + 255) / 256);
   int split = (int)std::min<int64_t>(26, std::max<int64_t>(1, (2 * c->num_sms + blocks2 - 1) / blocks2));

@@ -5,6 +5,10 @@
 // grid, k = (q, s, alpha) runs over the 26 neighbour octs of its parent, their
 // 8 cells and the multipole coefficients, and B is the translation operator
 // (translation invariant, so one table serves every oct and every level).
+// The Delta l = 2 variant (footnote of Sec. 2) adds two modes: M2P from the
+// level l-2 grid (2048 columns: the 512 level-l cells under a row oct, found
+// through two child links) and the near-field ring, whose "coefficients" are
+// the 8 child masses of each source cell (exact P2P as a contraction).
 // Each operand is split x = hi + lo with hi, lo in BF16; the product keeps
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).  In TF32
 // precision each operand is one FP32 value rounded to TF32 and each product is
@@ -74,6 +78,7 @@ struct TcSeg {
   const int32_t* rows;
   const int32_t* nbr;
   const int32_t* cell_child_rows;  // M2P: cell_child of the row level
+  const int32_t* cell_child_mid;   // M2P2: cell_child of the level between rows and targets
   const int32_t* cell_child_tgt;   // M2P: cell_child of the target level (refined targets get nothing)
   const uint8_t* leafmask_tgt;     // M2P: leaf masks of the target level (or null: use cell_child_tgt)
   const int32_t* slot;             // M2L: local-expansion slot of each row oct
@@ -400,13 +405,27 @@ __global__ void __launch_bounds__(THREADS, 1)
       int32_t ch[8];
       uint32_t tmask[8];
       int64_t slot = 0;
-      if (P.mode == kModeM2P) {
+      if (P.mode == kModeM2P2) {
+        // 32 columns = the 8 targets of one level-l oct: cell f & 7 of the child
+        // oct of cell f >> 3 of the row oct
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          ch[j] = -1;
+          const int f = (ytile * P.BN + j * 32) >> 5;
+          if (valid && j < nchunk && f < 64) {
+            const int32_t mid = S.cell_child_rows[(int64_t)roct * 8 + (f >> 3)];
+            if (mid >= 0) ch[j] = S.cell_child_mid[(int64_t)mid * 8 + (f & 7)];
+          }
+        }
+      } else if (P.mode != kModeM2L) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           ch[j] = -1;
           const int f = (ytile * P.BN + j * 32) >> 5;
           if (valid && j < nchunk && f < 8) ch[j] = S.cell_child_rows[(int64_t)roct * 8 + f];
         }
+      }
+      if (P.mode != kModeM2L) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           tmask[j] = 0;
@@ -432,7 +451,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (!have || !valid) continue;
         const int n0 = ytile * P.BN + j * 32;
-        if (P.mode == kModeM2P) {
+        if (P.mode != kModeM2L) {
           if (ch[j] >= 0) {
             float* dst = S.out + (int64_t)ch[j] * 32;
 #pragma unroll
@@ -631,20 +650,24 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   for (int i = 0; i < nlev && P.nseg < kMaxSeg; ++i) {
     const int lr = levels[i];  // row level
     LevelTree& R = c->lev[lr];
-    // M2P: octs with a refined cell (their children hold the targets);
-    // M2L: octs with a cell that has grandchildren (those need a local expansion)
-    const int64_t nr = (rows && rows[i]) ? nrows[i] : ((mode == kModeM2P) ? R.n_rows : R.n_rowsL);
+    // M2P (and the ring P2P, Delta l = 2's M2P): octs with a refined cell (their
+    // descendants hold the targets); M2L: octs with a cell that has grandchildren
+    // (those need a local expansion)
+    const bool m2l = mode == kModeM2L;
+    const int lt = lr + (mode == kModeM2P2 ? 2 : 1);  // target level of the bottom modes
+    const int64_t nr = (rows && rows[i]) ? nrows[i] : (m2l ? R.n_rowsL : R.n_rows);
     if (!nr) continue;
     TcSeg& S = P.seg[P.nseg++];
-    S.Ahi = (const __nv_bfloat16*)R.Mhi.ptr;
-    S.Alo = (const __nv_bfloat16*)R.Mlo.ptr;
-    S.rows = (rows && rows[i]) ? rows[i] : (const int32_t*)((mode == kModeM2P) ? R.rows.ptr : R.rowsL.ptr);
-    S.cell_child_tgt = (mode == kModeM2P) ? (const int32_t*)c->lev[lr + 1].cell_child.ptr : nullptr;
-    S.leafmask_tgt = (mode == kModeM2P) ? (const uint8_t*)c->lev[lr + 1].leafmask.ptr : nullptr;
+    S.Ahi = (const __nv_bfloat16*)(mode == kModeP2PR ? R.Chi.ptr : R.Mhi.ptr);
+    S.Alo = (const __nv_bfloat16*)(mode == kModeP2PR ? R.Clo.ptr : R.Mlo.ptr);
+    S.rows = (rows && rows[i]) ? rows[i] : (const int32_t*)(m2l ? R.rowsL.ptr : R.rows.ptr);
+    S.cell_child_tgt = m2l ? nullptr : (const int32_t*)c->lev[lt].cell_child.ptr;
+    S.leafmask_tgt = m2l ? nullptr : (const uint8_t*)c->lev[lt].leafmask.ptr;
+    S.cell_child_mid = mode == kModeM2P2 ? (const int32_t*)c->lev[lr + 1].cell_child.ptr : nullptr;
     S.slot = (const int32_t*)R.slotL.ptr;
     S.nbr = (const int32_t*)R.nbr.ptr;
     S.cell_child_rows = (const int32_t*)R.cell_child.ptr;
-    S.out = (mode == kModeM2P) ? (float*)c->lev[lr + 1].acc.ptr : (float*)R.Lm.ptr;
+    S.out = m2l ? (float*)R.Lm.ptr : (float*)c->lev[lt].acc.ptr;
     S.nrows = (int)nr;
     S.tile0 = tiles;
     if ((uintptr_t)S.Ahi % 32 || (uintptr_t)S.Alo % 32) P.v8 = 0;
@@ -655,7 +678,7 @@ void launch_gemm_tc(Ctx* c, const GemmOperand& op, int mode, const int* levels, 
   P.KQP = op.kqp;
   std::vector<int> chunks(op.ntile);
   for (int y = 0; y < op.ntile; ++y) chunks[y] = 26 * op.tile_slices[y];
-  const int tuned = c->tune_split[mode == kModeM2P ? 0 : 1];
+  const int tuned = c->tune_split[mode == kModeM2L ? 1 : 0];
   P.chunks_per_split = choose_chunks_per_split(tiles, chunks, sm_budget > 0 ? sm_budget : c->num_sms, tuned);
   P.nyz = 0;
   for (int y = 0; y < op.ntile; ++y)

@@ -270,4 +270,68 @@ void Tables::build(int p_, int p_m) {
   }
 }
 
+
+void Tables::build_dl2() {
+  const int K = 26 * 8 * nc, KP = 26 * 64;
+  std::vector<double> D;
+  m2p2.assign((size_t)2048 * K, 0.0);
+  for (int g = 0; g < 8; ++g)
+    for (int qi = 0; qi < 26; ++qi) {
+      const int q27 = kNbr26[qi];
+      const int dq[3] = {q27 % 3 - 1, (q27 / 3) % 3 - 1, q27 / 9 - 1};
+      for (int s = 0; s < 8; ++s) {
+        int rel[3], adj = 1;
+        for (int i = 0; i < 3; ++i) {
+          rel[i] = bit(g, i) - 2 * dq[i] - bit(s, i);  // c_G - c_S in level l-2 cells
+          if (std::abs(rel[i]) > 1) adj = 0;
+        }
+        if (adj) continue;  // S touches G: near field
+        for (int f = 0; f < 8; ++f)
+          for (int t = 0; t < 8; ++t) {
+            int64_t u[3];
+            for (int i = 0; i < 3; ++i) u[i] = 8 * rel[i] + 4 * bit(f, i) + 2 * bit(t, i) - 3;  // 8 (c_t - c_S)
+            deriv_g(u, 8.0, p + 1, mi, D);
+            const size_t n0 = (size_t)((g * 8 + f) * 8 + t) * 4;
+            for (int a = 0; a < nc; ++a) {
+              if (degree[a] > pm) continue;
+              const auto& al = mi.list[a];
+              const double w = ((degree[a] & 1) ? -1.0 : 1.0) / mfact(al);
+              const size_t k = (size_t)(qi * 8 + s) * nc + a;
+              // level l-2 units to level l-1 units: phi x 1/2, accel x 1/4
+              m2p2[(n0 + 0) * K + k] = 0.5 * w * D[mi.at(al[0], al[1], al[2])];
+              m2p2[(n0 + 1) * K + k] = -0.25 * w * D[mi.at(al[0] + 1, al[1], al[2])];
+              m2p2[(n0 + 2) * K + k] = -0.25 * w * D[mi.at(al[0], al[1] + 1, al[2])];
+              m2p2[(n0 + 3) * K + k] = -0.25 * w * D[mi.at(al[0], al[1], al[2] + 1)];
+            }
+          }
+      }
+    }
+  p2pr.assign((size_t)256 * KP, 0.0);
+  for (int f = 0; f < 8; ++f)
+    for (int qi = 0; qi < 26; ++qi) {
+      const int q27 = kNbr26[qi];
+      const int dq[3] = {q27 % 3 - 1, (q27 / 3) % 3 - 1, q27 / 9 - 1};
+      for (int s = 0; s < 8; ++s) {
+        int rel[3], adj = 1;
+        for (int i = 0; i < 3; ++i) {
+          rel[i] = bit(f, i) - 2 * dq[i] - bit(s, i);  // c_F - c_S in level l-1 cells
+          if (std::abs(rel[i]) > 1) adj = 0;
+        }
+        if (adj) continue;  // S touches F: Delta l = 1's near field
+        for (int t = 0; t < 8; ++t)
+          for (int kc = 0; kc < 8; ++kc) {
+            int64_t u[3];
+            for (int i = 0; i < 3; ++i) u[i] = 2 * rel[i] + bit(t, i) - bit(kc, i);  // 2 (c_t - c_child)
+            deriv_g(u, 2.0, 1, mi, D);
+            const size_t n0 = (size_t)(f * 8 + t) * 4;
+            const size_t k = (size_t)(qi * 8 + s) * 8 + kc;
+            p2pr[(n0 + 0) * KP + k] = D[mi.at(0, 0, 0)];
+            p2pr[(n0 + 1) * KP + k] = -D[mi.at(1, 0, 0)];
+            p2pr[(n0 + 2) * KP + k] = -D[mi.at(0, 1, 0)];
+            p2pr[(n0 + 3) * KP + k] = -D[mi.at(0, 0, 1)];
+          }
+      }
+    }
+}
+
 }  // namespace fmm

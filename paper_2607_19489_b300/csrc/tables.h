@@ -70,7 +70,20 @@ struct Tables {
   // degree of each coefficient (|alpha|) for alpha < nc
   std::vector<int> degree;
 
+  // Delta l = 2 (footnote of Sec. 2; unigrids), built by build_dl2():
+  // M2P from the interaction list of the level l-2 box G: rows of the level
+  // l-2 grid, output n = ((g*8+f)*8+t)*4+comp for target t of cell f of the
+  // child oct of cell g, input k = (qi*8+s)*nc + alpha; results in level l-1
+  // units (the accumulator's).
+  std::vector<double> m2p2;  // [2048][26*8*nc]
+  // the near-field ring: P2P from the level-l children of the level l-1 cells
+  // in the interaction list of the target's parent F (inside the 12^3 near
+  // field of Delta l = 2 but outside Delta l = 1's 6^3): rows of the level l-1
+  // grid, output as m2p, input k = (qi*8+s)*8 + child; level l-1 units.
+  std::vector<double> p2pr;  // [256][26*64]
+
   void build(int p, int p_m = 0);  // p_m = 0: p
+  void build_dl2();
 };
 
 }  // namespace fmm

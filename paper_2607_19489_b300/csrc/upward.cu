@@ -93,6 +93,27 @@ __global__ void k_leaf_mono(int64_t ncell, const int32_t* __restrict__ cell_chil
   mono[i] = (TMono)mass[-1 - (int64_t)ch];
 }
 
+// Delta l = 2: the masses of the 8 children of every cell of level lmax-1, as
+// the operand rows of the near-field ring contraction (one thread per child;
+// consecutive threads write consecutive entries of an oct's row).
+template <typename TMono>
+__global__ void k_child_masses(int64_t n, const int32_t* __restrict__ cell_child, const TMono* __restrict__ mono,
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                               double* __restrict__ f64) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t cell = (i >> 6) * 8 + (i & 7);  // i = 64 oct + 8 child + cell in oct
+  const int k = (int)((i >> 3) & 7);
+  const int32_t ch = cell_child[cell];
+  const TMono v = ch >= 0 ? mono[(int64_t)ch * 8 + k] : (TMono)0;
+  if (f64)
+    f64[cell * 8 + k] = (double)v;
+  else
+    put_operand(v, hi, lo, op_index(cell, k, 8));
+}
+
 // Coefficient rows of the leaf cells that a contraction can read: a leaf is a
 // source of M2L or M2P only when its oct lies in the 3^3 neighbourhood of an
 // oct with a refined cell, i.e. only in the interface octs (irows).  Those
@@ -665,6 +686,24 @@ fmm_status upward_init(Ctx* c) {
     return FMM_ERR_CUDA;
   }
   return FMM_OK;
+}
+
+void launch_child_masses(Ctx* c, cudaStream_t st) {
+  const int l1 = c->lmax - 1;
+  LevelTree& T = c->lev[l1];
+  const int64_t n = 64 * T.n_oct;
+  if (l1 < 1 || !n) return;
+  const int32_t* cc = (const int32_t*)T.cell_child.ptr;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  ++c->n_launch;
+  if (c->cfg.precision == FMM_FP64) {
+    launch_pdl(k_child_masses<double>, g, 256, 0, st, n, cc, (const double*)c->lev[c->lmax].mono.ptr,
+               (__nv_bfloat16*)nullptr, (__nv_bfloat16*)nullptr, (double*)T.Chi.ptr);
+  } else {
+    __nv_bfloat16* lo = c->cfg.precision == FMM_MIXED_TF32 ? nullptr : (__nv_bfloat16*)T.Clo.ptr;
+    launch_pdl(k_child_masses<float>, g, 256, 0, st, n, cc, (const float*)c->lev[c->lmax].mono.ptr,
+               (__nv_bfloat16*)T.Chi.ptr, lo, (double*)nullptr);
+  }
 }
 
 void launch_mono_leaves(Ctx* c, int l, cudaStream_t st) {

@@ -39,7 +39,8 @@ class FMMError(RuntimeError):
 class _Config(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("G", ctypes.c_double),
                 ("out_fp32", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("bottom_mode", ctypes.c_int),
-                ("p_m", ctypes.c_int), ("mass_fp32", ctypes.c_int), ("fp64_top", ctypes.c_int)]
+                ("p_m", ctypes.c_int), ("mass_fp32", ctypes.c_int), ("fp64_top", ctypes.c_int),
+                ("delta_l", ctypes.c_int)]
 
 
 # fmm_alloc_fn: (user, ptr, bytes, stream) -> ptr
@@ -170,20 +171,23 @@ class Solver:
     parent box + L2P); p_m: multipole order of the translations (None: p);
     mass_fp32: masses are given as float32; fp64_top: mixed precisions keep FP64
     for the top-of-tree M2M and the L2L chain / local-expansion accumulation;
-    allocator: "torch" (PyTorch's caching allocator supplies the library's device
+    delta_l: levels between the cells and the finest FMM box, 1 (the paper's) or 2
+    (the variant of the footnote of Sec. 2: a 12^3-cell near field; one complete
+    level only); allocator: "torch" (PyTorch's caching allocator supplies the library's device
     memory) or "cuda" (cudaMalloc)."""
 
     def __init__(self, p: int = 6, precision: str = "mixed", G: float = 1.0, out_fp32: bool = False,
                  mem_budget: int = 0, bottom: str = "m2p", p_m: int | None = None, mass_fp32: bool = False,
-                 allocator: str = "torch", fp64_top: bool = False):
+                 allocator: str = "torch", fp64_top: bool = False, delta_l: int = 1):
         self.p = p
         self.precision = precision
         self.out_fp32 = out_fp32
         self.mass_fp32 = mass_fp32
         self.bottom = bottom
         self.p_m = p if p_m is None else p_m
+        self.delta_l = delta_l
         cfg = _Config(p, PRECISION[precision], float(G), int(out_fp32), int(mem_budget), BOTTOM[bottom],
-                      0 if p_m is None else int(p_m), int(mass_fp32), int(fp64_top))
+                      0 if p_m is None else int(p_m), int(mass_fp32), int(fp64_top), int(delta_l))
         if allocator not in ("torch", "cuda"):
             raise ValueError("allocator must be 'torch' or 'cuda'")
         h = ctypes.c_void_p()
