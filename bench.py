@@ -495,7 +495,7 @@ def gpu_arm(args, rank, world, local):
     legs = [x for x in args.legs.split(",") if x and x != "none"] if not args.quick else []
     for name in legs:
         fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats, "sweep": leg_sweep,
-              "binary": leg_binary}.get(name)
+              "binary": leg_binary, "delta_l": leg_delta_l}.get(name)
         if fn is None:
             continue
         try:
@@ -671,6 +671,65 @@ def leg_sweep(args, torch, dev, stream, flush):
     del keep
     return {"unit": UNIT, "step": "fmm_set_levels + fmm_solve (inputs resident)", "runs": rows,
             "reference": "fmm_direct_sum (FP64 exact sum) on the listed cells", "wall_s": time.perf_counter() - t0}
+
+
+def leg_delta_l(args, torch, dev, stream, flush):
+    """Delta l = 1 (the paper's) against Delta l = 2 (the footnote of Sec. 2,
+    which Paper I tested on unigrids: a 12^3-cell near field, M2P one box level
+    up, M2L one level shorter) on the Plummer unigrids 32^3, 64^3 and 128^3, at
+    p = 4 and 6 in FP64, split-BF16 and TF32.  Each entry: cell-updates/s of
+    fmm_set_levels + fmm_solve, the in-order stage times of one solve, and the
+    relative RMS error against the exact sum (fmm_direct_sum, FP64) on 4096
+    seeded cells."""
+    from paper_2607_19489_b300 import fmm, workloads as W
+    rows = []
+    t0 = time.perf_counter()
+    for level in (5, 6, 7):
+        h = W.unigrid_plummer(level)
+        ijk = [torch.as_tensor(a, device=dev).contiguous() for a in h.ijk]
+        mass = [torch.as_tensor(m, device=dev).contiguous() for m in h.mass]
+        l = h.lmin
+        sel = torch.as_tensor(np.unique((W.uniform(67, l, np.arange(4096)) * h.n(l)).astype(np.int64)), device=dev)
+        ref = fmm.Solver(4, "fp64")
+        ref.set_levels(l, l, ijk, mass)
+        d_phi, d_acc = ref.direct_sum(l, sel)
+        ref.sync()
+        del ref
+        for p in (4, 6):
+            for prec in ("fp64", "mixed", "tf32"):
+                if prec == "fp64" and level == 7:
+                    continue  # seconds per solve; the two smaller grids carry the FP64 comparison
+                for dl in (1, 2):
+                    s = fmm.Solver(p, prec, delta_l=dl)
+                    s.set_levels(l, l, ijk, mass)
+                    out = s.alloc_outputs(device=dev)
+
+                    def step():
+                        s.set_levels(l, l, ijk, mass)
+                        s.solve(out=out)
+
+                    K = 2 if prec == "fp64" else 10
+                    ms = _timed(torch, step, K, 3, stream)
+                    s.sync()
+                    ga = out[1][l][sel].double()
+                    gp = out[0][l][sel].double()
+                    s.set_timing(True)
+                    s.update_masses(mass)
+                    s.solve(out=out)
+                    s.sync()
+                    st = s.stage_times()
+                    s.set_timing(False)
+                    rows.append({"grid": f"{2 ** level}^3", "p": p, "precision": prec, "delta_l": dl,
+                                 "cells": h.n_cells, "ms": ms, "value": h.n_cells / (ms * 1e-3),
+                                 "stages_ms": st,
+                                 "rel_rms_accel_vs_direct": float(((ga - d_acc) ** 2).sum().sqrt() /
+                                                                  (d_acc ** 2).sum().sqrt()),
+                                 "rel_rms_phi_vs_direct": float(((gp - d_phi) ** 2).sum().sqrt() /
+                                                                (d_phi ** 2).sum().sqrt())})
+                    del s, out
+    return {"unit": UNIT, "step": "fmm_set_levels + fmm_solve (inputs resident)", "runs": rows,
+            "workload": "Plummer unigrids (a = 0.1, 1% noise)",
+            "reference": "fmm_direct_sum (FP64 exact sum) on 4096 seeded cells", "wall_s": time.perf_counter() - t0}
 
 
 def leg_binary(args, torch, dev, stream, flush):
@@ -951,7 +1010,7 @@ def main():
                     help="two_level: the measured configuration; unigrid16: a small check of the launch paths")
     ap.add_argument("--fd-cells", type=int, default=100,
                     help="adjoint leg: finite differences on this many seeded cells (one FP64 solve each)")
-    ap.add_argument("--legs", default="sweep,batched,adjoint,ats,binary",
+    ap.add_argument("--legs", default="sweep,batched,adjoint,ats,binary,delta_l",
                     help="extra workloads reported beside the headline (comma list, or 'none')")
     ap.add_argument("--quick", action="store_true",
                     help="the mixed headline and its stage times only (no FP64 arm, e2e, legs or CPU baseline)")
