@@ -47,6 +47,11 @@ def lib():
                                        P, ctypes.c_int]
         L.oracle_fmm_solve_dl2.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                            P, P, P, P, ctypes.c_int]
+        L.oracle_fmm_solve_periodic.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P, P, P, ctypes.c_int]
+        L.oracle_ewald_sum.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, P, P, P, P, ctypes.c_int]
+        L.oracle_lattice_tensor.argtypes = [ctypes.c_int, ctypes.c_double, P]
         L.oracle_direct_sum.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_double,
                                         ctypes.c_int, P, P, P, P, ctypes.c_int]
         L.oracle_tree.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P]
@@ -155,6 +160,27 @@ def solve_dl2(h, p: int, G: float = 1.0, sel: dict | None = None, threads: int |
         return lib().oracle_fmm_solve_dl2(lmin, n, ijk, mass, p_, G_, pm_, nsel, sel_, phi, acc, threads_)
 
     return _call(fn, h, None, sel, (p, G, 0 if p_m is None else p_m), threads)
+
+
+def solve_periodic(h, p: int, G: float = 1.0, lo: int | None = None, sel: dict | None = None,
+                   threads: int | None = None, p_m: int | None = None):
+    """FMM with periodic boundaries (images everywhere, neutralising background;
+    see fmm_oracle.cpp), bottom M2P, lmin >= 3.  Returns (phi, acc) dicts."""
+    return _call(lib().oracle_fmm_solve_periodic, h, lo, sel, (p, G, 0 if p_m is None else p_m), threads)
+
+
+def ewald(h, G: float = 1.0, alpha: float = 8.0, lo: int | None = None, sel: dict | None = None,
+          threads: int | None = None):
+    """The periodic potential and acceleration by Ewald's sum over all pairs
+    (splitting parameter alpha >= 6; the result does not depend on it)."""
+    return _call(lib().oracle_ewald_sum, h, lo, sel, (G, float(alpha)), threads)
+
+
+def lattice_tensor(q: int, alpha: float = 2.0) -> np.ndarray:
+    """T_gamma = d^gamma psi_far(0), |gamma| <= q, in multi-index order."""
+    out = np.zeros(ncoef(q))
+    lib().oracle_lattice_tensor(q, float(alpha), _ptr(out))
+    return out
 
 
 def direct(h, G: float = 1.0, lo: int | None = None, sel: dict | None = None,

@@ -54,6 +54,25 @@
 //     is the direct sum over the cells of G's 3^3 neighbours (12^3 = 1728
 //     cells less the target).
 //
+// Periodic boundaries (an extension: Sec. 6 names periodic domains as the next
+// step for cosmology without fixing a method).  The unit box tiles space, every
+// cell has images at all integer offsets n, and a uniform background of the
+// opposite total mass makes the problem solvable (lap phi = 4 pi G (rho -
+// mean rho)).  The pair potential is Ewald's lattice sum, written in this
+// solver's sign convention g = -1/r (box volume 1, splitting parameter a):
+//   psi(r) = -[ sum_n erfc(a|r+n|)/|r+n|
+//               + (1/pi) sum_{k != 0} exp(-pi^2 k^2 / a^2) / k^2 cos(2 pi k.r) - pi/a^2 ]
+// which does not depend on a and has zero mean over the box.  A cell's own
+// images act on it (psi minus its 1/r singularity).  The FMM reading: every
+// neighbour and interaction list wraps around the box at every level (the
+// geometry is that of the image, the content that of the wrapped box); the
+// root's 3^3 images reach the targets through the lists of levels 1 and
+// below, with M2L now also at box level 1; every farther image, and the
+// background, reaches the root's local expansion through the lattice tensor
+// T_gamma = d^gamma psi_far(0), psi_far = psi minus the 27 nearest images of
+// g (Eq. 3 with D = T and the root multipole as the source), which L2L hands
+// down to level 1.  Periodic solves need lmin >= 3.
+//
 // Parity status: pinned by the tests in tests/test_oracle_*.py against the
 // O(N^2) direct sum (exact agreement where the FMM has no far field, error
 // falling with p elsewhere), closed forms of the derivatives of 1/r, the M2M
@@ -67,6 +86,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <set>
 #include <vector>
 #ifdef _OPENMP
@@ -340,6 +360,183 @@ inline void p2p(double m, const double* y, const double* x, double* phi, double*
 }
 
 // ---------------------------------------------------------------------------
+// Periodic boundaries: Ewald's pair potential psi (see the header) and the
+// lattice tensor of the root.
+constexpr double kPi = 3.14159265358979323846;
+
+// psi(r) and grad psi(r) for r in (-1, 1)^3, r != 0.  With a >= 6 every image
+// beyond the 27 around r adds less than erfc(a) (< 2e-17), and the reciprocal
+// sum stops where exp(-pi^2 k^2 / a^2) < exp(-40).
+struct Ewald {
+  double a;
+  int kmax;
+  std::vector<std::array<double, 4>> kv;  // (kx, ky, kz, weight (1/pi) exp(-pi^2 k^2/a^2)/k^2)
+  explicit Ewald(double a_) : a(a_) {
+    kmax = (int)std::ceil(a * std::sqrt(40.0) / kPi);
+    for (int z = -kmax; z <= kmax; ++z)
+      for (int y = -kmax; y <= kmax; ++y)
+        for (int x = -kmax; x <= kmax; ++x) {
+          if (!x && !y && !z) continue;
+          double k2 = (double)(x * x + y * y + z * z);
+          double w = std::exp(-kPi * kPi * k2 / (a * a)) / (kPi * k2);
+          if (w < 1e-300) continue;
+          kv.push_back({(double)x, (double)y, (double)z, w});
+        }
+  }
+  // erfc(a rho)/rho and its derivative factor: grad = -x (erfc(a rho) + 2 a rho e^{-a^2 rho^2}/sqrt(pi)) / rho^3
+  void real(const double* x, double* v, double* g) const {
+    double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    double r = std::sqrt(r2);
+    double e = std::erfc(a * r);
+    *v += e / r;
+    double f = -(e + 2.0 * a * r * std::exp(-a * a * r2) / std::sqrt(kPi)) / (r2 * r);
+    for (int i = 0; i < 3; ++i) g[i] += f * x[i];
+  }
+  // psi and grad psi at r (r not a lattice point)
+  void pair(const double* r, double* psi, double* grad) const {
+    double v = 0.0, g[3] = {0.0, 0.0, 0.0};
+    for (int nz = -1; nz <= 1; ++nz)
+      for (int ny = -1; ny <= 1; ++ny)
+        for (int nx = -1; nx <= 1; ++nx) {
+          double x[3] = {r[0] + nx, r[1] + ny, r[2] + nz};
+          real(x, &v, g);
+        }
+    for (const auto& k : kv) {
+      double ph = 2.0 * kPi * (k[0] * r[0] + k[1] * r[1] + k[2] * r[2]);
+      v += k[3] * std::cos(ph);
+      double s = -k[3] * 2.0 * kPi * std::sin(ph);
+      for (int i = 0; i < 3; ++i) g[i] += s * k[i];
+    }
+    v -= kPi / (a * a);
+    *psi = -v;
+    for (int i = 0; i < 3; ++i) grad[i] = -g[i];
+  }
+  // lim_{r -> 0} psi(r) + 1/r: what a cell's own images (and the background) add
+  double self() const {
+    double v = 0.0, g[3];
+    for (int nz = -1; nz <= 1; ++nz)
+      for (int ny = -1; ny <= 1; ++ny)
+        for (int nx = -1; nx <= 1; ++nx) {
+          if (!nx && !ny && !nz) continue;
+          double x[3] = {(double)nx, (double)ny, (double)nz};
+          real(x, &v, g);
+        }
+    for (const auto& k : kv) v += k[3];
+    v += -kPi / (a * a) - 2.0 * a / std::sqrt(kPi);
+    return -v;
+  }
+};
+
+// Lattice tensor T_gamma = d^gamma psi_far(0), |gamma| <= q, where psi_far is
+// psi minus g over the 27 images n in {-1,0,1}^3.  By the Ewald split:
+//   T = -sum_{n != 0} d^gamma [erfc(a|x|)/|x|](n) + d^gamma [erf(a r)/r](0)
+//       - (1/pi) sum_k e^{-pi^2 k^2/a^2}/k^2 d^gamma cos(2 pi k.x)(0) + pi/a^2 [gamma = 0]
+//       + sum_{n in 27, n != 0} d^gamma (1/|x|)(n).
+// The real-space derivatives of the radial f(rho) = erfc(a rho)/rho use
+// d_i f_k = x_i f_{k+1} with f_k = (rho^-1 d/drho)^k f = (-1)^k B_k and
+// B_k = ((2k - 1) B_{k-1} + (2a^2)^k e^{-a^2 rho^2} / (a sqrt(pi))) / rho^2, so
+// d^gamma f = sum_k c_{gamma,k}(x) f_k with polynomials c built by the product rule.
+struct RadialPoly {  // sum over (x^e, k) of coefficient * x^e * f_k
+  std::map<std::array<int, 4>, double> t;
+};
+
+Vec lattice_tensor(int q, double a) {
+  MultiIndex mi;
+  mi.build(q);
+  const int nq = mi.size();
+  // product-rule polynomials for every gamma, built from gamma - e_i
+  std::vector<RadialPoly> C(nq);
+  C[0].t[{0, 0, 0, 0}] = 1.0;
+  for (int k = 1; k < nq; ++k) {
+    I3 gmm = mi.list[k];
+    int i = (gmm[0] > 0) ? 0 : (gmm[1] > 0 ? 1 : 2);
+    I3 gp = gmm;
+    gp[i] -= 1;
+    const RadialPoly& src = C[mi.at(gp[0], gp[1], gp[2])];
+    RadialPoly out;
+    for (const auto& kv : src.t) {
+      std::array<int, 4> e = kv.first;
+      if (e[i] > 0) {  // derivative of the monomial
+        std::array<int, 4> d = e;
+        d[i] -= 1;
+        out.t[d] += kv.second * e[i];
+      }
+      std::array<int, 4> u = e;  // x_i f_{k+1}
+      u[i] += 1;
+      u[3] += 1;
+      out.t[u] += kv.second;
+    }
+    C[k] = out;
+  }
+  Vec T(nq, 0.0);
+  // real space, n != 0, |n_i| <= 5 (erfc(2a) and beyond are below 1e-40 for a = 2)
+  const int R = 5;
+  for (int nz = -R; nz <= R; ++nz)
+    for (int ny = -R; ny <= R; ++ny)
+      for (int nx = -R; nx <= R; ++nx) {
+        if (!nx && !ny && !nz) continue;
+        double x[3] = {(double)nx, (double)ny, (double)nz};
+        double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        double r = std::sqrt(r2);
+        std::vector<double> f(q + 1);
+        double B = std::erfc(a * r) / r;
+        f[0] = B;
+        for (int k = 1; k <= q; ++k) {
+          B = ((2 * k - 1) * B + std::pow(2.0 * a * a, k) * std::exp(-a * a * r2) / (a * std::sqrt(kPi))) / r2;
+          f[k] = (k % 2) ? -B : B;
+        }
+        for (int k = 0; k < nq; ++k) {
+          double s = 0.0;
+          for (const auto& kv : C[k].t) {
+            const auto& e = kv.first;
+            s += kv.second * mpow(x, I3{e[0], e[1], e[2]}) * f[e[3]];
+          }
+          T[k] -= s;
+        }
+      }
+  // n = 0: erf(a r)/r = (2a/sqrt(pi)) sum_m (-1)^m a^{2m} r^{2m} / (m! (2m+1));
+  // d^gamma r^{2m} at 0 is nonzero only for gamma = 2 (a, b, c), a + b + c = m:
+  // m!/(a! b! c!) (2a)! (2b)! (2c)!
+  for (int k = 0; k < nq; ++k) {
+    const I3& g = mi.list[k];
+    if ((g[0] | g[1] | g[2]) & 1) continue;
+    int m = deg(g) / 2;
+    double coef = (2.0 * a / std::sqrt(kPi)) * ((m % 2) ? -1.0 : 1.0) * std::pow(a, 2 * m) /
+                  (factorial(m) * (2 * m + 1));
+    double d = factorial(m) / (factorial(g[0] / 2) * factorial(g[1] / 2) * factorial(g[2] / 2)) *
+               factorial(g[0]) * factorial(g[1]) * factorial(g[2]);
+    T[k] += coef * d;
+  }
+  // reciprocal space: d^gamma cos(2 pi k.x) at 0 = (2 pi)^|gamma| k^gamma (-1)^{|gamma|/2}, |gamma| even
+  Ewald ew(a);
+  for (int k = 0; k < nq; ++k) {
+    const I3& g = mi.list[k];
+    int n = deg(g);
+    if (n % 2) continue;
+    double sgn = ((n / 2) % 2) ? -1.0 : 1.0;
+    double s = 0.0;
+    for (const auto& kk : ew.kv) {
+      double kvv[3] = {kk[0], kk[1], kk[2]};
+      s += kk[3] * mpow(kvv, g);
+    }
+    T[k] -= s * std::pow(2.0 * kPi, n) * sgn;
+  }
+  T[0] += kPi / (a * a);
+  // the 26 nearest images other than n = 0, removed from psi: + d^gamma (1/|x|)(n)
+  ensure_derivs(q);
+  Vec d(g_der.mi.size());
+  for (int nz = -1; nz <= 1; ++nz)
+    for (int ny = -1; ny <= 1; ++ny)
+      for (int nx = -1; nx <= 1; ++nx) {
+        if (!nx && !ny && !nz) continue;
+        double x[3] = {(double)nx, (double)ny, (double)nz};
+        g_der.inv_r(x, d.data());
+        for (int k = 0; k < nq; ++k) T[k] += d[k];
+      }
+  return T;
+}
+
+// ---------------------------------------------------------------------------
 // AMR hierarchy (Sec. 3): per level, leaf cells with masses and refined cells.
 uint64_t morton(const I3& c, int lev) {
   uint64_t k = 0;
@@ -354,6 +551,10 @@ I3 parent_of(const I3& c) { return I3{c[0] >> 1, c[1] >> 1, c[2] >> 1}; }
 void centre(const I3& c, int lev, double* x) {
   double h = std::ldexp(1.0, -lev);
   for (int i = 0; i < 3; ++i) x[i] = (c[i] + 0.5) * h;
+}
+I3 wrap(const I3& c, int lev) {  // the box holding image c (periodic)
+  const int m = (1 << lev) - 1;
+  return I3{c[0] & m, c[1] & m, c[2] & m};
 }
 bool inside(const I3& c, int lev) {
   int n = 1 << lev;
@@ -378,7 +579,7 @@ struct Hier {
   double leaf_mass(int lev, const I3& c) const { return mass[lev][leaf[lev].at(c)]; }
 
   int build(int lmin_, int lmax_, const int64_t* n, const int32_t* const* ijk,
-            const double* const* m) {
+            const double* const* m, bool periodic = false) {
     lmin = lmin_;
     lmax = lmax_;
     if (lmin < 2 || lmax < lmin || lmax > 20) return ORC_ERR_ARG;
@@ -424,6 +625,7 @@ struct Hier {
           for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
               I3 nb{f[0] + dx, f[1] + dy, f[2] + dz};
+              if (periodic) nb = wrap(nb, l - 1);  // the rule holds across the boundary too
               if (!inside(nb, l - 1)) continue;
               if (!refined[l - 1].count(nb)) return ORC_ERR_NOT_GRADED;
             }
@@ -471,6 +673,9 @@ struct Solver {
   int p;
   int bottom;               // 0: M2P bottom intermediate field (paper); 1: M2L into F + L2P
   int delta = 1;            // levels between the cells and the finest FMM box (2: unigrids only)
+  bool periodic = false;    // images of the box everywhere (see the header); set by set_periodic
+  Vec T;                    // lattice tensor, |gamma| <= p + 1
+  Vec Mroot;                // multipole of every leaf about the box centre
   Ops op;
   std::vector<Tree> trees;  // indexed by AMR level j
 
@@ -479,6 +684,22 @@ struct Solver {
     trees.resize(H.lmax + 1);
     for (int j = H.lmin; j <= H.lmax; ++j) trees[j] = build_tree(H, op, j);
   }
+
+  void set_periodic() {
+    periodic = true;
+    T = lattice_tensor(p + 1, 2.0);
+    Mroot.assign(op.n(), 0.0);
+    const double c0[3] = {0.5, 0.5, 0.5};
+    for (int j = H.lmin; j <= H.lmax; ++j)
+      for (const auto& kv : H.leaf[j]) {
+        double x[3];
+        centre(kv.first, j, x);
+        op.p2m(H.mass[j][kv.second], x, c0, Mroot);
+      }
+  }
+  // the box a (possibly image) index refers to, and whether it exists
+  I3 W(const I3& c, int lev) const { return periodic ? wrap(c, lev) : c; }
+  bool keep(const I3& c, int lev) const { return periodic || inside(c, lev); }
 
   // Multipole drifting of the stale trees j < lo (see the header): vel[j] holds
   // the velocity of each leaf of level j (input order), dt[j - lmin] the time
@@ -537,14 +758,15 @@ struct Solver {
 
   // Interaction list of box B at level b (Sec. 2): children of the 3^3
   // neighbours of B's parent, minus the 3^3 neighbours of B, inside the box.
-  static std::vector<I3> ilist(const I3& B, int b) {
+  // Periodic: the boxes are images (geometry), W() gives the box they show.
+  std::vector<I3> ilist(const I3& B, int b) const {
     std::vector<I3> out;
     I3 P = parent_of(B);
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
           I3 Q{P[0] + dx, P[1] + dy, P[2] + dz};
-          if (!inside(Q, b - 1)) continue;
+          if (!keep(Q, b - 1)) continue;
           for (int k = 0; k < 8; ++k) {
             I3 S{2 * Q[0] + (k & 1), 2 * Q[1] + ((k >> 1) & 1), 2 * Q[2] + ((k >> 2) & 1)};
             if (std::abs(S[0] - B[0]) <= 1 && std::abs(S[1] - B[1]) <= 1 &&
@@ -563,18 +785,27 @@ struct Solver {
   std::vector<Grid> downward(int l, const std::vector<Grid>& mt, int nthreads) const {
     std::vector<Grid> L(l + 1);
     const int top = bottom ? l - 1 : l - 1 - delta;
-    if (top < 2) return L;
+    const int b0 = periodic ? 1 : 2;  // first level with an interaction list
+    if (top < b0) return L;
     // boxes that need L: ancestors of level-l leaves
     std::vector<std::set<I3>> need(l + 1);
     for (const auto& kv : H.leaf[l]) {
       I3 c = kv.first;
-      for (int b = l - 1; b >= 2; --b) {
+      for (int b = l - 1; b >= b0; --b) {
         c = parent_of(c);
         if (b <= top) need[b].insert(c);
       }
     }
     int nc = op.n();
-    for (int b = 2; b <= top; ++b) {
+    // periodic: the root's local expansion from every image beyond its 3^3
+    // (and the background): Eq. 3 with the lattice tensor, about the box centre
+    Vec Lroot;
+    const double c0[3] = {0.5, 0.5, 0.5};
+    if (periodic) {
+      Lroot.assign(nc, 0.0);
+      op.m2l(Mroot, T, Lroot);
+    }
+    for (int b = b0; b <= top; ++b) {
       std::vector<I3> boxes(need[b].begin(), need[b].end());
       std::vector<Vec> res(boxes.size(), Vec(nc, 0.0));
 #pragma omp parallel num_threads(nthreads)
@@ -586,15 +817,18 @@ struct Solver {
           Vec& Lb = res[ib];
           double cB[3];
           centre(B, b, cB);
-          if (b >= 3) {  // ShiftLocal of the parent's expansion (Eq. 4)
+          if (b > b0) {  // ShiftLocal of the parent's expansion (Eq. 4)
             I3 P = parent_of(B);
             double cP[3];
             centre(P, b - 1, cP);
             op.l2l(L[b - 1].at(P), cP, cB, Lb);
+          } else if (periodic) {  // level 1: the root's lattice expansion
+            op.l2l(Lroot, c0, cB, Lb);
           }
-          for (const I3& S : ilist(B, b)) {
+          for (const I3& Si : ilist(B, b)) {
+            const I3 S = W(Si, b);  // content
             double cS[3], R[3];
-            centre(S, b, cS);
+            centre(Si, b, cS);  // geometry of the image
             for (int i = 0; i < 3; ++i) R[i] = cB[i] - cS[i];
             CellKind k = H.kind(b, S);
             if (k == LEAF) {  // tree j = b carries cell masses: P2L
@@ -665,7 +899,7 @@ struct Solver {
         centre(F, l - 1, c);
         op.l2p(L[l - 1].at(F), c, xt, phi, grad);
       }
-    } else if (l - 2 >= 2) {
+    } else if (l - 2 >= (periodic ? 1 : 2)) {
       // far field: local expansion of the level l-2 box
       I3 G2 = parent_of(F);
       double c[3];
@@ -674,9 +908,10 @@ struct Solver {
     }
     // intermediate field: interaction list of F at level l-1 (bottom mode 0)
     if (!bottom)
-    for (const I3& S : ilist(F, l - 1)) {
+    for (const I3& Si : ilist(F, l - 1)) {
+      const I3 S = W(Si, l - 1);
       double cS[3], R[3];
-      centre(S, l - 1, cS);
+      centre(Si, l - 1, cS);
       CellKind k = H.kind(l - 1, S);
       if (k == LEAF) {  // (i) coarse leaves: P2P with their mass
         p2p(H.leaf_mass(l - 1, S), cS, xt, phi, grad);
@@ -692,23 +927,23 @@ struct Solver {
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
           I3 N{F[0] + dx, F[1] + dy, F[2] + dz};
-          CellKind kn = H.kind(l - 1, N);
+          CellKind kn = H.kind(l - 1, W(N, l - 1));
           if (kn == OUTSIDE) continue;
           double cN[3];
           centre(N, l - 1, cN);
           if (kn == LEAF) {  // a level l-1 leaf covers 8 positions: counted once
-            p2p(H.leaf_mass(l - 1, N), cN, xt, phi, grad);
+            p2p(H.leaf_mass(l - 1, W(N, l - 1)), cN, xt, phi, grad);
             continue;
           }
           if (kn != REFINED) { std::fprintf(stderr, "oracle: near cell absent\n"); continue; }
           for (int k = 0; k < 8; ++k) {
             I3 P{2 * N[0] + (k & 1), 2 * N[1] + ((k >> 1) & 1), 2 * N[2] + ((k >> 2) & 1)};
             if (P == t) continue;
-            CellKind kp = H.kind(l, P);
+            CellKind kp = H.kind(l, W(P, l));
             double cP[3];
             centre(P, l, cP);
             if (kp == LEAF) {
-              p2p(H.leaf_mass(l, P), cP, xt, phi, grad);
+              p2p(H.leaf_mass(l, W(P, l)), cP, xt, phi, grad);
               continue;
             }
             bool touching = std::abs(P[0] - t[0]) <= 1 && std::abs(P[1] - t[1]) <= 1 &&
@@ -716,17 +951,17 @@ struct Solver {
             if (touching) {  // nearest field (Sec. 3.2): P2P from the 2^3 children
               for (int kc = 0; kc < 8; ++kc) {
                 I3 C{2 * P[0] + (kc & 1), 2 * P[1] + ((kc >> 1) & 1), 2 * P[2] + ((kc >> 2) & 1)};
-                if (H.kind(l + 1, C) != LEAF) {
+                if (H.kind(l + 1, W(C, l + 1)) != LEAF) {
                   std::fprintf(stderr, "oracle: nearest child not a leaf\n");
                   continue;
                 }
                 double cC[3];
                 centre(C, l + 1, cC);
-                p2p(H.leaf_mass(l + 1, C), cC, xt, phi, grad);
+                p2p(H.leaf_mass(l + 1, W(C, l + 1)), cC, xt, phi, grad);
               }
             } else {  // near field refined cell: M2P from the merged tree at FMM level l
               double R[3] = {xt[0] - cP[0], xt[1] - cP[1], xt[2] - cP[2]};
-              if (const Vec* M = grid_box(mt, l, P)) op.m2p(*M, dc.get(R), phi, grad);
+              if (const Vec* M = grid_box(mt, l, W(P, l))) op.m2p(*M, dc.get(R), phi, grad);
             }
           }
         }
@@ -752,14 +987,15 @@ static int solve_impl(int lmin, int lmax, const int64_t* n, const int32_t* const
                       const double* const* mass, int p, double G, int p_m, int bottom, int delta,
                       const double* const* vel, const double* dt, int lo,
                       const int64_t* n_sel, const int64_t* const* sel, double* const* phi,
-                      double* const* acc, int nthreads) {
+                      double* const* acc, int nthreads, bool periodic = false) {
   if (p < 1 || p > 12 || nthreads < 1 || p_m < 0 || p_m > p || (bottom != 0 && bottom != 1)) return ORC_ERR_ARG;
   Hier H;
-  int rc = H.build(lmin, lmax, n, ijk, mass);
+  int rc = H.build(lmin, lmax, n, ijk, mass, periodic);
   if (rc) return rc;
   if (lo < lmin || lo > lmax) return ORC_ERR_ARG;
   Solver S(H, p, p_m, bottom);
   S.delta = delta;
+  if (periodic) S.set_periodic();
   if (vel && dt) S.drift(lo, vel, dt);
   for (int l = lo; l <= lmax; ++l) {
     int64_t nt = n_sel ? n_sel[l - lmin] : n[l - lmin];
@@ -802,6 +1038,106 @@ int oracle_fmm_solve_dl2(int level, const int64_t* n, const int32_t* const* ijk,
   if (n[0] != ((int64_t)1 << (3 * level))) return ORC_ERR_INCOMPLETE;
   return solve_impl(level, level, n, ijk, mass, p, G, p_m, 0, 2, nullptr, nullptr, level, n_sel, sel, phi, acc,
                     nthreads);
+}
+
+// Periodic boundaries (see the header), bottom M2P, lmin >= 3; arguments as
+// oracle_fmm_solve without the bottom mode and drifting.
+int oracle_fmm_solve_periodic(int lmin, int lmax, const int64_t* n, const int32_t* const* ijk,
+                              const double* const* mass, int p, double G, int p_m, int lo,
+                              const int64_t* n_sel, const int64_t* const* sel, double* const* phi,
+                              double* const* acc, int nthreads) {
+  if (lmin < 3) return ORC_ERR_ARG;
+  return solve_impl(lmin, lmax, n, ijk, mass, p, G, p_m, 0, 1, nullptr, nullptr, lo, n_sel, sel, phi, acc,
+                    nthreads, true);
+}
+
+// The periodic potential by Ewald's sum over all pairs (O(N^2 K)), with
+// splitting parameter `alpha` (>= 6): phi_t = G (sum_{j != t} m_j psi(x_t - x_j)
+// + m_t psi_self), accel_t = -G sum_{j != t} m_j grad psi(x_t - x_j).  The
+// reciprocal part goes through the structure factors S(k) = sum_j m_j e^{2 pi i k.x_j}.
+int oracle_ewald_sum(int lmin, int lmax, const int64_t* n, const int32_t* const* ijk, const double* const* mass,
+                     double G, double alpha, int lo, const int64_t* n_sel, const int64_t* const* sel,
+                     double* const* phi, double* const* acc, int nthreads) {
+  if (nthreads < 1 || lmin < 0 || lmax < lmin || lo < lmin || lo > lmax || !(alpha >= 6.0)) return ORC_ERR_ARG;
+  std::vector<double> X, M;
+  for (int l = lmin; l <= lmax; ++l)
+    for (int64_t i = 0; i < n[l - lmin]; ++i) {
+      I3 c{ijk[l - lmin][3 * i], ijk[l - lmin][3 * i + 1], ijk[l - lmin][3 * i + 2]};
+      double x[3];
+      centre(c, l, x);
+      X.insert(X.end(), x, x + 3);
+      M.push_back(mass[l - lmin][i]);
+    }
+  const int64_t N = (int64_t)M.size();
+  Ewald ew(alpha);
+  const int64_t K = (int64_t)ew.kv.size();
+  std::vector<double> Sre(K, 0.0), Sim(K, 0.0);
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (int64_t q = 0; q < K; ++q) {
+    double re = 0.0, im = 0.0;
+    for (int64_t j = 0; j < N; ++j) {
+      double ph = 2.0 * kPi * (ew.kv[q][0] * X[3 * j] + ew.kv[q][1] * X[3 * j + 1] + ew.kv[q][2] * X[3 * j + 2]);
+      re += M[j] * std::cos(ph);
+      im += M[j] * std::sin(ph);
+    }
+    Sre[q] = re;
+    Sim[q] = im;
+  }
+  const double self = ew.self();
+  for (int l = lo; l <= lmax; ++l) {
+    int64_t nt = n_sel ? n_sel[l - lmin] : n[l - lmin];
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 16)
+    for (int64_t i = 0; i < nt; ++i) {
+      int64_t idx = n_sel ? sel[l - lmin][i] : i;
+      I3 c{ijk[l - lmin][3 * idx], ijk[l - lmin][3 * idx + 1], ijk[l - lmin][3 * idx + 2]};
+      double xt[3];
+      centre(c, l, xt);
+      double v = 0.0, g[3] = {0.0, 0.0, 0.0}, mself = 0.0;
+      // real space: the 27 images of every other mass
+      for (int64_t j = 0; j < N; ++j) {
+        const double* y = &X[3 * j];
+        if (y[0] == xt[0] && y[1] == xt[1] && y[2] == xt[2]) {
+          mself += M[j];
+          continue;
+        }
+        double r[3] = {xt[0] - y[0], xt[1] - y[1], xt[2] - y[2]};
+        double vv = 0.0, gg[3] = {0.0, 0.0, 0.0};
+        for (int nz = -1; nz <= 1; ++nz)
+          for (int ny = -1; ny <= 1; ++ny)
+            for (int nx = -1; nx <= 1; ++nx) {
+              double x[3] = {r[0] + nx, r[1] + ny, r[2] + nz};
+              ew.real(x, &vv, gg);
+            }
+        v += M[j] * vv;
+        for (int k = 0; k < 3; ++k) g[k] += M[j] * gg[k];
+      }
+      // reciprocal space over all masses, then the target's own share removed
+      // (its images enter through psi_self)
+      double vr = 0.0, gr[3] = {0.0, 0.0, 0.0};
+      for (int64_t q = 0; q < K; ++q) {
+        const auto& k = ew.kv[q];
+        double ph = 2.0 * kPi * (k[0] * xt[0] + k[1] * xt[1] + k[2] * xt[2]);
+        double cs = std::cos(ph), sn = std::sin(ph);
+        // sum_j m_j cos(2 pi k.(x - x_j)) = cos(k.x) Re S + sin(k.x) Im S
+        vr += k[3] * (cs * Sre[q] + sn * Sim[q]);
+        double d = k[3] * 2.0 * kPi * (-sn * Sre[q] + cs * Sim[q]);
+        for (int a = 0; a < 3; ++a) gr[a] += d * k[a];
+      }
+      double recip_self = 0.0;
+      for (int64_t q = 0; q < K; ++q) recip_self += ew.kv[q][3];
+      vr -= mself * recip_self;
+      double psi_sum = -(v + vr - kPi / (alpha * alpha) * (std::accumulate(M.begin(), M.end(), 0.0) - mself));
+      phi[l - lmin][i] = G * (psi_sum + mself * self);
+      for (int k = 0; k < 3; ++k) acc[l - lmin][3 * i + k] = G * (g[k] + gr[k]);
+    }
+  }
+  return ORC_OK;
+}
+
+// The lattice tensor T_gamma, |gamma| <= q, multi-index order (see lattice_tensor).
+void oracle_lattice_tensor(int q, double alpha, double* out) {
+  Vec T = lattice_tensor(q, alpha);
+  for (size_t k = 0; k < T.size(); ++k) out[k] = T[k];
 }
 
 // O(N^2) direct sum over all leaves of all levels (self term excluded), for
