@@ -106,6 +106,18 @@ typedef struct {
                          >= 3; otherwise FMM_ERR_ARG) and the bottom mode must be
                          FMM_BOTTOM_M2P; fmm_solve_adjoint and the static unigrid
                          entry return FMM_ERR_ARG. */
+  int periodic;       /* 0: isolated boundaries (the paper's); 1: periodic boundaries
+                         (Sec. 6 names them as the next step): the box tiles space, a
+                         uniform background of the opposite total mass is added (lap
+                         phi = 4 pi G (rho - mean rho)), and phi is Ewald's periodic
+                         potential (zero mean over the box; a cell's own images act on
+                         it).  Every neighbour and interaction list wraps around the
+                         box, M2L also runs at box level 1, and the images beyond the
+                         root's 3^3 reach level 1 through a lattice tensor built on the
+                         host.  Needs lmin >= 3 (fmm_set_levels returns FMM_ERR_ARG),
+                         the graded rule across the box edges (FMM_ERR_NOT_GRADED),
+                         bottom mode FMM_BOTTOM_M2P and delta_l 1; fmm_solve_adjoint,
+                         fmm_direct_sum and the static unigrid entry return FMM_ERR_ARG. */
 } fmm_config;
 
 /* Device memory for the library, supplied by the caller (for instance a caching
@@ -121,8 +133,9 @@ typedef void* (*fmm_alloc_fn)(void* user, void* ptr, size_t bytes, void* stream)
  * makes (its workspace, and the translation tables it shares with the other
  * contexts of the same device, order, precision and allocator); NULL uses
  * cudaMalloc / cudaFree.  Returns FMM_ERR_ARG for p outside 1..8, p_m outside
- * 0..p, an unknown precision or bottom mode, or delta_l outside 0..2 (2 with
- * bottom mode FMM_BOTTOM_M2L_L2P). */
+ * 0..p, an unknown precision or bottom mode, delta_l outside 0..2 (2 with
+ * bottom mode FMM_BOTTOM_M2L_L2P), or periodic outside 0..1 (1 with another
+ * bottom mode or delta_l = 2). */
 fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_user, fmm_ctx** out);
 
 /* Set the AMR hierarchy, or replace its levels lo..lmax (adaptive time
@@ -170,7 +183,9 @@ fmm_status fmm_update_masses(fmm_ctx* ctx, int lo, const void* const* mass, void
  * since level lmin+k was set (only levels below a solve's lo are drifted); NULL
  * turns drifting off.  A drifting solve recomputes every multipole from the
  * masses (a full upward pass) before it adds the drift; the first call after a
- * new hierarchy sizes the drift scratch (the solves then allocate nothing). */
+ * new hierarchy sizes the drift scratch (the solves then allocate nothing).
+ * Periodic contexts (whose level-1 multipoles would need drifting too):
+ * FMM_ERR_ARG. */
 fmm_status fmm_set_velocities(fmm_ctx* ctx, int lo, const double* const* vel, void* stream);
 fmm_status fmm_set_drift(fmm_ctx* ctx, const double* dt, int n);
 
@@ -314,6 +329,13 @@ fmm_status fmm_host_numerators(int q, const int64_t* u, int64_t* out);
  *         3: L2P          [64][nc][4]      (position f*8+t inside the level l-2 box)
  *         4: M2M          [8][nc][nc]      (child c, output alpha, input gamma)
  *         5: L2L          [8][nc][nc]      (child c, output beta, input gamma)
+ *         6: lattice tensor [ncoef(p)]     (T_gamma = d^gamma psi_far(0), periodic
+ *                                           boundaries; psi_far = Ewald's potential of
+ *                                           a unit mass with its background minus g over
+ *                                           the 27 nearest images; physical units)
+ *         7: level-1 lattice operator [8*nc][8*nc] (the level-1 local expansions
+ *                                           from the level-1 multipoles through the root)
+ *         8: Delta l = 2 M2P [2048][26*8*nc] (n = ((g*8+f)*8+t)*4+comp)
  * Expansions are in box units (multipoles / h^|alpha|, locals * h^(|beta|+1));
  * comp 0 is phi, comps 1..3 are accel = -grad phi.  Returns FMM_ERR_ARG if
  * `n` (doubles) is too small.  Needs no GPU. */

@@ -371,6 +371,14 @@ fmm_status init_tables(Ctx* c) {
   }
   TRY(build_operator(c, c->op_m2p, t.m2p, 256, kOpM2P));
   TRY(build_operator(c, c->op_m2l, t.m2l, 8 * t.nc, kOpM2L));
+  if (c->cfg.periodic) {
+    t.build_lattice();
+    if (c->cfg.precision == FMM_FP64)
+      TRY(upload(c, c->d_lat64, t.lattice));
+    else
+      TRY(upload(c, c->d_lat32, std::vector<float>(t.lattice.begin(), t.lattice.end())));
+    std::vector<double>().swap(t.lattice);
+  }
   if (c->cfg.delta_l == 2) {
     t.build_dl2();
     TRY(build_operator(c, c->op_m2p2, t.m2p2, 2048, kOpM2P));
@@ -431,7 +439,7 @@ fmm_status size_expansions(Ctx* c, cudaStream_t st) {
 fmm_status size_locals(Ctx* c, cudaStream_t st) {
   const int nc = c->tab.nc;
   const bool f64 = c->cfg.precision == FMM_FP64;
-  for (int l = 2; l <= top_local_level(c); ++l) {
+  for (int l = first_local_level(c); l <= top_local_level(c); ++l) {
     LevelTree& T = c->lev[l];
     const int64_t nrow = 8 * std::max<int64_t>(T.n_rowsL, 1);
     if (f64) CKS(buf_ensure(c, T.L, nrow * nc * 8));  // the mixed paths keep the FP32 expansions only
@@ -569,7 +577,8 @@ fmm_status adjoint_lists(Ctx* c, cudaStream_t st) {
 DevBuf Ctx::*const kTableBufs[] = {
     &Ctx::d_m2m_off, &Ctx::d_m2m_g,   &Ctx::d_m2m_e,    &Ctx::d_m2m_c,  &Ctx::d_m2m_c32, &Ctx::d_m2m_w0,
     &Ctx::d_m2m_w0_32, &Ctx::d_m2m_e0, &Ctx::d_l2l_off, &Ctx::d_l2l_off8, &Ctx::d_l2l_g, &Ctx::d_l2l_e,
-    &Ctx::d_l2l_c,   &Ctx::d_l2l_c32, &Ctx::d_near64,  &Ctx::d_near32,   &Ctx::d_l2p64,  &Ctx::d_l2p32};
+    &Ctx::d_l2l_c,   &Ctx::d_l2l_c32, &Ctx::d_near64,  &Ctx::d_near32,   &Ctx::d_l2p64,  &Ctx::d_l2p32,
+    &Ctx::d_lat64,   &Ctx::d_lat32};
 constexpr int kNumTableBufs = sizeof(kTableBufs) / sizeof(kTableBufs[0]);
 
 struct TableSet {
@@ -578,15 +587,16 @@ struct TableSet {
   DevBuf bufs[kNumTableBufs];
   GemmOperand op_m2p, op_m2l, op_m2p2, op_p2pr;
 };
-// (device, p, precision, p_m, Delta l, allocator, allocator's user pointer):
-// contexts of another allocator get their own copy, released through that allocator
-using TableKey = std::tuple<int, int, int, int, int, uintptr_t, uintptr_t>;
+// (device, p, precision, p_m, Delta l, periodic, allocator, allocator's user
+// pointer): contexts of another allocator get their own copy, released through
+// that allocator
+using TableKey = std::tuple<int, int, int, int, int, int, uintptr_t, uintptr_t>;
 std::mutex g_tables_mu;
 std::map<TableKey, TableSet*> g_tables;
 
 TableKey table_key(const Ctx* c) {
-  return TableKey(c->device, c->cfg.p, c->cfg.precision, c->cfg.p_m, c->cfg.delta_l, (uintptr_t)c->alloc,
-                  (uintptr_t)c->alloc_user);
+  return TableKey(c->device, c->cfg.p, c->cfg.precision, c->cfg.p_m, c->cfg.delta_l, c->cfg.periodic,
+                  (uintptr_t)c->alloc, (uintptr_t)c->alloc_user);
 }
 
 fmm_status acquire_tables(Ctx* c) {
@@ -690,6 +700,8 @@ fmm_status fmm_create(const fmm_config* cfg, fmm_alloc_fn alloc, void* alloc_use
   if (cfg->fp64_top != 0 && cfg->fp64_top != 1) return FMM_ERR_ARG;
   if (cfg->delta_l < 0 || cfg->delta_l > 2) return FMM_ERR_ARG;
   if (cfg->delta_l == 2 && cfg->bottom_mode != FMM_BOTTOM_M2P) return FMM_ERR_ARG;
+  if (cfg->periodic != 0 && cfg->periodic != 1) return FMM_ERR_ARG;
+  if (cfg->periodic && (cfg->bottom_mode != FMM_BOTTOM_M2P || cfg->delta_l == 2)) return FMM_ERR_ARG;
   if (!std::isfinite(cfg->G)) return FMM_ERR_ARG;
   fmm_ctx* c = new fmm_ctx();
   c->cfg = *cfg;
@@ -836,6 +848,10 @@ static fmm_status set_levels_impl(fmm_ctx* c, int lmin, int lmax, int lo, const 
     c->last_error = "delta_l = 2 takes one complete level (lmin == lmax >= 3)";
     return FMM_ERR_ARG;
   }
+  if (c->cfg.periodic && lmin < 3) {
+    c->last_error = "periodic boundaries need lmin >= 3";
+    return FMM_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
   ++c->n_set;
@@ -946,10 +962,12 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   const bool dl2 = c->cfg.delta_l == 2;  // one level: lo == lmin, no stale trees
   const int top = top_local_level(c);
   const int top_m2l = top_m2l_level(c);
+  const int l0 = first_local_level(c);  // 1 with periodic boundaries
+  const bool periodic = c->cfg.periodic;
   const bool restrict_dn = lo > lmin && c->anc_d == lo;
   std::vector<const int32_t*> drows(lmax + 1, nullptr);
   std::vector<int64_t> dn(lmax + 1, 0);
-  for (int b = 2; b <= top; ++b)
+  for (int b = l0; b <= top; ++b)
     if (restrict_dn && b <= lo - 3 + m1) {
       drows[b] = (const int32_t*)c->lev[b].anc.ptr;
       dn[b] = c->lev[b].n_anc;
@@ -957,7 +975,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   std::vector<int> dl;  // box levels with M2L rows
   std::vector<const int32_t*> dr;
   std::vector<int64_t> dnr;
-  for (int b = 2; b <= top_m2l; ++b) {
+  for (int b = l0; b <= top_m2l; ++b) {
     if (drows[b] && !dn[b]) continue;
     dl.push_back(b);
     dr.push_back(drows[b]);
@@ -967,7 +985,7 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
   if (d <= lmin || (d <= lmax && c->anc_d != d) || drift) {
     for (int l = 1; l <= lmax; ++l) launch_mono_leaves(c, l, st);
     if (dl2) launch_child_masses(c, st);
-    for (int b = lmax - 1; b >= 2; --b) launch_upward(c, b, st);
+    for (int b = lmax - 1; b >= l0; --b) launch_upward(c, b, st);
     if (drift) launch_drift(c, lo, st);
   } else if (d <= lmax) {
     for (int l = d; l <= lmax; ++l) launch_mono_leaves(c, l, st);
@@ -980,12 +998,21 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
     for (; b >= 2 && (w == 0 || c->lev[b + 1].n_anc > 2 * w); --b)
       launch_upward(c, b, st, (const int32_t*)c->lev[b + 1].anc.ptr, c->lev[b + 1].n_anc);
     if (b >= 2) launch_m2m_chain(c, b, st);
+    if (periodic) launch_upward(c, 1, st);  // the level-1 multipoles feed level-1 M2L and the lattice
   }
+  // periodic: the images of the root beyond its 3^3 (and the background), and
+  // level 1's M2L from the 26 nearest, into the level-1 M2L sums (FP64: in the
+  // L2L chain, after level 1's expansion is set)
+  if (periodic && !f64) launch_lattice(c, st);
   stage_event(c, 1, st);
   // 2. downward (below): the M2L rows of each box level
   // M2L of all box levels: one tcgen05 launch (mixed), or per level (FP64)
+  // (periodic: level 1's M2L is part of the lattice product, launch_lattice)
+  const size_t tc0 = (!dl.empty() && dl[0] == 1) ? 1 : 0;
   auto m2l_tc = [&](cudaStream_t s2) {
-    if (!dl.empty()) launch_gemm_tc(c, c->op_m2l, kModeM2L, dl.data(), (int)dl.size(), s2, dr.data(), dnr.data());
+    if (dl.size() > tc0)
+      launch_gemm_tc(c, c->op_m2l, kModeM2L, dl.data() + tc0, (int)(dl.size() - tc0), s2, dr.data() + tc0,
+                     dnr.data() + tc0);
   };
   // Delta l = 2: the level lmax-2 expansions (read by the near field) are the
   // L2L of lmax-3's, zero when lmax-3 < 2
@@ -996,7 +1023,10 @@ static fmm_status enqueue_solve(Ctx* c, int lo, void* const* dphi, void* const* 
     }
     for (size_t i = 0; i < dl.size(); ++i) {
       launch_l2l_add(c, dl[i], s2, dr[i], dnr[i]);
-      if (f64) launch_gemm_f64(c, c->op_m2l, kModeM2L, dl[i], s2, dr[i], dnr[i]);
+      if (dl[i] == 1)  // periodic: the lattice and level 1's own M2L in one product
+        launch_lattice(c, s2);
+      else
+        launch_gemm_f64(c, c->op_m2l, kModeM2L, dl[i], s2, dr[i], dnr[i]);
     }
     if (dl2 && top >= 2) launch_l2l_add(c, top, s2);
   };
@@ -1417,8 +1447,8 @@ fmm_status fmm_solve_adjoint(fmm_ctx* c, int lo, const void* const* g_phi, const
     c->last_error = "fmm_solve_adjoint needs an FMM_FP64 context";
     return FMM_ERR_ARG;
   }
-  if (c->cfg.delta_l == 2) {
-    c->last_error = "fmm_solve_adjoint: delta_l = 1 only";
+  if (c->cfg.delta_l == 2 || c->cfg.periodic) {
+    c->last_error = "fmm_solve_adjoint: isolated boundaries and delta_l = 1 only";
     return FMM_ERR_ARG;
   }
   if (c->cfg.bottom_mode != FMM_BOTTOM_M2P) {
@@ -1536,6 +1566,10 @@ fmm_status fmm_set_drift(fmm_ctx* c, const double* dt, int n) {
     c->drift_dt.clear();
     return FMM_OK;
   }
+  if (c->cfg.periodic) {  // the level-1 multipoles (level-1 M2L, the lattice) are not drifted
+    c->last_error = "fmm_set_drift: isolated boundaries only";
+    return FMM_ERR_ARG;
+  }
   if (!c->have_levels) {
     c->last_error = "fmm_set_drift before fmm_set_levels";
     return FMM_ERR_STATE;
@@ -1605,7 +1639,7 @@ void fmm_destroy(fmm_ctx* c) {
                     &c->op_m2p.f64, &c->op_m2p.hi, &c->op_m2p.lo, &c->op_m2p.klimit, &c->op_m2l.colmap, &c->op_m2l.f64,
                     &c->op_m2l.hi, &c->op_m2l.lo, &c->op_m2l.klimit, &c->op_m2p2.f64, &c->op_m2p2.hi,
                     &c->op_m2p2.lo, &c->op_m2p2.klimit, &c->op_p2pr.f64, &c->op_p2pr.hi, &c->op_p2pr.lo,
-                    &c->op_p2pr.klimit, &c->sort_tmp, &c->keys_a, &c->keys_b,
+                    &c->op_p2pr.klimit, &c->d_lat64, &c->d_lat32, &c->sort_tmp, &c->keys_a, &c->keys_b,
                     &c->vals_a, &c->vals_b, &c->flags, &c->scan, &c->counter, &c->anc_flags, &c->out_stage, &c->in_stage,
                     &c->mass_stage, &c->err_buf, &c->d_alpha})
     buf_free(c, *b);
@@ -1665,11 +1699,24 @@ fmm_status fmm_host_numerators(int q, const int64_t* u, int64_t* out) {
 }
 
 fmm_status fmm_host_table(int p, int which, double* out, int64_t n) {
-  if (p < 1 || p > 8 || !out || which < 0 || which > 5) return FMM_ERR_ARG;
+  if (p < 1 || p > 8 || !out || which < 0 || which > 8) return FMM_ERR_ARG;
   Tables t;
   t.build(p);
   const int nc = t.nc;
   std::vector<double> v;
+  if (which == 6) {  // the lattice tensor, |gamma| <= p
+    MultiIdx mq;
+    mq.build(p);
+    v = lattice_tensor(p, mq);
+  }
+  if (which == 7) {
+    t.build_lattice();
+    v = t.lattice;
+  }
+  if (which == 8) {
+    t.build_dl2();
+    v = t.m2p2;
+  }
   if (which == 0) v = t.m2p;
   if (which == 1) v = t.m2l;
   if (which == 2) v = t.nearop;

@@ -102,6 +102,10 @@ extern "C" fmm_status fmm_direct_sum(fmm_ctx* cx, int level, int64_t n_sel, cons
     c->last_error = "fmm_direct_sum: level outside lmin..lmax or a negative count";
     return FMM_ERR_ARG;
   }
+  if (c->cfg.periodic) {
+    c->last_error = "fmm_direct_sum: the isolated sum; a periodic context has no plain pair sum";
+    return FMM_ERR_ARG;
+  }
   if (n_sel == 0 || level > c->lmax) return FMM_OK;
   if (!is_device_ptr(sel) || !is_device_ptr(phi) || !is_device_ptr(accel)) {
     c->last_error = "fmm_direct_sum: sel, phi and accel must be device pointers";

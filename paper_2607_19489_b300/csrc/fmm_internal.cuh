@@ -189,6 +189,7 @@ struct Ctx {
   DevBuf d_near64, d_near32, d_l2p64, d_l2p32;
   GemmOperand op_m2p, op_m2l;
   GemmOperand op_m2p2, op_p2pr;  // Delta l = 2: M2P from level l-2, P2P ring from level l-1
+  DevBuf d_lat64, d_lat32;       // periodic: the level-1 lattice operator [8 nc][8 nc]
   // scratch
   DevBuf sort_tmp, keys_a, keys_b, vals_a, vals_b, flags, scan, err_word, counter;
   DevBuf anc_flags;     // uint8: one visited flag per oct of levels 1..anc_req-1 (ancestor walks)
@@ -325,6 +326,9 @@ enum { kOpM2P = 0, kOpM2L = 1, kOpP2P = 2 };
 
 // Delta l = 2: the 8 child masses of every cell of level lmax-1 as operand rows
 void launch_child_masses(Ctx* c, cudaStream_t st);
+// periodic boundaries: the level-1 local expansions from the lattice (adds into
+// Lm of level 1, or L in FP64)
+void launch_lattice(Ctx* c, cudaStream_t st);
 
 // Highest box level holding local expansions: lmax-2 (the paper's bottom
 // M2P), lmax-1 with bottom mode 1 (M2L into the parent box, then L2P).
@@ -334,5 +338,8 @@ inline int top_local_level(const Ctx* c) {
   return c->lmax - 2 + (c->cfg.bottom_mode == FMM_BOTTOM_M2L_L2P ? 1 : 0);
 }
 inline int top_m2l_level(const Ctx* c) { return top_local_level(c) - (c->cfg.delta_l == 2 ? 1 : 0); }
+// First box level with an interaction list (and a local expansion): 2, or 1
+// with periodic boundaries (the images of the root around level 1).
+inline int first_local_level(const Ctx* c) { return c->cfg.periodic ? 1 : 2; }
 
 }  // namespace fmm

@@ -682,7 +682,7 @@ void launch_near(Ctx* c, int lo, void* const* phi, void* const* accel, int out_f
       S.mono_dn = (l < c->lmax) ? c->lev[l + 1].mono.ptr : nullptr;
       S.M_l = T.M.ptr;
       S.M_l_f64 = T.m_is_f64 ? 1 : 0;
-      S.L2 = (l - dl >= 2) ? (f64 ? c->lev[l - dl].L.ptr : c->lev[l - dl].Lf.ptr) : nullptr;
+      S.L2 = (l - dl >= first_local_level(c)) ? (f64 ? c->lev[l - dl].L.ptr : c->lev[l - dl].Lf.ptr) : nullptr;
       S.lslot = (const int32_t*)T.lslot.ptr;
       S.leafmask = (const uint8_t*)T.leafmask.ptr;
       S.acc = T.acc.ptr;

@@ -140,7 +140,8 @@ extern "C" fmm_status fmm_solve_unigrid_static(fmm_ctx* cx, int level, int64_t n
     c->last_error = "fmm_solve_unigrid_static: n must be 8^level (every cell of the grid once)";
     return FMM_ERR_ARG;
   }
-  if (c->cfg.bottom_mode != FMM_BOTTOM_M2P || c->cfg.precision == FMM_MIXED_TF32 || c->cfg.delta_l == 2) {
+  if (c->cfg.bottom_mode != FMM_BOTTOM_M2P || c->cfg.precision == FMM_MIXED_TF32 || c->cfg.delta_l == 2 ||
+      c->cfg.periodic) {
     c->last_error = "fmm_solve_unigrid_static: needs the bottom M2P mode, delta_l = 1 and FP64 or split-BF16 precision";
     return FMM_ERR_ARG;
   }

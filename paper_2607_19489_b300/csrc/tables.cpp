@@ -334,4 +334,247 @@ void Tables::build_dl2() {
     }
 }
 
+
+// ---- periodic boundaries --------------------------------------------------------
+// The lattice tensor by Ewald's split psi = psi_real + psi_recip + pi/a^2 (in the
+// g = -1/r convention, psi_real = -sum_n erfc(a|x+n|)/|x+n|, psi_recip =
+// -(1/pi) sum_{k != 0} exp(-pi^2 k^2/a^2)/k^2 cos(2 pi k.x)), its Taylor
+// coefficients at 0 taken in truncated power-series arithmetic over the three
+// coordinates (Taylor-mode differentiation: each term is a function of one
+// variable composed with a polynomial in x), then T_gamma = gamma! * coefficient.
+namespace {
+
+struct Series {  // truncated power series in (x, y, z), graded order of mi
+  const MultiIdx* mi;
+  int q;
+  std::vector<double> c;
+  Series(const MultiIdx& m, int q_) : mi(&m), q(q_), c(m.size(), 0.0) {}
+};
+
+Series mul(const Series& a, const Series& b) {
+  Series o(*a.mi, a.q);
+  const auto& L = a.mi->list;
+  for (int i = 0; i < (int)L.size(); ++i) {
+    if (a.c[i] == 0.0) continue;
+    const int di = L[i][0] + L[i][1] + L[i][2];
+    for (int j = 0; j < (int)L.size(); ++j) {
+      const int dj = L[j][0] + L[j][1] + L[j][2];
+      if (di + dj > a.q) break;  // graded order: degrees only grow
+      if (b.c[j] == 0.0) continue;
+      o.c[a.mi->at(L[i][0] + L[j][0], L[i][1] + L[j][1], L[i][2] + L[j][2])] += a.c[i] * b.c[j];
+    }
+  }
+  return o;
+}
+
+// sum_k f[k] d^k for a series d without constant term (Horner)
+Series compose(const std::vector<double>& f, const Series& d) {
+  Series o(*d.mi, d.q);
+  for (int k = (int)f.size() - 1; k >= 0; --k) {
+    o = mul(o, d);
+    o.c[0] += f[k];
+  }
+  return o;
+}
+
+// univariate truncated series helpers (coefficients in t)
+std::vector<double> umul(const std::vector<double>& a, const std::vector<double>& b) {
+  std::vector<double> o(a.size(), 0.0);
+  for (size_t i = 0; i < a.size(); ++i)
+    for (size_t j = 0; i + j < a.size(); ++j) o[i + j] += a[i] * b[j];
+  return o;
+}
+// (1 + t/s0)^e as a series in t
+std::vector<double> upow1(double s0, double e, int q) {
+  std::vector<double> o(q + 1, 0.0);
+  double c = 1.0;
+  for (int k = 0; k <= q; ++k) {
+    o[k] = c;
+    c *= (e - k) / (k + 1) / s0;
+  }
+  return o;
+}
+
+}  // namespace
+
+std::vector<double> lattice_tensor(int q, const MultiIdx& mi) {
+  const double a = 2.0, pi = 3.14159265358979323846, sqpi = std::sqrt(pi);
+  Series T(mi, q);
+  // real space, n != 0: h(s) = erfc(a sqrt(s)) / sqrt(s) at s = |n + x|^2 = s0 + t,
+  // t = 2 n.x + |x|^2 (|n_i| <= 4: beyond, erfc(8) ~ 1e-29)
+  const int R = 4;
+  for (int nz = -R; nz <= R; ++nz)
+    for (int ny = -R; ny <= R; ++ny)
+      for (int nx = -R; nx <= R; ++nx) {
+        if (!nx && !ny && !nz) continue;
+        const double n3[3] = {(double)nx, (double)ny, (double)nz};
+        const double s0 = n3[0] * n3[0] + n3[1] * n3[1] + n3[2] * n3[2];
+        // y(t) = a sqrt(s0 + t) - y0, a series without constant term
+        std::vector<double> y = upow1(s0, 0.5, q);
+        const double y0 = a * std::sqrt(s0);
+        for (auto& v : y) v *= y0;
+        y[0] = 0.0;
+        // erfc(y0 + y) = erfc(y0) + sum_k erfc^(k)(y0)/k! y^k, with
+        // erfc^(k)(u) = (-1)^k (2/sqrt(pi)) H_{k-1}(u) e^{-u^2} (physicists' Hermite)
+        std::vector<double> Hn(q + 1, 0.0), ek(q + 1, 0.0);  // H_n(y0), n < q
+        Hn[0] = 1.0;
+        if (q >= 2) Hn[1] = 2.0 * y0;
+        for (int n = 1; n + 1 < q; ++n) Hn[n + 1] = 2.0 * y0 * Hn[n] - 2.0 * n * Hn[n - 1];
+        ek[0] = std::erfc(y0);
+        double fk = 1.0;
+        for (int k = 1; k <= q; ++k) {
+          fk *= k;
+          ek[k] = ((k % 2) ? -1.0 : 1.0) * (2.0 / sqpi) * Hn[k - 1] * std::exp(-y0 * y0) / fk;
+        }
+        std::vector<double> ys(q + 1, 0.0), er(q + 1, 0.0);
+        ys[0] = 1.0;  // y^k accumulated
+        for (int k = 0; k <= q; ++k) {
+          for (int j = 0; j <= q; ++j) er[j] += ek[k] * ys[j];
+          ys = umul(ys, y);
+        }
+        std::vector<double> inv = upow1(s0, -0.5, q);
+        for (auto& v : inv) v /= std::sqrt(s0);
+        std::vector<double> h = umul(er, inv);  // erfc(a sqrt s)/sqrt s in powers of t
+        Series t(mi, q);
+        for (int i = 0; i < 3; ++i) {
+          int e[3] = {0, 0, 0};
+          e[i] = 1;
+          t.c[mi.at(e[0], e[1], e[2])] += 2.0 * n3[i];
+          e[i] = 2;
+          t.c[mi.at(e[0], e[1], e[2])] += 1.0;
+        }
+        Series f = compose(h, t);
+        for (int k = 0; k < mi.size(); ++k) T.c[k] -= f.c[k];
+      }
+  // n = 0, with g removed: erf(a r)/r = (2a/sqrt(pi)) sum_m (-a^2 s)^m / (m! (2m + 1)), s = |x|^2
+  {
+    std::vector<double> h(q / 2 + 1, 0.0);
+    double fm = 1.0;
+    for (int m = 0; m <= q / 2; ++m) {
+      if (m) fm *= m;
+      h[m] = (2.0 * a / sqpi) * std::pow(-a * a, m) / (fm * (2 * m + 1));
+    }
+    Series s2(mi, q);
+    s2.c[mi.at(2, 0, 0)] = s2.c[mi.at(0, 2, 0)] = s2.c[mi.at(0, 0, 2)] = 1.0;
+    if (q >= 2) {
+      Series f = compose(h, s2);
+      for (int k = 0; k < mi.size(); ++k) T.c[k] += f.c[k];
+    } else {
+      T.c[0] += h[0];
+    }
+  }
+  // reciprocal space: cos(2 pi k.x) = sum_j (-1)^j (2 pi k.x)^(2j) / (2j)!
+  const int kmax = (int)std::ceil(a * std::sqrt(40.0) / pi);
+  {
+    std::vector<double> cosf(q + 1, 0.0);
+    double f = 1.0;
+    for (int j = 0; j <= q; ++j) {
+      if (j) f *= j;
+      if (j % 2 == 0) cosf[j] = (((j / 2) % 2) ? -1.0 : 1.0) / f;
+    }
+    Series acc(mi, q);
+    for (int kz = -kmax; kz <= kmax; ++kz)
+      for (int ky = -kmax; ky <= kmax; ++ky)
+        for (int kx = -kmax; kx <= kmax; ++kx) {
+          if (!kx && !ky && !kz) continue;
+          const double k2 = (double)(kx * kx + ky * ky + kz * kz);
+          const double w = std::exp(-pi * pi * k2 / (a * a)) / (pi * k2);
+          Series th(mi, q);
+          if (q >= 1) {
+            th.c[mi.at(1, 0, 0)] = 2.0 * pi * kx;
+            th.c[mi.at(0, 1, 0)] = 2.0 * pi * ky;
+            th.c[mi.at(0, 0, 1)] = 2.0 * pi * kz;
+          }
+          Series cs = compose(cosf, th);
+          for (int k = 0; k < mi.size(); ++k) acc.c[k] += w * cs.c[k];
+        }
+    for (int k = 0; k < mi.size(); ++k) T.c[k] -= acc.c[k];
+  }
+  T.c[0] += pi / (a * a);
+  // derivatives from Taylor coefficients, then + d^gamma (1/|x|) at the 26 nearest images
+  std::vector<double> out(mi.size());
+  for (int k = 0; k < mi.size(); ++k) {
+    const auto& g = mi.list[k];
+    out[k] = T.c[k] * fact(g[0]) * fact(g[1]) * fact(g[2]);
+  }
+  std::vector<double> D;
+  for (int nz = -1; nz <= 1; ++nz)
+    for (int ny = -1; ny <= 1; ++ny)
+      for (int nx = -1; nx <= 1; ++nx) {
+        if (!nx && !ny && !nz) continue;
+        const int64_t u[3] = {nx, ny, nz};
+        deriv_g(u, 1.0, q, mi, D);  // d^gamma (-1/r)
+        for (int k = 0; k < mi.size(); ++k)
+          if (mi.list[k][0] + mi.list[k][1] + mi.list[k][2] <= q) out[k] -= D[k];
+      }
+  return out;
+}
+
+void Tables::build_lattice() {
+  MultiIdx mq;
+  mq.build(p);
+  const std::vector<double> T = lattice_tensor(p, mq);
+  auto Tat = [&](int a0, int a1, int a2) { return T[mq.at(a0, a1, a2)]; };
+  const int K = 8 * nc;
+  lattice.assign((size_t)K * K, 0.0);
+  const double h1 = 0.5;
+  std::vector<double> M0(nc), L0(nc);
+  for (int cs = 0; cs < 8; ++cs)
+    for (int al = 0; al < nc; ++al) {
+      // a unit physical moment alpha of child cs, about its centre, shifted to the root (Eq. 2)
+      const auto& A = mi.list[al];
+      double d[3];
+      for (int i = 0; i < 3; ++i) d[i] = (bit(cs, i) - 0.5) * h1;
+      for (int g = 0; g < nc; ++g) {
+        const auto& Gm = mi.list[g];
+        M0[g] = 0.0;
+        if (Gm[0] < A[0] || Gm[1] < A[1] || Gm[2] < A[2]) continue;
+        double v = binom(Gm[0], A[0]) * binom(Gm[1], A[1]) * binom(Gm[2], A[2]);
+        for (int i = 0; i < 3; ++i) v *= std::pow(d[i], Gm[i] - A[i]);
+        M0[g] = v;
+      }
+      // the lattice M2L at the root (Eq. 3 with D = T, same truncation as M2L)
+      for (int be = 0; be < nc; ++be) {
+        const auto& B = mi.list[be];
+        double v = 0.0;
+        for (int g = 0; g < nc; ++g) {
+          if (degree[g] + degree[be] > p || degree[g] > pm || M0[g] == 0.0) continue;
+          const auto& Gm = mi.list[g];
+          v += ((degree[g] & 1) ? -1.0 : 1.0) / mfact(Gm) * Tat(Gm[0] + B[0], Gm[1] + B[1], Gm[2] + B[2]) * M0[g];
+        }
+        L0[be] = v;
+      }
+      // L2L (Eq. 4) to each child ct, then to box units of level 1
+      for (int ct = 0; ct < 8; ++ct) {
+        double r[3];
+        for (int i = 0; i < 3; ++i) r[i] = (bit(ct, i) - 0.5) * h1;
+        for (int be = 0; be < nc; ++be) {
+          const auto& B = mi.list[be];
+          double v = 0.0;
+          for (int de = 0; de < nc; ++de) {
+            if (degree[de] + degree[be] > p) continue;
+            const auto& Dl = mi.list[de];
+            v += std::pow(r[0], Dl[0]) * std::pow(r[1], Dl[1]) * std::pow(r[2], Dl[2]) / mfact(Dl) *
+                 L0[mi.at(Dl[0] + B[0], Dl[1] + B[1], Dl[2] + B[2])];
+          }
+          lattice[(size_t)(ct * nc + be) * K + cs * nc + al] =
+              v * std::pow(h1, degree[be] + 1) * std::pow(h1, degree[al]);
+        }
+      }
+    }
+  // Level-1 M2L: all 26 neighbour octs of the one level-1 oct are its own
+  // images, so its M2L (box units, the same operator at every level) is a
+  // fixed map too; it joins the lattice map and runs in the same FP64 product.
+  if (!m2l.empty()) {
+    const size_t KM = (size_t)26 * K;
+    for (int b = 0; b < 8; ++b)
+      for (int be = 0; be < nc; ++be)
+        for (int qi = 0; qi < 26; ++qi)
+          for (int s2 = 0; s2 < 8; ++s2)
+            for (int al = 0; al < nc; ++al)
+              lattice[(size_t)(b * nc + be) * K + s2 * nc + al] +=
+                  m2l[(size_t)(b * nc + be) * KM + (size_t)(qi * 8 + s2) * nc + al];
+  }
+}
+
 }  // namespace fmm

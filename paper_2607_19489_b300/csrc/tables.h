@@ -82,8 +82,23 @@ struct Tables {
   // grid, output as m2p, input k = (qi*8+s)*8 + child; level l-1 units.
   std::vector<double> p2pr;  // [256][26*64]
 
+  // Periodic boundaries: the local expansions of the 8 level-1 boxes (box
+  // units) from their multipoles (box units): through the root, from every
+  // image of the root beyond its 3^3 and the neutralising background (M2M to
+  // the root, the lattice M2L = Eq. 3 with D = the lattice tensor, L2L back
+  // down), plus the level-1 M2L from the root's 26 nearest images (built
+  // after m2l).  lattice[(c nc + beta) 8 nc + c' nc + alpha].
+  std::vector<double> lattice;
+
   void build(int p, int p_m = 0);  // p_m = 0: p
   void build_dl2();
+  void build_lattice();
 };
+
+// The lattice tensor T_gamma = d^gamma psi_far(0), |gamma| <= q, in the order
+// of mi: psi_far = Ewald's periodic potential of a unit mass with its uniform
+// neutralising background (box [0,1)^3, g = -1/r) minus g over the 27 images
+// n in {-1,0,1}^3.
+std::vector<double> lattice_tensor(int q, const MultiIdx& mi);
 
 }  // namespace fmm

@@ -229,6 +229,7 @@ __global__ void k_dense_place(int level, int64_t n_leaf, int64_t n_ref, int64_t 
 // all these levels; level lmin's cells come from k_place_complete.
 struct CompleteLevels {
   int lmin;
+  int periodic;  // neighbours wrap around the box
   int64_t oct0[kMaxLevel + 2];  // first oct of level l in the thread index space
   uint64_t* oct_key[kMaxLevel + 1];
   int32_t* oct_parent[kMaxLevel + 1];
@@ -259,7 +260,12 @@ __global__ void k_complete_levels(const __grid_constant__ CompleteLevels P) {
   const int lim = 1 << pl;
   int32_t* nb = P.nbr[l] + o * 27;
   for (int q = 0; q < 27; ++q) {
-    const int x = px + q % 3 - 1, y = py + (q / 3) % 3 - 1, z = pz + q / 9 - 1;
+    int x = px + q % 3 - 1, y = py + (q / 3) % 3 - 1, z = pz + q / 9 - 1;
+    if (P.periodic) {  // the image's box (lim is a power of two)
+      x &= lim - 1;
+      y &= lim - 1;
+      z &= lim - 1;
+    }
     nb[q] = (x < 0 || y < 0 || z < 0 || x >= lim || y >= lim || z >= lim)
                 ? -1
                 : (int32_t)(spread3(x) | (spread3(y) << 1) | (spread3(z) << 2));
@@ -755,6 +761,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
   if (!partial) {
     CompleteLevels P{};
     P.lmin = lmin;
+    P.periodic = c->cfg.periodic;
     int64_t tot = 0;
     for (int l = 1; l <= lmin; ++l) {
       LevelTree& T = c->lev[l];
@@ -813,7 +820,7 @@ fmm_status tree_enqueue(Ctx* c, cudaStream_t st) {
       L.want_irows = l >= lmin;
       L.oct_parent = (const int32_t*)T.oct_parent.ptr;
       L.oct_parent_up = l >= 2 ? (const int32_t*)c->lev[l - 1].oct_parent.ptr : nullptr;
-      L.slotL_far = l - (2 - m1) >= 2 ? (const int32_t*)c->lev[l - (2 - m1)].slotL.ptr : nullptr;
+      L.slotL_far = l - (2 - m1) >= first_local_level(c) ? (const int32_t*)c->lev[l - (2 - m1)].slotL.ptr : nullptr;
       L.lslot = (int32_t*)T.lslot.ptr;
       L.n_oct_up = l >= 2 ? c->lev[l - 1].n_oct : 0;
       L.n_oct_far = l - (2 - m1) >= 1 ? c->lev[l - (2 - m1)].n_oct : 0;

@@ -531,6 +531,7 @@ struct L2LPathSeg {
 struct L2LPathParams {
   L2LPathSeg seg[kMaxLevel];
   int nseg, nc, npairs, max_level;
+  int l0;  // first level of every path (2; 1 with periodic boundaries)
   const int32_t* oct_parent[kMaxLevel + 1];
   const int32_t* slotL[kMaxLevel + 1];
   const float* Lm[kMaxLevel + 1];  // M2L sums, per slot in the contraction's column order (lmcol)
@@ -564,26 +565,26 @@ __global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant
   TA* S = Lp + nc;                            // [8][nc] pattern sums
   int* gg = (int*)(S + 8 * nc);               // [np]
   int* off = gg + np;                         // [8 nc + 1]
-  float* Lmp = (float*)(off + 8 * nc + 1);    // [max_level - 2][nc] M2L sums of the path cells
+  float* Lmp = (float*)(off + 8 * nc + 1);    // [max_level - l0][nc] M2L sums of the path cells
   __shared__ int32_t s_row[kMaxLevel + 1];    // row (8 slot + cell) of the path cell at level k
   __shared__ int s_pos[kMaxLevel + 1];        // its position in its oct
   int si = 0;
   while (si + 1 < P.nseg && (int)blockIdx.x >= P.seg[si + 1].blk0) ++si;
   const L2LPathSeg& Sg = P.seg[si];
-  const int b = Sg.level;
+  const int b = Sg.level, l0 = P.l0;
   // tree data and tables (written before this solve): read before the wait
   const int32_t o = Sg.rows[blockIdx.x - Sg.blk0];
   const int64_t so = P.slotL[b][o];
   if (threadIdx.x == 0) {
-    int32_t cell = b > 2 ? P.oct_parent[b][o] : 0;
-    for (int k = b - 1; k >= 2; --k) {
+    int32_t cell = b > l0 ? P.oct_parent[b][o] : 0;
+    for (int k = b - 1; k >= l0; --k) {
       const int32_t oc = cell >> 3;
       s_row[k] = P.slotL[k][oc] * 8 + (cell & 7);
       s_pos[k] = cell & 7;
-      if (k > 2) cell = P.oct_parent[k][oc];
+      if (k > l0) cell = P.oct_parent[k][oc];
     }
   }
-  if (b > 2) {
+  if (b > l0) {
     stage_block<8>(np, [&](int j) { return ((const TA*)P.pc)[j]; }, cf);
     stage_block<8>(np, [&](int j) { return P.pg[j]; }, gg);
     stage_block<4>(8 * nc + 1, [&](int k) { return P.poff8[k]; }, off);
@@ -591,23 +592,23 @@ __global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant
   pdl_wait();
   pdl_trigger();
   __syncthreads();
-  // the M2L sums: the path's (levels 2..b-1) to shared memory, the own oct's to registers
-  for (int k = 2; k < b; ++k)
+  // the M2L sums: the path's (levels l0..b-1) to shared memory, the own oct's to registers
+  for (int k = l0; k < b; ++k)
     for (int j = threadIdx.x; j < nc; j += kPathThreads)
-      Lmp[(k - 2) * nc + j] = P.Lm[k][(int64_t)(s_row[k] >> 3) * 8 * nc + __ldg(P.lmcol + (s_row[k] & 7) * nc + j)];
+      Lmp[(k - l0) * nc + j] = P.Lm[k][(int64_t)(s_row[k] >> 3) * 8 * nc + __ldg(P.lmcol + (s_row[k] & 7) * nc + j)];
   const int beta = threadIdx.x;  // nc <= 165 < kPathThreads
   float own[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) own[c] = beta < nc ? P.Lm[b][so * 8 * nc + __ldg(P.lmcol + c * nc + beta)] : 0.f;
   __syncthreads();
-  if (b > 2 && beta < nc) Lp[beta] = (TA)Lmp[beta];  // level 2: the M2L sum alone
+  if (b > l0 && beta < nc) Lp[beta] = (TA)Lmp[beta];  // level l0: the M2L sum alone
   __syncthreads();
-  for (int k = 3; k < b; ++k) {
+  for (int k = l0 + 1; k < b; ++k) {
     l2l_pattern_sums(nc, Lp, cf, gg, off, S);
     __syncthreads();
     if (beta < nc) {
       const unsigned nc_pos = ~(unsigned)s_pos[k] & 7u;
-      TA y = (TA)Lmp[(k - 2) * nc + beta];
+      TA y = (TA)Lmp[(k - l0) * nc + beta];
 #pragma unroll
       for (int e = 0; e < 8; ++e) y += (__popc((unsigned)e & nc_pos) & 1) ? -S[e * nc + beta] : S[e * nc + beta];
       Lp[beta] = y;  // every thread has read Lp (barrier above) before it changes
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant
   TA acc[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0;
-  if (b > 2) {
+  if (b > l0) {
     l2l_pattern_sums(nc, Lp, cf, gg, off, S);
     __syncthreads();
     if (beta < nc) {
@@ -633,9 +634,37 @@ __global__ void __launch_bounds__(kPathThreads) k_l2l_path(const __grid_constant
 }
 
 template <typename TA>
-inline size_t l2l_path_smem(int nc, int npairs, int max_level) {
+inline size_t l2l_path_smem(int nc, int npairs, int max_level, int l0 = 2) {
   return (size_t)npairs * (sizeof(TA) + 4) + (size_t)nc * sizeof(TA) * 9 + (size_t)(8 * nc + 1) * 4 +
-         (size_t)std::max(max_level - 2, 0) * nc * 4;
+         (size_t)std::max(max_level - l0, 0) * nc * 4;
+}
+
+// Periodic boundaries: the level-1 local expansions gain the images of the root
+// beyond its 3^3 and the background, L(1) += A M(1), A the dense 8 nc x 8 nc
+// host-built map (M2M to the root, the lattice M2L, L2L back).  One warp per
+// output row; M(1) is the one level-1 oct's 8 cells (oct 0), its expansion slot
+// slot1[0].  The mixed paths add into the M2L sums (column order lmcol), FP64
+// into L.
+template <typename TM, typename TA>
+__global__ void __launch_bounds__(256) k_lattice(int nc, const TA* __restrict__ A, const TM* __restrict__ M1,
+                                                 const int32_t* __restrict__ slot1, float* __restrict__ Lm,
+                                                 const int* __restrict__ lmcol, double* __restrict__ L64) {
+  pdl_wait();
+  pdl_trigger();
+  const int K = 8 * nc;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= K) return;
+  double s = 0.0;
+  for (int k = lane; k < K; k += 32) s += (double)A[(int64_t)row * K + k] * (double)M1[k];
+#pragma unroll
+  for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if (lane) return;
+  const int64_t so = slot1[0];
+  const int c = row / nc, beta = row - c * nc;
+  if (L64)
+    atomicAdd(L64 + (so * 8 + c) * nc + beta, s);
+  else
+    atomicAdd(Lm + so * 8 * nc + lmcol[c * nc + beta], (float)s);
 }
 
 // Clears the M2L sums of the row octs the next M2L writes (their slots: 8 nc
@@ -672,10 +701,10 @@ fmm_status upward_init(Ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2m_smem(165, 3003));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_l2l_path<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)l2l_path_smem<double>(165, 3003, kMaxLevel));
+                             (int)l2l_path_smem<double>(165, 3003, kMaxLevel, 1));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_l2l_path<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)l2l_path_smem<float>(165, 3003, kMaxLevel));
+                             (int)l2l_path_smem<float>(165, 3003, kMaxLevel, 1));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_m2m_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmemMax);
   if (e == cudaSuccess)
@@ -781,7 +810,9 @@ void launch_l2l_path(Ctx* c, int lo, cudaStream_t st) {
   const int top = top_local_level(c);
   L2LPathParams P{};
   int blocks = 0;
-  for (int b = std::max(2, lo - (2 - m1)); b <= top; ++b) {
+  const int l0 = first_local_level(c);
+  P.l0 = l0;
+  for (int b = std::max(l0, lo - (2 - m1)); b <= top; ++b) {
     LevelTree& T = c->lev[b];
     if (!T.n_rowsL) continue;
     L2LPathSeg& S = P.seg[P.nseg++];
@@ -793,7 +824,7 @@ void launch_l2l_path(Ctx* c, int lo, cudaStream_t st) {
     P.max_level = b;
   }
   if (!blocks) return;
-  for (int k = 2; k <= P.max_level; ++k) {
+  for (int k = l0; k <= P.max_level; ++k) {
     LevelTree& T = c->lev[k];
     P.oct_parent[k] = (const int32_t*)T.oct_parent.ptr;
     P.slotL[k] = (const int32_t*)T.slotL.ptr;
@@ -808,12 +839,12 @@ void launch_l2l_path(Ctx* c, int lo, cudaStream_t st) {
   ++c->n_launch;
   if (c->cfg.fp64_top) {
     P.pc = c->d_l2l_c.ptr;
-    launch_pdl(k_l2l_path<double>, (unsigned)blocks, kPathThreads, l2l_path_smem<double>(P.nc, P.npairs, P.max_level),
-               st, P);
+    launch_pdl(k_l2l_path<double>, (unsigned)blocks, kPathThreads,
+               l2l_path_smem<double>(P.nc, P.npairs, P.max_level, l0), st, P);
   } else {
     P.pc = c->d_l2l_c32.ptr;
-    launch_pdl(k_l2l_path<float>, (unsigned)blocks, kPathThreads, l2l_path_smem<float>(P.nc, P.npairs, P.max_level),
-               st, P);
+    launch_pdl(k_l2l_path<float>, (unsigned)blocks, kPathThreads,
+               l2l_path_smem<float>(P.nc, P.npairs, P.max_level, l0), st, P);
   }
 }
 
@@ -885,6 +916,25 @@ void launch_m2m_chain(Ctx* c, int b_top, cudaStream_t st) {
     launch_pdl(k_m2m_chain<float>, 1u, 32u * w, chain_smem(nc, P.npairs, w), st, P);
 }
 
+void launch_lattice(Ctx* c, cudaStream_t st) {
+  LevelTree& T = c->lev[1];
+  if (!T.n_rowsL) return;
+  const int nc = c->tab.nc;
+  const unsigned g = (unsigned)((8 * nc + 7) / 8);
+  const int32_t* slot1 = (const int32_t*)T.slotL.ptr;
+  ++c->n_launch;
+  if (c->cfg.precision == FMM_FP64) {
+    launch_pdl(k_lattice<double, double>, g, 256, 0, st, nc, (const double*)c->d_lat64.ptr, (const double*)T.M.ptr,
+               slot1, (float*)nullptr, (const int*)nullptr, (double*)T.L.ptr);
+  } else if (T.m_is_f64) {
+    launch_pdl(k_lattice<double, float>, g, 256, 0, st, nc, (const float*)c->d_lat32.ptr, (const double*)T.M.ptr,
+               slot1, (float*)T.Lm.ptr, (const int*)c->op_m2l.colmap.ptr, (double*)nullptr);
+  } else {
+    launch_pdl(k_lattice<float, float>, g, 256, 0, st, nc, (const float*)c->d_lat32.ptr, (const float*)T.M.ptr,
+               slot1, (float*)T.Lm.ptr, (const int*)c->op_m2l.colmap.ptr, (double*)nullptr);
+  }
+}
+
 void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t nrows) {
   LevelTree& T = c->lev[b];
   if (!rows) {
@@ -896,7 +946,8 @@ void launch_l2l_add(Ctx* c, int b, cudaStream_t st, const int32_t* rows, int64_t
   const int np = (int)c->tab.l2l_g.size();
   launch_pdl(k_l2l_add, (unsigned)nrows, 128, l2l_smem(c->tab.nc, np), st,
       c->tab.nc, np, rows, (const int32_t*)T.oct_parent.ptr, (const int32_t*)T.slotL.ptr,
-      b >= 3 ? (const int32_t*)c->lev[b - 1].slotL.ptr : nullptr, b >= 3 ? (const double*)c->lev[b - 1].L.ptr : nullptr,
+      b > first_local_level(c) ? (const int32_t*)c->lev[b - 1].slotL.ptr : nullptr,
+      b > first_local_level(c) ? (const double*)c->lev[b - 1].L.ptr : nullptr,
       c->cfg.precision == FMM_FP64 ? nullptr : (float*)T.Lm.ptr, (double*)T.L.ptr, (float*)T.Lf.ptr,
       (const int*)c->op_m2l.colmap.ptr, (const int*)c->d_l2l_off8.ptr, (const int*)c->d_l2l_g.ptr, (const double*)c->d_l2l_c.ptr);
 }

@@ -40,7 +40,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("precision", ctypes.c_int), ("G", ctypes.c_double),
                 ("out_fp32", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("bottom_mode", ctypes.c_int),
                 ("p_m", ctypes.c_int), ("mass_fp32", ctypes.c_int), ("fp64_top", ctypes.c_int),
-                ("delta_l", ctypes.c_int)]
+                ("delta_l", ctypes.c_int), ("periodic", ctypes.c_int)]
 
 
 # fmm_alloc_fn: (user, ptr, bytes, stream) -> ptr
@@ -148,8 +148,10 @@ def host_numerators(q: int, u) -> np.ndarray:
 
 _TABLE_SHAPES = {
     0: lambda nc: (256, 26 * 8 * nc), 1: lambda nc: (8 * nc, 26 * 8 * nc), 2: lambda nc: (343, nc, 4),
-    3: lambda nc: (64, nc, 4), 4: lambda nc: (8, nc, nc), 5: lambda nc: (8, nc, nc)}
-TABLES = {"m2p": 0, "m2l": 1, "near": 2, "l2p": 3, "m2m": 4, "l2l": 5}
+    3: lambda nc: (64, nc, 4), 4: lambda nc: (8, nc, nc), 5: lambda nc: (8, nc, nc), 6: lambda nc: (nc,),
+    7: lambda nc: (8 * nc, 8 * nc), 8: lambda nc: (2048, 26 * 8 * nc)}
+TABLES = {"m2p": 0, "m2l": 1, "near": 2, "l2p": 3, "m2m": 4, "l2l": 5, "lattice_tensor": 6, "lattice": 7,
+          "m2p_dl2": 8}
 
 
 def host_table(p: int, which: str) -> np.ndarray:
@@ -173,12 +175,13 @@ class Solver:
     for the top-of-tree M2M and the L2L chain / local-expansion accumulation;
     delta_l: levels between the cells and the finest FMM box, 1 (the paper's) or 2
     (the variant of the footnote of Sec. 2: a 12^3-cell near field; one complete
-    level only); allocator: "torch" (PyTorch's caching allocator supplies the library's device
+    level only); periodic: periodic boundaries (Ewald's potential with a
+    neutralising background, lmin >= 3); allocator: "torch" (PyTorch's caching allocator supplies the library's device
     memory) or "cuda" (cudaMalloc)."""
 
     def __init__(self, p: int = 6, precision: str = "mixed", G: float = 1.0, out_fp32: bool = False,
                  mem_budget: int = 0, bottom: str = "m2p", p_m: int | None = None, mass_fp32: bool = False,
-                 allocator: str = "torch", fp64_top: bool = False, delta_l: int = 1):
+                 allocator: str = "torch", fp64_top: bool = False, delta_l: int = 1, periodic: bool = False):
         self.p = p
         self.precision = precision
         self.out_fp32 = out_fp32
@@ -186,8 +189,9 @@ class Solver:
         self.bottom = bottom
         self.p_m = p if p_m is None else p_m
         self.delta_l = delta_l
+        self.periodic = bool(periodic)
         cfg = _Config(p, PRECISION[precision], float(G), int(out_fp32), int(mem_budget), BOTTOM[bottom],
-                      0 if p_m is None else int(p_m), int(mass_fp32), int(fp64_top), int(delta_l))
+                      0 if p_m is None else int(p_m), int(mass_fp32), int(fp64_top), int(delta_l), int(periodic))
         if allocator not in ("torch", "cuda"):
             raise ValueError("allocator must be 'torch' or 'cuda'")
         h = ctypes.c_void_p()

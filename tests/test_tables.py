@@ -5,6 +5,8 @@ Box units: a box of size h stores Mt_alpha = M_alpha / h^|alpha| and
 Lt_beta = L_beta h^(|beta|+1).  The geometry of each table is set up here
 with the source box of size 1 (so box units and physical units coincide for
 the source) and compared operator by operator."""
+import math
+
 import numpy as np
 import pytest
 
@@ -127,3 +129,68 @@ def test_l2l_table(p):
         cc = (bits(c) - 0.5) / 2
         ref = oracle.l2l(p, Lp, [0.0, 0.0, 0.0], cc) * 0.5 ** (d + 1)
         np.testing.assert_allclose(T[c] @ Lp, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_m2p_delta_l2_table(p):
+    """Delta l = 2: M2P from a level l-2 source box (size 1 here) to the 512
+    level-l cells under a row oct, returned in level l-1 units (phi / 2, accel / 4)."""
+    nc = oracle.ncoef(p)
+    T = fmm.host_table(p, "m2p_dl2")
+    rng = np.random.default_rng(30 + p)
+    checked = 0
+    for g in (0, 6):
+        for f in (1, 7):
+            for t in (0, 5):
+                for qi in (0, 9, 13, 25):
+                    for s in (0, 7):
+                        q27 = NBR26[qi]
+                        cS = 2 * dq_of(q27) + bits(s) + 0.5
+                        x = bits(g) + (2 * bits(f) + bits(t) + 0.5) / 4
+                        n0 = ((g * 8 + f) * 8 + t) * 4
+                        block = T[n0:n0 + 4, (qi * 8 + s) * nc:(qi * 8 + s + 1) * nc]
+                        if np.abs(bits(g) - 2 * dq_of(q27) - bits(s)).max() <= 1:
+                            assert np.all(block == 0)
+                            continue
+                        M = rng.normal(size=nc)
+                        ref = oracle.m2p(p, M, cS, x)
+                        got = block @ M
+                        np.testing.assert_allclose(got[0], 0.5 * ref[0], rtol=1e-12, atol=1e-13)
+                        np.testing.assert_allclose(got[1:], -0.25 * ref[1:], rtol=1e-11, atol=1e-13)
+                        checked += 1
+    assert checked > 20
+
+
+def test_lattice_tables(p):
+    """Periodic boundaries: the library's lattice tensor (Taylor-mode Ewald) against
+    the oracle's (radial recursion), and the level-1 operator against the oracle's
+    M2M, Eq. 3 with that tensor and L2L, plus the oracle's M2L from the 26 images of
+    the level-1 oct around it, in level-1 box units."""
+    T_lib = fmm.host_table(p, "lattice_tensor")
+    T = oracle.lattice_tensor(p)
+    assert np.max(np.abs(T_lib - T) / np.maximum(np.abs(T), 1.0)) < 1e-9
+    nc = oracle.ncoef(p)
+    mi = oracle.multi_index(p)
+    idx = {tuple(int(v) for v in m): k for k, m in enumerate(mi)}
+    deg = mi.sum(1)
+    fact = np.array([np.prod([math.factorial(int(v)) for v in m]) for m in mi], dtype=np.float64)
+    A = fmm.host_table(p, "lattice")
+    h1, c0 = 0.5, np.full(3, 0.5)
+    rng = np.random.default_rng(p)
+    for cs in (0, 5):
+        Mt = rng.normal(size=nc)
+        M0 = oracle.m2m(p, Mt * h1 ** deg, (bits(cs) + 0.5) * h1, c0)
+        L0 = np.zeros(nc)
+        for b, B in enumerate(mi):
+            for a, Al in enumerate(mi):
+                if deg[a] + deg[b] <= p:
+                    L0[b] += (-1.0) ** deg[a] / fact[a] * T[idx[tuple(int(v) for v in Al + B)]] * M0[a]
+        for ct in (0, 3, 7):
+            cT = (bits(ct) + 0.5) * h1
+            Lp = oracle.l2l(p, L0, c0, cT)
+            for q27 in NBR26:
+                cS = (2 * dq_of(q27) + bits(cs) + 0.5) * h1
+                if np.abs(bits(ct) - 2 * dq_of(q27) - bits(cs)).max() > 1:
+                    Lp = Lp + oracle.m2l(p, Mt * h1 ** deg, cS, cT)
+            ref = Lp * h1 ** (deg + 1)
+            got = A[ct * nc:(ct + 1) * nc, cs * nc:(cs + 1) * nc] @ Mt
+            np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
