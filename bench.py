@@ -50,7 +50,7 @@ NC = (P_ORDER + 1) * (P_ORDER + 2) * (P_ORDER + 3) // 6
 # DRAM bytes (read + write) of the stage-timed M2P launch (k_gemm_tc, in-order
 # solve, split-K from the built-in heuristic) of the headline workload, from one
 # ncu capture of that launch shape; None until captured for the current kernel.
-M2P_TRAFFIC_BYTES = 37021952
+M2P_TRAFFIC_BYTES = 37026816
 # FP32 work per P2P interaction, the usual count for a softened-free gravity
 # pair (3 differences, r^2, rsqrt ~4, m/r, m/r^3, 4 accumulations)
 FLOP_PER_PAIR = 20
@@ -495,7 +495,7 @@ def gpu_arm(args, rank, world, local):
     legs = [x for x in args.legs.split(",") if x and x != "none"] if not args.quick else []
     for name in legs:
         fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats, "sweep": leg_sweep,
-              "binary": leg_binary, "delta_l": leg_delta_l}.get(name)
+              "binary": leg_binary, "delta_l": leg_delta_l, "periodic": leg_periodic}.get(name)
         if fn is None:
             continue
         try:
@@ -730,6 +730,55 @@ def leg_delta_l(args, torch, dev, stream, flush):
     return {"unit": UNIT, "step": "fmm_set_levels + fmm_solve (inputs resident)", "runs": rows,
             "workload": "Plummer unigrids (a = 0.1, 1% noise)",
             "reference": "fmm_direct_sum (FP64 exact sum) on 4096 seeded cells", "wall_s": time.perf_counter() - t0}
+
+
+def leg_periodic(args, torch, dev, stream, flush):
+    """Periodic boundaries (the extension Sec. 6 names for cosmology): the
+    headline two-level 64^3 + 32^3 hierarchy and the 64^3 Plummer unigrid with
+    the box tiled by images and a neutralising background, p = 6, split-BF16 and
+    FP64.  Each entry: cell-updates/s of fmm_set_levels + fmm_solve, the
+    in-order stage times, and the mixed path's error against the FP64 GPU path
+    (relative RMS of accel; phi against max(RMS, G M_total), the periodic
+    field's scale)."""
+    from paper_2607_19489_b300 import fmm, workloads as W
+    rows = []
+    t0 = time.perf_counter()
+    for cname, h in (("two-level 64^3 + 32^3 Plummer a=0.05, lognormal 0.3", W.two_level_plummer()),
+                     ("unigrid 64^3 Plummer a=0.1, 1% noise", W.unigrid_plummer(6))):
+        ijk = [torch.as_tensor(a, device=dev).contiguous() for a in h.ijk]
+        mass = [torch.as_tensor(m, device=dev).contiguous() for m in h.mass]
+        outs = {}
+        for prec in ("fp64", "mixed"):
+            s = fmm.Solver(P_ORDER, prec, periodic=True)
+            s.set_levels(h.lmin, h.lmax, ijk, mass)
+            out = s.alloc_outputs(device=dev)
+
+            def step():
+                s.set_levels(h.lmin, h.lmax, ijk, mass)
+                s.solve(out=out)
+
+            ms = _timed(torch, step, 2 if prec == "fp64" else 50, 3, stream)
+            s.sync()
+            s.set_timing(True)
+            s.update_masses(mass)
+            s.solve(out=out)
+            s.sync()
+            st = s.stage_times()
+            s.set_timing(False)
+            outs[prec] = ({l: out[0][l].double() for l in h.levels}, {l: out[1][l].double() for l in h.levels})
+            rows.append({"config": cname, "precision": prec, "cells": h.n_cells, "ms": ms,
+                         "value": h.n_cells / (ms * 1e-3), "stages_ms": st})
+            del s, out
+        (pm, am), (pd, ad) = outs["mixed"], outs["fp64"]
+        num_a = sum(float(((am[l] - ad[l]) ** 2).sum()) for l in h.levels)
+        den_a = sum(float((ad[l] ** 2).sum()) for l in h.levels)
+        n = sum(h.n(l) for l in h.levels)
+        num_p = sum(float(((pm[l] - pd[l]) ** 2).sum()) for l in h.levels)
+        rms_p = np.sqrt(sum(float((pd[l] ** 2).sum()) for l in h.levels) / n)
+        rows[-1]["rel_rms_accel_vs_fp64"] = float(np.sqrt(num_a / den_a))
+        rows[-1]["rms_phi_err_vs_fp64_over_scale"] = float(np.sqrt(num_p / n) / max(rms_p, h.total_mass()))
+    return {"unit": UNIT, "step": "fmm_set_levels + fmm_solve (inputs resident), periodic boundaries", "runs": rows,
+            "wall_s": time.perf_counter() - t0}
 
 
 def leg_binary(args, torch, dev, stream, flush):
@@ -1010,7 +1059,7 @@ def main():
                     help="two_level: the measured configuration; unigrid16: a small check of the launch paths")
     ap.add_argument("--fd-cells", type=int, default=100,
                     help="adjoint leg: finite differences on this many seeded cells (one FP64 solve each)")
-    ap.add_argument("--legs", default="sweep,batched,adjoint,ats,binary,delta_l",
+    ap.add_argument("--legs", default="sweep,batched,adjoint,ats,binary,delta_l,periodic",
                     help="extra workloads reported beside the headline (comma list, or 'none')")
     ap.add_argument("--quick", action="store_true",
                     help="the mixed headline and its stage times only (no FP64 arm, e2e, legs or CPU baseline)")
