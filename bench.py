@@ -969,6 +969,27 @@ def leg_ats(args, torch, dev, stream, flush):
     evs[-1].synchronize()
     per_solve = [{"lo": lo, "ms": evs[i].elapsed_time(evs[i + 1]),
                   "cells": sum(h.n(l) for l in range(lo, h.lmax + 1))} for i, lo in enumerate(sched)]
+    # Each kind of solve alone, as a subcycle loop runs it: the stream idle and
+    # the host core busy before it (a solve that follows a 60 ms one in the
+    # schedule starts on a host core that idled meanwhile, and its launch work
+    # then runs several times slower), median of 20 rebuild + solve pairs.
+    per_lo = {}
+    for lo, ms in zip(sched, pert):
+        if lo in per_lo or lo == h.lmin:
+            continue
+        tt = []
+        for _ in range(20):
+            torch.cuda.synchronize()
+            host_warm(0.05)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.set_levels(h.lmin, h.lmax, ijk[lo - h.lmin:], ms, lo=lo)
+            s.solve(lo, out=outs[lo])
+            e1.record(stream)
+            e1.synchronize()
+            tt.append(e0.elapsed_time(e1))
+        per_lo[str(lo)] = statistics.median(tt)
     # in-order stage times of each kind of solve in the schedule (one rebuild + solve per lo)
     s.set_timing(True)
     stages = {}
@@ -999,7 +1020,8 @@ def leg_ats(args, torch, dev, stream, flush):
     res = {"workload": h.name + ", p=6 mixed, FP32 outputs", "cells": h.n_cells,
            "levels": [h.n(l) for l in h.levels], "schedule_lo": sched,
            "value": updated / (ms_step * 1e-3), "unit": UNIT, "ms_per_coarse_step": ms_step,
-           "per_solve": per_solve, "stages_ms_by_lo": {str(k): v for k, v in sorted(stages.items())},
+           "per_solve": per_solve, "solve_alone_ms_by_lo": per_lo,
+           "stages_ms_by_lo": {str(k): v for k, v in sorted(stages.items())},
            "cell_updates_per_coarse_step": updated, "full_rebuild_and_solve_ms": ms_full,
            "tuning": tuning, "generation_s": gen_s, "rel_rms_accel_mixed_vs_fp64": err_ats,
            "step": "per solve of the schedule: fmm_set_levels(lo) with perturbed masses + fmm_solve(lo)"}

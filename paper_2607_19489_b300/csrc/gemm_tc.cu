@@ -301,9 +301,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  pdl_wait();  // rows, neighbour tables and multipoles come from earlier kernels
-  pdl_trigger();
-
+  // Programmatic dependent launch: the row lists and neighbour tables (tree
+  // build) and the operator (built at creation) are read before the wait on
+  // the previous kernel; only the multipole rows it produces, and the outputs,
+  // come after it (the producer warps, which also run the epilogue, wait).
   if (warp < kProducerWarps) {
     // ---------------- A rows into TMEM ----------------
     const int q = warp & 3;             // lane quarter: rows 32 q .. 32 q + 31
@@ -319,6 +320,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int qq = 0; qq < 26; ++qq) myn[qq] = valid ? S.nbr[(int64_t)roct * 27 + c_nbr26[qq]] : -1;
     }
     asm volatile("bar.sync 1, %0;" ::"n"(32 * kProducerWarps) : "memory");  // tables of all rows written
+    pdl_wait();  // the multipole rows come from the previous kernel
+    pdl_trigger();
     const uint32_t myn_s = smem_u32(s_nbr + t * kNbrStride);  // read back with ld.shared
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);   // this warp's lanes, column 0
     bool ok = true;
@@ -475,7 +478,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp == kWarpTma) {
-    // ---------------- B tiles by TMA ----------------
+    // ---------------- B tiles by TMA (the operator: no wait) ----------------
+    pdl_trigger();
     if (lane == 0) {
       bool ok = true;
       int issued = 0;
@@ -501,7 +505,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncwarp();
   } else if (warp == kWarpMma) {
-    // ---------------- MMA issue ----------------
+    // ---------------- MMA issue (shared and tensor memory only) ----------------
+    pdl_trigger();
     if (lane == 0) {
       // kind::f16, D = F32, A = B = BF16 (format 1), or kind::tf32, A = B = TF32 (format 2);
       // both K-major, M = 128, N = BN

@@ -170,8 +170,6 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
     __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, float* __restrict__ mono,
     const int* __restrict__ poff, const int* __restrict__ pg, const int* __restrict__ pe,
     const float* __restrict__ pc, const float* __restrict__ w0, const int* __restrict__ e0) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(16) unsigned char dsm[];
   float* cf = (float*)dsm;                   // [npairs] coefficients
   int* gx = (int*)(cf + npairs);             // [npairs] gamma + nc * e
@@ -179,6 +177,10 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
   int* ccs = off + nc + 1;                   // [warps][8] children of each warp's oct
   float* Sall = (float*)(ccs + 8 * kM2MWarps);  // [warps][8 * nc]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Before the wait on the previous kernel (the level below, whose rows this
+  // one reads): the tree links and leaf masses (set by the tree build and the
+  // input staging, kernels that completed before that one started) and the
+  // pair tables, so that their latency overlaps the previous level's tail.
   const int64_t i = (int64_t)blockIdx.x * kM2MWarps + warp;
   const bool valid = i < n_oct_next;
   const int64_t o = valid ? (octs ? octs[i] : i) : 0;
@@ -193,6 +195,8 @@ __global__ void __launch_bounds__(32 * kM2MWarps) k_m2m(
     stage_block<1>(nc + 1, [&](int j) { return poff[j]; }, off);
     __syncthreads();
   }
+  pdl_wait();
+  pdl_trigger();
   if (!valid) return;  // warp-uniform; no block-wide barrier below
   if (leaf_only) {
     // table entries first (independent of the masses), all loads in flight together
