@@ -50,7 +50,7 @@ NC = (P_ORDER + 1) * (P_ORDER + 2) * (P_ORDER + 3) // 6
 # DRAM bytes (read + write) of the stage-timed M2P launch (k_gemm_tc, in-order
 # solve, split-K from the built-in heuristic) of the headline workload, from one
 # ncu capture of that launch shape; None until captured for the current kernel.
-M2P_TRAFFIC_BYTES = 37026816
+M2P_TRAFFIC_BYTES = 37023488
 # FP32 work per P2P interaction, the usual count for a softened-free gravity
 # pair (3 differences, r^2, rsqrt ~4, m/r, m/r^3, 4 accumulations)
 FLOP_PER_PAIR = 20
