@@ -40,6 +40,10 @@ def test_create_rejects_bad_arguments_without_gpu():
                                           (4, 1, 0, 0, 2, 0), (4, 1, 0, 0, 0, 3)]:
         cfg = fmm._Config(p, prec, 1.0, 0, 0, bottom, pm, m32, t64)
         assert L.fmm_create(ctypes.byref(cfg), none, None, ctypes.byref(h)) == -1, (p, prec, bottom, pm, m32, t64)
+    # (delta_l, periodic, bottom mode): out of range, or a combination the variants exclude
+    for dl, per, bottom in [(3, 0, 0), (-1, 0, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (2, 1, 0)]:
+        cfg = fmm._Config(4, 1, 1.0, 0, 0, bottom, 0, 0, 0, dl, per)
+        assert L.fmm_create(ctypes.byref(cfg), none, None, ctypes.byref(h)) == -1, (dl, per, bottom)
     assert L.fmm_create(None, none, None, ctypes.byref(h)) == -1
     assert L.fmm_set_wait_limit(None, 1.0) == -1
     assert L.fmm_set_levels(None, 2, 3, 2, None, None, None, None) == -1
