@@ -492,7 +492,8 @@ def gpu_arm(args, rank, world, local):
         "clocks": clocks,
     }
     del mixed, fp64, e2e_solver
-    legs = [x for x in args.legs.split(",") if x and x != "none"] if not args.quick else []
+    # the extra workloads characterise one GPU: a multi-rank run reports the headline only
+    legs = [x for x in args.legs.split(",") if x and x != "none"] if not args.quick and world == 1 else []
     for name in legs:
         fn = {"batched": leg_batched, "adjoint": leg_adjoint, "ats": leg_ats, "sweep": leg_sweep,
               "binary": leg_binary, "delta_l": leg_delta_l, "periodic": leg_periodic}.get(name)
@@ -680,10 +681,10 @@ def leg_delta_l(args, torch, dev, stream, flush):
     p = 4 and 6 in FP64, split-BF16 and TF32.  Each entry: cell-updates/s of
     fmm_set_levels + fmm_solve, the in-order stage times of one solve, and the
     relative RMS error against the exact sum (fmm_direct_sum, FP64) on 4096
-    seeded cells."""
+    seeded cells.  One context per (p, precision, Delta l) serves every grid."""
     from paper_2607_19489_b300 import fmm, workloads as W
-    rows = []
     t0 = time.perf_counter()
+    grids = []
     for level in (5, 6, 7):
         h = W.unigrid_plummer(level)
         ijk = [torch.as_tensor(a, device=dev).contiguous() for a in h.ijk]
@@ -695,12 +696,16 @@ def leg_delta_l(args, torch, dev, stream, flush):
         d_phi, d_acc = ref.direct_sum(l, sel)
         ref.sync()
         del ref
-        for p in (4, 6):
-            for prec in ("fp64", "mixed", "tf32"):
-                if prec == "fp64" and level == 7:
-                    continue  # seconds per solve; the two smaller grids carry the FP64 comparison
-                for dl in (1, 2):
-                    s = fmm.Solver(p, prec, delta_l=dl)
+        grids.append((level, h, ijk, mass, sel, d_phi, d_acc))
+    rows = []
+    for p in (4, 6):
+        for prec in ("fp64", "mixed", "tf32"):
+            for dl in (1, 2):
+                s = fmm.Solver(p, prec, delta_l=dl)
+                for level, h, ijk, mass, sel, d_phi, d_acc in grids:
+                    if prec == "fp64" and level == 7:
+                        continue  # seconds per solve; the two smaller grids carry the FP64 comparison
+                    l = h.lmin
                     s.set_levels(l, l, ijk, mass)
                     out = s.alloc_outputs(device=dev)
 
@@ -726,7 +731,9 @@ def leg_delta_l(args, torch, dev, stream, flush):
                                                                   (d_acc ** 2).sum().sqrt()),
                                  "rel_rms_phi_vs_direct": float(((gp - d_phi) ** 2).sum().sqrt() /
                                                                 (d_phi ** 2).sum().sqrt())})
-                    del s, out
+                    del out
+                del s
+    rows.sort(key=lambda r: (r["grid"], r["p"], ["fp64", "mixed", "tf32"].index(r["precision"]), r["delta_l"]))
     return {"unit": UNIT, "step": "fmm_set_levels + fmm_solve (inputs resident)", "runs": rows,
             "workload": "Plummer unigrids (a = 0.1, 1% noise)",
             "reference": "fmm_direct_sum (FP64 exact sum) on 4096 seeded cells", "wall_s": time.perf_counter() - t0}
