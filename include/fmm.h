@@ -336,6 +336,7 @@ fmm_status fmm_host_numerators(int q, const int64_t* u, int64_t* out);
  *         7: level-1 lattice operator [8*nc][8*nc] (the level-1 local expansions
  *                                           from the level-1 multipoles through the root)
  *         8: Delta l = 2 M2P [2048][26*8*nc] (n = ((g*8+f)*8+t)*4+comp)
+ *         9: Delta l = 2 near-field ring [256][26*64] (k = (q*8+s)*8+child)
  * Expansions are in box units (multipoles / h^|alpha|, locals * h^(|beta|+1));
  * comp 0 is phi, comps 1..3 are accel = -grad phi.  Returns FMM_ERR_ARG if
  * `n` (doubles) is too small.  Needs no GPU. */

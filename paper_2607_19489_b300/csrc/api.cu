@@ -1699,7 +1699,7 @@ fmm_status fmm_host_numerators(int q, const int64_t* u, int64_t* out) {
 }
 
 fmm_status fmm_host_table(int p, int which, double* out, int64_t n) {
-  if (p < 1 || p > 8 || !out || which < 0 || which > 8) return FMM_ERR_ARG;
+  if (p < 1 || p > 8 || !out || which < 0 || which > 9) return FMM_ERR_ARG;
   Tables t;
   t.build(p);
   const int nc = t.nc;
@@ -1713,9 +1713,9 @@ fmm_status fmm_host_table(int p, int which, double* out, int64_t n) {
     t.build_lattice();
     v = t.lattice;
   }
-  if (which == 8) {
+  if (which == 8 || which == 9) {
     t.build_dl2();
-    v = t.m2p2;
+    v = which == 8 ? t.m2p2 : t.p2pr;
   }
   if (which == 0) v = t.m2p;
   if (which == 1) v = t.m2l;

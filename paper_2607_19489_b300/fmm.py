@@ -149,9 +149,9 @@ def host_numerators(q: int, u) -> np.ndarray:
 _TABLE_SHAPES = {
     0: lambda nc: (256, 26 * 8 * nc), 1: lambda nc: (8 * nc, 26 * 8 * nc), 2: lambda nc: (343, nc, 4),
     3: lambda nc: (64, nc, 4), 4: lambda nc: (8, nc, nc), 5: lambda nc: (8, nc, nc), 6: lambda nc: (nc,),
-    7: lambda nc: (8 * nc, 8 * nc), 8: lambda nc: (2048, 26 * 8 * nc)}
+    7: lambda nc: (8 * nc, 8 * nc), 8: lambda nc: (2048, 26 * 8 * nc), 9: lambda nc: (256, 26 * 64)}
 TABLES = {"m2p": 0, "m2l": 1, "near": 2, "l2p": 3, "m2m": 4, "l2l": 5, "lattice_tensor": 6, "lattice": 7,
-          "m2p_dl2": 8}
+          "m2p_dl2": 8, "p2p_ring_dl2": 9}
 
 
 def host_table(p: int, which: str) -> np.ndarray:

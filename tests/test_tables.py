@@ -160,6 +160,38 @@ def test_m2p_delta_l2_table(p):
     assert checked > 20
 
 
+def test_p2p_ring_delta_l2_table():
+    """Delta l = 2: the near-field ring as point-mass sources (the 8 children of
+    each level l-1 source cell), level l-1 units, zero where the source cell
+    touches the target's parent F (Delta l = 1's near field)."""
+    T = fmm.host_table(4, "p2p_ring_dl2")
+    checked = 0
+    for f in (0, 5):
+        for t in (1, 6):
+            for qi in (0, 9, 13, 25):
+                for s in (0, 3, 7):
+                    q27 = NBR26[qi]
+                    n0 = (f * 8 + t) * 4
+                    block = T[n0:n0 + 4, (qi * 8 + s) * 8:(qi * 8 + s + 1) * 8]
+                    if np.abs(bits(f) - 2 * dq_of(q27) - bits(s)).max() <= 1:
+                        assert np.all(block == 0)
+                        continue
+                    x = bits(f) + (bits(t) + 0.5) / 2  # target centre, level l-1 cells
+                    m = np.random.default_rng(checked).uniform(0.5, 1.5, 8)
+                    phi, acc = 0.0, np.zeros(3)
+                    for kc in range(8):
+                        y = 2 * dq_of(q27) + bits(s) + (bits(kc) + 0.5) / 2
+                        r = x - y
+                        d = np.sqrt(r @ r)
+                        phi -= m[kc] / d
+                        acc -= m[kc] * r / d ** 3
+                    got = block @ m
+                    np.testing.assert_allclose(got[0], phi, rtol=1e-13)
+                    np.testing.assert_allclose(got[1:], acc, rtol=1e-12, atol=1e-14)
+                    checked += 1
+    assert checked > 10
+
+
 def test_lattice_tables(p):
     """Periodic boundaries: the library's lattice tensor (Taylor-mode Ewald) against
     the oracle's (radial recursion), and the level-1 operator against the oracle's
