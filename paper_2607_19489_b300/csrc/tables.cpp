@@ -441,7 +441,7 @@ std::vector<double> lattice_tensor(int q, const MultiIdx& mi) {
           e[i] = 1;
           t.c[mi.at(e[0], e[1], e[2])] += 2.0 * n3[i];
           e[i] = 2;
-          t.c[mi.at(e[0], e[1], e[2])] += 1.0;
+          if (q >= 2) t.c[mi.at(e[0], e[1], e[2])] += 1.0;  // |x|^2 (above degree 1 it exists)
         }
         Series f = compose(h, t);
         for (int k = 0; k < mi.size(); ++k) T.c[k] -= f.c[k];
@@ -454,9 +454,9 @@ std::vector<double> lattice_tensor(int q, const MultiIdx& mi) {
       if (m) fm *= m;
       h[m] = (2.0 * a / sqpi) * std::pow(-a * a, m) / (fm * (2 * m + 1));
     }
-    Series s2(mi, q);
-    s2.c[mi.at(2, 0, 0)] = s2.c[mi.at(0, 2, 0)] = s2.c[mi.at(0, 0, 2)] = 1.0;
     if (q >= 2) {
+      Series s2(mi, q);
+      s2.c[mi.at(2, 0, 0)] = s2.c[mi.at(0, 2, 0)] = s2.c[mi.at(0, 0, 2)] = 1.0;
       Series f = compose(h, s2);
       for (int k = 0; k < mi.size(); ++k) T.c[k] += f.c[k];
     } else {

@@ -226,3 +226,13 @@ def test_lattice_tables(p):
             ref = Lp * h1 ** (deg + 1)
             got = A[ct * nc:(ct + 1) * nc, cs * nc:(cs + 1) * nc] @ Mt
             np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_variant_tables_at_low_orders(order):
+    """The periodic and Delta l = 2 tables at the lowest orders (series of degree
+    1 have no |x|^2 term): finite, and the lattice tensor equal to the oracle's."""
+    for w in ("lattice", "m2p_dl2", "p2p_ring_dl2"):
+        assert np.isfinite(fmm.host_table(order, w)).all(), w
+    T = oracle.lattice_tensor(order)
+    assert np.max(np.abs(fmm.host_table(order, "lattice_tensor") - T) / np.maximum(np.abs(T), 1.0)) < 1e-12
