@@ -439,9 +439,9 @@ std::vector<double> lattice_tensor(int q, const MultiIdx& mi) {
         for (int i = 0; i < 3; ++i) {
           int e[3] = {0, 0, 0};
           e[i] = 1;
-          t.c[mi.at(e[0], e[1], e[2])] += 2.0 * n3[i];
+          if (q >= 1) t.c[mi.at(e[0], e[1], e[2])] += 2.0 * n3[i];  // terms beyond the series' degree drop
           e[i] = 2;
-          if (q >= 2) t.c[mi.at(e[0], e[1], e[2])] += 1.0;  // |x|^2 (above degree 1 it exists)
+          if (q >= 2) t.c[mi.at(e[0], e[1], e[2])] += 1.0;
         }
         Series f = compose(h, t);
         for (int k = 0; k < mi.size(); ++k) T.c[k] -= f.c[k];
