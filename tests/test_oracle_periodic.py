@@ -12,8 +12,10 @@ The lattice tensor of the root (the far images and the background) is pinned
 by closed forms: the Laplacian of the background in its second moments
 (T_200 = T_020 = T_002 = -4 pi / 3), harmonic traces at higher orders, zero odd
 moments, cubic symmetry, independence of the splitting parameter.  The
-periodic FMM then converges to the Ewald sum as p grows (unigrids and AMR),
-and the graded rule wraps around the box.
+periodic FMM then converges to the Ewald sum as p grows (unigrids and AMR,
+also with the refined regions moved across the box edge, where the Ewald sum
+itself is translation invariant and force-free in total), and the graded rule
+wraps around the box.
 """
 import itertools
 
@@ -134,3 +136,49 @@ def test_periodic_graded_rule_wraps():
     assert e.value.code == -2
     with pytest.raises(oracle.OracleError):
         oracle.solve_periodic(W.unigrid_plummer(2), 4)  # lmin >= 3
+
+
+def _shifted(h, shift):
+    """The same masses moved by `shift` cells of each level (periodic wrap), and
+    for each level the index map old -> new."""
+    g = h.copy()
+    maps = {}
+    for k, l in enumerate(h.levels):
+        n = 1 << l
+        s = np.asarray(shift, np.int64) * (1 << (l - h.lmin))
+        new = (h.ijk[k].astype(np.int64) + s) % n
+        g.ijk[k] = np.ascontiguousarray(new.astype(np.int32))
+        maps[l] = np.arange(h.n(l))
+    return g, maps
+
+
+def test_ewald_is_translation_invariant_and_force_free():
+    h = W.unigrid_plummer(3, noise=0.3, seed=7)
+    p0, a0 = oracle.ewald(h, alpha=7.0)
+    g, _ = _shifted(h, (3, 5, 1))  # any whole-cell shift of the torus
+    p1, a1 = oracle.ewald(g, alpha=7.0)
+    assert rel_rms(p1, p0) < 1e-12 and rel_rms(a1, a0) < 1e-12
+    m = h.mass[0]
+    tot = (m[:, None] * a0[3]).sum(0)  # Newton's third law; the background pulls every cell alike
+    assert np.abs(tot).max() < 1e-12 * (np.abs(m[:, None] * a0[3]).sum(0)).max()
+
+
+def test_periodic_fmm_across_the_box_edge():
+    """Moving every mass by half the box carries the refined regions across the
+    box edge (the lists and the graded rule then wrap through them).  The Ewald
+    sum moves with the masses exactly; the FMM's root expansion does not (the
+    root box does not map onto itself), so the shifted FMM is checked against
+    the shifted Ewald sum: of the same size as before the shift (masses near
+    the root's corners converge more slowly in its expansion) and falling
+    with p."""
+    h = W.random_amr(3, 5, seed=13)
+    sel = {l: np.arange(0, h.n(l), max(1, h.n(l) // 300)) for l in h.levels}
+    ep, ea = oracle.ewald(h, alpha=8.0, sel=sel)
+    e0 = rel_rms(oracle.solve_periodic(h, 6, sel=sel)[1], ea)
+    for shift in ((4, 0, 0), (0, 4, 4), (4, 4, 4)):
+        g, _ = _shifted(h, shift)
+        gp, ga = oracle.ewald(g, alpha=8.0, sel=sel)
+        assert rel_rms(ga, ea) < 1e-12 and rel_rms(gp, ep) < 1e-12, shift
+        errs = [rel_rms(oracle.solve_periodic(g, p, sel=sel)[1], ga) for p in (4, 6, 8)]
+        assert errs[1] < 3 * e0, (shift, e0, errs)
+        assert errs[2] < errs[1] < errs[0], (shift, errs)
