@@ -1,7 +1,8 @@
 """Periodic boundaries on the GPU against the oracle's periodic FMM.
 
 Unigrids of 8^3 to 32^3 (level-1 M2L and the lattice term carry most of the
-far field at 8^3), random graded AMR and a two-level workload whose refined
+far field at 8^3), random graded AMR (also moved by half the box, so that its
+refined regions cross the box edge) and a two-level workload whose refined
 block sits inside the box, in FP64, split-BF16 and TF32; a subcycle (lo >
 lmin); a mass update; the rejections.  FP64 has the plain relative bars; the
 reduced precisions measure errors against the field scale G M_total / L when
@@ -48,12 +49,22 @@ def _sel(h, n, seed):
     return {l: np.sort(rng.choice(h.n(l), min(n, h.n(l)), replace=False)) for l in h.levels if h.n(l)}
 
 
+def _across_edge():
+    """random_amr(3, 5, 13) moved by half the box: its refined regions cross the box edge."""
+    h = W.random_amr(3, 5, seed=13).copy()
+    for k, l in enumerate(h.levels):
+        s = 4 << (l - h.lmin)
+        h.ijk[k] = np.ascontiguousarray(((h.ijk[k].astype(np.int64) + s) % (1 << l)).astype(np.int32))
+    return h
+
+
 CASES = {
     "unigrid8": (lambda: W.unigrid_plummer(3, noise=0.3, seed=2), None),
     "unigrid16": (lambda: W.unigrid_plummer(4, noise=0.3, seed=3), None),
     "unigrid32": (lambda: W.unigrid_plummer(5, noise=0.3, seed=4), 2500),
     "amr_3_5": (lambda: W.random_amr(3, 5, seed=13), None),
     "twolevel16": (lambda: W.two_level_plummer(base=4, lo=4, hi=12, seed=3), None),
+    "amr_across_edge": (_across_edge, None),
 }
 
 
