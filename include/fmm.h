@@ -117,7 +117,8 @@ typedef struct {
                          host.  Needs lmin >= 3 (fmm_set_levels returns FMM_ERR_ARG),
                          the graded rule across the box edges (FMM_ERR_NOT_GRADED),
                          bottom mode FMM_BOTTOM_M2P and delta_l 1; fmm_solve_adjoint,
-                         fmm_direct_sum and the static unigrid entry return FMM_ERR_ARG. */
+                         fmm_direct_sum, fmm_set_drift and the static unigrid entry
+                         return FMM_ERR_ARG. */
 } fmm_config;
 
 /* Device memory for the library, supplied by the caller (for instance a caching
